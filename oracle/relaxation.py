@@ -1,0 +1,388 @@
+"""Subspace-correction relaxation: stars, patches, static condensation,
+Cholesky / ICC(0) patch factors, the p=1 coarse space, additive and hybrid
+compositions (Sec. 4).
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+Passages: stars and V_h|star (Sec. 4.1, fig. stars); PAFW and PH
+decompositions (Eqs. pafw, ph) and their algebraic forms (Eqs. asm-afw,
+asm-hiptmair); static condensation (Eqs. LDU, schur) and the SC forms
+(Eqs. sc-pafw, sc-ph, sc-asm-afw, sc-asm-hiptmair); ICC on the
+static-condensation pattern and edge-star Cholesky (Sec. 4.5); hybrid
+multigrid/Schwarz V(1,1) (Sec. 5).
+
+Readings where the paper is silent or ambiguous:
+* stars are taken over ALL vertices / edges / faces (Eq. pafw sums over
+  E^0), boundary entities included; Dirichlet DOFs are never in a patch;
+* a DOF belongs to the star of an entity when, in every direction, its
+  support lies in the cells around the entity and it vanishes on the star's
+  boundary (the support rule of Sec. 4.1);
+* patch ordering is nested dissection by entity: cell interiors, then faces,
+  then edges, then vertices, lexicographic in the global index within each
+  group; this fixes the ICC(0) factor;
+* ICC(0) keeps the entries of the patch matrix with
+  |S_ij| > 1e-12 sqrt(|S_ii S_jj|) (numerically zero couplings are not in
+  the static-condensation pattern); a non-positive pivot is a breakdown;
+* the coarse correction R_0^T A_0^{-1} R_0 acts on the full space; R_0^T is
+  the injection of V_{h,1} into V_{h,p} (dual functionals of Eq.
+  fdmdualbasis applied to the p=1 basis) and A_0 is a^k rediscretised at p=1
+  with its own ceil(3*2/2)=3-point GLL rule;
+* in the SC forms the interior solve uses the auxiliary operator's P_II and
+  the harmonic extension uses its P_GI (the preconditioner is built from P);
+* the H(curl) Hiptmair potential operator is B = D^T P^1 D, which equals the
+  H(grad) auxiliary operator with mass 0 and stiffness beta; D-tilde is the
+  discrete gradient restricted to interface rows and columns;
+* hybrid V(1,1): pre-smooth omega*M^{-1}, exact coarse correction,
+  post-smooth omega*M^{-1}, with M^{-1} the additive fine-level relaxation.
+
+Pins: a dense patch Cholesky solve equals numpy.linalg.solve; ICC(0) with
+the full pattern equals Cholesky; the SC identity A^{-1} = R_I^T A_II^{-1}
+R_I + R_G^T S^{-1} R_G and R_G A R_I^T = 0 (Eq. schur); Galerkin
+R_0 A R_0^T = A_0 on Cartesian cells; hybrid V(1,1) with p = 1 converges in
+one CG iteration (tab. hgrad-iter, l = 0 entries "1/1").
+"""
+
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from .basis import FDM1D
+from .discretization import Lattice, Problem
+
+ICC_DROP = 1e-12
+
+
+# ---------------------------------------------------------------------------
+# stars and patches
+# ---------------------------------------------------------------------------
+class DofGeometry:
+    """Per lattice entry: lattice coordinates and which directions are
+    'vertex-type' (an s-type index on a mesh plane)."""
+
+    def __init__(self, lat: Lattice):
+        self.lat = lat
+        comp, g1, g2, g3 = lat.coords()
+        self.comp = comp
+        self.G = np.stack([g1, g2, g3], 1)
+        p = lat.p
+        stype = np.array([[t[d] == "s" for d in range(3)] for t in lat.types])
+        self.vtx = stype[comp] & (self.G % p == 0)
+        self.cell = self.G // p              # owning cell for non-vertex type
+        self.plane = self.G // p             # mesh plane for vertex type
+        self.dim = 3 - self.vtx.sum(1)       # dimension of the entity the DOF lives on
+
+    def star(self, corner, span, candidates):
+        """DOFs (among `candidates`, lattice indices) supported in the star of
+        the entity with lower corner `corner` spanning directions `span`."""
+        c = candidates
+        ok = np.ones(len(c), bool)
+        for d in range(3):
+            a = corner[d]
+            vt = self.vtx[c, d]
+            if d in span:
+                ok &= (~vt) & (self.cell[c, d] == a)
+            else:
+                ok &= (vt & (self.plane[c, d] == a)) | \
+                      ((~vt) & ((self.cell[c, d] == a - 1) | (self.cell[c, d] == a)))
+        sel = c[ok]
+        order = np.lexsort((sel, -self.dim[sel]))
+        return sel[order]
+
+
+def entities(n, span):
+    """Lower corners of all entities spanning `span` on an n1 x n2 x n3 mesh."""
+    rng = [range(n[d]) if d in span else range(n[d] + 1) for d in range(3)]
+    out = []
+    for a3 in rng[2]:
+        for a2 in rng[1]:
+            for a1 in rng[0]:
+                out.append((a1, a2, a3))
+    return out
+
+
+def patch_lists(lat: Lattice, span, candidates):
+    """Patches (lattice indices, nested-dissection order) of every entity."""
+    geo = DofGeometry(lat)
+    pats = []
+    for a in entities(lat.n, span):
+        s = geo.star(a, span, candidates)
+        if len(s):
+            pats.append(s)
+    return pats
+
+
+# ---------------------------------------------------------------------------
+# patch factorizations
+# ---------------------------------------------------------------------------
+def icc0(Adense: np.ndarray, drop: float = ICC_DROP) -> np.ndarray:
+    """Incomplete Cholesky with zero fill-in on the pattern of Adense
+    (right-looking elimination restricted to the pattern)."""
+    A = np.array(Adense, float, copy=True)
+    n = A.shape[0]
+    d = np.sqrt(np.abs(np.diag(A)))
+    mask = np.abs(A) > drop * np.outer(d, d)
+    np.fill_diagonal(mask, True)
+    A[~mask] = 0.0
+    for k in range(n):
+        if A[k, k] <= 0.0:
+            raise np.linalg.LinAlgError(f"ICC(0) breakdown at pivot {k}")
+        A[k, k] = np.sqrt(A[k, k])
+        col = k + 1 + np.flatnonzero(mask[k + 1:, k])
+        A[col, k] /= A[k, k]
+        if len(col):
+            upd = np.outer(A[col, k], A[col, k]) * mask[np.ix_(col, col)]
+            A[np.ix_(col, col)] -= upd
+    return np.tril(A)
+
+
+def cholesky(Adense: np.ndarray) -> np.ndarray:
+    return np.linalg.cholesky(Adense)
+
+
+class PatchSolver:
+    """sum_j R_j^T (L_j L_j^T)^{-1} R_j over patches of a matrix (free DOF
+    numbering)."""
+
+    def __init__(self, M: sp.csr_matrix, patches, factor: str):
+        self.patches = patches
+        self.L = []
+        M = M.tocsr()
+        for idx in patches:
+            Aj = M[idx][:, idx].toarray()
+            self.L.append(icc0(Aj) if factor == "icc" else cholesky(Aj))
+
+    def apply(self, r):
+        z = np.zeros_like(r)
+        for idx, L in zip(self.patches, self.L):
+            y = scipy.linalg.solve_triangular(L, r[idx], lower=True)
+            z[idx] += scipy.linalg.solve_triangular(L.T, y, lower=False)
+        return z
+
+
+# ---------------------------------------------------------------------------
+# coarse space
+# ---------------------------------------------------------------------------
+def prolongation(lat_f: Lattice, lat_c: Lattice) -> sp.csr_matrix:
+    """Injection V_{h,1} -> V_{h,p} on the full lattices (fine x coarse)."""
+    e = FDM1D(lat_f.p)
+    Js, Jr = e.injection_from_p1()
+    J = {"s": Js, "r": Jr}
+    blocks = []
+    for t in lat_f.types:
+        blocks.append(np.kron(J[t[2]], np.kron(J[t[1]], J[t[0]])))
+    Jloc = scipy.linalg.block_diag(*blocks)
+    entries = {}
+    for cell, _ in lat_f.cells():
+        fd = lat_f.cell_dofs(cell)
+        cd = lat_c.cell_dofs(cell)
+        for i in range(len(fd)):
+            for j in range(len(cd)):
+                v = Jloc[i, j]
+                if v != 0.0:
+                    entries[(int(fd[i]), int(cd[j]))] = v
+    r = np.array([k[0] for k in entries], int)
+    c = np.array([k[1] for k in entries], int)
+    v = np.array(list(entries.values()))
+    return sp.coo_matrix((v, (r, c)), shape=(lat_f.size, lat_c.size)).tocsr()
+
+
+class Coarse:
+    """R_0^T A_0^{-1} R_0 with A_0 the p=1 rediscretisation (Eq. asm-afw)."""
+
+    def __init__(self, problem: Problem):
+        X = problem.mesh.X
+        self.cp = Problem(problem.k, problem.n, 1, X, problem.alpha, problem.beta)
+        P0 = prolongation(problem.lat, self.cp.lat)
+        self.R0T = P0[problem.free][:, self.cp.free].tocsr()
+        self.A0 = self.cp.A_free().toarray()
+        self.A0_chol = scipy.linalg.cho_factor(self.A0, lower=True)
+
+    def apply(self, r):
+        c = self.R0T.T @ r
+        return self.R0T @ scipy.linalg.cho_solve(self.A0_chol, c)
+
+
+# ---------------------------------------------------------------------------
+# static condensation
+# ---------------------------------------------------------------------------
+def interior_mask(lat: Lattice, free):
+    """Free DOFs interior to a cell: no s-type index on a mesh plane."""
+    geo = DofGeometry(lat)
+    return ~geo.vtx[free].any(1)
+
+
+class Condensed:
+    """Block split of a free-DOF matrix P into interior I and interface G,
+    with S = P_GG - P_GI P_II^{-1} P_IG (Eqs. LDU, schur)."""
+
+    def __init__(self, P: sp.csr_matrix, lat: Lattice, free):
+        self.free = free
+        imask = interior_mask(lat, free)
+        self.I = np.flatnonzero(imask)
+        self.G = np.flatnonzero(~imask)
+        P = P.tocsc()
+        self.PII = P[self.I][:, self.I].tocsc()
+        self.PIG = P[self.I][:, self.G].tocsc()
+        self.PGI = P[self.G][:, self.I].tocsr()
+        PGG = P[self.G][:, self.G].tocsr()
+        self.PII_lu = spla.splu(self.PII)
+        X = spla.spsolve(self.PII, self.PIG)
+        X = sp.csr_matrix(X) if not sp.issparse(X) else X
+        self.S = (PGG - self.PGI @ X).tocsr()
+
+    def condense(self, r):
+        """(y_I, R_G r) with y_I = P_II^{-1} r_I."""
+        yI = self.PII_lu.solve(r[self.I])
+        return yI, r[self.G] - self.PGI @ yI
+
+    def expand(self, yI, zG):
+        """z = R_I^T y_I + R_G^T z_G, written as [y_I - P_II^{-1} P_IG z_G; z_G]."""
+        z = np.zeros(len(self.free))
+        z[self.I] = yI - self.PII_lu.solve(self.PIG @ zG)
+        z[self.G] = zG
+        return z
+
+
+# ---------------------------------------------------------------------------
+# preconditioners (free-DOF numbering)
+# ---------------------------------------------------------------------------
+def free_position(free, size):
+    pos = -np.ones(size, int)
+    pos[free] = np.arange(len(free))
+    return pos
+
+
+class PAFW:
+    """Non-condensed PAFW, Eq. asm-afw: sum over vertex stars of A_v^{-1}
+    (exact Cholesky or ICC(0) of R_v M R_v^T), optionally plus the coarse
+    correction."""
+
+    def __init__(self, problem: Problem, M=None, factor="chol", coarse=True):
+        self.problem = problem
+        free = problem.free
+        M = problem.A_free() if M is None else M
+        pos = free_position(free, problem.lat.size)
+        pats = patch_lists(problem.lat, (), free)
+        self.patches = PatchSolver(M, [pos[s] for s in pats], factor)
+        self.coarse = Coarse(problem) if coarse else None
+
+    def smooth(self, r):
+        return self.patches.apply(r)
+
+    def apply(self, r):
+        z = self.smooth(r)
+        if self.coarse is not None:
+            z += self.coarse.apply(r)
+        return z
+
+
+class SCPAFW:
+    """SC-PAFW (Eqs. sc-pafw, sc-asm-afw) on the auxiliary operator P:
+    interior solve + harmonic extension of sum_v S_v^{-1}, plus coarse."""
+
+    def __init__(self, problem: Problem, P_free, factor="icc", coarse=True):
+        self.problem = problem
+        free = problem.free
+        self.sc = Condensed(P_free, problem.lat, free)
+        pos = free_position(free[self.sc.G], problem.lat.size)
+        pats = patch_lists(problem.lat, (), free[self.sc.G])
+        self.patches = PatchSolver(self.sc.S, [pos[s] for s in pats], factor)
+        self.coarse = Coarse(problem) if coarse else None
+
+    def smooth(self, r):
+        yI, rG = self.sc.condense(r)
+        return self.sc.expand(yI, self.patches.apply(rG))
+
+    def apply(self, r):
+        z = self.smooth(r)
+        if self.coarse is not None:
+            z += self.coarse.apply(r)
+        return z
+
+
+def discrete_gradient(lat0: Lattice, lat1: Lattice) -> sp.csr_matrix:
+    """D: V^0 lattice -> V^1 lattice (full lattices), cellwise D-hat_3d."""
+    from .discretization import dhat_3d
+    Dl = dhat_3d(0, FDM1D(lat0.p))
+    entries = {}
+    for cell, _ in lat0.cells():
+        d0 = lat0.cell_dofs(cell)
+        d1 = lat1.cell_dofs(cell)
+        nz = np.nonzero(Dl)
+        for i, j in zip(*nz):
+            entries[(int(d1[i]), int(d0[j]))] = Dl[i, j]
+    r = np.array([k[0] for k in entries], int)
+    c = np.array([k[1] for k in entries], int)
+    v = np.array(list(entries.values()))
+    return sp.coo_matrix((v, (r, c)), shape=(lat1.size, lat0.size)).tocsr()
+
+
+class SCPH:
+    """SC-PH for H(curl) (Eqs. sc-ph, sc-asm-hiptmair): edge-star patches of
+    S (exact Cholesky), plus D-tilde (sum_v B-tilde_v^{-1}) D-tilde^T with
+    vertex-star ICC(0) patches of the potential Schur complement, plus the
+    interior solve, harmonic extension and coarse correction."""
+
+    def __init__(self, problem: Problem, P_free, edge_factor="chol",
+                 vertex_factor="icc", coarse=True):
+        from .auxiliary import assemble_aux
+        assert problem.k == 1
+        self.problem = problem
+        lat1 = problem.lat
+        free1 = problem.free
+        self.sc = Condensed(P_free, lat1, free1)
+        G1 = free1[self.sc.G]
+        pos1 = free_position(G1, lat1.size)
+        self.edge = []
+        for m in range(3):
+            pats = patch_lists(lat1, (m,), G1)
+            self.edge.append(PatchSolver(self.sc.S, [pos1[s] for s in pats],
+                                         edge_factor))
+        # potential space
+        p0 = Problem(0, problem.n, problem.p, problem.mesh.X,
+                     problem.alpha, problem.beta)
+        B = assemble_aux(p0, mass_coef=np.zeros_like(problem.beta),
+                         stiff_coef=problem.beta)
+        free0 = p0.free
+        self.sc0 = Condensed(B[free0][:, free0].tocsr(), p0.lat, free0)
+        G0 = free0[self.sc0.G]
+        pos0 = free_position(G0, p0.lat.size)
+        pats0 = patch_lists(p0.lat, (), G0)
+        self.vertex = PatchSolver(self.sc0.S, [pos0[s] for s in pats0],
+                                  vertex_factor)
+        D = discrete_gradient(p0.lat, lat1)
+        self.Dt = D[G1][:, G0].tocsr()
+        self.coarse = Coarse(problem) if coarse else None
+
+    def interface(self, rG):
+        z = np.zeros_like(rG)
+        for ps in self.edge:
+            z += ps.apply(rG)
+        z += self.Dt @ self.vertex.apply(self.Dt.T @ rG)
+        return z
+
+    def smooth(self, r):
+        yI, rG = self.sc.condense(r)
+        return self.sc.expand(yI, self.interface(rG))
+
+    def apply(self, r):
+        z = self.smooth(r)
+        if self.coarse is not None:
+            z += self.coarse.apply(r)
+        return z
+
+
+class Hybrid:
+    """Hybrid multigrid/Schwarz V(1,1) (Sec. 5): smoother omega*M^{-1}
+    (additive fine-level relaxation), exact coarse solve in between."""
+
+    def __init__(self, A, relax, coarse: Coarse, omega: float):
+        self.A, self.relax, self.coarse, self.omega = A, relax, coarse, omega
+
+    def apply(self, r):
+        z = self.omega * self.relax.smooth(r)
+        z = z + self.coarse.apply(r - self.A @ z)
+        return z + self.omega * self.relax.smooth(r - self.A @ z)

@@ -1,0 +1,20 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+    config.addinivalue_line("markers", "slow: oracle runs of more than a few seconds")
+
+
+@pytest.fixture(scope="session")
+def lib():
+    """The CUDA path's C-ABI library (built in-tree by __graft_entry__.build)."""
+    from paper_2211_14284_gb300 import rm
+    return rm.load()

@@ -1,0 +1,214 @@
+"""Pins of the oracle's auxiliary operator, patches, static condensation,
+coarse space, compositions and Krylov solver (Sec. 3.2, 4, 5.1)."""
+
+import numpy as np
+import pytest
+import scipy.linalg
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from oracle.auxiliary import assemble_aux
+from oracle.discretization import Lattice, Problem
+from oracle.krylov import pcg
+from oracle.relaxation import (PAFW, SCPAFW, SCPH, Coarse, Condensed,
+                               DofGeometry, Hybrid, PatchSolver, cholesky,
+                               icc0, patch_lists, prolongation)
+from paper_2211_14284_gb300 import inputs
+
+
+def _problem(k, n, p, perturb=0.0, alpha=1.0, beta=1.0, seed=1):
+    X = inputs.vertices(n, perturb=perturb, seed=seed)
+    return Problem(k, n, p, X, alpha, beta)
+
+
+# -- auxiliary operator ------------------------------------------------------
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_aux_equals_A_on_cartesian(k):
+    """P = A on Cartesian cells with cellwise-constant coefficients: the
+    broken mass matrix is diagonal there (Sec. 3.2)."""
+    n, p = 2, 3
+    al = inputs.loguniform_coefficient(n, 0.1, 10, seed=2)
+    be = inputs.loguniform_coefficient(n, 0.1, 10, seed=3)
+    pr = _problem(k, n, p, alpha=al, beta=be)
+    A = pr.assemble()
+    P = assemble_aux(pr)
+    assert abs(A - P).max() < 1e-12 * abs(A).max()
+
+
+@pytest.mark.parametrize("k,bound", [(0, 1), (1, 3), (2, 3)])
+def test_aux_distorted_spd_and_sparse(k, bound):
+    """On distorted cells P is SPD, differs from A, and its interior block
+    keeps the Cartesian sparsity (Remark after Eq. schur)."""
+    n, p = 2, 3
+    pr = _problem(k, n, p, perturb=0.15, seed=4)
+    A = pr.A_free()
+    P = assemble_aux(pr)[pr.free][:, pr.free]
+    assert abs(P - P.T).max() < 1e-13 * abs(P).max()
+    assert np.linalg.eigvalsh(P.toarray()).min() > 0
+    assert abs(A - P).max() > 1e-6 * abs(A).max()
+    sc = Condensed(P, pr.lat, pr.free)
+    PII = sc.PII.toarray()
+    nnz = (np.abs(PII) > 1e-14 * np.abs(PII).max()).sum(1)
+    assert nnz.max() <= bound
+
+
+# -- patches -----------------------------------------------------------------
+def test_star_sizes_closed_form():
+    """Interior-vertex star sizes: Q_p (2p-1)^3 DOFs, of which
+    (2p-1)^3 - 8(p-1)^3 on the interface; NCE_p 3*2p(2p-1)^2."""
+    p, n = 4, 3
+    for k, full in [(0, (2 * p - 1) ** 3), (1, 3 * 2 * p * (2 * p - 1) ** 2)]:
+        lat = Lattice(k, n, p)
+        free = lat.free()
+        geo = DofGeometry(lat)
+        s = geo.star((1, 1, 1), (), free)
+        assert len(s) == full
+    lat = Lattice(0, n, p)
+    free = lat.free()
+    geo = DofGeometry(lat)
+    G = free[geo.vtx[free].any(1)]
+    assert len(geo.star((1, 1, 1), (), G)) == (2 * p - 1) ** 3 - 8 * (p - 1) ** 3
+    # p = 7: 469 interface DOFs per interior vertex
+    assert (13 ** 3 - 8 * 6 ** 3) == 469
+
+
+def test_patches_cover_every_free_dof():
+    for k in (0, 1, 2):
+        lat = Lattice(k, 3, 3)
+        free = lat.free()
+        pats = patch_lists(lat, (), free)
+        cover = np.zeros(lat.size, int)
+        for s in pats:
+            cover[s] += 1
+        assert np.all(cover[free] >= 1)
+        assert cover.max() <= 8
+
+
+def test_icc_full_pattern_is_cholesky():
+    rng = np.random.default_rng(0)
+    M = rng.standard_normal((30, 30))
+    A = M @ M.T + 30 * np.eye(30)
+    assert np.allclose(icc0(A), np.linalg.cholesky(A), atol=1e-12)
+
+
+def test_icc_zero_fill():
+    """ICC(0) keeps the pattern: L has no entry where A is zero."""
+    A = np.diag(np.full(6, 4.0)) + np.diag(np.full(5, -1.0), 1) + np.diag(np.full(5, -1.0), -1)
+    A[0, 5] = A[5, 0] = -1.0
+    L = icc0(A)
+    assert np.all(L[np.tril(np.abs(A) == 0)] == 0)
+    # tridiagonal part with a corner: not exact, but close
+    assert np.abs(L @ L.T - A)[np.abs(A) > 0].max() < 1e-12
+
+
+def test_patch_solve_equals_dense_solve():
+    rng = np.random.default_rng(1)
+    M = rng.standard_normal((12, 12))
+    A = sp.csr_matrix(M @ M.T + 12 * np.eye(12))
+    ps = PatchSolver(A, [np.arange(12)], "chol")
+    r = rng.standard_normal(12)
+    assert np.allclose(ps.apply(r), np.linalg.solve(A.toarray(), r), atol=1e-12)
+
+
+def test_edge_star_blocks():
+    """Edge-star interface patches of H(curl) split into p decoupled blocks
+    on a Cartesian mesh (Sec. 4.5, fig. spy_feec(e))."""
+    p = 4
+    pr = _problem(1, 3, p)
+    P = assemble_aux(pr)[pr.free][:, pr.free]
+    sc = Condensed(P, pr.lat, pr.free)
+    G1 = pr.free[sc.G]
+    pos = -np.ones(pr.lat.size, int)
+    pos[G1] = np.arange(len(G1))
+    geo = DofGeometry(pr.lat)
+    s = geo.star((1, 1, 1), (0,), G1)
+    Se = sc.S[pos[s]][:, pos[s]]
+    Se = sp.csr_matrix(np.where(np.abs(Se.toarray()) > 1e-12 * abs(Se).max(), 1.0, 0.0))
+    ncomp, _ = sp.csgraph.connected_components(Se)
+    assert ncomp == p
+
+
+# -- static condensation ----------------------------------------------------
+@pytest.mark.parametrize("k", [0, 1])
+def test_schur_identity(k):
+    """A^{-1} = R_I^T A_II^{-1} R_I + R_G^T S^{-1} R_G (Eq. schur) with
+    R_G = [-A_GI A_II^{-1}, I], and R_G A R_I^T = 0."""
+    pr = _problem(k, 2, 3)
+    A = pr.A_free()
+    sc = Condensed(A, pr.lat, pr.free)
+    r = np.random.default_rng(2).standard_normal(A.shape[0])
+    yI, rG = sc.condense(r)
+    zG = np.linalg.solve(sc.S.toarray(), rG)
+    z = sc.expand(yI, zG)
+    assert np.allclose(z, spla.spsolve(A.tocsc(), r), rtol=1e-10, atol=1e-12)
+    # R_G A R_I^T: columns of A at interior DOFs, condensed
+    AI = A[:, sc.I].toarray()
+    RG = np.hstack([-(sc.PGI @ np.linalg.inv(sc.PII.toarray())), np.eye(len(sc.G))])
+    perm = np.r_[sc.I, sc.G]
+    assert np.abs(RG @ AI[perm]).max() < 1e-12 * abs(A).max()
+
+
+# -- coarse space -----------------------------------------------------------
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_galerkin_coarse_equals_rediscretised(k):
+    """On Cartesian cells R_0 A R_0^T = A_0 (V_{h,1} is a subspace and both
+    quadratures are exact)."""
+    pr = _problem(k, 2, 3, alpha=2.0, beta=0.5)
+    c = Coarse(pr)
+    G = c.R0T.T @ pr.A_free() @ c.R0T
+    assert abs(G - c.A0).max() < 1e-12 * abs(c.A0).max()
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+@pytest.mark.parametrize("perturb", [0.0, 0.15])
+def test_hybrid_p1_one_iteration(k, perturb):
+    """p = 1: the p-coarse space is the whole space, so hybrid V(1,1) is an
+    exact solve and CG converges in one iteration (tab. hgrad-iter,
+    hcurl-iter, hdiv-iter: l = 0 entries 1/1 and 2/2 are for exact coarse
+    solves on the paper's meshes)."""
+    pr = _problem(k, 3, 1, perturb=perturb)
+    A = pr.A_free()
+    relax = PAFW(pr, factor="chol", coarse=False)
+    H = Hybrid(A, relax, Coarse(pr), omega=1.0 / 8)
+    b = inputs.normal_rhs(pr.lat.size, 5)[pr.free]
+    _, info = pcg(A, b, H.apply, rtol=1e-10)
+    assert info["iterations"] == 1
+
+
+def test_exact_preconditioner_one_iteration():
+    pr = _problem(0, 2, 3)
+    A = pr.A_free()
+    lu = spla.splu(A.tocsc())
+    b = inputs.normal_rhs(pr.lat.size, 6)[pr.free]
+    x, info = pcg(A, b, lu.solve, rtol=1e-12)
+    assert info["iterations"] == 1
+    x2, info2 = pcg(A, b, None, rtol=1e-13, maxit=5000)
+    assert np.allclose(x2, lu.solve(b), rtol=1e-9)
+
+
+# -- iteration counts -------------------------------------------------------
+@pytest.mark.slow
+def test_iterations_flat_in_p():
+    """CG iteration counts of additive two-level PAFW do not grow with p
+    (tab. hgrad-iter: 14, 12, 11, 10 Cartesian chol counts for p=3..15)."""
+    its = []
+    for p in (2, 3, 4, 5):
+        pr = _problem(0, 3, p)
+        A = pr.A_free()
+        M = PAFW(pr)
+        b = inputs.normal_rhs(pr.lat.size, 7)[pr.free]
+        _, info = pcg(A, b, M.apply, rtol=1e-8)
+        its.append(info["iterations"])
+    assert max(its) - min(its) <= 4, its
+    assert its[-1] <= its[0] + 2, its
+
+
+@pytest.mark.slow
+def test_scph_converges_hcurl():
+    pr = _problem(1, 3, 3, perturb=0.1)
+    A = pr.A_free()
+    P = assemble_aux(pr)[pr.free][:, pr.free]
+    M = SCPH(pr, P)
+    b = inputs.normal_rhs(pr.lat.size, 8)[pr.free]
+    x, info = pcg(A, b, M.apply, rtol=1e-8)
+    assert info["converged"] and info["iterations"] < 60, info["iterations"]
