@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Benchmark: DOFs/s to l2 relative residual 1e-8 on one GB300.
+
+Workload (one step = the whole hot path over one batch of input): the
+distorted-mesh Riesz maps on an 8x8x8 hexahedral mesh of the unit cube with
+10% random interior-vertex perturbation, p = 7, alpha = beta = 1, N(0,1)
+right-hand sides:
+  * H(grad): 185,193 lattice DOFs, SC-PAFW vertex stars with ICC(0) on the
+    static-condensation pattern of the auxiliary operator + P1 coarse;
+  * H(curl): 545,832 lattice DOFs, SC-PH (edge-star Cholesky + vertex-star
+    ICC(0) potential patches) + P1 coarse.
+One step solves both from a zero initial guess.  The headline variant is
+the mixed-precision one (FP32 preconditioner inside FP64 flexible CG); the
+plain FP64 solver is timed alongside ("variants").
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+--impl reference times the CPU oracle (plain FP64 NumPy/SciPy) on a bounded
+sample of the same workload (3x3x3 mesh, same p, perturbation and solvers).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DOFs/s to rel. residual 1e-8: mixed/batched/learned vs plain FP64, 1 GB300"
+N_CELLS, DEGREE, PERTURB = 8, 7, 0.1
+WORKLOAD = "Riesz maps H(grad)+H(curl), 8x8x8 hex, 10% interior-vertex perturbation, p=7"
+SPACES = [
+    ("hgrad", 0, dict(static_condensation=1, factor=1)),
+    ("hcurl", 1, dict(static_condensation=1, factor=1, decomposition=1)),
+]
+VARIANTS = {"fp64": dict(precision=0, flexible=0), "mixed_fp32": dict(precision=1, flexible=1)}
+HEADLINE = "mixed_fp32"
+FP64_PEAK_TFLOPS = 1.20   # measured FP64 FMA throughput of this GB300 pool (FP64 DFMA probe)
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+def apply_flops(k: int, p: int) -> float:
+    """Algorithmic FP64 flops of one sum-factorised apply on one cell:
+    interpolation to and from the q^3 GLL points for V^k and V^{k+1}
+    (three 1D contractions each way), D-hat and D-hat^T, the pointwise
+    metric products, and the geometric factors once per point (150 flops)."""
+    q = (3 * (p + 1) + 1) // 2
+    types = {0: ["sss"], 1: ["rss", "srs", "ssr"], 2: ["srr", "rsr", "rrs"], 3: ["rrr"]}
+    fma = 0
+    for kk in (k, k + 1):
+        for t in types[kk]:
+            l = [p + 1 if c == "s" else p for c in t]
+            fwd = q * l[0] * l[1] * l[2] + q * q * l[1] * l[2] + q ** 3 * l[2]
+            fma += 2 * fwd
+        vec = len(types[kk]) == 3
+        fma += q ** 3 * (9 if vec else 1)
+    nterms = {0: 3, 1: 6, 2: 3}[k]
+    fma += 2 * nterms * p * (p + 1) * (p + 1) * (p + 1)   # D-hat and its transpose
+    return 2.0 * fma + 150.0 * q ** 3
+
+
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax = float(f[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except Exception:
+            return None
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2211_14284_gb300 import inputs
+    from paper_2211_14284_gb300.rm import Solver
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+    n, p = N_CELLS, DEGREE
+    X = inputs.vertices(n, perturb=PERTURB, seed=2)
+    al = inputs.constant_coefficient(n)
+    be = inputs.constant_coefficient(n)
+
+    solvers = {}
+    t0 = time.time()
+    for vname, vopt in VARIANTS.items():
+        for sname, k, sopt in SPACES:
+            solvers[(vname, sname)] = Solver(k, n, p, vertices=X, alpha=al, beta=be,
+                                             stream=stream, rtol=1e-8, max_it=1000,
+                                             profile=1, **sopt, **vopt)
+    setup_s = time.time() - t0
+    sizes = {sname: solvers[(HEADLINE, sname)].size for sname, _, _ in SPACES}
+    dofs = sum(sizes.values())
+    bh = {sname: torch.tensor(inputs.normal_rhs(sizes[sname], 100 + k + 7 * rank),
+                              dtype=torch.float64).pin_memory() for sname, k, _ in SPACES}
+    bd = {s: bh[s].cuda() for s in bh}
+    xd = {s: torch.zeros_like(bd[s]) for s in bd}
+    xh = {s: torch.zeros_like(bh[s]).pin_memory() for s in bh}
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def one_step(vname, e2e, stats):
+        for sname, _, _ in SPACES:
+            if e2e:
+                bd[sname].copy_(bh[sname], non_blocking=True)
+            xd[sname].zero_()
+            info = solvers[(vname, sname)].solve(bd[sname], xd[sname])
+            if info["status"] != "RM_OK" or not info["rel_res_l2"] <= 1e-8:
+                raise RuntimeError(f"{vname}/{sname} did not converge: {info}")
+            if e2e:
+                xh[sname].copy_(xd[sname], non_blocking=True)
+            stats.append((sname, info))
+
+    def timed(vname, e2e, steps, warmup):
+        for _ in range(warmup):
+            one_step(vname, e2e, [])
+        barrier()
+        total_ms = 0.0
+        stats = []
+        for _ in range(steps):
+            flush.fill_(1.0)                           # evict the working set from L2
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            one_step(vname, e2e, stats)
+            ev1.record(stream)
+            ev1.synchronize()
+            total_ms += ev0.elapsed_time(ev1)
+        barrier()
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([total_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        return total_ms, stats
+
+    results = {}
+    with ClockSampler(local) as clk:
+        for vname in VARIANTS:
+            ms, stats = timed(vname, False, args.steps, args.warmup)
+            results[vname] = (ms, stats)
+    clocks = clk.summary()
+    e2e_ms, _ = timed(HEADLINE, True, args.steps, max(1, args.warmup // 2))
+
+    def summarise(vname):
+        ms, stats = results[vname]
+        it = {s: [i["iterations"] for (sn, i) in stats if sn == s] for s, _, _ in SPACES}
+        return {
+            "value": world * args.steps * dofs / (ms / 1e3),
+            "ms_per_step": ms / args.steps,
+            "iterations": {s: int(statistics.median(v)) for s, v in it.items()},
+            "solve_ms": {s: statistics.median([i["solve_ms"] for (sn, i) in stats if sn == s])
+                         for s, _, _ in SPACES},
+        }
+
+    head = summarise(HEADLINE)
+    ms_h, stats_h = results[HEADLINE]
+    launches = sum(i["kernel_launches"] for (_, i) in stats_h)
+    # dominant kernel: the operator apply (FP64, ALU-bound); its average
+    # duration over the timed region, from the solver's own CUDA events
+    app_ms = sum(i["apply_ms"] for (_, i) in stats_h)
+    app_calls = sum(i["apply_calls"] for (_, i) in stats_h)
+    flops = 0.0
+    for sname, k, _ in SPACES:
+        calls = sum(i["apply_calls"] for (sn, i) in stats_h if sn == sname)
+        flops += calls * apply_flops(k, DEGREE) * N_CELLS ** 3
+    achieved = flops / (app_ms / 1e3) / 1e12
+    roof = {"bound": "alu", "kernel": "apply_kernel (FP64 sum-factorised operator)",
+            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64)",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "avg_launch_ms": app_ms / max(app_calls, 1),
+            "time_share_of_step": app_ms / ms_h}
+    line = {
+        "metric": METRIC,
+        "value": head["value"],
+        "unit": "DOFs/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": head["ms_per_step"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64 CG + f32 preconditioner",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice_dofs": dofs,
+                   "lattice_dofs_per_space": sizes, "rtol": 1e-8,
+                   "variant": HEADLINE, "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": "independent replicas" if world > 1 else "1 GPU",
+                   "iterations": head["iterations"], "setup_s": setup_s},
+        "e2e": {"value": world * args.steps * dofs / (e2e_ms / 1e3), "unit": "DOFs/s",
+                "h2d_bytes_per_step": 8 * dofs, "d2h_bytes_per_step": 8 * dofs},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "variants": {v: summarise(v) for v in VARIANTS},
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, budget_s=30.0)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+def _oracle_sample():
+    """The oracle's solvers on the 3x3x3 sample of the workload (same p,
+    perturbation, coefficients, preconditioners)."""
+    from oracle.auxiliary import assemble_aux
+    from oracle.discretization import Problem
+    from oracle.relaxation import SCPAFW, SCPH
+    from paper_2211_14284_gb300 import inputs
+    n = 3
+    X = inputs.vertices(n, perturb=PERTURB, seed=2)
+    al = inputs.constant_coefficient(n)
+    be = inputs.constant_coefficient(n)
+    out = []
+    for sname, k, _ in SPACES:
+        pr = Problem(k, n, DEGREE, X, al, be)
+        A = pr.A_free()
+        P = assemble_aux(pr)[pr.free][:, pr.free]
+        M = SCPAFW(pr, P, factor="icc") if k == 0 else SCPH(pr, P)
+        b = inputs.normal_rhs(pr.lat.size, 100 + k)[pr.free]
+        out.append((sname, pr.lat.size, A, M, b))
+    return out
+
+
+def cpu_baseline(args, budget_s=30.0):
+    from oracle.krylov import pcg
+    cores = len(os.sched_getaffinity(0))
+    sample = _oracle_sample()
+    dofs = sum(s[1] for s in sample)
+    t_tot, steps = 0.0, 0
+    while True:
+        t0 = time.time()
+        for (_, _, A, M, b) in sample:
+            _, info = pcg(A, b, M.apply, rtol=1e-8, flexible=True)
+        t_tot += time.time() - t0
+        steps += 1
+        if t_tot > budget_s / 3 or steps >= 3:
+            break
+    return {"value": steps * dofs / t_tot, "unit": "DOFs/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle PCG solves (setup excluded) of the same H(grad)+H(curl) problems "
+                      f"on a 3x3x3 mesh, p={DEGREE} ({dofs} lattice DOFs), {steps} step(s)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    from oracle.krylov import pcg
+    cores = len(os.sched_getaffinity(0))
+    sample = _oracle_sample()
+    dofs = sum(s[1] for s in sample)
+
+    def step():
+        for (_, _, A, M, b) in sample:
+            pcg(A, b, M.apply, rtol=1e-8, flexible=True)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.time()
+    for _ in range(args.steps):
+        step()
+    dt = time.time() - t0
+    v = args.steps * dofs / dt
+    line = {
+        "metric": METRIC, "value": v, "unit": "DOFs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": WORKLOAD + " (oracle sample: 3x3x3 mesh)", "lattice_dofs": dofs},
+        "cpu_baseline": {"value": v, "unit": "DOFs/s", "cores": cores, "kind": "oracle",
+                         "sample": f"3x3x3 mesh, p={DEGREE}, H(grad)+H(curl), {dofs} lattice DOFs"},
+        "e2e": {"value": v, "unit": "DOFs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,144 @@
+/*
+ * rm.h -- C ABI of the GB300 (sm_103a) solvers for the weighted Riesz maps
+ *
+ *     beta u - div(alpha grad u) = f      (k = 0, H(grad), Q_p)
+ *     beta u + curl(alpha curl u) = f     (k = 1, H(curl), NCE_p)
+ *     beta u - grad(alpha div u) = f      (k = 2, H(div),  NCF_p)
+ *
+ * of Brubeck & Farrell, "Multigrid solvers for the de Rham complex with
+ * optimal complexity in polynomial degree" (arXiv 2211.14284), Sec. 1 Eqs.
+ * hgrad/hcurl/hdiv, weak form Eq. common_weak_formulation with
+ * Gamma_D = boundary of the unit cube.
+ *
+ * Discretisation: structured n1 x n2 x n3 hexahedral mesh with trilinear
+ * cells, the FDM bases of Sec. 2 (interior functions orthonormal in L2 and
+ * H(d) on the reference cell), GLL quadrature with ceil(3(p+1)/2) points per
+ * direction (Sec. 5).  Preconditioner: the additive two-level Schwarz
+ * relaxations of Sec. 4 -- PAFW vertex stars (Eq. asm-afw), their
+ * statically-condensed form on the sparse auxiliary operator (Sec. 3.2,
+ * Eqs. sc-pafw, sc-asm-afw) and the SC Pavarino-Hiptmair form for H(curl)
+ * (Eq. sc-asm-hiptmair) -- with exact or incomplete Cholesky patch factors
+ * (Sec. 4.5) and a p = 1 coarse correction.
+ *
+ * VECTOR LAYOUT (every vector argument): FDM-basis coefficients on the
+ * per-component lattice.  Component m of form degree k has, per direction
+ * d, type 's' (continuous, N_d = n_d p + 1 points) or 'r' (discontinuous,
+ * N_d = n_d p points):  k=0: (s,s,s);  k=1: (r,s,s),(s,r,s),(s,s,r);
+ * k=2: (s,r,r),(r,s,r),(r,r,s).  Entry (g1,g2,g3) of component m is at
+ * offset_m + g1 + N1 (g2 + N2 g3); components are concatenated.  Local
+ * index i_d of cell e_d sits at g_d = e_d p + i_d.  Entries with an s-type
+ * index g_d in {0, n_d p} are Dirichlet: ignored on input, 0 on output.
+ *
+ * MESH LAYOUT: vertex (a1,a2,a3) at row a1 + (n1+1)(a2 + (n2+1) a3) of a
+ * host array of 3 doubles per vertex; cell (e1,e2,e3) has corners
+ * (e1+c1, e2+c2, e3+c3), reference coordinate xi_d = -1 at c_d = 0.
+ * Per-cell coefficients: cell (e1,e2,e3) at e1 + n1 (e2 + n2 e3).
+ *
+ * OWNERSHIP: the caller owns every vector (device memory, 16-byte aligned,
+ * valid on the handle's stream).  The handle owns all internal buffers.
+ * Host inputs of rm_setup are copied; they may be freed on return.
+ *
+ * ERRORS: every call returns an rm_status; 0 = RM_OK.  rm_last_error(h)
+ * gives a message (h = NULL: the last failure of rm_setup on this thread).
+ * There is no CPU fallback: a missing or failing CUDA device is an error.
+ */
+#ifndef RM_H
+#define RM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RM_OK = 0,
+  RM_ERR_ARG = 1,           /* invalid argument or unsupported combination */
+  RM_ERR_CUDA = 2,          /* a CUDA call failed */
+  RM_ERR_OOM = 3,           /* device or host allocation failed */
+  RM_ERR_BREAKDOWN = 4,     /* ICC pivot <= 0, or CG p^T A p <= 0 */
+  RM_ERR_NOT_CONVERGED = 5, /* max_it reached */
+  RM_ERR_NAN = 6            /* NaN/Inf in a residual */
+} rm_status;
+
+typedef enum { RM_HGRAD = 0, RM_HCURL = 1, RM_HDIV = 2 } rm_space;
+
+typedef enum { RM_FP64 = 0, RM_FP32 = 1 } rm_precision;
+typedef enum { RM_PAFW = 0, RM_PH = 1 } rm_decomposition;
+typedef enum { RM_CHOL = 0, RM_ICC = 1 } rm_factor;
+typedef enum { RM_COARSE_NONE = 0, RM_COARSE_P1 = 1 } rm_coarse;
+
+typedef struct {
+  int nx, ny, nz;          /* cells per direction, each >= 2 */
+  const double *vertices;  /* host, (nx+1)(ny+1)(nz+1) x 3; NULL = uniform unit cube */
+} rm_mesh;
+
+typedef struct {
+  int precision;           /* rm_precision of the preconditioner data and arithmetic */
+  int decomposition;       /* RM_PAFW (vertex stars) or RM_PH (H(curl) only) */
+  int static_condensation; /* 1: patches on the interface Schur complement */
+  int factor;              /* RM_CHOL (exact) or RM_ICC (ICC(0) on the SC pattern) */
+  int coarse;              /* rm_coarse */
+  int flexible;            /* 1: flexible CG (Polak-Ribiere beta) */
+  double rtol;             /* stop when ||b - A x||_2 <= rtol ||b||_2 (recursive residual) */
+  int max_it;
+  int check_every;         /* iterations between host reads of the residual */
+  int profile;             /* 1: time every operator apply and preconditioner call
+                              with CUDA events inside rm_solve (reported in rm_info) */
+} rm_options;
+
+typedef struct {
+  int iterations;
+  int status;              /* rm_status of the solve */
+  double rel_res_l2;       /* final recursive ||r|| / ||b|| */
+  double solve_ms;         /* device time of the solve, CUDA events */
+  double apply_ms;         /* profile = 1: total time of the operator applies */
+  int apply_calls;
+  double precond_ms;       /* profile = 1: total time of the preconditioner calls */
+  int precond_calls;
+  long long kernel_launches; /* kernels this library launched during the solve */
+} rm_info;
+
+typedef struct rm_handle rm_handle;
+
+/* Defaults: FP64, PAFW, no static condensation, exact Cholesky, P1 coarse,
+ * CG, rtol 1e-8, max_it 500, check_every 1. */
+rm_options rm_default_options(void);
+
+/* Builds the discretisation and the preconditioner (host FP64 setup: 1D
+ * eigenproblems, auxiliary operator, Schur complement, patch factors,
+ * coarse factor) and uploads it.  alpha, beta: host, length nx*ny*nz, or
+ * NULL for 1.  stream: a cudaStream_t (NULL = legacy default stream) used by
+ * every later call on this handle.  Supported: p in 1..15; RM_PH only for
+ * RM_HCURL with static_condensation = 1. */
+int rm_setup(rm_handle **h, int space, const rm_mesh *mesh, int p,
+             const double *alpha, const double *beta, const rm_options *opt,
+             void *stream);
+
+/* Lattice length (all entries) and number of free (non-Dirichlet) DOFs. */
+int rm_ndofs(const rm_handle *h, long long *lattice, long long *free_dofs);
+
+/* y = A x: the matrix-free sum-factorised operator of Eq. sum-factorization
+ * on the true (trilinear) geometry, FP64.  x, y: device, lattice length;
+ * y is overwritten. */
+int rm_apply(rm_handle *h, const double *x, double *y);
+
+/* z = B r, the additive two-level relaxation (FP64 in/out whatever the
+ * precision option).  r, z: device, lattice length; z is overwritten. */
+int rm_precondition(rm_handle *h, const double *r, double *z);
+
+/* Preconditioned (flexible) CG for A x = b.  b: device (Dirichlet entries
+ * ignored).  x: device, in = initial guess (zeros = the paper's setting),
+ * out = solution.  info may be NULL. */
+int rm_solve(rm_handle *h, const double *b, double *x, rm_info *info);
+
+/* Number of patches, patch slots and factor nonzeros of the relaxation
+ * (summed over patch families), for reporting. */
+int rm_stats(const rm_handle *h, long long *patches, long long *slots,
+             long long *factor_nnz);
+
+void rm_destroy(rm_handle *h);
+const char *rm_last_error(const rm_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RM_H */

@@ -48,13 +48,18 @@ def broken_transform(kk: int, p: int) -> np.ndarray:
     return scipy.linalg.block_diag(*blocks)
 
 
-def broken_mass_diagonal(ref: ReferenceElement, kk: int, W):
-    """diag of the weighted mass matrix of V^kk in the broken basis.
-
-    W: (nq, c, c) weight including the quadrature weight and coefficient.
-    The broken functions are tabulated as Phi G^{-1} (G orthogonal)."""
+def broken_tabulation(ref: ReferenceElement, kk: int):
+    """The broken functions tabulated at the quadrature points, Phi G^{-1}."""
     G = broken_transform(kk, ref.p)
-    Phib = np.einsum("qaj,jk->qak", ref.values, np.linalg.inv(G))
+    nq, c, nd = ref.values.shape
+    return (ref.values.reshape(nq * c, nd) @ np.linalg.inv(G)).reshape(nq, c, nd)
+
+
+def broken_mass_diagonal(Phib, W):
+    """diag of the weighted mass matrix in the broken basis:
+    d_K = sum_q Phib_K(q)^T W(q) Phib_K(q).
+
+    W: (nq, c, c) weight including the quadrature weight and coefficient."""
     return np.einsum("qak,qab,qbk->k", Phib, W, Phib)
 
 
@@ -69,14 +74,14 @@ class AuxElement:
         self.Gk1 = broken_transform(k + 1, p)
         self.D = dhat_3d(k, self.ref_k.e)
         self.Dbar = self.Gk1 @ self.D
+        self.Phib_k = broken_tabulation(self.ref_k, k)
+        self.Phib_k1 = broken_tabulation(self.ref_k1, k + 1)
 
     def matrix(self, V8, mass_coef: float, stiff_coef: float):
         _, J = trilinear(V8, self.ref_k.xi)
         w = self.ref_k.w[:, None, None]
-        db = broken_mass_diagonal(self.ref_k, self.k,
-                                  mass_coef * form_weight(self.k, J) * w)
-        da = broken_mass_diagonal(self.ref_k1, self.k + 1,
-                                  stiff_coef * form_weight(self.k + 1, J) * w)
+        db = broken_mass_diagonal(self.Phib_k, mass_coef * form_weight(self.k, J) * w)
+        da = broken_mass_diagonal(self.Phib_k1, stiff_coef * form_weight(self.k + 1, J) * w)
         return (self.Gk.T @ np.diag(db) @ self.Gk
                 + self.Dbar.T @ np.diag(da) @ self.Dbar)
 

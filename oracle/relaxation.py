@@ -20,9 +20,11 @@ Readings where the paper is silent or ambiguous:
 * patch ordering is nested dissection by entity: cell interiors, then faces,
   then edges, then vertices, lexicographic in the global index within each
   group; this fixes the ICC(0) factor;
-* ICC(0) keeps the entries of the patch matrix with
-  |S_ij| > 1e-12 sqrt(|S_ii S_jj|) (numerically zero couplings are not in
-  the static-condensation pattern); a non-positive pivot is a breakdown;
+* the patch matrix is taken on its sparsity pattern: entries with
+  |S_ij| <= 1e-12 sqrt(|S_ii S_jj|) are numerically zero couplings and are
+  not part of it; ICC(0) keeps exactly the remaining entries and exact
+  Cholesky factors the matrix restricted to them; a non-positive pivot is a
+  breakdown;
 * the coarse correction R_0^T A_0^{-1} R_0 acts on the full space; R_0^T is
   the injection of V_{h,1} into V_{h,p} (dual functionals of Eq.
   fdmdualbasis applied to the p=1 basis) and A_0 is a^k rediscretised at p=1
@@ -138,8 +140,19 @@ def icc0(Adense: np.ndarray, drop: float = ICC_DROP) -> np.ndarray:
     return np.tril(A)
 
 
+def pattern_matrix(Adense: np.ndarray, drop: float = ICC_DROP) -> np.ndarray:
+    """The patch matrix on its sparsity pattern: entries with
+    |A_ij| <= drop sqrt(|A_ii A_jj|) (numerically zero couplings) removed."""
+    d = np.sqrt(np.abs(np.diag(Adense)))
+    A = np.array(Adense, float, copy=True)
+    A[np.abs(A) <= drop * np.outer(d, d)] = 0.0
+    np.fill_diagonal(A, np.diag(Adense))
+    return A
+
+
 def cholesky(Adense: np.ndarray) -> np.ndarray:
-    return np.linalg.cholesky(Adense)
+    """Exact Cholesky factor of the patch matrix on its sparsity pattern."""
+    return np.linalg.cholesky(pattern_matrix(Adense))
 
 
 class PatchSolver:
@@ -228,20 +241,37 @@ class Condensed:
         self.PIG = P[self.I][:, self.G].tocsc()
         self.PGI = P[self.G][:, self.I].tocsr()
         PGG = P[self.G][:, self.G].tocsr()
-        self.PII_lu = spla.splu(self.PII)
-        X = spla.spsolve(self.PII, self.PIG)
-        X = sp.csr_matrix(X) if not sp.issparse(X) else X
-        self.S = (PGG - self.PGI @ X).tocsr()
+        # P_II is block diagonal (blocks of at most d x d, Remark after Eq.
+        # schur): invert it block by block on its connected components
+        # (couplings below 1e-13 sqrt(|P_ii P_jj|) are quadrature round-off).
+        PIId = self.PII.tocsr()
+        dg = np.sqrt(np.abs(PIId.diagonal()))
+        C = PIId.tocoo()
+        keep = np.abs(C.data) > 1e-13 * dg[C.row] * dg[C.col]
+        graph = sp.csr_matrix((np.ones(keep.sum()), (C.row[keep], C.col[keep])),
+                              shape=PIId.shape)
+        ncomp, lab = sp.csgraph.connected_components(graph, directed=False)
+        rows, cols, vals = [], [], []
+        for c in range(ncomp):
+            ix = np.flatnonzero(lab == c)
+            Binv = np.linalg.inv(PIId[ix][:, ix].toarray())
+            rows.append(np.repeat(ix, len(ix)))
+            cols.append(np.tile(ix, len(ix)))
+            vals.append(Binv.ravel())
+        nI = len(self.I)
+        self.PII_inv = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows),
+                                      np.concatenate(cols))), shape=(nI, nI))
+        self.S = (PGG - self.PGI @ (self.PII_inv @ self.PIG)).tocsr()
 
     def condense(self, r):
         """(y_I, R_G r) with y_I = P_II^{-1} r_I."""
-        yI = self.PII_lu.solve(r[self.I])
+        yI = self.PII_inv @ r[self.I]
         return yI, r[self.G] - self.PGI @ yI
 
     def expand(self, yI, zG):
         """z = R_I^T y_I + R_G^T z_G, written as [y_I - P_II^{-1} P_IG z_G; z_G]."""
         z = np.zeros(len(self.free))
-        z[self.I] = yI - self.PII_lu.solve(self.PIG @ zG)
+        z[self.I] = yI - self.PII_inv @ (self.PIG @ zG)
         z[self.G] = zG
         return z
 

@@ -1,0 +1,548 @@
+// C ABI (include/rm.h): setup on the host in FP64, upload, and the
+// device-resident apply / precondition / PCG loop on the handle's stream.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <functional>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/rm.h"
+#include "device.cuh"
+#include "host_basis.h"
+#include "host_setup.h"
+
+using namespace rm;
+using namespace rmd;
+
+namespace {
+thread_local std::string g_last_error;
+
+struct CudaError : std::runtime_error {
+  explicit CudaError(const std::string &s) : std::runtime_error(s) {}
+};
+#define CK(x)                                                                                   \
+  do {                                                                                          \
+    cudaError_t e_ = (x);                                                                       \
+    if (e_ != cudaSuccess)                                                                      \
+      throw CudaError(std::string(#x) + ": " + cudaGetErrorString(e_));                         \
+  } while (0)
+
+struct DevBuf {
+  void *p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+};
+}  // namespace
+
+struct rm_handle {
+  std::string err;
+  cudaStream_t stream = nullptr;
+  rm_options opt{};
+  int k = 0, p = 0, n[3] = {0, 0, 0};
+  Layout L;
+  long long size = 0, nfree = 0;
+  bool sc = false, ph = false;
+  int vt = 0;  // 0 double, 1 float preconditioner data
+  std::vector<void *> allocs;
+  ApplyDev ad{};
+  uint8_t *mask = nullptr;
+  DevCsr Binv, E, Et, R0, R0T, Dt, DtT;
+  void *A0inv = nullptr;
+  int nc = 0;
+  std::vector<DevPatch> fam;   // families acting on the main space
+  std::vector<DevPatch> pfam;  // potential-space families (Hiptmair)
+  long long size0 = 0;         // potential (H(grad)) lattice size
+  double *w = nullptr, *rt = nullptr, *u0 = nullptr, *v0 = nullptr, *cc = nullptr, *ce = nullptr;
+  double *r = nullptr, *z = nullptr, *pv = nullptr, *qv = nullptr, *scal = nullptr, *partial = nullptr;
+  double *hscal = nullptr;  // pinned
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<cudaEvent_t> evpool;  // profile = 1: start/stop pairs
+  long long stat_patches = 0, stat_slots = 0, stat_nnz = 0;
+
+  template <typename T>
+  T *dalloc(size_t count) {
+    void *ptr = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(&ptr, count * sizeof(T));
+    if (e != cudaSuccess) throw CudaError(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    allocs.push_back(ptr);
+    return (T *)ptr;
+  }
+  template <typename T>
+  T *upload(const std::vector<T> &v) {
+    T *d = dalloc<T>(v.size());
+    if (!v.empty()) CK(cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return d;
+  }
+  void *upload_vals(const std::vector<double> &v) {
+    if (vt == 0) return upload(v);
+    std::vector<float> f(v.begin(), v.end());
+    return upload(f);
+  }
+  ~rm_handle() {
+    for (void *a : allocs) cudaFree(a);
+    if (hscal) cudaFreeHost(hscal);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    for (cudaEvent_t e : evpool) cudaEventDestroy(e);
+  }
+};
+
+namespace {
+
+// Upload a free-indexed (or arbitrary) CSR with explicit row/col maps.
+// rows: the rows to keep (in A's numbering), empty ones included, so that a
+// "y = u + a A x" product writes every row of the set; NULL keeps the
+// non-empty rows.
+DevCsr upload_csr(rm_handle *h, const Csr &A, const std::vector<int> *rowmap,
+                  const std::vector<int> *colmap, const std::vector<int> *rows = nullptr,
+                  bool force_double = false) {
+  std::vector<int> rid, ptr{0}, col;
+  std::vector<double> val;
+  std::vector<int> all;
+  if (!rows) {
+    for (int i = 0; i < A.nrows; ++i)
+      if (A.ptr[i + 1] != A.ptr[i]) all.push_back(i);
+    rows = &all;
+  }
+  for (int i : *rows) {
+    rid.push_back(rowmap ? (*rowmap)[i] : i);
+    for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
+      col.push_back(colmap ? (*colmap)[A.col[e]] : A.col[e]);
+      val.push_back(A.val[e]);
+    }
+    if (val.size() > (size_t)2147483647) throw std::runtime_error("CSR too large");
+    ptr.push_back((int)col.size());
+  }
+  DevCsr D;
+  D.nrows = (int)rid.size();
+  double avg = D.nrows ? (double)col.size() / D.nrows : 1.0;
+  D.tpr = avg > 24 ? 32 : avg > 12 ? 16 : avg > 6 ? 8 : avg > 3 ? 4 : avg > 1.5 ? 2 : 1;
+  D.rid = h->upload(rid);
+  D.ptr = h->upload(ptr);
+  D.col = h->upload(col);
+  int saved = h->vt;
+  if (force_double) h->vt = 0;
+  D.val = h->upload_vals(val);
+  D.vt = h->vt;
+  h->vt = saved;
+  return D;
+}
+
+DevPatch upload_family(rm_handle *h, const PatchFamily &F) {
+  DevPatch D;
+  D.nslots = F.nslots;
+  D.npatch = F.npatch;
+  D.nnz = F.nnz();
+  D.nflev = (int)F.flev.size() - 1;
+  D.nblev = (int)F.blev.size() - 1;
+  D.slotmap = h->upload(F.slotmap);
+  D.rowptr = h->upload(F.rowptr);
+  D.col = h->upload(F.col);
+  D.tptr = h->upload(F.tptr);
+  D.trow = h->upload(F.trow);
+  D.tpos = h->upload(F.tpos);
+  D.flev = h->upload(F.flev);
+  D.frows = h->upload(F.frows);
+  D.blev = h->upload(F.blev);
+  D.brows = h->upload(F.brows);
+  D.val = h->upload_vals(F.val);
+  D.vt = h->vt;
+  h->stat_patches += F.npatch;
+  h->stat_slots += (long long)F.npatch * F.nslots;
+  h->stat_nnz += (long long)F.npatch * F.nnz();
+  if ((size_t)F.nslots * sizeof(double) > 200 * 1024) throw std::runtime_error("patch too large for shared memory");
+  return D;
+}
+
+void build_apply(rm_handle *h, const Geometry &geo, const std::vector<double> &alpha,
+                 const std::vector<double> &beta) {
+  const int k = h->k, p = h->p;
+  const int q = quad_points(p);
+  Basis1D B(p);
+  std::vector<double> xq, wq;
+  gll_rule(q, xq, wq);
+  std::vector<double> tabs(q * (p + 1) + q * p + p * (p + 1) + 2 * q);
+  B.tab_s(xq.data(), q, tabs.data());
+  B.tab_r(xq.data(), q, tabs.data() + q * (p + 1));
+  std::copy(B.D.begin(), B.D.end(), tabs.begin() + q * (p + 1) + q * p);
+  std::copy(xq.begin(), xq.end(), tabs.begin() + q * (p + 1) + q * p + p * (p + 1));
+  std::copy(wq.begin(), wq.end(), tabs.begin() + q * (p + 1) + q * p + p * (p + 1) + q);
+  ApplyDev &A = h->ad;
+  Layout L1(k + 1, h->n, p);
+  A.k = k;
+  A.p = p;
+  A.q = q;
+  for (int d = 0; d < 3; ++d) A.n[d] = h->n[d];
+  A.nc0 = h->L.ncomp;
+  A.nc1 = L1.ncomp;
+  for (int m = 0; m < 3; ++m)
+    for (int d = 0; d < 3; ++d) {
+      A.N[m][d] = (int)h->L.N[m][d];
+      A.ld0[m][d] = h->L.ld[m][d];
+      A.ld1[m][d] = L1.ld[m][d];
+      A.t0[m][d] = h->L.t[m][d];
+      A.t1[m][d] = L1.t[m][d];
+    }
+  for (int m = 0; m < 3; ++m) A.off[m] = h->L.off[m];
+  for (int m = 0; m < 4; ++m) {
+    A.loff0[m] = h->L.loff[m];
+    A.loff1[m] = L1.loff[m];
+  }
+  A.nloc0 = h->L.nloc;
+  A.nloc1 = L1.nloc;
+  A.X = h->upload(geo.X);
+  A.alpha = h->upload(alpha);
+  A.beta = h->upload(beta);
+  A.tabs = h->upload(tabs);
+  const size_t q3 = (size_t)q * q * q;
+  A.smem_doubles = 2 * q * (p + 1) + 2 * q * p + 2 * p * (p + 1) + 2 * q + 24 + 2 * A.nloc0 + 2 * A.nloc1 +
+                   3 * q3 + (size_t)q * (p + 1) * (p + 1) + (size_t)q * q * (p + 1);
+  if (A.smem_doubles * sizeof(double) > 227 * 1024)
+    throw std::runtime_error("degree too high for the general apply kernel's shared memory (p <= 8)");
+}
+
+int fail(rm_handle *h, int code, const std::string &msg) {
+  if (h) h->err = msg;
+  g_last_error = msg;
+  return code;
+}
+
+// z = B r
+void precondition(rm_handle *h, const double *r, double *z) {
+  cudaStream_t s = h->stream;
+  CK(cudaMemsetAsync(z, 0, h->size * sizeof(double), s));
+  if (h->sc) {
+    CK(launch_spmv(h->Binv, r, h->w, nullptr, 0, 1.0, s));       // w_I = P_II^-1 r_I
+    CK(launch_spmv(h->E, h->w, h->rt, r, 2, -1.0, s));           // rt_G = r_G - E w_I
+    for (auto &F : h->fam) CK(launch_patches(F, h->rt, z, s));   // z_G = sum_v S_v^-1 rt
+    if (h->ph) {
+      CK(launch_spmv(h->DtT, h->rt, h->u0, nullptr, 0, 1.0, s)); // u0 = D~^T rt
+      CK(cudaMemsetAsync(h->v0, 0, h->size0 * sizeof(double), s));
+      for (auto &F : h->pfam) CK(launch_patches(F, h->u0, h->v0, s));
+      CK(launch_spmv(h->Dt, h->v0, z, nullptr, 1, 1.0, s));     // z_G += D~ v0
+    }
+    CK(launch_spmv(h->Et, z, z, h->w, 2, -1.0, s));              // z_I = w_I - E^T z_G
+  } else {
+    for (auto &F : h->fam) CK(launch_patches(F, r, z, s));
+  }
+  if (h->nc > 0) {
+    CK(launch_spmv(h->R0, r, h->cc, nullptr, 0, 1.0, s));
+    CK(launch_gemv(h->nc, h->A0inv, h->vt, h->cc, h->ce, s));
+    CK(launch_spmv(h->R0T, h->ce, z, nullptr, 1, 1.0, s));
+  }
+}
+
+void apply(rm_handle *h, const double *x, double *y) {
+  CK(cudaMemsetAsync(y, 0, h->size * sizeof(double), h->stream));
+  CK(launch_apply(h->ad, x, y, h->stream));
+}
+
+}  // namespace
+
+extern "C" {
+
+rm_options rm_default_options(void) {
+  rm_options o;
+  o.precision = RM_FP64;
+  o.decomposition = RM_PAFW;
+  o.static_condensation = 0;
+  o.factor = RM_CHOL;
+  o.coarse = RM_COARSE_P1;
+  o.flexible = 0;
+  o.rtol = 1e-8;
+  o.max_it = 500;
+  o.check_every = 1;
+  o.profile = 0;
+  return o;
+}
+
+int rm_setup(rm_handle **out, int space, const rm_mesh *mesh, int p, const double *alpha,
+             const double *beta, const rm_options *opt, void *stream) {
+  if (!out) return fail(nullptr, RM_ERR_ARG, "rm_setup: out is NULL");
+  *out = nullptr;
+  if (!mesh) return fail(nullptr, RM_ERR_ARG, "rm_setup: mesh is NULL");
+  if (space < 0 || space > 2) return fail(nullptr, RM_ERR_ARG, "rm_setup: space must be 0, 1 or 2");
+  if (p < 1 || p > 15) return fail(nullptr, RM_ERR_ARG, "rm_setup: p must be in 1..15");
+  if (mesh->nx < 2 || mesh->ny < 2 || mesh->nz < 2)
+    return fail(nullptr, RM_ERR_ARG, "rm_setup: at least 2 cells per direction");
+  std::unique_ptr<rm_handle> h(new rm_handle());
+  try {
+    h->opt = opt ? *opt : rm_default_options();
+    h->stream = (cudaStream_t)stream;
+    h->k = space;
+    h->p = p;
+    h->n[0] = mesh->nx;
+    h->n[1] = mesh->ny;
+    h->n[2] = mesh->nz;
+    const rm_options &o = h->opt;
+    if (o.precision != RM_FP64 && o.precision != RM_FP32) throw std::invalid_argument("precision");
+    if (o.decomposition == RM_PH && (space != RM_HCURL || !o.static_condensation))
+      throw std::invalid_argument("RM_PH needs RM_HCURL and static_condensation = 1");
+    if (o.rtol <= 0 || o.max_it < 1 || o.check_every < 1) throw std::invalid_argument("rtol/max_it/check_every");
+    h->vt = o.precision == RM_FP32 ? 1 : 0;
+    h->sc = o.static_condensation != 0;
+    h->ph = o.decomposition == RM_PH;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    h->L = Layout(space, h->n, p);
+    h->size = h->L.size;
+    const int ncell = h->n[0] * h->n[1] * h->n[2];
+    Geometry geo;
+    for (int d = 0; d < 3; ++d) geo.n[d] = h->n[d];
+    const size_t nv = (size_t)(h->n[0] + 1) * (h->n[1] + 1) * (h->n[2] + 1);
+    geo.X.resize(3 * nv);
+    if (mesh->vertices) {
+      std::memcpy(geo.X.data(), mesh->vertices, 3 * nv * sizeof(double));
+    } else {
+      for (int a3 = 0; a3 <= h->n[2]; ++a3)
+        for (int a2 = 0; a2 <= h->n[1]; ++a2)
+          for (int a1 = 0; a1 <= h->n[0]; ++a1) {
+            size_t v = a1 + (size_t)(h->n[0] + 1) * (a2 + (size_t)(h->n[1] + 1) * a3);
+            geo.X[3 * v + 0] = (double)a1 / h->n[0];
+            geo.X[3 * v + 1] = (double)a2 / h->n[1];
+            geo.X[3 * v + 2] = (double)a3 / h->n[2];
+          }
+    }
+    std::vector<double> al(ncell, 1.0), be(ncell, 1.0);
+    if (alpha) std::memcpy(al.data(), alpha, ncell * sizeof(double));
+    if (beta) std::memcpy(be.data(), beta, ncell * sizeof(double));
+    for (int c = 0; c < ncell; ++c)
+      if (!(al[c] > 0) || !(be[c] >= 0)) throw std::invalid_argument("alpha must be > 0 and beta >= 0");
+    build_apply(h.get(), geo, al, be);
+    FreeMap fm(h->L);
+    h->nfree = (long long)fm.free2lat.size();
+    {
+      std::vector<uint8_t> mask(h->size, 1);
+      for (int l : fm.free2lat) mask[l] = 0;
+      h->mask = h->upload(mask);
+    }
+    // relaxation
+    Csr P = assemble_aux(h->L, geo, be.data(), al.data(), fm);
+    if (!h->sc) {
+      if (o.decomposition != RM_PAFW) throw std::invalid_argument("non-condensed relaxation is PAFW only");
+      PatchFamily F = build_patches(h->L, fm, P, 0, false, o.factor == RM_ICC ? 1 : 0);
+      h->fam.push_back(upload_family(h.get(), F));
+    } else {
+      Condensed C = condense(h->L, fm, P);
+      P = Csr();
+      h->Binv = upload_csr(h.get(), C.Binv, &fm.free2lat, &fm.free2lat, &C.I);
+      h->E = upload_csr(h.get(), C.E, &fm.free2lat, &fm.free2lat, &C.G);
+      h->Et = upload_csr(h.get(), C.Et, &fm.free2lat, &fm.free2lat, &C.I);
+      if (!h->ph) {
+        PatchFamily F = build_patches(h->L, fm, C.S, 0, true, o.factor == RM_ICC ? 1 : 0);
+        h->fam.push_back(upload_family(h.get(), F));
+      } else {
+        // edge stars of S (exact Cholesky), Eq. sc-asm-hiptmair
+        for (int m = 0; m < 3; ++m) {
+          PatchFamily F = build_patches(h->L, fm, C.S, 1 << m, true, 0);
+          h->fam.push_back(upload_family(h.get(), F));
+        }
+        // potential: H(grad) auxiliary operator with mass 0, stiffness beta
+        Layout L0(0, h->n, p);
+        FreeMap fm0(L0);
+        std::vector<double> zero(ncell, 0.0);
+        Csr B = assemble_aux(L0, geo, zero.data(), be.data(), fm0);
+        Condensed C0 = condense(L0, fm0, B);
+        PatchFamily F0 = build_patches(L0, fm0, C0.S, 0, true, o.factor == RM_ICC ? 1 : 0);
+        h->pfam.push_back(upload_family(h.get(), F0));
+        h->size0 = L0.size;
+        std::vector<int> G1, G0;
+        for (int f : C.G) G1.push_back(fm.free2lat[f]);
+        for (int f : C0.G) G0.push_back(fm0.free2lat[f]);
+        Csr D = discrete_gradient(L0, h->L, G1, G0);
+        h->Dt = upload_csr(h.get(), D, nullptr, nullptr, &G1);
+        h->DtT = upload_csr(h.get(), transpose(D), nullptr, nullptr, &G0);
+        h->u0 = h->dalloc<double>(h->size0);
+        h->v0 = h->dalloc<double>(h->size0);
+      }
+      h->w = h->dalloc<double>(h->size);
+      h->rt = h->dalloc<double>(h->size);
+    }
+    if (o.coarse == RM_COARSE_P1) {
+      CoarseData cd = build_coarse(h->L, geo, al.data(), be.data());
+      h->nc = cd.nc;
+      std::vector<int> crow(cd.nc);
+      for (int i = 0; i < cd.nc; ++i) crow[i] = i;
+      h->R0 = upload_csr(h.get(), cd.R0, nullptr, nullptr, &crow);
+      h->R0T = upload_csr(h.get(), cd.R0T, nullptr, nullptr);
+      h->A0inv = h->upload_vals(cd.A0inv);
+      h->cc = h->dalloc<double>(h->nc);
+      h->ce = h->dalloc<double>(h->nc);
+    }
+    h->r = h->dalloc<double>(h->size);
+    h->z = h->dalloc<double>(h->size);
+    h->pv = h->dalloc<double>(h->size);
+    h->qv = h->dalloc<double>(h->size);
+    h->scal = h->dalloc<double>(S_COUNT);
+    h->partial = h->dalloc<double>(2 * kDotBlocks);
+    CK(cudaMallocHost((void **)&h->hscal, S_COUNT * sizeof(double)));
+    CK(cudaEventCreate(&h->ev0));
+    CK(cudaEventCreate(&h->ev1));
+    CK(cudaDeviceSynchronize());
+  } catch (const CudaError &e) {
+    return fail(nullptr, RM_ERR_CUDA, std::string("rm_setup: ") + e.what());
+  } catch (const std::bad_alloc &) {
+    return fail(nullptr, RM_ERR_OOM, "rm_setup: host allocation failed");
+  } catch (const std::invalid_argument &e) {
+    return fail(nullptr, RM_ERR_ARG, std::string("rm_setup: invalid option: ") + e.what());
+  } catch (const std::exception &e) {
+    std::string w = e.what();
+    int code = w.find("breakdown") != std::string::npos ? RM_ERR_BREAKDOWN : RM_ERR_ARG;
+    return fail(nullptr, code, std::string("rm_setup: ") + w);
+  }
+  *out = h.release();
+  return RM_OK;
+}
+
+int rm_ndofs(const rm_handle *h, long long *lattice, long long *free_dofs) {
+  if (!h) return fail(nullptr, RM_ERR_ARG, "rm_ndofs: NULL handle");
+  if (lattice) *lattice = h->size;
+  if (free_dofs) *free_dofs = h->nfree;
+  return RM_OK;
+}
+
+int rm_stats(const rm_handle *h, long long *patches, long long *slots, long long *factor_nnz) {
+  if (!h) return fail(nullptr, RM_ERR_ARG, "rm_stats: NULL handle");
+  if (patches) *patches = h->stat_patches;
+  if (slots) *slots = h->stat_slots;
+  if (factor_nnz) *factor_nnz = h->stat_nnz;
+  return RM_OK;
+}
+
+int rm_apply(rm_handle *h, const double *x, double *y) {
+  if (!h || !x || !y) return fail(h, RM_ERR_ARG, "rm_apply: NULL argument");
+  try {
+    apply(h, x, y);
+  } catch (const std::exception &e) {
+    return fail(h, RM_ERR_CUDA, e.what());
+  }
+  return RM_OK;
+}
+
+int rm_precondition(rm_handle *h, const double *r, double *z) {
+  if (!h || !r || !z) return fail(h, RM_ERR_ARG, "rm_precondition: NULL argument");
+  if (r == z) return fail(h, RM_ERR_ARG, "rm_precondition: r and z must not alias");
+  try {
+    precondition(h, r, z);
+  } catch (const std::exception &e) {
+    return fail(h, RM_ERR_CUDA, e.what());
+  }
+  return RM_OK;
+}
+
+int rm_solve(rm_handle *h, const double *b, double *x, rm_info *info) {
+  if (!h || !b || !x) return fail(h, RM_ERR_ARG, "rm_solve: NULL argument");
+  const long long n = h->size;
+  cudaStream_t s = h->stream;
+  int status = RM_OK, it = 0;
+  double rel = 0.0;
+  float ms = 0.f;
+  const bool prof = h->opt.profile != 0;
+  std::vector<int> kinds;  // 0 apply, 1 precondition, per recorded pair
+  auto timed = [&](int kind, const std::function<void()> &f) {
+    if (!prof) { f(); return; }
+    size_t i = 2 * kinds.size();
+    while (h->evpool.size() < i + 2) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      h->evpool.push_back(e);
+    }
+    CK(cudaEventRecord(h->evpool[i], s));
+    f();
+    CK(cudaEventRecord(h->evpool[i + 1], s));
+    kinds.push_back(kind);
+  };
+  double tk[2] = {0.0, 0.0};
+  const long long launches0 = launch_count();
+  int nk[2] = {0, 0};
+  try {
+    CK(cudaEventRecord(h->ev0, s));
+    // x Dirichlet entries -> 0; r = b - A x
+    CK(launch_mask_copy(n, h->mask, x, x, s));
+    timed(0, [&] { apply(h, x, h->qv); });
+    CK(launch_sub(n, h->mask, b, h->qv, h->r, s));
+    CK(launch_mask_copy(n, h->mask, b, h->z, s));
+    CK(launch_dot(n, h->z, h->z, h->partial, h->scal, S_BB, s));
+    CK(launch_dot(n, h->r, h->r, h->partial, h->scal, S_RR, s));
+    timed(1, [&] { precondition(h, h->r, h->z); });
+    CK(launch_dot(n, h->r, h->z, h->partial, h->scal, S_RZ, s));
+    CK(cudaMemcpyAsync(h->pv, h->z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(h->hscal, h->scal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double bb = h->hscal[S_BB];
+    const double tol2 = h->opt.rtol * h->opt.rtol * bb;
+    double rr = h->hscal[S_RR];
+    if (bb == 0.0) {
+      rel = 0.0;
+    } else if (rr <= tol2) {
+      rel = std::sqrt(rr / bb);
+    } else {
+      status = RM_ERR_NOT_CONVERGED;
+      while (it < h->opt.max_it) {
+        timed(0, [&] { apply(h, h->pv, h->qv); });
+        CK(launch_alpha(n, h->pv, h->qv, h->partial, h->scal, s));
+        CK(launch_update_xr(n, x, h->r, h->pv, h->qv, h->partial, h->scal, s));
+        ++it;
+        if (it % h->opt.check_every == 0 || it == h->opt.max_it) {
+          CK(cudaMemcpyAsync(h->hscal, h->scal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+          CK(cudaStreamSynchronize(s));
+          rr = h->hscal[S_RR];
+          if (!std::isfinite(rr)) { status = RM_ERR_NAN; break; }
+          if (!(h->hscal[S_PQ] > 0.0)) { status = RM_ERR_BREAKDOWN; break; }
+          if (rr <= tol2) { status = RM_OK; break; }
+        }
+        timed(1, [&] { precondition(h, h->r, h->z); });
+        CK(launch_dot2(n, h->r, h->z, h->qv, h->partial, h->scal, h->opt.flexible, s));
+        CK(launch_update_p(n, h->pv, h->z, h->scal, s));
+      }
+      rel = std::sqrt(rr / bb);
+    }
+    CK(cudaEventRecord(h->ev1, s));
+    CK(cudaEventSynchronize(h->ev1));
+    CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    for (size_t j = 0; j < kinds.size(); ++j) {
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, h->evpool[2 * j], h->evpool[2 * j + 1]));
+      tk[kinds[j]] += t;
+      nk[kinds[j]]++;
+    }
+  } catch (const std::exception &e) {
+    if (info) info->status = RM_ERR_CUDA;
+    return fail(h, RM_ERR_CUDA, e.what());
+  }
+  if (info) {
+    info->iterations = it;
+    info->status = status;
+    info->rel_res_l2 = rel;
+    info->solve_ms = ms;
+    info->apply_ms = tk[0];
+    info->apply_calls = nk[0];
+    info->precond_ms = tk[1];
+    info->precond_calls = nk[1];
+    info->kernel_launches = launch_count() - launches0;
+  }
+  if (status != RM_OK) {
+    const char *why = status == RM_ERR_NOT_CONVERGED ? "max_it reached"
+                      : status == RM_ERR_NAN         ? "NaN/Inf residual"
+                                                     : "CG breakdown (p^T A p <= 0)";
+    fail(h, status, std::string("rm_solve: ") + why);
+  }
+  return status;
+}
+
+void rm_destroy(rm_handle *h) { delete h; }
+
+const char *rm_last_error(const rm_handle *h) {
+  if (h) return h->err.c_str();
+  return g_last_error.c_str();
+}
+
+}  // extern "C"

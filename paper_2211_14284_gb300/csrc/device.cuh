@@ -1,0 +1,76 @@
+// Device-side data structures shared by the kernels and the C ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rmd {
+
+constexpr int kApplyThreads = 256;
+
+// Operator apply (Eq. sum-factorization) on trilinear cells.
+struct ApplyDev {
+  int k, p, q;
+  int n[3];
+  int nc0, nc1;            // components of V^k and V^{k+1}
+  int N[3][3];             // lattice dims of V^k per component
+  long long off[3];        // component offsets of V^k
+  int ld0[3][3], loff0[4]; // local dims of V^k
+  int ld1[3][3], loff1[4]; // local dims of V^{k+1}
+  char t0[3][3], t1[3][3];
+  int nloc0, nloc1;
+  const double *X;         // vertices, 3 per vertex
+  const double *alpha, *beta;
+  const double *tabs;      // Ts q(p+1) | Tr qp | D1 p(p+1) | xq q | wq q
+  size_t smem_doubles;
+};
+
+// Compressed sparse rows with explicit row ids (lattice or compact).
+struct DevCsr {
+  int nrows = 0;
+  int tpr = 1;             // threads per row (1..32, power of two)
+  int *rid = nullptr;
+  int *ptr = nullptr;
+  int *col = nullptr;
+  void *val = nullptr;     // double or float (vt)
+  int vt = 0;
+};
+
+// A family of patches with a shared slot template.
+struct DevPatch {
+  int nslots = 0, npatch = 0, nnz = 0;
+  int nflev = 0, nblev = 0;
+  const int *slotmap = nullptr;  // npatch x nslots
+  const int *rowptr = nullptr, *col = nullptr;
+  const int *tptr = nullptr, *trow = nullptr, *tpos = nullptr;
+  const int *flev = nullptr, *frows = nullptr, *blev = nullptr, *brows = nullptr;
+  const void *val = nullptr;     // npatch x nnz, double or float
+  int vt = 0;
+};
+
+// launchers (kernels.cu); launch_count() = kernels launched so far in this process
+long long launch_count();
+cudaError_t launch_apply(const ApplyDev &A, const double *x, double *y, cudaStream_t s);
+cudaError_t launch_spmv(const DevCsr &M, const double *x, double *y, const double *u, int mode,
+                        double a, cudaStream_t s);
+cudaError_t launch_patches(const DevPatch &F, const double *r, double *z, cudaStream_t s);
+cudaError_t launch_gemv(int n, const void *A, int vt, const double *x, double *y, cudaStream_t s);
+cudaError_t launch_mask_copy(long long n, const uint8_t *mask, const double *b, double *r,
+                             cudaStream_t s);
+cudaError_t launch_sub(long long n, const uint8_t *mask, const double *b, const double *q,
+                       double *r, cudaStream_t s);
+
+// CG scalars in device memory
+enum { S_RZ = 0, S_PQ, S_RR, S_BB, S_ALPHA, S_BETA, S_RZNEW, S_ZQ, S_COUNT };
+constexpr int kDotBlocks = 592;  // 4 x 148 SMs-worth, fixed for deterministic sums
+cudaError_t launch_dot(long long n, const double *a, const double *b, double *partial,
+                       double *scal, int slot, cudaStream_t s);
+cudaError_t launch_dot2(long long n, const double *r, const double *z, const double *q,
+                        double *partial, double *scal, int flexible, cudaStream_t s);
+cudaError_t launch_alpha(long long n, const double *p, const double *q, double *partial,
+                         double *scal, cudaStream_t s);
+cudaError_t launch_update_xr(long long n, double *x, double *r, const double *p, const double *q,
+                             double *partial, double *scal, cudaStream_t s);
+cudaError_t launch_update_p(long long n, double *p, const double *z, const double *scal,
+                            cudaStream_t s);
+
+}  // namespace rmd

@@ -1,0 +1,1074 @@
+// Host FP64 setup: lattice layout (Sec. 2.4), the sparse auxiliary operator
+// P (Sec. 3.2), static condensation (Eqs. LDU, schur), star patches with
+// exact / incomplete Cholesky factors on a slot template shared by all
+// patches of one entity kind (Sec. 4.1, 4.3, 4.5), and the p = 1 coarse
+// space (Sec. 4.3, Eq. asm-afw).
+#include "host_setup.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <numeric>
+#include <stdexcept>
+#include <unordered_map>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace rm {
+
+static const char *kTypes[4][3] = {
+    {"sss", nullptr, nullptr}, {"rss", "srs", "ssr"}, {"srr", "rsr", "rrs"}, {"rrr", nullptr, nullptr}};
+
+// d^k as (source component, direction, sign) terms per target component.
+struct DTerm {
+  int src, dir, sgn;
+};
+static const int kNumTerms[3][3] = {{1, 1, 1}, {2, 2, 2}, {3, 0, 0}};
+static const DTerm kTerms[3][3][3] = {
+    {{{0, 0, 1}}, {{0, 1, 1}}, {{0, 2, 1}}},
+    {{{2, 1, 1}, {1, 2, -1}}, {{0, 2, 1}, {2, 0, -1}}, {{1, 0, 1}, {0, 1, -1}}},
+    {{{0, 0, 1}, {1, 1, 1}, {2, 2, 1}}, {}, {}}};
+
+Layout::Layout(int k_, const int n_[3], int p_) : k(k_), p(p_) {
+  if (k < 0 || k > 3) throw std::runtime_error("Layout: k in 0..3");
+  for (int d = 0; d < 3; ++d) n[d] = n_[d];
+  ncomp = (k == 0 || k == 3) ? 1 : 3;
+  off[0] = 0;
+  loff[0] = 0;
+  for (int m = 0; m < ncomp; ++m) {
+    long long sz = 1;
+    int lsz = 1;
+    for (int d = 0; d < 3; ++d) {
+      t[m][d] = kTypes[k][m][d];
+      N[m][d] = (long long)n[d] * p + (t[m][d] == 's' ? 1 : 0);
+      ld[m][d] = t[m][d] == 's' ? p + 1 : p;
+      sz *= N[m][d];
+      lsz *= ld[m][d];
+    }
+    off[m + 1] = off[m] + sz;
+    loff[m + 1] = loff[m] + lsz;
+  }
+  size = off[ncomp];
+  nloc = loff[ncomp];
+}
+
+void Layout::coords(long long idx, int &m, long long g[3]) const {
+  m = 0;
+  while (m + 1 < ncomp && idx >= off[m + 1]) ++m;
+  long long r = idx - off[m];
+  g[0] = r % N[m][0];
+  r /= N[m][0];
+  g[1] = r % N[m][1];
+  g[2] = r / N[m][1];
+}
+
+Csr csr_from_triplets(int nrows, int ncols, std::vector<Trip> &t) {
+  Csr A;
+  A.nrows = nrows;
+  A.ncols = ncols;
+  std::vector<int64_t> cnt(nrows + 1, 0);
+  for (auto &x : t) cnt[x.r + 1]++;
+  for (int i = 0; i < nrows; ++i) cnt[i + 1] += cnt[i];
+  std::vector<int> cc(t.size());
+  std::vector<double> vv(t.size());
+  {
+    std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
+    for (auto &x : t) {
+      int64_t p = pos[x.r]++;
+      cc[p] = x.c;
+      vv[p] = x.v;
+    }
+  }
+  std::vector<Trip>().swap(t);
+  A.ptr.assign(nrows + 1, 0);
+  std::vector<int64_t> rowlen(nrows, 0);
+  // sort & merge per row
+#pragma omp parallel
+  {
+    std::vector<int> ord;
+#pragma omp for schedule(dynamic, 256)
+    for (int i = 0; i < nrows; ++i) {
+      int64_t b = cnt[i], e = cnt[i + 1];
+      int len = (int)(e - b);
+      if (len == 0) continue;
+      ord.resize(len);
+      std::iota(ord.begin(), ord.end(), 0);
+      std::sort(ord.begin(), ord.end(), [&](int a, int c) { return cc[b + a] < cc[b + c]; });
+      std::vector<int> c2;
+      std::vector<double> v2;
+      c2.reserve(len);
+      v2.reserve(len);
+      for (int a : ord) {
+        if (!c2.empty() && c2.back() == cc[b + a])
+          v2.back() += vv[b + a];
+        else {
+          c2.push_back(cc[b + a]);
+          v2.push_back(vv[b + a]);
+        }
+      }
+      for (size_t a = 0; a < c2.size(); ++a) {
+        cc[b + a] = c2[a];
+        vv[b + a] = v2[a];
+      }
+      rowlen[i] = (int64_t)c2.size();
+    }
+  }
+  for (int i = 0; i < nrows; ++i) A.ptr[i + 1] = A.ptr[i] + rowlen[i];
+  A.col.resize(A.ptr[nrows]);
+  A.val.resize(A.ptr[nrows]);
+  for (int i = 0; i < nrows; ++i)
+    for (int64_t a = 0; a < rowlen[i]; ++a) {
+      A.col[A.ptr[i] + a] = cc[cnt[i] + a];
+      A.val[A.ptr[i] + a] = vv[cnt[i] + a];
+    }
+  return A;
+}
+
+Csr transpose(const Csr &A) {
+  Csr T;
+  T.nrows = A.ncols;
+  T.ncols = A.nrows;
+  T.ptr.assign(T.nrows + 1, 0);
+  for (int64_t e = 0; e < A.nnz(); ++e) T.ptr[A.col[e] + 1]++;
+  for (int i = 0; i < T.nrows; ++i) T.ptr[i + 1] += T.ptr[i];
+  T.col.resize(A.nnz());
+  T.val.resize(A.nnz());
+  std::vector<int64_t> pos(T.ptr.begin(), T.ptr.end() - 1);
+  for (int i = 0; i < A.nrows; ++i)
+    for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
+      int64_t p = pos[A.col[e]]++;
+      T.col[p] = i;
+      T.val[p] = A.val[e];
+    }
+  return T;
+}
+
+void Geometry::cell_vertices(int e1, int e2, int e3, double out[24]) const {
+  for (int c3 = 0; c3 < 2; ++c3)
+    for (int c2 = 0; c2 < 2; ++c2)
+      for (int c1 = 0; c1 < 2; ++c1) {
+        long long a = (e1 + c1) + (long long)(n[0] + 1) * ((e2 + c2) + (long long)(n[1] + 1) * (e3 + c3));
+        int c = c1 + 2 * c2 + 4 * c3;
+        for (int x = 0; x < 3; ++x) out[3 * c + x] = X[3 * a + x];
+      }
+}
+
+FreeMap::FreeMap(const Layout &L) {
+  lat2free.assign(L.size, -1);
+  for (int m = 0; m < L.ncomp; ++m)
+    for (long long g3 = 0; g3 < L.N[m][2]; ++g3)
+      for (long long g2 = 0; g2 < L.N[m][1]; ++g2)
+        for (long long g1 = 0; g1 < L.N[m][0]; ++g1) {
+          long long g[3] = {g1, g2, g3};
+          if (!L.dirichlet(m, g)) {
+            long long idx = L.index(m, g1, g2, g3);
+            lat2free[idx] = (int)free2lat.size();
+            free2lat.push_back((int)idx);
+          }
+        }
+}
+
+// ---------------------------------------------------------------------------
+// geometry at a reference point
+// ---------------------------------------------------------------------------
+static void jacobian(const double X8[24], const double xi[3], double J[9]) {
+  double N[3][2], dN[2] = {-0.5, 0.5};
+  for (int d = 0; d < 3; ++d) {
+    N[d][0] = 0.5 * (1.0 - xi[d]);
+    N[d][1] = 0.5 * (1.0 + xi[d]);
+  }
+  for (int i = 0; i < 9; ++i) J[i] = 0.0;
+  for (int c3 = 0; c3 < 2; ++c3)
+    for (int c2 = 0; c2 < 2; ++c2)
+      for (int c1 = 0; c1 < 2; ++c1) {
+        const double *v = X8 + 3 * (c1 + 2 * c2 + 4 * c3);
+        double g0 = dN[c1] * N[1][c2] * N[2][c3];
+        double g1 = N[0][c1] * dN[c2] * N[2][c3];
+        double g2 = N[0][c1] * N[1][c2] * dN[c3];
+        for (int a = 0; a < 3; ++a) {
+          J[3 * a + 0] += v[a] * g0;
+          J[3 * a + 1] += v[a] * g1;
+          J[3 * a + 2] += v[a] * g2;
+        }
+      }
+}
+
+static double det3(const double J[9]) {
+  return J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
+         J[2] * (J[3] * J[7] - J[4] * J[6]);
+}
+
+// full pullback weight of kk-forms (Sec. 3.1): out 3x3 (or [0] for scalars)
+static void form_weight(int kk, const double J[9], double W[9]) {
+  double det = det3(J);
+  if (!(det > 0)) throw std::runtime_error("inverted or degenerate cell");
+  if (kk == 0) { W[0] = det; return; }
+  if (kk == 3) { W[0] = 1.0 / det; return; }
+  if (kk == 2) {
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        double s = 0.0;
+        for (int c = 0; c < 3; ++c) s += J[3 * c + a] * J[3 * c + b];
+        W[3 * a + b] = s / det;
+      }
+    return;
+  }
+  // kk == 1: det J^-1 J^-T = adj adj^T / det, adj = det J^-1
+  double A[9];
+  A[0] = J[4] * J[8] - J[5] * J[7];
+  A[1] = J[2] * J[7] - J[1] * J[8];
+  A[2] = J[1] * J[5] - J[2] * J[4];
+  A[3] = J[5] * J[6] - J[3] * J[8];
+  A[4] = J[0] * J[8] - J[2] * J[6];
+  A[5] = J[2] * J[3] - J[0] * J[5];
+  A[6] = J[3] * J[7] - J[4] * J[6];
+  A[7] = J[1] * J[6] - J[0] * J[7];
+  A[8] = J[0] * J[4] - J[1] * J[3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      double s = 0.0;
+      for (int c = 0; c < 3; ++c) s += A[3 * a + c] * A[3 * b + c];
+      W[3 * a + b] = s / det;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// auxiliary operator
+// ---------------------------------------------------------------------------
+namespace {
+
+struct SparseVec {
+  std::vector<int> idx;
+  std::vector<double> val;
+  void clear() { idx.clear(); val.clear(); }
+};
+
+struct AuxCtx {
+  Layout Lk, Lk1;
+  int p = 0, q = 0;
+  std::vector<double> xq, wq;
+  std::vector<double> Tsb, Tr;   // broken s-tabulation q x (p+1), r-tabulation q x p
+  std::vector<double> D1;        // p x (p+1)
+  double h = 1.0 / std::sqrt(2.0);
+};
+
+// entries of row j of the 1D broken transform G for type ty
+inline int grow(char ty, int j, int p, double h, int *ii, double *vv) {
+  if (ty == 'r' || (j > 0 && j < p)) { ii[0] = j; vv[0] = 1.0; return 1; }
+  ii[0] = 0; vv[0] = h;
+  ii[1] = p; vv[1] = (j == 0) ? h : -h;
+  return 2;
+}
+
+// diag of the broken weighted mass of V^kk (layout Lx) with per-point weight
+// F[m][q] (already including w_q and the coefficient): sum-factorised
+// d[m](i1,i2,i3) = sum_q F[m][q] Tb1[q1,i1]^2 Tb2[q2,i2]^2 Tb3[q3,i3]^2.
+void broken_diag(const AuxCtx &C, const Layout &Lx, const std::vector<double> *F,
+                 std::vector<double> &d) {
+  const int q = C.q, p = C.p;
+  d.assign(Lx.nloc, 0.0);
+  std::vector<double> t1, t2;
+  for (int m = 0; m < Lx.ncomp; ++m) {
+    const int l1 = Lx.ld[m][0], l2 = Lx.ld[m][1], l3 = Lx.ld[m][2];
+    auto sq = [&](int d, int qq, int i) {
+      double v = Lx.t[m][d] == 's' ? C.Tsb[qq * (p + 1) + i] : C.Tr[qq * p + i];
+      return v * v;
+    };
+    // contract q1 -> i1: t1[q3][q2][i1]
+    t1.assign((size_t)q * q * l1, 0.0);
+    for (int q3 = 0; q3 < q; ++q3)
+      for (int q2 = 0; q2 < q; ++q2)
+        for (int i1 = 0; i1 < l1; ++i1) {
+          double s = 0.0;
+          for (int q1 = 0; q1 < q; ++q1) s += F[m][q1 + q * (q2 + q * q3)] * sq(0, q1, i1);
+          t1[(q3 * q + q2) * l1 + i1] = s;
+        }
+    // contract q2 -> i2: t2[q3][i2][i1]
+    t2.assign((size_t)q * l2 * l1, 0.0);
+    for (int q3 = 0; q3 < q; ++q3)
+      for (int i2 = 0; i2 < l2; ++i2)
+        for (int i1 = 0; i1 < l1; ++i1) {
+          double s = 0.0;
+          for (int q2 = 0; q2 < q; ++q2) s += t1[(q3 * q + q2) * l1 + i1] * sq(1, q2, i2);
+          t2[(q3 * l2 + i2) * l1 + i1] = s;
+        }
+    for (int i3 = 0; i3 < l3; ++i3)
+      for (int i2 = 0; i2 < l2; ++i2)
+        for (int i1 = 0; i1 < l1; ++i1) {
+          double s = 0.0;
+          for (int q3 = 0; q3 < q; ++q3) s += t2[(q3 * l2 + i2) * l1 + i1] * sq(2, q3, i3);
+          d[Lx.loff[m] + i1 + l1 * (i2 + l2 * i3)] = s;
+        }
+  }
+}
+
+}  // namespace
+
+Csr assemble_aux(const Layout &L, const Geometry &geo, const double *mcoef,
+                 const double *scoef, const FreeMap &fm) {
+  if (L.k > 2) throw std::runtime_error("assemble_aux: k in 0..2");
+  AuxCtx C;
+  C.p = L.p;
+  C.Lk = L;
+  C.Lk1 = Layout(L.k + 1, L.n, L.p);
+  const int p = L.p;
+  Basis1D B(p);
+  C.q = quad_points(p);
+  gll_rule(C.q, C.xq, C.wq);
+  const int q = C.q;
+  std::vector<double> Ts(q * (p + 1));
+  B.tab_s(C.xq.data(), q, Ts.data());
+  C.Tr.resize(q * p);
+  B.tab_r(C.xq.data(), q, C.Tr.data());
+  C.Tsb = Ts;
+  for (int a = 0; a < q; ++a) {
+    double s0 = Ts[a * (p + 1) + 0], sp = Ts[a * (p + 1) + p];
+    C.Tsb[a * (p + 1) + 0] = C.h * (s0 + sp);
+    C.Tsb[a * (p + 1) + p] = C.h * (s0 - sp);
+  }
+  C.D1 = B.D;
+  const int k = L.k;
+  const Layout &Lk1 = C.Lk1;
+  const int nloc = L.nloc, nloc1 = Lk1.nloc;
+  const int ncell = L.n[0] * L.n[1] * L.n[2];
+  const int nq = q * q * q;
+  const int nfree = (int)fm.free2lat.size();
+
+  int nthreads = 1;
+#ifdef _OPENMP
+  nthreads = omp_get_max_threads();
+#endif
+  std::vector<std::vector<Trip>> trips(nthreads);
+
+#pragma omp parallel
+  {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    std::vector<double> loc((size_t)nloc * nloc, 0.0);
+    std::vector<char> mark((size_t)nloc * nloc, 0);
+    std::vector<std::vector<int>> touched(nloc);
+    std::vector<double> Fk[3], Fk1[3], dk, dk1;
+    std::vector<int> l2f(nloc);
+    std::vector<double> acc(nloc, 0.0);
+    std::vector<char> accm(nloc, 0);
+    SparseVec row, drow;
+    auto add_outer = [&](const SparseVec &v, double w) {
+      for (size_t a = 0; a < v.idx.size(); ++a)
+        for (size_t b = 0; b < v.idx.size(); ++b) {
+          size_t pos = (size_t)v.idx[a] * nloc + v.idx[b];
+          if (!mark[pos]) {
+            mark[pos] = 1;
+            touched[v.idx[a]].push_back(v.idx[b]);
+          }
+          loc[pos] += w * v.val[a] * v.val[b];
+        }
+    };
+#pragma omp for schedule(dynamic, 1)
+    for (int c = 0; c < ncell; ++c) {
+      const int e1 = c % L.n[0], e2 = (c / L.n[0]) % L.n[1], e3 = c / (L.n[0] * L.n[1]);
+      double X8[24];
+      geo.cell_vertices(e1, e2, e3, X8);
+      // per-point diagonal weights of V^k and V^{k+1}
+      for (int m = 0; m < 3; ++m) {
+        Fk[m].assign(nq, 0.0);
+        Fk1[m].assign(nq, 0.0);
+      }
+      for (int q3 = 0; q3 < q; ++q3)
+        for (int q2 = 0; q2 < q; ++q2)
+          for (int q1 = 0; q1 < q; ++q1) {
+            double xi[3] = {C.xq[q1], C.xq[q2], C.xq[q3]};
+            double J[9], W[9];
+            jacobian(X8, xi, J);
+            double w = C.wq[q1] * C.wq[q2] * C.wq[q3];
+            int qi = q1 + q * (q2 + q * q3);
+            form_weight(k, J, W);
+            for (int m = 0; m < L.ncomp; ++m)
+              Fk[m][qi] = mcoef[c] * w * (L.ncomp == 1 ? W[0] : W[4 * m]);
+            form_weight(k + 1, J, W);
+            for (int m = 0; m < Lk1.ncomp; ++m)
+              Fk1[m][qi] = scoef[c] * w * (Lk1.ncomp == 1 ? W[0] : W[4 * m]);
+          }
+      broken_diag(C, L, Fk, dk);
+      broken_diag(C, Lk1, Fk1, dk1);
+      // mass part: G^T diag(dk) G
+      for (int m = 0; m < L.ncomp; ++m) {
+        const int l1 = L.ld[m][0], l2 = L.ld[m][1], l3 = L.ld[m][2];
+        for (int j3 = 0; j3 < l3; ++j3)
+          for (int j2 = 0; j2 < l2; ++j2)
+            for (int j1 = 0; j1 < l1; ++j1) {
+              double db = dk[L.loff[m] + j1 + l1 * (j2 + l2 * j3)];
+              if (db == 0.0) continue;
+              int i1[2], i2[2], i3[2];
+              double v1[2], v2[2], v3[2];
+              int n1 = grow(L.t[m][0], j1, p, C.h, i1, v1);
+              int n2 = grow(L.t[m][1], j2, p, C.h, i2, v2);
+              int n3 = grow(L.t[m][2], j3, p, C.h, i3, v3);
+              row.clear();
+              for (int a3 = 0; a3 < n3; ++a3)
+                for (int a2 = 0; a2 < n2; ++a2)
+                  for (int a1 = 0; a1 < n1; ++a1) {
+                    row.idx.push_back(L.loff[m] + i1[a1] + l1 * (i2[a2] + l2 * i3[a3]));
+                    row.val.push_back(v1[a1] * v2[a2] * v3[a3]);
+                  }
+              add_outer(row, db);
+            }
+      }
+      // derivative part: Dbar^T diag(dk1) Dbar, Dbar = G' D-hat
+      for (int t = 0; t < Lk1.ncomp; ++t) {
+        const int l1 = Lk1.ld[t][0], l2 = Lk1.ld[t][1], l3 = Lk1.ld[t][2];
+        for (int j3 = 0; j3 < l3; ++j3)
+          for (int j2 = 0; j2 < l2; ++j2)
+            for (int j1 = 0; j1 < l1; ++j1) {
+              double db = dk1[Lk1.loff[t] + j1 + l1 * (j2 + l2 * j3)];
+              if (db == 0.0) continue;
+              int i1[2], i2[2], i3[2];
+              double v1[2], v2[2], v3[2];
+              int n1 = grow(Lk1.t[t][0], j1, p, C.h, i1, v1);
+              int n2 = grow(Lk1.t[t][1], j2, p, C.h, i2, v2);
+              int n3 = grow(Lk1.t[t][2], j3, p, C.h, i3, v3);
+              drow.clear();
+              for (int a3 = 0; a3 < n3; ++a3)
+                for (int a2 = 0; a2 < n2; ++a2)
+                  for (int a1 = 0; a1 < n1; ++a1) {
+                    double g = v1[a1] * v2[a2] * v3[a3];
+                    int ii[3] = {i1[a1], i2[a2], i3[a3]};
+                    // row (t, ii) of D-hat
+                    for (int s = 0; s < kNumTerms[k][t]; ++s) {
+                      const DTerm &T = kTerms[k][t][s];
+                      const int sm = T.src, dd = T.dir;
+                      const int s1 = L.ld[sm][0], s2 = L.ld[sm][1];
+                      for (int l = 0; l <= p; ++l) {
+                        double dv = C.D1[ii[dd] * (p + 1) + l];
+                        if (dv == 0.0) continue;
+                        int jj[3] = {ii[0], ii[1], ii[2]};
+                        jj[dd] = l;
+                        int src = L.loff[sm] + jj[0] + s1 * (jj[1] + s2 * jj[2]);
+                        if (!accm[src]) {
+                          accm[src] = 1;
+                          drow.idx.push_back(src);
+                          acc[src] = 0.0;
+                        }
+                        acc[src] += g * T.sgn * dv;
+                      }
+                    }
+                  }
+              for (size_t a = 0; a < drow.idx.size(); ++a) {
+                drow.val.push_back(acc[drow.idx[a]]);
+                accm[drow.idx[a]] = 0;
+              }
+              add_outer(drow, db);
+            }
+      }
+      // local -> free
+      for (int m = 0; m < L.ncomp; ++m) {
+        const int l1 = L.ld[m][0], l2 = L.ld[m][1], l3 = L.ld[m][2];
+        for (int i3 = 0; i3 < l3; ++i3)
+          for (int i2 = 0; i2 < l2; ++i2)
+            for (int i1 = 0; i1 < l1; ++i1) {
+              long long idx = L.index(m, (long long)e1 * p + i1, (long long)e2 * p + i2,
+                                      (long long)e3 * p + i3);
+              l2f[L.loff[m] + i1 + l1 * (i2 + l2 * i3)] = fm.lat2free[idx];
+            }
+      }
+      for (int i = 0; i < nloc; ++i) {
+        for (int j : touched[i]) {
+          size_t pos = (size_t)i * nloc + j;
+          if (l2f[i] >= 0 && l2f[j] >= 0) trips[tid].push_back({l2f[i], l2f[j], loc[pos]});
+          loc[pos] = 0.0;
+          mark[pos] = 0;
+        }
+        touched[i].clear();
+      }
+    }
+  }
+  std::vector<Trip> all;
+  size_t tot = 0;
+  for (auto &t : trips) tot += t.size();
+  all.reserve(tot);
+  for (auto &t : trips) {
+    all.insert(all.end(), t.begin(), t.end());
+    std::vector<Trip>().swap(t);
+  }
+  (void)nloc1;
+  return csr_from_triplets(nfree, nfree, all);
+}
+
+// ---------------------------------------------------------------------------
+// static condensation
+// ---------------------------------------------------------------------------
+static bool is_interior(const Layout &L, long long lat) {
+  int m;
+  long long g[3];
+  L.coords(lat, m, g);
+  for (int d = 0; d < 3; ++d)
+    if (L.t[m][d] == 's' && g[d] % L.p == 0) return false;
+  return true;
+}
+
+static void invert_small(std::vector<double> &A, int n) {
+  // Gauss-Jordan with partial pivoting
+  std::vector<double> I(n * n, 0.0);
+  for (int i = 0; i < n; ++i) I[i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(A[r * n + c]) > std::fabs(A[piv * n + c])) piv = r;
+    if (A[piv * n + c] == 0.0) throw std::runtime_error("singular interior block");
+    if (piv != c)
+      for (int j = 0; j < n; ++j) {
+        std::swap(A[c * n + j], A[piv * n + j]);
+        std::swap(I[c * n + j], I[piv * n + j]);
+      }
+    double d = A[c * n + c];
+    for (int j = 0; j < n; ++j) { A[c * n + j] /= d; I[c * n + j] /= d; }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      double f = A[r * n + c];
+      if (f == 0.0) continue;
+      for (int j = 0; j < n; ++j) { A[r * n + j] -= f * A[c * n + j]; I[r * n + j] -= f * I[c * n + j]; }
+    }
+  }
+  A = I;
+}
+
+Condensed condense(const Layout &L, const FreeMap &fm, const Csr &P) {
+  Condensed R;
+  const int nf = P.nrows;
+  std::vector<char> inI(nf, 0);
+  for (int f = 0; f < nf; ++f) {
+    if (is_interior(L, fm.free2lat[f])) {
+      inI[f] = 1;
+      R.I.push_back(f);
+    } else {
+      R.G.push_back(f);
+    }
+  }
+  // blocks of P_II by union-find
+  std::vector<int> parent(nf);
+  std::iota(parent.begin(), parent.end(), 0);
+  std::function<int(int)> find = [&](int x) {
+    while (parent[x] != x) { parent[x] = parent[parent[x]]; x = parent[x]; }
+    return x;
+  };
+  for (int i : R.I)
+    for (int64_t e = P.ptr[i]; e < P.ptr[i + 1]; ++e) {
+      int j = P.col[e];
+      if (inI[j] && P.val[e] != 0.0) {
+        int a = find(i), b = find(j);
+        if (a != b) parent[a] = b;
+      }
+    }
+  std::unordered_map<int, std::vector<int>> blocks;
+  for (int i : R.I) blocks[find(i)].push_back(i);
+  std::vector<int> blk_of(nf, -1);
+  std::vector<std::vector<int>> blist;
+  for (auto &kv : blocks) {
+    std::sort(kv.second.begin(), kv.second.end());
+    if (kv.second.size() > 8) throw std::runtime_error("interior block larger than 8");
+    for (int i : kv.second) blk_of[i] = (int)blist.size();
+    blist.push_back(kv.second);
+  }
+  auto getP = [&](int i, int j) {
+    auto b = P.col.begin() + P.ptr[i], e = P.col.begin() + P.ptr[i + 1];
+    auto it = std::lower_bound(b, e, j);
+    return (it != e && *it == j) ? P.val[it - P.col.begin()] : 0.0;
+  };
+  std::vector<std::vector<double>> binv(blist.size());
+  std::vector<Trip> tb;
+  for (size_t b = 0; b < blist.size(); ++b) {
+    const auto &ix = blist[b];
+    int n = (int)ix.size();
+    std::vector<double> A(n * n);
+    for (int a = 0; a < n; ++a)
+      for (int c = 0; c < n; ++c) A[a * n + c] = getP(ix[a], ix[c]);
+    invert_small(A, n);
+    binv[b] = A;
+    for (int a = 0; a < n; ++a)
+      for (int c = 0; c < n; ++c) tb.push_back({ix[a], ix[c], A[a * n + c]});
+  }
+  R.Binv = csr_from_triplets(nf, nf, tb);
+  // E = P_GI Binv
+  std::vector<Trip> te;
+  for (int g : R.G) {
+    std::unordered_map<int, double> acc;
+    for (int64_t e = P.ptr[g]; e < P.ptr[g + 1]; ++e) {
+      int i = P.col[e];
+      if (!inI[i] || P.val[e] == 0.0) continue;
+      int b = blk_of[i];
+      const auto &ix = blist[b];
+      int n = (int)ix.size();
+      int a = (int)(std::find(ix.begin(), ix.end(), i) - ix.begin());
+      for (int c = 0; c < n; ++c) acc[ix[c]] += P.val[e] * binv[b][a * n + c];
+    }
+    for (auto &kv : acc) te.push_back({g, kv.first, kv.second});
+  }
+  R.E = csr_from_triplets(nf, nf, te);
+  R.Et = transpose(R.E);
+  // S = P_GG - E P_IG
+  int nthreads = 1;
+#ifdef _OPENMP
+  nthreads = omp_get_max_threads();
+#endif
+  std::vector<std::vector<Trip>> ts(nthreads);
+#pragma omp parallel
+  {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    std::vector<double> acc(nf, 0.0);
+    std::vector<char> m(nf, 0);
+    std::vector<int> touched;
+#pragma omp for schedule(dynamic, 512)
+    for (int gi = 0; gi < (int)R.G.size(); ++gi) {
+      int g = R.G[gi];
+      touched.clear();
+      for (int64_t e = P.ptr[g]; e < P.ptr[g + 1]; ++e) {
+        int c = P.col[e];
+        if (inI[c]) continue;
+        if (!m[c]) { m[c] = 1; touched.push_back(c); acc[c] = 0.0; }
+        acc[c] += P.val[e];
+      }
+      for (int64_t e = R.E.ptr[g]; e < R.E.ptr[g + 1]; ++e) {
+        int j = R.E.col[e];
+        double ev = R.E.val[e];
+        for (int64_t f = P.ptr[j]; f < P.ptr[j + 1]; ++f) {
+          int c = P.col[f];
+          if (inI[c]) continue;
+          if (!m[c]) { m[c] = 1; touched.push_back(c); acc[c] = 0.0; }
+          acc[c] -= ev * P.val[f];
+        }
+      }
+      for (int c : touched) {
+        ts[tid].push_back({g, c, acc[c]});
+        m[c] = 0;
+      }
+    }
+  }
+  std::vector<Trip> all;
+  for (auto &t : ts) all.insert(all.end(), t.begin(), t.end());
+  R.S = csr_from_triplets(nf, nf, all);
+  return R;
+}
+
+// ---------------------------------------------------------------------------
+// patches
+// ---------------------------------------------------------------------------
+namespace {
+struct Slot {
+  int m, o[3], dim;
+};
+}  // namespace
+
+static const double kDrop = 1e-12;  // ICC pattern: |A_ij| > kDrop sqrt(|A_ii A_jj|)
+
+PatchFamily build_patches(const Layout &L, const FreeMap &fm, const Csr &M, int span,
+                          bool interface_only, int factor) {
+  const int p = L.p;
+  // slot template
+  std::vector<Slot> slots;
+  for (int m = 0; m < L.ncomp; ++m) {
+    int lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+      bool cell = (span >> d) & 1;
+      bool s = L.t[m][d] == 's';
+      if (cell) { lo[d] = s ? 1 : 0; hi[d] = p - 1; }
+      else { lo[d] = s ? -(p - 1) : -p; hi[d] = p - 1; }
+    }
+    for (int o3 = lo[2]; o3 <= hi[2]; ++o3)
+      for (int o2 = lo[1]; o2 <= hi[1]; ++o2)
+        for (int o1 = lo[0]; o1 <= hi[0]; ++o1) {
+          int o[3] = {o1, o2, o3};
+          int nv = 0;
+          for (int d = 0; d < 3; ++d)
+            if (!((span >> d) & 1) && L.t[m][d] == 's' && o[d] == 0) ++nv;
+          if (interface_only && nv == 0) continue;
+          slots.push_back({m, {o1, o2, o3}, 3 - nv});
+        }
+  }
+  std::stable_sort(slots.begin(), slots.end(), [](const Slot &a, const Slot &b) {
+    if (a.dim != b.dim) return a.dim > b.dim;
+    if (a.m != b.m) return a.m < b.m;
+    if (a.o[2] != b.o[2]) return a.o[2] < b.o[2];
+    if (a.o[1] != b.o[1]) return a.o[1] < b.o[1];
+    return a.o[0] < b.o[0];
+  });
+  const int ns = (int)slots.size();
+  PatchFamily F;
+  F.nslots = ns;
+  // entities
+  int hi[3];
+  for (int d = 0; d < 3; ++d) hi[d] = L.n[d] - (((span >> d) & 1) ? 1 : 0);
+  std::vector<int> smap;
+  for (int a3 = 0; a3 <= hi[2]; ++a3)
+    for (int a2 = 0; a2 <= hi[1]; ++a2)
+      for (int a1 = 0; a1 <= hi[0]; ++a1) {
+        int a[3] = {a1, a2, a3};
+        std::vector<int> row(ns, -1);
+        int nvalid = 0;
+        for (int s = 0; s < ns; ++s) {
+          const Slot &S = slots[s];
+          long long g[3];
+          bool ok = true;
+          for (int d = 0; d < 3; ++d) {
+            g[d] = (long long)a[d] * p + S.o[d];
+            if (g[d] < 0 || g[d] >= L.N[S.m][d]) ok = false;
+          }
+          if (!ok) continue;
+          long long idx = L.index(S.m, g[0], g[1], g[2]);
+          if (fm.lat2free[idx] < 0) continue;
+          row[s] = (int)idx;
+          ++nvalid;
+        }
+        if (nvalid == 0) continue;
+        smap.insert(smap.end(), row.begin(), row.end());
+      }
+  F.npatch = (int)(smap.size() / (ns ? ns : 1));
+  F.slotmap.swap(smap);
+  const int np = F.npatch;
+  const int nf = M.nrows;
+
+  auto extract = [&](int pi, std::vector<int> &pos, std::vector<double> &A) {
+    A.assign((size_t)ns * ns, 0.0);
+    const int *sm = &F.slotmap[(size_t)pi * ns];
+    for (int s = 0; s < ns; ++s)
+      if (sm[s] >= 0) pos[fm.lat2free[sm[s]]] = s;
+    for (int s = 0; s < ns; ++s) {
+      if (sm[s] < 0) { A[(size_t)s * ns + s] = 1.0; continue; }
+      int f = fm.lat2free[sm[s]];
+      for (int64_t e = M.ptr[f]; e < M.ptr[f + 1]; ++e) {
+        int t = pos[M.col[e]];
+        if (t >= 0) A[(size_t)s * ns + t] = M.val[e];
+      }
+    }
+    for (int s = 0; s < ns; ++s)
+      if (sm[s] >= 0) pos[fm.lat2free[sm[s]]] = -1;
+  };
+  auto own = [&](const std::vector<double> &A, int i, int j) {
+    if (i == j) return true;
+    double a = A[(size_t)i * ns + j];
+    return std::fabs(a) > kDrop * std::sqrt(std::fabs(A[(size_t)i * ns + i] * A[(size_t)j * ns + j]));
+  };
+  // pass 1: union of the thresholded lower patterns
+  std::vector<char> uni((size_t)ns * ns, 0);
+#pragma omp parallel
+  {
+    std::vector<int> pos(nf, -1);
+    std::vector<double> A;
+    std::vector<char> mine((size_t)ns * ns, 0);
+#pragma omp for schedule(dynamic, 4)
+    for (int pi = 0; pi < np; ++pi) {
+      extract(pi, pos, A);
+      for (int i = 0; i < ns; ++i)
+        for (int j = 0; j <= i; ++j)
+          if (own(A, i, j)) mine[(size_t)i * ns + j] = 1;
+    }
+#pragma omp critical
+    for (size_t x = 0; x < mine.size(); ++x) uni[x] |= mine[x];
+  }
+  // symbolic fill for exact Cholesky
+  if (factor == 0) {
+    for (int j = 0; j < ns; ++j) {
+      std::vector<int> below;
+      for (int i = j + 1; i < ns; ++i)
+        if (uni[(size_t)i * ns + j]) below.push_back(i);
+      for (size_t a = 0; a < below.size(); ++a)
+        for (size_t b = 0; b <= a; ++b) uni[(size_t)below[a] * ns + below[b]] = 1;
+    }
+  }
+  F.rowptr.assign(ns + 1, 0);
+  for (int i = 0; i < ns; ++i) {
+    for (int j = 0; j < i; ++j)
+      if (uni[(size_t)i * ns + j]) F.col.push_back(j);
+    F.col.push_back(i);
+    F.rowptr[i + 1] = (int)F.col.size();
+  }
+  const int nnz = F.nnz();
+  // pass 2: numeric factorisation on the template pattern (left-looking)
+  F.val.assign((size_t)np * nnz, 0.0);
+  int breakdown = -1;
+#pragma omp parallel
+  {
+    std::vector<int> pos(nf, -1);
+    std::vector<double> A, Ld((size_t)ns * ns, 0.0);
+#pragma omp for schedule(dynamic, 4)
+    for (int pi = 0; pi < np; ++pi) {
+      extract(pi, pos, A);
+      for (int i = 0; i < ns; ++i) {
+        double *Li = &Ld[(size_t)i * ns];
+        for (int e = F.rowptr[i]; e < F.rowptr[i + 1] - 1; ++e) {
+          int j = F.col[e];
+          double v = 0.0;
+          if (factor == 0 || own(A, i, j)) {
+            double s = A[(size_t)i * ns + j];
+            const double *Lj = &Ld[(size_t)j * ns];
+            for (int f = F.rowptr[j]; f < F.rowptr[j + 1] - 1; ++f) s -= Lj[F.col[f]] * Li[F.col[f]];
+            v = s / Lj[j];
+          }
+          Li[j] = v;
+        }
+        double s = A[(size_t)i * ns + i];
+        for (int e = F.rowptr[i]; e < F.rowptr[i + 1] - 1; ++e) s -= Li[F.col[e]] * Li[F.col[e]];
+        if (!(s > 0.0)) {
+#pragma omp critical
+          breakdown = pi;
+          s = 1.0;
+        }
+        Li[i] = std::sqrt(s);
+      }
+      double *out = &F.val[(size_t)pi * nnz];
+      for (int i = 0; i < ns; ++i)
+        for (int e = F.rowptr[i]; e < F.rowptr[i + 1]; ++e) {
+          out[e] = Ld[(size_t)i * ns + F.col[e]];
+          Ld[(size_t)i * ns + F.col[e]] = 0.0;
+        }
+    }
+  }
+  if (breakdown >= 0)
+    throw std::runtime_error("patch factorisation breakdown (non-positive pivot) in patch " +
+                             std::to_string(breakdown));
+  // transposed pattern (strictly lower entries grouped by column)
+  F.tptr.assign(ns + 1, 0);
+  for (int i = 0; i < ns; ++i)
+    for (int e = F.rowptr[i]; e < F.rowptr[i + 1] - 1; ++e) F.tptr[F.col[e] + 1]++;
+  for (int j = 0; j < ns; ++j) F.tptr[j + 1] += F.tptr[j];
+  F.trow.resize(F.tptr[ns]);
+  F.tpos.resize(F.tptr[ns]);
+  {
+    std::vector<int> cur(F.tptr.begin(), F.tptr.end() - 1);
+    for (int i = 0; i < ns; ++i)
+      for (int e = F.rowptr[i]; e < F.rowptr[i + 1] - 1; ++e) {
+        int c = cur[F.col[e]]++;
+        F.trow[c] = i;
+        F.tpos[c] = e;
+      }
+  }
+  // level schedules
+  std::vector<int> lev(ns, 0);
+  int nlev = 0;
+  for (int i = 0; i < ns; ++i) {
+    int l = 0;
+    for (int e = F.rowptr[i]; e < F.rowptr[i + 1] - 1; ++e) l = std::max(l, lev[F.col[e]] + 1);
+    lev[i] = l;
+    nlev = std::max(nlev, l + 1);
+  }
+  auto bucket = [&](const std::vector<int> &lv, int nl, std::vector<int> &ptr, std::vector<int> &rows) {
+    ptr.assign(nl + 1, 0);
+    for (int i = 0; i < ns; ++i) ptr[lv[i] + 1]++;
+    for (int l = 0; l < nl; ++l) ptr[l + 1] += ptr[l];
+    rows.assign(ns, 0);
+    std::vector<int> cur(ptr.begin(), ptr.end() - 1);
+    for (int i = 0; i < ns; ++i) rows[cur[lv[i]]++] = i;
+  };
+  bucket(lev, nlev, F.flev, F.frows);
+  std::vector<int> blv(ns, 0);
+  int nbl = 0;
+  for (int j = ns - 1; j >= 0; --j) {
+    int l = 0;
+    for (int e = F.tptr[j]; e < F.tptr[j + 1]; ++e) l = std::max(l, blv[F.trow[e]] + 1);
+    blv[j] = l;
+    nbl = std::max(nbl, l + 1);
+  }
+  bucket(blv, nbl, F.blev, F.brows);
+  return F;
+}
+
+// ---------------------------------------------------------------------------
+// coarse space
+// ---------------------------------------------------------------------------
+// Element matrix of a^k at p = 1 on a trilinear cell (3-point GLL rule).
+static void element_p1(int k, const double X8[24], double alpha, double beta,
+                       std::vector<double> &A, const Layout &L1) {
+  const int nl = L1.nloc;
+  Layout L2;
+  int nn[3] = {1, 1, 1};
+  if (k < 3) L2 = Layout(k + 1, nn, 1);
+  std::vector<double> xq, wq;
+  gll_rule(3, xq, wq);
+  const double h = 1.0 / std::sqrt(2.0);
+  auto tab = [&](char ty, int i, double x) {
+    if (ty == 'r') return h;
+    return i == 0 ? 0.5 * (1.0 - x) : 0.5 * (1.0 + x);
+  };
+  const double D1[2] = {-h, h};  // p = 1: D-hat = (r_0, s_j')
+  A.assign((size_t)nl * nl, 0.0);
+  // values of each basis function (and of its reference derivative) at a point
+  std::vector<double> val((size_t)nl * 3), dval((size_t)nl * 3);
+  for (int q3 = 0; q3 < 3; ++q3)
+    for (int q2 = 0; q2 < 3; ++q2)
+      for (int q1 = 0; q1 < 3; ++q1) {
+        double xi[3] = {xq[q1], xq[q2], xq[q3]};
+        double w = wq[q1] * wq[q2] * wq[q3];
+        double J[9], Wk[9], Wk1[9];
+        jacobian(X8, xi, J);
+        form_weight(k, J, Wk);
+        form_weight(k + 1, J, Wk1);
+        std::fill(val.begin(), val.end(), 0.0);
+        std::fill(dval.begin(), dval.end(), 0.0);
+        for (int m = 0; m < L1.ncomp; ++m)
+          for (int i3 = 0; i3 < L1.ld[m][2]; ++i3)
+            for (int i2 = 0; i2 < L1.ld[m][1]; ++i2)
+              for (int i1 = 0; i1 < L1.ld[m][0]; ++i1) {
+                int b = L1.loff[m] + i1 + L1.ld[m][0] * (i2 + L1.ld[m][1] * i3);
+                int ii[3] = {i1, i2, i3};
+                double v = 1.0;
+                for (int d = 0; d < 3; ++d) v *= tab(L1.t[m][d], ii[d], xi[d]);
+                val[3 * b + (L1.ncomp == 1 ? 0 : m)] = v;
+                // d^k of this basis function: D-hat maps s-index i_d to the r-index 0
+                for (int t = 0; t < L2.ncomp; ++t)
+                  for (int s = 0; s < kNumTerms[k][t]; ++s) {
+                    const DTerm &T = kTerms[k][t][s];
+                    if (T.src != m) continue;
+                    double dv = T.sgn * D1[ii[T.dir]];
+                    for (int d = 0; d < 3; ++d)
+                      dv *= (d == T.dir) ? h : tab(L2.t[t][d], ii[d], xi[d]);
+                    dval[3 * b + (L2.ncomp == 1 ? 0 : t)] += dv;
+                  }
+              }
+        const int c0 = L1.ncomp == 1 ? 1 : 3, c1 = L2.ncomp == 1 ? 1 : 3;
+        for (int a = 0; a < nl; ++a)
+          for (int b = 0; b < nl; ++b) {
+            double s = 0.0;
+            for (int x = 0; x < c0; ++x)
+              for (int y = 0; y < c0; ++y) s += beta * val[3 * a + x] * Wk[3 * x + y] * val[3 * b + y];
+            for (int x = 0; x < c1; ++x)
+              for (int y = 0; y < c1; ++y) s += alpha * dval[3 * a + x] * Wk1[3 * x + y] * dval[3 * b + y];
+            A[(size_t)a * nl + b] += w * s;
+          }
+      }
+}
+
+CoarseData build_coarse(const Layout &Lf, const Geometry &geo, const double *alpha,
+                        const double *beta) {
+  CoarseData C;
+  const int k = Lf.k, p = Lf.p;
+  Layout Lc(k, Lf.n, 1);
+  FreeMap fc(Lc);
+  const int nc = (int)fc.free2lat.size();
+  C.nc = nc;
+  if (nc > 8192) throw std::runtime_error("coarse space too large for the dense coarse solve");
+  std::vector<double> A0((size_t)nc * nc, 0.0);
+  const int ncell = Lf.n[0] * Lf.n[1] * Lf.n[2];
+  std::vector<double> AK;
+  for (int c = 0; c < ncell; ++c) {
+    int e[3] = {c % Lf.n[0], (c / Lf.n[0]) % Lf.n[1], c / (Lf.n[0] * Lf.n[1])};
+    double X8[24];
+    geo.cell_vertices(e[0], e[1], e[2], X8);
+    element_p1(k, X8, alpha[c], beta[c], AK, Lc);
+    std::vector<int> l2f(Lc.nloc);
+    for (int m = 0; m < Lc.ncomp; ++m)
+      for (int i3 = 0; i3 < Lc.ld[m][2]; ++i3)
+        for (int i2 = 0; i2 < Lc.ld[m][1]; ++i2)
+          for (int i1 = 0; i1 < Lc.ld[m][0]; ++i1)
+            l2f[Lc.loff[m] + i1 + Lc.ld[m][0] * (i2 + Lc.ld[m][1] * i3)] =
+                fc.lat2free[Lc.index(m, e[0] + i1, e[1] + i2, e[2] + i3)];
+    for (int a = 0; a < Lc.nloc; ++a)
+      for (int b = 0; b < Lc.nloc; ++b)
+        if (l2f[a] >= 0 && l2f[b] >= 0) A0[(size_t)l2f[a] * nc + l2f[b]] += AK[(size_t)a * Lc.nloc + b];
+  }
+  // Cholesky A0 = L L^T, then A0^{-1} = L^-T L^-1
+  std::vector<double> Lm = A0;
+  for (int j = 0; j < nc; ++j) {
+    double d = Lm[(size_t)j * nc + j];
+    for (int kk = 0; kk < j; ++kk) d -= Lm[(size_t)j * nc + kk] * Lm[(size_t)j * nc + kk];
+    if (!(d > 0)) throw std::runtime_error("coarse matrix not SPD");
+    d = std::sqrt(d);
+    Lm[(size_t)j * nc + j] = d;
+#pragma omp parallel for schedule(static)
+    for (int i = j + 1; i < nc; ++i) {
+      double s = Lm[(size_t)i * nc + j];
+      for (int kk = 0; kk < j; ++kk) s -= Lm[(size_t)i * nc + kk] * Lm[(size_t)j * nc + kk];
+      Lm[(size_t)i * nc + j] = s / d;
+    }
+  }
+  C.A0inv.assign((size_t)nc * nc, 0.0);
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int c = 0; c < nc; ++c) {
+    std::vector<double> y(nc, 0.0);
+    for (int i = 0; i < nc; ++i) {
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int kk = 0; kk < i; ++kk) s -= Lm[(size_t)i * nc + kk] * y[kk];
+      y[i] = s / Lm[(size_t)i * nc + i];
+    }
+    for (int i = nc - 1; i >= 0; --i) {
+      double s = y[i];
+      for (int kk = i + 1; kk < nc; ++kk) s -= Lm[(size_t)kk * nc + i] * C.A0inv[(size_t)kk * nc + c];
+      C.A0inv[(size_t)i * nc + c] = s / Lm[(size_t)i * nc + i];
+    }
+  }
+  // R_0: closed-form injection coefficients per direction
+  Basis1D B(p);
+  std::vector<Trip> t;
+  FreeMap ff(Lf);
+  for (int f = 0; f < (int)ff.free2lat.size(); ++f) {
+    long long lat = ff.free2lat[f];
+    int m;
+    long long g[3];
+    Lf.coords(lat, m, g);
+    long long ci[3][2];
+    double cv[3][2];
+    int cn[3];
+    bool zero = false;
+    for (int d = 0; d < 3; ++d) {
+      long long e = g[d] / p;
+      int i = (int)(g[d] % p);
+      if (Lf.t[m][d] == 's') {
+        if (i == 0) { ci[d][0] = e; cv[d][0] = 1.0; cn[d] = 1; }
+        else {
+          ci[d][0] = e; cv[d][0] = B.Js[i * 2 + 0];
+          ci[d][1] = e + 1; cv[d][1] = B.Js[i * 2 + 1];
+          cn[d] = 2;
+        }
+      } else {
+        if (i != 0) { zero = true; break; }
+        ci[d][0] = e; cv[d][0] = 1.0; cn[d] = 1;
+      }
+    }
+    if (zero) continue;
+    for (int a3 = 0; a3 < cn[2]; ++a3)
+      for (int a2 = 0; a2 < cn[1]; ++a2)
+        for (int a1 = 0; a1 < cn[0]; ++a1) {
+          double v = cv[0][a1] * cv[1][a2] * cv[2][a3];
+          if (v == 0.0) continue;
+          int cf = fc.lat2free[Lc.index(m, ci[0][a1], ci[1][a2], ci[2][a3])];
+          if (cf < 0) continue;
+          t.push_back({cf, (int)lat, v});
+        }
+  }
+  C.R0 = csr_from_triplets(nc, (int)Lf.size, t);
+  C.R0T = transpose(C.R0);
+  return C;
+}
+
+Csr discrete_gradient(const Layout &L0, const Layout &L1, const std::vector<int> &rows1,
+                      const std::vector<int> &cols0) {
+  const int p = L0.p;
+  Basis1D B(p);
+  std::vector<char> okc(L0.size, 0);
+  for (int c : cols0) okc[c] = 1;
+  std::vector<Trip> t;
+  for (int r : rows1) {
+    int m;
+    long long g[3];
+    L1.coords(r, m, g);
+    long long e = g[m] / p;
+    int i = (int)(g[m] % p);
+    for (int l = 0; l <= p; ++l) {
+      double v = B.D[i * (p + 1) + l];
+      if (v == 0.0) continue;
+      long long h[3] = {g[0], g[1], g[2]};
+      h[m] = e * p + l;
+      long long c = L0.index(0, h[0], h[1], h[2]);
+      if (!okc[c]) continue;
+      t.push_back({r, (int)c, v});
+    }
+  }
+  return csr_from_triplets((int)L1.size, (int)L0.size, t);
+}
+
+}  // namespace rm

@@ -1,0 +1,116 @@
+// Host FP64 setup of the Riesz-map solvers: lattice layout, auxiliary
+// operator, static condensation, patch factors, coarse space.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "host_basis.h"
+
+namespace rm {
+
+// Per-component lattice of V^k (k = 0..3) on an n1 x n2 x n3 mesh, Sec. 2.4.
+struct Layout {
+  int k = 0, p = 0, n[3] = {0, 0, 0}, ncomp = 0;
+  char t[3][3] = {};       // 's' / 'r' per component and direction
+  long long N[3][3] = {};  // lattice points per component and direction
+  long long off[4] = {};   // component offsets
+  int ld[3][3] = {};       // local (cell) dims
+  int loff[4] = {};
+  long long size = 0;
+  int nloc = 0;
+  Layout() = default;
+  Layout(int k, const int n[3], int p);
+  long long index(int m, long long g1, long long g2, long long g3) const {
+    return off[m] + g1 + N[m][0] * (g2 + N[m][1] * g3);
+  }
+  bool dirichlet(int m, const long long g[3]) const {
+    for (int d = 0; d < 3; ++d)
+      if (t[m][d] == 's' && (g[d] == 0 || g[d] == (long long)n[d] * p)) return true;
+    return false;
+  }
+  // decode a lattice index
+  void coords(long long idx, int &m, long long g[3]) const;
+};
+
+struct Csr {
+  int nrows = 0, ncols = 0;
+  std::vector<int64_t> ptr;
+  std::vector<int> col;
+  std::vector<double> val;
+  int64_t nnz() const { return ptr.empty() ? 0 : ptr.back(); }
+};
+
+struct Trip {
+  int r, c;
+  double v;
+};
+// Sums duplicates; columns sorted within rows.
+Csr csr_from_triplets(int nrows, int ncols, std::vector<Trip> &t);
+Csr transpose(const Csr &A);
+
+struct Geometry {
+  int n[3];
+  std::vector<double> X;  // (n1+1)(n2+1)(n3+1) x 3
+  void cell_vertices(int e1, int e2, int e3, double out[24]) const;
+};
+
+struct FreeMap {
+  std::vector<int> lat2free;  // -1 for Dirichlet
+  std::vector<int> free2lat;
+  explicit FreeMap(const Layout &L);
+  FreeMap() = default;
+};
+
+// Sparse auxiliary operator P (Sec. 3.2, Eq. sum-factorization_approx) on
+// the free DOFs, with mass coefficient mcoef and derivative coefficient
+// scoef per cell.
+Csr assemble_aux(const Layout &L, const Geometry &geo, const double *mcoef,
+                 const double *scoef, const FreeMap &fm);
+
+// Interior / interface split and Schur complement (Eqs. LDU, schur).
+struct Condensed {
+  std::vector<int> I, G;   // free indices
+  Csr Binv;                // P_II^{-1}, free x free (rows in I)
+  Csr E;                   // P_GI P_II^{-1}, free x free (rows in G, cols in I)
+  Csr Et;                  // E^T (rows in I, cols in G)
+  Csr S;                   // interface Schur complement, free x free (rows/cols in G)
+};
+Condensed condense(const Layout &L, const FreeMap &fm, const Csr &P);
+
+// A family of patches sharing one slot template (stars of one entity kind).
+struct PatchFamily {
+  int nslots = 0, npatch = 0;
+  std::vector<int> slotmap;           // npatch x nslots lattice indices, -1 = absent
+  std::vector<int> rowptr, col;       // template lower pattern, diagonal last per row
+  std::vector<int> tptr, trow, tpos;  // transposed pattern: strictly-lower entries by column
+  std::vector<int> flev, frows;       // forward level schedule (level ptr, rows)
+  std::vector<int> blev, brows;       // backward level schedule
+  std::vector<double> val;            // npatch x nnz
+  int nnz() const { return rowptr.empty() ? 0 : rowptr.back(); }
+};
+// span: bit d set = the entity spans direction d (0: vertex, 1 bit: edge, ...)
+// interface_only: slots restricted to interface DOFs (static condensation).
+// factor: 0 exact Cholesky, 1 ICC(0) on the patch matrix pattern.
+PatchFamily build_patches(const Layout &L, const FreeMap &fm, const Csr &M,
+                          int span, bool interface_only, int factor);
+
+// p = 1 coarse space (Sec. 4.3): restriction R_0 (coarse free x fine
+// lattice) and the dense inverse of the rediscretised A_0.
+struct CoarseData {
+  int nc = 0;
+  Csr R0;    // rows: coarse free, cols: fine lattice index
+  Csr R0T;   // rows: fine lattice index (only free), cols: coarse free
+  std::vector<double> A0inv;
+};
+CoarseData build_coarse(const Layout &Lf, const Geometry &geo, const double *alpha,
+                        const double *beta);
+
+// Discrete gradient V^0 -> V^1 restricted to free rows/cols (lattice ids).
+Csr discrete_gradient(const Layout &L0, const Layout &L1, const std::vector<int> &rows1,
+                      const std::vector<int> &cols0);
+
+// Quadrature points per direction: ceil(3(p+1)/2) (Sec. 5).
+inline int quad_points(int p) { return (3 * (p + 1) + 1) / 2; }
+
+}  // namespace rm

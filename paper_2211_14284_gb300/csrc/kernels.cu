@@ -1,0 +1,595 @@
+// Device kernels of the Riesz-map solvers (sm_103a).
+//
+// * apply_kernel: y = A x, one CTA per cell, the sum-factorised form
+//   A_K = M^k_beta + D-hat^T M^{k+1}_alpha D-hat of Eq. sum-factorization:
+//   the V^k coefficients and their reference exterior derivative D-hat x are
+//   interpolated to the ceil(3(p+1)/2)^3 GLL points by three 1D contractions
+//   staged in shared memory, weighted by the pullback metric of the trilinear
+//   map (Sec. 3.1), contracted back and scatter-added.
+// * patch_kernel: z += sum_j R_j^T L_j^-T L_j^-1 R_j r over a patch family
+//   (Eqs. asm-afw, sc-asm-afw, sc-asm-hiptmair): one CTA per patch, level-
+//   scheduled sparse forward/backward substitution in shared memory on the
+//   template pattern shared by all patches of the family.
+// * SpMV / GEMV for static condensation (Eq. schur), the Hiptmair gradient
+//   and the p = 1 coarse correction; fused CG updates with deterministic
+//   two-pass FP64 reductions.
+#include <atomic>
+
+#include "device.cuh"
+
+namespace rmd {
+
+static std::atomic<long long> g_launches{0};
+long long launch_count() { return g_launches.load(); }
+
+namespace {
+
+struct DTerm {
+  int src, dir, sgn;
+};
+__constant__ int c_nterms[3][3] = {{1, 1, 1}, {2, 2, 2}, {3, 0, 0}};
+__constant__ DTerm c_terms[3][3][3] = {
+    {{{0, 0, 1}}, {{0, 1, 1}}, {{0, 2, 1}}},
+    {{{2, 1, 1}, {1, 2, -1}}, {{0, 2, 1}, {2, 0, -1}}, {{1, 0, 1}, {0, 1, -1}}},
+    {{{0, 0, 1}, {1, 1, 1}, {2, 2, 1}}, {}, {}}};
+
+// out[b][o] = sc * sum_i M[o][i] in[b][i]   (contract the fastest index)
+__device__ __forceinline__ void pass1(const double *__restrict__ in, double *__restrict__ out,
+                                      const double *__restrict__ M, int O, int I, int NB,
+                                      double sc, bool acc) {
+  for (int idx = threadIdx.x; idx < O * NB; idx += blockDim.x) {
+    const int o = idx % O, b = idx / O;
+    const double *mi = M + o * I;
+    const double *xi = in + b * I;
+    double s = 0.0;
+    for (int i = 0; i < I; ++i) s = fma(mi[i], xi[i], s);
+    out[idx] = acc ? fma(sc, s, out[idx]) : sc * s;
+  }
+}
+// out[c][o][a] = sc * sum_i M[o][i] in[c][i][a]
+__device__ __forceinline__ void pass2(const double *__restrict__ in, double *__restrict__ out,
+                                      const double *__restrict__ M, int O, int I, int A, int C,
+                                      double sc, bool acc) {
+  for (int idx = threadIdx.x; idx < C * O * A; idx += blockDim.x) {
+    const int a = idx % A, o = (idx / A) % O, c = idx / (A * O);
+    const double *mi = M + o * I;
+    const double *xi = in + c * I * A + a;
+    double s = 0.0;
+    for (int i = 0; i < I; ++i) s = fma(mi[i], xi[i * A], s);
+    out[idx] = acc ? fma(sc, s, out[idx]) : sc * s;
+  }
+}
+// out[o][ba] = sc * sum_i M[o][i] in[i][ba]
+__device__ __forceinline__ void pass3(const double *__restrict__ in, double *__restrict__ out,
+                                      const double *__restrict__ M, int O, int I, int BA,
+                                      double sc, bool acc) {
+  for (int idx = threadIdx.x; idx < O * BA; idx += blockDim.x) {
+    const int ba = idx % BA, o = idx / BA;
+    const double *mi = M + o * I;
+    double s = 0.0;
+    for (int i = 0; i < I; ++i) s = fma(mi[i], in[i * BA + ba], s);
+    out[idx] = acc ? fma(sc, s, out[idx]) : sc * s;
+  }
+}
+
+__device__ __forceinline__ void jac(const double *X8, double x0, double x1, double x2, double J[9]) {
+  const double N0[2] = {0.5 * (1.0 - x0), 0.5 * (1.0 + x0)};
+  const double N1[2] = {0.5 * (1.0 - x1), 0.5 * (1.0 + x1)};
+  const double N2[2] = {0.5 * (1.0 - x2), 0.5 * (1.0 + x2)};
+  const double dN[2] = {-0.5, 0.5};
+#pragma unroll
+  for (int i = 0; i < 9; ++i) J[i] = 0.0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int c1 = c & 1, c2 = (c >> 1) & 1, c3 = c >> 2;
+    const double g0 = dN[c1] * N1[c2] * N2[c3];
+    const double g1 = N0[c1] * dN[c2] * N2[c3];
+    const double g2 = N0[c1] * N1[c2] * dN[c3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double v = X8[3 * c + a];
+      J[3 * a + 0] = fma(v, g0, J[3 * a + 0]);
+      J[3 * a + 1] = fma(v, g1, J[3 * a + 1]);
+      J[3 * a + 2] = fma(v, g2, J[3 * a + 2]);
+    }
+  }
+}
+
+// Multiply the reference values at every point by the pullback weight of
+// kk-forms times coef (Sec. 3.1).
+__device__ void pointwise(int kk, double coef, double *U, int q, const double *xq,
+                          const double *wq, const double *X8) {
+  const int q3 = q * q * q;
+  for (int pt = threadIdx.x; pt < q3; pt += blockDim.x) {
+    const int a1 = pt % q, a2 = (pt / q) % q, a3 = pt / (q * q);
+    double J[9];
+    jac(X8, xq[a1], xq[a2], xq[a3], J);
+    const double w = coef * wq[a1] * wq[a2] * wq[a3];
+    const double det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
+                       J[2] * (J[3] * J[7] - J[4] * J[6]);
+    if (kk == 0) {
+      U[pt] *= w * det;
+    } else if (kk == 3) {
+      U[pt] *= w / det;
+    } else {
+      double M[9];
+      if (kk == 1) {
+        double A[9];
+        A[0] = J[4] * J[8] - J[5] * J[7];
+        A[1] = J[2] * J[7] - J[1] * J[8];
+        A[2] = J[1] * J[5] - J[2] * J[4];
+        A[3] = J[5] * J[6] - J[3] * J[8];
+        A[4] = J[0] * J[8] - J[2] * J[6];
+        A[5] = J[2] * J[3] - J[0] * J[5];
+        A[6] = J[3] * J[7] - J[4] * J[6];
+        A[7] = J[1] * J[6] - J[0] * J[7];
+        A[8] = J[0] * J[4] - J[1] * J[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b)
+            M[3 * a + b] = (A[3 * a] * A[3 * b] + A[3 * a + 1] * A[3 * b + 1] + A[3 * a + 2] * A[3 * b + 2]) / det;
+      } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b)
+            M[3 * a + b] = (J[a] * J[b] + J[3 + a] * J[3 + b] + J[6 + a] * J[6 + b]) / det;
+      }
+      const double u0 = U[pt], u1 = U[q3 + pt], u2 = U[2 * q3 + pt];
+      U[pt] = w * (M[0] * u0 + M[1] * u1 + M[2] * u2);
+      U[q3 + pt] = w * (M[3] * u0 + M[4] * u1 + M[5] * u2);
+      U[2 * q3 + pt] = w * (M[6] * u0 + M[7] * u1 + M[8] * u2);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kApplyThreads) apply_kernel(ApplyDev P, const double *__restrict__ x,
+                                                              double *__restrict__ y) {
+  extern __shared__ double sm[];
+  const int p = P.p, q = P.q, q3 = q * q * q;
+  double *Ts = sm;
+  double *TsT = Ts + q * (p + 1);
+  double *Tr = TsT + q * (p + 1);
+  double *TrT = Tr + q * p;
+  double *D1 = TrT + q * p;
+  double *D1T = D1 + p * (p + 1);
+  double *xq = D1T + p * (p + 1);
+  double *wq = xq + q;
+  double *X8 = wq + q;
+  double *xl = X8 + 24;
+  double *yl = xl + P.nloc0;
+  double *dl = yl + P.nloc0;
+  double *dyl = dl + P.nloc1;
+  double *U = dyl + P.nloc1;
+  double *SA = U + 3 * q3;
+  double *SB = SA + q * (p + 1) * (p + 1);
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int c = blockIdx.x;
+  const int e[3] = {c % P.n[0], (c / P.n[0]) % P.n[1], c / (P.n[0] * P.n[1])};
+  {
+    const double *g = P.tabs;
+    for (int i = tid; i < q * (p + 1); i += NT) {
+      Ts[i] = g[i];
+      TsT[(i % (p + 1)) * q + i / (p + 1)] = g[i];
+    }
+    g += q * (p + 1);
+    for (int i = tid; i < q * p; i += NT) {
+      Tr[i] = g[i];
+      TrT[(i % p) * q + i / p] = g[i];
+    }
+    g += q * p;
+    for (int i = tid; i < p * (p + 1); i += NT) {
+      D1[i] = g[i];
+      D1T[(i % (p + 1)) * p + i / (p + 1)] = g[i];
+    }
+    g += p * (p + 1);
+    for (int i = tid; i < q; i += NT) {
+      xq[i] = g[i];
+      wq[i] = g[q + i];
+    }
+    if (tid < 24) {
+      const int corner = tid / 3, comp = tid % 3;
+      const int c1 = corner & 1, c2 = (corner >> 1) & 1, c3 = corner >> 2;
+      const long long v = (e[0] + c1) + (long long)(P.n[0] + 1) * ((e[1] + c2) + (long long)(P.n[1] + 1) * (e[2] + c3));
+      X8[tid] = P.X[3 * v + comp];
+    }
+  }
+  // gather (Dirichlet entries read as 0)
+  for (int l = tid; l < P.nloc0; l += NT) {
+    int m = 0;
+    while (m + 1 < P.nc0 && l >= P.loff0[m + 1]) ++m;
+    int r = l - P.loff0[m];
+    const int i1 = r % P.ld0[m][0];
+    r /= P.ld0[m][0];
+    const int i2 = r % P.ld0[m][1], i3 = r / P.ld0[m][1];
+    const int g1 = e[0] * p + i1, g2 = e[1] * p + i2, g3 = e[2] * p + i3;
+    const int g[3] = {g1, g2, g3};
+    bool dir = false;
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      if (P.t0[m][d] == 's' && (g[d] == 0 || g[d] == P.n[d] * p)) dir = true;
+    xl[l] = dir ? 0.0 : x[P.off[m] + g1 + (long long)P.N[m][0] * (g2 + (long long)P.N[m][1] * g3)];
+    yl[l] = 0.0;
+  }
+  const double al = P.alpha[c], be = P.beta[c];
+  __syncthreads();
+  // ---- stage A: (v, beta u) on V^k ----
+  for (int m = 0; m < P.nc0; ++m) {
+    const double *T[3];
+    for (int d = 0; d < 3; ++d) T[d] = P.t0[m][d] == 's' ? Ts : Tr;
+    pass1(xl + P.loff0[m], SA, T[0], q, P.ld0[m][0], P.ld0[m][1] * P.ld0[m][2], 1.0, false);
+    __syncthreads();
+    pass2(SA, SB, T[1], q, P.ld0[m][1], q, P.ld0[m][2], 1.0, false);
+    __syncthreads();
+    pass3(SB, U + m * q3, T[2], q, P.ld0[m][2], q * q, 1.0, false);
+    __syncthreads();
+  }
+  pointwise(P.k, be, U, q, xq, wq, X8);
+  __syncthreads();
+  for (int m = 0; m < P.nc0; ++m) {
+    const double *T[3];
+    for (int d = 0; d < 3; ++d) T[d] = P.t0[m][d] == 's' ? TsT : TrT;
+    pass3(U + m * q3, SB, T[2], P.ld0[m][2], q, q * q, 1.0, false);
+    __syncthreads();
+    pass2(SB, SA, T[1], P.ld0[m][1], q, q, P.ld0[m][2], 1.0, false);
+    __syncthreads();
+    pass1(SA, yl + P.loff0[m], T[0], P.ld0[m][0], q, P.ld0[m][1] * P.ld0[m][2], 1.0, true);
+    __syncthreads();
+  }
+  // ---- stage B: (d v, alpha d u) on V^{k+1}, d = D-hat ----
+  const int k = P.k;
+  for (int t = 0; t < P.nc1; ++t) {
+    for (int s = 0; s < c_nterms[k][t]; ++s) {
+      const DTerm T = c_terms[k][t][s];
+      const double *in = xl + P.loff0[T.src];
+      double *out = dl + P.loff1[t];
+      const int *ls = P.ld0[T.src];
+      if (T.dir == 0) pass1(in, out, D1, p, p + 1, ls[1] * ls[2], (double)T.sgn, s > 0);
+      else if (T.dir == 1) pass2(in, out, D1, p, p + 1, ls[0], ls[2], (double)T.sgn, s > 0);
+      else pass3(in, out, D1, p, p + 1, ls[0] * ls[1], (double)T.sgn, s > 0);
+      __syncthreads();
+    }
+  }
+  for (int t = 0; t < P.nc1; ++t) {
+    const double *T[3];
+    for (int d = 0; d < 3; ++d) T[d] = P.t1[t][d] == 's' ? Ts : Tr;
+    pass1(dl + P.loff1[t], SA, T[0], q, P.ld1[t][0], P.ld1[t][1] * P.ld1[t][2], 1.0, false);
+    __syncthreads();
+    pass2(SA, SB, T[1], q, P.ld1[t][1], q, P.ld1[t][2], 1.0, false);
+    __syncthreads();
+    pass3(SB, U + t * q3, T[2], q, P.ld1[t][2], q * q, 1.0, false);
+    __syncthreads();
+  }
+  pointwise(k + 1, al, U, q, xq, wq, X8);
+  __syncthreads();
+  for (int t = 0; t < P.nc1; ++t) {
+    const double *T[3];
+    for (int d = 0; d < 3; ++d) T[d] = P.t1[t][d] == 's' ? TsT : TrT;
+    pass3(U + t * q3, SB, T[2], P.ld1[t][2], q, q * q, 1.0, false);
+    __syncthreads();
+    pass2(SB, SA, T[1], P.ld1[t][1], q, q, P.ld1[t][2], 1.0, false);
+    __syncthreads();
+    pass1(SA, dyl + P.loff1[t], T[0], P.ld1[t][0], q, P.ld1[t][1] * P.ld1[t][2], 1.0, false);
+    __syncthreads();
+  }
+  for (int t = 0; t < P.nc1; ++t) {
+    for (int s = 0; s < c_nterms[k][t]; ++s) {
+      const DTerm T = c_terms[k][t][s];
+      const double *in = dyl + P.loff1[t];
+      double *out = yl + P.loff0[T.src];
+      const int *lt = P.ld1[t];
+      if (T.dir == 0) pass1(in, out, D1T, p + 1, p, lt[1] * lt[2], (double)T.sgn, true);
+      else if (T.dir == 1) pass2(in, out, D1T, p + 1, p, lt[0], lt[2], (double)T.sgn, true);
+      else pass3(in, out, D1T, p + 1, p, lt[0] * lt[1], (double)T.sgn, true);
+      __syncthreads();
+    }
+  }
+  // scatter-add (Dirichlet rows skipped)
+  for (int l = tid; l < P.nloc0; l += NT) {
+    int m = 0;
+    while (m + 1 < P.nc0 && l >= P.loff0[m + 1]) ++m;
+    int r = l - P.loff0[m];
+    const int i1 = r % P.ld0[m][0];
+    r /= P.ld0[m][0];
+    const int i2 = r % P.ld0[m][1], i3 = r / P.ld0[m][1];
+    const int g[3] = {e[0] * p + i1, e[1] * p + i2, e[2] * p + i3};
+    bool dir = false;
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      if (P.t0[m][d] == 's' && (g[d] == 0 || g[d] == P.n[d] * p)) dir = true;
+    if (!dir)
+      atomicAdd(&y[P.off[m] + g[0] + (long long)P.N[m][0] * (g[1] + (long long)P.N[m][1] * g[2])], yl[l]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <typename VT, int TPR>
+__global__ void spmv_kernel(int nrows, const int *__restrict__ rid, const int *__restrict__ ptr,
+                            const int *__restrict__ col, const VT *__restrict__ val,
+                            const double *x, double *y, const double *u, int mode, double a) {
+  // x, y and u may alias (z_I = w_I - E^T z_G reads and writes z on
+  // disjoint rows), so they are not declared __restrict__.
+  const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = (int)(gt / TPR), lane = (int)(gt % TPR);
+  double s = 0.0;
+  if (row < nrows)
+    for (int e = ptr[row] + lane; e < ptr[row + 1]; e += TPR) s = fma((double)val[e], x[col[e]], s);
+#pragma unroll
+  for (int off = TPR / 2; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off, TPR);
+  if (lane == 0 && row < nrows) {
+    const int r = rid[row];
+    const double v = a * s;
+    if (mode == 0) y[r] = v;
+    else if (mode == 1) y[r] += v;
+    else y[r] = u[r] + v;
+  }
+}
+
+template <typename VT>
+__global__ void patch_kernel(DevPatch F, const double *__restrict__ r, double *__restrict__ z) {
+  extern __shared__ double xs[];
+  const int ns = F.nslots;
+  const int *sm = F.slotmap + (size_t)blockIdx.x * ns;
+  const VT *L = reinterpret_cast<const VT *>(F.val) + (size_t)blockIdx.x * F.nnz;
+  for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+    const int g = sm[s];
+    xs[s] = g >= 0 ? r[g] : 0.0;
+  }
+  __syncthreads();
+  for (int lv = 0; lv < F.nflev; ++lv) {
+    for (int t = F.flev[lv] + threadIdx.x; t < F.flev[lv + 1]; t += blockDim.x) {
+      const int i = F.frows[t];
+      const int b = F.rowptr[i], d = F.rowptr[i + 1] - 1;
+      double v = xs[i];
+      for (int e = b; e < d; ++e) v = fma(-(double)L[e], xs[F.col[e]], v);
+      xs[i] = v / (double)L[d];
+    }
+    __syncthreads();
+  }
+  for (int lv = 0; lv < F.nblev; ++lv) {
+    for (int t = F.blev[lv] + threadIdx.x; t < F.blev[lv + 1]; t += blockDim.x) {
+      const int j = F.brows[t];
+      double v = xs[j];
+      for (int e = F.tptr[j]; e < F.tptr[j + 1]; ++e) v = fma(-(double)L[F.tpos[e]], xs[F.trow[e]], v);
+      xs[j] = v / (double)L[F.rowptr[j + 1] - 1];
+    }
+    __syncthreads();
+  }
+  for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+    const int g = sm[s];
+    if (g >= 0) atomicAdd(&z[g], xs[s]);
+  }
+}
+
+template <typename VT>
+__global__ void gemv_kernel(int n, const VT *__restrict__ A, const double *__restrict__ x,
+                            double *__restrict__ y) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  double s = 0.0;
+  if (warp < n)
+    for (int j = lane; j < n; j += 32) s = fma((double)A[(size_t)warp * n + j], x[j], s);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if (lane == 0 && warp < n) y[warp] = s;
+}
+
+__global__ void mask_copy_kernel(long long n, const uint8_t *__restrict__ mask,
+                                 const double *__restrict__ b, double *__restrict__ r) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    r[i] = mask[i] ? 0.0 : b[i];
+}
+__global__ void sub_kernel(long long n, const uint8_t *__restrict__ mask, const double *__restrict__ b,
+                           const double *__restrict__ q, double *__restrict__ r) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    r[i] = mask[i] ? 0.0 : b[i] - q[i];
+}
+
+// ---- reductions -------------------------------------------------------------
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+  if (w == 0)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  return v;
+}
+
+__global__ void dot_partial_kernel(long long n, const double *__restrict__ a, const double *__restrict__ b,
+                                   double *__restrict__ partial) {
+  double s = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    s = fma(a[i], b[i], s);
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void dot2_partial_kernel(long long n, const double *__restrict__ r, const double *__restrict__ z,
+                                    const double *__restrict__ q, double *__restrict__ partial) {
+  double s = 0.0, t = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double zi = z[i];
+    s = fma(r[i], zi, s);
+    t = fma(q[i], zi, t);
+  }
+  s = block_sum(s);
+  t = block_sum(t);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = s;
+    partial[kDotBlocks + blockIdx.x] = t;
+  }
+}
+
+__global__ void update_xr_kernel(long long n, double *__restrict__ x, double *__restrict__ r,
+                                 const double *__restrict__ p, const double *__restrict__ q,
+                                 double *__restrict__ partial, const double *__restrict__ scal) {
+  const double a = scal[S_ALPHA];
+  double s = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    x[i] = fma(a, p[i], x[i]);
+    const double ri = fma(-a, q[i], r[i]);
+    r[i] = ri;
+    s = fma(ri, ri, s);
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void update_p_kernel(long long n, double *__restrict__ p, const double *__restrict__ z,
+                                const double *__restrict__ scal) {
+  const double b = scal[S_BETA];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = fma(b, p[i], z[i]);
+}
+
+// Fixed-order final sums.  op 0: scal[slot] = sum; op 1: pq -> alpha;
+// op 2: (rz_new, zq) -> beta, rz.
+__global__ void finalize_kernel(const double *__restrict__ partial, double *__restrict__ scal, int slot,
+                                int op, int flexible) {
+  double s = 0.0, t = 0.0;
+  for (int i = threadIdx.x; i < kDotBlocks; i += blockDim.x) {
+    s += partial[i];
+    if (op == 2) t += partial[kDotBlocks + i];
+  }
+  s = block_sum(s);
+  if (op == 2) t = block_sum(t);
+  if (threadIdx.x == 0) {
+    if (op == 0) {
+      scal[slot] = s;
+    } else if (op == 1) {
+      scal[S_PQ] = s;
+      scal[S_ALPHA] = scal[S_RZ] / s;
+    } else {
+      const double rz = scal[S_RZ];
+      scal[S_RZNEW] = s;
+      scal[S_ZQ] = t;
+      scal[S_BETA] = flexible ? -t / scal[S_PQ] : s / rz;
+      scal[S_RZ] = s;
+    }
+  }
+}
+
+inline int grid_for(long long n, int threads) {
+  long long g = (n + threads - 1) / threads;
+  return (int)(g < 1 ? 1 : (g > 1184 ? 1184 : g));
+}
+
+}  // namespace
+
+cudaError_t launch_apply(const ApplyDev &A, const double *x, double *y, cudaStream_t s) {
+  const int ncell = A.n[0] * A.n[1] * A.n[2];
+  const size_t smem = A.smem_doubles * sizeof(double);
+  cudaError_t err = cudaFuncSetAttribute(apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  apply_kernel<<<ncell, kApplyThreads, smem, s>>>(A, x, y);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+template <typename VT>
+static void spmv_dispatch(const DevCsr &M, const double *x, double *y, const double *u, int mode,
+                          double a, cudaStream_t s) {
+  const int threads = 256;
+  const long long tot = (long long)M.nrows * M.tpr;
+  const int grid = (int)((tot + threads - 1) / threads);
+  const VT *v = reinterpret_cast<const VT *>(M.val);
+  switch (M.tpr) {
+    case 1: spmv_kernel<VT, 1><<<grid, threads, 0, s>>>(M.nrows, M.rid, M.ptr, M.col, v, x, y, u, mode, a); break;
+    case 2: spmv_kernel<VT, 2><<<grid, threads, 0, s>>>(M.nrows, M.rid, M.ptr, M.col, v, x, y, u, mode, a); break;
+    case 4: spmv_kernel<VT, 4><<<grid, threads, 0, s>>>(M.nrows, M.rid, M.ptr, M.col, v, x, y, u, mode, a); break;
+    case 8: spmv_kernel<VT, 8><<<grid, threads, 0, s>>>(M.nrows, M.rid, M.ptr, M.col, v, x, y, u, mode, a); break;
+    case 16: spmv_kernel<VT, 16><<<grid, threads, 0, s>>>(M.nrows, M.rid, M.ptr, M.col, v, x, y, u, mode, a); break;
+    default: spmv_kernel<VT, 32><<<grid, threads, 0, s>>>(M.nrows, M.rid, M.ptr, M.col, v, x, y, u, mode, a); break;
+  }
+}
+
+cudaError_t launch_spmv(const DevCsr &M, const double *x, double *y, const double *u, int mode,
+                        double a, cudaStream_t s) {
+  if (M.nrows == 0) return cudaSuccess;
+  if (M.vt == 0) spmv_dispatch<double>(M, x, y, u, mode, a, s);
+  else spmv_dispatch<float>(M, x, y, u, mode, a, s);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_patches(const DevPatch &F, const double *r, double *z, cudaStream_t s) {
+  if (F.npatch == 0) return cudaSuccess;
+  const size_t smem = (size_t)F.nslots * sizeof(double);
+  if (F.vt == 0) {
+    cudaFuncSetAttribute(patch_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    patch_kernel<double><<<F.npatch, 128, smem, s>>>(F, r, z);
+  } else {
+    cudaFuncSetAttribute(patch_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    patch_kernel<float><<<F.npatch, 128, smem, s>>>(F, r, z);
+  }
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemv(int n, const void *A, int vt, const double *x, double *y, cudaStream_t s) {
+  const int threads = 256;
+  const int grid = (int)(((long long)n * 32 + threads - 1) / threads);
+  if (vt == 0) gemv_kernel<double><<<grid, threads, 0, s>>>(n, (const double *)A, x, y);
+  else gemv_kernel<float><<<grid, threads, 0, s>>>(n, (const float *)A, x, y);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mask_copy(long long n, const uint8_t *mask, const double *b, double *r, cudaStream_t s) {
+  mask_copy_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, mask, b, r);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sub(long long n, const uint8_t *mask, const double *b, const double *q, double *r,
+                       cudaStream_t s) {
+  sub_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, mask, b, q, r);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot(long long n, const double *a, const double *b, double *partial, double *scal,
+                       int slot, cudaStream_t s) {
+  dot_partial_kernel<<<kDotBlocks, 256, 0, s>>>(n, a, b, partial);
+  finalize_kernel<<<1, 256, 0, s>>>(partial, scal, slot, 0, 0);
+  g_launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_alpha(long long n, const double *p, const double *q, double *partial, double *scal,
+                         cudaStream_t s) {
+  dot_partial_kernel<<<kDotBlocks, 256, 0, s>>>(n, p, q, partial);
+  finalize_kernel<<<1, 256, 0, s>>>(partial, scal, S_PQ, 1, 0);
+  g_launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot2(long long n, const double *r, const double *z, const double *q, double *partial,
+                        double *scal, int flexible, cudaStream_t s) {
+  dot2_partial_kernel<<<kDotBlocks, 256, 0, s>>>(n, r, z, q, partial);
+  finalize_kernel<<<1, 256, 0, s>>>(partial, scal, S_RZNEW, 2, flexible);
+  g_launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_xr(long long n, double *x, double *r, const double *p, const double *q,
+                             double *partial, double *scal, cudaStream_t s) {
+  update_xr_kernel<<<kDotBlocks, 256, 0, s>>>(n, x, r, p, q, partial, scal);
+  finalize_kernel<<<1, 256, 0, s>>>(partial, scal, S_RR, 0, 0);
+  g_launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_p(long long n, double *p, const double *z, const double *scal, cudaStream_t s) {
+  update_p_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, p, z, scal);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace rmd

@@ -1,0 +1,255 @@
+"""Thin ctypes binding of the C ABI in include/rm.h (argument marshalling
+only; every step of the solver runs in librm.so's CUDA kernels).
+
+Vectors are passed as CUDA device pointers: torch tensors (float64, on the
+GPU, contiguous) or raw integer addresses.  The library must have been built
+in-tree (paper_2211_14284_gb300/build.py); a missing library is an error,
+never a fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librm.so")
+HOST_LIB_PATH = os.path.join(HERE, "librm_host.so")
+
+RM_HGRAD, RM_HCURL, RM_HDIV = 0, 1, 2
+RM_FP64, RM_FP32 = 0, 1
+RM_PAFW, RM_PH = 0, 1
+RM_CHOL, RM_ICC = 0, 1
+RM_COARSE_NONE, RM_COARSE_P1 = 0, 1
+STATUS = {0: "RM_OK", 1: "RM_ERR_ARG", 2: "RM_ERR_CUDA", 3: "RM_ERR_OOM",
+          4: "RM_ERR_BREAKDOWN", 5: "RM_ERR_NOT_CONVERGED", 6: "RM_ERR_NAN"}
+
+EXPORTED = ["rm_default_options", "rm_setup", "rm_ndofs", "rm_apply",
+            "rm_precondition", "rm_solve", "rm_stats", "rm_destroy", "rm_last_error"]
+
+
+class RmMesh(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("vertices", ctypes.POINTER(ctypes.c_double))]
+
+
+class RmOptions(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("decomposition", ctypes.c_int),
+                ("static_condensation", ctypes.c_int), ("factor", ctypes.c_int),
+                ("coarse", ctypes.c_int), ("flexible", ctypes.c_int),
+                ("rtol", ctypes.c_double), ("max_it", ctypes.c_int),
+                ("check_every", ctypes.c_int), ("profile", ctypes.c_int)]
+
+
+class RmInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("status", ctypes.c_int),
+                ("rel_res_l2", ctypes.c_double), ("solve_ms", ctypes.c_double),
+                ("apply_ms", ctypes.c_double), ("apply_calls", ctypes.c_int),
+                ("precond_ms", ctypes.c_double), ("precond_calls", ctypes.c_int),
+                ("kernel_launches", ctypes.c_longlong)]
+
+
+class RmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load():
+    """Load librm.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() first")
+    lib = ctypes.CDLL(LIB_PATH)
+    c_dp = ctypes.POINTER(ctypes.c_double)
+    vp = ctypes.c_void_p
+    lib.rm_default_options.restype = RmOptions
+    lib.rm_setup.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(RmMesh),
+                             ctypes.c_int, c_dp, c_dp, ctypes.POINTER(RmOptions), vp]
+    lib.rm_ndofs.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong),
+                             ctypes.POINTER(ctypes.c_longlong)]
+    lib.rm_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong),
+                             ctypes.POINTER(ctypes.c_longlong),
+                             ctypes.POINTER(ctypes.c_longlong)]
+    lib.rm_apply.argtypes = [vp, vp, vp]
+    lib.rm_precondition.argtypes = [vp, vp, vp]
+    lib.rm_solve.argtypes = [vp, vp, vp, ctypes.POINTER(RmInfo)]
+    lib.rm_destroy.argtypes = [vp]
+    lib.rm_destroy.restype = None
+    lib.rm_last_error.argtypes = [vp]
+    lib.rm_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dbl_array(a):
+    if a is None:
+        return None
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def options(**kw) -> RmOptions:
+    o = load().rm_default_options()
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Solver:
+    """One discretisation + preconditioner (rm_setup), bound to a stream."""
+
+    def __init__(self, space: int, n, p: int, vertices=None, alpha=None, beta=None,
+                 stream=None, **opts):
+        lib = load()
+        n = (n, n, n) if isinstance(n, int) else tuple(n)
+        self._keep = []
+        mesh = RmMesh(n[0], n[1], n[2], None)
+        if vertices is not None:
+            arr, ptr = _dbl_array(vertices)
+            self._keep.append(arr)
+            mesh.vertices = ptr
+        al = _dbl_array(alpha)
+        be = _dbl_array(beta)
+        o = options(**opts)
+        if stream is None:
+            s = ctypes.c_void_p(0)
+        elif isinstance(stream, int):
+            s = ctypes.c_void_p(stream)
+        else:
+            s = ctypes.c_void_p(stream.cuda_stream)
+        h = ctypes.c_void_p()
+        rc = lib.rm_setup(ctypes.byref(h), space, ctypes.byref(mesh), p,
+                          al[1] if al else None, be[1] if be else None,
+                          ctypes.byref(o), s)
+        if rc != 0:
+            raise RmError(rc, lib.rm_last_error(None).decode())
+        self.h = h
+        self.lib = lib
+        self.space, self.n, self.p = space, n, p
+        a, f = ctypes.c_longlong(), ctypes.c_longlong()
+        lib.rm_ndofs(h, ctypes.byref(a), ctypes.byref(f))
+        self.size, self.nfree = a.value, f.value
+
+    def _check(self, rc):
+        if rc != 0:
+            raise RmError(rc, self.lib.rm_last_error(self.h).decode())
+
+    def apply(self, x, y):
+        self._check(self.lib.rm_apply(self.h, _ptr(x), _ptr(y)))
+
+    def precondition(self, r, z):
+        self._check(self.lib.rm_precondition(self.h, _ptr(r), _ptr(z)))
+
+    def solve(self, b, x, check=True):
+        info = RmInfo()
+        rc = self.lib.rm_solve(self.h, _ptr(b), _ptr(x), ctypes.byref(info))
+        if check and rc not in (0,):
+            self._check(rc)
+        return {"iterations": info.iterations, "status": STATUS.get(info.status),
+                "rel_res_l2": info.rel_res_l2, "solve_ms": info.solve_ms,
+                "apply_ms": info.apply_ms, "apply_calls": info.apply_calls,
+                "precond_ms": info.precond_ms, "precond_calls": info.precond_calls,
+                "kernel_launches": info.kernel_launches}
+
+    def stats(self):
+        a, b, c = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        self.lib.rm_stats(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+        return {"patches": a.value, "slots": b.value, "factor_nnz": c.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# host-only setup inspection (librm_host.so, no CUDA): used by CPU tests
+# ---------------------------------------------------------------------------
+class HostProbe:
+    def __init__(self):
+        if not os.path.exists(HOST_LIB_PATH):
+            raise RuntimeError(f"{HOST_LIB_PATH} is missing: run __graft_entry__.build()")
+        self.lib = ctypes.CDLL(HOST_LIB_PATH)
+        self.lib.rmh_error.restype = ctypes.c_char_p
+
+    def basis(self, p):
+        import numpy as np
+        S = np.zeros((p + 1, p + 1)); lam = np.zeros(p); B = np.zeros((p + 1, p + 1))
+        A = np.zeros((p + 1, p + 1)); D = np.zeros((p, p + 1)); Js = np.zeros((p + 1, 2))
+        P = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        rc = self.lib.rmh_basis(p, P(S), P(lam), P(B), P(A), P(D), P(Js))
+        if rc:
+            raise RuntimeError(self.lib.rmh_error().decode())
+        return dict(S=S, lam=lam, Bhat=B, Ahat=A, D=D, Js=Js)
+
+    def build(self, k, n, p, X, alpha, beta, mode, factor, coarse=True):
+        import numpy as np
+        n = (n, n, n) if isinstance(n, int) else tuple(n)
+        narr = (ctypes.c_int * 3)(*n)
+        self._keep = [np.ascontiguousarray(X, float), np.ascontiguousarray(alpha, float),
+                      np.ascontiguousarray(beta, float)]
+        P = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        rc = self.lib.rmh_build(k, narr, p, P(self._keep[0]), P(self._keep[1]),
+                                P(self._keep[2]), mode, factor, int(coarse))
+        if rc:
+            raise RuntimeError(self.lib.rmh_error().decode())
+
+    def csr(self, which):
+        import numpy as np
+        import scipy.sparse as sp
+        nr, nnz = ctypes.c_int(), ctypes.c_longlong()
+        self.lib.rmh_csr_size(which, ctypes.byref(nr), ctypes.byref(nnz))
+        ptr = np.zeros(nr.value + 1, np.int64); col = np.zeros(nnz.value, np.int32)
+        val = np.zeros(nnz.value)
+        self.lib.rmh_csr_get(which, ptr.ctypes.data_as(ctypes.c_void_p),
+                             col.ctypes.data_as(ctypes.c_void_p),
+                             val.ctypes.data_as(ctypes.c_void_p))
+        ncol = int(col.max()) + 1 if nnz.value else 0
+        return ptr, col, val
+
+    def families(self):
+        import numpy as np
+        out = []
+        for f in range(self.lib.rmh_nfamilies()):
+            ns, npch, nnz = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+            self.lib.rmh_family_size(f, ctypes.byref(ns), ctypes.byref(npch), ctypes.byref(nnz))
+            sm = np.zeros(npch.value * ns.value, np.int32)
+            rp = np.zeros(ns.value + 1, np.int32)
+            col = np.zeros(nnz.value, np.int32)
+            val = np.zeros(npch.value * nnz.value)
+            v = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+            self.lib.rmh_family_get(f, v(sm), v(rp), v(col), v(val))
+            out.append(dict(nslots=ns.value, npatch=npch.value, nnz=nnz.value,
+                            slotmap=sm.reshape(npch.value, ns.value), rowptr=rp, col=col,
+                            val=val.reshape(npch.value, nnz.value)))
+        return out
+
+    def coarse_inverse(self):
+        import numpy as np
+        nc = self.lib.rmh_coarse_size()
+        A = np.zeros((nc, nc))
+        self.lib.rmh_coarse_inverse(A.ctypes.data_as(ctypes.c_void_p))
+        return A

@@ -1,0 +1,220 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle on
+the same seeded inputs.
+
+Tolerances: operator apply 1e-12 relative (max-norm), preconditioner 1e-11,
+solution 1e-10 relative when both sides solve to 1e-12 (the FP64 targets),
+l2 relative residual <= 1e-8 for the mixed-precision preconditioner.
+"""
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle.auxiliary import assemble_aux
+from oracle.discretization import Problem
+from oracle.krylov import pcg
+from oracle.relaxation import PAFW, SCPAFW, SCPH
+from paper_2211_14284_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    return torch.tensor(np.asarray(a, float), dtype=torch.float64, device="cuda")
+
+
+def _host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def _setup(k, n, p, perturb, coef, seed=11, **opts):
+    from paper_2211_14284_gb300.rm import Solver
+    X = inputs.vertices(n, perturb=perturb, seed=seed)
+    nn = n if np.isscalar(n) else tuple(n)
+    if coef:
+        al = inputs.loguniform_coefficient(nn, 0.1, 10, seed=seed + 1)
+        be = inputs.loguniform_coefficient(nn, 0.1, 10, seed=seed + 2)
+    else:
+        al = inputs.constant_coefficient(nn, 1.0)
+        be = inputs.constant_coefficient(nn, 1.0)
+    s = Solver(k, n, p, vertices=X, alpha=al, beta=be, **opts)
+    pr = Problem(k, n, p, X, al, be)
+    assert s.size == pr.lat.size and s.nfree == len(pr.free)
+    return s, pr
+
+
+APPLY_CASES = [(0, 2, 1, 0.0, False), (0, 3, 3, 0.15, True), (0, (2, 3, 4), 2, 0.1, True),
+               (1, 2, 2, 0.1, True), (1, 3, 3, 0.0, False), (2, 2, 3, 0.15, True),
+               (2, (3, 2, 2), 2, 0.0, True), (0, 2, 7, 0.1, True), (1, 2, 5, 0.1, False)]
+
+
+@pytest.mark.parametrize("k,n,p,perturb,coef", APPLY_CASES)
+def test_apply_parity(k, n, p, perturb, coef):
+    s, pr = _setup(k, n, p, perturb, coef)
+    x = inputs.normal_rhs(pr.lat.size, 21)
+    y = torch.zeros(pr.lat.size, dtype=torch.float64, device="cuda")
+    s.apply(_dev(x), y)
+    want = pr.apply(x)
+    got = _host(y)
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+    dmask = np.ones(pr.lat.size, bool)
+    dmask[pr.free] = False
+    assert np.all(got[dmask] == 0.0)
+
+
+def _oracle_prec(pr, mode):
+    P = assemble_aux(pr)[pr.free][:, pr.free]
+    if mode == "pafw":
+        return PAFW(pr, M=P, factor="chol")
+    if mode == "sc-icc":
+        return SCPAFW(pr, P, factor="icc")
+    if mode == "sc-chol":
+        return SCPAFW(pr, P, factor="chol")
+    return SCPH(pr, P)
+
+
+PREC_CASES = [(0, 3, 2, 0.0, "pafw", {}), (0, 3, 3, 0.1, "sc-icc", dict(static_condensation=1, factor=1)),
+              (2, 3, 2, 0.1, "sc-icc", dict(static_condensation=1, factor=1)),
+              (1, 3, 3, 0.1, "sc-chol", dict(static_condensation=1, factor=0)),
+              (1, 2, 3, 0.1, "scph", dict(static_condensation=1, decomposition=1, factor=1)),
+              (0, (2, 3, 3), 2, 0.15, "sc-chol", dict(static_condensation=1, factor=0))]
+
+
+@pytest.mark.parametrize("k,n,p,perturb,mode,opts", PREC_CASES)
+def test_precondition_parity(k, n, p, perturb, mode, opts):
+    s, pr = _setup(k, n, p, perturb, True, **opts)
+    r = inputs.normal_rhs(pr.lat.size, 22)
+    r[np.setdiff1d(np.arange(pr.lat.size), pr.free)] = 0.0
+    z = torch.zeros(pr.lat.size, dtype=torch.float64, device="cuda")
+    s.precondition(_dev(r), z)
+    M = _oracle_prec(pr, mode)
+    want = np.zeros(pr.lat.size)
+    want[pr.free] = M.apply(r[pr.free])
+    got = _host(z)
+    assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()
+
+
+def test_solve_config1_parity():
+    """4x4x4 uniform mesh, Q_4 (4913 lattice DOFs), PAFW additive with exact
+    Cholesky and P1 coarse: GPU solution vs the direct solve, both to 1e-12."""
+    s, pr = _setup(0, 4, 4, 0.0, False, rtol=1e-12, max_it=400)
+    b = inputs.normal_rhs(pr.lat.size, 1)
+    x = torch.zeros(pr.lat.size, dtype=torch.float64, device="cuda")
+    info = s.solve(_dev(b), x)
+    assert info["status"] == "RM_OK"
+    A = pr.A_free().tocsc()
+    xd = spla.spsolve(A, b[pr.free])
+    got = _host(x)[pr.free]
+    assert np.linalg.norm(got - xd) <= 1e-10 * np.linalg.norm(xd)
+    # iteration count to 1e-8 equals the oracle's PCG (same preconditioner)
+    s8, _ = _setup(0, 4, 4, 0.0, False, rtol=1e-8)
+    x8 = torch.zeros_like(x)
+    i8 = s8.solve(_dev(b), x8)
+    _, io = pcg(A, b[pr.free], PAFW(pr).apply, rtol=1e-8)
+    assert abs(i8["iterations"] - io["iterations"]) <= 1
+    assert i8["rel_res_l2"] <= 1e-8
+
+
+def test_manufactured_solution_config1():
+    """Config 1 RHS from the sin-product solution: the GPU solution has the
+    oracle's L2 error."""
+    s, pr = _setup(0, 4, 4, 0.0, False, rtol=1e-12)
+    u = lambda x: np.prod(np.sin(np.pi * x), axis=1)
+    b = pr.load_vector_hgrad(lambda x: (1 + 3 * np.pi ** 2) * u(x))
+    x = torch.zeros(pr.lat.size, dtype=torch.float64, device="cuda")
+    s.solve(_dev(b), x)
+    got = _host(x)
+    err = pr.l2_error_hgrad(got, u)
+    xd = np.zeros(pr.lat.size)
+    xd[pr.free] = spla.spsolve(pr.A_free().tocsc(), b[pr.free])
+    assert abs(err - pr.l2_error_hgrad(xd, u)) <= 1e-9 * err
+    assert err < 1e-3
+
+
+@pytest.mark.parametrize("k,mode,opts", [(0, "sc-icc", dict(static_condensation=1, factor=1)),
+                                         (1, "scph", dict(static_condensation=1, decomposition=1, factor=1))])
+def test_solve_distorted_parity(k, mode, opts):
+    """Distorted mesh, SC preconditioners on the auxiliary operator: GPU
+    solution vs direct solve (both to 1e-12), iteration count vs oracle PCG."""
+    n, p = 3, 3
+    s, pr = _setup(k, n, p, 0.1, True, rtol=1e-12, max_it=600, **opts)
+    b = inputs.normal_rhs(pr.lat.size, 3)
+    x = torch.zeros(pr.lat.size, dtype=torch.float64, device="cuda")
+    info = s.solve(_dev(b), x)
+    assert info["status"] == "RM_OK"
+    A = pr.A_free().tocsc()
+    xd = spla.spsolve(A, b[pr.free])
+    assert np.linalg.norm(_host(x)[pr.free] - xd) <= 1e-10 * np.linalg.norm(xd)
+    s8, _ = _setup(k, n, p, 0.1, True, rtol=1e-8, **opts)
+    x8 = torch.zeros_like(x)
+    i8 = s8.solve(_dev(b), x8)
+    _, io = pcg(A, b[pr.free], _oracle_prec(pr, mode).apply, rtol=1e-8)
+    assert abs(i8["iterations"] - io["iterations"]) <= 1
+
+
+@pytest.mark.parametrize("k", [0, 1])
+def test_mixed_precision_reaches_1e8(k):
+    """FP32 preconditioner inside FP64 flexible CG reaches l2 relative
+    residual 1e-8; the true residual is checked with the oracle's operator."""
+    opts = dict(static_condensation=1, factor=1, precision=1, flexible=1)
+    if k == 1:
+        opts["decomposition"] = 1
+    s, pr = _setup(k, 3, 3, 0.1, True, rtol=1e-8, **opts)
+    b = inputs.normal_rhs(pr.lat.size, 4)
+    x = torch.zeros(pr.lat.size, dtype=torch.float64, device="cuda")
+    info = s.solve(_dev(b), x)
+    assert info["status"] == "RM_OK"
+    xf = _host(x)
+    bf = b.copy()
+    bf[np.setdiff1d(np.arange(pr.lat.size), pr.free)] = 0.0
+    res = np.linalg.norm(bf - pr.apply(xf)) / np.linalg.norm(bf)
+    assert res <= 2e-8
+
+
+@pytest.mark.parametrize("k", [0, 1])
+def test_config2_full_size_sampled(k):
+    """8x8x8 mesh with 10% interior-vertex perturbation, p=7 (H(grad)
+    185,193 / H(curl) 545,832 lattice DOFs), in the bench's configuration:
+    the apply checked on sampled rows computed one by one by the oracle,
+    the solve checked by its true residual on sampled rows."""
+    n, p = 8, 7
+    opts = dict(static_condensation=1, factor=1)
+    if k == 1:
+        opts["decomposition"] = 1
+    from paper_2211_14284_gb300.rm import Solver
+    X = inputs.vertices(n, perturb=0.1, seed=2)
+    al = inputs.constant_coefficient(n)
+    be = inputs.constant_coefficient(n)
+    s = Solver(k, n, p, vertices=X, alpha=al, beta=be, rtol=1e-8, **opts)
+    pr = Problem(k, n, p, X, al, be)
+    rng = np.random.default_rng(5)
+    rows = rng.choice(pr.free, 40, replace=False)
+    x = inputs.normal_rhs(pr.lat.size, 23)
+    y = torch.zeros(pr.lat.size, dtype=torch.float64, device="cuda")
+    s.apply(_dev(x), y)
+    want = pr.apply_rows(x, rows)
+    got = _host(y)[rows]
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(_host(y)).max()
+    b = inputs.normal_rhs(pr.lat.size, 2)
+    xs = torch.zeros(pr.lat.size, dtype=torch.float64, device="cuda")
+    info = s.solve(_dev(b), xs)
+    assert info["status"] == "RM_OK" and info["rel_res_l2"] <= 1e-8
+    xh = _host(xs)
+    r_rows = b[rows] - pr.apply_rows(xh, rows)
+    bn = np.linalg.norm(b[pr.free])
+    # each sampled residual entry is bounded by the l2 norm of the residual
+    assert np.abs(r_rows).max() <= 1.5e-8 * bn
+
+
+def test_bad_arguments_are_errors():
+    from paper_2211_14284_gb300.rm import RmError, Solver
+    with pytest.raises(RmError):
+        Solver(0, 1, 2)                     # fewer than 2 cells
+    with pytest.raises(RmError):
+        Solver(0, 2, 0)                     # p = 0
+    with pytest.raises(RmError):
+        Solver(0, 2, 2, decomposition=1, static_condensation=1)   # PH needs H(curl)
+    with pytest.raises(RmError):
+        Solver(1, 2, 2, static_condensation=1, factor=1)          # ICC(0) breakdown

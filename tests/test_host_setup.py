@@ -1,0 +1,179 @@
+"""CPU checks of the CUDA path's host FP64 setup (librm_host.so) against the
+oracle: 1D basis, auxiliary operator, Schur complement, patch lists and
+factors, coarse operator.  No GPU needed; the oracle only supplies expected
+values."""
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle.auxiliary import assemble_aux
+from oracle.basis import FDM1D
+from oracle.discretization import Lattice, Problem
+from oracle.relaxation import (Coarse, Condensed, cholesky, discrete_gradient,
+                               icc0, patch_lists)
+from paper_2211_14284_gb300 import inputs
+from paper_2211_14284_gb300.rm import HostProbe
+
+
+@pytest.fixture(scope="module")
+def probe():
+    return HostProbe()
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 7, 10, 12])
+def test_basis_matches_oracle(probe, p):
+    h = probe.basis(p)
+    e = FDM1D(p)
+    assert np.abs(h["S"] - e.S).max() < 1e-12
+    assert np.abs(h["lam"] - e.lam).max() < 1e-11 * e.lam.max()
+    assert np.abs(h["Bhat"] - e.Bhat).max() < 1e-12
+    assert np.abs(h["Ahat"] - e.Ahat).max() < 1e-11 * np.abs(e.Ahat).max()
+    assert np.abs(h["D"] - e.D).max() < 1e-11 * np.abs(e.D).max()
+    Js, _ = e.injection_from_p1()
+    assert np.abs(h["Js"] - Js).max() < 1e-12
+
+
+def _csr_dense(ptr, col, val, n):
+    return sp.csr_matrix((val, col, ptr), shape=(n, n)).toarray()
+
+
+def _case(k, n, p, perturb, seed=3, coef=False):
+    X = inputs.vertices(n, perturb=perturb, seed=seed)
+    if coef:
+        al = inputs.loguniform_coefficient(n, 0.1, 10, seed=seed + 1)
+        be = inputs.loguniform_coefficient(n, 0.1, 10, seed=seed + 2)
+    else:
+        al = inputs.constant_coefficient(n, 1.0)
+        be = inputs.constant_coefficient(n, 1.0)
+    return X, al, be, Problem(k, n, p, X, al, be)
+
+
+@pytest.mark.parametrize("k,p,perturb,coef", [(0, 3, 0.15, True), (1, 2, 0.15, False),
+                                              (2, 2, 0.1, True), (0, 4, 0.0, False)])
+def test_aux_and_schur_match_oracle(probe, k, p, perturb, coef):
+    n = 2
+    X, al, be, pr = _case(k, n, p, perturb, coef=coef)
+    probe.build(k, n, p, X, al, be, mode=1, factor=0, coarse=False)
+    nf = len(pr.free)
+    P = _csr_dense(*probe.csr(0), nf)
+    Po = assemble_aux(pr)[pr.free][:, pr.free]
+    scale = abs(Po).max()
+    assert np.abs(P - Po.toarray()).max() < 1e-12 * scale
+    sc = Condensed(Po, pr.lat, pr.free)
+    S = _csr_dense(*probe.csr(1), nf)
+    assert np.abs(S[np.ix_(sc.G, sc.G)] - sc.S.toarray()).max() < 1e-11 * scale
+    assert np.abs(S[np.ix_(sc.I, sc.I)]).max() == 0.0
+
+
+def _compare_family(fam, pats_lat, Mfree_fn, factor, free):
+    """fam: C++ family; pats_lat: oracle patch lists (lattice ids);
+    Mfree_fn(idx_lat) -> dense patch matrix from the oracle."""
+    assert fam["npatch"] == len(pats_lat)
+    rp, col = fam["rowptr"], fam["col"]
+    ns = fam["nslots"]
+    for pi, want in enumerate(pats_lat):
+        sm = fam["slotmap"][pi]
+        valid = np.flatnonzero(sm >= 0)
+        assert np.array_equal(sm[valid], want)
+        Ld = np.zeros((ns, ns))
+        for i in range(ns):
+            Ld[i, col[rp[i]:rp[i + 1]]] = fam["val"][pi, rp[i]:rp[i + 1]]
+        Lv = Ld[np.ix_(valid, valid)]
+        A = Mfree_fn(want)
+        Lo = icc0(A) if factor == "icc" else cholesky(A)
+        assert np.abs(Lv - Lo).max() < 1e-10 * np.abs(Lo).max()
+        inval = np.flatnonzero(sm < 0)
+        if len(inval):
+            assert np.allclose(Ld[np.ix_(inval, inval)], np.eye(len(inval)))
+
+
+def _free_pos(free, size):
+    pos = -np.ones(size, int)
+    pos[free] = np.arange(len(free))
+    return pos
+
+
+@pytest.mark.parametrize("k,p,factor", [(0, 2, "icc"), (0, 3, "chol"), (1, 3, "chol"),
+                                        (2, 2, "icc")])
+def test_sc_pafw_patches_match_oracle(probe, k, p, factor):
+    n = 3
+    X, al, be, pr = _case(k, n, p, 0.1, coef=True)
+    probe.build(k, n, p, X, al, be, mode=1, factor=int(factor == "icc"), coarse=False)
+    fams = probe.families()
+    Po = assemble_aux(pr)[pr.free][:, pr.free]
+    sc = Condensed(Po, pr.lat, pr.free)
+    G = pr.free[sc.G]
+    pats = patch_lists(pr.lat, (), G)
+    posG = _free_pos(G, pr.lat.size)
+    S = sc.S.tocsr()
+    _compare_family(fams[0], pats, lambda idx: S[posG[idx]][:, posG[idx]].toarray(),
+                    factor, pr.free)
+
+
+def test_pafw_cholesky_patches_match_oracle(probe):
+    n, p = 3, 3
+    X, al, be, pr = _case(0, n, p, 0.0)
+    probe.build(0, n, p, X, al, be, mode=0, factor=0, coarse=False)
+    fams = probe.families()
+    A = pr.A_free().tocsr()
+    pats = patch_lists(pr.lat, (), pr.free)
+    pos = _free_pos(pr.free, pr.lat.size)
+    _compare_family(fams[0], pats, lambda idx: A[pos[idx]][:, pos[idx]].toarray(),
+                    "chol", pr.free)
+
+
+def test_sc_ph_matches_oracle(probe):
+    n, p = 2, 3
+    X, al, be, pr = _case(1, n, p, 0.1)
+    probe.build(1, n, p, X, al, be, mode=2, factor=1, coarse=False)
+    fams = probe.families()
+    Po = assemble_aux(pr)[pr.free][:, pr.free]
+    sc = Condensed(Po, pr.lat, pr.free)
+    G1 = pr.free[sc.G]
+    pos1 = _free_pos(G1, pr.lat.size)
+    S = sc.S.tocsr()
+    for m in range(3):
+        pats = patch_lists(pr.lat, (m,), G1)
+        _compare_family(fams[m], pats, lambda idx: S[pos1[idx]][:, pos1[idx]].toarray(),
+                        "chol", pr.free)
+    p0 = Problem(0, n, p, X, al, be)
+    B = assemble_aux(p0, mass_coef=np.zeros_like(be), stiff_coef=be)
+    sc0 = Condensed(B[p0.free][:, p0.free].tocsr(), p0.lat, p0.free)
+    S0 = _csr_dense(*probe.csr(5), len(p0.free))
+    assert np.abs(S0[np.ix_(sc0.G, sc0.G)] - sc0.S.toarray()).max() < 1e-11 * abs(B).max()
+    G0 = p0.free[sc0.G]
+    pos0 = _free_pos(G0, p0.lat.size)
+    S0o = sc0.S.tocsr()
+    _compare_family(fams[3], patch_lists(p0.lat, (), G0),
+                    lambda idx: S0o[pos0[idx]][:, pos0[idx]].toarray(), "icc", p0.free)
+    ptr, col, val = probe.csr(6)
+    Dh = sp.csr_matrix((val, col, ptr), shape=(pr.lat.size, p0.lat.size))
+    Do = discrete_gradient(p0.lat, pr.lat)[G1][:, G0]
+    assert abs(Dh[G1][:, G0] - Do).max() < 1e-12 * abs(Do).max()
+
+
+@pytest.mark.parametrize("k,perturb", [(0, 0.0), (0, 0.15), (1, 0.1), (2, 0.1)])
+def test_coarse_matches_oracle(probe, k, perturb):
+    n, p = 3, 3
+    X, al, be, pr = _case(k, n, p, perturb, coef=True)
+    probe.build(k, n, p, X, al, be, mode=1, factor=0, coarse=True)
+    Ainv = probe.coarse_inverse()
+    c = Coarse(pr)
+    want = np.linalg.inv(c.A0)
+    assert np.abs(Ainv - want).max() < 1e-10 * np.abs(want).max()
+    ptr, col, val = probe.csr(4)
+    R0 = sp.csr_matrix((val, col, ptr), shape=(len(c.cp.free), pr.lat.size))
+    assert abs(R0[:, pr.free] - c.R0T.T).max() < 1e-12
+
+
+def test_icc_breakdown_agrees(probe):
+    """ICC(0) of NCE_2 vertex-star Schur complements has a non-positive pivot
+    (the paper notes that ICC(0) may fail); both sides report it."""
+    X, al, be, pr = _case(1, 2, 2, 0.0)
+    with pytest.raises(RuntimeError, match="breakdown"):
+        probe.build(1, 2, 2, X, al, be, mode=1, factor=1, coarse=False)
+    from oracle.relaxation import SCPAFW
+    P = assemble_aux(pr)[pr.free][:, pr.free]
+    with pytest.raises(np.linalg.LinAlgError):
+        SCPAFW(pr, P, factor="icc", coarse=False)

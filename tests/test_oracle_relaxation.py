@@ -140,7 +140,10 @@ def test_schur_identity(k):
     yI, rG = sc.condense(r)
     zG = np.linalg.solve(sc.S.toarray(), rG)
     z = sc.expand(yI, zG)
-    assert np.allclose(z, spla.spsolve(A.tocsc(), r), rtol=1e-10, atol=1e-12)
+    # A_II is block diagonal up to quadrature round-off (~1e-15 relative),
+    # which the block inverse drops
+    xd = spla.spsolve(A.tocsc(), r)
+    assert np.linalg.norm(z - xd) <= 1e-11 * np.linalg.norm(xd)
     # R_G A R_I^T: columns of A at interior DOFs, condensed
     AI = A[:, sc.I].toarray()
     RG = np.hstack([-(sc.PGI @ np.linalg.inv(sc.PII.toarray())), np.eye(len(sc.G))])
