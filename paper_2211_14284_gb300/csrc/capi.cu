@@ -221,7 +221,7 @@ void precondition(rm_handle *h, const double *r, double *z) {
   CK(cudaMemsetAsync(z, 0, h->size * sizeof(double), s));
   if (h->sc) {
     CK(launch_spmv(h->Binv, r, h->w, nullptr, 0, 1.0, s));       // w_I = P_II^-1 r_I
-    CK(launch_spmv(h->E, h->w, h->rt, r, 2, -1.0, s));           // rt_G = r_G - E w_I
+    CK(launch_spmv(h->E, r, h->rt, r, 2, -1.0, s));              // rt_G = r_G - P_GI P_II^-1 r_I
     for (auto &F : h->fam) CK(launch_patches(F, h->rt, z, s));   // z_G = sum_v S_v^-1 rt
     if (h->ph) {
       CK(launch_spmv(h->DtT, h->rt, h->u0, nullptr, 0, 1.0, s)); // u0 = D~^T rt
