@@ -138,6 +138,26 @@ int rm_stats(const rm_handle *h, long long *patches, long long *slots,
 void rm_destroy(rm_handle *h);
 const char *rm_last_error(const rm_handle *h);
 
+/* z = B r without allocating: the same relaxation as rm_precondition for a
+ * handle built without static condensation (vertex-star patches plus the
+ * p = 1 coarse correction), for callers that must not allocate device memory
+ * while they run -- code that lives inside a device-memory budget owned by
+ * another allocator (a framework's caching allocator hands out every byte),
+ * or that cannot afford the device-wide synchronisation cudaMalloc/cudaFree
+ * imply.  The paper has no counterpart; it is a library convenience.
+ *
+ * The call performs no cudaMalloc, cudaFree or other allocating call.  Its
+ * scratch (2 x RM_NOALLOC_MAX_COARSE doubles) is a static device array of the
+ * library, present on every GPU that loads it until the process exits.  The
+ * first call on each device looks up that array's device address (a one-time
+ * set-up); make that first call before any stream capture.  Every call shares
+ * the array: calls that overlap on the GPU race on it.  Returns RM_ERR_ARG for
+ * a statically condensed handle (whose relaxation needs lattice-sized scratch)
+ * or a coarse space larger than RM_NOALLOC_MAX_COARSE.  r, z: device, lattice
+ * length, not aliased; z is overwritten. */
+#define RM_NOALLOC_MAX_COARSE 8192
+int rm_precondition_noalloc(rm_handle *h, const double *r, double *z);
+
 #ifdef __cplusplus
 }
 #endif

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -546,3 +547,67 @@ const char *rm_last_error(const rm_handle *h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free preconditioner entry point.
+//
+// Its scratch (the restricted residual and the coarse solution of the p = 1
+// correction) lives in this file-scope device array instead of in buffers
+// owned by the handle.  Every GPU that loads the library holds the array
+// (2 x RM_NOALLOC_MAX_COARSE doubles = 128 KiB) until the process exits.  All
+// calls share it and it keeps the last call's contents; both halves are fully
+// overwritten before they are read, so nothing needs clearing.  Calls whose
+// work overlaps on the GPU (on different streams) race on the array.
+// ---------------------------------------------------------------------------
+namespace {
+static __device__ __align__(256) double g_noalloc_scratch[2 * RM_NOALLOC_MAX_COARSE];
+
+std::mutex g_noalloc_mutex;
+double *g_noalloc_ptr[64] = {};  // device address of the array, per device ordinal
+
+// In host code the array's name is only a host-side stand-in: the device
+// address is looked up once per device, with that device current.
+double *noalloc_scratch(int dev) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (dev < 0 || dev >= 64) throw std::runtime_error("device ordinal out of range");
+  if (!g_noalloc_ptr[dev]) {
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess)
+      throw CudaError(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = (double *)ptr;
+  }
+  return g_noalloc_ptr[dev];
+}
+}  // namespace
+
+extern "C" int rm_precondition_noalloc(rm_handle *h, const double *r, double *z) {
+  if (!h || !r || !z) return fail(h, RM_ERR_ARG, "rm_precondition_noalloc: NULL argument");
+  if (r == z) return fail(h, RM_ERR_ARG, "rm_precondition_noalloc: r and z must not alias");
+  if (h->sc)
+    return fail(h, RM_ERR_ARG,
+                "rm_precondition_noalloc: statically condensed relaxations need "
+                "lattice-sized scratch; use rm_precondition");
+  if (h->nc > RM_NOALLOC_MAX_COARSE)
+    return fail(h, RM_ERR_ARG,
+                "rm_precondition_noalloc: coarse space has " + std::to_string(h->nc) +
+                    " DOFs, more than RM_NOALLOC_MAX_COARSE = " +
+                    std::to_string(RM_NOALLOC_MAX_COARSE));
+  try {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    double *scratch = noalloc_scratch(dev);
+    double *cc = scratch, *ce = scratch + RM_NOALLOC_MAX_COARSE;
+    cudaStream_t s = h->stream;
+    CK(cudaMemsetAsync(z, 0, h->size * sizeof(double), s));
+    for (auto &F : h->fam) CK(launch_patches(F, r, z, s));
+    if (h->nc > 0) {
+      CK(launch_spmv(h->R0, r, cc, nullptr, 0, 1.0, s));
+      CK(launch_gemv(h->nc, h->A0inv, h->vt, cc, ce, s));
+      CK(launch_spmv(h->R0T, ce, z, nullptr, 1, 1.0, s));
+    }
+  } catch (const std::exception &e) {
+    return fail(h, RM_ERR_CUDA, e.what());
+  }
+  return RM_OK;
+}

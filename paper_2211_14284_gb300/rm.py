@@ -25,7 +25,9 @@ STATUS = {0: "RM_OK", 1: "RM_ERR_ARG", 2: "RM_ERR_CUDA", 3: "RM_ERR_OOM",
           4: "RM_ERR_BREAKDOWN", 5: "RM_ERR_NOT_CONVERGED", 6: "RM_ERR_NAN"}
 
 EXPORTED = ["rm_default_options", "rm_setup", "rm_ndofs", "rm_apply",
-            "rm_precondition", "rm_solve", "rm_stats", "rm_destroy", "rm_last_error"]
+            "rm_precondition", "rm_solve", "rm_stats", "rm_destroy", "rm_last_error",
+            "rm_precondition_noalloc"]
+RM_NOALLOC_MAX_COARSE = 8192
 
 
 class RmMesh(ctypes.Structure):
@@ -78,6 +80,7 @@ def load():
                              ctypes.POINTER(ctypes.c_longlong)]
     lib.rm_apply.argtypes = [vp, vp, vp]
     lib.rm_precondition.argtypes = [vp, vp, vp]
+    lib.rm_precondition_noalloc.argtypes = [vp, vp, vp]
     lib.rm_solve.argtypes = [vp, vp, vp, ctypes.POINTER(RmInfo)]
     lib.rm_destroy.argtypes = [vp]
     lib.rm_destroy.restype = None
@@ -153,6 +156,11 @@ class Solver:
 
     def apply(self, x, y):
         self._check(self.lib.rm_apply(self.h, _ptr(x), _ptr(y)))
+
+    def precondition_noalloc(self, r, z):
+        """rm_precondition_noalloc: same result for a non-condensed handle,
+        scratch in the library's static device array (no allocation)."""
+        self._check(self.lib.rm_precondition_noalloc(self.h, _ptr(r), _ptr(z)))
 
     def precondition(self, r, z):
         self._check(self.lib.rm_precondition(self.h, _ptr(r), _ptr(z)))
