@@ -154,11 +154,21 @@ DevPatch upload_family(rm_handle *h, const PatchFamily &F) {
   D.frows = h->upload(F.frows);
   D.blev = h->upload(F.blev);
   D.brows = h->upload(F.brows);
-  D.val = h->upload_vals(F.val);
   D.vt = h->vt;
+  if (F.inverse) {
+    D.inverse = 1;
+    D.ivals = F.ivals();
+    D.pos_slot = h->upload(F.pos_slot);
+    D.pos_blk = h->upload(F.pos_blk);
+    D.bptr = h->upload(F.bptr);
+    D.boff = h->upload(F.boff);
+    D.val = h->upload_vals(F.ival);
+  } else {
+    D.val = h->upload_vals(F.val);
+  }
   h->stat_patches += F.npatch;
   h->stat_slots += (long long)F.npatch * F.nslots;
-  h->stat_nnz += (long long)F.npatch * F.nnz();
+  h->stat_nnz += (long long)F.npatch * (F.inverse ? F.ivals() : F.nnz());
   if ((size_t)F.nslots * sizeof(double) > 200 * 1024) throw std::runtime_error("patch too large for shared memory");
   return D;
 }
@@ -208,6 +218,14 @@ void build_apply(rm_handle *h, const Geometry &geo, const std::vector<double> &a
                    3 * q3 + (size_t)q * (p + 1) * (p + 1) + (size_t)q * q * (p + 1);
   if (A.smem_doubles * sizeof(double) > 227 * 1024)
     throw std::runtime_error("degree too high for the general apply kernel's shared memory (p <= 8)");
+  // pullback weights at every quadrature point, computed once on the device
+  A.nA = k == 0 ? 1 : 6;
+  A.nAB = A.nA + (k == 2 ? 1 : 6);
+  const int ncell = h->n[0] * h->n[1] * h->n[2];
+  double *G = h->dalloc<double>((size_t)ncell * A.nAB * q3);
+  A.G = G;
+  CK(launch_metric(A, G, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
 }
 
 int fail(rm_handle *h, int code, const std::string &msg) {

@@ -21,6 +21,8 @@ struct ApplyDev {
   const double *X;         // vertices, 3 per vertex
   const double *alpha, *beta;
   const double *tabs;      // Ts q(p+1) | Tr qp | D1 p(p+1) | xq q | wq q
+  const double *G;         // pullback weights per cell and point (metric_kernel)
+  int nA, nAB;             // entries of stage A, of both stages (1 or 6 each)
   size_t smem_doubles;
 };
 
@@ -45,11 +47,16 @@ struct DevPatch {
   const int *flev = nullptr, *frows = nullptr, *blev = nullptr, *brows = nullptr;
   const void *val = nullptr;     // npatch x nnz, double or float
   int vt = 0;
+  // block-inverse form (exact factorisations): per patch the dense inverse
+  // of every decoupled block, column-major, concatenated (ivals values)
+  int inverse = 0, ivals = 0;
+  const int *pos_slot = nullptr, *pos_blk = nullptr, *bptr = nullptr, *boff = nullptr;
 };
 
 // launchers (kernels.cu); launch_count() = kernels launched so far in this process
 long long launch_count();
 cudaError_t launch_apply(const ApplyDev &A, const double *x, double *y, cudaStream_t s);
+cudaError_t launch_metric(const ApplyDev &A, double *G, cudaStream_t s);
 cudaError_t launch_spmv(const DevCsr &M, const double *x, double *y, const double *u, int mode,
                         double a, cudaStream_t s);
 cudaError_t launch_patches(const DevPatch &F, const double *r, double *z, cudaStream_t s);

@@ -148,6 +148,26 @@ int rmh_family_get(int f, int *slotmap, int *rowptr, int *col, double *val) {
   return 0;
 }
 
+// Block-inverse form of a family: is_inverse, number of blocks, values per patch.
+int rmh_family_inverse_size(int f, int *is_inverse, int *nblocks, int *nvals) {
+  if (!g || f < 0 || f >= (int)g->fams.size()) return 1;
+  const PatchFamily &F = g->fams[f];
+  *is_inverse = F.inverse;
+  *nblocks = F.inverse ? (int)F.bptr.size() - 1 : 0;
+  *nvals = F.ivals();
+  return 0;
+}
+
+int rmh_family_inverse_get(int f, int *bptr, int *pos_slot, int *boff, double *ival) {
+  if (!g || f < 0 || f >= (int)g->fams.size()) return 1;
+  const PatchFamily &F = g->fams[f];
+  std::memcpy(bptr, F.bptr.data(), F.bptr.size() * sizeof(int));
+  std::memcpy(pos_slot, F.pos_slot.data(), F.pos_slot.size() * sizeof(int));
+  std::memcpy(boff, F.boff.data(), F.boff.size() * sizeof(int));
+  std::memcpy(ival, F.ival.data(), F.ival.size() * sizeof(double));
+  return 0;
+}
+
 int rmh_coarse_size() { return g ? g->coarse.nc : 0; }
 
 int rmh_coarse_inverse(double *A0inv) {

@@ -771,6 +771,113 @@ PatchFamily build_patches(const Layout &L, const FreeMap &fm, const Csr &M, int 
 #pragma omp critical
     for (size_t x = 0; x < mine.size(); ++x) uni[x] |= mine[x];
   }
+  // Exact factorisation: the patch matrix splits into decoupled blocks (the
+  // connected components of the union pattern; p blocks for H(curl) edge
+  // stars, fig. spy_feec(e)).  Store the dense inverse of each block, so the
+  // device applies L^-T L^-1 as one parallel product with no level chain.
+  if (factor == 0) {
+    std::vector<int> comp(ns, -1);
+    std::vector<std::vector<int>> adj(ns);
+    for (int i = 0; i < ns; ++i)
+      for (int j = 0; j < i; ++j)
+        if (uni[(size_t)i * ns + j]) {
+          adj[i].push_back(j);
+          adj[j].push_back(i);
+        }
+    int nblk = 0;
+    std::vector<std::vector<int>> blocks;
+    for (int s0 = 0; s0 < ns; ++s0) {
+      if (comp[s0] >= 0) continue;
+      std::vector<int> stack{s0}, members;
+      comp[s0] = nblk;
+      while (!stack.empty()) {
+        int u = stack.back();
+        stack.pop_back();
+        members.push_back(u);
+        for (int v : adj[u])
+          if (comp[v] < 0) {
+            comp[v] = nblk;
+            stack.push_back(v);
+          }
+      }
+      std::sort(members.begin(), members.end());
+      blocks.push_back(members);
+      ++nblk;
+    }
+    F.inverse = 1;
+    F.bptr.assign(1, 0);
+    F.boff.assign(1, 0);
+    for (int b = 0; b < nblk; ++b) {
+      for (int s : blocks[b]) {
+        F.pos_slot.push_back(s);
+        F.pos_blk.push_back(b);
+      }
+      const int nb = (int)blocks[b].size();
+      F.bptr.push_back(F.bptr.back() + nb);
+      F.boff.push_back(F.boff.back() + nb * nb);
+    }
+    const int nv = F.boff.back();
+    F.ival.assign((size_t)np * nv, 0.0);
+    int bad = -1;
+#pragma omp parallel
+    {
+      std::vector<int> pos(nf, -1);
+      std::vector<double> A, Bk;
+#pragma omp for schedule(dynamic, 4)
+      for (int pi = 0; pi < np; ++pi) {
+        extract(pi, pos, A);
+        double *out = &F.ival[(size_t)pi * nv];
+        for (int b = 0; b < nblk; ++b) {
+          const std::vector<int> &m = blocks[b];
+          const int nb = (int)m.size();
+          Bk.assign((size_t)nb * nb, 0.0);
+          for (int x = 0; x < nb; ++x)
+            for (int y = 0; y < nb; ++y)
+              if (own(A, m[x], m[y])) Bk[(size_t)x * nb + y] = A[(size_t)m[x] * ns + m[y]];
+          // Cholesky, then the inverse L^-T L^-1
+          bool ok = true;
+          for (int j = 0; j < nb && ok; ++j) {
+            double d = Bk[(size_t)j * nb + j];
+            for (int kk = 0; kk < j; ++kk) d -= Bk[(size_t)j * nb + kk] * Bk[(size_t)j * nb + kk];
+            if (!(d > 0.0)) { ok = false; break; }
+            d = std::sqrt(d);
+            Bk[(size_t)j * nb + j] = d;
+            for (int i = j + 1; i < nb; ++i) {
+              double s = Bk[(size_t)i * nb + j];
+              for (int kk = 0; kk < j; ++kk) s -= Bk[(size_t)i * nb + kk] * Bk[(size_t)j * nb + kk];
+              Bk[(size_t)i * nb + j] = s / d;
+            }
+          }
+          if (!ok) {
+#pragma omp critical
+            bad = pi;
+            continue;
+          }
+          std::vector<double> Linv((size_t)nb * nb, 0.0);  // lower, L^-1
+          for (int c = 0; c < nb; ++c) {
+            Linv[(size_t)c * nb + c] = 1.0 / Bk[(size_t)c * nb + c];
+            for (int i = c + 1; i < nb; ++i) {
+              double s = 0.0;
+              for (int kk = c; kk < i; ++kk) s -= Bk[(size_t)i * nb + kk] * Linv[(size_t)kk * nb + c];
+              Linv[(size_t)i * nb + c] = s / Bk[(size_t)i * nb + i];
+            }
+          }
+          double *ob = out + F.boff[b];
+          for (int x = 0; x < nb; ++x)
+            for (int y = 0; y <= x; ++y) {
+              double s = 0.0;
+              for (int kk = x; kk < nb; ++kk) s += Linv[(size_t)kk * nb + x] * Linv[(size_t)kk * nb + y];
+              ob[(size_t)y * nb + x] = s;
+              ob[(size_t)x * nb + y] = s;
+            }
+        }
+      }
+    }
+    if (bad >= 0)
+      throw std::runtime_error("patch factorisation breakdown (non-positive pivot) in patch " +
+                               std::to_string(bad));
+    return F;
+  }
   // symbolic fill for exact Cholesky
   if (factor == 0) {
     for (int j = 0; j < ns; ++j) {

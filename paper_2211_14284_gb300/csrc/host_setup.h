@@ -88,6 +88,16 @@ struct PatchFamily {
   std::vector<int> blev, brows;       // backward level schedule
   std::vector<double> val;            // npatch x nnz
   int nnz() const { return rowptr.empty() ? 0 : rowptr.back(); }
+  // Block-inverse form (exact factorisation only): the template pattern
+  // splits into decoupled blocks; each patch stores the dense inverse of
+  // every block (column-major, nb x nb), applied as one parallel product.
+  int inverse = 0;
+  std::vector<int> bptr;              // block b = positions bptr[b]..bptr[b+1]
+  std::vector<int> pos_slot;          // slot at position t (blocks contiguous)
+  std::vector<int> pos_blk;           // block of position t
+  std::vector<int> boff;              // value offset of block b within a patch
+  std::vector<double> ival;           // npatch x boff.back()
+  int ivals() const { return boff.empty() ? 0 : boff.back(); }
 };
 // span: bit d set = the entity spans direction d (0: vertex, 1 bit: edge, ...)
 // interface_only: slots restricted to interface DOFs (static condensation).

@@ -33,43 +33,63 @@ __constant__ DTerm c_terms[3][3][3] = {
     {{{2, 1, 1}, {1, 2, -1}}, {{0, 2, 1}, {2, 0, -1}}, {{1, 0, 1}, {0, 1, -1}}},
     {{{0, 0, 1}, {1, 1, 1}, {2, 2, 1}}, {}, {}}};
 
-// out[b][o] = sc * sum_i M[o][i] in[b][i]   (contract the fastest index)
+// Store modes of the 1D contractions: out = s, out += s, out -= s, out = -s
+// (the D-hat terms carry signs +-1; no multiply is spent on them).
+enum { SET = 0, ADD = 1, SUB = 2, NEG = 3 };
+template <int MODE>
+__device__ __forceinline__ void put(double &o, double s) {
+  if (MODE == SET) o = s;
+  else if (MODE == ADD) o += s;
+  else if (MODE == SUB) o -= s;
+  else o = -s;
+}
+
+// out[b][o] (op)= sum_i M[o][i] in[b][i]   (contract the fastest index)
+template <int MODE>
 __device__ __forceinline__ void pass1(const double *__restrict__ in, double *__restrict__ out,
-                                      const double *__restrict__ M, int O, int I, int NB,
-                                      double sc, bool acc) {
+                                      const double *__restrict__ M, int O, int I, int NB) {
   for (int idx = threadIdx.x; idx < O * NB; idx += blockDim.x) {
     const int o = idx % O, b = idx / O;
     const double *mi = M + o * I;
     const double *xi = in + b * I;
     double s = 0.0;
     for (int i = 0; i < I; ++i) s = fma(mi[i], xi[i], s);
-    out[idx] = acc ? fma(sc, s, out[idx]) : sc * s;
+    put<MODE>(out[idx], s);
   }
 }
-// out[c][o][a] = sc * sum_i M[o][i] in[c][i][a]
+// out[c][o][a] (op)= sum_i M[o][i] in[c][i][a]
+template <int MODE>
 __device__ __forceinline__ void pass2(const double *__restrict__ in, double *__restrict__ out,
-                                      const double *__restrict__ M, int O, int I, int A, int C,
-                                      double sc, bool acc) {
+                                      const double *__restrict__ M, int O, int I, int A, int C) {
   for (int idx = threadIdx.x; idx < C * O * A; idx += blockDim.x) {
     const int a = idx % A, o = (idx / A) % O, c = idx / (A * O);
     const double *mi = M + o * I;
     const double *xi = in + c * I * A + a;
     double s = 0.0;
     for (int i = 0; i < I; ++i) s = fma(mi[i], xi[i * A], s);
-    out[idx] = acc ? fma(sc, s, out[idx]) : sc * s;
+    put<MODE>(out[idx], s);
   }
 }
-// out[o][ba] = sc * sum_i M[o][i] in[i][ba]
+// out[o][ba] (op)= sum_i M[o][i] in[i][ba]
+template <int MODE>
 __device__ __forceinline__ void pass3(const double *__restrict__ in, double *__restrict__ out,
-                                      const double *__restrict__ M, int O, int I, int BA,
-                                      double sc, bool acc) {
+                                      const double *__restrict__ M, int O, int I, int BA) {
   for (int idx = threadIdx.x; idx < O * BA; idx += blockDim.x) {
     const int ba = idx % BA, o = idx / BA;
     const double *mi = M + o * I;
     double s = 0.0;
     for (int i = 0; i < I; ++i) s = fma(mi[i], in[i * BA + ba], s);
-    out[idx] = acc ? fma(sc, s, out[idx]) : sc * s;
+    put<MODE>(out[idx], s);
   }
+}
+
+// One signed D-hat (or D-hat^T) term along direction dir.
+template <int MODE>
+__device__ __forceinline__ void dpass(int dir, const double *in, double *out, const double *M,
+                                      int O, int I, const int *ls) {
+  if (dir == 0) pass1<MODE>(in, out, M, O, I, ls[1] * ls[2]);
+  else if (dir == 1) pass2<MODE>(in, out, M, O, I, ls[0], ls[2]);
+  else pass3<MODE>(in, out, M, O, I, ls[0] * ls[1]);
 }
 
 __device__ __forceinline__ void jac(const double *X8, double x0, double x1, double x2, double J[9]) {
@@ -95,51 +115,83 @@ __device__ __forceinline__ void jac(const double *X8, double x0, double x1, doub
   }
 }
 
-// Multiply the reference values at every point by the pullback weight of
-// kk-forms times coef (Sec. 3.1).
-__device__ void pointwise(int kk, double coef, double *U, int q, const double *xq,
-                          const double *wq, const double *X8) {
-  const int q3 = q * q * q;
+// Pullback weight of kk-forms (Sec. 3.1) times cw = coefficient x quadrature
+// weight: kk = 0: det J; kk = 3: 1/det J; kk = 1: det J J^-1 J^-T =
+// adj(J) adj(J)^T / det J; kk = 2: J^T J / det J.  Symmetric entries are
+// returned as (00, 11, 22, 01, 02, 12).
+__device__ __forceinline__ int point_weight(int kk, double cw, const double J[9], double W[6]) {
+  const double det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
+                     J[2] * (J[3] * J[7] - J[4] * J[6]);
+  if (kk == 0) { W[0] = cw * det; return 1; }
+  const double s = cw / det;
+  if (kk == 3) { W[0] = s; return 1; }
+  double A[9];
+  if (kk == 1) {  // rows of the adjugate
+    A[0] = J[4] * J[8] - J[5] * J[7];
+    A[1] = J[2] * J[7] - J[1] * J[8];
+    A[2] = J[1] * J[5] - J[2] * J[4];
+    A[3] = J[5] * J[6] - J[3] * J[8];
+    A[4] = J[0] * J[8] - J[2] * J[6];
+    A[5] = J[2] * J[3] - J[0] * J[5];
+    A[6] = J[3] * J[7] - J[4] * J[6];
+    A[7] = J[1] * J[6] - J[0] * J[7];
+    A[8] = J[0] * J[4] - J[1] * J[3];
+  } else {        // columns of J as rows
+    A[0] = J[0]; A[1] = J[3]; A[2] = J[6];
+    A[3] = J[1]; A[4] = J[4]; A[5] = J[7];
+    A[6] = J[2]; A[7] = J[5]; A[8] = J[8];
+  }
+  const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+  for (int e = 0; e < 6; ++e)
+    W[e] = s * (A[3 * ia[e]] * A[3 * ib[e]] + A[3 * ia[e] + 1] * A[3 * ib[e] + 1] +
+                A[3 * ia[e] + 2] * A[3 * ib[e] + 2]);
+  return 6;
+}
+
+// Setup: the weights of both stages at every quadrature point of every cell,
+// G[cell][entry][point], entries = stage A (V^k, beta) then stage B
+// (V^{k+1}, alpha).
+__global__ void metric_kernel(ApplyDev P, double *__restrict__ G) {
+  const int p = P.p, q = P.q, q3 = q * q * q;
+  const int c = blockIdx.x;
+  const int e[3] = {c % P.n[0], (c / P.n[0]) % P.n[1], c / (P.n[0] * P.n[1])};
+  __shared__ double X8[24];
+  if (threadIdx.x < 24) {
+    const int corner = threadIdx.x / 3, comp = threadIdx.x % 3;
+    const int c1 = corner & 1, c2 = (corner >> 1) & 1, c3 = corner >> 2;
+    const long long v = (e[0] + c1) + (long long)(P.n[0] + 1) * ((e[1] + c2) + (long long)(P.n[1] + 1) * (e[2] + c3));
+    X8[threadIdx.x] = P.X[3 * v + comp];
+  }
+  __syncthreads();
+  const double *xq = P.tabs + q * (p + 1) + q * p + p * (p + 1);
+  const double *wq = xq + q;
+  double *Gc = G + (size_t)c * P.nAB * q3;
   for (int pt = threadIdx.x; pt < q3; pt += blockDim.x) {
     const int a1 = pt % q, a2 = (pt / q) % q, a3 = pt / (q * q);
-    double J[9];
+    double J[9], W[6];
     jac(X8, xq[a1], xq[a2], xq[a3], J);
-    const double w = coef * wq[a1] * wq[a2] * wq[a3];
-    const double det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
-                       J[2] * (J[3] * J[7] - J[4] * J[6]);
-    if (kk == 0) {
-      U[pt] *= w * det;
-    } else if (kk == 3) {
-      U[pt] *= w / det;
+    const double w = wq[a1] * wq[a2] * wq[a3];
+    const int na = point_weight(P.k, P.beta[c] * w, J, W);
+    for (int j = 0; j < na; ++j) Gc[(size_t)j * q3 + pt] = W[j];
+    const int nb = point_weight(P.k + 1, P.alpha[c] * w, J, W);
+    for (int j = 0; j < nb; ++j) Gc[(size_t)(na + j) * q3 + pt] = W[j];
+  }
+}
+
+// Multiply the reference values at every point by the stored weight:
+// scalar (n = 1) or symmetric 3x3 (n = 6).
+__device__ __forceinline__ void apply_weight(const double *__restrict__ Gc, int n, double *U, int q3) {
+  for (int pt = threadIdx.x; pt < q3; pt += blockDim.x) {
+    if (n == 1) {
+      U[pt] *= Gc[pt];
     } else {
-      double M[9];
-      if (kk == 1) {
-        double A[9];
-        A[0] = J[4] * J[8] - J[5] * J[7];
-        A[1] = J[2] * J[7] - J[1] * J[8];
-        A[2] = J[1] * J[5] - J[2] * J[4];
-        A[3] = J[5] * J[6] - J[3] * J[8];
-        A[4] = J[0] * J[8] - J[2] * J[6];
-        A[5] = J[2] * J[3] - J[0] * J[5];
-        A[6] = J[3] * J[7] - J[4] * J[6];
-        A[7] = J[1] * J[6] - J[0] * J[7];
-        A[8] = J[0] * J[4] - J[1] * J[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-          for (int b = 0; b < 3; ++b)
-            M[3 * a + b] = (A[3 * a] * A[3 * b] + A[3 * a + 1] * A[3 * b + 1] + A[3 * a + 2] * A[3 * b + 2]) / det;
-      } else {
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-          for (int b = 0; b < 3; ++b)
-            M[3 * a + b] = (J[a] * J[b] + J[3 + a] * J[3 + b] + J[6 + a] * J[6 + b]) / det;
-      }
+      const double w00 = Gc[pt], w11 = Gc[q3 + pt], w22 = Gc[2 * q3 + pt];
+      const double w01 = Gc[3 * q3 + pt], w02 = Gc[4 * q3 + pt], w12 = Gc[5 * q3 + pt];
       const double u0 = U[pt], u1 = U[q3 + pt], u2 = U[2 * q3 + pt];
-      U[pt] = w * (M[0] * u0 + M[1] * u1 + M[2] * u2);
-      U[q3 + pt] = w * (M[3] * u0 + M[4] * u1 + M[5] * u2);
-      U[2 * q3 + pt] = w * (M[6] * u0 + M[7] * u1 + M[8] * u2);
+      U[pt] = fma(w00, u0, fma(w01, u1, w02 * u2));
+      U[q3 + pt] = fma(w01, u0, fma(w11, u1, w12 * u2));
+      U[2 * q3 + pt] = fma(w02, u0, fma(w12, u1, w22 * u2));
     }
   }
 }
@@ -212,29 +264,28 @@ __global__ void __launch_bounds__(kApplyThreads) apply_kernel(ApplyDev P, const 
     xl[l] = dir ? 0.0 : x[P.off[m] + g1 + (long long)P.N[m][0] * (g2 + (long long)P.N[m][1] * g3)];
     yl[l] = 0.0;
   }
-  const double al = P.alpha[c], be = P.beta[c];
   __syncthreads();
   // ---- stage A: (v, beta u) on V^k ----
   for (int m = 0; m < P.nc0; ++m) {
     const double *T[3];
     for (int d = 0; d < 3; ++d) T[d] = P.t0[m][d] == 's' ? Ts : Tr;
-    pass1(xl + P.loff0[m], SA, T[0], q, P.ld0[m][0], P.ld0[m][1] * P.ld0[m][2], 1.0, false);
+    pass1<SET>(xl + P.loff0[m], SA, T[0], q, P.ld0[m][0], P.ld0[m][1] * P.ld0[m][2]);
     __syncthreads();
-    pass2(SA, SB, T[1], q, P.ld0[m][1], q, P.ld0[m][2], 1.0, false);
+    pass2<SET>(SA, SB, T[1], q, P.ld0[m][1], q, P.ld0[m][2]);
     __syncthreads();
-    pass3(SB, U + m * q3, T[2], q, P.ld0[m][2], q * q, 1.0, false);
+    pass3<SET>(SB, U + m * q3, T[2], q, P.ld0[m][2], q * q);
     __syncthreads();
   }
-  pointwise(P.k, be, U, q, xq, wq, X8);
+  apply_weight(P.G + (size_t)c * P.nAB * q3, P.nA, U, q3);
   __syncthreads();
   for (int m = 0; m < P.nc0; ++m) {
     const double *T[3];
     for (int d = 0; d < 3; ++d) T[d] = P.t0[m][d] == 's' ? TsT : TrT;
-    pass3(U + m * q3, SB, T[2], P.ld0[m][2], q, q * q, 1.0, false);
+    pass3<SET>(U + m * q3, SB, T[2], P.ld0[m][2], q, q * q);
     __syncthreads();
-    pass2(SB, SA, T[1], P.ld0[m][1], q, q, P.ld0[m][2], 1.0, false);
+    pass2<SET>(SB, SA, T[1], P.ld0[m][1], q, q, P.ld0[m][2]);
     __syncthreads();
-    pass1(SA, yl + P.loff0[m], T[0], P.ld0[m][0], q, P.ld0[m][1] * P.ld0[m][2], 1.0, true);
+    pass1<ADD>(SA, yl + P.loff0[m], T[0], P.ld0[m][0], q, P.ld0[m][1] * P.ld0[m][2]);
     __syncthreads();
   }
   // ---- stage B: (d v, alpha d u) on V^{k+1}, d = D-hat ----
@@ -245,32 +296,33 @@ __global__ void __launch_bounds__(kApplyThreads) apply_kernel(ApplyDev P, const 
       const double *in = xl + P.loff0[T.src];
       double *out = dl + P.loff1[t];
       const int *ls = P.ld0[T.src];
-      if (T.dir == 0) pass1(in, out, D1, p, p + 1, ls[1] * ls[2], (double)T.sgn, s > 0);
-      else if (T.dir == 1) pass2(in, out, D1, p, p + 1, ls[0], ls[2], (double)T.sgn, s > 0);
-      else pass3(in, out, D1, p, p + 1, ls[0] * ls[1], (double)T.sgn, s > 0);
+      if (s == 0 && T.sgn > 0) dpass<SET>(T.dir, in, out, D1, p, p + 1, ls);
+      else if (s == 0) dpass<NEG>(T.dir, in, out, D1, p, p + 1, ls);
+      else if (T.sgn > 0) dpass<ADD>(T.dir, in, out, D1, p, p + 1, ls);
+      else dpass<SUB>(T.dir, in, out, D1, p, p + 1, ls);
       __syncthreads();
     }
   }
   for (int t = 0; t < P.nc1; ++t) {
     const double *T[3];
     for (int d = 0; d < 3; ++d) T[d] = P.t1[t][d] == 's' ? Ts : Tr;
-    pass1(dl + P.loff1[t], SA, T[0], q, P.ld1[t][0], P.ld1[t][1] * P.ld1[t][2], 1.0, false);
+    pass1<SET>(dl + P.loff1[t], SA, T[0], q, P.ld1[t][0], P.ld1[t][1] * P.ld1[t][2]);
     __syncthreads();
-    pass2(SA, SB, T[1], q, P.ld1[t][1], q, P.ld1[t][2], 1.0, false);
+    pass2<SET>(SA, SB, T[1], q, P.ld1[t][1], q, P.ld1[t][2]);
     __syncthreads();
-    pass3(SB, U + t * q3, T[2], q, P.ld1[t][2], q * q, 1.0, false);
+    pass3<SET>(SB, U + t * q3, T[2], q, P.ld1[t][2], q * q);
     __syncthreads();
   }
-  pointwise(k + 1, al, U, q, xq, wq, X8);
+  apply_weight(P.G + ((size_t)c * P.nAB + P.nA) * q3, P.nAB - P.nA, U, q3);
   __syncthreads();
   for (int t = 0; t < P.nc1; ++t) {
     const double *T[3];
     for (int d = 0; d < 3; ++d) T[d] = P.t1[t][d] == 's' ? TsT : TrT;
-    pass3(U + t * q3, SB, T[2], P.ld1[t][2], q, q * q, 1.0, false);
+    pass3<SET>(U + t * q3, SB, T[2], P.ld1[t][2], q, q * q);
     __syncthreads();
-    pass2(SB, SA, T[1], P.ld1[t][1], q, q, P.ld1[t][2], 1.0, false);
+    pass2<SET>(SB, SA, T[1], P.ld1[t][1], q, q, P.ld1[t][2]);
     __syncthreads();
-    pass1(SA, dyl + P.loff1[t], T[0], P.ld1[t][0], q, P.ld1[t][1] * P.ld1[t][2], 1.0, false);
+    pass1<SET>(SA, dyl + P.loff1[t], T[0], P.ld1[t][0], q, P.ld1[t][1] * P.ld1[t][2]);
     __syncthreads();
   }
   for (int t = 0; t < P.nc1; ++t) {
@@ -279,9 +331,8 @@ __global__ void __launch_bounds__(kApplyThreads) apply_kernel(ApplyDev P, const 
       const double *in = dyl + P.loff1[t];
       double *out = yl + P.loff0[T.src];
       const int *lt = P.ld1[t];
-      if (T.dir == 0) pass1(in, out, D1T, p + 1, p, lt[1] * lt[2], (double)T.sgn, true);
-      else if (T.dir == 1) pass2(in, out, D1T, p + 1, p, lt[0], lt[2], (double)T.sgn, true);
-      else pass3(in, out, D1T, p + 1, p, lt[0] * lt[1], (double)T.sgn, true);
+      if (T.sgn > 0) dpass<ADD>(T.dir, in, out, D1T, p + 1, p, lt);
+      else dpass<SUB>(T.dir, in, out, D1T, p + 1, p, lt);
       __syncthreads();
     }
   }
@@ -326,16 +377,23 @@ __global__ void spmv_kernel(int nrows, const int *__restrict__ rid, const int *_
   }
 }
 
-template <typename VT>
+// Level-scheduled forward/backward substitution with the template factor.
+// STAGE: the patch's factor values are first copied to shared memory with
+// coalesced loads, so the dependency chain reads only shared memory.
+template <typename VT, bool STAGE>
 __global__ void patch_kernel(DevPatch F, const double *__restrict__ r, double *__restrict__ z) {
   extern __shared__ double xs[];
   const int ns = F.nslots;
   const int *sm = F.slotmap + (size_t)blockIdx.x * ns;
-  const VT *L = reinterpret_cast<const VT *>(F.val) + (size_t)blockIdx.x * F.nnz;
+  const VT *Lg = reinterpret_cast<const VT *>(F.val) + (size_t)blockIdx.x * F.nnz;
+  VT *Ls = reinterpret_cast<VT *>(xs + ns);
   for (int s = threadIdx.x; s < ns; s += blockDim.x) {
     const int g = sm[s];
     xs[s] = g >= 0 ? r[g] : 0.0;
   }
+  if (STAGE)
+    for (int e = threadIdx.x; e < F.nnz; e += blockDim.x) Ls[e] = Lg[e];
+  const VT *L = STAGE ? Ls : Lg;
   __syncthreads();
   for (int lv = 0; lv < F.nflev; ++lv) {
     for (int t = F.flev[lv] + threadIdx.x; t < F.flev[lv + 1]; t += blockDim.x) {
@@ -359,6 +417,37 @@ __global__ void patch_kernel(DevPatch F, const double *__restrict__ r, double *_
   for (int s = threadIdx.x; s < ns; s += blockDim.x) {
     const int g = sm[s];
     if (g >= 0) atomicAdd(&z[g], xs[s]);
+  }
+}
+
+// Block-inverse patches: y_block = (A_block)^{-1} x_block for every decoupled
+// block of the patch, one row per thread, the column-major inverse read with
+// coalesced loads; no level chain.
+template <typename VT>
+__global__ void patch_inv_kernel(DevPatch F, const double *__restrict__ r, double *__restrict__ z) {
+  extern __shared__ double xs[];
+  const int ns = F.nslots;
+  double *ys = xs + ns;
+  const int *sm = F.slotmap + (size_t)blockIdx.x * ns;
+  const VT *V = reinterpret_cast<const VT *>(F.val) + (size_t)blockIdx.x * F.ivals;
+  for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+    const int g = sm[s];
+    xs[s] = g >= 0 ? r[g] : 0.0;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < ns; t += blockDim.x) {
+    const int b = F.pos_blk[t];
+    const int p0 = F.bptr[b], nb = F.bptr[b + 1] - p0, i = t - p0;
+    const VT *Vb = V + F.boff[b] + i;
+    const int *ps = F.pos_slot + p0;
+    double acc = 0.0;
+    for (int j = 0; j < nb; ++j) acc = fma((double)Vb[(size_t)j * nb], xs[ps[j]], acc);
+    ys[t] = acc;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < ns; t += blockDim.x) {
+    const int g = sm[F.pos_slot[t]];
+    if (g >= 0) atomicAdd(&z[g], ys[t]);
   }
 }
 
@@ -482,6 +571,13 @@ inline int grid_for(long long n, int threads) {
 
 }  // namespace
 
+cudaError_t launch_metric(const ApplyDev &A, double *G, cudaStream_t s) {
+  const int ncell = A.n[0] * A.n[1] * A.n[2];
+  metric_kernel<<<ncell, 256, 0, s>>>(A, G);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_apply(const ApplyDev &A, const double *x, double *y, cudaStream_t s) {
   const int ncell = A.n[0] * A.n[1] * A.n[2];
   const size_t smem = A.smem_doubles * sizeof(double);
@@ -518,16 +614,29 @@ cudaError_t launch_spmv(const DevCsr &M, const double *x, double *y, const doubl
   return cudaGetLastError();
 }
 
+template <typename VT>
+static void patch_dispatch(const DevPatch &F, const double *r, double *z, cudaStream_t s) {
+  if (F.inverse) {
+    const size_t smem = 2 * (size_t)F.nslots * sizeof(double);
+    cudaFuncSetAttribute(patch_inv_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    patch_inv_kernel<VT><<<F.npatch, 256, smem, s>>>(F, r, z);
+    return;
+  }
+  const size_t base = (size_t)F.nslots * sizeof(double);
+  const size_t staged = base + (size_t)F.nnz * sizeof(VT);
+  if (staged <= 96 * 1024) {
+    cudaFuncSetAttribute(patch_kernel<VT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)staged);
+    patch_kernel<VT, true><<<F.npatch, 128, staged, s>>>(F, r, z);
+  } else {
+    cudaFuncSetAttribute(patch_kernel<VT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)base);
+    patch_kernel<VT, false><<<F.npatch, 128, base, s>>>(F, r, z);
+  }
+}
+
 cudaError_t launch_patches(const DevPatch &F, const double *r, double *z, cudaStream_t s) {
   if (F.npatch == 0) return cudaSuccess;
-  const size_t smem = (size_t)F.nslots * sizeof(double);
-  if (F.vt == 0) {
-    cudaFuncSetAttribute(patch_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    patch_kernel<double><<<F.npatch, 128, smem, s>>>(F, r, z);
-  } else {
-    cudaFuncSetAttribute(patch_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    patch_kernel<float><<<F.npatch, 128, smem, s>>>(F, r, z);
-  }
+  if (F.vt == 0) patch_dispatch<double>(F, r, z, s);
+  else patch_dispatch<float>(F, r, z, s);
   g_launches += 1;
   return cudaGetLastError();
 }

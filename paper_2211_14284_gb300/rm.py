@@ -250,10 +250,36 @@ class HostProbe:
             val = np.zeros(npch.value * nnz.value)
             v = lambda a: a.ctypes.data_as(ctypes.c_void_p)
             self.lib.rmh_family_get(f, v(sm), v(rp), v(col), v(val))
-            out.append(dict(nslots=ns.value, npatch=npch.value, nnz=nnz.value,
-                            slotmap=sm.reshape(npch.value, ns.value), rowptr=rp, col=col,
-                            val=val.reshape(npch.value, nnz.value)))
+            fam = dict(nslots=ns.value, npatch=npch.value, nnz=nnz.value,
+                       slotmap=sm.reshape(npch.value, ns.value), rowptr=rp, col=col,
+                       val=val.reshape(npch.value, nnz.value), inverse=None)
+            isinv, nb, nv = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+            self.lib.rmh_family_inverse_size(f, ctypes.byref(isinv), ctypes.byref(nb),
+                                             ctypes.byref(nv))
+            if isinv.value:
+                bptr = np.zeros(nb.value + 1, np.int32)
+                pslot = np.zeros(ns.value, np.int32)
+                boff = np.zeros(nb.value + 1, np.int32)
+                ival = np.zeros(npch.value * nv.value)
+                self.lib.rmh_family_inverse_get(f, v(bptr), v(pslot), v(boff), v(ival))
+                fam["inverse"] = dict(bptr=bptr, pos_slot=pslot, boff=boff,
+                                      ival=ival.reshape(npch.value, nv.value))
+            out.append(fam)
         return out
+
+    @staticmethod
+    def patch_inverse(fam, pi):
+        """Dense (slots x slots) inverse of patch pi of a block-inverse family."""
+        import numpy as np
+        ns = fam["nslots"]
+        inv = fam["inverse"]
+        M = np.zeros((ns, ns))
+        for b in range(len(inv["bptr"]) - 1):
+            sl = inv["pos_slot"][inv["bptr"][b]:inv["bptr"][b + 1]]
+            nb = len(sl)
+            blk = inv["ival"][pi, inv["boff"][b]:inv["boff"][b] + nb * nb].reshape(nb, nb).T
+            M[np.ix_(sl, sl)] = blk
+        return M
 
     def coarse_inverse(self):
         import numpy as np

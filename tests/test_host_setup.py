@@ -72,6 +72,26 @@ def _compare_family(fam, pats_lat, Mfree_fn, factor, free):
     assert fam["npatch"] == len(pats_lat)
     rp, col = fam["rowptr"], fam["col"]
     ns = fam["nslots"]
+    if fam["inverse"] is not None:
+        # exact factorisation stored as block inverses: compare with the
+        # inverse of the oracle's (pattern) patch matrix
+        assert factor == "chol"
+        for pi, want in enumerate(pats_lat):
+            sm = fam["slotmap"][pi]
+            valid = np.flatnonzero(sm >= 0)
+            assert np.array_equal(sm[valid], want)
+            Minv = HostProbe.patch_inverse(fam, pi)
+            Lo = cholesky(Mfree_fn(want))
+            Ao = Lo @ Lo.T
+            Ao_inv = np.linalg.inv(Ao)
+            # setup round-off (~1e-13 relative) amplified by cond(A_v)
+            tol = max(1e-10, 1e-12 * np.linalg.cond(Ao))
+            assert np.abs(Minv[np.ix_(valid, valid)] - Ao_inv).max() < tol * np.abs(Ao_inv).max()
+            inval = np.flatnonzero(sm < 0)
+            if len(inval):
+                assert np.allclose(Minv[np.ix_(inval, inval)], np.eye(len(inval)))
+                assert np.abs(Minv[np.ix_(valid, inval)]).max(initial=0.0) == 0.0
+        return
     for pi, want in enumerate(pats_lat):
         sm = fam["slotmap"][pi]
         valid = np.flatnonzero(sm >= 0)
