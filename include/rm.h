@@ -64,7 +64,11 @@ typedef enum { RM_HGRAD = 0, RM_HCURL = 1, RM_HDIV = 2 } rm_space;
 typedef enum { RM_FP64 = 0, RM_FP32 = 1 } rm_precision;
 typedef enum { RM_PAFW = 0, RM_PH = 1 } rm_decomposition;
 typedef enum { RM_CHOL = 0, RM_ICC = 1 } rm_factor;
-typedef enum { RM_COARSE_NONE = 0, RM_COARSE_P1 = 1 } rm_coarse;
+/* RM_COARSE_P1: exact p = 1 coarse solve (dense inverse, <= 8,192 coarse DOFs);
+ * RM_COARSE_GMG: the p = 1 problem approximated by one symmetric V(2,2)
+ * geometric multigrid cycle (Galerkin levels, damped Jacobi), as the paper's
+ * p-coarse GMG; for coarse spaces too large for the dense inverse. */
+typedef enum { RM_COARSE_NONE = 0, RM_COARSE_P1 = 1, RM_COARSE_GMG = 2 } rm_coarse;
 
 typedef struct {
   int nx, ny, nz;          /* cells per direction, each >= 2 */

@@ -202,20 +202,98 @@ def prolongation(lat_f: Lattice, lat_c: Lattice) -> sp.csr_matrix:
     return sp.coo_matrix((v, (r, c)), shape=(lat_f.size, lat_c.size)).tocsr()
 
 
-class Coarse:
-    """R_0^T A_0^{-1} R_0 with A_0 the p=1 rediscretisation (Eq. asm-afw)."""
+def refinement(lat_f: Lattice, lat_c: Lattice) -> sp.csr_matrix:
+    """Lowest-order (p=1) refinement from the mesh n/2 (lat_c) to n (lat_f),
+    on the full lattices: along an s-type direction the coarse hat is 1 at
+    its own vertex and 1/2 at the two fine vertices beside it; along an
+    r-type direction a coarse cell's constant is carried by its two fine
+    halves with weight 1/2 each (the reference-value scaling of the 1- and
+    2-form pullbacks when the cell length halves)."""
+    rows, cols, vals = [], [], []
+    comp, g1, g2, g3 = lat_f.coords()
+    G = np.stack([g1, g2, g3], 1)
+    for idx in range(lat_f.size):
+        m = comp[idx]
+        opts = []
+        for d in range(3):
+            g = G[idx, d]
+            if lat_f.types[m][d] == "s":
+                opts.append([(g // 2, 1.0)] if g % 2 == 0 else [((g - 1) // 2, 0.5), ((g + 1) // 2, 0.5)])
+            else:
+                opts.append([(g // 2, 0.5)])
+        for (a, wa) in opts[0]:
+            for (b, wb) in opts[1]:
+                for (c, wc) in opts[2]:
+                    rows.append(idx)
+                    cols.append(lat_c.index(m, a, b, c))
+                    vals.append(wa * wb * wc)
+    return sp.coo_matrix((vals, (rows, cols)), shape=(lat_f.size, lat_c.size)).tocsr()
 
-    def __init__(self, problem: Problem):
+
+class Coarse:
+    """R_0^T A_0^{-1} R_0 with A_0 the p=1 rediscretisation (Eq. asm-afw).
+
+    mode "exact": A_0^{-1} by a dense Cholesky solve.  mode "gmg": A_0^{-1}
+    replaced by one symmetric V(2,2) cycle of geometric multigrid (the
+    paper's p-coarse multigrid, Sec. 5.1): Galerkin levels P^T A P with the
+    lowest-order refinement while every n_d is even and >= 4 and the level
+    has more than 512 DOFs; damped point Jacobi with weight
+    1 / ||D^-1 A||_inf; a dense solve on the coarsest level.  Parity unpinned
+    against the paper (its smoother is Hiptmair-Jacobi; point Jacobi here)."""
+
+    def __init__(self, problem: Problem, mode: str = "exact"):
         X = problem.mesh.X
+        self.mode = mode
         self.cp = Problem(problem.k, problem.n, 1, X, problem.alpha, problem.beta)
         P0 = prolongation(problem.lat, self.cp.lat)
         self.R0T = P0[problem.free][:, self.cp.free].tocsr()
-        self.A0 = self.cp.A_free().toarray()
-        self.A0_chol = scipy.linalg.cho_factor(self.A0, lower=True)
+        A0 = self.cp.A_free().tocsr()
+        self.A0 = A0.toarray()
+        if mode == "exact":
+            self.A0_chol = scipy.linalg.cho_factor(self.A0, lower=True)
+            return
+        self.levels = []
+        A, lat, free, n = A0, self.cp.lat, self.cp.free, list(problem.n)
+        while all(v % 2 == 0 and v >= 4 for v in n) and A.shape[0] > 512:
+            nh = [v // 2 for v in n]
+            lat_h = Lattice(problem.k, tuple(nh), 1)
+            free_h = lat_h.free()
+            P = refinement(lat, lat_h)[free][:, free_h].tocsr()
+            D = A.diagonal()
+            omega = 1.0 / np.max(np.asarray(abs(A).sum(1)).ravel() / D)
+            star = None
+            if problem.k >= 1:
+                pos = free_position(free, lat.size)
+                star = PatchSolver(A, [pos[s] for s in patch_lists(lat, (), free)], "chol")
+            self.levels.append((A, P, omega / D, star))
+            A = (P.T @ A @ P).tocsr()
+            lat, free, n = lat_h, free_h, nh
+        self.A_last = A.toarray()
+
+    def _vcycle(self, l, b):
+        if l == len(self.levels):
+            return np.linalg.solve(self.A_last, b)
+        A, P, w, star = self.levels[l]
+        if star is not None:
+            # H(curl)/H(div): additive vertex-star smoother (Arnold-Falk-Winther),
+            # weight 1/8 (at most 8 stars overlap a DOF)
+            om = 0.125
+            x = om * star.apply(b)
+            x = x + om * star.apply(b - A @ x)
+            x = x + P @ self._vcycle(l + 1, P.T @ (b - A @ x))
+            x = x + om * star.apply(b - A @ x)
+            return x + om * star.apply(b - A @ x)
+        x = w * b
+        x = x + w * (b - A @ x)
+        x = x + P @ self._vcycle(l + 1, P.T @ (b - A @ x))
+        x = x + w * (b - A @ x)
+        return x + w * (b - A @ x)
 
     def apply(self, r):
         c = self.R0T.T @ r
-        return self.R0T @ scipy.linalg.cho_solve(self.A0_chol, c)
+        if self.mode == "exact":
+            return self.R0T @ scipy.linalg.cho_solve(self.A0_chol, c)
+        return self.R0T @ self._vcycle(0, c)
 
 
 # ---------------------------------------------------------------------------
@@ -297,7 +375,8 @@ class PAFW:
         pos = free_position(free, problem.lat.size)
         pats = patch_lists(problem.lat, (), free)
         self.patches = PatchSolver(M, [pos[s] for s in pats], factor)
-        self.coarse = Coarse(problem) if coarse else None
+        self.coarse = (Coarse(problem, coarse if isinstance(coarse, str) else "exact")
+                       if coarse else None)
 
     def smooth(self, r):
         return self.patches.apply(r)
@@ -320,7 +399,8 @@ class SCPAFW:
         pos = free_position(free[self.sc.G], problem.lat.size)
         pats = patch_lists(problem.lat, (), free[self.sc.G])
         self.patches = PatchSolver(self.sc.S, [pos[s] for s in pats], factor)
-        self.coarse = Coarse(problem) if coarse else None
+        self.coarse = (Coarse(problem, coarse if isinstance(coarse, str) else "exact")
+                       if coarse else None)
 
     def smooth(self, r):
         yI, rG = self.sc.condense(r)
@@ -385,7 +465,8 @@ class SCPH:
                                   vertex_factor)
         D = discrete_gradient(p0.lat, lat1)
         self.Dt = D[G1][:, G0].tocsr()
-        self.coarse = Coarse(problem) if coarse else None
+        self.coarse = (Coarse(problem, coarse if isinstance(coarse, str) else "exact")
+                       if coarse else None)
 
     def interface(self, rG):
         z = np.zeros_like(rG)

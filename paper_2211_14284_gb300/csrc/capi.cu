@@ -57,6 +57,15 @@ struct rm_handle {
   DevCsr Binv, E, Et, R0, R0T, Dt, DtT;
   void *A0inv = nullptr;
   int nc = 0;
+  // coarse multigrid (RM_COARSE_GMG): per level A, P (l+1 -> l), P^T, Jacobi
+  // weights and vectors B (right-hand side), X (iterate), T, R (work)
+  int mg_levels = 0, mg_ncoarsest = 0;
+  std::vector<DevCsr> mgA, mgP, mgPT;
+  std::vector<double *> mgW, mgB, mgX, mgT, mgR;
+  std::vector<int> mgN;
+  double *mgAinv = nullptr;
+  std::vector<DevPatch> mgStar;  // k = 1, 2: vertex-star smoother per level
+  double mgOmega = 0.125;
   std::vector<DevPatch> fam;   // families acting on the main space
   std::vector<DevPatch> pfam;  // potential-space families (Hiptmair)
   long long size0 = 0;         // potential (H(grad)) lattice size
@@ -214,6 +223,36 @@ void build_apply(rm_handle *h, const Geometry &geo, const std::vector<double> &a
   A.beta = h->upload(beta);
   A.tabs = h->upload(tabs);
   const size_t q3 = (size_t)q * q * q;
+  const int ncell = h->n[0] * h->n[1] * h->n[2];
+  // Cartesian fast path when every cell is an axis-aligned box
+  {
+    std::vector<double> hc(3 * (size_t)ncell);
+    bool cart = true;
+    for (int c = 0; c < ncell && cart; ++c) {
+      double X8[24];
+      geo.cell_vertices(c % h->n[0], (c / h->n[0]) % h->n[1], c / (h->n[0] * h->n[1]), X8);
+      double hh[3];
+      for (int d = 0; d < 3; ++d) hh[d] = X8[3 * (1 << d) + d] - X8[d];
+      const double tol = 1e-12 * std::max(hh[0], std::max(hh[1], hh[2]));
+      for (int d = 0; d < 3; ++d)
+        if (!(hh[d] > 0)) cart = false;
+      for (int corner = 0; corner < 8 && cart; ++corner)
+        for (int d = 0; d < 3; ++d)
+          if (std::fabs(X8[3 * corner + d] - (X8[d] + ((corner >> d) & 1) * hh[d])) > tol) cart = false;
+      for (int d = 0; d < 3; ++d) hc[3 * (size_t)c + d] = hh[d];
+    }
+    A.cartesian = cart ? 1 : 0;
+    if (cart) {
+      A.h = h->upload(hc);
+      A.bh_a = B.Bhat[0];
+      A.bh_b = B.Bhat[p];
+      const size_t smem = (size_t)p * (p + 1) + 2 * (size_t)A.nloc0 + 2 * (size_t)A.nloc1;
+      if (smem * sizeof(double) > 227 * 1024)
+        throw std::runtime_error("degree too high for the Cartesian apply kernel's shared memory");
+      A.G = nullptr;
+      return;
+    }
+  }
   A.smem_doubles = 2 * q * (p + 1) + 2 * q * p + 2 * p * (p + 1) + 2 * q + 24 + 2 * A.nloc0 + 2 * A.nloc1 +
                    3 * q3 + (size_t)q * (p + 1) * (p + 1) + (size_t)q * q * (p + 1);
   if (A.smem_doubles * sizeof(double) > 227 * 1024)
@@ -221,7 +260,6 @@ void build_apply(rm_handle *h, const Geometry &geo, const std::vector<double> &a
   // pullback weights at every quadrature point, computed once on the device
   A.nA = k == 0 ? 1 : 6;
   A.nAB = A.nA + (k == 2 ? 1 : 6);
-  const int ncell = h->n[0] * h->n[1] * h->n[2];
   double *G = h->dalloc<double>((size_t)ncell * A.nAB * q3);
   A.G = G;
   CK(launch_metric(A, G, h->stream));
@@ -232,6 +270,50 @@ int fail(rm_handle *h, int code, const std::string &msg) {
   if (h) h->err = msg;
   g_last_error = msg;
   return code;
+}
+
+// One symmetric V(2,2) cycle on level l: X[l] = V_l B[l] (damped Jacobi,
+// Galerkin coarse levels, dense solve on the coarsest).
+void vcycle(rm_handle *h, int l) {
+  cudaStream_t s = h->stream;
+  if (l == h->mg_levels) {
+    CK(launch_gemv(h->mg_ncoarsest, h->mgAinv, 0, h->mgB[l], h->mgX[l], s));
+    return;
+  }
+  const DevCsr &A = h->mgA[l];
+  const int nl = h->mgN[l];
+  double *b = h->mgB[l], *x = h->mgX[l], *t = h->mgT[l], *w = h->mgW[l], *r = h->mgR[l];
+  if (!h->mgStar.empty()) {
+    // additive vertex-star smoother: x += omega sum_v R_v^T A_v^-1 R_v (b - A x)
+    const DevPatch &F = h->mgStar[l];
+    auto sweep = [&](bool first) {
+      const double *rhs = b;
+      if (!first) {
+        CK(launch_spmv(A, x, r, b, 2, -1.0, s));
+        rhs = r;
+      }
+      CK(cudaMemsetAsync(t, 0, nl * sizeof(double), s));
+      CK(launch_patches(F, rhs, t, s));
+      CK(launch_axpy(nl, h->mgOmega, t, x, first ? 0 : 1, s));
+    };
+    sweep(true);
+    sweep(false);
+    CK(launch_spmv(A, x, r, b, 2, -1.0, s));
+    CK(launch_spmv(h->mgPT[l], r, h->mgB[l + 1], nullptr, 0, 1.0, s));
+    vcycle(h, l + 1);
+    CK(launch_spmv(h->mgP[l], h->mgX[l + 1], x, nullptr, 1, 1.0, s));
+    sweep(false);
+    sweep(false);
+    return;
+  }
+  CK(launch_diag_scale(nl, w, b, t, s));                        // sweep 1 from 0
+  CK(launch_jacobi(A, b, t, w, x, s));                          // sweep 2
+  CK(launch_spmv(A, x, r, b, 2, -1.0, s));                      // r = b - A x
+  CK(launch_spmv(h->mgPT[l], r, h->mgB[l + 1], nullptr, 0, 1.0, s));
+  vcycle(h, l + 1);
+  CK(launch_spmv(h->mgP[l], h->mgX[l + 1], x, nullptr, 1, 1.0, s));
+  CK(launch_jacobi(A, b, x, w, t, s));
+  CK(launch_jacobi(A, b, t, w, x, s));
 }
 
 // z = B r
@@ -254,7 +336,8 @@ void precondition(rm_handle *h, const double *r, double *z) {
   }
   if (h->nc > 0) {
     CK(launch_spmv(h->R0, r, h->cc, nullptr, 0, 1.0, s));
-    CK(launch_gemv(h->nc, h->A0inv, h->vt, h->cc, h->ce, s));
+    if (h->mg_levels > 0 || h->mgAinv) vcycle(h, 0);            // cc -> ce by V(2,2)
+    else CK(launch_gemv(h->nc, h->A0inv, 0, h->cc, h->ce, s));
     CK(launch_spmv(h->R0T, h->ce, z, nullptr, 1, 1.0, s));
   }
 }
@@ -390,11 +473,49 @@ int rm_setup(rm_handle **out, int space, const rm_mesh *mesh, int p, const doubl
       h->nc = cd.nc;
       std::vector<int> crow(cd.nc);
       for (int i = 0; i < cd.nc; ++i) crow[i] = i;
-      h->R0 = upload_csr(h.get(), cd.R0, nullptr, nullptr, &crow);
-      h->R0T = upload_csr(h.get(), cd.R0T, nullptr, nullptr);
-      h->A0inv = h->upload_vals(cd.A0inv);
+      h->R0 = upload_csr(h.get(), cd.R0, nullptr, nullptr, &crow, true);  // coarse in FP64
+      h->R0T = upload_csr(h.get(), cd.R0T, nullptr, nullptr, nullptr, true);
+      h->A0inv = h->upload(cd.A0inv);
       h->cc = h->dalloc<double>(h->nc);
       h->ce = h->dalloc<double>(h->nc);
+    } else if (o.coarse == RM_COARSE_GMG) {
+      CoarseGMG mg;
+      CoarseData cd = build_coarse_gmg(h->L, geo, al.data(), be.data(), mg);
+      h->nc = cd.nc;
+      std::vector<int> crow(cd.nc);
+      for (int i = 0; i < cd.nc; ++i) crow[i] = i;
+      h->R0 = upload_csr(h.get(), cd.R0, nullptr, nullptr, &crow, true);  // coarse in FP64
+      h->R0T = upload_csr(h.get(), cd.R0T, nullptr, nullptr, nullptr, true);
+      h->mg_levels = mg.levels;
+      h->mg_ncoarsest = mg.ncoarsest;
+      for (int l = 0; l <= mg.levels; ++l) {
+        const int nl = mg.A[l].nrows;
+        std::vector<int> rows(nl);
+        for (int i = 0; i < nl; ++i) rows[i] = i;
+        h->mgN.push_back(nl);
+        h->mgB.push_back(h->dalloc<double>(nl));
+        h->mgX.push_back(h->dalloc<double>(nl));
+        if (l == mg.levels) break;
+        h->mgA.push_back(upload_csr(h.get(), mg.A[l], nullptr, nullptr, &rows, true));
+        std::vector<int> prow(mg.P[l].nrows), trow(mg.PT[l].nrows);
+        for (size_t i = 0; i < prow.size(); ++i) prow[i] = (int)i;
+        for (size_t i = 0; i < trow.size(); ++i) trow[i] = (int)i;
+        h->mgP.push_back(upload_csr(h.get(), mg.P[l], nullptr, nullptr, &prow, true));
+        h->mgPT.push_back(upload_csr(h.get(), mg.PT[l], nullptr, nullptr, &trow, true));
+        h->mgW.push_back(h->upload(mg.dinv[l]));
+        if (!mg.star.empty()) {
+          const int saved = h->vt;
+          h->vt = 0;  // the coarse cycle stays in FP64
+          h->mgStar.push_back(upload_family(h.get(), mg.star[l]));
+          h->vt = saved;
+          h->mgOmega = mg.star_omega;
+        }
+        h->mgT.push_back(h->dalloc<double>(nl));
+        h->mgR.push_back(h->dalloc<double>(nl));
+      }
+      h->mgAinv = h->upload(mg.Ainv);
+      h->cc = h->mgB[0];
+      h->ce = h->mgX[0];
     }
     h->r = h->dalloc<double>(h->size);
     h->z = h->dalloc<double>(h->size);
@@ -606,6 +727,10 @@ extern "C" int rm_precondition_noalloc(rm_handle *h, const double *r, double *z)
     return fail(h, RM_ERR_ARG,
                 "rm_precondition_noalloc: statically condensed relaxations need "
                 "lattice-sized scratch; use rm_precondition");
+  if (h->mgAinv)
+    return fail(h, RM_ERR_ARG,
+                "rm_precondition_noalloc: the coarse multigrid cycle needs per-level vectors; "
+                "use rm_precondition");
   if (h->nc > RM_NOALLOC_MAX_COARSE)
     return fail(h, RM_ERR_ARG,
                 "rm_precondition_noalloc: coarse space has " + std::to_string(h->nc) +
@@ -621,7 +746,7 @@ extern "C" int rm_precondition_noalloc(rm_handle *h, const double *r, double *z)
     for (auto &F : h->fam) CK(launch_patches(F, r, z, s));
     if (h->nc > 0) {
       CK(launch_spmv(h->R0, r, cc, nullptr, 0, 1.0, s));
-      CK(launch_gemv(h->nc, h->A0inv, h->vt, cc, ce, s));
+      CK(launch_gemv(h->nc, h->A0inv, 0, cc, ce, s));
       CK(launch_spmv(h->R0T, ce, z, nullptr, 1, 1.0, s));
     }
   } catch (const std::exception &e) {

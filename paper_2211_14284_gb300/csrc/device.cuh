@@ -23,6 +23,11 @@ struct ApplyDev {
   const double *tabs;      // Ts q(p+1) | Tr qp | D1 p(p+1) | xq q | wq q
   const double *G;         // pullback weights per cell and point (metric_kernel)
   int nA, nAB;             // entries of stage A, of both stages (1 or 6 each)
+  // Cartesian fast path (every cell an axis-aligned box): cell sizes
+  // h[3 * cell + d] and the 1D factors of B-hat (a = B_00 = B_pp, b = B_0p)
+  int cartesian;
+  const double *h;
+  double bh_a, bh_b;
   size_t smem_doubles;
 };
 
@@ -61,6 +66,11 @@ cudaError_t launch_spmv(const DevCsr &M, const double *x, double *y, const doubl
                         double a, cudaStream_t s);
 cudaError_t launch_patches(const DevPatch &F, const double *r, double *z, cudaStream_t s);
 cudaError_t launch_gemv(int n, const void *A, int vt, const double *x, double *y, cudaStream_t s);
+// coarse multigrid: x_out = x_in + w (b - A x_in) (A FP64, rows compact); x = w b
+cudaError_t launch_jacobi(const DevCsr &A, const double *b, const double *xin, const double *w,
+                          double *xout, cudaStream_t s);
+cudaError_t launch_diag_scale(int n, const double *w, const double *b, double *x, cudaStream_t s);
+cudaError_t launch_axpy(int n, double a, const double *x, double *y, int acc, cudaStream_t s);
 cudaError_t launch_mask_copy(long long n, const uint8_t *mask, const double *b, double *r,
                              cudaStream_t s);
 cudaError_t launch_sub(long long n, const uint8_t *mask, const double *b, const double *q,

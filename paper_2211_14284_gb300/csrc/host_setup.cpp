@@ -349,9 +349,8 @@ Csr assemble_aux(const Layout &L, const Geometry &geo, const double *mcoef,
 #ifdef _OPENMP
     tid = omp_get_thread_num();
 #endif
-    std::vector<double> loc((size_t)nloc * nloc, 0.0);
-    std::vector<char> mark((size_t)nloc * nloc, 0);
-    std::vector<std::vector<int>> touched(nloc);
+    // local entries of P_K as (i * nloc + j, value), merged after the cell
+    std::vector<std::pair<long long, double>> ent;
     std::vector<double> Fk[3], Fk1[3], dk, dk1;
     std::vector<int> l2f(nloc);
     std::vector<double> acc(nloc, 0.0);
@@ -359,14 +358,8 @@ Csr assemble_aux(const Layout &L, const Geometry &geo, const double *mcoef,
     SparseVec row, drow;
     auto add_outer = [&](const SparseVec &v, double w) {
       for (size_t a = 0; a < v.idx.size(); ++a)
-        for (size_t b = 0; b < v.idx.size(); ++b) {
-          size_t pos = (size_t)v.idx[a] * nloc + v.idx[b];
-          if (!mark[pos]) {
-            mark[pos] = 1;
-            touched[v.idx[a]].push_back(v.idx[b]);
-          }
-          loc[pos] += w * v.val[a] * v.val[b];
-        }
+        for (size_t b = 0; b < v.idx.size(); ++b)
+          ent.push_back({(long long)v.idx[a] * nloc + v.idx[b], w * v.val[a] * v.val[b]});
     };
 #pragma omp for schedule(dynamic, 1)
     for (int c = 0; c < ncell; ++c) {
@@ -475,15 +468,18 @@ Csr assemble_aux(const Layout &L, const Geometry &geo, const double *mcoef,
               l2f[L.loff[m] + i1 + l1 * (i2 + l2 * i3)] = fm.lat2free[idx];
             }
       }
-      for (int i = 0; i < nloc; ++i) {
-        for (int j : touched[i]) {
-          size_t pos = (size_t)i * nloc + j;
-          if (l2f[i] >= 0 && l2f[j] >= 0) trips[tid].push_back({l2f[i], l2f[j], loc[pos]});
-          loc[pos] = 0.0;
-          mark[pos] = 0;
-        }
-        touched[i].clear();
+      std::sort(ent.begin(), ent.end(),
+                [](const std::pair<long long, double> &x, const std::pair<long long, double> &y) {
+                  return x.first < y.first;
+                });
+      for (size_t a = 0; a < ent.size();) {
+        const long long key = ent[a].first;
+        double v = 0.0;
+        for (; a < ent.size() && ent[a].first == key; ++a) v += ent[a].second;
+        const int i = (int)(key / nloc), j = (int)(key % nloc);
+        if (l2f[i] >= 0 && l2f[j] >= 0) trips[tid].push_back({l2f[i], l2f[j], v});
       }
+      ent.clear();
     }
   }
   std::vector<Trip> all;
@@ -699,6 +695,9 @@ PatchFamily build_patches(const Layout &L, const FreeMap &fm, const Csr &M, int 
     return a.o[0] < b.o[0];
   });
   const int ns = (int)slots.size();
+  if (ns > 6000)
+    throw std::runtime_error("patch template of " + std::to_string(ns) +
+                             " slots is too large (> 6000): use static condensation");
   PatchFamily F;
   F.nslots = ns;
   // entities
@@ -1050,17 +1049,13 @@ static void element_p1(int k, const double X8[24], double alpha, double beta,
       }
 }
 
-CoarseData build_coarse(const Layout &Lf, const Geometry &geo, const double *alpha,
-                        const double *beta) {
-  CoarseData C;
-  const int k = Lf.k, p = Lf.p;
-  Layout Lc(k, Lf.n, 1);
-  FreeMap fc(Lc);
-  const int nc = (int)fc.free2lat.size();
-  C.nc = nc;
-  if (nc > 8192) throw std::runtime_error("coarse space too large for the dense coarse solve");
-  std::vector<double> A0((size_t)nc * nc, 0.0);
+// Triplets of A_0 (a^k at p = 1, Sec. 4.3) over the coarse free DOFs.
+static std::vector<Trip> coarse_triplets(const Layout &Lf, const Layout &Lc, const FreeMap &fc,
+                                         const Geometry &geo, const double *alpha,
+                                         const double *beta) {
+  const int k = Lf.k;
   const int ncell = Lf.n[0] * Lf.n[1] * Lf.n[2];
+  std::vector<Trip> t;
   std::vector<double> AK;
   for (int c = 0; c < ncell; ++c) {
     int e[3] = {c % Lf.n[0], (c / Lf.n[0]) % Lf.n[1], c / (Lf.n[0] * Lf.n[1])};
@@ -1076,39 +1071,16 @@ CoarseData build_coarse(const Layout &Lf, const Geometry &geo, const double *alp
                 fc.lat2free[Lc.index(m, e[0] + i1, e[1] + i2, e[2] + i3)];
     for (int a = 0; a < Lc.nloc; ++a)
       for (int b = 0; b < Lc.nloc; ++b)
-        if (l2f[a] >= 0 && l2f[b] >= 0) A0[(size_t)l2f[a] * nc + l2f[b]] += AK[(size_t)a * Lc.nloc + b];
+        if (l2f[a] >= 0 && l2f[b] >= 0) t.push_back({l2f[a], l2f[b], AK[(size_t)a * Lc.nloc + b]});
   }
-  // Cholesky A0 = L L^T, then A0^{-1} = L^-T L^-1
-  std::vector<double> Lm = A0;
-  for (int j = 0; j < nc; ++j) {
-    double d = Lm[(size_t)j * nc + j];
-    for (int kk = 0; kk < j; ++kk) d -= Lm[(size_t)j * nc + kk] * Lm[(size_t)j * nc + kk];
-    if (!(d > 0)) throw std::runtime_error("coarse matrix not SPD");
-    d = std::sqrt(d);
-    Lm[(size_t)j * nc + j] = d;
-#pragma omp parallel for schedule(static)
-    for (int i = j + 1; i < nc; ++i) {
-      double s = Lm[(size_t)i * nc + j];
-      for (int kk = 0; kk < j; ++kk) s -= Lm[(size_t)i * nc + kk] * Lm[(size_t)j * nc + kk];
-      Lm[(size_t)i * nc + j] = s / d;
-    }
-  }
-  C.A0inv.assign((size_t)nc * nc, 0.0);
-#pragma omp parallel for schedule(dynamic, 8)
-  for (int c = 0; c < nc; ++c) {
-    std::vector<double> y(nc, 0.0);
-    for (int i = 0; i < nc; ++i) {
-      double s = (i == c) ? 1.0 : 0.0;
-      for (int kk = 0; kk < i; ++kk) s -= Lm[(size_t)i * nc + kk] * y[kk];
-      y[i] = s / Lm[(size_t)i * nc + i];
-    }
-    for (int i = nc - 1; i >= 0; --i) {
-      double s = y[i];
-      for (int kk = i + 1; kk < nc; ++kk) s -= Lm[(size_t)kk * nc + i] * C.A0inv[(size_t)kk * nc + c];
-      C.A0inv[(size_t)i * nc + c] = s / Lm[(size_t)i * nc + i];
-    }
-  }
-  // R_0: closed-form injection coefficients per direction
+  return t;
+}
+
+// R_0 (coarse free rows, fine lattice columns): closed-form injection
+// coefficients per direction (dual functionals of Eq. fdmdualbasis applied
+// to the p = 1 basis).
+static void restriction_R0(const Layout &Lf, const Layout &Lc, const FreeMap &fc, CoarseData &C) {
+  const int p = Lf.p;
   Basis1D B(p);
   std::vector<Trip> t;
   FreeMap ff(Lf);
@@ -1147,8 +1119,183 @@ CoarseData build_coarse(const Layout &Lf, const Geometry &geo, const double *alp
           t.push_back({cf, (int)lat, v});
         }
   }
-  C.R0 = csr_from_triplets(nc, (int)Lf.size, t);
+  C.R0 = csr_from_triplets(C.nc, (int)Lf.size, t);
   C.R0T = transpose(C.R0);
+}
+
+// Dense SPD inverse by Cholesky (n x n row-major), OpenMP over columns.
+static std::vector<double> dense_spd_inverse(std::vector<double> Lm, int nc) {
+  for (int j = 0; j < nc; ++j) {
+    double d = Lm[(size_t)j * nc + j];
+    for (int kk = 0; kk < j; ++kk) d -= Lm[(size_t)j * nc + kk] * Lm[(size_t)j * nc + kk];
+    if (!(d > 0)) throw std::runtime_error("coarse matrix not SPD");
+    d = std::sqrt(d);
+    Lm[(size_t)j * nc + j] = d;
+#pragma omp parallel for schedule(static)
+    for (int i = j + 1; i < nc; ++i) {
+      double s = Lm[(size_t)i * nc + j];
+      for (int kk = 0; kk < j; ++kk) s -= Lm[(size_t)i * nc + kk] * Lm[(size_t)j * nc + kk];
+      Lm[(size_t)i * nc + j] = s / d;
+    }
+  }
+  // Y = L^-1 stored transposed (row c of Yt = column c of Y), so both the
+  // substitution and the product A^-1 = Y^T Y run over contiguous rows.
+  std::vector<double> Yt((size_t)nc * nc, 0.0);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int c = 0; c < nc; ++c) {
+    double *y = &Yt[(size_t)c * nc];
+    for (int i = c; i < nc; ++i) {
+      const double *Li = &Lm[(size_t)i * nc];
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int kk = c; kk < i; ++kk) s -= Li[kk] * y[kk];
+      y[i] = s / Li[i];
+    }
+  }
+  std::vector<double>().swap(Lm);
+  std::vector<double> inv((size_t)nc * nc, 0.0);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int a = 0; a < nc; ++a) {
+    const double *ya = &Yt[(size_t)a * nc];
+    for (int b = 0; b <= a; ++b) {
+      const double *yb = &Yt[(size_t)b * nc];
+      double s = 0.0;
+      for (int i = a; i < nc; ++i) s += ya[i] * yb[i];
+      inv[(size_t)a * nc + b] = s;
+      inv[(size_t)b * nc + a] = s;
+    }
+  }
+  return inv;
+}
+
+CoarseData build_coarse(const Layout &Lf, const Geometry &geo, const double *alpha,
+                        const double *beta) {
+  CoarseData C;
+  Layout Lc(Lf.k, Lf.n, 1);
+  FreeMap fc(Lc);
+  const int nc = (int)fc.free2lat.size();
+  C.nc = nc;
+  if (nc > 16384)
+    throw std::runtime_error("coarse space too large for the dense coarse solve (> 16384 DOFs): "
+                             "use RM_COARSE_GMG");
+  std::vector<double> A0((size_t)nc * nc, 0.0);
+  for (const Trip &x : coarse_triplets(Lf, Lc, fc, geo, alpha, beta))
+    A0[(size_t)x.r * nc + x.c] += x.v;
+  C.A0inv = dense_spd_inverse(A0, nc);
+  restriction_R0(Lf, Lc, fc, C);
+  return C;
+}
+
+// Sparse product A B (rows of A, columns of B).
+static Csr spgemm(const Csr &A, const Csr &B) {
+  std::vector<Trip> t;
+  std::vector<double> acc(B.ncols, 0.0);
+  std::vector<char> m(B.ncols, 0);
+  std::vector<int> touched;
+  for (int i = 0; i < A.nrows; ++i) {
+    touched.clear();
+    for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
+      const int j = A.col[e];
+      for (int64_t f = B.ptr[j]; f < B.ptr[j + 1]; ++f) {
+        const int c = B.col[f];
+        if (!m[c]) { m[c] = 1; acc[c] = 0.0; touched.push_back(c); }
+        acc[c] += A.val[e] * B.val[f];
+      }
+    }
+    for (int c : touched) { t.push_back({i, c, acc[c]}); m[c] = 0; }
+  }
+  return csr_from_triplets(A.nrows, B.ncols, t);
+}
+
+CoarseData build_coarse_gmg(const Layout &Lf, const Geometry &geo, const double *alpha,
+                            const double *beta, CoarseGMG &mg) {
+  CoarseData C;
+  const int k = Lf.k;
+  Layout Lc(k, Lf.n, 1);
+  FreeMap fc(Lc);
+  C.nc = (int)fc.free2lat.size();
+  std::vector<Trip> t = coarse_triplets(Lf, Lc, fc, geo, alpha, beta);
+  Csr A = csr_from_triplets(C.nc, C.nc, t);
+  restriction_R0(Lf, Lc, fc, C);
+  mg = CoarseGMG();
+  int n[3] = {Lf.n[0], Lf.n[1], Lf.n[2]};
+  Layout L = Lc;
+  FreeMap fm = fc;
+  while (true) {
+    const bool can = n[0] % 2 == 0 && n[1] % 2 == 0 && n[2] % 2 == 0 && n[0] >= 4 && n[1] >= 4 &&
+                     n[2] >= 4 && A.nrows > 512;
+    if (!can) break;
+    int nh[3] = {n[0] / 2, n[1] / 2, n[2] / 2};
+    Layout Lh(k, nh, 1);
+    FreeMap fh(Lh);
+    // P: level l+1 (mesh nh) -> level l (mesh n), per direction
+    // s-type: fine index g from coarse g/2 (even) or (g-1)/2, (g+1)/2 with 1/2
+    // r-type: fine cell g from coarse cell g/2 with weight 1/2
+    std::vector<Trip> pt;
+    for (int f = 0; f < (int)fm.free2lat.size(); ++f) {
+      int m;
+      long long g[3];
+      L.coords(fm.free2lat[f], m, g);
+      long long ci[3][2];
+      double cv[3][2];
+      int cn[3];
+      for (int d = 0; d < 3; ++d) {
+        if (L.t[m][d] == 's') {
+          if (g[d] % 2 == 0) { ci[d][0] = g[d] / 2; cv[d][0] = 1.0; cn[d] = 1; }
+          else { ci[d][0] = (g[d] - 1) / 2; ci[d][1] = (g[d] + 1) / 2; cv[d][0] = cv[d][1] = 0.5; cn[d] = 2; }
+        } else {
+          ci[d][0] = g[d] / 2; cv[d][0] = 0.5; cn[d] = 1;
+        }
+      }
+      for (int a3 = 0; a3 < cn[2]; ++a3)
+        for (int a2 = 0; a2 < cn[1]; ++a2)
+          for (int a1 = 0; a1 < cn[0]; ++a1) {
+            int cf = fh.lat2free[Lh.index(m, ci[0][a1], ci[1][a2], ci[2][a3])];
+            if (cf < 0) continue;
+            pt.push_back({f, cf, cv[0][a1] * cv[1][a2] * cv[2][a3]});
+          }
+    }
+    Csr P = csr_from_triplets((int)fm.free2lat.size(), (int)fh.free2lat.size(), pt);
+    Csr PT = transpose(P);
+    Csr Ah = spgemm(PT, spgemm(A, P));
+    // smoother weights
+    std::vector<double> dinv(A.nrows);
+    double norm = 0.0;
+    for (int i = 0; i < A.nrows; ++i) {
+      double diag = 0.0, rs = 0.0;
+      for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
+        rs += std::fabs(A.val[e]);
+        if (A.col[e] == i) diag = A.val[e];
+      }
+      if (!(diag > 0)) throw std::runtime_error("coarse multigrid: non-positive diagonal");
+      dinv[i] = 1.0 / diag;
+      norm = std::max(norm, rs / diag);
+    }
+    for (double &v : dinv) v /= norm;
+    mg.A.push_back(A);
+    mg.P.push_back(P);
+    mg.PT.push_back(PT);
+    mg.dinv.push_back(dinv);
+    if (k >= 1) {
+      // vertex stars of the level (exact, block inverses); slot maps renumbered
+      // to the level's compact free numbering
+      PatchFamily F = build_patches(L, fm, A, 0, false, 0);
+      for (int &s : F.slotmap)
+        if (s >= 0) s = fm.lat2free[s];
+      mg.star.push_back(std::move(F));
+    }
+    A = Ah;
+    L = Lh;
+    fm = fh;
+    for (int d = 0; d < 3; ++d) n[d] = nh[d];
+  }
+  mg.levels = (int)mg.A.size();
+  mg.ncoarsest = A.nrows;
+  if (mg.ncoarsest > 8192) throw std::runtime_error("coarse multigrid: coarsest level too large");
+  std::vector<double> dense((size_t)A.nrows * A.nrows, 0.0);
+  for (int i = 0; i < A.nrows; ++i)
+    for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; ++e) dense[(size_t)i * A.nrows + A.col[e]] += A.val[e];
+  mg.Ainv = dense_spd_inverse(dense, A.nrows);
+  mg.A.push_back(A);
   return C;
 }
 

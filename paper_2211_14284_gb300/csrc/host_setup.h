@@ -116,6 +116,29 @@ struct CoarseData {
 CoarseData build_coarse(const Layout &Lf, const Geometry &geo, const double *alpha,
                         const double *beta);
 
+// Multigrid hierarchy for the p = 1 coarse problem when it is too large for
+// a dense inverse: level 0 is A_0 (sparse); level l+1 is the Galerkin
+// product P^T A_l P with the lowest-order refinement P from the mesh n_l/2 to
+// n_l (hat weights along s-type directions, 1/2 per r-type direction);
+// damped point Jacobi (omega = 1 / ||D^-1 A||_inf) pre- and post-smoothing;
+// dense inverse on the coarsest level.
+struct CoarseGMG {
+  int levels = 0;               // smoothed levels; level `levels` is solved densely
+  std::vector<Csr> A;           // A[l], compact free numbering of level l
+  std::vector<Csr> P, PT;       // P[l]: level l+1 -> level l
+  std::vector<std::vector<double>> dinv;  // omega / diag(A_l)  (k = 0)
+  // k = 1, 2: additive vertex-star smoother omega sum_v R_v^T A_v^-1 R_v with
+  // omega = 1/8 (at most 8 stars overlap a DOF); slot maps in the level's
+  // compact numbering
+  std::vector<PatchFamily> star;
+  double star_omega = 0.125;
+  std::vector<double> Ainv;     // coarsest dense inverse
+  int ncoarsest = 0;
+};
+// R_0 and the multigrid hierarchy of the coarse problem.
+CoarseData build_coarse_gmg(const Layout &Lf, const Geometry &geo, const double *alpha,
+                            const double *beta, CoarseGMG &mg);
+
 // Discrete gradient V^0 -> V^1 restricted to free rows/cols (lattice ids).
 Csr discrete_gradient(const Layout &L0, const Layout &L1, const std::vector<int> &rows1,
                       const std::vector<int> &cols0);

@@ -355,6 +355,200 @@ __global__ void __launch_bounds__(kApplyThreads) apply_kernel(ApplyDev P, const 
 }
 
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Cartesian cells (axis-aligned boxes with constant alpha, beta): the cell
+// matrix is a Kronecker sum of the 1D FDM factors (Sec. 2.2-2.4).  The mass
+// of V^kk is c_m (x)_d F_d per component m, F_d = B-hat (s-type) or I
+// (r-type), with the box metric c_m; the derivative term is
+// D-hat^T (alpha M^{k+1}) D-hat.  B-hat is the identity on the interior plus
+// a 2x2 block on {0, p}; a row of D-hat has at most three nonzeros.  No
+// quadrature is needed (~30 flops per DOF).
+
+// Box metric of kk-forms, component m (J = diag(h/2)).
+__device__ __forceinline__ double box_metric(int kk, int m, const double h[3]) {
+  const double det = 0.125 * h[0] * h[1] * h[2];
+  if (kk == 0) return det;
+  if (kk == 3) return 1.0 / det;
+  if (kk == 1) return det * 4.0 / (h[m] * h[m]);
+  return 0.25 * h[m] * h[m] / det;
+}
+
+// out (SET) = c (x)_d F_d in, for one component with types t and dims ld.
+__device__ void box_mass(const double *__restrict__ in, double *__restrict__ out, const int *ld,
+                         const char *t, int p, double a, double b, double c) {
+  const int n = ld[0] * ld[1] * ld[2];
+  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    const int ii[3] = {idx % ld[0], (idx / ld[0]) % ld[1], idx / (ld[0] * ld[1])};
+    int jj[3][2], nj[3];
+    double ww[3][2];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (t[d] == 's' && (ii[d] == 0 || ii[d] == p)) {
+        jj[d][0] = 0; ww[d][0] = ii[d] == 0 ? a : b;
+        jj[d][1] = p; ww[d][1] = ii[d] == 0 ? b : a;
+        nj[d] = 2;
+      } else {
+        jj[d][0] = ii[d]; ww[d][0] = 1.0; nj[d] = 1;
+      }
+    }
+    double s = 0.0;
+    for (int c3 = 0; c3 < nj[2]; ++c3)
+      for (int c2 = 0; c2 < nj[1]; ++c2)
+        for (int c1 = 0; c1 < nj[0]; ++c1)
+          s = fma(ww[0][c1] * ww[1][c2] * ww[2][c3],
+                  in[jj[0][c1] + ld[0] * (jj[1][c2] + ld[1] * jj[2][c3])], s);
+    out[idx] = c * s;
+  }
+}
+
+__global__ void __launch_bounds__(kApplyThreads) apply_cart_kernel(ApplyDev P, const double *__restrict__ x,
+                                                                   double *__restrict__ y) {
+  extern __shared__ double sm[];
+  const int p = P.p, k = P.k;
+  double *D1 = sm;
+  double *xl = D1 + p * (p + 1);
+  double *yl = xl + P.nloc0;
+  double *dl = yl + P.nloc0;
+  double *dyl = dl + P.nloc1;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int c = blockIdx.x;
+  const int e[3] = {c % P.n[0], (c / P.n[0]) % P.n[1], c / (P.n[0] * P.n[1])};
+  const double h[3] = {P.h[3 * c], P.h[3 * c + 1], P.h[3 * c + 2]};
+  const double al = P.alpha[c], be = P.beta[c];
+  {
+    const double *g = P.tabs + P.q * (p + 1) + P.q * p;
+    for (int i = tid; i < p * (p + 1); i += NT) D1[i] = g[i];
+  }
+  for (int l = tid; l < P.nloc0; l += NT) {
+    int m = 0;
+    while (m + 1 < P.nc0 && l >= P.loff0[m + 1]) ++m;
+    int r = l - P.loff0[m];
+    const int i1 = r % P.ld0[m][0];
+    r /= P.ld0[m][0];
+    const int i2 = r % P.ld0[m][1], i3 = r / P.ld0[m][1];
+    const int g[3] = {e[0] * p + i1, e[1] * p + i2, e[2] * p + i3};
+    bool dir = false;
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      if (P.t0[m][d] == 's' && (g[d] == 0 || g[d] == P.n[d] * p)) dir = true;
+    xl[l] = dir ? 0.0 : x[P.off[m] + g[0] + (long long)P.N[m][0] * (g[1] + (long long)P.N[m][1] * g[2])];
+  }
+  __syncthreads();
+  // y = beta M^k x
+  for (int m = 0; m < P.nc0; ++m)
+    box_mass(xl + P.loff0[m], yl + P.loff0[m], P.ld0[m], P.t0[m], p, P.bh_a, P.bh_b,
+             be * box_metric(k, m, h));
+  // d = D-hat x (target component t, r-type along each term's direction)
+  for (int t = 0; t < P.nc1; ++t) {
+    const int *lt = P.ld1[t];
+    const int n = lt[0] * lt[1] * lt[2];
+    for (int idx = tid; idx < n; idx += NT) {
+      const int jj[3] = {idx % lt[0], (idx / lt[0]) % lt[1], idx / (lt[0] * lt[1])};
+      double s = 0.0;
+      for (int q = 0; q < c_nterms[k][t]; ++q) {
+        const DTerm T = c_terms[k][t][q];
+        const int *ls = P.ld0[T.src];
+        const double *in = xl + P.loff0[T.src];
+        const int j = jj[T.dir];
+        int ii[3] = {jj[0], jj[1], jj[2]};
+        double v = 0.0;
+        ii[T.dir] = 0;
+        v = fma(D1[j * (p + 1)], in[ii[0] + ls[0] * (ii[1] + ls[1] * ii[2])], v);
+        ii[T.dir] = p;
+        v = fma(D1[j * (p + 1) + p], in[ii[0] + ls[0] * (ii[1] + ls[1] * ii[2])], v);
+        if (j >= 1) {
+          ii[T.dir] = j;
+          v = fma(D1[j * (p + 1) + j], in[ii[0] + ls[0] * (ii[1] + ls[1] * ii[2])], v);
+        }
+        s += T.sgn > 0 ? v : -v;
+      }
+      dl[P.loff1[t] + idx] = s;
+    }
+  }
+  __syncthreads();
+  // dy = alpha M^{k+1} d
+  for (int t = 0; t < P.nc1; ++t)
+    box_mass(dl + P.loff1[t], dyl + P.loff1[t], P.ld1[t], P.t1[t], p, P.bh_a, P.bh_b,
+             al * box_metric(k + 1, t, h));
+  __syncthreads();
+  // y += D-hat^T dy
+  for (int m = 0; m < P.nc0; ++m) {
+    const int *ls = P.ld0[m];
+    const int n = ls[0] * ls[1] * ls[2];
+    for (int idx = tid; idx < n; idx += NT) {
+      const int ii[3] = {idx % ls[0], (idx / ls[0]) % ls[1], idx / (ls[0] * ls[1])};
+      double s = 0.0;
+      for (int t = 0; t < P.nc1; ++t)
+        for (int q = 0; q < c_nterms[k][t]; ++q) {
+          const DTerm T = c_terms[k][t][q];
+          if (T.src != m) continue;
+          const int *lt = P.ld1[t];
+          const double *in = dyl + P.loff1[t];
+          const int i = ii[T.dir];
+          int jj[3] = {ii[0], ii[1], ii[2]};
+          double v = 0.0;
+          if (i == 0 || i == p) {
+            for (int j = 0; j < p; ++j) {
+              jj[T.dir] = j;
+              v = fma(D1[j * (p + 1) + i], in[jj[0] + lt[0] * (jj[1] + lt[1] * jj[2])], v);
+            }
+          } else {
+            jj[T.dir] = i;
+            v = D1[i * (p + 1) + i] * in[jj[0] + lt[0] * (jj[1] + lt[1] * jj[2])];
+          }
+          s += T.sgn > 0 ? v : -v;
+        }
+      yl[P.loff0[m] + idx] += s;
+    }
+  }
+  __syncthreads();
+  for (int l = tid; l < P.nloc0; l += NT) {
+    int m = 0;
+    while (m + 1 < P.nc0 && l >= P.loff0[m + 1]) ++m;
+    int r = l - P.loff0[m];
+    const int i1 = r % P.ld0[m][0];
+    r /= P.ld0[m][0];
+    const int i2 = r % P.ld0[m][1], i3 = r / P.ld0[m][1];
+    const int g[3] = {e[0] * p + i1, e[1] * p + i2, e[2] * p + i3};
+    bool dir = false;
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      if (P.t0[m][d] == 's' && (g[d] == 0 || g[d] == P.n[d] * p)) dir = true;
+    if (!dir)
+      atomicAdd(&y[P.off[m] + g[0] + (long long)P.N[m][0] * (g[1] + (long long)P.N[m][1] * g[2])], yl[l]);
+  }
+}
+
+// One damped Jacobi sweep of the coarse multigrid: x_out = x_in + w (b - A x_in),
+// w = omega / diag(A) (FP64 CSR, TPR threads per row).
+template <int TPR>
+__global__ void jacobi_kernel(int nrows, const int *__restrict__ ptr, const int *__restrict__ col,
+                              const double *__restrict__ val, const double *__restrict__ b,
+                              const double *__restrict__ xin, const double *__restrict__ w,
+                              double *__restrict__ xout) {
+  const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = (int)(gt / TPR), lane = (int)(gt % TPR);
+  double s = 0.0;
+  if (row < nrows)
+    for (int e = ptr[row] + lane; e < ptr[row + 1]; e += TPR) s = fma(val[e], xin[col[e]], s);
+#pragma unroll
+  for (int off = TPR / 2; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off, TPR);
+  if (lane == 0 && row < nrows) xout[row] = fma(w[row], b[row] - s, xin[row]);
+}
+
+__global__ void diag_scale_kernel(int n, const double *__restrict__ w, const double *__restrict__ b,
+                                  double *__restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = w[i] * b[i];
+}
+
+// y = a x (acc = 0) or y += a x (acc = 1)
+__global__ void axpy_kernel(int n, double a, const double *__restrict__ x, double *__restrict__ y,
+                            int acc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = acc ? fma(a, x[i], y[i]) : a * x[i];
+}
+
 template <typename VT, int TPR>
 __global__ void spmv_kernel(int nrows, const int *__restrict__ rid, const int *__restrict__ ptr,
                             const int *__restrict__ col, const VT *__restrict__ val,
@@ -580,6 +774,14 @@ cudaError_t launch_metric(const ApplyDev &A, double *G, cudaStream_t s) {
 
 cudaError_t launch_apply(const ApplyDev &A, const double *x, double *y, cudaStream_t s) {
   const int ncell = A.n[0] * A.n[1] * A.n[2];
+  if (A.cartesian) {
+    const size_t smem = ((size_t)A.p * (A.p + 1) + 2 * (size_t)A.nloc0 + 2 * (size_t)A.nloc1) * sizeof(double);
+    cudaError_t err = cudaFuncSetAttribute(apply_cart_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    apply_cart_kernel<<<ncell, kApplyThreads, smem, s>>>(A, x, y);
+    g_launches += 1;
+    return cudaGetLastError();
+  }
   const size_t smem = A.smem_doubles * sizeof(double);
   cudaError_t err = cudaFuncSetAttribute(apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
@@ -624,7 +826,7 @@ static void patch_dispatch(const DevPatch &F, const double *r, double *z, cudaSt
   }
   const size_t base = (size_t)F.nslots * sizeof(double);
   const size_t staged = base + (size_t)F.nnz * sizeof(VT);
-  if (staged <= 96 * 1024) {
+  if (staged <= 220 * 1024) {
     cudaFuncSetAttribute(patch_kernel<VT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)staged);
     patch_kernel<VT, true><<<F.npatch, 128, staged, s>>>(F, r, z);
   } else {
@@ -637,6 +839,36 @@ cudaError_t launch_patches(const DevPatch &F, const double *r, double *z, cudaSt
   if (F.npatch == 0) return cudaSuccess;
   if (F.vt == 0) patch_dispatch<double>(F, r, z, s);
   else patch_dispatch<float>(F, r, z, s);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jacobi(const DevCsr &A, const double *b, const double *xin, const double *w,
+                          double *xout, cudaStream_t s) {
+  const int threads = 256;
+  const long long tot = (long long)A.nrows * A.tpr;
+  const int grid = (int)((tot + threads - 1) / threads);
+  const double *v = reinterpret_cast<const double *>(A.val);
+  switch (A.tpr) {
+    case 1: jacobi_kernel<1><<<grid, threads, 0, s>>>(A.nrows, A.ptr, A.col, v, b, xin, w, xout); break;
+    case 2: jacobi_kernel<2><<<grid, threads, 0, s>>>(A.nrows, A.ptr, A.col, v, b, xin, w, xout); break;
+    case 4: jacobi_kernel<4><<<grid, threads, 0, s>>>(A.nrows, A.ptr, A.col, v, b, xin, w, xout); break;
+    case 8: jacobi_kernel<8><<<grid, threads, 0, s>>>(A.nrows, A.ptr, A.col, v, b, xin, w, xout); break;
+    case 16: jacobi_kernel<16><<<grid, threads, 0, s>>>(A.nrows, A.ptr, A.col, v, b, xin, w, xout); break;
+    default: jacobi_kernel<32><<<grid, threads, 0, s>>>(A.nrows, A.ptr, A.col, v, b, xin, w, xout); break;
+  }
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy(int n, double a, const double *x, double *y, int acc, cudaStream_t s) {
+  axpy_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, a, x, y, acc);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag_scale(int n, const double *w, const double *b, double *x, cudaStream_t s) {
+  diag_scale_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, w, b, x);
   g_launches += 1;
   return cudaGetLastError();
 }

@@ -20,7 +20,7 @@ RM_HGRAD, RM_HCURL, RM_HDIV = 0, 1, 2
 RM_FP64, RM_FP32 = 0, 1
 RM_PAFW, RM_PH = 0, 1
 RM_CHOL, RM_ICC = 0, 1
-RM_COARSE_NONE, RM_COARSE_P1 = 0, 1
+RM_COARSE_NONE, RM_COARSE_P1, RM_COARSE_GMG = 0, 1, 2
 STATUS = {0: "RM_OK", 1: "RM_ERR_ARG", 2: "RM_ERR_CUDA", 3: "RM_ERR_OOM",
           4: "RM_ERR_BREAKDOWN", 5: "RM_ERR_NOT_CONVERGED", 6: "RM_ERR_NAN"}
 

@@ -64,6 +64,21 @@ def test_apply_parity(k, n, p, perturb, coef):
     assert np.all(got[dmask] == 0.0)
 
 
+@pytest.mark.parametrize("k,n,p", [(2, (2, 2, 3), 10), (1, 2, 10), (0, 2, 12)])
+def test_apply_parity_cartesian_high_p(k, n, p):
+    """High degrees on Cartesian meshes (the Kronecker kernel): sampled rows
+    computed one by one by the oracle's quadrature."""
+    opts = dict(static_condensation=1, factor=1, decomposition=1 if k == 1 else 0)
+    s, pr = _setup(k, n, p, 0.0, True, **opts)
+    x = inputs.normal_rhs(pr.lat.size, 24)
+    y = torch.zeros(pr.lat.size, dtype=torch.float64, device="cuda")
+    s.apply(_dev(x), y)
+    got = _host(y)
+    rows = np.random.default_rng(6).choice(pr.free, 24, replace=False)
+    want = pr.apply_rows(x, rows)
+    assert np.abs(got[rows] - want).max() <= 1e-12 * np.abs(got).max()
+
+
 def _oracle_prec(pr, mode):
     P = assemble_aux(pr)[pr.free][:, pr.free]
     if mode == "pafw":
