@@ -270,6 +270,9 @@ def run_ours(args):
         "variants": {v: summarise(v) for v in VARIANTS},
         "clocks": clocks,
     }
+    if args.batch_count > 0:
+        line["variants"]["batched"] = run_batched(args.batch_count, args.steps,
+                                                  max(1, args.warmup // 2), stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, budget_s=30.0)
     if rank == 0:
@@ -354,6 +357,85 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def batched_problems(count):
+    """The uneven H(curl) batch (n ~ U{4..12}, p ~ U{3..12}, beta log-uniform
+    in [0.1, 10], alpha = 1); count < 64 takes the first `count` problems with
+    n, p <= 8 (a bounded sample whose host setup stays short)."""
+    from paper_2211_14284_gb300 import inputs
+    probs = inputs.batched_hcurl_problems(64, seed=4)
+    if count < 64:
+        probs = [p for p in probs if p["n"] <= 8 and p["p"] <= 8][:count]
+    out = []
+    for pr in probs:
+        nc = pr["n"] ** 3
+        out.append({"space": 1, "n": pr["n"], "p": pr["p"], "alpha": [pr["alpha"]] * nc,
+                    "beta": [pr["beta"]] * nc, "rhs_seed": pr["rhs_seed"]})
+    return out
+
+
+def run_batched(count, steps, warmup, stream):
+    """Uneven H(curl) problems: the batched solver (one graph-captured
+    lock-step iteration for all) against solving them one after another with
+    the single-problem solver; SC-PH, ICC(0) potential patches, P1 coarse."""
+    import torch
+    from paper_2211_14284_gb300 import inputs
+    from paper_2211_14284_gb300.rm import BatchSolver, Solver
+    probs = batched_problems(count)
+    opts = dict(static_condensation=1, decomposition=1, factor=1, rtol=1e-8, max_it=1000)
+    t0 = time.time()
+    B = BatchSolver(probs, check_every=8, **opts)
+    setup_s = time.time() - t0
+    singles = [Solver(1, pr["n"], pr["p"], alpha=pr["alpha"], beta=pr["beta"], stream=stream, **opts)
+               for pr in probs]
+    bs = [torch.tensor(inputs.normal_rhs(sz, pr["rhs_seed"]), device="cuda")
+          for pr, sz in zip(probs, B.sizes)]
+    xs = [torch.zeros_like(b) for b in bs]
+    dofs = sum(B.sizes)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def time_it(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(steps):
+            flush.fill_(1.0)
+            for x in xs:
+                x.zero_()
+            torch.cuda.synchronize()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            out = fn()
+            ev1.record(stream)
+            ev1.synchronize()
+            tot += ev0.elapsed_time(ev1)
+        return tot / steps, out
+
+    def batched():
+        infos = B.solve(bs, xs, stream=stream)
+        if not all(i["status"] == "RM_OK" for i in infos):
+            raise RuntimeError("batched solve did not converge")
+        return infos
+
+    def sequential():
+        infos = [s.solve(b, x) for s, b, x in zip(singles, bs, xs)]
+        if not all(i["status"] == "RM_OK" for i in infos):
+            raise RuntimeError("sequential solve did not converge")
+        return infos
+
+    ms_b, ib = time_it(batched)
+    ms_s, isq = time_it(sequential)
+    return {"problems": len(probs), "lattice_dofs": dofs, "setup_s": setup_s,
+            "value": dofs / (ms_b / 1e3), "ms_per_step": ms_b,
+            "sequential_value": dofs / (ms_s / 1e3), "sequential_ms_per_step": ms_s,
+            "speedup_vs_sequential": ms_s / ms_b,
+            "iterations_max": max(i["iterations"] for i in ib),
+            "kernel_launches_per_solve": ib[0]["kernel_launches"],
+            "sample": ("all 64 problems" if count >= 64 else
+                       f"first {len(probs)} problems with n, p <= 8")}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -361,6 +443,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=8,
+                    help="problems of the uneven H(curl) batch to time (64 = all; 0 = skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

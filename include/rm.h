@@ -142,6 +142,36 @@ int rm_stats(const rm_handle *h, long long *patches, long long *slots,
 void rm_destroy(rm_handle *h);
 const char *rm_last_error(const rm_handle *h);
 
+/* ---- batched solves --------------------------------------------------------
+ * Many independent problems of uneven mesh size and degree (Cartesian meshes:
+ * every cell an axis-aligned box) solved together with the same options.
+ * The problems are set up one by one on the host (as rm_setup would) and
+ * concatenated on the device into one block-diagonal system: one launch per
+ * patch template (problems of equal space and p share templates), one apply
+ * launch per (space, p) over a (problem, cell) work list whose CTA size is
+ * picked by timing at setup, lock-step CG with per-problem scalars and
+ * convergence masks, one iteration captured in a CUDA graph and replayed
+ * check_every times between host reads of the convergence flags.
+ * Coarse correction: RM_COARSE_P1 (exact) or RM_COARSE_NONE. */
+typedef struct rm_batch rm_batch;
+
+/* space, meshes, p: host arrays of nprob entries; alpha, beta: host arrays of
+ * nprob host pointers (each per-cell, or NULL for 1), or NULL.  stream is
+ * unused (the batch runs on its own stream; see rm_batch_solve). */
+int rm_batch_setup(rm_batch **b, int nprob, const int *space, const rm_mesh *meshes, const int *p,
+                   const double *const *alpha, const double *const *beta, const rm_options *opt,
+                   void *stream);
+int rm_batch_ndofs(const rm_batch *b, int i, long long *lattice);
+/* bvec, x: host arrays of nprob device pointers (problem i's vectors in the
+ * layout of rm_apply); x is the initial guess in and the solution out.
+ * stream: the caller's stream holding b and x (synchronised on entry; the
+ * call returns after the results are written).  infos: nprob entries or
+ * NULL.  Returns RM_ERR_NOT_CONVERGED if any problem misses rtol. */
+int rm_batch_solve(rm_batch *b, const double *const *bvec, double *const *x, rm_info *infos,
+                   void *stream);
+void rm_batch_destroy(rm_batch *b);
+const char *rm_batch_last_error(const rm_batch *b);
+
 /* z = B r without allocating: the same relaxation as rm_precondition for a
  * handle built without static condensation (vertex-star patches plus the
  * p = 1 coarse correction), for callers that must not allocate device memory

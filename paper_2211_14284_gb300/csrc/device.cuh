@@ -90,4 +90,22 @@ cudaError_t launch_update_xr(long long n, double *x, double *r, const double *p,
 cudaError_t launch_update_p(long long n, double *p, const double *z, const double *scal,
                             cudaStream_t s);
 
+// batched solver (batch.cu)
+cudaError_t launch_apply_batch(const ApplyDev *descs, const int2 *work, int nwork, int threads,
+                               size_t smem, const double *x, double *y, cudaStream_t s);
+cudaError_t launch_seg_dot(const int4 *chunk, int nchunk, const int *cptr, int nprob, const double *a,
+                           const double *b, double *partial, double *scal, int *done, int *iters,
+                           int slot, int op, double tol2, cudaStream_t s);
+cudaError_t launch_seg_update_xr(const int4 *chunk, int nchunk, const int *cptr, int nprob, double *x,
+                                 double *r, const double *p, const double *q, double *partial,
+                                 double *scal, int *done, int *iters, double tol2, cudaStream_t s);
+cudaError_t launch_seg_dot2(const int4 *chunk, int nchunk, const int *cptr, int nprob, const double *r,
+                            const double *z, const double *q, double *partial, double *scal, int *done,
+                            int *iters, int flexible, cudaStream_t s);
+cudaError_t launch_seg_update_p(const int4 *chunk, int nchunk, double *p, const double *z,
+                                const double *scal, cudaStream_t s);
+cudaError_t launch_gemv_batch(int nrows, const int *rowprob, const long long *aoff, const int *cstart,
+                              const int *csz, const double *A, const double *x, double *y,
+                              cudaStream_t s);
+
 }  // namespace rmd

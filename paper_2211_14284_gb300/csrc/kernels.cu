@@ -401,8 +401,11 @@ __device__ void box_mass(const double *__restrict__ in, double *__restrict__ out
   }
 }
 
-__global__ void __launch_bounds__(kApplyThreads) apply_cart_kernel(ApplyDev P, const double *__restrict__ x,
-                                                                   double *__restrict__ y) {
+// One Cartesian cell c of the problem described by P (shared by the single
+// and the batched kernels; the batched one bakes each problem's offset in
+// the concatenated vectors into P.off).
+__device__ void cart_cell(const ApplyDev &P, const int c, const double *__restrict__ x,
+                          double *__restrict__ y) {
   extern __shared__ double sm[];
   const int p = P.p, k = P.k;
   double *D1 = sm;
@@ -411,7 +414,6 @@ __global__ void __launch_bounds__(kApplyThreads) apply_cart_kernel(ApplyDev P, c
   double *dl = yl + P.nloc0;
   double *dyl = dl + P.nloc1;
   const int tid = threadIdx.x, NT = blockDim.x;
-  const int c = blockIdx.x;
   const int e[3] = {c % P.n[0], (c / P.n[0]) % P.n[1], c / (P.n[0] * P.n[1])};
   const double h[3] = {P.h[3 * c], P.h[3 * c + 1], P.h[3 * c + 2]};
   const double al = P.alpha[c], be = P.beta[c];
@@ -517,6 +519,23 @@ __global__ void __launch_bounds__(kApplyThreads) apply_cart_kernel(ApplyDev P, c
     if (!dir)
       atomicAdd(&y[P.off[m] + g[0] + (long long)P.N[m][0] * (g[1] + (long long)P.N[m][1] * g[2])], yl[l]);
   }
+}
+
+__global__ void __launch_bounds__(kApplyThreads) apply_cart_kernel(ApplyDev P, const double *__restrict__ x,
+                                                                   double *__restrict__ y) {
+  cart_cell(P, blockIdx.x, x, y);
+}
+
+// Batched: work[b] = (problem, cell); descriptors in global memory.
+__global__ void __launch_bounds__(kApplyThreads) apply_cart_batch_kernel(const ApplyDev *__restrict__ descs,
+                                                                         const int2 *__restrict__ work,
+                                                                         const double *__restrict__ x,
+                                                                         double *__restrict__ y) {
+  __shared__ ApplyDev Ps;
+  const int2 w = work[blockIdx.x];
+  if (threadIdx.x == 0) Ps = descs[w.x];
+  __syncthreads();
+  cart_cell(Ps, w.y, x, y);
 }
 
 // One damped Jacobi sweep of the coarse multigrid: x_out = x_in + w (b - A x_in),
@@ -758,6 +777,115 @@ __global__ void finalize_kernel(const double *__restrict__ partial, double *__re
   }
 }
 
+
+// ---- batched (segmented) CG: block b works on chunk[b] = (problem, begin,
+// end) of the concatenated vectors; per-problem scalars scal[prob * S_COUNT];
+// done[prob] freezes a converged problem (alpha = beta = 0) --------------------
+__global__ void seg_dot_kernel(const int4 *__restrict__ chunk, const double *__restrict__ a,
+                               const double *__restrict__ b, double *__restrict__ partial) {
+  const int4 c = chunk[blockIdx.x];
+  double s = 0.0;
+  for (int i = c.y + threadIdx.x; i < c.z; i += blockDim.x) s = fma(a[i], b[i], s);
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+__global__ void seg_dot2_kernel(const int4 *__restrict__ chunk, int nchunk, const double *__restrict__ r,
+                                const double *__restrict__ z, const double *__restrict__ q,
+                                double *__restrict__ partial) {
+  const int4 c = chunk[blockIdx.x];
+  double s = 0.0, t = 0.0;
+  for (int i = c.y + threadIdx.x; i < c.z; i += blockDim.x) {
+    s = fma(r[i], z[i], s);
+    t = fma(q[i], z[i], t);
+  }
+  s = block_sum(s);
+  t = block_sum(t);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = s;
+    partial[nchunk + blockIdx.x] = t;
+  }
+}
+__global__ void seg_update_xr_kernel(const int4 *__restrict__ chunk, double *__restrict__ x,
+                                     double *__restrict__ r, const double *__restrict__ p,
+                                     const double *__restrict__ q, const double *__restrict__ scal,
+                                     double *__restrict__ partial) {
+  const int4 c = chunk[blockIdx.x];
+  const double a = scal[c.x * S_COUNT + S_ALPHA];
+  double s = 0.0;
+  for (int i = c.y + threadIdx.x; i < c.z; i += blockDim.x) {
+    x[i] = fma(a, p[i], x[i]);
+    const double ri = fma(-a, q[i], r[i]);
+    r[i] = ri;
+    s = fma(ri, ri, s);
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+__global__ void seg_update_p_kernel(const int4 *__restrict__ chunk, double *__restrict__ p,
+                                    const double *__restrict__ z, const double *__restrict__ scal) {
+  const int4 c = chunk[blockIdx.x];
+  const double b = scal[c.x * S_COUNT + S_BETA];
+  for (int i = c.y + threadIdx.x; i < c.z; i += blockDim.x) p[i] = fma(b, p[i], z[i]);
+}
+// One block per problem: fixed-order sum of its chunks' partials.
+// op 0: scal[slot] = s; op 1: pq -> alpha; op 2: rr -> convergence test;
+// op 3: (rz_new, zq) -> beta.
+__global__ void seg_finalize_kernel(const int *__restrict__ cptr, int nchunk,
+                                    const double *__restrict__ partial, double *__restrict__ scal,
+                                    int *__restrict__ done, int *__restrict__ iters, int slot, int op,
+                                    int flexible, double tol2) {
+  const int prob = blockIdx.x;
+  double s = 0.0, t = 0.0;
+  for (int i = cptr[prob] + threadIdx.x; i < cptr[prob + 1]; i += blockDim.x) {
+    s += partial[i];
+    if (op == 3) t += partial[nchunk + i];
+  }
+  s = block_sum(s);
+  if (op == 3) t = block_sum(t);
+  if (threadIdx.x != 0) return;
+  double *sc = scal + prob * S_COUNT;
+  const bool dn = done[prob] != 0;
+  if (op == 0) {
+    sc[slot] = s;
+  } else if (op == 1) {
+    sc[S_PQ] = s;
+    sc[S_ALPHA] = dn ? 0.0 : sc[S_RZ] / s;
+  } else if (op == 2) {
+    if (!dn) {
+      sc[S_RR] = s;
+      iters[prob] += 1;
+      if (s <= tol2 * sc[S_BB]) done[prob] = 1;
+    }
+  } else {
+    sc[S_RZNEW] = s;
+    sc[S_ZQ] = t;
+    sc[S_BETA] = dn ? 0.0 : (flexible ? -t / sc[S_PQ] : s / sc[S_RZ]);
+    sc[S_RZ] = s;
+  }
+}
+
+// Batched dense GEMV of the per-problem coarse inverses: one warp per coarse
+// row of the concatenation; rowprob maps it to its problem.
+__global__ void gemv_batch_kernel(int nrows, const int *__restrict__ rowprob,
+                                  const long long *__restrict__ aoff, const int *__restrict__ cstart,
+                                  const int *__restrict__ csz, const double *__restrict__ A,
+                                  const double *__restrict__ x, double *__restrict__ y) {
+  const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  double s = 0.0;
+  int pr = 0, lr = 0, n = 0;
+  if (g < nrows) {
+    pr = rowprob[g];
+    n = csz[pr];
+    lr = g - cstart[pr];
+    const double *Ar = A + aoff[pr] + (long long)lr * n;
+    const double *xp = x + cstart[pr];
+    for (int j = lane; j < n; j += 32) s = fma(Ar[j], xp[j], s);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if (lane == 0 && g < nrows) y[g] = s;
+}
+
 inline int grid_for(long long n, int threads) {
   long long g = (n + threads - 1) / threads;
   return (int)(g < 1 ? 1 : (g > 1184 ? 1184 : g));
@@ -933,4 +1061,60 @@ cudaError_t launch_update_p(long long n, double *p, const double *z, const doubl
   return cudaGetLastError();
 }
 
+cudaError_t launch_apply_batch(const ApplyDev *descs, const int2 *work, int nwork, int threads,
+                               size_t smem, const double *x, double *y, cudaStream_t s) {
+  cudaError_t err = cudaFuncSetAttribute(apply_cart_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+  if (err != cudaSuccess) return err;
+  apply_cart_batch_kernel<<<nwork, threads, smem, s>>>(descs, work, x, y);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seg_dot(const int4 *chunk, int nchunk, const int *cptr, int nprob, const double *a,
+                           const double *b, double *partial, double *scal, int *done, int *iters,
+                           int slot, int op, double tol2, cudaStream_t s) {
+  seg_dot_kernel<<<nchunk, 256, 0, s>>>(chunk, a, b, partial);
+  seg_finalize_kernel<<<nprob, 128, 0, s>>>(cptr, nchunk, partial, scal, done, iters, slot, op, 0, tol2);
+  g_launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seg_update_xr(const int4 *chunk, int nchunk, const int *cptr, int nprob, double *x,
+                                 double *r, const double *p, const double *q, double *partial,
+                                 double *scal, int *done, int *iters, double tol2, cudaStream_t s) {
+  seg_update_xr_kernel<<<nchunk, 256, 0, s>>>(chunk, x, r, p, q, scal, partial);
+  seg_finalize_kernel<<<nprob, 128, 0, s>>>(cptr, nchunk, partial, scal, done, iters, S_RR, 2, 0, tol2);
+  g_launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seg_dot2(const int4 *chunk, int nchunk, const int *cptr, int nprob, const double *r,
+                            const double *z, const double *q, double *partial, double *scal, int *done,
+                            int *iters, int flexible, cudaStream_t s) {
+  seg_dot2_kernel<<<nchunk, 256, 0, s>>>(chunk, nchunk, r, z, q, partial);
+  seg_finalize_kernel<<<nprob, 128, 0, s>>>(cptr, nchunk, partial, scal, done, iters, S_RZNEW, 3, flexible,
+                                            0.0);
+  g_launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seg_update_p(const int4 *chunk, int nchunk, double *p, const double *z,
+                                const double *scal, cudaStream_t s) {
+  seg_update_p_kernel<<<nchunk, 256, 0, s>>>(chunk, p, z, scal);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemv_batch(int nrows, const int *rowprob, const long long *aoff, const int *cstart,
+                              const int *csz, const double *A, const double *x, double *y,
+                              cudaStream_t s) {
+  const int threads = 256;
+  const int grid = (int)(((long long)nrows * 32 + threads - 1) / threads);
+  gemv_batch_kernel<<<grid, threads, 0, s>>>(nrows, rowprob, aoff, cstart, csz, A, x, y);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
 }  // namespace rmd
+

@@ -26,7 +26,8 @@ STATUS = {0: "RM_OK", 1: "RM_ERR_ARG", 2: "RM_ERR_CUDA", 3: "RM_ERR_OOM",
 
 EXPORTED = ["rm_default_options", "rm_setup", "rm_ndofs", "rm_apply",
             "rm_precondition", "rm_solve", "rm_stats", "rm_destroy", "rm_last_error",
-            "rm_precondition_noalloc"]
+            "rm_precondition_noalloc", "rm_batch_setup", "rm_batch_ndofs", "rm_batch_solve",
+            "rm_batch_destroy", "rm_batch_last_error"]
 RM_NOALLOC_MAX_COARSE = 8192
 
 
@@ -86,6 +87,17 @@ def load():
     lib.rm_destroy.restype = None
     lib.rm_last_error.argtypes = [vp]
     lib.rm_last_error.restype = ctypes.c_char_p
+    lib.rm_batch_setup.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(RmMesh), ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(c_dp), ctypes.POINTER(c_dp),
+                                   ctypes.POINTER(RmOptions), vp]
+    lib.rm_batch_ndofs.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]
+    lib.rm_batch_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                   ctypes.POINTER(RmInfo), vp]
+    lib.rm_batch_destroy.argtypes = [vp]
+    lib.rm_batch_destroy.restype = None
+    lib.rm_batch_last_error.argtypes = [vp]
+    lib.rm_batch_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
@@ -184,6 +196,73 @@ class Solver:
     def close(self):
         if getattr(self, "h", None):
             self.lib.rm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchSolver:
+    """rm_batch_*: independent problems (list of dicts with space, n, p and
+    optional alpha, beta, vertices) solved together with shared options."""
+
+    def __init__(self, problems, **opts):
+        lib = load()
+        nprob = len(problems)
+        self._keep = []
+        space = (ctypes.c_int * nprob)(*[pr["space"] for pr in problems])
+        degs = (ctypes.c_int * nprob)(*[pr["p"] for pr in problems])
+        meshes = (RmMesh * nprob)()
+        c_dp = ctypes.POINTER(ctypes.c_double)
+        al = (c_dp * nprob)()
+        be = (c_dp * nprob)()
+        for i, pr in enumerate(problems):
+            n = pr["n"]
+            n = (n, n, n) if isinstance(n, int) else tuple(n)
+            meshes[i] = RmMesh(n[0], n[1], n[2], None)
+            if pr.get("vertices") is not None:
+                arr, ptr = _dbl_array(pr["vertices"])
+                self._keep.append(arr)
+                meshes[i].vertices = ptr
+            for key, dst in (("alpha", al), ("beta", be)):
+                if pr.get(key) is not None:
+                    arr, ptr = _dbl_array(pr[key])
+                    self._keep.append(arr)
+                    dst[i] = ptr
+        o = options(**opts)
+        h = ctypes.c_void_p()
+        rc = lib.rm_batch_setup(ctypes.byref(h), nprob, space, meshes, degs, al, be,
+                                ctypes.byref(o), None)
+        if rc != 0:
+            raise RmError(rc, lib.rm_batch_last_error(None).decode())
+        self.h, self.lib, self.nprob = h, lib, nprob
+        self.sizes = []
+        for i in range(nprob):
+            v = ctypes.c_longlong()
+            lib.rm_batch_ndofs(h, i, ctypes.byref(v))
+            self.sizes.append(v.value)
+
+    def solve(self, bs, xs, stream=None, check=True):
+        n = self.nprob
+        bp = (ctypes.c_void_p * n)(*[_ptr(b).value for b in bs])
+        xp = (ctypes.c_void_p * n)(*[_ptr(x).value for x in xs])
+        infos = (RmInfo * n)()
+        s = ctypes.c_void_p(0) if stream is None else ctypes.c_void_p(
+            stream if isinstance(stream, int) else stream.cuda_stream)
+        rc = self.lib.rm_batch_solve(self.h, bp, xp, infos, s)
+        if check and rc != 0:
+            raise RmError(rc, self.lib.rm_batch_last_error(self.h).decode())
+        return [{"iterations": i.iterations, "status": STATUS.get(i.status),
+                 "rel_res_l2": i.rel_res_l2, "solve_ms": i.solve_ms,
+                 "kernel_launches": i.kernel_launches, "graph_rounds": i.precond_calls}
+                for i in infos]
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rm_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):
