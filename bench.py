@@ -273,6 +273,9 @@ def run_ours(args):
     if args.batch_count > 0:
         line["variants"]["batched"] = run_batched(args.batch_count, args.steps,
                                                   max(1, args.warmup // 2), stream)
+    if args.learned_epochs > 0:
+        line["variants"]["learned"] = run_learned(args.steps, max(1, args.warmup // 2),
+                                                  args.learned_epochs, args.learned_size, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, budget_s=30.0)
     if rank == 0:
@@ -436,6 +439,67 @@ def run_batched(count, steps, warmup, stream):
                        f"first {len(probs)} problems with n, p <= 8")}
 
 
+def run_learned(steps, warmup, epochs, n, stream):
+    """H(grad) on n^3 (default 32^3) uniform cells, p = 6, lognormal Gaussian-random-field
+    alpha: the learned coarse corrector (trained here on pairs the solver
+    generates) against the plain coarse correction (the V(2,2) cycle) and
+    against no coarse term; SC-PAFW with ICC(0) patches."""
+    import torch
+    from paper_2211_14284_gb300 import inputs
+    from paper_2211_14284_gb300.rm import (RM_CORRECTOR_LEARNED, RM_CORRECTOR_OFF,
+                                           RM_CORRECTOR_PLAIN, Solver)
+    p = 6
+    al = inputs.lognormal_grf_coefficient(n, 1.0, 0.1, seed=5)
+    t0 = time.time()
+    s = Solver(0, n, p, alpha=al, stream=stream, static_condensation=1, factor=1, coarse=2,
+               rtol=1e-8, max_it=1000)
+    setup_s = time.time() - t0
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(20221125)
+    rhs = torch.randn(150, s.size, dtype=torch.float64, device="cuda", generator=gen)
+    train = s.corrector_train(rhs, pairs=2000, epochs=epochs, levels=3, width=16, batch=16,
+                              lr=2e-3)
+    del rhs
+    b = torch.tensor(inputs.normal_rhs(s.size, 77), device="cuda")
+    x = torch.zeros_like(b)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def time_mode(mode, every, jmax, nsteps, nwarm):
+        s.corrector_use(mode, every, jmax)
+        for _ in range(nwarm):
+            x.zero_()
+            s.solve(b, x)
+        torch.cuda.synchronize()
+        tot, info = 0.0, None
+        for _ in range(nsteps):
+            flush.fill_(1.0)
+            x.zero_()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            info = s.solve(b, x)
+            ev1.record(stream)
+            ev1.synchronize()
+            tot += ev0.elapsed_time(ev1)
+            if info["status"] != "RM_OK":
+                raise RuntimeError(f"learned-corrector bench: {info}")
+        ms = tot / nsteps
+        return {"value": s.size / (ms / 1e3), "ms_per_solve": ms, "iterations": info["iterations"],
+                "learned_calls": info["learned_calls"], "judge_calls": info["judge_calls"],
+                "fallback_at": info["fallback_at"], "judge_eta": info["judge_eta"]}
+
+    out = {"workload": f"H(grad), {n}^3 uniform hex, p=6, lognormal GRF alpha (sigma 1, "
+                       "ell 0.1), beta=1, SC-PAFW + ICC, V(2,2) coarse cycle",
+           "lattice_dofs": s.size, "setup_s": setup_s, "train": train,
+           "plain": time_mode(RM_CORRECTOR_PLAIN, 0, 1.0, steps, warmup),
+           "learned": time_mode(RM_CORRECTOR_LEARNED, 4, 0.9, steps, warmup),
+           "learned_unjudged": time_mode(RM_CORRECTOR_LEARNED, 0, 1.0, 1, 0),
+           "off": time_mode(RM_CORRECTOR_OFF, 0, 1.0, 1, 0)}
+    s.corrector_use(RM_CORRECTOR_PLAIN, 0, 1.0)
+    out["value"] = out["learned"]["value"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -445,6 +509,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-count", type=int, default=8,
                     help="problems of the uneven H(curl) batch to time (64 = all; 0 = skip)")
+    ap.add_argument("--learned-size", type=int, default=32,
+                    help="cells per direction of the learned-corrector workload (multiple of 8)")
+    ap.add_argument("--learned-epochs", type=int, default=10,
+                    help="training epochs of the learned coarse corrector (0 = skip that variant)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

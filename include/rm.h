@@ -64,7 +64,7 @@ typedef enum { RM_HGRAD = 0, RM_HCURL = 1, RM_HDIV = 2 } rm_space;
 typedef enum { RM_FP64 = 0, RM_FP32 = 1 } rm_precision;
 typedef enum { RM_PAFW = 0, RM_PH = 1 } rm_decomposition;
 typedef enum { RM_CHOL = 0, RM_ICC = 1 } rm_factor;
-/* RM_COARSE_P1: exact p = 1 coarse solve (dense inverse, <= 8,192 coarse DOFs);
+/* RM_COARSE_P1: exact p = 1 coarse solve (dense inverse, <= 16,384 coarse DOFs);
  * RM_COARSE_GMG: the p = 1 problem approximated by one symmetric V(2,2)
  * geometric multigrid cycle (Galerkin levels, damped Jacobi), as the paper's
  * p-coarse GMG; for coarse spaces too large for the dense inverse. */
@@ -99,6 +99,11 @@ typedef struct {
   double precond_ms;       /* profile = 1: total time of the preconditioner calls */
   int precond_calls;
   long long kernel_launches; /* kernels this library launched during the solve */
+  /* learned coarse corrector (rm_corrector_use mode RM_CORRECTOR_LEARNED) */
+  int learned_calls;       /* preconditioner calls whose coarse term came from the network */
+  int judge_calls;         /* calls on which the plain coarse correction judged it */
+  int fallback_at;         /* call at which the judge rejected it (-1: never) */
+  double judge_eta;        /* last judged relative A_0-energy error (see rm_corrector_use) */
 } rm_info;
 
 typedef struct rm_handle rm_handle;
@@ -191,6 +196,111 @@ const char *rm_batch_last_error(const rm_batch *b);
  * length, not aliased; z is overwritten. */
 #define RM_NOALLOC_MAX_COARSE 8192
 int rm_precondition_noalloc(rm_handle *h, const double *r, double *z);
+
+/* ---- learned coarse corrector (H(grad) only) ---------------------------------
+ * Not in the paper.  A small convolutional network N (a 3D U-Net, BF16
+ * weights and activations, FP32 accumulation; its layers are listed at
+ * rm_net_create) maps the coarse residual r_0 = R_0 r (R_0 the restriction of
+ * the p = 1 coarse correction, Sec. 4.1) and the log-coefficient on the
+ * vertex grid of the coarse space to a coarse correction c_L:
+ *     x = (sqrt(n_0) r_0 / ||r_0||, log alpha - mean) at the grid vertices
+ *     c_L = N(x) at the free vertices,   c = t c_L,   t = (c_L^T r_0) / (c_L^T A_0 c_L)
+ * t is the step that minimises the A_0-energy error of c along c_L, so the
+ * term added to the Schwarz relaxation is R_0^T c in place of R_0^T A_0^-1 r_0.
+ * The plain coarse correction c_P (RM_COARSE_P1 or RM_COARSE_GMG of the
+ * handle) is its judge: on judged calls
+ *     eta^2 = 1 - (c_L^T r_0)^2 / ((c_L^T A_0 c_L)(r_0^T c_P)),
+ * the A_0-energy error of c relative to that of c_P = A_0^-1 r_0, and an eta
+ * above judge_max makes the solve fall back to c_P for the rest of the solve.
+ * The preconditioner is then nonlinear: rm_solve uses flexible CG. */
+typedef struct {
+  int pairs;               /* (residual, error) pairs to collect (default 2000) */
+  int epochs;              /* passes over the training pairs (default 20) */
+  int batch;               /* samples per Adam step (default 16) */
+  float lr;                /* Adam step (default 1e-3; halved at 1/2 and 3/4 of the epochs) */
+  int levels;              /* network levels below the coarse grid (default 3) */
+  int width;               /* channels C_0 of the finest level (default 16) */
+  unsigned long long seed; /* initial weights and sample order */
+  double val_fraction;     /* pairs held out for validation (default 0.1) */
+  int target_cycles;       /* with RM_COARSE_GMG: V-cycles per target (default 12) */
+  double off_fraction;     /* pairs recorded from one-level solves (no coarse term,
+                              64 iterations each), the rest from plain two-level
+                              solves (default 0) */
+} rm_train_options;
+
+typedef struct {
+  int pairs, solves;       /* pairs collected, plain solves run to collect them */
+  long long params;        /* network parameters */
+  double gen_s, train_s;   /* wall time of data generation and of training */
+  double train_loss;       /* mean squared error over the last epoch */
+  double val_loss;         /* mean squared error on the held-out pairs */
+  double val_eta;          /* mean eta (above, with the exact target) on the held-out pairs */
+} rm_train_info;
+
+rm_train_options rm_default_train_options(void);
+
+/* Collects training pairs and trains the handle's corrector on the GPU.
+ * Pairs: the handle's solver is run on the right-hand sides rhs[i * lattice ..]
+ * (device, nrhs vectors in the layout of rm_apply), first without a coarse
+ * term (off_fraction of the pairs), then with the plain coarse correction; at
+ * every preconditioner call r_0 = R_0 r is recorded, until o->pairs are
+ * collected (nrhs too small: RM_ERR_ARG).  Each
+ * pair's target is A_0^-1 r_0 (RM_COARSE_P1: the dense inverse; RM_COARSE_GMG:
+ * target_cycles iterations of the V-cycle).  Inputs and targets are scaled to
+ * sqrt(n_0) / norm.  Training: Adam on the mean squared error over the free
+ * vertices, hand-written forward and backward kernels.  Replaces any previous
+ * network; leaves the corrector mode unchanged.  info may be NULL. */
+int rm_corrector_train(rm_handle *h, const rm_train_options *o, int nrhs, const double *rhs,
+                       rm_train_info *info);
+
+/* Writes / reads the network (magic "RMCORR01", int32 dims[3], levels, width,
+ * in_channels, int64 parameter count, FP32 parameters in the order of
+ * rm_net_get_params).  Loading checks that the grid matches the handle's
+ * coarse space. */
+int rm_corrector_save(const rm_handle *h, const char *path);
+int rm_corrector_load(rm_handle *h, const char *path);
+
+typedef enum {
+  RM_CORRECTOR_PLAIN = 0,   /* the plain coarse correction (default) */
+  RM_CORRECTOR_LEARNED = 1, /* the network, judged by the plain correction */
+  RM_CORRECTOR_OFF = 2      /* no coarse term (one-level relaxation), for comparison */
+} rm_corrector_mode;
+
+/* Selects the coarse term of later rm_precondition / rm_solve calls.
+ * judge_every: judge calls 0, judge_every, 2 judge_every, ... of each solve
+ * (0: never); judge_max: the largest eta accepted.  LEARNED needs a trained
+ * or loaded network. */
+int rm_corrector_use(rm_handle *h, int mode, int judge_every, double judge_max);
+
+/* ---- the corrector's network on its own ----------------------------------------
+ * Layers (levels L, width C, input channels c_in, grid D_0 = dims; level l has
+ * the grid D_l = (D_{l-1} - 1)/2 + 1 and C 2^l channels; every conv 3x3x3
+ * with zero padding, ReLU after all but the last):
+ *   e0a = conv(x), e0 = conv(e0a); for l = 1..L: d_l = conv_stride2(e_{l-1}),
+ *   e_l = conv(d_l); h_L = e_L; for l = L-1..0: u_l = up(h_{l+1}) (vertex-centred
+ *   linear interpolation), a_l = conv(u_l), s_l = a_l + e_l, h_l = conv(s_l);
+ *   y = conv(h_0) (one channel, no ReLU).
+ * A stride-2 conv reads its input at 2 o + tap - 1.  Parameters: per conv in
+ * that order W[c_out][27][c_in] (tap (dz * 3 + dy) * 3 + dx for the offset
+ * (dx-1, dy-1, dz-1)), then b[c_out].  Tensors are channels-last FP32 on the
+ * device, [batch][voxel][channel] with voxel (z * ny + y) * nx + x; the
+ * kernels round activations and weights to BF16 and accumulate in FP32.
+ * Errors: rm_net_last_error() (this thread). */
+typedef struct rm_net rm_net;
+int rm_net_create(rm_net **net, const int dims[3], int levels, int width, int in_channels,
+                  int max_batch, unsigned long long seed, void *stream);
+long long rm_net_num_params(const rm_net *net);
+int rm_net_get_params(const rm_net *net, float *params);  /* host, FP32 master copy */
+int rm_net_set_params(rm_net *net, const float *params);  /* host; resets Adam */
+/* x: device [batch][voxel][in_channels]; y: device [batch][voxel] */
+int rm_net_forward(rm_net *net, int batch, const float *x, float *y);
+/* After rm_net_forward: gradients of sum(dy * y).  grad: device, num_params
+ * (or NULL); dx: device, shaped like x (or NULL). */
+int rm_net_backward(rm_net *net, const float *dy, float *grad, float *dx);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with the last gradients. */
+int rm_net_adam(rm_net *net, float lr);
+void rm_net_destroy(rm_net *net);
+const char *rm_net_last_error(void);
 
 #ifdef __cplusplus
 }

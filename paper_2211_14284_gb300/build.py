@@ -21,7 +21,7 @@ LIB = os.path.join(HERE, "librm.so")
 HOSTLIB = os.path.join(HERE, "librm_host.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 HOST_SOURCES = ["host_basis.cpp", "host_setup.cpp", "host_probe.cpp"]
-DEVICE_SOURCES = ["kernels.cu", "capi.cu", "batch.cu"]
+DEVICE_SOURCES = ["kernels.cu", "capi.cu", "batch.cu", "learned.cu"]
 
 
 def _nvcc():

@@ -697,6 +697,10 @@ int rm_batch_solve(rm_batch *B, const double *const *bvec, double *const *xvec, 
         infos[i].precond_ms = 0.0;
         infos[i].precond_calls = rounds;
         infos[i].kernel_launches = launches;
+        infos[i].learned_calls = 0;
+        infos[i].judge_calls = 0;
+        infos[i].fallback_at = -1;
+        infos[i].judge_eta = -1.0;
       }
     }
   } catch (const std::exception &e) {

@@ -2,6 +2,7 @@
 // device-resident apply / precondition / PCG loop on the handle's stream.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <functional>
 #include <cmath>
@@ -17,6 +18,7 @@
 #include "device.cuh"
 #include "host_basis.h"
 #include "host_setup.h"
+#include "learned.cuh"
 
 using namespace rm;
 using namespace rmd;
@@ -75,6 +77,23 @@ struct rm_handle {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<cudaEvent_t> evpool;  // profile = 1: start/stop pairs
   long long stat_patches = 0, stat_slots = 0, stat_nnz = 0;
+  // learned coarse corrector (k = 0): coarse operator, grid maps, centred
+  // log alpha at the grid vertices, network and its batch-1 buffers
+  DevCsr A0;
+  int cdims[3] = {0, 0, 0};
+  long long cnvox = 0;
+  int *c_free2lat = nullptr, *c_lat2free = nullptr;
+  float *c_logal = nullptr, *cx = nullptr, *cy = nullptr;
+  double *cl = nullptr, *cq = nullptr, *lscal = nullptr, *lpart = nullptr;
+  rmn::Net *net = nullptr;
+  int corr_mode = RM_CORRECTOR_PLAIN, judge_every = 8;
+  double judge_max = 0.9;
+  // per solve: calls, judged calls, fallback call, last eta
+  int lc_calls = 0, lc_judged = 0, lc_fallback = -1;
+  double lc_eta = -1.0;
+  // recording of r_0 = R_0 r for training (device, rec_cap x nc)
+  double *rec = nullptr;
+  int rec_cap = 0, rec_n = 0;
 
   template <typename T>
   T *dalloc(size_t count) {
@@ -97,6 +116,7 @@ struct rm_handle {
     return upload(f);
   }
   ~rm_handle() {
+    if (net) rmn::destroy(net);
     for (void *a : allocs) cudaFree(a);
     if (hscal) cudaFreeHost(hscal);
     if (ev0) cudaEventDestroy(ev0);
@@ -316,6 +336,83 @@ void vcycle(rm_handle *h, int l) {
   CK(launch_jacobi(A, b, t, w, x, s));
 }
 
+// Coarse-grid data of the learned corrector (H(grad)): A_0, the maps between
+// coarse free DOFs and the (n+1)^3 vertex grid, and log alpha at the
+// vertices (mean over the adjacent cells) minus its mean over the grid.
+void corrector_data(rm_handle *h, const CoarseData &cd, const std::vector<double> &alpha) {
+  std::vector<int> rows(cd.nc);
+  for (int i = 0; i < cd.nc; ++i) rows[i] = i;
+  h->A0 = upload_csr(h, cd.A0, nullptr, nullptr, &rows, true);
+  for (int d = 0; d < 3; ++d) h->cdims[d] = h->n[d] + 1;
+  h->cnvox = (long long)h->cdims[0] * h->cdims[1] * h->cdims[2];
+  std::vector<int> l2f(h->cnvox, -1);
+  for (int f = 0; f < cd.nc; ++f) l2f[cd.free2lat[f]] = f;
+  h->c_free2lat = h->upload(cd.free2lat);
+  h->c_lat2free = h->upload(l2f);
+  std::vector<double> s(h->cnvox, 0.0), cnt(h->cnvox, 0.0);
+  for (int e3 = 0; e3 < h->n[2]; ++e3)
+    for (int e2 = 0; e2 < h->n[1]; ++e2)
+      for (int e1 = 0; e1 < h->n[0]; ++e1) {
+        const double la = std::log(alpha[e1 + (size_t)h->n[0] * (e2 + (size_t)h->n[1] * e3)]);
+        for (int c = 0; c < 8; ++c) {
+          const long long v = (e1 + (c & 1)) +
+                              h->cdims[0] * ((e2 + ((c >> 1) & 1)) + (long long)h->cdims[1] * (e3 + (c >> 2)));
+          s[v] += la;
+          cnt[v] += 1.0;
+        }
+      }
+  double mean = 0.0;
+  for (long long v = 0; v < h->cnvox; ++v) mean += (s[v] /= cnt[v]);
+  mean /= (double)h->cnvox;
+  std::vector<float> la(h->cnvox);
+  for (long long v = 0; v < h->cnvox; ++v) la[v] = (float)(s[v] - mean);
+  h->c_logal = h->upload(la);
+  h->cx = h->dalloc<float>(2 * h->cnvox);
+  h->cy = h->dalloc<float>(h->cnvox);
+  h->cl = h->dalloc<double>(h->nc);
+  h->cq = h->dalloc<double>(h->nc);
+  h->lscal = h->dalloc<double>(8);
+  h->lpart = h->dalloc<double>(2 * kDotBlocks);
+}
+
+// ce = A_0^-1 cc (dense inverse) or its V(2,2) approximation
+void plain_coarse(rm_handle *h) {
+  if (h->mg_levels > 0 || h->mgAinv) vcycle(h, 0);
+  else CK(launch_gemv(h->nc, h->A0inv, 0, h->cc, h->ce, h->stream));
+}
+
+// ce = t N(cc) with the A_0-energy optimal step t; on judged calls the plain
+// correction decides whether to keep the network (see rm_corrector_use)
+void learned_coarse(rm_handle *h) {
+  cudaStream_t s = h->stream;
+  const int nc = h->nc;
+  CK(launch_dot(nc, h->cc, h->cc, h->lpart, h->lscal, 0, s));
+  rmn::corr_pack(nc, h->cnvox, h->cc, h->c_lat2free, h->c_logal, h->lscal, h->cx, s);
+  rmn::forward(h->net, 1, h->cx, h->cy);
+  rmn::corr_gather(nc, h->cy, h->c_free2lat, h->cl, s);
+  CK(launch_spmv(h->A0, h->cl, h->cq, nullptr, 0, 1.0, s));
+  CK(launch_dot(nc, h->cl, h->cc, h->lpart, h->lscal, 1, s));
+  CK(launch_dot(nc, h->cl, h->cq, h->lpart, h->lscal, 2, s));
+  const int call = h->lc_calls++;
+  if (h->judge_every > 0 && call % h->judge_every == 0) {
+    plain_coarse(h);
+    CK(launch_dot(nc, h->cc, h->ce, h->lpart, h->lscal, 3, s));
+    double hs[4];
+    CK(cudaMemcpyAsync(hs, h->lscal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double a = hs[1], b = hs[2], e = hs[3];
+    double eta = 1.0;
+    if (b > 0.0 && e > 0.0) eta = std::sqrt(std::min(1.0, std::max(0.0, 1.0 - a * a / (b * e))));
+    h->lc_judged++;
+    h->lc_eta = eta;
+    if (!(eta <= h->judge_max)) {
+      h->lc_fallback = call;  // ce already holds the plain correction
+      return;
+    }
+  }
+  rmn::corr_scale(nc, h->cl, h->lscal, h->ce, s);
+}
+
 // z = B r
 void precondition(rm_handle *h, const double *r, double *z) {
   cudaStream_t s = h->stream;
@@ -334,10 +431,17 @@ void precondition(rm_handle *h, const double *r, double *z) {
   } else {
     for (auto &F : h->fam) CK(launch_patches(F, r, z, s));
   }
-  if (h->nc > 0) {
+  const bool record = h->rec && h->rec_n < h->rec_cap;
+  if (h->nc > 0 && (h->corr_mode != RM_CORRECTOR_OFF || record)) {
     CK(launch_spmv(h->R0, r, h->cc, nullptr, 0, 1.0, s));
-    if (h->mg_levels > 0 || h->mgAinv) vcycle(h, 0);            // cc -> ce by V(2,2)
-    else CK(launch_gemv(h->nc, h->A0inv, 0, h->cc, h->ce, s));
+    if (record) {
+      CK(cudaMemcpyAsync(h->rec + (size_t)h->rec_n * h->nc, h->cc, h->nc * sizeof(double),
+                         cudaMemcpyDeviceToDevice, s));
+      h->rec_n++;
+    }
+    if (h->corr_mode == RM_CORRECTOR_OFF) return;
+    if (h->corr_mode == RM_CORRECTOR_LEARNED && h->net && h->lc_fallback < 0) learned_coarse(h);
+    else plain_coarse(h);                                       // cc -> ce
     CK(launch_spmv(h->R0T, h->ce, z, nullptr, 1, 1.0, s));
   }
 }
@@ -478,6 +582,7 @@ int rm_setup(rm_handle **out, int space, const rm_mesh *mesh, int p, const doubl
       h->A0inv = h->upload(cd.A0inv);
       h->cc = h->dalloc<double>(h->nc);
       h->ce = h->dalloc<double>(h->nc);
+      if (space == RM_HGRAD) corrector_data(h.get(), cd, al);
     } else if (o.coarse == RM_COARSE_GMG) {
       CoarseGMG mg;
       CoarseData cd = build_coarse_gmg(h->L, geo, al.data(), be.data(), mg);
@@ -516,6 +621,7 @@ int rm_setup(rm_handle **out, int space, const rm_mesh *mesh, int p, const doubl
       h->mgAinv = h->upload(mg.Ainv);
       h->cc = h->mgB[0];
       h->ce = h->mgX[0];
+      if (space == RM_HGRAD) corrector_data(h.get(), cd, al);
     }
     h->r = h->dalloc<double>(h->size);
     h->z = h->dalloc<double>(h->size);
@@ -602,6 +708,12 @@ int rm_solve(rm_handle *h, const double *b, double *x, rm_info *info) {
   };
   double tk[2] = {0.0, 0.0};
   const long long launches0 = launch_count();
+  h->lc_calls = 0;
+  h->lc_judged = 0;
+  h->lc_fallback = -1;
+  h->lc_eta = -1.0;
+  // the learned coarse term makes the preconditioner nonlinear: flexible CG
+  const int flexible = h->opt.flexible || (h->corr_mode == RM_CORRECTOR_LEARNED && h->net);
   int nk[2] = {0, 0};
   try {
     CK(cudaEventRecord(h->ev0, s));
@@ -640,7 +752,7 @@ int rm_solve(rm_handle *h, const double *b, double *x, rm_info *info) {
           if (rr <= tol2) { status = RM_OK; break; }
         }
         timed(1, [&] { precondition(h, h->r, h->z); });
-        CK(launch_dot2(n, h->r, h->z, h->qv, h->partial, h->scal, h->opt.flexible, s));
+        CK(launch_dot2(n, h->r, h->z, h->qv, h->partial, h->scal, flexible, s));
         CK(launch_update_p(n, h->pv, h->z, h->scal, s));
       }
       rel = std::sqrt(rr / bb);
@@ -668,6 +780,12 @@ int rm_solve(rm_handle *h, const double *b, double *x, rm_info *info) {
     info->precond_ms = tk[1];
     info->precond_calls = nk[1];
     info->kernel_launches = launch_count() - launches0;
+    const bool learned = h->corr_mode == RM_CORRECTOR_LEARNED && h->net;
+    info->learned_calls =
+        learned ? (h->lc_fallback < 0 ? h->lc_calls : h->lc_fallback) : 0;
+    info->judge_calls = h->lc_judged;
+    info->fallback_at = h->lc_fallback;
+    info->judge_eta = h->lc_eta;
   }
   if (status != RM_OK) {
     const char *why = status == RM_ERR_NOT_CONVERGED ? "max_it reached"
@@ -683,6 +801,313 @@ void rm_destroy(rm_handle *h) { delete h; }
 const char *rm_last_error(const rm_handle *h) {
   if (h) return h->err.c_str();
   return g_last_error.c_str();
+}
+
+// ---------------------------------------------------------------------------
+// learned coarse corrector
+
+// iterations of each one-level solve that supplies training pairs
+static const int kOffSolveIterations = 64;
+
+rm_train_options rm_default_train_options(void) {
+  rm_train_options o;
+  o.pairs = 2000;
+  o.epochs = 20;
+  o.batch = 16;
+  o.lr = 1e-3f;
+  o.levels = 3;
+  o.width = 16;
+  o.seed = 20221125ULL;
+  o.val_fraction = 0.1;
+  o.target_cycles = 12;
+  o.off_fraction = 0.0;
+  return o;
+}
+
+int rm_corrector_train(rm_handle *h, const rm_train_options *opt, int nrhs, const double *rhs,
+                       rm_train_info *info) {
+  if (!h || !rhs || nrhs < 1) return fail(h, RM_ERR_ARG, "rm_corrector_train: bad argument");
+  if (h->k != RM_HGRAD || !h->c_logal)
+    return fail(h, RM_ERR_ARG,
+                "rm_corrector_train: needs an H(grad) handle with RM_COARSE_P1 or RM_COARSE_GMG");
+  const rm_train_options o = opt ? *opt : rm_default_train_options();
+  if (o.pairs < 2 || o.epochs < 1 || o.batch < 1 || o.batch > 256 || !(o.lr > 0.f) ||
+      o.levels < 0 || o.levels > 4 || o.width < 1 || o.width > 128 || !(o.val_fraction >= 0.0) ||
+      o.val_fraction > 0.5 || o.target_cycles < 1 || !(o.off_fraction >= 0.0) ||
+      o.off_fraction > 1.0)
+    return fail(h, RM_ERR_ARG, "rm_corrector_train: option out of range");
+  for (int d = 0; d < 3; ++d)
+    if (h->n[d] % (1 << o.levels) != 0)
+      return fail(h, RM_ERR_ARG, "rm_corrector_train: the mesh size must be divisible by 2^levels");
+  using clock = std::chrono::steady_clock;
+  cudaStream_t s = h->stream;
+  const int nc = h->nc;
+  const long long nv = h->cnvox;
+  const int saved_mode = h->corr_mode;
+  try {
+    const auto t0 = clock::now();
+    // 1. r_0 = R_0 r at every preconditioner call of plain solves
+    DevBuf recb, xb;
+    CK(cudaMalloc(&recb.p, (size_t)o.pairs * nc * sizeof(double)));
+    CK(cudaMalloc(&xb.p, h->size * sizeof(double)));
+    double *rec = (double *)recb.p, *x = (double *)xb.p;
+    h->rec = rec;
+    h->rec_n = 0;
+    int solves = 0;
+    // the first off_fraction of the pairs from one-level solves (no coarse
+    // term: residuals rich in the coarse-scale error the corrector must
+    // remove), the rest from plain two-level solves
+    const int n_off = (int)(o.off_fraction * o.pairs);
+    const int max_it = h->opt.max_it;
+    for (int i = 0; i < nrhs && h->rec_n < o.pairs; ++i) {
+      const bool off = h->rec_n < n_off;
+      h->corr_mode = off ? RM_CORRECTOR_OFF : RM_CORRECTOR_PLAIN;
+      h->rec_cap = off ? n_off : o.pairs;
+      h->opt.max_it = off ? std::min(max_it, kOffSolveIterations) : max_it;
+      CK(cudaMemsetAsync(x, 0, h->size * sizeof(double), s));
+      rm_info inf;
+      const int st = rm_solve(h, rhs + (size_t)i * h->size, x, &inf);
+      h->opt.max_it = max_it;
+      ++solves;
+      if (st != RM_OK && st != RM_ERR_NOT_CONVERGED) throw std::runtime_error(h->err);
+    }
+    h->rec = nullptr;
+    h->rec_cap = 0;
+    h->corr_mode = saved_mode;
+    const int np = h->rec_n;
+    if (np < o.pairs)
+      return fail(h, RM_ERR_ARG,
+                  "rm_corrector_train: " + std::to_string(nrhs) + " right-hand sides gave only " +
+                      std::to_string(np) + " pairs; pass more");
+    // 2. targets c* = A_0^-1 r_0; inputs and targets scaled to sqrt(nc) / norm
+    DevBuf Rb, Tb, cb, db;
+    CK(cudaMalloc(&Rb.p, (size_t)np * nc * sizeof(float)));
+    CK(cudaMalloc(&Tb.p, (size_t)np * nc * sizeof(float)));
+    CK(cudaMalloc(&cb.p, (size_t)nc * sizeof(double)));
+    CK(cudaMalloc(&db.p, (size_t)3 * np * sizeof(double)));
+    float *R = (float *)Rb.p, *T = (float *)Tb.p;
+    double *cs = (double *)cb.p, *dd = (double *)db.p;
+    for (int j = 0; j < np; ++j) {
+      const double *r0 = rec + (size_t)j * nc;
+      if (h->mgAinv) {
+        CK(cudaMemsetAsync(cs, 0, nc * sizeof(double), s));
+        for (int c = 0; c < o.target_cycles; ++c) {
+          CK(launch_spmv(h->A0, cs, h->mgB[0], r0, 2, -1.0, s));  // B = r0 - A0 c
+          vcycle(h, 0);
+          CK(launch_axpy(nc, 1.0, h->mgX[0], cs, 1, s));
+        }
+      } else {
+        CK(launch_gemv(nc, h->A0inv, 0, r0, cs, s));
+      }
+      CK(launch_dot(nc, r0, r0, h->lpart, dd, 3 * j, s));
+      CK(launch_dot(nc, cs, cs, h->lpart, dd, 3 * j + 1, s));
+      CK(launch_dot(nc, r0, cs, h->lpart, dd, 3 * j + 2, s));
+      rmn::corr_normalise(nc, r0, dd + 3 * j, R + (size_t)j * nc, s);
+      rmn::corr_normalise(nc, cs, dd + 3 * j + 1, T + (size_t)j * nc, s);
+    }
+    std::vector<double> hd(3 * (size_t)np);
+    CK(cudaMemcpyAsync(hd.data(), dd, hd.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double gen_s = std::chrono::duration<double>(clock::now() - t0).count();
+    // 3. split (seeded permutation), network, training
+    uint64_t st = o.seed ^ 0x5DEECE66DULL;
+    auto next = [&st]() {
+      uint64_t z = (st += 0x9E3779B97F4A7C15ULL);
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+      return z ^ (z >> 31);
+    };
+    std::vector<int> perm(np);
+    for (int j = 0; j < np; ++j) perm[j] = j;
+    for (int j = np - 1; j > 0; --j) std::swap(perm[j], perm[next() % (uint64_t)(j + 1)]);
+    const int nval = std::min(np - 1, (int)(o.val_fraction * np));
+    const int ntrain = np - nval;
+    if (h->net) {
+      rmn::destroy(h->net);
+      h->net = nullptr;
+    }
+    rmn::NetSpec spec{{h->cdims[0], h->cdims[1], h->cdims[2]}, o.levels, o.width, 2, o.batch};
+    h->net = rmn::create(spec, o.seed, s);
+    DevBuf Xb, Ttb, Yb, dYb, mb, ib, lb;
+    const int B = o.batch;
+    CK(cudaMalloc(&Xb.p, (size_t)B * nv * 2 * sizeof(float)));
+    CK(cudaMalloc(&Ttb.p, (size_t)B * nv * sizeof(float)));
+    CK(cudaMalloc(&Yb.p, (size_t)B * nv * sizeof(float)));
+    CK(cudaMalloc(&dYb.p, (size_t)B * nv * sizeof(float)));
+    CK(cudaMalloc(&mb.p, (size_t)nv));
+    CK(cudaMalloc(&ib.p, (size_t)np * sizeof(int)));
+    CK(cudaMalloc(&lb.p, 2 * sizeof(double)));
+    float *X = (float *)Xb.p, *Tt = (float *)Ttb.p, *Y = (float *)Yb.p, *dY = (float *)dYb.p;
+    uint8_t *mask = (uint8_t *)mb.p;
+    int *idx = (int *)ib.p;
+    double *loss = (double *)lb.p;
+    {
+      std::vector<int> l2f(nv);
+      CK(cudaMemcpy(l2f.data(), h->c_lat2free, nv * sizeof(int), cudaMemcpyDeviceToHost));
+      std::vector<uint8_t> m(nv);
+      for (long long v = 0; v < nv; ++v) m[v] = l2f[v] >= 0;
+      CK(cudaMemcpy(mask, m.data(), nv, cudaMemcpyHostToDevice));
+    }
+    const auto t1 = clock::now();
+    double train_loss = 0.0;
+    for (int e = 0; e < o.epochs; ++e) {
+      for (int j = ntrain - 1; j > 0; --j) std::swap(perm[j], perm[next() % (uint64_t)(j + 1)]);
+      CK(cudaMemcpyAsync(idx, perm.data(), np * sizeof(int), cudaMemcpyHostToDevice, s));
+      float lr = o.lr;
+      if (2 * e >= o.epochs) lr *= 0.5f;
+      if (4 * e >= 3 * o.epochs) lr *= 0.5f;
+      CK(cudaMemsetAsync(loss, 0, sizeof(double), s));
+      int nb = 0;
+      for (int off = 0; off < ntrain; off += B) {
+        const int bs = std::min(B, ntrain - off);
+        rmn::corr_batch(bs, nc, nv, idx + off, R, T, h->c_lat2free, h->c_logal, X, Tt, s);
+        rmn::forward(h->net, bs, X, Y);
+        rmn::mse(bs, (int)nv, Y, Tt, mask, 1.f / ((float)bs * nc), dY, loss, s);
+        rmn::backward(h->net, dY, nullptr);
+        rmn::adam(h->net, lr, 0.9f, 0.999f, 1e-8f);
+        ++nb;
+      }
+      double hl = 0.0;
+      CK(cudaMemcpyAsync(&hl, loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      train_loss = hl / nb;
+    }
+    const double train_s = std::chrono::duration<double>(clock::now() - t1).count();
+    // 4. held-out pairs: loss and eta of the optimally scaled correction
+    double val_loss = 0.0, val_eta = 0.0;
+    if (nval > 0) {
+      DevBuf vb;
+      CK(cudaMalloc(&vb.p, 2 * (size_t)nval * sizeof(double)));
+      double *vd = (double *)vb.p;
+      CK(cudaMemsetAsync(loss, 0, sizeof(double), s));
+      int nb = 0;
+      for (int off = ntrain; off < np; off += B) {
+        const int bs = std::min(B, np - off);
+        rmn::corr_batch(bs, nc, nv, idx + off, R, T, h->c_lat2free, h->c_logal, X, Tt, s);
+        rmn::forward(h->net, bs, X, Y);
+        rmn::mse(bs, (int)nv, Y, Tt, mask, 1.f / ((float)bs * nc), dY, loss, s);
+        for (int b = 0; b < bs; ++b) {
+          const int j = perm[off + b], v = off + b - ntrain;
+          rmn::corr_gather(nc, Y + (size_t)b * nv, h->c_free2lat, h->cl, s);
+          CK(launch_spmv(h->A0, h->cl, h->cq, nullptr, 0, 1.0, s));
+          CK(launch_dot(nc, h->cl, rec + (size_t)j * nc, h->lpart, vd, 2 * v, s));
+          CK(launch_dot(nc, h->cl, h->cq, h->lpart, vd, 2 * v + 1, s));
+        }
+        ++nb;
+      }
+      std::vector<double> hv(2 * (size_t)nval);
+      double hl = 0.0;
+      CK(cudaMemcpyAsync(hv.data(), vd, hv.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(&hl, loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      val_loss = hl / nb;
+      for (int v = 0; v < nval; ++v) {
+        const double a = hv[2 * v], b = hv[2 * v + 1], ee = hd[3 * (size_t)perm[ntrain + v] + 2];
+        double eta = 1.0;
+        if (b > 0.0 && ee > 0.0) eta = std::sqrt(std::min(1.0, std::max(0.0, 1.0 - a * a / (b * ee))));
+        val_eta += eta / nval;
+      }
+    }
+    if (info) {
+      info->pairs = np;
+      info->solves = solves;
+      info->params = rmn::num_params(h->net);
+      info->gen_s = gen_s;
+      info->train_s = train_s;
+      info->train_loss = train_loss;
+      info->val_loss = val_loss;
+      info->val_eta = val_eta;
+    }
+  } catch (const std::exception &e) {
+    h->rec = nullptr;
+    h->rec_cap = 0;
+    h->corr_mode = saved_mode;
+    return fail(h, RM_ERR_CUDA, std::string("rm_corrector_train: ") + e.what());
+  }
+  return RM_OK;
+}
+
+int rm_corrector_save(const rm_handle *h, const char *path) {
+  if (!h || !path || !h->net) return fail(nullptr, RM_ERR_ARG, "rm_corrector_save: no network");
+  try {
+    const rmn::NetSpec &sp = rmn::spec(h->net);
+    const long long np = rmn::num_params(h->net);
+    std::vector<float> w(np);
+    rmn::get_params(h->net, w.data());
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(nullptr, RM_ERR_ARG, std::string("rm_corrector_save: cannot open ") + path);
+    int32_t hdr[6] = {sp.dims[0], sp.dims[1], sp.dims[2], sp.levels, sp.width, sp.in_ch};
+    int64_t n64 = np;
+    bool ok = std::fwrite("RMCORR01", 1, 8, f) == 8 && std::fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+              std::fwrite(&n64, sizeof(n64), 1, f) == 1 &&
+              std::fwrite(w.data(), sizeof(float), np, f) == (size_t)np;
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(nullptr, RM_ERR_ARG, "rm_corrector_save: write failed");
+  } catch (const std::exception &e) {
+    return fail(nullptr, RM_ERR_CUDA, std::string("rm_corrector_save: ") + e.what());
+  }
+  return RM_OK;
+}
+
+int rm_corrector_load(rm_handle *h, const char *path) {
+  if (!h || !path) return fail(h, RM_ERR_ARG, "rm_corrector_load: NULL argument");
+  if (h->k != RM_HGRAD || !h->c_logal)
+    return fail(h, RM_ERR_ARG,
+                "rm_corrector_load: needs an H(grad) handle with RM_COARSE_P1 or RM_COARSE_GMG");
+  FILE *f = std::fopen(path, "rb");
+  if (!f) return fail(h, RM_ERR_ARG, std::string("rm_corrector_load: cannot open ") + path);
+  char magic[8];
+  int32_t hdr[6];
+  int64_t n64 = 0;
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "RMCORR01", 8) == 0 &&
+            std::fread(hdr, sizeof(hdr), 1, f) == 1 && std::fread(&n64, sizeof(n64), 1, f) == 1;
+  if (!ok || hdr[0] != h->cdims[0] || hdr[1] != h->cdims[1] || hdr[2] != h->cdims[2] ||
+      hdr[5] != 2 || n64 <= 0) {
+    std::fclose(f);
+    return fail(h, RM_ERR_ARG,
+                "rm_corrector_load: not a corrector file for this coarse grid (magic, dims or channels)");
+  }
+  try {
+    rmn::NetSpec spec{{hdr[0], hdr[1], hdr[2]}, hdr[3], hdr[4], hdr[5], 1};
+    rmn::Net *net = rmn::create(spec, 0, h->stream);
+    if (rmn::num_params(net) != n64) {
+      rmn::destroy(net);
+      std::fclose(f);
+      return fail(h, RM_ERR_ARG, "rm_corrector_load: parameter count does not match the layers");
+    }
+    std::vector<float> w(n64);
+    const bool rd = std::fread(w.data(), sizeof(float), n64, f) == (size_t)n64;
+    std::fclose(f);
+    f = nullptr;
+    if (!rd) {
+      rmn::destroy(net);
+      return fail(h, RM_ERR_ARG, "rm_corrector_load: truncated file");
+    }
+    rmn::set_params(net, w.data());
+    if (h->net) rmn::destroy(h->net);
+    h->net = net;
+  } catch (const std::exception &e) {
+    if (f) std::fclose(f);
+    return fail(h, RM_ERR_CUDA, std::string("rm_corrector_load: ") + e.what());
+  }
+  return RM_OK;
+}
+
+int rm_corrector_use(rm_handle *h, int mode, int judge_every, double judge_max) {
+  if (!h) return fail(nullptr, RM_ERR_ARG, "rm_corrector_use: NULL handle");
+  if (mode < RM_CORRECTOR_PLAIN || mode > RM_CORRECTOR_OFF || judge_every < 0 || !(judge_max >= 0.0))
+    return fail(h, RM_ERR_ARG, "rm_corrector_use: bad mode, judge_every or judge_max");
+  if (mode == RM_CORRECTOR_LEARNED && !h->net)
+    return fail(h, RM_ERR_ARG, "rm_corrector_use: no network; train or load one first");
+  h->corr_mode = mode;
+  h->judge_every = judge_every;
+  h->judge_max = judge_max;
+  // a new mode starts without a fallback (rm_solve also resets these)
+  h->lc_calls = 0;
+  h->lc_judged = 0;
+  h->lc_fallback = -1;
+  h->lc_eta = -1.0;
+  return RM_OK;
 }
 
 }  // extern "C"
@@ -731,6 +1156,9 @@ extern "C" int rm_precondition_noalloc(rm_handle *h, const double *r, double *z)
     return fail(h, RM_ERR_ARG,
                 "rm_precondition_noalloc: the coarse multigrid cycle needs per-level vectors; "
                 "use rm_precondition");
+  if (h->corr_mode != RM_CORRECTOR_PLAIN)
+    return fail(h, RM_ERR_ARG,
+                "rm_precondition_noalloc: only the plain coarse correction; use rm_precondition");
   if (h->nc > RM_NOALLOC_MAX_COARSE)
     return fail(h, RM_ERR_ARG,
                 "rm_precondition_noalloc: coarse space has " + std::to_string(h->nc) +

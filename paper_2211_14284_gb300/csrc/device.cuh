@@ -60,6 +60,7 @@ struct DevPatch {
 
 // launchers (kernels.cu); launch_count() = kernels launched so far in this process
 long long launch_count();
+void add_launches(long long k);  // for launchers in other files (learned.cu)
 cudaError_t launch_apply(const ApplyDev &A, const double *x, double *y, cudaStream_t s);
 cudaError_t launch_metric(const ApplyDev &A, double *G, cudaStream_t s);
 cudaError_t launch_spmv(const DevCsr &M, const double *x, double *y, const double *u, int mode,

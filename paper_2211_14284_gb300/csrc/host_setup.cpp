@@ -1178,9 +1178,11 @@ CoarseData build_coarse(const Layout &Lf, const Geometry &geo, const double *alp
     throw std::runtime_error("coarse space too large for the dense coarse solve (> 16384 DOFs): "
                              "use RM_COARSE_GMG");
   std::vector<double> A0((size_t)nc * nc, 0.0);
-  for (const Trip &x : coarse_triplets(Lf, Lc, fc, geo, alpha, beta))
-    A0[(size_t)x.r * nc + x.c] += x.v;
+  std::vector<Trip> t = coarse_triplets(Lf, Lc, fc, geo, alpha, beta);
+  for (const Trip &x : t) A0[(size_t)x.r * nc + x.c] += x.v;
   C.A0inv = dense_spd_inverse(A0, nc);
+  C.A0 = csr_from_triplets(nc, nc, t);
+  C.free2lat = fc.free2lat;
   restriction_R0(Lf, Lc, fc, C);
   return C;
 }
@@ -1216,6 +1218,8 @@ CoarseData build_coarse_gmg(const Layout &Lf, const Geometry &geo, const double 
   std::vector<Trip> t = coarse_triplets(Lf, Lc, fc, geo, alpha, beta);
   Csr A = csr_from_triplets(C.nc, C.nc, t);
   restriction_R0(Lf, Lc, fc, C);
+  C.A0 = A;
+  C.free2lat = fc.free2lat;
   mg = CoarseGMG();
   int n[3] = {Lf.n[0], Lf.n[1], Lf.n[2]};
   Layout L = Lc;

@@ -112,6 +112,8 @@ struct CoarseData {
   Csr R0;    // rows: coarse free, cols: fine lattice index
   Csr R0T;   // rows: fine lattice index (only free), cols: coarse free
   std::vector<double> A0inv;
+  Csr A0;                      // the p = 1 operator on the coarse free DOFs
+  std::vector<int> free2lat;   // coarse free index -> coarse lattice index
 };
 CoarseData build_coarse(const Layout &Lf, const Geometry &geo, const double *alpha,
                         const double *beta);

@@ -21,6 +21,7 @@ namespace rmd {
 
 static std::atomic<long long> g_launches{0};
 long long launch_count() { return g_launches.load(); }
+void add_launches(long long k) { g_launches += k; }
 
 namespace {
 

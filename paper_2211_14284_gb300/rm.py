@@ -27,8 +27,13 @@ STATUS = {0: "RM_OK", 1: "RM_ERR_ARG", 2: "RM_ERR_CUDA", 3: "RM_ERR_OOM",
 EXPORTED = ["rm_default_options", "rm_setup", "rm_ndofs", "rm_apply",
             "rm_precondition", "rm_solve", "rm_stats", "rm_destroy", "rm_last_error",
             "rm_precondition_noalloc", "rm_batch_setup", "rm_batch_ndofs", "rm_batch_solve",
-            "rm_batch_destroy", "rm_batch_last_error"]
+            "rm_batch_destroy", "rm_batch_last_error", "rm_default_train_options",
+            "rm_corrector_train", "rm_corrector_save", "rm_corrector_load", "rm_corrector_use",
+            "rm_net_create", "rm_net_num_params", "rm_net_get_params", "rm_net_set_params",
+            "rm_net_forward", "rm_net_backward", "rm_net_adam", "rm_net_destroy",
+            "rm_net_last_error"]
 RM_NOALLOC_MAX_COARSE = 8192
+RM_CORRECTOR_PLAIN, RM_CORRECTOR_LEARNED, RM_CORRECTOR_OFF = 0, 1, 2
 
 
 class RmMesh(ctypes.Structure):
@@ -49,7 +54,23 @@ class RmInfo(ctypes.Structure):
                 ("rel_res_l2", ctypes.c_double), ("solve_ms", ctypes.c_double),
                 ("apply_ms", ctypes.c_double), ("apply_calls", ctypes.c_int),
                 ("precond_ms", ctypes.c_double), ("precond_calls", ctypes.c_int),
-                ("kernel_launches", ctypes.c_longlong)]
+                ("kernel_launches", ctypes.c_longlong),
+                ("learned_calls", ctypes.c_int), ("judge_calls", ctypes.c_int),
+                ("fallback_at", ctypes.c_int), ("judge_eta", ctypes.c_double)]
+
+
+class RmTrainOptions(ctypes.Structure):
+    _fields_ = [("pairs", ctypes.c_int), ("epochs", ctypes.c_int), ("batch", ctypes.c_int),
+                ("lr", ctypes.c_float), ("levels", ctypes.c_int), ("width", ctypes.c_int),
+                ("seed", ctypes.c_ulonglong), ("val_fraction", ctypes.c_double),
+                ("target_cycles", ctypes.c_int), ("off_fraction", ctypes.c_double)]
+
+
+class RmTrainInfo(ctypes.Structure):
+    _fields_ = [("pairs", ctypes.c_int), ("solves", ctypes.c_int), ("params", ctypes.c_longlong),
+                ("gen_s", ctypes.c_double), ("train_s", ctypes.c_double),
+                ("train_loss", ctypes.c_double), ("val_loss", ctypes.c_double),
+                ("val_eta", ctypes.c_double)]
 
 
 class RmError(RuntimeError):
@@ -98,6 +119,24 @@ def load():
     lib.rm_batch_destroy.restype = None
     lib.rm_batch_last_error.argtypes = [vp]
     lib.rm_batch_last_error.restype = ctypes.c_char_p
+    lib.rm_default_train_options.restype = RmTrainOptions
+    lib.rm_corrector_train.argtypes = [vp, ctypes.POINTER(RmTrainOptions), ctypes.c_int, vp,
+                                       ctypes.POINTER(RmTrainInfo)]
+    lib.rm_corrector_save.argtypes = [vp, ctypes.c_char_p]
+    lib.rm_corrector_load.argtypes = [vp, ctypes.c_char_p]
+    lib.rm_corrector_use.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double]
+    lib.rm_net_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                  ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, vp]
+    lib.rm_net_num_params.argtypes = [vp]
+    lib.rm_net_num_params.restype = ctypes.c_longlong
+    lib.rm_net_get_params.argtypes = [vp, vp]
+    lib.rm_net_set_params.argtypes = [vp, vp]
+    lib.rm_net_forward.argtypes = [vp, ctypes.c_int, vp, vp]
+    lib.rm_net_backward.argtypes = [vp, vp, vp, vp]
+    lib.rm_net_adam.argtypes = [vp, ctypes.c_float]
+    lib.rm_net_destroy.argtypes = [vp]
+    lib.rm_net_destroy.restype = None
+    lib.rm_net_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
@@ -186,7 +225,34 @@ class Solver:
                 "rel_res_l2": info.rel_res_l2, "solve_ms": info.solve_ms,
                 "apply_ms": info.apply_ms, "apply_calls": info.apply_calls,
                 "precond_ms": info.precond_ms, "precond_calls": info.precond_calls,
-                "kernel_launches": info.kernel_launches}
+                "kernel_launches": info.kernel_launches, "learned_calls": info.learned_calls,
+                "judge_calls": info.judge_calls, "fallback_at": info.fallback_at,
+                "judge_eta": info.judge_eta}
+
+    def corrector_train(self, rhs, **opts):
+        """rm_corrector_train: rhs is a contiguous float64 CUDA tensor holding
+        nrhs right-hand sides one after another (nrhs x size)."""
+        o = self.lib.rm_default_train_options()
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise KeyError(k)
+            setattr(o, k, v)
+        nrhs = rhs.numel() // self.size
+        info = RmTrainInfo()
+        self._check(self.lib.rm_corrector_train(self.h, ctypes.byref(o), nrhs, _ptr(rhs),
+                                                ctypes.byref(info)))
+        return {f: getattr(info, f) for f, _ in RmTrainInfo._fields_}
+
+    def corrector_save(self, path):
+        rc = self.lib.rm_corrector_save(self.h, os.fsencode(path))
+        if rc != 0:
+            raise RmError(rc, self.lib.rm_last_error(None).decode())
+
+    def corrector_load(self, path):
+        self._check(self.lib.rm_corrector_load(self.h, os.fsencode(path)))
+
+    def corrector_use(self, mode, judge_every=8, judge_max=0.9):
+        self._check(self.lib.rm_corrector_use(self.h, mode, judge_every, judge_max))
 
     def stats(self):
         a, b, c = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
@@ -196,6 +262,61 @@ class Solver:
     def close(self):
         if getattr(self, "h", None):
             self.lib.rm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Net:
+    """rm_net_*: the corrector's network on its own (FP32 tensors on the GPU,
+    channels-last [batch][voxel][channel])."""
+
+    def __init__(self, dims, levels, width, in_channels, max_batch=1, seed=1, stream=None):
+        lib = load()
+        d = (ctypes.c_int * 3)(*dims)
+        s = ctypes.c_void_p(0 if stream is None else stream.cuda_stream)
+        h = ctypes.c_void_p()
+        rc = lib.rm_net_create(ctypes.byref(h), d, levels, width, in_channels, max_batch, seed, s)
+        if rc != 0:
+            raise RmError(rc, lib.rm_net_last_error().decode())
+        self.h, self.lib = h, lib
+        self.dims, self.levels, self.width, self.in_channels = tuple(dims), levels, width, in_channels
+        self.nparams = lib.rm_net_num_params(h)
+
+    def _check(self, rc):
+        if rc != 0:
+            raise RmError(rc, self.lib.rm_net_last_error().decode())
+
+    def get_params(self):
+        import numpy as np
+        w = np.empty(self.nparams, dtype=np.float32)
+        self._check(self.lib.rm_net_get_params(self.h, ctypes.c_void_p(w.ctypes.data)))
+        return w
+
+    def set_params(self, w):
+        import numpy as np
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        assert w.size == self.nparams
+        self._check(self.lib.rm_net_set_params(self.h, ctypes.c_void_p(w.ctypes.data)))
+
+    def forward(self, x, y):
+        self._check(self.lib.rm_net_forward(self.h, x.shape[0], _ptr(x), _ptr(y)))
+
+    def backward(self, dy, grad=None, dx=None):
+        self._check(self.lib.rm_net_backward(self.h, _ptr(dy),
+                                             _ptr(grad) if grad is not None else None,
+                                             _ptr(dx) if dx is not None else None))
+
+    def adam(self, lr):
+        self._check(self.lib.rm_net_adam(self.h, lr))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rm_net_destroy(self.h)
             self.h = None
 
     def __del__(self):
