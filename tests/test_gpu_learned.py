@@ -245,6 +245,25 @@ def test_corrector_save_load_roundtrip(trained):
     assert torch.linalg.norm(x1 - x2) <= 1e-6 * torch.linalg.norm(x1)
 
 
+def test_corrector_rejects_bad_files(trained, tmp_path):
+    from paper_2211_14284_gb300.rm import RmError
+    _, _, path = trained
+    good = open(path, "rb").read()
+    s = _solver()
+    cases = {"magic": b"XXXXXXXX" + good[8:],
+             "truncated": good[:len(good) // 2],
+             "dims": good[:8] + struct.pack("<i", N + 3) + good[12:],
+             "count": good[:32] + struct.pack("<q", 12345) + good[40:]}
+    for name, data in cases.items():
+        p = tmp_path / f"{name}.rmcorr"
+        p.write_bytes(data)
+        with pytest.raises(RmError):
+            s.corrector_load(str(p))
+    with pytest.raises(RmError):
+        s.corrector_load(str(tmp_path / "missing.rmcorr"))
+    s.corrector_load(path)          # the handle is still usable
+
+
 def test_corrector_rejects_bad_use():
     from paper_2211_14284_gb300.rm import RmError, Solver
     s = Solver(1, 2, 2)          # H(curl): no corrector

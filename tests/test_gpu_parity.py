@@ -239,3 +239,22 @@ def test_bad_arguments_are_errors():
         Solver(0, 2, 2, decomposition=1, static_condensation=1)   # PH needs H(curl)
     with pytest.raises(RmError):
         Solver(1, 2, 2, static_condensation=1, factor=1)          # ICC(0) breakdown
+
+
+def test_failures_are_status_codes():
+    """Failures made on the host: a NaN in the right-hand side, max_it."""
+    from paper_2211_14284_gb300.rm import Solver
+    s = Solver(0, 3, 3, rtol=1e-12, max_it=2)
+    b = torch.tensor(inputs.normal_rhs(s.size, 3), device="cuda")
+    x = torch.zeros_like(b)
+    assert s.solve(b, x, check=False)["status"] == "RM_ERR_NOT_CONVERGED"
+    s2 = Solver(0, 3, 3)
+    N = 3 * 3 + 1
+    centre = (N // 2) * (1 + N + N * N)          # an interior (free) lattice entry
+    b[centre] = float("nan")
+    x.zero_()
+    assert s2.solve(b, x, check=False)["status"] == "RM_ERR_NAN"
+    # the handle stays usable
+    b[centre] = 0.0
+    x.zero_()
+    assert s2.solve(b, x)["status"] == "RM_OK"
