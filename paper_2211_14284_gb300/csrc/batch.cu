@@ -440,10 +440,11 @@ int rm_batch_setup(rm_batch **out, int nprob, const int *space, const rm_mesh *m
           A.h = B->upload(P.hcell);
           A.bh_a = P.bh_a;
           A.bh_b = P.bh_b;
+          A.cidx = B->upload(cart_index_table(A.k, P.p));
           descs.push_back(A);
           const int ncell = P.n[0] * P.n[1] * P.n[2];
           for (int c = 0; c < ncell; ++c) work.push_back(make_int2(gi, c));
-          g.smem = ((size_t)P.p * (P.p + 1) + 2 * (size_t)A.nloc0 + 2 * (size_t)A.nloc1) * sizeof(double);
+          g.smem = std::max(g.smem, cart_smem_doubles(A.k, P.p, A.nloc0, A.nloc1) * sizeof(double));
         }
         if (g.smem > 227 * 1024) throw std::invalid_argument("degree too high for the Cartesian apply kernel");
         g.descs = B->upload(descs);

@@ -266,7 +266,8 @@ void build_apply(rm_handle *h, const Geometry &geo, const std::vector<double> &a
       A.h = h->upload(hc);
       A.bh_a = B.Bhat[0];
       A.bh_b = B.Bhat[p];
-      const size_t smem = (size_t)p * (p + 1) + 2 * (size_t)A.nloc0 + 2 * (size_t)A.nloc1;
+      A.cidx = h->upload(cart_index_table(h->k, p));
+      const size_t smem = cart_smem_doubles(h->k, p, A.nloc0, A.nloc1);
       if (smem * sizeof(double) > 227 * 1024)
         throw std::runtime_error("degree too high for the Cartesian apply kernel's shared memory");
       A.G = nullptr;

@@ -1,6 +1,7 @@
 // Device-side data structures shared by the kernels and the C ABI.
 #pragma once
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 namespace rmd {
@@ -28,8 +29,48 @@ struct ApplyDev {
   int cartesian;
   const double *h;
   double bh_a, bh_b;
+  const int *cidx;         // cart_index_table(k, p)
   size_t smem_doubles;
 };
+
+// s-type test of component m of V^kk in direction d (Sec. 2.4): H(grad) all
+// s; NCE component m r-type along m; NCF component m s-type along m only.
+__host__ __device__ constexpr bool styp(int kk, int m, int d) {
+  return kk == 0 ? true : (kk == 3 ? false : (kk == 1 ? d != m : d == m));
+}
+__host__ __device__ constexpr int ncomp(int kk) { return (kk == 0 || kk == 3) ? 1 : 3; }
+
+// Local indices of a Cartesian cell block, packed i0 | i1 << 8 | i2 << 16 |
+// m << 24: the elements of V^k, then those of V^{k+1}, components one
+// after another (each of the same size).  Within a component the elements
+// are grouped by which directions put them on the interface {0, p} of an
+// s-type direction, so the threads of a warp take the same branches.
+inline std::vector<int> cart_index_table(int k, int p) {
+  std::vector<int> t;
+  for (int kk = k; kk <= k + 1; ++kk)
+    for (int m = 0; m < ncomp(kk); ++m) {
+      const int l0 = styp(kk, m, 0) ? p + 1 : p, l1 = styp(kk, m, 1) ? p + 1 : p,
+                l2 = styp(kk, m, 2) ? p + 1 : p;
+      for (int sig = 0; sig < 8; ++sig)
+        for (int i2 = 0; i2 < l2; ++i2)
+          for (int i1 = 0; i1 < l1; ++i1)
+            for (int i0 = 0; i0 < l0; ++i0) {
+              const int ii[3] = {i0, i1, i2};
+              int s = 0;
+              for (int d = 0; d < 3; ++d)
+                if (styp(kk, m, d) && (ii[d] == 0 || ii[d] == p)) s |= 1 << d;
+              if (s == sig) t.push_back(i0 | i1 << 8 | i2 << 16 | m << 24);
+            }
+    }
+  return t;
+}
+
+// Shared memory of the Cartesian apply (doubles): D-hat, x and y on V^k, d
+// and dy on V^{k+1}, and the interface line sums of every D-hat term.
+inline size_t cart_smem_doubles(int k, int p, int nloc0, int nloc1) {
+  return (size_t)p * (p + 1) + 2 * (size_t)nloc0 + 2 * (size_t)nloc1 +
+         (size_t)(k == 1 ? 6 : 3) * 2 * (p + 1) * (p + 1);
+}
 
 // Compressed sparse rows with explicit row ids (lattice or compact).
 struct DevCsr {

@@ -366,165 +366,214 @@ __global__ void __launch_bounds__(kApplyThreads) apply_kernel(ApplyDev P, const 
 // quadrature is needed (~30 flops per DOF).
 
 // Box metric of kk-forms, component m (J = diag(h/2)).
-__device__ __forceinline__ double box_metric(int kk, int m, const double h[3]) {
-  const double det = 0.125 * h[0] * h[1] * h[2];
+__device__ __forceinline__ double box_metric(int kk, int m, double h0, double h1, double h2) {
+  const double det = 0.125 * h0 * h1 * h2;
+  const double hm = m == 0 ? h0 : (m == 1 ? h1 : h2);
   if (kk == 0) return det;
   if (kk == 3) return 1.0 / det;
-  if (kk == 1) return det * 4.0 / (h[m] * h[m]);
-  return 0.25 * h[m] * h[m] / det;
+  if (kk == 1) return det * 4.0 / (hm * hm);
+  return 0.25 * hm * hm / det;
 }
 
-// out (SET) = c (x)_d F_d in, for one component with types t and dims ld.
-__device__ void box_mass(const double *__restrict__ in, double *__restrict__ out, const int *ld,
-                         const char *t, int p, double a, double b, double c) {
-  const int n = ld[0] * ld[1] * ld[2];
-  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-    const int ii[3] = {idx % ld[0], (idx / ld[0]) % ld[1], idx / (ld[0] * ld[1])};
-    int jj[3][2], nj[3];
-    double ww[3][2];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      if (t[d] == 's' && (ii[d] == 0 || ii[d] == p)) {
-        jj[d][0] = 0; ww[d][0] = ii[d] == 0 ? a : b;
-        jj[d][1] = p; ww[d][1] = ii[d] == 0 ? b : a;
-        nj[d] = 2;
-      } else {
-        jj[d][0] = ii[d]; ww[d][0] = 1.0; nj[d] = 1;
-      }
-    }
-    double s = 0.0;
-    for (int c3 = 0; c3 < nj[2]; ++c3)
-      for (int c2 = 0; c2 < nj[1]; ++c2)
-        for (int c1 = 0; c1 < nj[0]; ++c1)
-          s = fma(ww[0][c1] * ww[1][c2] * ww[2][c3],
-                  in[jj[0][c1] + ld[0] * (jj[1][c2] + ld[1] * jj[2][c3])], s);
-    out[idx] = c * s;
-  }
+// (x)_d F_d applied to one component at local index (i0, i1, i2), F_d =
+// B-hat (s-type) or I (r-type): an s-type index on the interface {0, p}
+// couples to itself with weight a and to the opposite interface index p - i
+// with weight b; any other index only to itself.  Evaluated direction by
+// direction, so an interior element costs no FP64 operation and each
+// interface direction one FMA pair (the FP64 pipe is the limit here).
+__device__ __forceinline__ double mass_at(const double *__restrict__ in, bool s0, bool s1, bool s2,
+                                          int i0, int i1, int i2, int l0, int l1, int p, double a,
+                                          double b) {
+  const bool t0 = s0 && (i0 == 0 || i0 == p), t1 = s1 && (i1 == 0 || i1 == p),
+             t2 = s2 && (i2 == 0 || i2 == p);
+  const int o0 = p - i0, o1 = p - i1, o2 = p - i2;
+  auto line = [&](const double *row) { return t0 ? fma(b, row[o0], a * row[i0]) : row[i0]; };
+  auto plane = [&](int j2) {
+    const double *base = in + l0 * l1 * j2;
+    const double v = line(base + l0 * i1);
+    return t1 ? fma(b, line(base + l0 * o1), a * v) : v;
+  };
+  const double v = plane(i2);
+  return t2 ? fma(b, plane(o2), a * v) : v;
 }
 
-// One Cartesian cell c of the problem described by P (shared by the single
-// and the batched kernels; the batched one bakes each problem's offset in
-// the concatenated vectors into P.off).
-__device__ void cart_cell(const ApplyDev &P, const int c, const double *__restrict__ x,
-                          double *__restrict__ y) {
+// One Cartesian cell c of the problem described by P, form degree K (shared
+// by the single and the batched kernels; the batched one bakes each
+// problem's offset in the concatenated vectors into P.off).  Every
+// component of V^kk has the same local size on a cell, so component m of a
+// cell block starts at m * size.  The cell matrix is a Kronecker sum of the
+// 1D FDM factors (Sec. 2.2-2.4): the mass of V^kk is c_m (x)_d F_d per
+// component with the box metric c_m, the derivative term D-hat^T
+// (alpha M^{k+1}) D-hat; a row of D-hat has at most three nonzeros (columns
+// 0, p and its own index).  No quadrature (~30 flops per DOF).
+template <int K>
+__device__ void cart_cell_k(const ApplyDev &P, const int c, const double *__restrict__ x,
+                            double *__restrict__ y) {
+  constexpr int NC0 = ncomp(K), NC1 = ncomp(K + 1);
   extern __shared__ double sm[];
-  const int p = P.p, k = P.k;
-  double *D1 = sm;
-  double *xl = D1 + p * (p + 1);
-  double *yl = xl + P.nloc0;
-  double *dl = yl + P.nloc0;
-  double *dyl = dl + P.nloc1;
+  const int p = P.p, q1 = p + 1;
   const int tid = threadIdx.x, NT = blockDim.x;
-  const int e[3] = {c % P.n[0], (c / P.n[0]) % P.n[1], c / (P.n[0] * P.n[1])};
-  const double h[3] = {P.h[3 * c], P.h[3 * c + 1], P.h[3 * c + 2]};
+  const int n0 = P.n[0], n1 = P.n[1], n2 = P.n[2];
+  const int e0 = c % n0, e1 = (c / n0) % n1, e2 = c / (n0 * n1);
+  const double h0 = P.h[3 * c], h1 = P.h[3 * c + 1], h2 = P.h[3 * c + 2];
   const double al = P.alpha[c], be = P.beta[c];
+  const double ba = P.bh_a, bb = P.bh_b;
+  // coefficient x box metric per component, once per thread (not per element)
+  const double cm00 = be * box_metric(K, 0, h0, h1, h2);
+  const double cm01 = NC0 > 1 ? be * box_metric(K, 1, h0, h1, h2) : 0.0;
+  const double cm02 = NC0 > 1 ? be * box_metric(K, 2, h0, h1, h2) : 0.0;
+  const double cm10 = al * box_metric(K + 1, 0, h0, h1, h2);
+  const double cm11 = NC1 > 1 ? al * box_metric(K + 1, 1, h0, h1, h2) : 0.0;
+  const double cm12 = NC1 > 1 ? al * box_metric(K + 1, 2, h0, h1, h2) : 0.0;
+  // local size of every component of V^K and V^{K+1}
+  constexpr int NS0 = K == 0 ? 3 : (K == 1 ? 2 : 1), NS1 = NS0 - 1;
+  int sz0 = 1, sz1 = 1;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    sz0 *= d < NS0 ? q1 : p;
+    sz1 *= d < NS1 ? q1 : p;
+  }
+  // D-hat terms: (target t, term s) -> line sums of the interface columns
+  constexpr int NTERMS = K == 1 ? 6 : 3;
+  const int lmax = q1 * q1;
+  double *D1 = sm;
+  double *xl = D1 + p * q1;
+  double *yl = xl + NC0 * sz0;
+  double *dl = yl + NC0 * sz0;
+  double *dyl = dl + NC1 * sz1;
+  double *ls = dyl + NC1 * sz1;  // NTERMS x lmax x 2
   {
-    const double *g = P.tabs + P.q * (p + 1) + P.q * p;
-    for (int i = tid; i < p * (p + 1); i += NT) D1[i] = g[i];
+    const double *g = P.tabs + P.q * q1 + P.q * p;
+    for (int i = tid; i < p * q1; i += NT) D1[i] = g[i];
   }
-  for (int l = tid; l < P.nloc0; l += NT) {
-    int m = 0;
-    while (m + 1 < P.nc0 && l >= P.loff0[m + 1]) ++m;
-    int r = l - P.loff0[m];
-    const int i1 = r % P.ld0[m][0];
-    r /= P.ld0[m][0];
-    const int i2 = r % P.ld0[m][1], i3 = r / P.ld0[m][1];
-    const int g[3] = {e[0] * p + i1, e[1] * p + i2, e[2] * p + i3};
-    bool dir = false;
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-      if (P.t0[m][d] == 's' && (g[d] == 0 || g[d] == P.n[d] * p)) dir = true;
-    xl[l] = dir ? 0.0 : x[P.off[m] + g[0] + (long long)P.N[m][0] * (g[1] + (long long)P.N[m][1] * g[2])];
+  const long long off0 = P.off[0], off1 = NC0 > 1 ? P.off[1] : 0, off2 = NC0 > 1 ? P.off[2] : 0;
+  const int *tab0 = P.cidx, *tab1 = P.cidx + NC0 * sz0;
+  // gather (Dirichlet entries read as 0)
+  for (int l = tid; l < NC0 * sz0; l += NT) {
+    const int pk = __ldg(tab0 + l);
+    const int m = pk >> 24, i0 = pk & 255, i1 = (pk >> 8) & 255, i2 = (pk >> 16) & 255;
+    const bool s0 = styp(K, m, 0), s1 = styp(K, m, 1), s2 = styp(K, m, 2);
+    const int l0 = s0 ? q1 : p, l1 = s1 ? q1 : p;
+    const int g0 = e0 * p + i0, g1 = e1 * p + i1, g2 = e2 * p + i2;
+    const bool dir = (s0 && (g0 == 0 || g0 == n0 * p)) || (s1 && (g1 == 0 || g1 == n1 * p)) ||
+                     (s2 && (g2 == 0 || g2 == n2 * p));
+    const long long N0 = (long long)n0 * p + s0, N1 = (long long)n1 * p + s1;
+    const long long off = m == 0 ? off0 : (m == 1 ? off1 : off2);
+    xl[m * sz0 + i0 + l0 * (i1 + l1 * i2)] = dir ? 0.0 : x[off + g0 + N0 * (g1 + N1 * g2)];
   }
   __syncthreads();
-  // y = beta M^k x
-  for (int m = 0; m < P.nc0; ++m)
-    box_mass(xl + P.loff0[m], yl + P.loff0[m], P.ld0[m], P.t0[m], p, P.bh_a, P.bh_b,
-             be * box_metric(k, m, h));
-  // d = D-hat x (target component t, r-type along each term's direction)
-  for (int t = 0; t < P.nc1; ++t) {
-    const int *lt = P.ld1[t];
-    const int n = lt[0] * lt[1] * lt[2];
-    for (int idx = tid; idx < n; idx += NT) {
-      const int jj[3] = {idx % lt[0], (idx / lt[0]) % lt[1], idx / (lt[0] * lt[1])};
-      double s = 0.0;
-      for (int q = 0; q < c_nterms[k][t]; ++q) {
-        const DTerm T = c_terms[k][t][q];
-        const int *ls = P.ld0[T.src];
-        const double *in = xl + P.loff0[T.src];
-        const int j = jj[T.dir];
-        int ii[3] = {jj[0], jj[1], jj[2]};
-        double v = 0.0;
-        ii[T.dir] = 0;
-        v = fma(D1[j * (p + 1)], in[ii[0] + ls[0] * (ii[1] + ls[1] * ii[2])], v);
-        ii[T.dir] = p;
-        v = fma(D1[j * (p + 1) + p], in[ii[0] + ls[0] * (ii[1] + ls[1] * ii[2])], v);
-        if (j >= 1) {
-          ii[T.dir] = j;
-          v = fma(D1[j * (p + 1) + j], in[ii[0] + ls[0] * (ii[1] + ls[1] * ii[2])], v);
-        }
-        s += T.sgn > 0 ? v : -v;
+  // y = beta M^K x;  d = D-hat x (component t of V^{K+1})
+  for (int l = tid; l < NC0 * sz0; l += NT) {
+    const int pk = __ldg(tab0 + l);
+    const int m = pk >> 24, i0 = pk & 255, i1 = (pk >> 8) & 255, i2 = (pk >> 16) & 255;
+    const bool s0 = styp(K, m, 0), s1 = styp(K, m, 1), s2 = styp(K, m, 2);
+    const int l0 = s0 ? q1 : p, l1 = s1 ? q1 : p;
+    yl[m * sz0 + i0 + l0 * (i1 + l1 * i2)] =
+        (m == 0 ? cm00 : (m == 1 ? cm01 : cm02)) *
+        mass_at(xl + m * sz0, s0, s1, s2, i0, i1, i2, l0, l1, p, ba, bb);
+  }
+  for (int l = tid; l < NC1 * sz1; l += NT) {
+    const int pk = __ldg(tab1 + l);
+    const int t = pk >> 24, j0 = pk & 255, j1 = (pk >> 8) & 255, j2 = (pk >> 16) & 255;
+    const bool s0 = styp(K + 1, t, 0), s1 = styp(K + 1, t, 1);
+    const int l0 = s0 ? q1 : p, l1 = s1 ? q1 : p;
+    double sacc = 0.0;
+    for (int s = 0; s < c_nterms[K][t]; ++s) {
+      const int src = c_terms[K][t][s].src, dr = c_terms[K][t][s].dir, sg = c_terms[K][t][s].sgn;
+      // the source component is s-type along dr (p+1 entries) and equal to
+      // the target elsewhere
+      const int sl0 = dr == 0 ? q1 : l0, sl1 = dr == 1 ? q1 : l1;
+      const double *in = xl + src * sz0;
+      const int j = dr == 0 ? j0 : (dr == 1 ? j1 : j2);
+      const int str = dr == 0 ? 1 : (dr == 1 ? sl0 : sl0 * sl1);
+      const int base = (dr == 0 ? 0 : j0) + sl0 * ((dr == 1 ? 0 : j1) + sl1 * (dr == 2 ? 0 : j2));
+      double v = D1[j * q1] * in[base];
+      v = fma(D1[j * q1 + p], in[base + p * str], v);
+      if (j >= 1) v = fma(D1[j * q1 + j], in[base + j * str], v);
+      sacc = sg > 0 ? sacc + v : sacc - v;
+    }
+    dl[t * sz1 + j0 + l0 * (j1 + l1 * j2)] = sacc;
+  }
+  __syncthreads();
+  // dy = alpha M^{K+1} d
+  for (int l = tid; l < NC1 * sz1; l += NT) {
+    const int pk = __ldg(tab1 + l);
+    const int t = pk >> 24, j0 = pk & 255, j1 = (pk >> 8) & 255, j2 = (pk >> 16) & 255;
+    const bool s0 = styp(K + 1, t, 0), s1 = styp(K + 1, t, 1), s2 = styp(K + 1, t, 2);
+    const int l0 = s0 ? q1 : p, l1 = s1 ? q1 : p;
+    dyl[t * sz1 + j0 + l0 * (j1 + l1 * j2)] =
+        (t == 0 ? cm10 : (t == 1 ? cm11 : cm12)) *
+        mass_at(dl + t * sz1, s0, s1, s2, j0, j1, j2, l0, l1, p, ba, bb);
+  }
+  __syncthreads();
+  // line sums of D-hat^T's interface rows: for every term (t, s) and every
+  // line of component t along the term's direction dr,
+  //   ls[0] = sum_j D-hat[j][0] dy[j],  ls[1] = sum_j D-hat[j][p] dy[j]
+  // (one thread per line: the same 2p FMAs in every lane)
+  for (int u = tid; u < NTERMS * lmax; u += NT) {
+    const int ts = u / lmax, line = u - ts * lmax;
+    const int t = K == 1 ? ts >> 1 : (K == 0 ? ts : 0), s = K == 1 ? ts & 1 : (K == 0 ? 0 : ts);
+    const int dr = c_terms[K][t][s].dir;
+    const bool s0 = styp(K + 1, t, 0), s1 = styp(K + 1, t, 1), s2 = styp(K + 1, t, 2);
+    const int l0 = s0 ? q1 : p, l1 = s1 ? q1 : p, l2 = s2 ? q1 : p;
+    const int la = dr == 0 ? l1 : l0, lb = dr == 2 ? l1 : l2;  // the two other dims
+    if (line >= la * lb) continue;
+    const int a = line % la, b = line / la;
+    const int c0 = dr == 0 ? 0 : a, c1 = dr == 0 ? a : (dr == 1 ? 0 : b), c2 = dr == 2 ? 0 : b;
+    const int str = dr == 0 ? 1 : (dr == 1 ? l0 : l0 * l1);
+    const double *in = dyl + t * sz1 + c0 + l0 * (c1 + l1 * c2);
+    double v0 = 0.0, vp = 0.0;
+    for (int j = 0; j < p; ++j) {
+      const double dj = in[j * str];
+      v0 = fma(D1[j * q1], dj, v0);
+      vp = fma(D1[j * q1 + p], dj, vp);
+    }
+    ls[2 * u] = v0;
+    ls[2 * u + 1] = vp;
+  }
+  __syncthreads();
+  // y += D-hat^T dy; scatter-add (Dirichlet rows skipped)
+  for (int l = tid; l < NC0 * sz0; l += NT) {
+    const int pk = __ldg(tab0 + l);
+    const int m = pk >> 24, i0 = pk & 255, i1 = (pk >> 8) & 255, i2 = (pk >> 16) & 255;
+    const bool s0 = styp(K, m, 0), s1 = styp(K, m, 1), s2 = styp(K, m, 2);
+    const int l0 = s0 ? q1 : p, l1 = s1 ? q1 : p;
+    double sacc = yl[m * sz0 + i0 + l0 * (i1 + l1 * i2)];
+#pragma unroll
+    for (int ts = 0; ts < NTERMS; ++ts) {
+      const int t = K == 1 ? ts >> 1 : (K == 0 ? ts : 0), s = K == 1 ? ts & 1 : (K == 0 ? 0 : ts);
+      if (c_terms[K][t][s].src != m) continue;
+      const int dr = c_terms[K][t][s].dir, sg = c_terms[K][t][s].sgn;
+      // the target component is r-type along dr (p entries), equal elsewhere
+      const int tl0 = dr == 0 ? p : l0, tl1 = dr == 1 ? p : l1;
+      const int i = dr == 0 ? i0 : (dr == 1 ? i1 : i2);
+      double v;
+      if (i == 0 || i == p) {
+        const int a = dr == 0 ? i1 : i0, b = dr == 2 ? i1 : i2;
+        const int la = dr == 0 ? tl1 : tl0;
+        v = ls[2 * (ts * lmax + a + la * b) + (i == 0 ? 0 : 1)];
+      } else {
+        const int str = dr == 0 ? 1 : (dr == 1 ? tl0 : tl0 * tl1);
+        const int base = (dr == 0 ? 0 : i0) + tl0 * ((dr == 1 ? 0 : i1) + tl1 * (dr == 2 ? 0 : i2));
+        v = D1[i * q1 + i] * dyl[t * sz1 + base + i * str];
       }
-      dl[P.loff1[t] + idx] = s;
+      sacc = sg > 0 ? sacc + v : sacc - v;
     }
-  }
-  __syncthreads();
-  // dy = alpha M^{k+1} d
-  for (int t = 0; t < P.nc1; ++t)
-    box_mass(dl + P.loff1[t], dyl + P.loff1[t], P.ld1[t], P.t1[t], p, P.bh_a, P.bh_b,
-             al * box_metric(k + 1, t, h));
-  __syncthreads();
-  // y += D-hat^T dy
-  for (int m = 0; m < P.nc0; ++m) {
-    const int *ls = P.ld0[m];
-    const int n = ls[0] * ls[1] * ls[2];
-    for (int idx = tid; idx < n; idx += NT) {
-      const int ii[3] = {idx % ls[0], (idx / ls[0]) % ls[1], idx / (ls[0] * ls[1])};
-      double s = 0.0;
-      for (int t = 0; t < P.nc1; ++t)
-        for (int q = 0; q < c_nterms[k][t]; ++q) {
-          const DTerm T = c_terms[k][t][q];
-          if (T.src != m) continue;
-          const int *lt = P.ld1[t];
-          const double *in = dyl + P.loff1[t];
-          const int i = ii[T.dir];
-          int jj[3] = {ii[0], ii[1], ii[2]};
-          double v = 0.0;
-          if (i == 0 || i == p) {
-            for (int j = 0; j < p; ++j) {
-              jj[T.dir] = j;
-              v = fma(D1[j * (p + 1) + i], in[jj[0] + lt[0] * (jj[1] + lt[1] * jj[2])], v);
-            }
-          } else {
-            jj[T.dir] = i;
-            v = D1[i * (p + 1) + i] * in[jj[0] + lt[0] * (jj[1] + lt[1] * jj[2])];
-          }
-          s += T.sgn > 0 ? v : -v;
-        }
-      yl[P.loff0[m] + idx] += s;
+    const int g0 = e0 * p + i0, g1 = e1 * p + i1, g2 = e2 * p + i2;
+    const bool dir = (s0 && (g0 == 0 || g0 == n0 * p)) || (s1 && (g1 == 0 || g1 == n1 * p)) ||
+                     (s2 && (g2 == 0 || g2 == n2 * p));
+    if (!dir) {
+      const long long N0 = (long long)n0 * p + s0, N1 = (long long)n1 * p + s1;
+      const long long off = m == 0 ? off0 : (m == 1 ? off1 : off2);
+      atomicAdd(&y[off + g0 + N0 * (g1 + N1 * g2)], sacc);
     }
-  }
-  __syncthreads();
-  for (int l = tid; l < P.nloc0; l += NT) {
-    int m = 0;
-    while (m + 1 < P.nc0 && l >= P.loff0[m + 1]) ++m;
-    int r = l - P.loff0[m];
-    const int i1 = r % P.ld0[m][0];
-    r /= P.ld0[m][0];
-    const int i2 = r % P.ld0[m][1], i3 = r / P.ld0[m][1];
-    const int g[3] = {e[0] * p + i1, e[1] * p + i2, e[2] * p + i3};
-    bool dir = false;
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-      if (P.t0[m][d] == 's' && (g[d] == 0 || g[d] == P.n[d] * p)) dir = true;
-    if (!dir)
-      atomicAdd(&y[P.off[m] + g[0] + (long long)P.N[m][0] * (g[1] + (long long)P.N[m][1] * g[2])], yl[l]);
   }
 }
 
+template <int K>
 __global__ void __launch_bounds__(kApplyThreads) apply_cart_kernel(ApplyDev P, const double *__restrict__ x,
                                                                    double *__restrict__ y) {
-  cart_cell(P, blockIdx.x, x, y);
+  cart_cell_k<K>(P, blockIdx.x, x, y);
 }
 
 // Batched: work[b] = (problem, cell); descriptors in global memory.
@@ -536,7 +585,9 @@ __global__ void __launch_bounds__(kApplyThreads) apply_cart_batch_kernel(const A
   const int2 w = work[blockIdx.x];
   if (threadIdx.x == 0) Ps = descs[w.x];
   __syncthreads();
-  cart_cell(Ps, w.y, x, y);
+  if (Ps.k == 0) cart_cell_k<0>(Ps, w.y, x, y);
+  else if (Ps.k == 1) cart_cell_k<1>(Ps, w.y, x, y);
+  else cart_cell_k<2>(Ps, w.y, x, y);
 }
 
 // One damped Jacobi sweep of the coarse multigrid: x_out = x_in + w (b - A x_in),
@@ -904,10 +955,19 @@ cudaError_t launch_metric(const ApplyDev &A, double *G, cudaStream_t s) {
 cudaError_t launch_apply(const ApplyDev &A, const double *x, double *y, cudaStream_t s) {
   const int ncell = A.n[0] * A.n[1] * A.n[2];
   if (A.cartesian) {
-    const size_t smem = ((size_t)A.p * (A.p + 1) + 2 * (size_t)A.nloc0 + 2 * (size_t)A.nloc1) * sizeof(double);
-    cudaError_t err = cudaFuncSetAttribute(apply_cart_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = cart_smem_doubles(A.k, A.p, A.nloc0, A.nloc1) * sizeof(double);
+    cudaError_t err = cudaSuccess;
+    if (A.k == 0) {
+      err = cudaFuncSetAttribute(apply_cart_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (err == cudaSuccess) apply_cart_kernel<0><<<ncell, kApplyThreads, smem, s>>>(A, x, y);
+    } else if (A.k == 1) {
+      err = cudaFuncSetAttribute(apply_cart_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (err == cudaSuccess) apply_cart_kernel<1><<<ncell, kApplyThreads, smem, s>>>(A, x, y);
+    } else {
+      err = cudaFuncSetAttribute(apply_cart_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (err == cudaSuccess) apply_cart_kernel<2><<<ncell, kApplyThreads, smem, s>>>(A, x, y);
+    }
     if (err != cudaSuccess) return err;
-    apply_cart_kernel<<<ncell, kApplyThreads, smem, s>>>(A, x, y);
     g_launches += 1;
     return cudaGetLastError();
   }
