@@ -524,7 +524,7 @@ int rm_batch_setup(rm_batch **out, int nprob, const int *space, const rm_mesh *m
             dst->tmpl.ival.clear();
           }
           for (int s : F.slotmap) dst->slotmap.push_back(s >= 0 ? (int)(s + voff) : -1);
-          const auto &v = F.inverse ? F.ival : F.val;
+          const std::vector<double> v = F.device_values();
           dst->val.insert(dst->val.end(), v.begin(), v.end());
           dst->npatch += F.npatch;
         }

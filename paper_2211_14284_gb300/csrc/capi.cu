@@ -191,9 +191,9 @@ DevPatch upload_family(rm_handle *h, const PatchFamily &F) {
     D.pos_blk = h->upload(F.pos_blk);
     D.bptr = h->upload(F.bptr);
     D.boff = h->upload(F.boff);
-    D.val = h->upload_vals(F.ival);
+    D.val = h->upload_vals(F.device_values());
   } else {
-    D.val = h->upload_vals(F.val);
+    D.val = h->upload_vals(F.device_values());
   }
   h->stat_patches += F.npatch;
   h->stat_slots += (long long)F.npatch * F.nslots;

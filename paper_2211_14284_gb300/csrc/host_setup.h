@@ -98,6 +98,19 @@ struct PatchFamily {
   std::vector<int> boff;              // value offset of block b within a patch
   std::vector<double> ival;           // npatch x boff.back()
   int ivals() const { return boff.empty() ? 0 : boff.back(); }
+  // The values the device kernels read: the block inverses, or the
+  // triangular factor with every diagonal entry replaced by its reciprocal.
+  std::vector<double> device_values() const {
+    if (inverse) return ival;
+    std::vector<double> v = val;
+    const int nz = nnz();
+    for (int pi = 0; pi < npatch; ++pi)
+      for (size_t i = 0; i + 1 < rowptr.size(); ++i) {
+        double &d = v[(size_t)pi * nz + rowptr[i + 1] - 1];
+        d = 1.0 / d;
+      }
+    return v;
+  }
 };
 // span: bit d set = the entity spans direction d (0: vertex, 1 bit: edge, ...)
 // interface_only: slots restricted to interface DOFs (static condensation).

@@ -626,16 +626,18 @@ __global__ void spmv_kernel(int nrows, const int *__restrict__ rid, const int *_
                             const double *x, double *y, const double *u, int mode, double a) {
   // x, y and u may alias (z_I = w_I - E^T z_G reads and writes z on
   // disjoint rows), so they are not declared __restrict__.
+  // Products accumulate in the matrix's precision VT (FP32 data: the
+  // mixed-precision preconditioner; the coarse path is always FP64).
   const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int row = (int)(gt / TPR), lane = (int)(gt % TPR);
-  double s = 0.0;
+  VT s = 0;
   if (row < nrows)
-    for (int e = ptr[row] + lane; e < ptr[row + 1]; e += TPR) s = fma((double)val[e], x[col[e]], s);
+    for (int e = ptr[row] + lane; e < ptr[row + 1]; e += TPR) s = fma(val[e], (VT)x[col[e]], s);
 #pragma unroll
   for (int off = TPR / 2; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off, TPR);
   if (lane == 0 && row < nrows) {
     const int r = rid[row];
-    const double v = a * s;
+    const double v = a * (double)s;
     if (mode == 0) y[r] = v;
     else if (mode == 1) y[r] += v;
     else y[r] = u[r] + v;
@@ -644,17 +646,22 @@ __global__ void spmv_kernel(int nrows, const int *__restrict__ rid, const int *_
 
 // Level-scheduled forward/backward substitution with the template factor.
 // STAGE: the patch's factor values are first copied to shared memory with
-// coalesced loads, so the dependency chain reads only shared memory.
+// coalesced loads, so the dependency chain reads only shared memory.  The
+// arithmetic runs in the factor's precision VT (FP32 for the mixed-precision
+// preconditioner: GB300's FP64 pipe is 1/64 of its FP32 rate), and the
+// factor's diagonal entries are stored as their reciprocals (no division).
 template <typename VT, bool STAGE>
 __global__ void patch_kernel(DevPatch F, const double *__restrict__ r, double *__restrict__ z) {
-  extern __shared__ double xs[];
+  extern __shared__ double smem_raw[];
+  VT *xs = reinterpret_cast<VT *>(smem_raw);
   const int ns = F.nslots;
   const int *sm = F.slotmap + (size_t)blockIdx.x * ns;
   const VT *Lg = reinterpret_cast<const VT *>(F.val) + (size_t)blockIdx.x * F.nnz;
-  VT *Ls = reinterpret_cast<VT *>(xs + ns);
+  // the factor follows x (ns values of VT, padded to whole doubles)
+  VT *Ls = reinterpret_cast<VT *>(smem_raw + (ns * sizeof(VT) + sizeof(double) - 1) / sizeof(double));
   for (int s = threadIdx.x; s < ns; s += blockDim.x) {
     const int g = sm[s];
-    xs[s] = g >= 0 ? r[g] : 0.0;
+    xs[s] = g >= 0 ? (VT)r[g] : (VT)0;
   }
   if (STAGE)
     for (int e = threadIdx.x; e < F.nnz; e += blockDim.x) Ls[e] = Lg[e];
@@ -664,40 +671,41 @@ __global__ void patch_kernel(DevPatch F, const double *__restrict__ r, double *_
     for (int t = F.flev[lv] + threadIdx.x; t < F.flev[lv + 1]; t += blockDim.x) {
       const int i = F.frows[t];
       const int b = F.rowptr[i], d = F.rowptr[i + 1] - 1;
-      double v = xs[i];
-      for (int e = b; e < d; ++e) v = fma(-(double)L[e], xs[F.col[e]], v);
-      xs[i] = v / (double)L[d];
+      VT v = xs[i];
+      for (int e = b; e < d; ++e) v = fma(-L[e], xs[F.col[e]], v);
+      xs[i] = v * L[d];
     }
     __syncthreads();
   }
   for (int lv = 0; lv < F.nblev; ++lv) {
     for (int t = F.blev[lv] + threadIdx.x; t < F.blev[lv + 1]; t += blockDim.x) {
       const int j = F.brows[t];
-      double v = xs[j];
-      for (int e = F.tptr[j]; e < F.tptr[j + 1]; ++e) v = fma(-(double)L[F.tpos[e]], xs[F.trow[e]], v);
-      xs[j] = v / (double)L[F.rowptr[j + 1] - 1];
+      VT v = xs[j];
+      for (int e = F.tptr[j]; e < F.tptr[j + 1]; ++e) v = fma(-L[F.tpos[e]], xs[F.trow[e]], v);
+      xs[j] = v * L[F.rowptr[j + 1] - 1];
     }
     __syncthreads();
   }
   for (int s = threadIdx.x; s < ns; s += blockDim.x) {
     const int g = sm[s];
-    if (g >= 0) atomicAdd(&z[g], xs[s]);
+    if (g >= 0) atomicAdd(&z[g], (double)xs[s]);
   }
 }
 
 // Block-inverse patches: y_block = (A_block)^{-1} x_block for every decoupled
 // block of the patch, one row per thread, the column-major inverse read with
-// coalesced loads; no level chain.
+// coalesced loads; no level chain.  Arithmetic in the data's precision VT.
 template <typename VT>
 __global__ void patch_inv_kernel(DevPatch F, const double *__restrict__ r, double *__restrict__ z) {
-  extern __shared__ double xs[];
+  extern __shared__ double smem_raw[];
+  VT *xs = reinterpret_cast<VT *>(smem_raw);
   const int ns = F.nslots;
-  double *ys = xs + ns;
+  VT *ys = xs + ns;
   const int *sm = F.slotmap + (size_t)blockIdx.x * ns;
   const VT *V = reinterpret_cast<const VT *>(F.val) + (size_t)blockIdx.x * F.ivals;
   for (int s = threadIdx.x; s < ns; s += blockDim.x) {
     const int g = sm[s];
-    xs[s] = g >= 0 ? r[g] : 0.0;
+    xs[s] = g >= 0 ? (VT)r[g] : (VT)0;
   }
   __syncthreads();
   for (int t = threadIdx.x; t < ns; t += blockDim.x) {
@@ -705,14 +713,14 @@ __global__ void patch_inv_kernel(DevPatch F, const double *__restrict__ r, doubl
     const int p0 = F.bptr[b], nb = F.bptr[b + 1] - p0, i = t - p0;
     const VT *Vb = V + F.boff[b] + i;
     const int *ps = F.pos_slot + p0;
-    double acc = 0.0;
-    for (int j = 0; j < nb; ++j) acc = fma((double)Vb[(size_t)j * nb], xs[ps[j]], acc);
+    VT acc = 0;
+    for (int j = 0; j < nb; ++j) acc = fma(Vb[(size_t)j * nb], xs[ps[j]], acc);
     ys[t] = acc;
   }
   __syncthreads();
   for (int t = threadIdx.x; t < ns; t += blockDim.x) {
     const int g = sm[F.pos_slot[t]];
-    if (g >= 0) atomicAdd(&z[g], ys[t]);
+    if (g >= 0) atomicAdd(&z[g], (double)ys[t]);
   }
 }
 
@@ -1008,12 +1016,13 @@ cudaError_t launch_spmv(const DevCsr &M, const double *x, double *y, const doubl
 template <typename VT>
 static void patch_dispatch(const DevPatch &F, const double *r, double *z, cudaStream_t s) {
   if (F.inverse) {
-    const size_t smem = 2 * (size_t)F.nslots * sizeof(double);
+    const size_t smem = 2 * (size_t)F.nslots * sizeof(VT);
     cudaFuncSetAttribute(patch_inv_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     patch_inv_kernel<VT><<<F.npatch, 256, smem, s>>>(F, r, z);
     return;
   }
-  const size_t base = (size_t)F.nslots * sizeof(double);
+  // x in VT, padded to whole doubles so the staged factor stays aligned
+  const size_t base = ((size_t)F.nslots * sizeof(VT) + sizeof(double) - 1) / sizeof(double) * sizeof(double);
   const size_t staged = base + (size_t)F.nnz * sizeof(VT);
   if (staged <= 220 * 1024) {
     cudaFuncSetAttribute(patch_kernel<VT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)staged);
