@@ -215,7 +215,16 @@ void build_apply(rm_handle *h, const Geometry &geo, const std::vector<double> &a
   std::copy(B.D.begin(), B.D.end(), tabs.begin() + q * (p + 1) + q * p);
   std::copy(xq.begin(), xq.end(), tabs.begin() + q * (p + 1) + q * p + p * (p + 1));
   std::copy(wq.begin(), wq.end(), tabs.begin() + q * (p + 1) + q * p + p * (p + 1) + q);
+  // reflection split of both tabulations (appended after wq)
+  std::vector<double> eod;
+  std::vector<int> eoh;
+  if (!eo_tables(tabs.data(), q, p + 1, eod, eoh) ||
+      !eo_tables(tabs.data() + q * (p + 1), q, p, eod, eoh))
+    throw std::runtime_error("1D tabulations lack the reflection symmetry of the GLL points");
+  tabs.insert(tabs.end(), eod.begin(), eod.end());
   ApplyDev &A = h->ad;
+  A.eo_dbls = (int)eod.size();
+  A.eoi = h->upload(eoh);
   Layout L1(k + 1, h->n, p);
   A.k = k;
   A.p = p;
@@ -274,8 +283,8 @@ void build_apply(rm_handle *h, const Geometry &geo, const std::vector<double> &a
       return;
     }
   }
-  A.smem_doubles = 2 * q * (p + 1) + 2 * q * p + 2 * p * (p + 1) + 2 * q + 24 + 2 * A.nloc0 + 2 * A.nloc1 +
-                   3 * q3 + (size_t)q * (p + 1) * (p + 1) + (size_t)q * q * (p + 1);
+  A.smem_doubles = (size_t)A.eo_dbls + kEoHeader + 2 * p * (p + 1) + 2 * q + 24 + 2 * A.nloc0 +
+                   2 * A.nloc1 + 3 * q3 + (size_t)q * (p + 1) * (p + 1) + (size_t)q * q * (p + 1);
   if (A.smem_doubles * sizeof(double) > 227 * 1024)
     throw std::runtime_error("degree too high for the general apply kernel's shared memory (p <= 8)");
   // pullback weights at every quadrature point, computed once on the device

@@ -7,6 +7,9 @@
 namespace rmd {
 
 constexpr int kApplyThreads = 256;
+// general-cell apply: 512 threads, two CTAs (32 warps) per SM to hide the
+// shared-memory latency of the contraction chains
+constexpr int kApplyThreadsGeneral = 512;
 
 // Operator apply (Eq. sum-factorization) on trilinear cells.
 struct ApplyDev {
@@ -21,7 +24,7 @@ struct ApplyDev {
   int nloc0, nloc1;
   const double *X;         // vertices, 3 per vertex
   const double *alpha, *beta;
-  const double *tabs;      // Ts q(p+1) | Tr qp | D1 p(p+1) | xq q | wq q
+  const double *tabs;      // Ts q(p+1) | Tr qp | D1 p(p+1) | xq q | wq q | eo_dbls
   const double *G;         // pullback weights per cell and point (metric_kernel)
   int nA, nAB;             // entries of stage A, of both stages (1 or 6 each)
   // Cartesian fast path (every cell an axis-aligned box): cell sizes
@@ -30,6 +33,10 @@ struct ApplyDev {
   const double *h;
   double bh_a, bh_b;
   const int *cidx;         // cart_index_table(k, p)
+  // reflection-split interpolation tables (general cells): eo_tables() of
+  // the s- and r-tabulations; doubles after wq in tabs, headers in eoi
+  int eo_dbls;
+  const int *eoi;
   size_t smem_doubles;
 };
 
@@ -63,6 +70,76 @@ inline std::vector<int> cart_index_table(int k, int p) {
             }
     }
   return t;
+}
+
+// Reflection split of a 1D tabulation T (q points x n functions, row-major)
+// at the symmetric GLL points x_{q-1-o} = -x_o.  Each function reflects
+// into plus or minus itself or one partner (the interface pair), so
+//   E[o][i] = (T[o][i] + T[q-1-o][i]) / 2   (o < he = ceil(q/2)),
+//   Od[o][i] = (T[o][i] - T[q-1-o][i]) / 2  (o < ho = floor(q/2))
+// vanish for whole columns (odd functions in E, even ones in Od).  Then
+//   T u at o and q-1-o = E u +- Od u       (forward: n + 2 FMAs per pair
+//                                            of points instead of 2n),
+//   T^T w = E^T w+ + Od^T w-,  w+- = w_o +- w_{q-1-o}  (backward).
+// Header per table (kEoHeader ints): n, he, ho, nse, nso, double offset,
+// se[16] (columns with an even part), so[16] (with an odd part), fl[16]
+// (bit 0 even, bit 1 odd).  Doubles: Ec[he][nse], Oc[ho][nso] (compressed
+// columns), ET[n][he], OT[n][ho].
+constexpr int kEoHeader = 6 + 3 * 16;
+inline bool eo_tables(const double *T, int q, int n, std::vector<double> &dbl,
+                      std::vector<int> &hdr) {
+  if (n > 16) return false;
+  double tmax = 0.0;
+  for (int i = 0; i < q * n; ++i) tmax = T[i] > tmax ? T[i] : (-T[i] > tmax ? -T[i] : tmax);
+  const double tol = 1e-10 * tmax;
+  std::vector<int> partner(n, -1), sig(n, 0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n && partner[i] < 0; ++j)
+      for (int sg = 1; sg >= -1 && partner[i] < 0; sg -= 2) {
+        bool ok = true;
+        for (int o = 0; o < q && ok; ++o) {
+          const double d = T[(q - 1 - o) * n + i] - sg * T[o * n + j];
+          ok = (d <= tol && -d <= tol);
+        }
+        if (ok) {
+          partner[i] = j;
+          sig[i] = sg;
+        }
+      }
+  for (int i = 0; i < n; ++i)
+    if (partner[i] < 0) return false;
+  const int he = (q + 1) / 2, ho = q / 2;
+  std::vector<int> se, so, fl(16, 0);
+  for (int i = 0; i < n; ++i) {
+    const bool ev = partner[i] != i || sig[i] > 0, od = partner[i] != i || sig[i] < 0;
+    if (ev) se.push_back(i);
+    if (od) so.push_back(i);
+    fl[i] = (ev ? 1 : 0) | (od ? 2 : 0);
+  }
+  auto E = [&](int o, int i) { return 0.5 * (T[o * n + i] + T[(q - 1 - o) * n + i]); };
+  auto O = [&](int o, int i) { return 0.5 * (T[o * n + i] - T[(q - 1 - o) * n + i]); };
+  const int off = (int)dbl.size();
+  for (int o = 0; o < he; ++o)
+    for (int i : se) dbl.push_back(E(o, i));
+  for (int o = 0; o < ho; ++o)
+    for (int i : so) dbl.push_back(O(o, i));
+  for (int i = 0; i < n; ++i)
+    for (int o = 0; o < he; ++o) dbl.push_back((fl[i] & 1) ? E(o, i) : 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int o = 0; o < ho; ++o) dbl.push_back((fl[i] & 2) ? O(o, i) : 0.0);
+  const size_t h0 = hdr.size();
+  hdr.resize(h0 + kEoHeader, 0);
+  int *hh = hdr.data() + h0;
+  hh[0] = n;
+  hh[1] = he;
+  hh[2] = ho;
+  hh[3] = (int)se.size();
+  hh[4] = (int)so.size();
+  hh[5] = off;
+  for (size_t k = 0; k < se.size(); ++k) hh[6 + k] = se[k];
+  for (size_t k = 0; k < so.size(); ++k) hh[22 + k] = so[k];
+  for (int i = 0; i < 16; ++i) hh[38 + i] = fl[i];
+  return true;
 }
 
 // Shared memory of the Cartesian apply (doubles): D-hat, x and y on V^k, d

@@ -182,6 +182,87 @@ __global__ void metric_kernel(ApplyDev P, double *__restrict__ G) {
 
 // Multiply the reference values at every point by the stored weight:
 // scalar (n = 1) or symmetric 3x3 (n = 6).
+// Reflection-split interpolation (eo_tables in device.cuh): a view of one
+// table in shared memory.
+struct EO {
+  int n, he, ho, nse, nso;
+  const double *Ec, *Oc, *ET, *OT;
+  const int *se, *so, *fl;
+};
+__device__ __forceinline__ EO eo_view(const int *h, const double *base) {
+  EO t;
+  t.n = h[0];
+  t.he = h[1];
+  t.ho = h[2];
+  t.nse = h[3];
+  t.nso = h[4];
+  t.Ec = base + h[5];
+  t.Oc = t.Ec + t.he * t.nse;
+  t.ET = t.Oc + t.ho * t.nso;
+  t.OT = t.ET + t.n * t.he;
+  t.se = h + 6;
+  t.so = h + 22;
+  t.fl = h + 38;
+  return t;
+}
+// out[c][o][a] (op)= sum_i T[o][i] in[c][i][a]  (i < n functions, o < q points):
+// one thread per mirror pair of points, the even and odd halves of T.
+template <int MODE>
+__device__ __forceinline__ void eo_fwd(const double *__restrict__ in, double *__restrict__ out,
+                                       const EO &t, int q, int C, int A) {
+  const int tot = C * t.he * A;
+  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+    const int a = idx % A, o = (idx / A) % t.he, c = idx / (A * t.he);
+    const double *xv = in + (c * t.n) * A + a;
+    const double *er = t.Ec + o * t.nse;
+    double ev = 0.0;
+    for (int k = 0; k < t.nse; ++k) ev = fma(er[k], xv[t.se[k] * A], ev);
+    double *yv = out + (c * q) * A + a;
+    if (o < t.ho) {
+      const double *orow = t.Oc + o * t.nso;
+      double od = 0.0;
+      for (int k = 0; k < t.nso; ++k) od = fma(orow[k], xv[t.so[k] * A], od);
+      put<MODE>(yv[o * A], ev + od);
+      put<MODE>(yv[(q - 1 - o) * A], ev - od);
+    } else {
+      put<MODE>(yv[o * A], ev);  // the middle point of an odd q
+    }
+  }
+}
+// In place along the point index of w[c][o][a]: w_o <- w_o + w_{q-1-o},
+// w_{q-1-o} <- w_o - w_{q-1-o} (o < ho); the middle point stays.
+__device__ __forceinline__ void eo_fold(double *w, const EO &t, int q, int C, int A) {
+  const int tot = C * t.ho * A;
+  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+    const int a = idx % A, o = (idx / A) % t.ho, c = idx / (A * t.ho);
+    double *wv = w + (c * q) * A + a;
+    const double u = wv[o * A], v = wv[(q - 1 - o) * A];
+    wv[o * A] = u + v;
+    wv[(q - 1 - o) * A] = u - v;
+  }
+}
+// out[c][i][a] (op)= sum_o T[o][i] w[c][o][a] for a folded w (eo_fold).
+template <int MODE>
+__device__ __forceinline__ void eo_bwd(const double *__restrict__ w, double *__restrict__ out,
+                                       const EO &t, int q, int C, int A) {
+  const int tot = C * t.n * A;
+  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+    const int a = idx % A, i = (idx / A) % t.n, c = idx / (A * t.n);
+    const double *wv = w + (c * q) * A + a;
+    const int f = t.fl[i];
+    double se = 0.0, so = 0.0;  // two independent chains
+    if (f & 1) {
+      const double *er = t.ET + i * t.he;
+      for (int o = 0; o < t.he; ++o) se = fma(er[o], wv[o * A], se);
+    }
+    if (f & 2) {
+      const double *orow = t.OT + i * t.ho;
+      for (int o = 0; o < t.ho; ++o) so = fma(orow[o], wv[(q - 1 - o) * A], so);
+    }
+    put<MODE>(out[idx], se + so);
+  }
+}
+
 __device__ __forceinline__ void apply_weight(const double *__restrict__ Gc, int n, double *U, int q3) {
   for (int pt = threadIdx.x; pt < q3; pt += blockDim.x) {
     if (n == 1) {
@@ -197,15 +278,13 @@ __device__ __forceinline__ void apply_weight(const double *__restrict__ Gc, int 
   }
 }
 
-__global__ void __launch_bounds__(kApplyThreads) apply_kernel(ApplyDev P, const double *__restrict__ x,
+__global__ void __launch_bounds__(kApplyThreadsGeneral) apply_kernel(ApplyDev P, const double *__restrict__ x,
                                                               double *__restrict__ y) {
   extern __shared__ double sm[];
   const int p = P.p, q = P.q, q3 = q * q * q;
-  double *Ts = sm;
-  double *TsT = Ts + q * (p + 1);
-  double *Tr = TsT + q * (p + 1);
-  double *TrT = Tr + q * p;
-  double *D1 = TrT + q * p;
+  double *EOd = sm;
+  int *EOi = reinterpret_cast<int *>(EOd + P.eo_dbls);
+  double *D1 = EOd + P.eo_dbls + kEoHeader;
   double *D1T = D1 + p * (p + 1);
   double *xq = D1T + p * (p + 1);
   double *wq = xq + q;
@@ -221,17 +300,7 @@ __global__ void __launch_bounds__(kApplyThreads) apply_kernel(ApplyDev P, const 
   const int c = blockIdx.x;
   const int e[3] = {c % P.n[0], (c / P.n[0]) % P.n[1], c / (P.n[0] * P.n[1])};
   {
-    const double *g = P.tabs;
-    for (int i = tid; i < q * (p + 1); i += NT) {
-      Ts[i] = g[i];
-      TsT[(i % (p + 1)) * q + i / (p + 1)] = g[i];
-    }
-    g += q * (p + 1);
-    for (int i = tid; i < q * p; i += NT) {
-      Tr[i] = g[i];
-      TrT[(i % p) * q + i / p] = g[i];
-    }
-    g += q * p;
+    const double *g = P.tabs + q * (p + 1) + q * p;
     for (int i = tid; i < p * (p + 1); i += NT) {
       D1[i] = g[i];
       D1T[(i % (p + 1)) * p + i / (p + 1)] = g[i];
@@ -241,6 +310,9 @@ __global__ void __launch_bounds__(kApplyThreads) apply_kernel(ApplyDev P, const 
       xq[i] = g[i];
       wq[i] = g[q + i];
     }
+    g += 2 * q;
+    for (int i = tid; i < P.eo_dbls; i += NT) EOd[i] = g[i];
+    for (int i = tid; i < 2 * kEoHeader; i += NT) EOi[i] = P.eoi[i];
     if (tid < 24) {
       const int corner = tid / 3, comp = tid % 3;
       const int c1 = corner & 1, c2 = (corner >> 1) & 1, c3 = corner >> 2;
@@ -266,27 +338,36 @@ __global__ void __launch_bounds__(kApplyThreads) apply_kernel(ApplyDev P, const 
     yl[l] = 0.0;
   }
   __syncthreads();
+  const EO Es = eo_view(EOi, EOd), Er = eo_view(EOi + kEoHeader, EOd);
   // ---- stage A: (v, beta u) on V^k ----
   for (int m = 0; m < P.nc0; ++m) {
-    const double *T[3];
-    for (int d = 0; d < 3; ++d) T[d] = P.t0[m][d] == 's' ? Ts : Tr;
-    pass1<SET>(xl + P.loff0[m], SA, T[0], q, P.ld0[m][0], P.ld0[m][1] * P.ld0[m][2]);
+    const int *ld = P.ld0[m];
+    const EO &T0 = P.t0[m][0] == 's' ? Es : Er, &T1 = P.t0[m][1] == 's' ? Es : Er,
+             &T2 = P.t0[m][2] == 's' ? Es : Er;
+    eo_fwd<SET>(xl + P.loff0[m], SA, T0, q, ld[1] * ld[2], 1);
     __syncthreads();
-    pass2<SET>(SA, SB, T[1], q, P.ld0[m][1], q, P.ld0[m][2]);
+    eo_fwd<SET>(SA, SB, T1, q, ld[2], q);
     __syncthreads();
-    pass3<SET>(SB, U + m * q3, T[2], q, P.ld0[m][2], q * q);
+    eo_fwd<SET>(SB, U + m * q3, T2, q, 1, q * q);
     __syncthreads();
   }
   apply_weight(P.G + (size_t)c * P.nAB * q3, P.nA, U, q3);
   __syncthreads();
   for (int m = 0; m < P.nc0; ++m) {
-    const double *T[3];
-    for (int d = 0; d < 3; ++d) T[d] = P.t0[m][d] == 's' ? TsT : TrT;
-    pass3<SET>(U + m * q3, SB, T[2], P.ld0[m][2], q, q * q);
+    const int *ld = P.ld0[m];
+    const EO &T0 = P.t0[m][0] == 's' ? Es : Er, &T1 = P.t0[m][1] == 's' ? Es : Er,
+             &T2 = P.t0[m][2] == 's' ? Es : Er;
+    eo_fold(U + m * q3, T2, q, 1, q * q);
     __syncthreads();
-    pass2<SET>(SB, SA, T[1], P.ld0[m][1], q, q, P.ld0[m][2]);
+    eo_bwd<SET>(U + m * q3, SB, T2, q, 1, q * q);
     __syncthreads();
-    pass1<ADD>(SA, yl + P.loff0[m], T[0], P.ld0[m][0], q, P.ld0[m][1] * P.ld0[m][2]);
+    eo_fold(SB, T1, q, ld[2], q);
+    __syncthreads();
+    eo_bwd<SET>(SB, SA, T1, q, ld[2], q);
+    __syncthreads();
+    eo_fold(SA, T0, q, ld[1] * ld[2], 1);
+    __syncthreads();
+    eo_bwd<ADD>(SA, yl + P.loff0[m], T0, q, ld[1] * ld[2], 1);
     __syncthreads();
   }
   // ---- stage B: (d v, alpha d u) on V^{k+1}, d = D-hat ----
@@ -305,25 +386,33 @@ __global__ void __launch_bounds__(kApplyThreads) apply_kernel(ApplyDev P, const 
     }
   }
   for (int t = 0; t < P.nc1; ++t) {
-    const double *T[3];
-    for (int d = 0; d < 3; ++d) T[d] = P.t1[t][d] == 's' ? Ts : Tr;
-    pass1<SET>(dl + P.loff1[t], SA, T[0], q, P.ld1[t][0], P.ld1[t][1] * P.ld1[t][2]);
+    const int *ld = P.ld1[t];
+    const EO &T0 = P.t1[t][0] == 's' ? Es : Er, &T1 = P.t1[t][1] == 's' ? Es : Er,
+             &T2 = P.t1[t][2] == 's' ? Es : Er;
+    eo_fwd<SET>(dl + P.loff1[t], SA, T0, q, ld[1] * ld[2], 1);
     __syncthreads();
-    pass2<SET>(SA, SB, T[1], q, P.ld1[t][1], q, P.ld1[t][2]);
+    eo_fwd<SET>(SA, SB, T1, q, ld[2], q);
     __syncthreads();
-    pass3<SET>(SB, U + t * q3, T[2], q, P.ld1[t][2], q * q);
+    eo_fwd<SET>(SB, U + t * q3, T2, q, 1, q * q);
     __syncthreads();
   }
   apply_weight(P.G + ((size_t)c * P.nAB + P.nA) * q3, P.nAB - P.nA, U, q3);
   __syncthreads();
   for (int t = 0; t < P.nc1; ++t) {
-    const double *T[3];
-    for (int d = 0; d < 3; ++d) T[d] = P.t1[t][d] == 's' ? TsT : TrT;
-    pass3<SET>(U + t * q3, SB, T[2], P.ld1[t][2], q, q * q);
+    const int *ld = P.ld1[t];
+    const EO &T0 = P.t1[t][0] == 's' ? Es : Er, &T1 = P.t1[t][1] == 's' ? Es : Er,
+             &T2 = P.t1[t][2] == 's' ? Es : Er;
+    eo_fold(U + t * q3, T2, q, 1, q * q);
     __syncthreads();
-    pass2<SET>(SB, SA, T[1], P.ld1[t][1], q, q, P.ld1[t][2]);
+    eo_bwd<SET>(U + t * q3, SB, T2, q, 1, q * q);
     __syncthreads();
-    pass1<SET>(SA, dyl + P.loff1[t], T[0], P.ld1[t][0], q, P.ld1[t][1] * P.ld1[t][2]);
+    eo_fold(SB, T1, q, ld[2], q);
+    __syncthreads();
+    eo_bwd<SET>(SB, SA, T1, q, ld[2], q);
+    __syncthreads();
+    eo_fold(SA, T0, q, ld[1] * ld[2], 1);
+    __syncthreads();
+    eo_bwd<SET>(SA, dyl + P.loff1[t], T0, q, ld[1] * ld[2], 1);
     __syncthreads();
   }
   for (int t = 0; t < P.nc1; ++t) {
@@ -982,7 +1071,7 @@ cudaError_t launch_apply(const ApplyDev &A, const double *x, double *y, cudaStre
   const size_t smem = A.smem_doubles * sizeof(double);
   cudaError_t err = cudaFuncSetAttribute(apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  apply_kernel<<<ncell, kApplyThreads, smem, s>>>(A, x, y);
+  apply_kernel<<<ncell, kApplyThreadsGeneral, smem, s>>>(A, x, y);
   g_launches += 1;
   return cudaGetLastError();
 }
