@@ -167,84 +167,329 @@ __global__ void conv_finish_kernel(long long n, int cout, int splits, const floa
   put(out + i, v);
 }
 
-// Weight and bias gradients of a forward conv:
-//   dW[c_out][tap][c_in] += sum_{b, o} g[b, o, c_out] x[b, stride o + tap - 1, c_in],
-//   db[c_out] += sum_{b, o} g[b, o, c_out].
-// Block = 16 x 16 (c_in, c_out) pairs with 27 accumulators each, over a
-// chunk of output voxels staged 16 at a time in shared memory; the partial
-// sums of the chunks meet in FP32 atomics.
+// Tensor-core form of the same convolution (output channels >= 16): an
+// implicit GEMM out[v][c_out] = sum_k A[v][k] W[c_out][k] with k = tap * c_in
+// + c_in index (K = 27 c_in), A the gathered input (im2col, built in shared
+// memory per chunk of 32 k, BF16) and mma.sync m16n8k16 BF16 -> FP32.  CTA
+// tile: 128 voxels (4 warps x 32) x BN output channels; blockIdx.z takes the
+// K chunks [z * per, (z + 1) * per) (split reduction for small grids, as in
+// conv_kernel).  Shared rows are padded to 40 BF16 (80 B) so the fragment
+// reads of the 8 row groups fall in distinct banks.
+constexpr int kMmaBM = 128, kMmaKC = 32, kMmaLd = 40;
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const uint32_t l = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
+  const uint32_t h = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
+  return l | (h << 16);
+}
+__device__ __forceinline__ float tof_any(bf16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float tof_any(float v) { return v; }
+
+template <typename TI, typename TO, int BN>
+__global__ void __launch_bounds__(128) conv_mma_kernel(ConvArgs a, long long total, int per,
+                                                       const TI *__restrict__ in,
+                                                       const bf16 *__restrict__ W,
+                                                       const float *__restrict__ bias,
+                                                       TO *__restrict__ out, float *__restrict__ part) {
+  __shared__ __align__(16) bf16 As[kMmaBM * kMmaLd];
+  __shared__ __align__(16) bf16 Bs[BN * kMmaLd];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = lane >> 2, t4 = lane & 3;
+  const long long v0 = (long long)blockIdx.x * kMmaBM;
+  const int n0 = blockIdx.y * BN;
+  const int K = 27 * a.cin;
+  const int nkc = (K + kMmaKC - 1) / kMmaKC;
+  const int kc1 = min(nkc, (int)(blockIdx.z + 1) * per);
+  const int nvo = a.dout[0] * a.dout[1] * a.dout[2];
+  const long long nvi = (long long)a.din[0] * a.din[1] * a.din[2];
+  // the voxel this thread stages (one row of A per thread)
+  const long long gv = v0 + tid;
+  const bool live = gv < total;
+  const long long b = live ? gv / nvo : 0;
+  const int vo = live ? (int)(gv - b * nvo) : 0;
+  const int ox = vo % a.dout[0], oy = (vo / a.dout[0]) % a.dout[1], oz = vo / (a.dout[0] * a.dout[1]);
+  const TI *base = in + b * nvi * a.cin;
+  // 16-byte staging only where every piece is aligned: c_in a multiple of 8
+  // (8 consecutive k in one tap) and 16-byte aligned tensors
+  const bool avec = a.cin % 8 == 0 && (reinterpret_cast<uintptr_t>(in) & 15) == 0;
+  const bool bvec = !a.transposed && a.w_si == 1 && a.cin % 8 == 0 && a.w_so % 8 == 0 &&
+                    (reinterpret_cast<uintptr_t>(W) & 15) == 0;
+  float acc[2][BN / 8][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < BN / 8; ++nt)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[mt][nt][r] = 0.f;
+  for (int kc = blockIdx.z * per; kc < kc1; ++kc) {
+    const int k0 = kc * kMmaKC;
+    __syncthreads();
+    // A: row tid, k0 .. k0 + 31 (zero outside the input, beyond K or the voxels)
+    if (avec) {
+      // 8 consecutive k share a tap: one source voxel, one 16-byte row piece
+      bf16 *row = As + tid * kMmaLd;
+#pragma unroll
+      for (int gq = 0; gq < kMmaKC / 8; ++gq) {
+        const int k = k0 + 8 * gq;
+        uint4 pk = make_uint4(0u, 0u, 0u, 0u);
+        if (live && k < K) {
+          const int tap = k / a.cin, ci = k - tap * a.cin;
+          const int ix = tap_src(ox, tap % 3, a.stride, a.din[0], a.transposed);
+          const int iy = tap_src(oy, (tap / 3) % 3, a.stride, a.din[1], a.transposed);
+          const int iz = tap_src(oz, tap / 9, a.stride, a.din[2], a.transposed);
+          if (ix >= 0 && iy >= 0 && iz >= 0) {
+            const TI *src = base + ((long long)(iz * a.din[1] + iy) * a.din[0] + ix) * a.cin + ci;
+            if constexpr (sizeof(TI) == 2) {
+              pk = *reinterpret_cast<const uint4 *>(src);
+            } else {
+              const float4 f0 = *reinterpret_cast<const float4 *>(src);
+              const float4 f1 = *reinterpret_cast<const float4 *>(src + 4);
+              pk = make_uint4(pack_bf16(f0.x, f0.y), pack_bf16(f0.z, f0.w), pack_bf16(f1.x, f1.y),
+                              pack_bf16(f1.z, f1.w));
+            }
+          }
+        }
+        *reinterpret_cast<uint4 *>(row + 8 * gq) = pk;
+      }
+    } else {
+      bf16 *row = As + tid * kMmaLd;
+#pragma unroll 4
+      for (int kk = 0; kk < kMmaKC; kk += 2) {
+        float x0 = 0.f, x1 = 0.f;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int k = k0 + kk + h;
+          float xv = 0.f;
+          if (live && k < K) {
+            const int tap = k / a.cin, ci = k - tap * a.cin;
+            const int ix = tap_src(ox, tap % 3, a.stride, a.din[0], a.transposed);
+            const int iy = tap_src(oy, (tap / 3) % 3, a.stride, a.din[1], a.transposed);
+            const int iz = tap_src(oz, tap / 9, a.stride, a.din[2], a.transposed);
+            if (ix >= 0 && iy >= 0 && iz >= 0)
+              xv = tof_any(base[((long long)(iz * a.din[1] + iy) * a.din[0] + ix) * a.cin + ci]);
+          }
+          if (h == 0) x0 = xv; else x1 = xv;
+        }
+        *reinterpret_cast<uint32_t *>(row + kk) = pack_bf16(x0, x1);
+      }
+    }
+    // B: BN rows (output channels) x 32 k; forward weights are contiguous in k
+    if (bvec) {
+      for (int e = tid; e < BN * (kMmaKC / 8); e += 128) {
+        const int n = e / (kMmaKC / 8), gq = e - n * (kMmaKC / 8), k = k0 + 8 * gq, co = n0 + n;
+        uint4 pk = make_uint4(0u, 0u, 0u, 0u);
+        if (co < a.cout && k < K)
+          pk = *reinterpret_cast<const uint4 *>(W + (long long)co * a.w_so + k);
+        *reinterpret_cast<uint4 *>(Bs + n * kMmaLd + 8 * gq) = pk;
+      }
+    } else
+    for (int e = tid; e < BN * kMmaKC; e += 128) {
+      const int n = e / kMmaKC, kk = e - n * kMmaKC, k = k0 + kk, co = n0 + n;
+      bf16 w = __float2bfloat16_rn(0.f);
+      if (co < a.cout && k < K) {
+        const int tap = k / a.cin, ci = k - tap * a.cin;
+        w = W[(long long)co * a.w_so + (long long)tap * a.w_sd + (long long)ci * a.w_si];
+      }
+      Bs[n * kMmaLd + kk] = w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < kMmaKC; ks += 16) {
+      uint32_t af[2][4];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        const bf16 *r0 = As + (warp * 32 + mt * 16 + g) * kMmaLd + ks + 2 * t4;
+        const bf16 *r8 = r0 + 8 * kMmaLd;
+        af[mt][0] = *reinterpret_cast<const uint32_t *>(r0);
+        af[mt][1] = *reinterpret_cast<const uint32_t *>(r8);
+        af[mt][2] = *reinterpret_cast<const uint32_t *>(r0 + 8);
+        af[mt][3] = *reinterpret_cast<const uint32_t *>(r8 + 8);
+      }
+#pragma unroll
+      for (int nt = 0; nt < BN / 8; ++nt) {
+        const bf16 *bp = Bs + (nt * 8 + g) * kMmaLd + ks + 2 * t4;
+        const uint32_t b0 = *reinterpret_cast<const uint32_t *>(bp);
+        const uint32_t b1 = *reinterpret_cast<const uint32_t *>(bp + 8);
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          float *c = acc[mt][nt];
+          asm volatile(
+              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+              "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
+              : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+              : "r"(af[mt][0]), "r"(af[mt][1]), "r"(af[mt][2]), "r"(af[mt][3]), "r"(b0), "r"(b1));
+        }
+      }
+    }
+  }
+  // epilogue: rows warp * 32 + mt * 16 + g (+8), columns nt * 8 + 2 t4 (+1)
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int hr = 0; hr < 2; ++hr) {
+      const long long vr = v0 + warp * 32 + mt * 16 + g + 8 * hr;
+      if (vr >= total) continue;
+#pragma unroll
+      for (int nt = 0; nt < BN / 8; ++nt)
+#pragma unroll
+        for (int hc = 0; hc < 2; ++hc) {
+          const int co = n0 + nt * 8 + 2 * t4 + hc;
+          if (co >= a.cout) continue;
+          const float v = acc[mt][nt][2 * hr + hc];
+          if (gridDim.z > 1) {
+            part[(long long)blockIdx.z * total * a.cout + vr * a.cout + co] = v;
+          } else {
+            float y = v + (bias ? bias[co] : 0.f);
+            if (a.relu) y = fmaxf(y, 0.f);
+            TO *dst = out + vr * a.cout + co;
+            if (a.accumulate) y += tof(*dst);
+            put(dst, y);
+          }
+        }
+    }
+}
+
+// Arguments of the weight gradient of a forward conv (wgrad_mma_kernel).
 struct WgArgs {
   int ci, co;
   int din[3], dout[3];
   int stride;
 };
 
-__global__ void __launch_bounds__(256) wgrad_kernel(WgArgs a, long long total, long long chunk,
-                                                    const float *__restrict__ g,
-                                                    const bf16 *__restrict__ x,
-                                                    float *__restrict__ dW, float *__restrict__ db) {
-  __shared__ float gs[16][16];
-  __shared__ float xs[16][27][16];
-  __shared__ long long vb_base[16];
-  __shared__ int vb_c[16][3];
-  const int ti = threadIdx.x & 15, to = threadIdx.x >> 4;
-  const int nti = (a.ci + 15) / 16;
-  const int i0 = (blockIdx.y % nti) * 16, o0 = (blockIdx.y / nti) * 16;
+// Tensor-core weight gradient: dW[c_out][k] += sum_v g[v][c_out] A[v][k] with
+// A the forward im2col (k = tap * c_in + c_in index), a GEMM with the voxels
+// as its reduction: mma.sync m16n8k16 BF16 -> FP32 on a 64 (c_out) x 64 (k)
+// tile per CTA (2 x 2 warps of 32 x 32), 32 voxels per step, a range of
+// voxels per CTA, FP32 atomics into dW at the end.  g is staged transposed
+// ([c_out][v]) and A as [k][v] (both with 40-element rows).
+constexpr int kWgTile = 64, kWgV = 32;
+
+__global__ void __launch_bounds__(128) wgrad_mma_kernel(WgArgs a, long long total, long long chunk,
+                                                        const float *__restrict__ g,
+                                                        const bf16 *__restrict__ x,
+                                                        float *__restrict__ dW) {
+  __shared__ __align__(16) bf16 Gs[kWgTile * kMmaLd];
+  __shared__ __align__(16) bf16 Xs[kWgTile * kMmaLd];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int gq = lane >> 2, t4 = lane & 3;
+  const int wm = warp >> 1, wn = warp & 1;
+  const int K = 27 * a.ci;
+  const int k0 = blockIdx.y * kWgTile, c0 = blockIdx.z * kWgTile;
   const int nvo = a.dout[0] * a.dout[1] * a.dout[2];
   const long long nvi = (long long)a.din[0] * a.din[1] * a.din[2];
-  float acc[27];
+  const bool xvec = a.ci % 8 == 0 && (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+  float acc[2][4][4];
 #pragma unroll
-  for (int d = 0; d < 27; ++d) acc[d] = 0.f;
-  float accb = 0.f;
-  const long long v0 = (long long)blockIdx.x * chunk;
-  const long long v1 = min(total, v0 + chunk);
-  for (long long vb = v0; vb < v1; vb += 16) {
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[mt][nt][r] = 0.f;
+  const long long va = (long long)blockIdx.x * chunk, vb = min(total, va + chunk);
+  for (long long v0 = va; v0 < vb; v0 += kWgV) {
     __syncthreads();
-    if (threadIdx.x < 16) {
-      const long long gv = vb + threadIdx.x;
-      long long bb = 0;
-      int vo = 0;
-      if (gv < v1) {
-        bb = gv / nvo;
-        vo = (int)(gv - bb * nvo);
-      }
-      vb_base[threadIdx.x] = gv < v1 ? bb * nvi : -1;
-      vb_c[threadIdx.x][0] = a.stride * (vo % a.dout[0]) - 1;
-      vb_c[threadIdx.x][1] = a.stride * ((vo / a.dout[0]) % a.dout[1]) - 1;
-      vb_c[threadIdx.x][2] = a.stride * (vo / (a.dout[0] * a.dout[1])) - 1;
-    }
-    {
-      const int v = threadIdx.x >> 4, o = threadIdx.x & 15;
-      const long long gv = vb + v;
-      gs[v][o] = (gv < v1 && o0 + o < a.co) ? g[gv * a.co + o0 + o] : 0.f;
-    }
-    __syncthreads();
-    for (int dv = to; dv < 16 * 27; dv += 16) {
-      const int v = dv / 27, d = dv - 27 * (dv / 27);
+    // G^T: [c_out][v], zero beyond c_out or the voxel range
+    for (int e = tid; e < kWgTile * kWgV; e += 128) {
+      const int co = e % kWgTile, v = e / kWgTile;
+      const long long gv = v0 + v;
       float val = 0.f;
-      const long long bbase = vb_base[v];
-      if (bbase >= 0 && i0 + ti < a.ci) {
-        const int ix = vb_c[v][0] + d % 3, iy = vb_c[v][1] + (d / 3) % 3, iz = vb_c[v][2] + d / 9;
-        if (ix >= 0 && ix < a.din[0] && iy >= 0 && iy < a.din[1] && iz >= 0 && iz < a.din[2])
-          val = __bfloat162float(
-              x[(bbase + ((long long)iz * a.din[1] + iy) * a.din[0] + ix) * a.ci + i0 + ti]);
+      if (gv < vb && c0 + co < a.co) val = g[gv * a.co + c0 + co];
+      Gs[co * kMmaLd + v] = __float2bfloat16_rn(val);
+    }
+    // A^T: [k][v]; 8 consecutive k share a tap when c_in % 8 == 0
+    for (int e = tid; e < (kWgTile / 8) * kWgV; e += 128) {
+      const int v = e % kWgV, kq = e / kWgV, kb = k0 + 8 * kq;
+      const long long gv = v0 + v;
+      bf16 vals[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) vals[j] = __float2bfloat16_rn(0.f);
+      if (gv < vb) {
+        const long long b = gv / nvo;
+        const int vo = (int)(gv - b * nvo);
+        const int ox = vo % a.dout[0], oy = (vo / a.dout[0]) % a.dout[1], oz = vo / (a.dout[0] * a.dout[1]);
+        const bf16 *base = x + b * nvi * a.ci;
+        if (xvec && kb < K) {
+          const int tap = kb / a.ci, ci = kb - tap * a.ci;
+          const int ix = a.stride * ox + tap % 3 - 1, iy = a.stride * oy + (tap / 3) % 3 - 1,
+                    iz = a.stride * oz + tap / 9 - 1;
+          if (ix >= 0 && ix < a.din[0] && iy >= 0 && iy < a.din[1] && iz >= 0 && iz < a.din[2]) {
+            const uint4 pk = *reinterpret_cast<const uint4 *>(
+                base + ((long long)(iz * a.din[1] + iy) * a.din[0] + ix) * a.ci + ci);
+            const bf16 *pv = reinterpret_cast<const bf16 *>(&pk);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) vals[j] = pv[j];
+          }
+        } else if (!xvec) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int k = kb + j;
+            if (k >= K) break;
+            const int tap = k / a.ci, ci = k - tap * a.ci;
+            const int ix = a.stride * ox + tap % 3 - 1, iy = a.stride * oy + (tap / 3) % 3 - 1,
+                      iz = a.stride * oz + tap / 9 - 1;
+            if (ix >= 0 && ix < a.din[0] && iy >= 0 && iy < a.din[1] && iz >= 0 && iz < a.din[2])
+              vals[j] = base[((long long)(iz * a.din[1] + iy) * a.din[0] + ix) * a.ci + ci];
+          }
+        }
       }
-      xs[v][d][ti] = val;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) Xs[(8 * kq + j) * kMmaLd + v] = vals[j];
     }
     __syncthreads();
-#pragma unroll 2
-    for (int v = 0; v < 16; ++v) {
-      const float gv = gs[v][to];
-      accb += gv;
 #pragma unroll
-      for (int d = 0; d < 27; ++d) acc[d] = fmaf(gv, xs[v][d][ti], acc[d]);
+    for (int ks = 0; ks < kWgV; ks += 16) {
+      uint32_t af[2][4];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        const bf16 *r0 = Gs + (wm * 32 + mt * 16 + gq) * kMmaLd + ks + 2 * t4;
+        const bf16 *r8 = r0 + 8 * kMmaLd;
+        af[mt][0] = *reinterpret_cast<const uint32_t *>(r0);
+        af[mt][1] = *reinterpret_cast<const uint32_t *>(r8);
+        af[mt][2] = *reinterpret_cast<const uint32_t *>(r0 + 8);
+        af[mt][3] = *reinterpret_cast<const uint32_t *>(r8 + 8);
+      }
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const bf16 *bp = Xs + (wn * 32 + nt * 8 + gq) * kMmaLd + ks + 2 * t4;
+        const uint32_t b0 = *reinterpret_cast<const uint32_t *>(bp);
+        const uint32_t b1 = *reinterpret_cast<const uint32_t *>(bp + 8);
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          float *c = acc[mt][nt];
+          asm volatile(
+              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+              "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
+              : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+              : "r"(af[mt][0]), "r"(af[mt][1]), "r"(af[mt][2]), "r"(af[mt][3]), "r"(b0), "r"(b1));
+        }
+      }
     }
   }
-  if (o0 + to < a.co && i0 + ti < a.ci) {
 #pragma unroll
-    for (int d = 0; d < 27; ++d) atomicAdd(&dW[((long long)(o0 + to) * 27 + d) * a.ci + i0 + ti], acc[d]);
-  }
-  if (db && ti == 0 && blockIdx.y % nti == 0 && o0 + to < a.co) atomicAdd(&db[o0 + to], accb);
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int hr = 0; hr < 2; ++hr) {
+      const int co = c0 + wm * 32 + mt * 16 + gq + 8 * hr;
+      if (co >= a.co) continue;
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+        for (int hc = 0; hc < 2; ++hc) {
+          const int k = k0 + wn * 32 + nt * 8 + 2 * t4 + hc;
+          if (k < K) atomicAdd(&dW[(long long)co * K + k], acc[mt][nt][2 * hr + hc]);
+        }
+    }
+}
+
+// db[c_out] += sum_v g[v][c_out]: one thread per channel and voxel range
+__global__ void bias_grad_kernel(int co, long long total, long long chunk, const float *__restrict__ g,
+                                 float *__restrict__ db) {
+  const int c = threadIdx.x;
+  if (c >= co) return;
+  const long long va = (long long)blockIdx.x * chunk, vb = min(total, va + chunk);
+  float s = 0.f;
+  for (long long v = va; v < vb; ++v) s += g[v * co + c];
+  atomicAdd(&db[c], s);
 }
 
 // Vertex-centred linear interpolation by 2 per direction (coarse dims c,
@@ -426,16 +671,49 @@ Idx layer_index(const NetSpec &s) {
 
 // Grids of fewer than two blocks per SM split the reduction (see
 // conv_kernel) to reach about four.  part: FP32 scratch for the splits'
-// slices, splits * total * cout <= (4 + 2) * kSMs * 128 * 16 floats
-// (kSplitScratch), since a split grid has fewer than 2 * kSMs blocks of
-// 128 voxels x 16 channels.
+// slices, splits * total * cout <= (4 + 2) * kSMs * 128 * 64 floats
+// (kSplitScratch), since a split grid has fewer than 2 * kSMs blocks of at
+// most 128 voxels x 64 channels.
 constexpr int kSMs = 152;
-constexpr long long kSplitScratch = (4LL + 2LL) * kSMs * 128 * 16;
+constexpr long long kSplitScratch = (4LL + 2LL) * kSMs * 128 * 64;
+
+// tensor-core path (output channels >= 16): BN = 16, 32 or 64 channels per CTA
+template <typename TI, typename TO>
+void run_conv_mma(const ConvArgs &a, int batch, const TI *in, const bf16 *W, const float *bias,
+                  TO *out, float *part, cudaStream_t s) {
+  const long long total = (long long)batch * a.dout[0] * a.dout[1] * a.dout[2];
+  const int bn = a.cout <= 16 ? 16 : (a.cout <= 32 ? 32 : 64);
+  const long long bxy = (long long)grid1(total, kMmaBM) * ((a.cout + bn - 1) / bn);
+  const int nkc = (27 * a.cin + kMmaKC - 1) / kMmaKC;
+  int splits = 1;
+  if (bxy < 2 * kSMs) splits = (int)std::min<long long>(nkc, (4 * kSMs + bxy - 1) / bxy);
+  const int per = (nkc + splits - 1) / splits;
+  splits = (nkc + per - 1) / per;
+  if (splits > 1 && (long long)splits * total * a.cout > kSplitScratch)
+    throw std::runtime_error("conv split scratch too small");
+  dim3 grid(grid1(total, kMmaBM), (a.cout + bn - 1) / bn, splits);
+  if (bn == 16) conv_mma_kernel<TI, TO, 16><<<grid, 128, 0, s>>>(a, total, per, in, W, bias, out, part);
+  else if (bn == 32) conv_mma_kernel<TI, TO, 32><<<grid, 128, 0, s>>>(a, total, per, in, W, bias, out, part);
+  else conv_mma_kernel<TI, TO, 64><<<grid, 128, 0, s>>>(a, total, per, in, W, bias, out, part);
+  CKN(cudaGetLastError());
+  rmd::add_launches(1);
+  if (splits > 1) {
+    const long long n = total * a.cout;
+    conv_finish_kernel<TO><<<grid1(n, 256), 256, 0, s>>>(n, a.cout, splits, part, bias, a.relu,
+                                                         a.accumulate, out);
+    CKN(cudaGetLastError());
+    rmd::add_launches(1);
+  }
+}
 
 template <typename TI, typename TO, int OT, int IC>
 void run_conv(const ConvArgs &a, int batch, const TI *in, const bf16 *W, const float *bias, TO *out,
               float *part, cudaStream_t s) {
   static_assert(OT <= 16, "split scratch bound assumes at most 16 channels per block");
+  if (OT == 16 && a.cout >= 16) {
+    run_conv_mma<TI, TO>(a, batch, in, W, bias, out, part, s);
+    return;
+  }
   const long long total = (long long)batch * a.dout[0] * a.dout[1] * a.dout[2];
   const long long bxy = (long long)grid1(total, 128) * ((a.cout + OT - 1) / OT);
   const int nunits = 3 * ((a.cin + IC - 1) / IC);
@@ -511,15 +789,25 @@ void conv_wgrad(Net *n, const Layer &L, const float *gout, const bf16 *in) {
   }
   a.stride = L.stride;
   const long long total = (long long)n->batch * n->nvox[L.lout];
-  const int tiles = ((L.cin + 15) / 16) * ((L.cout + 15) / 16);
-  long long blocks = std::max(1LL, std::min((total + 15) / 16, (long long)(4 * 152 / tiles) + 1));
-  long long chunk = (total + blocks - 1) / blocks;
-  chunk = (chunk + 15) / 16 * 16;
-  blocks = (total + chunk - 1) / chunk;
-  wgrad_kernel<<<dim3((unsigned)blocks, tiles), 256, 0, n->stream>>>(
-      a, total, chunk, gout, in, n->grad + L.woff, n->grad + L.boff);
-  CKN(cudaGetLastError());
-  rmd::add_launches(1);
+  {
+    // tensor cores: 64 x 64 tiles of dW (rows beyond c_out are zero), voxel
+    // ranges to fill ~4 CTAs per SM
+    const int kt = (27 * L.cin + kWgTile - 1) / kWgTile, ct = (L.cout + kWgTile - 1) / kWgTile;
+    long long blocks = std::max(1LL, std::min((total + kWgV - 1) / kWgV,
+                                              (long long)(4 * kSMs / (kt * ct)) + 1));
+    long long chunk = (total + blocks - 1) / blocks;
+    chunk = (chunk + kWgV - 1) / kWgV * kWgV;
+    blocks = (total + chunk - 1) / chunk;
+    wgrad_mma_kernel<<<dim3((unsigned)blocks, kt, ct), 128, 0, n->stream>>>(
+        a, total, chunk, gout, in, n->grad + L.woff);
+    CKN(cudaGetLastError());
+    const int bb = (int)std::min<long long>(4 * kSMs, (total + 255) / 256);
+    const long long bc = (total + bb - 1) / bb;
+    bias_grad_kernel<<<(unsigned)((total + bc - 1) / bc), ((L.cout + 31) / 32) * 32, 0, n->stream>>>(
+        L.cout, total, bc, gout, n->grad + L.boff);
+    CKN(cudaGetLastError());
+    rmd::add_launches(2);
+  }
 }
 
 void relu_mask(Net *n, float *g, const bf16 *a, long long count) {
