@@ -76,6 +76,11 @@ struct rm_handle {
   double *hscal = nullptr;  // pinned
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<cudaEvent_t> evpool;  // profile = 1: start/stop pairs
+  // independent branches of the relaxation (patch families, the Hiptmair
+  // potential branch, the coarse correction) run on their own streams
+  static constexpr int kBranches = 5;
+  cudaStream_t br[kBranches] = {};
+  cudaEvent_t fork = nullptr, join[kBranches] = {};
   long long stat_patches = 0, stat_slots = 0, stat_nnz = 0;
   // learned coarse corrector (k = 0): coarse operator, grid maps, centred
   // log alpha at the grid vertices, network and its batch-1 buffers
@@ -122,6 +127,11 @@ struct rm_handle {
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
     for (cudaEvent_t e : evpool) cudaEventDestroy(e);
+    for (int i = 0; i < kBranches; ++i) {
+      if (br[i]) cudaStreamDestroy(br[i]);
+      if (join[i]) cudaEventDestroy(join[i]);
+    }
+    if (fork) cudaEventDestroy(fork);
   }
 };
 
@@ -423,37 +433,70 @@ void learned_coarse(rm_handle *h) {
   rmn::corr_scale(nc, h->cl, h->lscal, h->ce, s);
 }
 
-// z = B r
+// z = B r.  The additive terms of the interface relaxation (each patch
+// family, the Hiptmair potential branch) only add into z with atomic adds,
+// so they run concurrently on the handle's branch streams between a fork
+// after the condensation and a join before the interior expansion; the
+// coarse solve runs beside them and its prolongation is added last (it
+// enters the interior rows too, which the expansion overwrites).
 void precondition(rm_handle *h, const double *r, double *z) {
   cudaStream_t s = h->stream;
   CK(cudaMemsetAsync(z, 0, h->size * sizeof(double), s));
+  const double *rr = r;
   if (h->sc) {
     CK(launch_spmv(h->Binv, r, h->w, nullptr, 0, 1.0, s));       // w_I = P_II^-1 r_I
     CK(launch_spmv(h->E, r, h->rt, r, 2, -1.0, s));              // rt_G = r_G - P_GI P_II^-1 r_I
-    for (auto &F : h->fam) CK(launch_patches(F, h->rt, z, s));   // z_G = sum_v S_v^-1 rt
-    if (h->ph) {
-      CK(launch_spmv(h->DtT, h->rt, h->u0, nullptr, 0, 1.0, s)); // u0 = D~^T rt
-      CK(cudaMemsetAsync(h->v0, 0, h->size0 * sizeof(double), s));
-      for (auto &F : h->pfam) CK(launch_patches(F, h->u0, h->v0, s));
-      CK(launch_spmv(h->Dt, h->v0, z, nullptr, 1, 1.0, s));     // z_G += D~ v0
-    }
-    CK(launch_spmv(h->Et, z, z, h->w, 2, -1.0, s));              // z_I = w_I - E^T z_G
-  } else {
-    for (auto &F : h->fam) CK(launch_patches(F, r, z, s));
+    rr = h->rt;
+  }
+  // the learned coarse term talks to the host (judge): keep everything on s
+  const bool fork = h->corr_mode != RM_CORRECTOR_LEARNED;
+  int nb = 0;
+  auto branch = [&]() -> cudaStream_t {
+    if (!fork) return s;
+    cudaStream_t b = h->br[nb % rm_handle::kBranches];
+    if (nb < rm_handle::kBranches) CK(cudaStreamWaitEvent(b, h->fork, 0));
+    ++nb;
+    return b;
+  };
+  if (fork) CK(cudaEventRecord(h->fork, s));
+  for (auto &F : h->fam) CK(launch_patches(F, rr, z, branch()));  // z_G += sum_v S_v^-1 rt
+  if (h->ph) {
+    cudaStream_t b = branch();
+    CK(launch_spmv(h->DtT, rr, h->u0, nullptr, 0, 1.0, b));        // u0 = D~^T rt
+    CK(cudaMemsetAsync(h->v0, 0, h->size0 * sizeof(double), b));
+    for (auto &F : h->pfam) CK(launch_patches(F, h->u0, h->v0, b));
+    CK(launch_spmv(h->Dt, h->v0, z, nullptr, 3, 1.0, b));          // z_G += D~ v0
   }
   const bool record = h->rec && h->rec_n < h->rec_cap;
   if (h->nc > 0 && (h->corr_mode != RM_CORRECTOR_OFF || record)) {
-    CK(launch_spmv(h->R0, r, h->cc, nullptr, 0, 1.0, s));
-    if (record) {
-      CK(cudaMemcpyAsync(h->rec + (size_t)h->rec_n * h->nc, h->cc, h->nc * sizeof(double),
-                         cudaMemcpyDeviceToDevice, s));
-      h->rec_n++;
+    cudaStream_t b = branch();
+    std::swap(h->stream, b);  // the coarse helpers launch on h->stream
+    try {
+      CK(launch_spmv(h->R0, r, h->cc, nullptr, 0, 1.0, h->stream));
+      if (record) {
+        CK(cudaMemcpyAsync(h->rec + (size_t)h->rec_n * h->nc, h->cc, h->nc * sizeof(double),
+                           cudaMemcpyDeviceToDevice, h->stream));
+        h->rec_n++;
+      }
+      if (h->corr_mode != RM_CORRECTOR_OFF) {
+        if (h->corr_mode == RM_CORRECTOR_LEARNED && h->net && h->lc_fallback < 0) learned_coarse(h);
+        else plain_coarse(h);                                      // cc -> ce
+      }
+    } catch (...) {
+      std::swap(h->stream, b);
+      throw;
     }
-    if (h->corr_mode == RM_CORRECTOR_OFF) return;
-    if (h->corr_mode == RM_CORRECTOR_LEARNED && h->net && h->lc_fallback < 0) learned_coarse(h);
-    else plain_coarse(h);                                       // cc -> ce
-    CK(launch_spmv(h->R0T, h->ce, z, nullptr, 1, 1.0, s));
+    std::swap(h->stream, b);
   }
+  if (fork)
+    for (int i = 0; i < std::min(nb, (int)rm_handle::kBranches); ++i) {
+      CK(cudaEventRecord(h->join[i], h->br[i]));
+      CK(cudaStreamWaitEvent(s, h->join[i], 0));
+    }
+  if (h->sc) CK(launch_spmv(h->Et, z, z, h->w, 2, -1.0, s));       // z_I = w_I - E^T z_G
+  // the coarse term enters every row, after the interior expansion
+  if (h->nc > 0 && h->corr_mode != RM_CORRECTOR_OFF)
+    CK(launch_spmv(h->R0T, h->ce, z, nullptr, 1, 1.0, s));       // z += R_0^T ce
 }
 
 void apply(rm_handle *h, const double *x, double *y) {
@@ -642,6 +685,11 @@ int rm_setup(rm_handle **out, int space, const rm_mesh *mesh, int p, const doubl
     CK(cudaMallocHost((void **)&h->hscal, S_COUNT * sizeof(double)));
     CK(cudaEventCreate(&h->ev0));
     CK(cudaEventCreate(&h->ev1));
+    CK(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
+    for (int i = 0; i < rm_handle::kBranches; ++i) {
+      CK(cudaStreamCreateWithFlags(&h->br[i], cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&h->join[i], cudaEventDisableTiming));
+    }
     CK(cudaDeviceSynchronize());
   } catch (const CudaError &e) {
     return fail(nullptr, RM_ERR_CUDA, std::string("rm_setup: ") + e.what());

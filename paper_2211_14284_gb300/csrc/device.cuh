@@ -181,6 +181,8 @@ long long launch_count();
 void add_launches(long long k);  // for launchers in other files (learned.cu)
 cudaError_t launch_apply(const ApplyDev &A, const double *x, double *y, cudaStream_t s);
 cudaError_t launch_metric(const ApplyDev &A, double *G, cudaStream_t s);
+// spmv modes: 0 y = a A x; 1 y += a A x; 2 y = u + a A x; 3 y += a A x with
+// atomic adds (rows shared with other kernels adding concurrently)
 cudaError_t launch_spmv(const DevCsr &M, const double *x, double *y, const double *u, int mode,
                         double a, cudaStream_t s);
 cudaError_t launch_patches(const DevPatch &F, const double *r, double *z, cudaStream_t s);

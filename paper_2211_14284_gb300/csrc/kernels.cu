@@ -729,6 +729,7 @@ __global__ void spmv_kernel(int nrows, const int *__restrict__ rid, const int *_
     const double v = a * (double)s;
     if (mode == 0) y[r] = v;
     else if (mode == 1) y[r] += v;
+    else if (mode == 3) atomicAdd(y + r, v);  // y += a A x beside concurrent atomic adders
     else y[r] = u[r] + v;
   }
 }
