@@ -141,8 +141,9 @@ HostProb build_prob(int k, const rm_mesh &mesh, int p, const double *alpha, cons
 
 // Concatenation of CSR pieces with offset row / column ids.
 struct CsrCat {
-  std::vector<int> rid, ptr{0}, col;
+  std::vector<int> rid, ptr{0}, col, rprob;
   std::vector<double> val;
+  int prob = 0;  // the problem whose rows append() adds
   // rows: row indices of A to append (empty rows kept); rmap/cmap: index maps
   // (nullptr = identity) applied before adding the offsets.
   void append(const Csr &A, const std::vector<int> *rows, const std::vector<int> *rmap,
@@ -155,6 +156,7 @@ struct CsrCat {
     }
     for (int i : *rows) {
       rid.push_back((int)((rmap ? (*rmap)[i] : i) + roff));
+      rprob.push_back(prob);
       for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
         col.push_back((int)((cmap ? (*cmap)[A.col[e]] : A.col[e]) + coff));
         val.push_back(A.val[e]);
@@ -168,7 +170,7 @@ struct CsrCat {
 // Patch families with identical templates, concatenated.
 struct FamCat {
   PatchFamily tmpl;
-  std::vector<int> slotmap;
+  std::vector<int> slotmap, pprob;
   std::vector<double> val;
   int npatch = 0;
 };
@@ -192,6 +194,12 @@ struct ApplyGroup {
 struct rm_batch {
   std::string err;
   cudaStream_t stream = nullptr;
+  // independent relaxation branches (merged patch families, the Hiptmair
+  // potential branch, the coarse solve) fork onto these streams; inside the
+  // captured iteration they become parallel graph branches
+  static constexpr int kBranches = 8;
+  cudaStream_t br[kBranches] = {};
+  cudaEvent_t fork = nullptr, join[kBranches] = {};
   rm_options opt{};
   int nprob = 0;
   int vt = 0;
@@ -248,6 +256,7 @@ struct rm_batch {
     D.col = upload(c.col);
     D.val = upload_vals(c.val, force_double);
     D.vt = force_double ? 0 : vt;
+    D.rprob = upload(c.rprob);
     return D;
   }
   DevPatch upload_fam(const FamCat &f) {
@@ -270,6 +279,7 @@ struct rm_batch {
     D.brows = upload(F.brows);
     D.vt = vt;
     D.val = upload_vals(f.val);
+    D.pprob = upload(f.pprob);
     if (F.inverse) {
       D.inverse = 1;
       D.ivals = F.ivals();
@@ -286,6 +296,11 @@ struct rm_batch {
     if (hdone) cudaFreeHost(hdone);
     if (hscal) cudaFreeHost(hscal);
     if (stream) cudaStreamDestroy(stream);
+    for (int i = 0; i < kBranches; ++i) {
+      if (br[i]) cudaStreamDestroy(br[i]);
+      if (join[i]) cudaEventDestroy(join[i]);
+    }
+    if (fork) cudaEventDestroy(fork);
   }
 };
 
@@ -300,31 +315,50 @@ int bfail(rm_batch *b, int code, const std::string &msg) {
 void batch_apply(rm_batch *B, const double *x, double *y) {
   BK(cudaMemsetAsync(y, 0, B->N * sizeof(double), B->stream));
   for (auto &g : B->groups)
-    BK(launch_apply_batch(g.descs, g.work, g.nwork, g.threads, g.smem, x, y, B->stream));
+    BK(launch_apply_batch(g.descs, g.work, g.nwork, g.threads, g.smem, x, y, B->done, B->stream));
 }
 
+// z = B r for every problem: the condensation on the batch stream, then the
+// additive interface terms (merged patch families, the Hiptmair potential
+// branch) and the coarse solve concurrently on the branch streams (atomic
+// adds into z), joined before the interior expansion; the coarse
+// prolongation is added last.
 void batch_precondition(rm_batch *B, const double *r, double *z) {
   cudaStream_t s = B->stream;
   BK(cudaMemsetAsync(z, 0, B->N * sizeof(double), s));
+  const double *rr = r;
   if (B->sc) {
     BK(launch_spmv(B->Binv, r, B->w, nullptr, 0, 1.0, s));
     BK(launch_spmv(B->E, r, B->rt, r, 2, -1.0, s));
-    for (auto &F : B->fam) BK(launch_patches(F, B->rt, z, s));
-    if (B->ph) {
-      BK(launch_spmv(B->DtT, B->rt, B->u0, nullptr, 0, 1.0, s));
-      BK(cudaMemsetAsync(B->v0, 0, B->N0 * sizeof(double), s));
-      for (auto &F : B->pfam) BK(launch_patches(F, B->u0, B->v0, s));
-      BK(launch_spmv(B->Dt, B->v0, z, nullptr, 1, 1.0, s));
-    }
-    BK(launch_spmv(B->Et, z, z, B->w, 2, -1.0, s));
-  } else {
-    for (auto &F : B->fam) BK(launch_patches(F, r, z, s));
+    rr = B->rt;
+  }
+  BK(cudaEventRecord(B->fork, s));
+  int nb = 0;
+  auto branch = [&]() {
+    cudaStream_t b = B->br[nb % rm_batch::kBranches];
+    if (nb < rm_batch::kBranches) BK(cudaStreamWaitEvent(b, B->fork, 0));
+    ++nb;
+    return b;
+  };
+  for (auto &F : B->fam) BK(launch_patches(F, rr, z, branch()));
+  if (B->ph) {
+    cudaStream_t b = branch();
+    BK(launch_spmv(B->DtT, rr, B->u0, nullptr, 0, 1.0, b));
+    BK(cudaMemsetAsync(B->v0, 0, B->N0 * sizeof(double), b));
+    for (auto &F : B->pfam) BK(launch_patches(F, B->u0, B->v0, b));
+    BK(launch_spmv(B->Dt, B->v0, z, nullptr, 3, 1.0, b));
   }
   if (B->NC > 0) {
-    BK(launch_spmv(B->R0, r, B->cc, nullptr, 0, 1.0, s));
-    BK(launch_gemv_batch((int)B->NC, B->rowprob, B->aoff, B->cstart, B->csz, B->A0inv, B->cc, B->ce, s));
-    BK(launch_spmv(B->R0T, B->ce, z, nullptr, 1, 1.0, s));
+    cudaStream_t b = branch();
+    BK(launch_spmv(B->R0, r, B->cc, nullptr, 0, 1.0, b));
+    BK(launch_gemv_batch((int)B->NC, B->rowprob, B->aoff, B->cstart, B->csz, B->A0inv, B->cc, B->ce, b));
   }
+  for (int i = 0; i < std::min(nb, (int)rm_batch::kBranches); ++i) {
+    BK(cudaEventRecord(B->join[i], B->br[i]));
+    BK(cudaStreamWaitEvent(s, B->join[i], 0));
+  }
+  if (B->sc) BK(launch_spmv(B->Et, z, z, B->w, 2, -1.0, s));
+  if (B->NC > 0) BK(launch_spmv(B->R0T, B->ce, z, nullptr, 1, 1.0, s));
 }
 
 // One lock-step iteration (captured in the graph).
@@ -370,6 +404,11 @@ int rm_batch_setup(rm_batch **out, int nprob, const int *space, const rm_mesh *m
     }
     if (B->ph && !B->sc) throw std::invalid_argument("RM_PH needs static_condensation = 1");
     BK(cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking));
+    BK(cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming));
+    for (int i = 0; i < rm_batch::kBranches; ++i) {
+      BK(cudaStreamCreateWithFlags(&B->br[i], cudaStreamNonBlocking));
+      BK(cudaEventCreateWithFlags(&B->join[i], cudaEventDisableTiming));
+    }
     // ---- host setup of every problem, offsets ----
     std::vector<HostProb> H;
     H.reserve(nprob);
@@ -412,6 +451,7 @@ int rm_batch_setup(rm_batch **out, int nprob, const int *space, const rm_mesh *m
           A.k = P.k;
           A.p = P.p;
           A.q = quad_points(P.p);
+          A.prob = kv.second[gi];
           for (int d = 0; d < 3; ++d) A.n[d] = P.n[d];
           A.nc0 = P.L.ncomp;
           A.nc1 = L1.ncomp;
@@ -458,11 +498,16 @@ int rm_batch_setup(rm_batch **out, int nprob, const int *space, const rm_mesh *m
       CsrCat cb, ce, cet, cd, cdt;
       for (int i = 0; i < nprob; ++i) {
         const HostProb &P = H[i];
+        cb.prob = i;
         cb.append(P.C.Binv, &P.C.I, &P.fm.free2lat, &P.fm.free2lat, B->off[i], B->off[i]);
+        ce.prob = i;
         ce.append(P.C.E, &P.C.G, &P.fm.free2lat, &P.fm.free2lat, B->off[i], B->off[i]);
+        cet.prob = i;
         cet.append(P.C.Et, &P.C.I, &P.fm.free2lat, &P.fm.free2lat, B->off[i], B->off[i]);
         if (B->ph) {
+          cd.prob = i;
           cd.append(P.D, &P.G1, nullptr, nullptr, B->off[i], B->off0[i]);
+          cdt.prob = i;
           cdt.append(transpose(P.D), &P.G0, nullptr, nullptr, B->off0[i], B->off[i]);
         }
       }
@@ -487,7 +532,9 @@ int rm_batch_setup(rm_batch **out, int nprob, const int *space, const rm_mesh *m
         const CoarseData &c = H[i].cd;
         std::vector<int> rows(c.nc);
         for (int j = 0; j < c.nc; ++j) rows[j] = j;
+        cr.prob = i;
         cr.append(c.R0, &rows, nullptr, nullptr, B->coff[i], B->off[i]);
+        crt.prob = i;
         crt.append(c.R0T, nullptr, nullptr, nullptr, B->off[i], B->coff[i]);
         aoff.push_back((long long)A0.size());
         A0.insert(A0.end(), c.A0inv.begin(), c.A0inv.end());
@@ -527,6 +574,7 @@ int rm_batch_setup(rm_batch **out, int nprob, const int *space, const rm_mesh *m
           const std::vector<double> v = F.device_values();
           dst->val.insert(dst->val.end(), v.begin(), v.end());
           dst->npatch += F.npatch;
+          dst->pprob.insert(dst->pprob.end(), F.npatch, i);
         }
       }
       std::vector<DevPatch> out;
@@ -559,6 +607,11 @@ int rm_batch_setup(rm_batch **out, int nprob, const int *space, const rm_mesh *m
     B->partial = B->dalloc<double>(2 * (size_t)B->nchunk);
     B->scal = B->dalloc<double>((size_t)nprob * S_COUNT);
     B->done = B->dalloc<int>(nprob);
+    BK(cudaMemset(B->done, 0, nprob * sizeof(int)));
+    // rows and patches of converged problems are skipped by the kernels
+    for (DevCsr *M : {&B->Binv, &B->E, &B->Et, &B->Dt, &B->DtT, &B->R0, &B->R0T}) M->done = B->done;
+    for (auto &F : B->fam) F.done = B->done;
+    for (auto &F : B->pfam) F.done = B->done;
     B->iters = B->dalloc<int>(nprob);
     BK(cudaMallocHost((void **)&B->hdone, nprob * sizeof(int)));
     BK(cudaMallocHost((void **)&B->hscal, (size_t)nprob * S_COUNT * sizeof(double)));
@@ -571,10 +624,10 @@ int rm_batch_setup(rm_batch **out, int nprob, const int *space, const rm_mesh *m
       float best = 1e30f;
       int bestt = kApplyThreads;
       for (int t : {64, 128, 256}) {
-        BK(launch_apply_batch(g.descs, g.work, g.nwork, t, g.smem, B->pv, B->qv, B->stream));
+        BK(launch_apply_batch(g.descs, g.work, g.nwork, t, g.smem, B->pv, B->qv, B->done, B->stream));
         BK(cudaEventRecord(e0, B->stream));
         for (int rep = 0; rep < 3; ++rep)
-          BK(launch_apply_batch(g.descs, g.work, g.nwork, t, g.smem, B->pv, B->qv, B->stream));
+          BK(launch_apply_batch(g.descs, g.work, g.nwork, t, g.smem, B->pv, B->qv, B->done, B->stream));
         BK(cudaEventRecord(e1, B->stream));
         BK(cudaEventSynchronize(e1));
         float ms = 0.f;

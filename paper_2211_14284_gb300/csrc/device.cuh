@@ -37,6 +37,7 @@ struct ApplyDev {
   // the s- and r-tabulations; doubles after wq in tabs, headers in eoi
   int eo_dbls;
   const int *eoi;
+  int prob;                // batched solves: the problem's index
   size_t smem_doubles;
 };
 
@@ -158,6 +159,9 @@ struct DevCsr {
   int *col = nullptr;
   void *val = nullptr;     // double or float (vt)
   int vt = 0;
+  // batched solves: the problem of every row and the device convergence
+  // flags; rows of converged problems are skipped (null: no skipping)
+  const int *rprob = nullptr, *done = nullptr;
 };
 
 // A family of patches with a shared slot template.
@@ -174,6 +178,8 @@ struct DevPatch {
   // of every decoupled block, column-major, concatenated (ivals values)
   int inverse = 0, ivals = 0;
   const int *pos_slot = nullptr, *pos_blk = nullptr, *bptr = nullptr, *boff = nullptr;
+  // batched solves: the problem of every patch and the convergence flags
+  const int *pprob = nullptr, *done = nullptr;
 };
 
 // launchers (kernels.cu); launch_count() = kernels launched so far in this process
@@ -213,7 +219,8 @@ cudaError_t launch_update_p(long long n, double *p, const double *z, const doubl
 
 // batched solver (batch.cu)
 cudaError_t launch_apply_batch(const ApplyDev *descs, const int2 *work, int nwork, int threads,
-                               size_t smem, const double *x, double *y, cudaStream_t s);
+                               size_t smem, const double *x, double *y, const int *done,
+                               cudaStream_t s);
 cudaError_t launch_seg_dot(const int4 *chunk, int nchunk, const int *cptr, int nprob, const double *a,
                            const double *b, double *partial, double *scal, int *done, int *iters,
                            int slot, int op, double tol2, cudaStream_t s);

@@ -669,11 +669,13 @@ __global__ void __launch_bounds__(kApplyThreads) apply_cart_kernel(ApplyDev P, c
 __global__ void __launch_bounds__(kApplyThreads) apply_cart_batch_kernel(const ApplyDev *__restrict__ descs,
                                                                          const int2 *__restrict__ work,
                                                                          const double *__restrict__ x,
-                                                                         double *__restrict__ y) {
+                                                                         double *__restrict__ y,
+                                                                         const int *__restrict__ done) {
   __shared__ ApplyDev Ps;
   const int2 w = work[blockIdx.x];
   if (threadIdx.x == 0) Ps = descs[w.x];
   __syncthreads();
+  if (done && done[Ps.prob]) return;  // converged problem: its y stays 0
   if (Ps.k == 0) cart_cell_k<0>(Ps, w.y, x, y);
   else if (Ps.k == 1) cart_cell_k<1>(Ps, w.y, x, y);
   else cart_cell_k<2>(Ps, w.y, x, y);
@@ -712,19 +714,23 @@ __global__ void axpy_kernel(int n, double a, const double *__restrict__ x, doubl
 template <typename VT, int TPR>
 __global__ void spmv_kernel(int nrows, const int *__restrict__ rid, const int *__restrict__ ptr,
                             const int *__restrict__ col, const VT *__restrict__ val,
-                            const double *x, double *y, const double *u, int mode, double a) {
+                            const double *x, double *y, const double *u, int mode, double a,
+                            const int *__restrict__ rprob, const int *__restrict__ done) {
   // x, y and u may alias (z_I = w_I - E^T z_G reads and writes z on
   // disjoint rows), so they are not declared __restrict__.
   // Products accumulate in the matrix's precision VT (FP32 data: the
   // mixed-precision preconditioner; the coarse path is always FP64).
   const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int row = (int)(gt / TPR), lane = (int)(gt % TPR);
+  // rows of converged problems (batched solves) are skipped; their lanes
+  // still take part in the shuffles
+  const bool live = row < nrows && !(rprob && done[rprob[row]]);
   VT s = 0;
-  if (row < nrows)
+  if (live)
     for (int e = ptr[row] + lane; e < ptr[row + 1]; e += TPR) s = fma(val[e], (VT)x[col[e]], s);
 #pragma unroll
   for (int off = TPR / 2; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off, TPR);
-  if (lane == 0 && row < nrows) {
+  if (lane == 0 && live) {
     const int r = rid[row];
     const double v = a * (double)s;
     if (mode == 0) y[r] = v;
@@ -742,6 +748,7 @@ __global__ void spmv_kernel(int nrows, const int *__restrict__ rid, const int *_
 // factor's diagonal entries are stored as their reciprocals (no division).
 template <typename VT, bool STAGE>
 __global__ void patch_kernel(DevPatch F, const double *__restrict__ r, double *__restrict__ z) {
+  if (F.pprob && F.done[F.pprob[blockIdx.x]]) return;  // converged problem (batched solves)
   extern __shared__ double smem_raw[];
   VT *xs = reinterpret_cast<VT *>(smem_raw);
   const int ns = F.nslots;
@@ -787,6 +794,7 @@ __global__ void patch_kernel(DevPatch F, const double *__restrict__ r, double *_
 // coalesced loads; no level chain.  Arithmetic in the data's precision VT.
 template <typename VT>
 __global__ void patch_inv_kernel(DevPatch F, const double *__restrict__ r, double *__restrict__ z) {
+  if (F.pprob && F.done[F.pprob[blockIdx.x]]) return;  // converged problem (batched solves)
   extern __shared__ double smem_raw[];
   VT *xs = reinterpret_cast<VT *>(smem_raw);
   const int ns = F.nslots;
@@ -1085,12 +1093,12 @@ static void spmv_dispatch(const DevCsr &M, const double *x, double *y, const dou
   const int grid = (int)((tot + threads - 1) / threads);
   const VT *v = reinterpret_cast<const VT *>(M.val);
   switch (M.tpr) {
-    case 1: spmv_kernel<VT, 1><<<grid, threads, 0, s>>>(M.nrows, M.rid, M.ptr, M.col, v, x, y, u, mode, a); break;
-    case 2: spmv_kernel<VT, 2><<<grid, threads, 0, s>>>(M.nrows, M.rid, M.ptr, M.col, v, x, y, u, mode, a); break;
-    case 4: spmv_kernel<VT, 4><<<grid, threads, 0, s>>>(M.nrows, M.rid, M.ptr, M.col, v, x, y, u, mode, a); break;
-    case 8: spmv_kernel<VT, 8><<<grid, threads, 0, s>>>(M.nrows, M.rid, M.ptr, M.col, v, x, y, u, mode, a); break;
-    case 16: spmv_kernel<VT, 16><<<grid, threads, 0, s>>>(M.nrows, M.rid, M.ptr, M.col, v, x, y, u, mode, a); break;
-    default: spmv_kernel<VT, 32><<<grid, threads, 0, s>>>(M.nrows, M.rid, M.ptr, M.col, v, x, y, u, mode, a); break;
+    case 1: spmv_kernel<VT, 1><<<grid, threads, 0, s>>>(M.nrows, M.rid, M.ptr, M.col, v, x, y, u, mode, a, M.rprob, M.done); break;
+    case 2: spmv_kernel<VT, 2><<<grid, threads, 0, s>>>(M.nrows, M.rid, M.ptr, M.col, v, x, y, u, mode, a, M.rprob, M.done); break;
+    case 4: spmv_kernel<VT, 4><<<grid, threads, 0, s>>>(M.nrows, M.rid, M.ptr, M.col, v, x, y, u, mode, a, M.rprob, M.done); break;
+    case 8: spmv_kernel<VT, 8><<<grid, threads, 0, s>>>(M.nrows, M.rid, M.ptr, M.col, v, x, y, u, mode, a, M.rprob, M.done); break;
+    case 16: spmv_kernel<VT, 16><<<grid, threads, 0, s>>>(M.nrows, M.rid, M.ptr, M.col, v, x, y, u, mode, a, M.rprob, M.done); break;
+    default: spmv_kernel<VT, 32><<<grid, threads, 0, s>>>(M.nrows, M.rid, M.ptr, M.col, v, x, y, u, mode, a, M.rprob, M.done); break;
   }
 }
 
@@ -1222,11 +1230,12 @@ cudaError_t launch_update_p(long long n, double *p, const double *z, const doubl
 }
 
 cudaError_t launch_apply_batch(const ApplyDev *descs, const int2 *work, int nwork, int threads,
-                               size_t smem, const double *x, double *y, cudaStream_t s) {
+                               size_t smem, const double *x, double *y, const int *done,
+                               cudaStream_t s) {
   cudaError_t err = cudaFuncSetAttribute(apply_cart_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
   if (err != cudaSuccess) return err;
-  apply_cart_batch_kernel<<<nwork, threads, smem, s>>>(descs, work, x, y);
+  apply_cart_batch_kernel<<<nwork, threads, smem, s>>>(descs, work, x, y, done);
   g_launches += 1;
   return cudaGetLastError();
 }
