@@ -25,7 +25,8 @@ struct ApplyDev {
   const double *X;         // vertices, 3 per vertex
   const double *alpha, *beta;
   const double *tabs;      // Ts q(p+1) | Tr qp | D1 p(p+1) | xq q | wq q | eo_dbls
-  const double *G;         // pullback weights per cell and point (metric_kernel)
+  const void *G;           // pullback weights per cell and point (metric_kernel),
+                           // in the general apply's number type (double-float)
   int nA, nAB;             // entries of stage A, of both stages (1 or 6 each)
   // Cartesian fast path (every cell an axis-aligned box): cell sizes
   // h[3 * cell + d] and the 1D factors of B-hat (a = B_00 = B_pp, b = B_0p)
@@ -186,7 +187,7 @@ struct DevPatch {
 long long launch_count();
 void add_launches(long long k);  // for launchers in other files (learned.cu)
 cudaError_t launch_apply(const ApplyDev &A, const double *x, double *y, cudaStream_t s);
-cudaError_t launch_metric(const ApplyDev &A, double *G, cudaStream_t s);
+cudaError_t launch_metric(const ApplyDev &A, void *G, cudaStream_t s);
 // spmv modes: 0 y = a A x; 1 y += a A x; 2 y = u + a A x; 3 y += a A x with
 // atomic adds (rows shared with other kernels adding concurrently)
 cudaError_t launch_spmv(const DevCsr &M, const double *x, double *y, const double *u, int mode,
