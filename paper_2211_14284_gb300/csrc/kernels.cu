@@ -526,22 +526,22 @@ __device__ __forceinline__ double box_metric(int kk, int m, double h0, double h1
 // B-hat (s-type) or I (r-type): an s-type index on the interface {0, p}
 // couples to itself with weight a and to the opposite interface index p - i
 // with weight b; any other index only to itself.  Evaluated direction by
-// direction, so an interior element costs no FP64 operation and each
-// interface direction one FMA pair (the FP64 pipe is the limit here).
-__device__ __forceinline__ double mass_at(const double *__restrict__ in, bool s0, bool s1, bool s2,
-                                          int i0, int i1, int i2, int l0, int l1, int p, double a,
-                                          double b) {
+// direction, so an interior element costs no arithmetic and each interface
+// direction one multiply-add pair.
+template <typename R>
+__device__ __forceinline__ R mass_at(const R *__restrict__ in, bool s0, bool s1, bool s2, int i0,
+                                     int i1, int i2, int l0, int l1, int p, R a, R b) {
   const bool t0 = s0 && (i0 == 0 || i0 == p), t1 = s1 && (i1 == 0 || i1 == p),
              t2 = s2 && (i2 == 0 || i2 == p);
   const int o0 = p - i0, o1 = p - i1, o2 = p - i2;
-  auto line = [&](const double *row) { return t0 ? fma(b, row[o0], a * row[i0]) : row[i0]; };
+  auto line = [&](const R *row) { return t0 ? rfma(b, row[o0], rmul(a, row[i0])) : row[i0]; };
   auto plane = [&](int j2) {
-    const double *base = in + l0 * l1 * j2;
-    const double v = line(base + l0 * i1);
-    return t1 ? fma(b, line(base + l0 * o1), a * v) : v;
+    const R *base = in + l0 * l1 * j2;
+    const R v = line(base + l0 * i1);
+    return t1 ? rfma(b, line(base + l0 * o1), rmul(a, v)) : v;
   };
-  const double v = plane(i2);
-  return t2 ? fma(b, plane(o2), a * v) : v;
+  const R v = plane(i2);
+  return t2 ? rfma(b, plane(o2), rmul(a, v)) : v;
 }
 
 // One Cartesian cell c of the problem described by P, form degree K (shared
@@ -553,25 +553,26 @@ __device__ __forceinline__ double mass_at(const double *__restrict__ in, bool s0
 // component with the box metric c_m, the derivative term D-hat^T
 // (alpha M^{k+1}) D-hat; a row of D-hat has at most three nonzeros (columns
 // 0, p and its own index).  No quadrature (~30 flops per DOF).
-template <int K>
+template <int K, typename R>
 __device__ void cart_cell_k(const ApplyDev &P, const int c, const double *__restrict__ x,
                             double *__restrict__ y) {
   constexpr int NC0 = ncomp(K), NC1 = ncomp(K + 1);
-  extern __shared__ double sm[];
+  extern __shared__ double smd[];
+  R *sm = reinterpret_cast<R *>(smd);
   const int p = P.p, q1 = p + 1;
   const int tid = threadIdx.x, NT = blockDim.x;
   const int n0 = P.n[0], n1 = P.n[1], n2 = P.n[2];
   const int e0 = c % n0, e1 = (c / n0) % n1, e2 = c / (n0 * n1);
   const double h0 = P.h[3 * c], h1 = P.h[3 * c + 1], h2 = P.h[3 * c + 2];
   const double al = P.alpha[c], be = P.beta[c];
-  const double ba = P.bh_a, bb = P.bh_b;
+  const R ba = rfrom<R>(P.bh_a), bb = rfrom<R>(P.bh_b);
   // coefficient x box metric per component, once per thread (not per element)
-  const double cm00 = be * box_metric(K, 0, h0, h1, h2);
-  const double cm01 = NC0 > 1 ? be * box_metric(K, 1, h0, h1, h2) : 0.0;
-  const double cm02 = NC0 > 1 ? be * box_metric(K, 2, h0, h1, h2) : 0.0;
-  const double cm10 = al * box_metric(K + 1, 0, h0, h1, h2);
-  const double cm11 = NC1 > 1 ? al * box_metric(K + 1, 1, h0, h1, h2) : 0.0;
-  const double cm12 = NC1 > 1 ? al * box_metric(K + 1, 2, h0, h1, h2) : 0.0;
+  const R cm00 = rfrom<R>(be * box_metric(K, 0, h0, h1, h2));
+  const R cm01 = rfrom<R>(NC0 > 1 ? be * box_metric(K, 1, h0, h1, h2) : 0.0);
+  const R cm02 = rfrom<R>(NC0 > 1 ? be * box_metric(K, 2, h0, h1, h2) : 0.0);
+  const R cm10 = rfrom<R>(al * box_metric(K + 1, 0, h0, h1, h2));
+  const R cm11 = rfrom<R>(NC1 > 1 ? al * box_metric(K + 1, 1, h0, h1, h2) : 0.0);
+  const R cm12 = rfrom<R>(NC1 > 1 ? al * box_metric(K + 1, 2, h0, h1, h2) : 0.0);
   // local size of every component of V^K and V^{K+1}
   constexpr int NS0 = K == 0 ? 3 : (K == 1 ? 2 : 1), NS1 = NS0 - 1;
   int sz0 = 1, sz1 = 1;
@@ -583,15 +584,15 @@ __device__ void cart_cell_k(const ApplyDev &P, const int c, const double *__rest
   // D-hat terms: (target t, term s) -> line sums of the interface columns
   constexpr int NTERMS = K == 1 ? 6 : 3;
   const int lmax = q1 * q1;
-  double *D1 = sm;
-  double *xl = D1 + p * q1;
-  double *yl = xl + NC0 * sz0;
-  double *dl = yl + NC0 * sz0;
-  double *dyl = dl + NC1 * sz1;
-  double *ls = dyl + NC1 * sz1;  // NTERMS x lmax x 2
+  R *D1 = sm;
+  R *xl = D1 + p * q1;
+  R *yl = xl + NC0 * sz0;
+  R *dl = yl + NC0 * sz0;
+  R *dyl = dl + NC1 * sz1;
+  R *ls = dyl + NC1 * sz1;  // NTERMS x lmax x 2
   {
     const double *g = P.tabs + P.q * q1 + P.q * p;
-    for (int i = tid; i < p * q1; i += NT) D1[i] = g[i];
+    for (int i = tid; i < p * q1; i += NT) D1[i] = rfrom<R>(g[i]);
   }
   const long long off0 = P.off[0], off1 = NC0 > 1 ? P.off[1] : 0, off2 = NC0 > 1 ? P.off[2] : 0;
   const int *tab0 = P.cidx, *tab1 = P.cidx + NC0 * sz0;
@@ -606,7 +607,7 @@ __device__ void cart_cell_k(const ApplyDev &P, const int c, const double *__rest
                      (s2 && (g2 == 0 || g2 == n2 * p));
     const long long N0 = (long long)n0 * p + s0, N1 = (long long)n1 * p + s1;
     const long long off = m == 0 ? off0 : (m == 1 ? off1 : off2);
-    xl[m * sz0 + i0 + l0 * (i1 + l1 * i2)] = dir ? 0.0 : x[off + g0 + N0 * (g1 + N1 * g2)];
+    xl[m * sz0 + i0 + l0 * (i1 + l1 * i2)] = rfrom<R>(dir ? 0.0 : x[off + g0 + N0 * (g1 + N1 * g2)]);
   }
   __syncthreads();
   // y = beta M^K x;  d = D-hat x (component t of V^{K+1})
@@ -616,28 +617,28 @@ __device__ void cart_cell_k(const ApplyDev &P, const int c, const double *__rest
     const bool s0 = styp(K, m, 0), s1 = styp(K, m, 1), s2 = styp(K, m, 2);
     const int l0 = s0 ? q1 : p, l1 = s1 ? q1 : p;
     yl[m * sz0 + i0 + l0 * (i1 + l1 * i2)] =
-        (m == 0 ? cm00 : (m == 1 ? cm01 : cm02)) *
-        mass_at(xl + m * sz0, s0, s1, s2, i0, i1, i2, l0, l1, p, ba, bb);
+        rmul(m == 0 ? cm00 : (m == 1 ? cm01 : cm02),
+             mass_at(xl + m * sz0, s0, s1, s2, i0, i1, i2, l0, l1, p, ba, bb));
   }
   for (int l = tid; l < NC1 * sz1; l += NT) {
     const int pk = __ldg(tab1 + l);
     const int t = pk >> 24, j0 = pk & 255, j1 = (pk >> 8) & 255, j2 = (pk >> 16) & 255;
     const bool s0 = styp(K + 1, t, 0), s1 = styp(K + 1, t, 1);
     const int l0 = s0 ? q1 : p, l1 = s1 ? q1 : p;
-    double sacc = 0.0;
+    R sacc = rzero(R());
     for (int s = 0; s < c_nterms[K][t]; ++s) {
       const int src = c_terms[K][t][s].src, dr = c_terms[K][t][s].dir, sg = c_terms[K][t][s].sgn;
       // the source component is s-type along dr (p+1 entries) and equal to
       // the target elsewhere
       const int sl0 = dr == 0 ? q1 : l0, sl1 = dr == 1 ? q1 : l1;
-      const double *in = xl + src * sz0;
+      const R *in = xl + src * sz0;
       const int j = dr == 0 ? j0 : (dr == 1 ? j1 : j2);
       const int str = dr == 0 ? 1 : (dr == 1 ? sl0 : sl0 * sl1);
       const int base = (dr == 0 ? 0 : j0) + sl0 * ((dr == 1 ? 0 : j1) + sl1 * (dr == 2 ? 0 : j2));
-      double v = D1[j * q1] * in[base];
-      v = fma(D1[j * q1 + p], in[base + p * str], v);
-      if (j >= 1) v = fma(D1[j * q1 + j], in[base + j * str], v);
-      sacc = sg > 0 ? sacc + v : sacc - v;
+      R v = rmul(D1[j * q1], in[base]);
+      v = rfma(D1[j * q1 + p], in[base + p * str], v);
+      if (j >= 1) v = rfma(D1[j * q1 + j], in[base + j * str], v);
+      sacc = sg > 0 ? radd(sacc, v) : rsub(sacc, v);
     }
     dl[t * sz1 + j0 + l0 * (j1 + l1 * j2)] = sacc;
   }
@@ -649,8 +650,8 @@ __device__ void cart_cell_k(const ApplyDev &P, const int c, const double *__rest
     const bool s0 = styp(K + 1, t, 0), s1 = styp(K + 1, t, 1), s2 = styp(K + 1, t, 2);
     const int l0 = s0 ? q1 : p, l1 = s1 ? q1 : p;
     dyl[t * sz1 + j0 + l0 * (j1 + l1 * j2)] =
-        (t == 0 ? cm10 : (t == 1 ? cm11 : cm12)) *
-        mass_at(dl + t * sz1, s0, s1, s2, j0, j1, j2, l0, l1, p, ba, bb);
+        rmul(t == 0 ? cm10 : (t == 1 ? cm11 : cm12),
+             mass_at(dl + t * sz1, s0, s1, s2, j0, j1, j2, l0, l1, p, ba, bb));
   }
   __syncthreads();
   // line sums of D-hat^T's interface rows: for every term (t, s) and every
@@ -668,12 +669,12 @@ __device__ void cart_cell_k(const ApplyDev &P, const int c, const double *__rest
     const int a = line % la, b = line / la;
     const int c0 = dr == 0 ? 0 : a, c1 = dr == 0 ? a : (dr == 1 ? 0 : b), c2 = dr == 2 ? 0 : b;
     const int str = dr == 0 ? 1 : (dr == 1 ? l0 : l0 * l1);
-    const double *in = dyl + t * sz1 + c0 + l0 * (c1 + l1 * c2);
-    double v0 = 0.0, vp = 0.0;
+    const R *in = dyl + t * sz1 + c0 + l0 * (c1 + l1 * c2);
+    R v0 = rzero(R()), vp = rzero(R());
     for (int j = 0; j < p; ++j) {
-      const double dj = in[j * str];
-      v0 = fma(D1[j * q1], dj, v0);
-      vp = fma(D1[j * q1 + p], dj, vp);
+      const R dj = in[j * str];
+      v0 = rfma(D1[j * q1], dj, v0);
+      vp = rfma(D1[j * q1 + p], dj, vp);
     }
     ls[2 * u] = v0;
     ls[2 * u + 1] = vp;
@@ -685,7 +686,7 @@ __device__ void cart_cell_k(const ApplyDev &P, const int c, const double *__rest
     const int m = pk >> 24, i0 = pk & 255, i1 = (pk >> 8) & 255, i2 = (pk >> 16) & 255;
     const bool s0 = styp(K, m, 0), s1 = styp(K, m, 1), s2 = styp(K, m, 2);
     const int l0 = s0 ? q1 : p, l1 = s1 ? q1 : p;
-    double sacc = yl[m * sz0 + i0 + l0 * (i1 + l1 * i2)];
+    R sacc = yl[m * sz0 + i0 + l0 * (i1 + l1 * i2)];
 #pragma unroll
     for (int ts = 0; ts < NTERMS; ++ts) {
       const int t = K == 1 ? ts >> 1 : (K == 0 ? ts : 0), s = K == 1 ? ts & 1 : (K == 0 ? 0 : ts);
@@ -694,7 +695,7 @@ __device__ void cart_cell_k(const ApplyDev &P, const int c, const double *__rest
       // the target component is r-type along dr (p entries), equal elsewhere
       const int tl0 = dr == 0 ? p : l0, tl1 = dr == 1 ? p : l1;
       const int i = dr == 0 ? i0 : (dr == 1 ? i1 : i2);
-      double v;
+      R v;
       if (i == 0 || i == p) {
         const int a = dr == 0 ? i1 : i0, b = dr == 2 ? i1 : i2;
         const int la = dr == 0 ? tl1 : tl0;
@@ -702,9 +703,9 @@ __device__ void cart_cell_k(const ApplyDev &P, const int c, const double *__rest
       } else {
         const int str = dr == 0 ? 1 : (dr == 1 ? tl0 : tl0 * tl1);
         const int base = (dr == 0 ? 0 : i0) + tl0 * ((dr == 1 ? 0 : i1) + tl1 * (dr == 2 ? 0 : i2));
-        v = D1[i * q1 + i] * dyl[t * sz1 + base + i * str];
+        v = rmul(D1[i * q1 + i], dyl[t * sz1 + base + i * str]);
       }
-      sacc = sg > 0 ? sacc + v : sacc - v;
+      sacc = sg > 0 ? radd(sacc, v) : rsub(sacc, v);
     }
     const int g0 = e0 * p + i0, g1 = e1 * p + i1, g2 = e2 * p + i2;
     const bool dir = (s0 && (g0 == 0 || g0 == n0 * p)) || (s1 && (g1 == 0 || g1 == n1 * p)) ||
@@ -712,7 +713,7 @@ __device__ void cart_cell_k(const ApplyDev &P, const int c, const double *__rest
     if (!dir) {
       const long long N0 = (long long)n0 * p + s0, N1 = (long long)n1 * p + s1;
       const long long off = m == 0 ? off0 : (m == 1 ? off1 : off2);
-      atomicAdd(&y[off + g0 + N0 * (g1 + N1 * g2)], sacc);
+      atomicAdd(&y[off + g0 + N0 * (g1 + N1 * g2)], rto(sacc));
     }
   }
 }
@@ -720,7 +721,7 @@ __device__ void cart_cell_k(const ApplyDev &P, const int c, const double *__rest
 template <int K>
 __global__ void __launch_bounds__(kApplyThreads) apply_cart_kernel(ApplyDev P, const double *__restrict__ x,
                                                                    double *__restrict__ y) {
-  cart_cell_k<K>(P, blockIdx.x, x, y);
+  cart_cell_k<K, DF>(P, blockIdx.x, x, y);
 }
 
 // Batched: work[b] = (problem, cell); descriptors in global memory.
@@ -734,9 +735,9 @@ __global__ void __launch_bounds__(kApplyThreads) apply_cart_batch_kernel(const A
   if (threadIdx.x == 0) Ps = descs[w.x];
   __syncthreads();
   if (done && done[Ps.prob]) return;  // converged problem: its y stays 0
-  if (Ps.k == 0) cart_cell_k<0>(Ps, w.y, x, y);
-  else if (Ps.k == 1) cart_cell_k<1>(Ps, w.y, x, y);
-  else cart_cell_k<2>(Ps, w.y, x, y);
+  if (Ps.k == 0) cart_cell_k<0, DF>(Ps, w.y, x, y);
+  else if (Ps.k == 1) cart_cell_k<1, DF>(Ps, w.y, x, y);
+  else cart_cell_k<2, DF>(Ps, w.y, x, y);
 }
 
 // One damped Jacobi sweep of the coarse multigrid: x_out = x_in + w (b - A x_in),
