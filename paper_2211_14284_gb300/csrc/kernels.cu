@@ -99,6 +99,34 @@ __device__ __forceinline__ DF rfrom<DF>(double x) {
 __device__ __forceinline__ double rto(double a) { return a; }
 __device__ __forceinline__ double rto(DF a) { return (double)a.hi + (double)a.lo; }
 
+// Dot-product accumulator: for double-float, the compensated scheme of
+// Ogita, Rump and Oishi (Dot2): the running sum h and a compensation l take
+// every exact product a.hi b.hi = p + e (plus the cross terms) through one
+// two-sum of h and p, and the pair is renormalised once at the end -- about
+// 12 FP32 instructions per term instead of a full double-float FMA's 15.
+template <typename R>
+struct Acc;
+template <>
+struct Acc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+  __device__ __forceinline__ double val() const { return s; }
+};
+template <>
+struct Acc<DF> {
+  float h = 0.f, l = 0.f;
+  __device__ __forceinline__ void add(DF a, DF b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const DF t = two_sum(h, p);
+    h = t.hi;
+    l = __fadd_rn(l, __fadd_rn(t.lo, e));
+  }
+  __device__ __forceinline__ DF val() const { return fast_two_sum(h, l); }
+};
+
 // Store modes of the 1D contractions: out = s, out += s, out -= s, out = -s
 // (the D-hat terms carry signs +-1; no multiply is spent on them).
 enum { SET = 0, ADD = 1, SUB = 2, NEG = 3 };
@@ -118,9 +146,9 @@ __device__ __forceinline__ void pass1(const R *__restrict__ in, R *__restrict__ 
     const int o = idx % O, b = idx / O;
     const R *mi = M + o * I;
     const R *xi = in + b * I;
-    R s = rzero(R());
-    for (int i = 0; i < I; ++i) s = rfma(mi[i], xi[i], s);
-    put<MODE>(out[idx], s);
+    Acc<R> s;
+    for (int i = 0; i < I; ++i) s.add(mi[i], xi[i]);
+    put<MODE>(out[idx], s.val());
   }
 }
 // out[c][o][a] (op)= sum_i M[o][i] in[c][i][a]
@@ -131,9 +159,9 @@ __device__ __forceinline__ void pass2(const R *__restrict__ in, R *__restrict__ 
     const int a = idx % A, o = (idx / A) % O, c = idx / (A * O);
     const R *mi = M + o * I;
     const R *xi = in + c * I * A + a;
-    R s = rzero(R());
-    for (int i = 0; i < I; ++i) s = rfma(mi[i], xi[i * A], s);
-    put<MODE>(out[idx], s);
+    Acc<R> s;
+    for (int i = 0; i < I; ++i) s.add(mi[i], xi[i * A]);
+    put<MODE>(out[idx], s.val());
   }
 }
 // out[o][ba] (op)= sum_i M[o][i] in[i][ba]
@@ -143,9 +171,9 @@ __device__ __forceinline__ void pass3(const R *__restrict__ in, R *__restrict__ 
   for (int idx = threadIdx.x; idx < O * BA; idx += blockDim.x) {
     const int ba = idx % BA, o = idx / BA;
     const R *mi = M + o * I;
-    R s = rzero(R());
-    for (int i = 0; i < I; ++i) s = rfma(mi[i], in[i * BA + ba], s);
-    put<MODE>(out[idx], s);
+    Acc<R> s;
+    for (int i = 0; i < I; ++i) s.add(mi[i], in[i * BA + ba]);
+    put<MODE>(out[idx], s.val());
   }
 }
 
@@ -281,13 +309,15 @@ __device__ __forceinline__ void eo_fwd(const R *__restrict__ in, R *__restrict__
     const int a = idx % A, o = (idx / A) % t.he, c = idx / (A * t.he);
     const R *xv = in + (c * t.n) * A + a;
     const R *er = t.Ec + o * t.nse;
-    R ev = rzero(R());
-    for (int k = 0; k < t.nse; ++k) ev = rfma(er[k], xv[t.se[k] * A], ev);
+    Acc<R> ea;
+    for (int k = 0; k < t.nse; ++k) ea.add(er[k], xv[t.se[k] * A]);
+    const R ev = ea.val();
     R *yv = out + (c * q) * A + a;
     if (o < t.ho) {
       const R *orow = t.Oc + o * t.nso;
-      R od = rzero(R());
-      for (int k = 0; k < t.nso; ++k) od = rfma(orow[k], xv[t.so[k] * A], od);
+      Acc<R> oa;
+      for (int k = 0; k < t.nso; ++k) oa.add(orow[k], xv[t.so[k] * A]);
+      const R od = oa.val();
       put<MODE>(yv[o * A], radd(ev, od));
       put<MODE>(yv[(q - 1 - o) * A], rsub(ev, od));
     } else {
@@ -317,16 +347,16 @@ __device__ __forceinline__ void eo_bwd(const R *__restrict__ w, R *__restrict__ 
     const int a = idx % A, i = (idx / A) % t.n, c = idx / (A * t.n);
     const R *wv = w + (c * q) * A + a;
     const int f = t.fl[i];
-    R se = rzero(R()), so = rzero(R());  // two independent chains
+    Acc<R> se, so;  // two independent chains
     if (f & 1) {
       const R *er = t.ET + i * t.he;
-      for (int o = 0; o < t.he; ++o) se = rfma(er[o], wv[o * A], se);
+      for (int o = 0; o < t.he; ++o) se.add(er[o], wv[o * A]);
     }
     if (f & 2) {
       const R *orow = t.OT + i * t.ho;
-      for (int o = 0; o < t.ho; ++o) so = rfma(orow[o], wv[(q - 1 - o) * A], so);
+      for (int o = 0; o < t.ho; ++o) so.add(orow[o], wv[(q - 1 - o) * A]);
     }
-    put<MODE>(out[idx], radd(se, so));
+    put<MODE>(out[idx], radd(se.val(), so.val()));
   }
 }
 
