@@ -21,7 +21,10 @@ LIB = os.path.join(HERE, "librm.so")
 HOSTLIB = os.path.join(HERE, "librm_host.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 HOST_SOURCES = ["host_basis.cpp", "host_setup.cpp", "host_probe.cpp"]
-DEVICE_SOURCES = ["kernels.cu", "capi.cu", "batch.cu", "learned.cu"]
+DEVICE_SOURCES = ["kernels.cu", "apply_general.cu", "capi.cu", "batch.cu", "learned.cu"]
+# apply_general_part.cu, once per (space k, first degree of four): the
+# compile-time instantiations of the general apply, compiled in parallel
+GENERAL_PARTS = [(k, plo) for k in (0, 1, 2) for plo in (1, 5)]
 
 
 def _nvcc():
@@ -48,10 +51,13 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
         objs.append(o)
         cmds.append(["g++", "-O3", "-std=c++17", "-fPIC", "-fopenmp", "-Wall",
                      "-Wno-unused-function", "-c", os.path.join(CSRC, s), "-o", o])
-    for s in DEVICE_SOURCES:
-        o = os.path.join(OUT, s + ".o")
+    units = [(s, s, []) for s in DEVICE_SOURCES]
+    units += [("apply_general_part.cu", f"apply_general_k{k}_p{plo}.cu",
+               [f"-DRM_GENERAL_K={k}", f"-DRM_GENERAL_PLO={plo}"]) for k, plo in GENERAL_PARTS]
+    for s, name, defs in units:
+        o = os.path.join(OUT, name + ".o")
         objs.append(o)
-        cmd = [nvcc, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-fopenmp",
+        cmd = [nvcc, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-fopenmp", *defs,
                "-c", os.path.join(CSRC, s), "-o", o]
         if ptxas_info:
             cmd.insert(1, "-Xptxas=-v")

@@ -233,8 +233,6 @@ void build_apply(rm_handle *h, const Geometry &geo, const std::vector<double> &a
     throw std::runtime_error("1D tabulations lack the reflection symmetry of the GLL points");
   tabs.insert(tabs.end(), eod.begin(), eod.end());
   ApplyDev &A = h->ad;
-  A.eo_dbls = (int)eod.size();
-  A.eoi = h->upload(eoh);
   Layout L1(k + 1, h->n, p);
   A.k = k;
   A.p = p;
@@ -293,10 +291,11 @@ void build_apply(rm_handle *h, const Geometry &geo, const std::vector<double> &a
       return;
     }
   }
-  A.smem_doubles = (size_t)A.eo_dbls + kEoHeader + 2 * p * (p + 1) + 2 * q + 24 + 2 * A.nloc0 +
-                   2 * A.nloc1 + 3 * q3 + (size_t)q * (p + 1) * (p + 1) + (size_t)q * q * (p + 1);
-  if (A.smem_doubles * sizeof(double) > 227 * 1024)
+  if (p > kMaxGeneralP ||
+      (size_t)general_smem_doubles(k, p) * sizeof(double) > 227 * 1024)
     throw std::runtime_error("degree too high for the general apply kernel's shared memory (p <= 8)");
+  if (!eo_rule_holds(p, eoh, eod))
+    throw std::runtime_error("1D tabulations do not follow the parity pattern the general apply is built for");
   // pullback weights at every quadrature point, computed once on the device
   A.nA = k == 0 ? 1 : 6;
   A.nAB = A.nA + (k == 2 ? 1 : 6);

@@ -24,7 +24,8 @@ struct ApplyDev {
   int nloc0, nloc1;
   const double *X;         // vertices, 3 per vertex
   const double *alpha, *beta;
-  const double *tabs;      // Ts q(p+1) | Tr qp | D1 p(p+1) | xq q | wq q | eo_dbls
+  const double *tabs;      // Ts q(p+1) | Tr qp | D1 p(p+1) | xq q | wq q | reflection-split
+                           // tables of Ts then Tr (eo_tables; general cells)
   const void *G;           // pullback weights per cell and point (metric_kernel),
                            // in the general apply's number type (double-float)
   int nA, nAB;             // entries of stage A, of both stages (1 or 6 each)
@@ -34,12 +35,7 @@ struct ApplyDev {
   const double *h;
   double bh_a, bh_b;
   const int *cidx;         // cart_index_table(k, p)
-  // reflection-split interpolation tables (general cells): eo_tables() of
-  // the s- and r-tabulations; doubles after wq in tabs, headers in eoi
-  int eo_dbls;
-  const int *eoi;
   int prob;                // batched solves: the problem's index
-  size_t smem_doubles;
 };
 
 // s-type test of component m of V^kk in direction d (Sec. 2.4): H(grad) all
@@ -88,6 +84,76 @@ inline std::vector<int> cart_index_table(int k, int p) {
 // (bit 0 even, bit 1 odd).  Doubles: Ec[he][nse], Oc[ho][nso] (compressed
 // columns), ET[n][he], OT[n][ho].
 constexpr int kEoHeader = 6 + 3 * 16;
+
+// The column lists follow from the parity of the FDM bases under x -> -x:
+// the s-type interface pair {0, p} swaps (s_p(x) = s_0(-x), both parts
+// present), the interior s_j is even for odd j and odd for even j, and r_i
+// is even for even i.  The general apply takes the lists as compile-time
+// constants for 1 <= p <= kMaxGeneralP; eo_rule_holds() checks the host
+// tables against them.
+constexpr int kMaxGeneralP = 8;
+__host__ __device__ constexpr int quad_q(int p) { return (3 * (p + 1) + 1) / 2; }
+__host__ __device__ constexpr int eo_n(bool s, int p) { return s ? p + 1 : p; }
+__host__ __device__ constexpr int eo_nse(bool s, int p) { return s ? 2 + p / 2 : (p + 1) / 2; }
+__host__ __device__ constexpr int eo_nso(bool s, int p) { return s ? 2 + (p - 1) / 2 : p / 2; }
+// k-th column with an even (se) or odd (so) part
+__host__ __device__ constexpr int eo_se(bool s, int p, int k) {
+  return s ? (k == 0 ? 0 : (k == eo_nse(s, p) - 1 ? p : 2 * k - 1)) : 2 * k;
+}
+__host__ __device__ constexpr int eo_so(bool s, int p, int k) {
+  return s ? (k == 0 ? 0 : (k == eo_nso(s, p) - 1 ? p : 2 * k)) : 2 * k + 1;
+}
+__host__ __device__ constexpr int eo_fl(bool s, int p, int i) {
+  return s ? ((i == 0 || i == p) ? 3 : ((i & 1) ? 1 : 2)) : ((i & 1) ? 2 : 1);
+}
+// doubles of one table (Ec, Oc, ET, OT)
+__host__ __device__ constexpr int eo_size(bool s, int p) {
+  return ((quad_q(p) + 1) / 2) * (eo_nse(s, p) + eo_n(s, p)) + (quad_q(p) / 2) * (eo_nso(s, p) + eo_n(s, p));
+}
+// The host tables (s-type header then r-type header, doubles dbl) match the
+// rule, and the interface pair has E[o][p] = E[o][0], Od[o][p] = -Od[o][0].
+inline bool eo_rule_holds(int p, const std::vector<int> &hdr, const std::vector<double> &dbl) {
+  if (p < 1 || p > kMaxGeneralP || (int)hdr.size() != 2 * kEoHeader) return false;
+  const int q = quad_q(p), he = (q + 1) / 2, ho = q / 2;
+  for (int t = 0; t < 2; ++t) {
+    const bool s = t == 0;
+    const int *h = hdr.data() + t * kEoHeader;
+    if (h[0] != eo_n(s, p) || h[1] != he || h[2] != ho || h[3] != eo_nse(s, p) || h[4] != eo_nso(s, p) ||
+        h[5] != (s ? 0 : eo_size(true, p)))
+      return false;
+    for (int k = 0; k < h[3]; ++k)
+      if (h[6 + k] != eo_se(s, p, k)) return false;
+    for (int k = 0; k < h[4]; ++k)
+      if (h[22 + k] != eo_so(s, p, k)) return false;
+    for (int i = 0; i < h[0]; ++i)
+      if (h[38 + i] != eo_fl(s, p, i)) return false;
+  }
+  if ((int)dbl.size() != eo_size(true, p) + eo_size(false, p)) return false;
+  const int n = p + 1, oET = he * eo_nse(true, p) + ho * eo_nso(true, p), oOT = oET + n * he;
+  double tmax = 0.0;
+  for (double v : dbl) tmax = v > tmax ? v : (-v > tmax ? -v : tmax);
+  const double tol = 1e-13 * tmax;
+  for (int o = 0; o < he; ++o) {
+    const double d = dbl[oET + p * he + o] - dbl[oET + o];
+    if (d > tol || -d > tol) return false;
+  }
+  for (int o = 0; o < ho; ++o) {
+    const double d = dbl[oOT + p * ho + o] + dbl[oOT + o];
+    if (d > tol || -d > tol) return false;
+  }
+  return true;
+}
+
+// Shared memory of the general apply (doubles): both split tables, D-hat
+// and its transpose, the V^k and V^{k+1} cell blocks (input, output), the
+// point values (3 components) and the two staging buffers.
+__host__ __device__ constexpr int general_smem_doubles(int k, int p) {
+  return eo_size(true, p) + eo_size(false, p) + 2 * p * (p + 1) +
+         2 * ncomp(k) * (styp(k, 0, 0) ? p + 1 : p) * (styp(k, 0, 1) ? p + 1 : p) * (styp(k, 0, 2) ? p + 1 : p) +
+         2 * ncomp(k + 1) * (styp(k + 1, 0, 0) ? p + 1 : p) * (styp(k + 1, 0, 1) ? p + 1 : p) *
+             (styp(k + 1, 0, 2) ? p + 1 : p) +
+         3 * quad_q(p) * quad_q(p) * quad_q(p) + quad_q(p) * (p + 1) * (p + 1) + quad_q(p) * quad_q(p) * (p + 1);
+}
 inline bool eo_tables(const double *T, int q, int n, std::vector<double> &dbl,
                       std::vector<int> &hdr) {
   if (n > 16) return false;
@@ -187,6 +253,8 @@ struct DevPatch {
 long long launch_count();
 void add_launches(long long k);  // for launchers in other files (learned.cu)
 cudaError_t launch_apply(const ApplyDev &A, const double *x, double *y, cudaStream_t s);
+// general cells (apply_general.cu)
+cudaError_t launch_apply_general(const ApplyDev &A, const double *x, double *y, cudaStream_t s);
 cudaError_t launch_metric(const ApplyDev &A, void *G, cudaStream_t s);
 // spmv modes: 0 y = a A x; 1 y += a A x; 2 y = u + a A x; 3 y += a A x with
 // atomic adds (rows shared with other kernels adding concurrently)

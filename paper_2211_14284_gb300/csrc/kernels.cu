@@ -15,7 +15,7 @@
 //   two-pass FP64 reductions.
 #include <atomic>
 
-#include "device.cuh"
+#include "df.cuh"
 
 namespace rmd {
 
@@ -25,514 +25,6 @@ void add_launches(long long k) { g_launches += k; }
 
 namespace {
 
-struct DTerm {
-  int src, dir, sgn;
-};
-__constant__ int c_nterms[3][3] = {{1, 1, 1}, {2, 2, 2}, {3, 0, 0}};
-__constant__ DTerm c_terms[3][3][3] = {
-    {{{0, 0, 1}}, {{0, 1, 1}}, {{0, 2, 1}}},
-    {{{2, 1, 1}, {1, 2, -1}}, {{0, 2, 1}, {2, 0, -1}}, {{1, 0, 1}, {0, 1, -1}}},
-    {{{0, 0, 1}, {1, 1, 1}, {2, 2, 1}}, {}, {}}};
-
-// ---- number types of the general apply --------------------------------------
-// The general apply runs in "double-float" arithmetic: a value is the
-// unevaluated sum hi + lo of two FP32 numbers (|lo| <= ulp(hi) / 2, about 48
-// significant bits), operated on with the error-free transformations of
-// Knuth (two-sum) and Dekker (two-product, here through one FMA).  On GB300
-// the FP32 pipe runs 64x the FP64 rate, so a double-float FMA (~15 FP32
-// instructions) beats one FP64 FMA by ~4x, at ~1e-14 relative accuracy.
-// The same templates instantiate with double.
-struct DF {
-  float hi, lo;
-};
-static_assert(sizeof(DF) == sizeof(double), "DF arrays share the double layout");
-
-// s + e = a + b exactly
-__device__ __forceinline__ DF two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
-}
-// s + e = a + b exactly when |a| >= |b| or a = 0
-__device__ __forceinline__ DF fast_two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-
-__device__ __forceinline__ double rzero(double) { return 0.0; }
-__device__ __forceinline__ DF rzero(DF) { return {0.f, 0.f}; }
-__device__ __forceinline__ double rfma(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ DF rfma(DF a, DF b, DF c) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  float e = fmaf(a.hi, b.hi, -p);  // a.hi b.hi = p + e exactly
-  e = fmaf(a.hi, b.lo, e);
-  e = fmaf(a.lo, b.hi, e);
-  const DF s = two_sum(p, c.hi);
-  return fast_two_sum(s.hi, __fadd_rn(__fadd_rn(s.lo, c.lo), e));
-}
-__device__ __forceinline__ double radd(double a, double b) { return a + b; }
-__device__ __forceinline__ DF radd(DF a, DF b) {
-  const DF s = two_sum(a.hi, b.hi);
-  return fast_two_sum(s.hi, __fadd_rn(__fadd_rn(s.lo, a.lo), b.lo));
-}
-__device__ __forceinline__ double rneg(double a) { return -a; }
-__device__ __forceinline__ DF rneg(DF a) { return {-a.hi, -a.lo}; }
-__device__ __forceinline__ double rsub(double a, double b) { return a - b; }
-__device__ __forceinline__ DF rsub(DF a, DF b) { return radd(a, rneg(b)); }
-__device__ __forceinline__ double rmul(double a, double b) { return a * b; }
-__device__ __forceinline__ DF rmul(DF a, DF b) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  float e = fmaf(a.hi, b.hi, -p);
-  e = fmaf(a.hi, b.lo, e);
-  e = fmaf(a.lo, b.hi, e);
-  return fast_two_sum(p, e);
-}
-template <typename R>
-__device__ __forceinline__ R rfrom(double x);
-template <>
-__device__ __forceinline__ double rfrom<double>(double x) { return x; }
-template <>
-__device__ __forceinline__ DF rfrom<DF>(double x) {
-  const float h = __double2float_rn(x);
-  return {h, __double2float_rn(x - (double)h)};
-}
-__device__ __forceinline__ double rto(double a) { return a; }
-__device__ __forceinline__ double rto(DF a) { return (double)a.hi + (double)a.lo; }
-
-// Dot-product accumulator: for double-float, the compensated scheme of
-// Ogita, Rump and Oishi (Dot2): the running sum h and a compensation l take
-// every exact product a.hi b.hi = p + e (plus the cross terms) through one
-// two-sum of h and p, and the pair is renormalised once at the end -- about
-// 12 FP32 instructions per term instead of a full double-float FMA's 15.
-template <typename R>
-struct Acc;
-template <>
-struct Acc<double> {
-  double s = 0.0;
-  __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
-  __device__ __forceinline__ double val() const { return s; }
-};
-template <>
-struct Acc<DF> {
-  float h = 0.f, l = 0.f;
-  __device__ __forceinline__ void add(DF a, DF b) {
-    const float p = __fmul_rn(a.hi, b.hi);
-    float e = fmaf(a.hi, b.hi, -p);
-    e = fmaf(a.hi, b.lo, e);
-    e = fmaf(a.lo, b.hi, e);
-    const DF t = two_sum(h, p);
-    h = t.hi;
-    l = __fadd_rn(l, __fadd_rn(t.lo, e));
-  }
-  __device__ __forceinline__ DF val() const { return fast_two_sum(h, l); }
-};
-
-// Store modes of the 1D contractions: out = s, out += s, out -= s, out = -s
-// (the D-hat terms carry signs +-1; no multiply is spent on them).
-enum { SET = 0, ADD = 1, SUB = 2, NEG = 3 };
-template <int MODE, typename R>
-__device__ __forceinline__ void put(R &o, R s) {
-  if (MODE == SET) o = s;
-  else if (MODE == ADD) o = radd(o, s);
-  else if (MODE == SUB) o = rsub(o, s);
-  else o = rneg(s);
-}
-
-// out[b][o] (op)= sum_i M[o][i] in[b][i]   (contract the fastest index)
-template <int MODE, typename R>
-__device__ __forceinline__ void pass1(const R *__restrict__ in, R *__restrict__ out,
-                                      const R *__restrict__ M, int O, int I, int NB) {
-  for (int idx = threadIdx.x; idx < O * NB; idx += blockDim.x) {
-    const int o = idx % O, b = idx / O;
-    const R *mi = M + o * I;
-    const R *xi = in + b * I;
-    Acc<R> s;
-    for (int i = 0; i < I; ++i) s.add(mi[i], xi[i]);
-    put<MODE>(out[idx], s.val());
-  }
-}
-// out[c][o][a] (op)= sum_i M[o][i] in[c][i][a]
-template <int MODE, typename R>
-__device__ __forceinline__ void pass2(const R *__restrict__ in, R *__restrict__ out,
-                                      const R *__restrict__ M, int O, int I, int A, int C) {
-  for (int idx = threadIdx.x; idx < C * O * A; idx += blockDim.x) {
-    const int a = idx % A, o = (idx / A) % O, c = idx / (A * O);
-    const R *mi = M + o * I;
-    const R *xi = in + c * I * A + a;
-    Acc<R> s;
-    for (int i = 0; i < I; ++i) s.add(mi[i], xi[i * A]);
-    put<MODE>(out[idx], s.val());
-  }
-}
-// out[o][ba] (op)= sum_i M[o][i] in[i][ba]
-template <int MODE, typename R>
-__device__ __forceinline__ void pass3(const R *__restrict__ in, R *__restrict__ out,
-                                      const R *__restrict__ M, int O, int I, int BA) {
-  for (int idx = threadIdx.x; idx < O * BA; idx += blockDim.x) {
-    const int ba = idx % BA, o = idx / BA;
-    const R *mi = M + o * I;
-    Acc<R> s;
-    for (int i = 0; i < I; ++i) s.add(mi[i], in[i * BA + ba]);
-    put<MODE>(out[idx], s.val());
-  }
-}
-
-// One signed D-hat (or D-hat^T) term along direction dir.
-template <int MODE, typename R>
-__device__ __forceinline__ void dpass(int dir, const R *in, R *out, const R *M, int O, int I,
-                                      const int *ls) {
-  if (dir == 0) pass1<MODE>(in, out, M, O, I, ls[1] * ls[2]);
-  else if (dir == 1) pass2<MODE>(in, out, M, O, I, ls[0], ls[2]);
-  else pass3<MODE>(in, out, M, O, I, ls[0] * ls[1]);
-}
-
-__device__ __forceinline__ void jac(const double *X8, double x0, double x1, double x2, double J[9]) {
-  const double N0[2] = {0.5 * (1.0 - x0), 0.5 * (1.0 + x0)};
-  const double N1[2] = {0.5 * (1.0 - x1), 0.5 * (1.0 + x1)};
-  const double N2[2] = {0.5 * (1.0 - x2), 0.5 * (1.0 + x2)};
-  const double dN[2] = {-0.5, 0.5};
-#pragma unroll
-  for (int i = 0; i < 9; ++i) J[i] = 0.0;
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const int c1 = c & 1, c2 = (c >> 1) & 1, c3 = c >> 2;
-    const double g0 = dN[c1] * N1[c2] * N2[c3];
-    const double g1 = N0[c1] * dN[c2] * N2[c3];
-    const double g2 = N0[c1] * N1[c2] * dN[c3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const double v = X8[3 * c + a];
-      J[3 * a + 0] = fma(v, g0, J[3 * a + 0]);
-      J[3 * a + 1] = fma(v, g1, J[3 * a + 1]);
-      J[3 * a + 2] = fma(v, g2, J[3 * a + 2]);
-    }
-  }
-}
-
-// Pullback weight of kk-forms (Sec. 3.1) times cw = coefficient x quadrature
-// weight: kk = 0: det J; kk = 3: 1/det J; kk = 1: det J J^-1 J^-T =
-// adj(J) adj(J)^T / det J; kk = 2: J^T J / det J.  Symmetric entries are
-// returned as (00, 11, 22, 01, 02, 12).
-__device__ __forceinline__ int point_weight(int kk, double cw, const double J[9], double W[6]) {
-  const double det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
-                     J[2] * (J[3] * J[7] - J[4] * J[6]);
-  if (kk == 0) { W[0] = cw * det; return 1; }
-  const double s = cw / det;
-  if (kk == 3) { W[0] = s; return 1; }
-  double A[9];
-  if (kk == 1) {  // rows of the adjugate
-    A[0] = J[4] * J[8] - J[5] * J[7];
-    A[1] = J[2] * J[7] - J[1] * J[8];
-    A[2] = J[1] * J[5] - J[2] * J[4];
-    A[3] = J[5] * J[6] - J[3] * J[8];
-    A[4] = J[0] * J[8] - J[2] * J[6];
-    A[5] = J[2] * J[3] - J[0] * J[5];
-    A[6] = J[3] * J[7] - J[4] * J[6];
-    A[7] = J[1] * J[6] - J[0] * J[7];
-    A[8] = J[0] * J[4] - J[1] * J[3];
-  } else {        // columns of J as rows
-    A[0] = J[0]; A[1] = J[3]; A[2] = J[6];
-    A[3] = J[1]; A[4] = J[4]; A[5] = J[7];
-    A[6] = J[2]; A[7] = J[5]; A[8] = J[8];
-  }
-  const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
-#pragma unroll
-  for (int e = 0; e < 6; ++e)
-    W[e] = s * (A[3 * ia[e]] * A[3 * ib[e]] + A[3 * ia[e] + 1] * A[3 * ib[e] + 1] +
-                A[3 * ia[e] + 2] * A[3 * ib[e] + 2]);
-  return 6;
-}
-
-// Setup: the weights of both stages at every quadrature point of every cell,
-// G[cell][entry][point], entries = stage A (V^k, beta) then stage B
-// (V^{k+1}, alpha), stored in the apply's number type R.
-template <typename R>
-__global__ void metric_kernel(ApplyDev P, R *__restrict__ G) {
-  const int p = P.p, q = P.q, q3 = q * q * q;
-  const int c = blockIdx.x;
-  const int e[3] = {c % P.n[0], (c / P.n[0]) % P.n[1], c / (P.n[0] * P.n[1])};
-  __shared__ double X8[24];
-  if (threadIdx.x < 24) {
-    const int corner = threadIdx.x / 3, comp = threadIdx.x % 3;
-    const int c1 = corner & 1, c2 = (corner >> 1) & 1, c3 = corner >> 2;
-    const long long v = (e[0] + c1) + (long long)(P.n[0] + 1) * ((e[1] + c2) + (long long)(P.n[1] + 1) * (e[2] + c3));
-    X8[threadIdx.x] = P.X[3 * v + comp];
-  }
-  __syncthreads();
-  const double *xq = P.tabs + q * (p + 1) + q * p + p * (p + 1);
-  const double *wq = xq + q;
-  R *Gc = G + (size_t)c * P.nAB * q3;
-  for (int pt = threadIdx.x; pt < q3; pt += blockDim.x) {
-    const int a1 = pt % q, a2 = (pt / q) % q, a3 = pt / (q * q);
-    double J[9], W[6];
-    jac(X8, xq[a1], xq[a2], xq[a3], J);
-    const double w = wq[a1] * wq[a2] * wq[a3];
-    const int na = point_weight(P.k, P.beta[c] * w, J, W);
-    for (int j = 0; j < na; ++j) Gc[(size_t)j * q3 + pt] = rfrom<R>(W[j]);
-    const int nb = point_weight(P.k + 1, P.alpha[c] * w, J, W);
-    for (int j = 0; j < nb; ++j) Gc[(size_t)(na + j) * q3 + pt] = rfrom<R>(W[j]);
-  }
-}
-
-// Reflection-split interpolation (eo_tables in device.cuh): a view of one
-// table in shared memory.
-template <typename R>
-struct EO {
-  int n, he, ho, nse, nso;
-  const R *Ec, *Oc, *ET, *OT;
-  const int *se, *so, *fl;
-};
-template <typename R>
-__device__ __forceinline__ EO<R> eo_view(const int *h, const R *base) {
-  EO<R> t;
-  t.n = h[0];
-  t.he = h[1];
-  t.ho = h[2];
-  t.nse = h[3];
-  t.nso = h[4];
-  t.Ec = base + h[5];
-  t.Oc = t.Ec + t.he * t.nse;
-  t.ET = t.Oc + t.ho * t.nso;
-  t.OT = t.ET + t.n * t.he;
-  t.se = h + 6;
-  t.so = h + 22;
-  t.fl = h + 38;
-  return t;
-}
-// out[c][o][a] (op)= sum_i T[o][i] in[c][i][a]  (i < n functions, o < q points):
-// one thread per mirror pair of points, the even and odd halves of T.
-template <int MODE, typename R>
-__device__ __forceinline__ void eo_fwd(const R *__restrict__ in, R *__restrict__ out,
-                                       const EO<R> &t, int q, int C, int A) {
-  const int tot = C * t.he * A;
-  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-    const int a = idx % A, o = (idx / A) % t.he, c = idx / (A * t.he);
-    const R *xv = in + (c * t.n) * A + a;
-    const R *er = t.Ec + o * t.nse;
-    Acc<R> ea;
-    for (int k = 0; k < t.nse; ++k) ea.add(er[k], xv[t.se[k] * A]);
-    const R ev = ea.val();
-    R *yv = out + (c * q) * A + a;
-    if (o < t.ho) {
-      const R *orow = t.Oc + o * t.nso;
-      Acc<R> oa;
-      for (int k = 0; k < t.nso; ++k) oa.add(orow[k], xv[t.so[k] * A]);
-      const R od = oa.val();
-      put<MODE>(yv[o * A], radd(ev, od));
-      put<MODE>(yv[(q - 1 - o) * A], rsub(ev, od));
-    } else {
-      put<MODE>(yv[o * A], ev);  // the middle point of an odd q
-    }
-  }
-}
-// In place along the point index of w[c][o][a]: w_o <- w_o + w_{q-1-o},
-// w_{q-1-o} <- w_o - w_{q-1-o} (o < ho); the middle point stays.
-template <typename R>
-__device__ __forceinline__ void eo_fold(R *w, const EO<R> &t, int q, int C, int A) {
-  const int tot = C * t.ho * A;
-  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-    const int a = idx % A, o = (idx / A) % t.ho, c = idx / (A * t.ho);
-    R *wv = w + (c * q) * A + a;
-    const R u = wv[o * A], v = wv[(q - 1 - o) * A];
-    wv[o * A] = radd(u, v);
-    wv[(q - 1 - o) * A] = rsub(u, v);
-  }
-}
-// out[c][i][a] (op)= sum_o T[o][i] w[c][o][a] for a folded w (eo_fold).
-template <int MODE, typename R>
-__device__ __forceinline__ void eo_bwd(const R *__restrict__ w, R *__restrict__ out,
-                                       const EO<R> &t, int q, int C, int A) {
-  const int tot = C * t.n * A;
-  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-    const int a = idx % A, i = (idx / A) % t.n, c = idx / (A * t.n);
-    const R *wv = w + (c * q) * A + a;
-    const int f = t.fl[i];
-    Acc<R> se, so;  // two independent chains
-    if (f & 1) {
-      const R *er = t.ET + i * t.he;
-      for (int o = 0; o < t.he; ++o) se.add(er[o], wv[o * A]);
-    }
-    if (f & 2) {
-      const R *orow = t.OT + i * t.ho;
-      for (int o = 0; o < t.ho; ++o) so.add(orow[o], wv[(q - 1 - o) * A]);
-    }
-    put<MODE>(out[idx], radd(se.val(), so.val()));
-  }
-}
-
-// Multiply the reference values at every point by the stored weight:
-// scalar (n = 1) or symmetric 3x3 (n = 6).
-template <typename R>
-__device__ __forceinline__ void apply_weight(const R *__restrict__ Gc, int n, R *U, int q3) {
-  for (int pt = threadIdx.x; pt < q3; pt += blockDim.x) {
-    if (n == 1) {
-      U[pt] = rmul(U[pt], Gc[pt]);
-    } else {
-      const R w00 = Gc[pt], w11 = Gc[q3 + pt], w22 = Gc[2 * q3 + pt];
-      const R w01 = Gc[3 * q3 + pt], w02 = Gc[4 * q3 + pt], w12 = Gc[5 * q3 + pt];
-      const R u0 = U[pt], u1 = U[q3 + pt], u2 = U[2 * q3 + pt];
-      U[pt] = rfma(w00, u0, rfma(w01, u1, rmul(w02, u2)));
-      U[q3 + pt] = rfma(w01, u0, rfma(w11, u1, rmul(w12, u2)));
-      U[2 * q3 + pt] = rfma(w02, u0, rfma(w12, u1, rmul(w22, u2)));
-    }
-  }
-}
-
-template <typename R>
-__global__ void __launch_bounds__(kApplyThreadsGeneral) apply_kernel(ApplyDev P, const double *__restrict__ x,
-                                                              double *__restrict__ y) {
-  extern __shared__ double smd[];
-  R *sm = reinterpret_cast<R *>(smd);
-  const int p = P.p, q = P.q, q3 = q * q * q;
-  R *EOd = sm;
-  int *EOi = reinterpret_cast<int *>(EOd + P.eo_dbls);
-  R *D1 = EOd + P.eo_dbls + kEoHeader;
-  R *D1T = D1 + p * (p + 1);
-  R *xl = D1T + p * (p + 1) + 2 * q + 24;  // (2q + 24 entries unused)
-  R *yl = xl + P.nloc0;
-  R *dl = yl + P.nloc0;
-  R *dyl = dl + P.nloc1;
-  R *U = dyl + P.nloc1;
-  R *SA = U + 3 * q3;
-  R *SB = SA + q * (p + 1) * (p + 1);
-  const int tid = threadIdx.x, NT = blockDim.x;
-  const int c = blockIdx.x;
-  const int e[3] = {c % P.n[0], (c / P.n[0]) % P.n[1], c / (P.n[0] * P.n[1])};
-  {
-    const double *g = P.tabs + q * (p + 1) + q * p;
-    for (int i = tid; i < p * (p + 1); i += NT) {
-      D1[i] = rfrom<R>(g[i]);
-      D1T[(i % (p + 1)) * p + i / (p + 1)] = rfrom<R>(g[i]);
-    }
-    g += p * (p + 1) + 2 * q;
-    for (int i = tid; i < P.eo_dbls; i += NT) EOd[i] = rfrom<R>(g[i]);
-    for (int i = tid; i < 2 * kEoHeader; i += NT) EOi[i] = P.eoi[i];
-  }
-  // gather (Dirichlet entries read as 0)
-  for (int l = tid; l < P.nloc0; l += NT) {
-    int m = 0;
-    while (m + 1 < P.nc0 && l >= P.loff0[m + 1]) ++m;
-    int r = l - P.loff0[m];
-    const int i1 = r % P.ld0[m][0];
-    r /= P.ld0[m][0];
-    const int i2 = r % P.ld0[m][1], i3 = r / P.ld0[m][1];
-    const int g1 = e[0] * p + i1, g2 = e[1] * p + i2, g3 = e[2] * p + i3;
-    const int g[3] = {g1, g2, g3};
-    bool dir = false;
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-      if (P.t0[m][d] == 's' && (g[d] == 0 || g[d] == P.n[d] * p)) dir = true;
-    xl[l] = rfrom<R>(dir ? 0.0 : x[P.off[m] + g1 + (long long)P.N[m][0] * (g2 + (long long)P.N[m][1] * g3)]);
-    yl[l] = rzero(R());
-  }
-  __syncthreads();
-  const EO<R> Es = eo_view(EOi, EOd), Er = eo_view(EOi + kEoHeader, EOd);
-  // ---- stage A: (v, beta u) on V^k ----
-  for (int m = 0; m < P.nc0; ++m) {
-    const int *ld = P.ld0[m];
-    const EO<R> &T0 = P.t0[m][0] == 's' ? Es : Er, &T1 = P.t0[m][1] == 's' ? Es : Er,
-             &T2 = P.t0[m][2] == 's' ? Es : Er;
-    eo_fwd<SET>(xl + P.loff0[m], SA, T0, q, ld[1] * ld[2], 1);
-    __syncthreads();
-    eo_fwd<SET>(SA, SB, T1, q, ld[2], q);
-    __syncthreads();
-    eo_fwd<SET>(SB, U + m * q3, T2, q, 1, q * q);
-    __syncthreads();
-  }
-  apply_weight(static_cast<const R *>(P.G) + (size_t)c * P.nAB * q3, P.nA, U, q3);
-  __syncthreads();
-  for (int m = 0; m < P.nc0; ++m) {
-    const int *ld = P.ld0[m];
-    const EO<R> &T0 = P.t0[m][0] == 's' ? Es : Er, &T1 = P.t0[m][1] == 's' ? Es : Er,
-             &T2 = P.t0[m][2] == 's' ? Es : Er;
-    eo_fold(U + m * q3, T2, q, 1, q * q);
-    __syncthreads();
-    eo_bwd<SET>(U + m * q3, SB, T2, q, 1, q * q);
-    __syncthreads();
-    eo_fold(SB, T1, q, ld[2], q);
-    __syncthreads();
-    eo_bwd<SET>(SB, SA, T1, q, ld[2], q);
-    __syncthreads();
-    eo_fold(SA, T0, q, ld[1] * ld[2], 1);
-    __syncthreads();
-    eo_bwd<ADD>(SA, yl + P.loff0[m], T0, q, ld[1] * ld[2], 1);
-    __syncthreads();
-  }
-  // ---- stage B: (d v, alpha d u) on V^{k+1}, d = D-hat ----
-  const int k = P.k;
-  for (int t = 0; t < P.nc1; ++t) {
-    for (int s = 0; s < c_nterms[k][t]; ++s) {
-      const DTerm T = c_terms[k][t][s];
-      const R *in = xl + P.loff0[T.src];
-      R *out = dl + P.loff1[t];
-      const int *ls = P.ld0[T.src];
-      if (s == 0 && T.sgn > 0) dpass<SET>(T.dir, in, out, D1, p, p + 1, ls);
-      else if (s == 0) dpass<NEG>(T.dir, in, out, D1, p, p + 1, ls);
-      else if (T.sgn > 0) dpass<ADD>(T.dir, in, out, D1, p, p + 1, ls);
-      else dpass<SUB>(T.dir, in, out, D1, p, p + 1, ls);
-      __syncthreads();
-    }
-  }
-  for (int t = 0; t < P.nc1; ++t) {
-    const int *ld = P.ld1[t];
-    const EO<R> &T0 = P.t1[t][0] == 's' ? Es : Er, &T1 = P.t1[t][1] == 's' ? Es : Er,
-             &T2 = P.t1[t][2] == 's' ? Es : Er;
-    eo_fwd<SET>(dl + P.loff1[t], SA, T0, q, ld[1] * ld[2], 1);
-    __syncthreads();
-    eo_fwd<SET>(SA, SB, T1, q, ld[2], q);
-    __syncthreads();
-    eo_fwd<SET>(SB, U + t * q3, T2, q, 1, q * q);
-    __syncthreads();
-  }
-  apply_weight(static_cast<const R *>(P.G) + ((size_t)c * P.nAB + P.nA) * q3, P.nAB - P.nA, U, q3);
-  __syncthreads();
-  for (int t = 0; t < P.nc1; ++t) {
-    const int *ld = P.ld1[t];
-    const EO<R> &T0 = P.t1[t][0] == 's' ? Es : Er, &T1 = P.t1[t][1] == 's' ? Es : Er,
-             &T2 = P.t1[t][2] == 's' ? Es : Er;
-    eo_fold(U + t * q3, T2, q, 1, q * q);
-    __syncthreads();
-    eo_bwd<SET>(U + t * q3, SB, T2, q, 1, q * q);
-    __syncthreads();
-    eo_fold(SB, T1, q, ld[2], q);
-    __syncthreads();
-    eo_bwd<SET>(SB, SA, T1, q, ld[2], q);
-    __syncthreads();
-    eo_fold(SA, T0, q, ld[1] * ld[2], 1);
-    __syncthreads();
-    eo_bwd<SET>(SA, dyl + P.loff1[t], T0, q, ld[1] * ld[2], 1);
-    __syncthreads();
-  }
-  for (int t = 0; t < P.nc1; ++t) {
-    for (int s = 0; s < c_nterms[k][t]; ++s) {
-      const DTerm T = c_terms[k][t][s];
-      const R *in = dyl + P.loff1[t];
-      R *out = yl + P.loff0[T.src];
-      const int *lt = P.ld1[t];
-      if (T.sgn > 0) dpass<ADD>(T.dir, in, out, D1T, p + 1, p, lt);
-      else dpass<SUB>(T.dir, in, out, D1T, p + 1, p, lt);
-      __syncthreads();
-    }
-  }
-  // scatter-add (Dirichlet rows skipped)
-  for (int l = tid; l < P.nloc0; l += NT) {
-    int m = 0;
-    while (m + 1 < P.nc0 && l >= P.loff0[m + 1]) ++m;
-    int r = l - P.loff0[m];
-    const int i1 = r % P.ld0[m][0];
-    r /= P.ld0[m][0];
-    const int i2 = r % P.ld0[m][1], i3 = r / P.ld0[m][1];
-    const int g[3] = {e[0] * p + i1, e[1] * p + i2, e[2] * p + i3};
-    bool dir = false;
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-      if (P.t0[m][d] == 's' && (g[d] == 0 || g[d] == P.n[d] * p)) dir = true;
-    if (!dir)
-      atomicAdd(&y[P.off[m] + g[0] + (long long)P.N[m][0] * (g[1] + (long long)P.N[m][1] * g[2])], rto(yl[l]));
-  }
-}
-
-// ---------------------------------------------------------------------------
 // ---------------------------------------------------------------------------
 // Cartesian cells (axis-aligned boxes with constant alpha, beta): the cell
 // matrix is a Kronecker sum of the 1D FDM factors (Sec. 2.2-2.4).  The mass
@@ -1140,13 +632,6 @@ inline int grid_for(long long n, int threads) {
 
 }  // namespace
 
-cudaError_t launch_metric(const ApplyDev &A, void *G, cudaStream_t s) {
-  const int ncell = A.n[0] * A.n[1] * A.n[2];
-  metric_kernel<DF><<<ncell, 256, 0, s>>>(A, static_cast<DF *>(G));
-  g_launches += 1;
-  return cudaGetLastError();
-}
-
 cudaError_t launch_apply(const ApplyDev &A, const double *x, double *y, cudaStream_t s) {
   const int ncell = A.n[0] * A.n[1] * A.n[2];
   if (A.cartesian) {
@@ -1166,12 +651,7 @@ cudaError_t launch_apply(const ApplyDev &A, const double *x, double *y, cudaStre
     g_launches += 1;
     return cudaGetLastError();
   }
-  const size_t smem = A.smem_doubles * sizeof(double);
-  cudaError_t err = cudaFuncSetAttribute(apply_kernel<DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (err != cudaSuccess) return err;
-  apply_kernel<DF><<<ncell, kApplyThreadsGeneral, smem, s>>>(A, x, y);
-  g_launches += 1;
-  return cudaGetLastError();
+  return launch_apply_general(A, x, y, s);
 }
 
 template <typename VT>
