@@ -99,6 +99,13 @@ struct rm_handle {
   // recording of r_0 = R_0 r for training (device, rec_cap x nc)
   double *rec = nullptr;
   int rec_cap = 0, rec_n = 0;
+  // z = B r on the solver's own r, z captured once as a CUDA graph (the
+  // branch streams' fork and join become graph edges) for the corrector
+  // mode it was captured in; replayed every CG iteration
+  cudaGraphExec_t pgraph = nullptr;
+  int pgraph_mode = -1;
+  long long pgraph_launches = 0;
+  cudaStream_t cap = nullptr;  // capture stream (the caller's may be the legacy one)
 
   template <typename T>
   T *dalloc(size_t count) {
@@ -121,6 +128,7 @@ struct rm_handle {
     return upload(f);
   }
   ~rm_handle() {
+    if (pgraph) cudaGraphExecDestroy(pgraph);
     if (net) rmn::destroy(net);
     for (void *a : allocs) cudaFree(a);
     if (hscal) cudaFreeHost(hscal);
@@ -132,6 +140,7 @@ struct rm_handle {
       if (join[i]) cudaEventDestroy(join[i]);
     }
     if (fork) cudaEventDestroy(fork);
+    if (cap) cudaStreamDestroy(cap);
   }
 };
 
@@ -689,6 +698,7 @@ int rm_setup(rm_handle **out, int space, const rm_mesh *mesh, int p, const doubl
       CK(cudaStreamCreateWithFlags(&h->br[i], cudaStreamNonBlocking));
       CK(cudaEventCreateWithFlags(&h->join[i], cudaEventDisableTiming));
     }
+    CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
     CK(cudaDeviceSynchronize());
   } catch (const CudaError &e) {
     return fail(nullptr, RM_ERR_CUDA, std::string("rm_setup: ") + e.what());
@@ -782,6 +792,41 @@ int rm_solve(rm_handle *h, const double *b, double *x, rm_info *info) {
     CK(launch_dot(n, h->z, h->z, h->partial, h->scal, S_BB, s));
     CK(launch_dot(n, h->r, h->r, h->partial, h->scal, S_RR, s));
     timed(1, [&] { precondition(h, h->r, h->z); });
+    // replay the preconditioner as a graph unless it talks to the host (the
+    // learned corrector's judge) or records coarse residuals
+    const bool replay = h->corr_mode != RM_CORRECTOR_LEARNED && !(h->rec && h->rec_n < h->rec_cap);
+    if (replay && (!h->pgraph || h->pgraph_mode != h->corr_mode)) {
+      if (h->pgraph) CK(cudaGraphExecDestroy(h->pgraph));
+      h->pgraph = nullptr;
+      const long long l0 = launch_count();
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeRelaxed));
+      h->stream = h->cap;  // precondition() launches on h->stream
+      try {
+        precondition(h, h->r, h->z);
+      } catch (...) {
+        h->stream = s;
+        cudaStreamEndCapture(h->cap, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+      }
+      h->stream = s;
+      CK(cudaStreamEndCapture(h->cap, &g));
+      h->pgraph_launches = launch_count() - l0;
+      add_launches(-h->pgraph_launches);  // captured, not launched
+      const cudaError_t ei = cudaGraphInstantiate(&h->pgraph, g, 0);
+      cudaGraphDestroy(g);
+      CK(ei);
+      h->pgraph_mode = h->corr_mode;
+    }
+    auto prec = [&] {
+      if (replay) {
+        CK(cudaGraphLaunch(h->pgraph, s));
+        add_launches(h->pgraph_launches);
+      } else {
+        precondition(h, h->r, h->z);
+      }
+    };
     CK(launch_dot(n, h->r, h->z, h->partial, h->scal, S_RZ, s));
     CK(cudaMemcpyAsync(h->pv, h->z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(h->hscal, h->scal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -808,7 +853,7 @@ int rm_solve(rm_handle *h, const double *b, double *x, rm_info *info) {
           if (!(h->hscal[S_PQ] > 0.0)) { status = RM_ERR_BREAKDOWN; break; }
           if (rr <= tol2) { status = RM_OK; break; }
         }
-        timed(1, [&] { precondition(h, h->r, h->z); });
+        timed(1, prec);
         CK(launch_dot2(n, h->r, h->z, h->qv, h->partial, h->scal, flexible, s));
         CK(launch_update_p(n, h->pv, h->z, h->scal, s));
       }
