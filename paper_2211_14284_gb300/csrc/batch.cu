@@ -250,7 +250,7 @@ struct rm_batch {
     DevCsr D;
     D.nrows = (int)c.rid.size();
     double avg = D.nrows ? (double)c.col.size() / D.nrows : 1.0;
-    D.tpr = avg > 24 ? 32 : avg > 12 ? 16 : avg > 6 ? 8 : avg > 3 ? 4 : avg > 1.5 ? 2 : 1;
+    D.tpr = spmv_tpr(avg);
     D.rid = upload(c.rid);
     D.ptr = upload(c.ptr);
     D.col = upload(c.col);

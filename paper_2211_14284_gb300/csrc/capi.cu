@@ -173,7 +173,7 @@ DevCsr upload_csr(rm_handle *h, const Csr &A, const std::vector<int> *rowmap,
   DevCsr D;
   D.nrows = (int)rid.size();
   double avg = D.nrows ? (double)col.size() / D.nrows : 1.0;
-  D.tpr = avg > 24 ? 32 : avg > 12 ? 16 : avg > 6 ? 8 : avg > 3 ? 4 : avg > 1.5 ? 2 : 1;
+  D.tpr = spmv_tpr(avg);
   D.rid = h->upload(rid);
   D.ptr = h->upload(ptr);
   D.col = h->upload(col);

@@ -218,9 +218,17 @@ inline size_t cart_smem_doubles(int k, int p, int nloc0, int nloc1) {
 }
 
 // Compressed sparse rows with explicit row ids (lattice or compact).
+// Threads per row of the CSR SpMV for an average row length avg: each
+// lane takes about four entries (their loads in flight together), few warps
+// per wave of dependent loads; rows of more than 256 entries get a CTA of
+// 256 threads each.
+inline int spmv_tpr(double avg) {
+  return avg > 256 ? 256 : avg > 128 ? 32 : avg > 64 ? 16 : avg > 32 ? 8 : avg > 16 ? 4 : avg > 8 ? 2 : 1;
+}
+
 struct DevCsr {
   int nrows = 0;
-  int tpr = 1;             // threads per row (1..32, power of two)
+  int tpr = 1;             // threads per row (spmv_tpr: 1..32 or 256, power of two)
   int *rid = nullptr;
   int *ptr = nullptr;
   int *col = nullptr;

@@ -307,8 +307,11 @@ __global__ void spmv_kernel(int nrows, const int *__restrict__ rid, const int *_
   // still take part in the shuffles
   const bool live = row < nrows && !(rprob && done[rprob[row]]);
   VT s = 0;
-  if (live)
-    for (int e = ptr[row] + lane; e < ptr[row + 1]; e += TPR) s = fma(val[e], (VT)x[col[e]], s);
+  if (live) {
+    const int e1 = ptr[row + 1];
+#pragma unroll 4
+    for (int e = ptr[row] + lane; e < e1; e += TPR) s = fma(val[e], (VT)x[col[e]], s);
+  }
 #pragma unroll
   for (int off = TPR / 2; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off, TPR);
   if (lane == 0 && live) {
@@ -317,6 +320,38 @@ __global__ void spmv_kernel(int nrows, const int *__restrict__ rid, const int *_
     if (mode == 0) y[r] = v;
     else if (mode == 1) y[r] += v;
     else if (mode == 3) atomicAdd(y + r, v);  // y += a A x beside concurrent atomic adders
+    else y[r] = u[r] + v;
+  }
+}
+
+// The same product with one CTA of kSpmvRowBlock threads per row (rows of
+// hundreds to thousands of entries: the p -> 1 restriction R_0).
+constexpr int kSpmvRowBlock = 256;
+template <typename VT>
+__global__ void __launch_bounds__(kSpmvRowBlock) spmv_row_block_kernel(
+    int nrows, const int *__restrict__ rid, const int *__restrict__ ptr, const int *__restrict__ col,
+    const VT *__restrict__ val, const double *x, double *y, const double *u, int mode, double a,
+    const int *__restrict__ rprob, const int *__restrict__ done) {
+  __shared__ VT part[kSpmvRowBlock / 32];
+  const int row = blockIdx.x;
+  if (rprob && done[rprob[row]]) return;  // uniform over the CTA
+  VT s = 0;
+  const int e1 = ptr[row + 1];
+#pragma unroll 4
+  for (int e = ptr[row] + threadIdx.x; e < e1; e += kSpmvRowBlock) s = fma(val[e], (VT)x[col[e]], s);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    VT t = 0;
+#pragma unroll
+    for (int w = 0; w < kSpmvRowBlock / 32; ++w) t += part[w];
+    const int r = rid[row];
+    const double v = a * (double)t;
+    if (mode == 0) y[r] = v;
+    else if (mode == 1) y[r] += v;
+    else if (mode == 3) atomicAdd(y + r, v);
     else y[r] = u[r] + v;
   }
 }
@@ -667,6 +702,10 @@ static void spmv_dispatch(const DevCsr &M, const double *x, double *y, const dou
     case 4: spmv_kernel<VT, 4><<<grid, threads, 0, s>>>(M.nrows, M.rid, M.ptr, M.col, v, x, y, u, mode, a, M.rprob, M.done); break;
     case 8: spmv_kernel<VT, 8><<<grid, threads, 0, s>>>(M.nrows, M.rid, M.ptr, M.col, v, x, y, u, mode, a, M.rprob, M.done); break;
     case 16: spmv_kernel<VT, 16><<<grid, threads, 0, s>>>(M.nrows, M.rid, M.ptr, M.col, v, x, y, u, mode, a, M.rprob, M.done); break;
+    case kSpmvRowBlock:
+      spmv_row_block_kernel<VT><<<M.nrows, kSpmvRowBlock, 0, s>>>(M.nrows, M.rid, M.ptr, M.col, v, x, y, u, mode, a,
+                                                                  M.rprob, M.done);
+      break;
     default: spmv_kernel<VT, 32><<<grid, threads, 0, s>>>(M.nrows, M.rid, M.ptr, M.col, v, x, y, u, mode, a, M.rprob, M.done); break;
   }
 }
@@ -711,10 +750,11 @@ cudaError_t launch_patches(const DevPatch &F, const double *r, double *z, cudaSt
 cudaError_t launch_jacobi(const DevCsr &A, const double *b, const double *xin, const double *w,
                           double *xout, cudaStream_t s) {
   const int threads = 256;
-  const long long tot = (long long)A.nrows * A.tpr;
+  const int tpr = A.tpr > 32 ? 32 : A.tpr;
+  const long long tot = (long long)A.nrows * tpr;
   const int grid = (int)((tot + threads - 1) / threads);
   const double *v = reinterpret_cast<const double *>(A.val);
-  switch (A.tpr) {
+  switch (tpr) {
     case 1: jacobi_kernel<1><<<grid, threads, 0, s>>>(A.nrows, A.ptr, A.col, v, b, xin, w, xout); break;
     case 2: jacobi_kernel<2><<<grid, threads, 0, s>>>(A.nrows, A.ptr, A.col, v, b, xin, w, xout); break;
     case 4: jacobi_kernel<4><<<grid, threads, 0, s>>>(A.nrows, A.ptr, A.col, v, b, xin, w, xout); break;
