@@ -385,6 +385,7 @@ __global__ void patch_kernel(DevPatch F, const double *__restrict__ r, double *_
       const int i = F.frows[t];
       const int b = F.rowptr[i], d = F.rowptr[i + 1] - 1;
       VT v = xs[i];
+#pragma unroll 4
       for (int e = b; e < d; ++e) v = fma(-L[e], xs[F.col[e]], v);
       xs[i] = v * L[d];
     }
@@ -394,7 +395,9 @@ __global__ void patch_kernel(DevPatch F, const double *__restrict__ r, double *_
     for (int t = F.blev[lv] + threadIdx.x; t < F.blev[lv + 1]; t += blockDim.x) {
       const int j = F.brows[t];
       VT v = xs[j];
-      for (int e = F.tptr[j]; e < F.tptr[j + 1]; ++e) v = fma(-L[F.tpos[e]], xs[F.trow[e]], v);
+      const int e1 = F.tptr[j + 1];
+#pragma unroll 4
+      for (int e = F.tptr[j]; e < e1; ++e) v = fma(-L[F.tpos[e]], xs[F.trow[e]], v);
       xs[j] = v * L[F.rowptr[j + 1] - 1];
     }
     __syncthreads();
@@ -428,7 +431,20 @@ __global__ void patch_inv_kernel(DevPatch F, const double *__restrict__ r, doubl
     const VT *Vb = V + F.boff[b] + i;
     const int *ps = F.pos_slot + p0;
     VT acc = 0;
-    for (int j = 0; j < nb; ++j) acc = fma(Vb[(size_t)j * nb], xs[ps[j]], acc);
+    int j = 0;
+    // eight column loads in flight before their multiply-adds (same order)
+    for (; j + 8 <= nb; j += 8) {
+      VT v[8];
+      int c[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        v[u] = Vb[(size_t)(j + u) * nb];
+        c[u] = ps[j + u];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc = fma(v[u], xs[c[u]], acc);
+    }
+    for (; j < nb; ++j) acc = fma(Vb[(size_t)j * nb], xs[ps[j]], acc);
     ys[t] = acc;
   }
   __syncthreads();
