@@ -356,6 +356,26 @@ __global__ void __launch_bounds__(kSpmvRowBlock) spmv_row_block_kernel(
   }
 }
 
+// xs[s] = r[sm[s]] (0 for slots outside the problem, sm[s] < 0): the slot
+// indices of four rounds are loaded before their gathers.
+template <typename VT>
+__device__ __forceinline__ void gather_slots(const int *__restrict__ sm, int ns, const double *__restrict__ r,
+                                             VT *xs) {
+  const int nt = blockDim.x;
+  int s = threadIdx.x;
+  for (; s + 3 * nt < ns; s += 4 * nt) {
+    int g[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) g[u] = sm[s + u * nt];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) xs[s + u * nt] = g[u] >= 0 ? (VT)r[g[u]] : (VT)0;
+  }
+  for (; s < ns; s += nt) {
+    const int g = sm[s];
+    xs[s] = g >= 0 ? (VT)r[g] : (VT)0;
+  }
+}
+
 // Level-scheduled forward/backward substitution with the template factor.
 // STAGE: the patch's factor values are first copied to shared memory with
 // coalesced loads, so the dependency chain reads only shared memory.  The
@@ -372,12 +392,20 @@ __global__ void patch_kernel(DevPatch F, const double *__restrict__ r, double *_
   const VT *Lg = reinterpret_cast<const VT *>(F.val) + (size_t)blockIdx.x * F.nnz;
   // the factor follows x (ns values of VT, padded to whole doubles)
   VT *Ls = reinterpret_cast<VT *>(smem_raw + (ns * sizeof(VT) + sizeof(double) - 1) / sizeof(double));
-  for (int s = threadIdx.x; s < ns; s += blockDim.x) {
-    const int g = sm[s];
-    xs[s] = g >= 0 ? (VT)r[g] : (VT)0;
+  gather_slots(sm, ns, r, xs);
+  if (STAGE) {
+    // coalesced copy, eight loads per thread in flight
+    const int nnz = F.nnz, nt = blockDim.x;
+    int e = threadIdx.x;
+    for (; e + 7 * nt < nnz; e += 8 * nt) {
+      VT t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t[u] = Lg[e + u * nt];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) Ls[e + u * nt] = t[u];
+    }
+    for (; e < nnz; e += nt) Ls[e] = Lg[e];
   }
-  if (STAGE)
-    for (int e = threadIdx.x; e < F.nnz; e += blockDim.x) Ls[e] = Lg[e];
   const VT *L = STAGE ? Ls : Lg;
   __syncthreads();
   for (int lv = 0; lv < F.nflev; ++lv) {
@@ -420,10 +448,7 @@ __global__ void patch_inv_kernel(DevPatch F, const double *__restrict__ r, doubl
   VT *ys = xs + ns;
   const int *sm = F.slotmap + (size_t)blockIdx.x * ns;
   const VT *V = reinterpret_cast<const VT *>(F.val) + (size_t)blockIdx.x * F.ivals;
-  for (int s = threadIdx.x; s < ns; s += blockDim.x) {
-    const int g = sm[s];
-    xs[s] = g >= 0 ? (VT)r[g] : (VT)0;
-  }
+  gather_slots(sm, ns, r, xs);
   __syncthreads();
   for (int t = threadIdx.x; t < ns; t += blockDim.x) {
     const int b = F.pos_blk[t];
