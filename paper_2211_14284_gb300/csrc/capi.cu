@@ -400,7 +400,8 @@ void corrector_data(rm_handle *h, const CoarseData &cd, const std::vector<double
   h->cl = h->dalloc<double>(h->nc);
   h->cq = h->dalloc<double>(h->nc);
   h->lscal = h->dalloc<double>(8);
-  h->lpart = h->dalloc<double>(2 * kDotBlocks);
+  h->lpart = h->dalloc<double>(kPartialDoubles);
+  CK(cudaMemset(h->lpart, 0, kPartialDoubles * sizeof(double)));
 }
 
 // ce = A_0^-1 cc (dense inverse) or its V(2,2) approximation
@@ -689,7 +690,8 @@ int rm_setup(rm_handle **out, int space, const rm_mesh *mesh, int p, const doubl
     h->pv = h->dalloc<double>(h->size);
     h->qv = h->dalloc<double>(h->size);
     h->scal = h->dalloc<double>(S_COUNT);
-    h->partial = h->dalloc<double>(2 * kDotBlocks);
+    h->partial = h->dalloc<double>(kPartialDoubles);
+    CK(cudaMemset(h->partial, 0, kPartialDoubles * sizeof(double)));
     CK(cudaMallocHost((void **)&h->hscal, S_COUNT * sizeof(double)));
     CK(cudaEventCreate(&h->ev0));
     CK(cudaEventCreate(&h->ev1));

@@ -283,6 +283,9 @@ cudaError_t launch_sub(long long n, const uint8_t *mask, const double *b, const 
 // CG scalars in device memory
 enum { S_RZ = 0, S_PQ, S_RR, S_BB, S_ALPHA, S_BETA, S_RZNEW, S_ZQ, S_COUNT };
 constexpr int kDotBlocks = 592;  // 4 x 148 SMs-worth, fixed for deterministic sums
+// partial buffer of the reductions below: 2 kDotBlocks partial sums and a
+// ticket counter (zero-initialised; the finishing CTA resets it)
+constexpr int kPartialDoubles = 2 * kDotBlocks + 1;
 cudaError_t launch_dot(long long n, const double *a, const double *b, double *partial,
                        double *scal, int slot, cudaStream_t s);
 cudaError_t launch_dot2(long long n, const double *r, const double *z, const double *q,

@@ -518,61 +518,24 @@ __device__ __forceinline__ double block_sum(double v) {
   return v;
 }
 
-__global__ void dot_partial_kernel(long long n, const double *__restrict__ a, const double *__restrict__ b,
-                                   double *__restrict__ partial) {
-  double s = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    s = fma(a[i], b[i], s);
-  s = block_sum(s);
-  if (threadIdx.x == 0) partial[blockIdx.x] = s;
-}
-
-__global__ void dot2_partial_kernel(long long n, const double *__restrict__ r, const double *__restrict__ z,
-                                    const double *__restrict__ q, double *__restrict__ partial) {
-  double s = 0.0, t = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const double zi = z[i];
-    s = fma(r[i], zi, s);
-    t = fma(q[i], zi, t);
-  }
-  s = block_sum(s);
-  t = block_sum(t);
-  if (threadIdx.x == 0) {
-    partial[blockIdx.x] = s;
-    partial[kDotBlocks + blockIdx.x] = t;
-  }
-}
-
-__global__ void update_xr_kernel(long long n, double *__restrict__ x, double *__restrict__ r,
-                                 const double *__restrict__ p, const double *__restrict__ q,
-                                 double *__restrict__ partial, const double *__restrict__ scal) {
-  const double a = scal[S_ALPHA];
-  double s = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    x[i] = fma(a, p[i], x[i]);
-    const double ri = fma(-a, q[i], r[i]);
-    r[i] = ri;
-    s = fma(ri, ri, s);
-  }
-  s = block_sum(s);
-  if (threadIdx.x == 0) partial[blockIdx.x] = s;
-}
-
-__global__ void update_p_kernel(long long n, double *__restrict__ p, const double *__restrict__ z,
-                                const double *__restrict__ scal) {
-  const double b = scal[S_BETA];
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    p[i] = fma(b, p[i], z[i]);
-}
-
-// Fixed-order final sums.  op 0: scal[slot] = sum; op 1: pq -> alpha;
-// op 2: (rz_new, zq) -> beta, rz.
-__global__ void finalize_kernel(const double *__restrict__ partial, double *__restrict__ scal, int slot,
-                                int op, int flexible) {
+// The CTA that finishes last (a ticket counter after the 2 kDotBlocks
+// partials) sums the partials in fixed order -- the order of one CTA of
+// blockDim threads, so the result does not depend on which CTA finishes
+// last -- applies op and resets the counter.  No CTA waits for another.
+// op 0: scal[slot] = sum; op 1: pq -> alpha; op 2: (rz_new, zq) -> beta, rz.
+__device__ __forceinline__ void finish_reduction(double *partial, double *scal, int slot, int op, int flexible) {
+  __shared__ bool last;
+  unsigned int *count = reinterpret_cast<unsigned int *>(partial + 2 * kDotBlocks);
+  __threadfence();  // this CTA's partials before its ticket
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(count, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
   double s = 0.0, t = 0.0;
   for (int i = threadIdx.x; i < kDotBlocks; i += blockDim.x) {
-    s += partial[i];
-    if (op == 2) t += partial[kDotBlocks + i];
+    s += __ldcg(partial + i);
+    if (op == 2) t += __ldcg(partial + kDotBlocks + i);
   }
   s = block_sum(s);
   if (op == 2) t = block_sum(t);
@@ -589,9 +552,60 @@ __global__ void finalize_kernel(const double *__restrict__ partial, double *__re
       scal[S_BETA] = flexible ? -t / scal[S_PQ] : s / rz;
       scal[S_RZ] = s;
     }
+    *count = 0u;
   }
 }
 
+__global__ void dot_kernel(long long n, const double *__restrict__ a, const double *__restrict__ b,
+                           double *__restrict__ partial, double *__restrict__ scal, int slot, int op) {
+  double s = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    s = fma(a[i], b[i], s);
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  finish_reduction(partial, scal, slot, op, 0);
+}
+
+__global__ void dot2_kernel(long long n, const double *__restrict__ r, const double *__restrict__ z,
+                            const double *__restrict__ q, double *__restrict__ partial, double *__restrict__ scal,
+                            int flexible) {
+  double s = 0.0, t = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double zi = z[i];
+    s = fma(r[i], zi, s);
+    t = fma(q[i], zi, t);
+  }
+  s = block_sum(s);
+  t = block_sum(t);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = s;
+    partial[kDotBlocks + blockIdx.x] = t;
+  }
+  finish_reduction(partial, scal, S_RZNEW, 2, flexible);
+}
+
+__global__ void update_xr_kernel(long long n, double *__restrict__ x, double *__restrict__ r,
+                                 const double *__restrict__ p, const double *__restrict__ q,
+                                 double *__restrict__ partial, double *__restrict__ scal) {
+  const double a = scal[S_ALPHA];
+  double s = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    x[i] = fma(a, p[i], x[i]);
+    const double ri = fma(-a, q[i], r[i]);
+    r[i] = ri;
+    s = fma(ri, ri, s);
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  finish_reduction(partial, scal, S_RR, 0, 0);
+}
+
+__global__ void update_p_kernel(long long n, double *__restrict__ p, const double *__restrict__ z,
+                                const double *__restrict__ scal) {
+  const double b = scal[S_BETA];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = fma(b, p[i], z[i]);
+}
 
 // ---- batched (segmented) CG: block b works on chunk[b] = (problem, begin,
 // end) of the concatenated vectors; per-problem scalars scal[prob * S_COUNT];
@@ -843,33 +857,29 @@ cudaError_t launch_sub(long long n, const uint8_t *mask, const double *b, const 
 
 cudaError_t launch_dot(long long n, const double *a, const double *b, double *partial, double *scal,
                        int slot, cudaStream_t s) {
-  dot_partial_kernel<<<kDotBlocks, 256, 0, s>>>(n, a, b, partial);
-  finalize_kernel<<<1, 256, 0, s>>>(partial, scal, slot, 0, 0);
-  g_launches += 2;
+  dot_kernel<<<kDotBlocks, 256, 0, s>>>(n, a, b, partial, scal, slot, 0);
+  g_launches += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_alpha(long long n, const double *p, const double *q, double *partial, double *scal,
                          cudaStream_t s) {
-  dot_partial_kernel<<<kDotBlocks, 256, 0, s>>>(n, p, q, partial);
-  finalize_kernel<<<1, 256, 0, s>>>(partial, scal, S_PQ, 1, 0);
-  g_launches += 2;
+  dot_kernel<<<kDotBlocks, 256, 0, s>>>(n, p, q, partial, scal, S_PQ, 1);
+  g_launches += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_dot2(long long n, const double *r, const double *z, const double *q, double *partial,
                         double *scal, int flexible, cudaStream_t s) {
-  dot2_partial_kernel<<<kDotBlocks, 256, 0, s>>>(n, r, z, q, partial);
-  finalize_kernel<<<1, 256, 0, s>>>(partial, scal, S_RZNEW, 2, flexible);
-  g_launches += 2;
+  dot2_kernel<<<kDotBlocks, 256, 0, s>>>(n, r, z, q, partial, scal, flexible);
+  g_launches += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_update_xr(long long n, double *x, double *r, const double *p, const double *q,
                              double *partial, double *scal, cudaStream_t s) {
   update_xr_kernel<<<kDotBlocks, 256, 0, s>>>(n, x, r, p, q, partial, scal);
-  finalize_kernel<<<1, 256, 0, s>>>(partial, scal, S_RR, 0, 0);
-  g_launches += 2;
+  g_launches += 1;
   return cudaGetLastError();
 }
 
