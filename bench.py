@@ -43,6 +43,7 @@ SPACES = [
 ]
 VARIANTS = {"fp64": dict(precision=0, flexible=0), "mixed_fp32": dict(precision=1, flexible=1)}
 HEADLINE = "mixed_fp32"
+APPLY_TRAFFIC_BYTES = 52_455_168  # ncu capture of the H(grad) general apply (profiles/)
 FP64_PEAK_TFLOPS = 1.20   # measured FP64 FMA throughput of this GB300 pool (FP64 DFMA probe)
 # The general apply computes in double-float (pairs of FP32, ~48 bits) on the
 # FP32 pipe.  Its ceiling from unit counts and clocks: 152 SMs x 128 FP32
@@ -248,7 +249,12 @@ def run_ours(args):
             "kernel": "apply_kernel (sum-factorised operator, double-float on the FP32 pipe)",
             "achieved": achieved, "peak": DF_PEAK_TFLOPS,
             "unit": "TFLOP/s (FP64-equivalent; peak = double-float FMA rate from unit counts)",
-            "frac": achieved / DF_PEAK_TFLOPS, "traffic": None,
+            "frac": achieved / DF_PEAK_TFLOPS,
+            # DRAM bytes of one launch (ncu dram__bytes_read.sum + write.sum,
+            # H(grad) instance, 512 cells): the pullback metric (49.5 MB) plus
+            # the cell gathers and scatters, no re-reads
+            "traffic": APPLY_TRAFFIC_BYTES,
+            "traffic_launch": "apply_kernel<0,7>, 8^3 cells, one launch (ncu)",
             "fp64_pipe_peak": FP64_PEAK_TFLOPS,
             "avg_launch_ms": app_ms / max(app_calls, 1),
             "time_share_of_step": app_ms / ms_h,
