@@ -1,18 +1,16 @@
 // Device kernels of the Riesz-map solvers (sm_103a).
 //
-// * apply_kernel: y = A x, one CTA per cell, the sum-factorised form
-//   A_K = M^k_beta + D-hat^T M^{k+1}_alpha D-hat of Eq. sum-factorization:
-//   the V^k coefficients and their reference exterior derivative D-hat x are
-//   interpolated to the ceil(3(p+1)/2)^3 GLL points by three 1D contractions
-//   staged in shared memory, weighted by the pullback metric of the trilinear
-//   map (Sec. 3.1), contracted back and scatter-added.
+// * apply_cart_kernel<k>: y = A x on axis-aligned cells, where the cell
+//   matrix of Eq. sum-factorization is a Kronecker sum of the 1D FDM factors
+//   (the general-cell apply is in apply_general.cuh).
 // * patch_kernel: z += sum_j R_j^T L_j^-T L_j^-1 R_j r over a patch family
 //   (Eqs. asm-afw, sc-asm-afw, sc-asm-hiptmair): one CTA per patch, level-
 //   scheduled sparse forward/backward substitution in shared memory on the
-//   template pattern shared by all patches of the family.
+//   template pattern shared by all patches of the family; patch_inv_kernel
+//   for exact factors stored as block inverses.
 // * SpMV / GEMV for static condensation (Eq. schur), the Hiptmair gradient
 //   and the p = 1 coarse correction; fused CG updates with deterministic
-//   two-pass FP64 reductions.
+//   fixed-order FP64 reductions finished by the last CTA.
 #include <atomic>
 
 #include "df.cuh"
