@@ -64,6 +64,23 @@ def test_apply_parity(k, n, p, perturb, coef):
     assert np.all(got[dmask] == 0.0)
 
 
+@pytest.mark.parametrize("k,p", [(k, p) for k in (0, 1, 2) for p in range(1, 9)])
+def test_apply_parity_every_instantiation(k, p):
+    """The general-cell apply is one kernel per space k and degree p <= 8:
+    each against the oracle on 2^3 cells around a moved interior vertex.
+    From p = 5 the preconditioner is condensed with ICC factors: the default
+    exact factors of uncondensed patches cost minutes of host setup there
+    (and H(curl) refuses them from p = 7); the apply does not depend on it."""
+    opts = {} if p <= 4 else dict(static_condensation=1, factor=1, decomposition=1 if k == 1 else 0)
+    s, pr = _setup(k, 2, p, 0.12, True, seed=5 + p, **opts)
+    x = inputs.normal_rhs(pr.lat.size, 30 + p)
+    y = torch.zeros(pr.lat.size, dtype=torch.float64, device="cuda")
+    s.apply(_dev(x), y)
+    want = pr.apply(x)
+    got = _host(y)
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
 @pytest.mark.parametrize("k,n,p", [(2, (2, 2, 3), 10), (1, 2, 10), (0, 2, 12)])
 def test_apply_parity_cartesian_high_p(k, n, p):
     """High degrees on Cartesian meshes (the Kronecker kernel): sampled rows
