@@ -79,7 +79,11 @@ typedef struct {
   int precision;           /* rm_precision of the preconditioner data and arithmetic */
   int decomposition;       /* RM_PAFW (vertex stars) or RM_PH (H(curl) only) */
   int static_condensation; /* 1: patches on the interface Schur complement */
-  int factor;              /* RM_CHOL (exact) or RM_ICC (ICC(0) on the SC pattern) */
+  int factor;              /* RM_CHOL (exact) or RM_ICC (ICC(0) on the SC pattern).
+                              Exact factors of uncondensed patches are dense per
+                              block and built on the host at a cost growing with
+                              the cube of the patch size (minutes for H(div) at
+                              p >= 5): condense or take RM_ICC there */
   int coarse;              /* rm_coarse */
   int flexible;            /* 1: flexible CG (Polak-Ribiere beta) */
   double rtol;             /* stop when ||b - A x||_2 <= rtol ||b||_2 (recursive residual) */
@@ -116,8 +120,10 @@ rm_options rm_default_options(void);
  * eigenproblems, auxiliary operator, Schur complement, patch factors,
  * coarse factor) and uploads it.  alpha, beta: host, length nx*ny*nz, or
  * NULL for 1.  stream: a cudaStream_t (NULL = legacy default stream) used by
- * every later call on this handle.  Supported: p in 1..15; RM_PH only for
- * RM_HCURL with static_condensation = 1. */
+ * every later call on this handle.  Supported: p in 1..15 when every cell is
+ * an axis-aligned box, p in 1..8 otherwise (the general-cell apply's shared
+ * memory; larger p returns RM_ERR_ARG); RM_PH only for RM_HCURL with
+ * static_condensation = 1. */
 int rm_setup(rm_handle **h, int space, const rm_mesh *mesh, int p,
              const double *alpha, const double *beta, const rm_options *opt,
              void *stream);
@@ -136,7 +142,11 @@ int rm_precondition(rm_handle *h, const double *r, double *z);
 
 /* Preconditioned (flexible) CG for A x = b.  b: device (Dirichlet entries
  * ignored).  x: device, in = initial guess (zeros = the paper's setting),
- * out = solution.  info may be NULL. */
+ * out = solution.  info may be NULL.  The preconditioner of the iterations
+ * is captured once per corrector mode as a CUDA graph (on a private stream
+ * of the handle) and replayed on the handle's stream; with the learned
+ * corrector or while recording training residuals it runs eagerly.  The
+ * host reads the residual every check_every iterations. */
 int rm_solve(rm_handle *h, const double *b, double *x, rm_info *info);
 
 /* Number of patches, patch slots and factor nonzeros of the relaxation
