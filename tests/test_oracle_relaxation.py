@@ -219,6 +219,31 @@ def test_paper_iterations_p1_unrefined(k, perturb):
     assert its == want
 
 
+@pytest.mark.parametrize("k,kind", [(0, "sc-pafw"), (1, "scph"), (2, "pafw")])
+def test_rescaling_invariance(k, kind):
+    """Sec. 5.1: the iteration counts depend only on alpha / beta -- A, the
+    auxiliary operator, its Schur complement, the patch factors and the
+    coarse operator all scale with (alpha, beta), so (c alpha, c beta) gives
+    the same preconditioned residual history for a fixed right-hand side."""
+    n, p = 2, 3
+    X = inputs.vertices(n, perturb=0.12, seed=4)
+    al = inputs.loguniform_coefficient(n, 0.1, 10, seed=5)
+    be = inputs.loguniform_coefficient(n, 0.1, 10, seed=6)
+    hists = []
+    for c in (1.0, 37.0):
+        pr = Problem(k, n, p, X, c * al, c * be)
+        A = pr.A_free()
+        if kind == "pafw":
+            M = PAFW(pr)
+        else:
+            P = assemble_aux(pr)[pr.free][:, pr.free]
+            M = SCPAFW(pr, P) if kind == "sc-pafw" else SCPH(pr, P)
+        b = inputs.normal_rhs(pr.lat.size, 9)[pr.free]
+        _, info = pcg(A, b, M.apply, rtol=0.0, maxit=6)
+        hists.append(np.array(info["history_natural"]))
+    assert np.allclose(hists[0], hists[1], rtol=1e-8, atol=0.0), hists
+
+
 def test_exact_preconditioner_one_iteration():
     pr = _problem(0, 2, 3)
     A = pr.A_free()
