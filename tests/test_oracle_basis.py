@@ -76,6 +76,27 @@ def test_duality_and_traces(p):
     assert np.all(e.ds(np.array([-1.0]))[0, 1:p] > 0)
 
 
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 7, 8, 11])
+def test_reflection_parity(p):
+    """Under x -> -x the interface pair swaps, s_p(x) = s_0(-x); the interior
+    s_j (the j-th eigenfunction of the interior eigenproblem, Eq. eigs) is
+    even for odd j and odd for even j; r_i is even for even i (r_0 constant,
+    r_j proportional to s_j').  The reflection split of the interpolations
+    at the mirrored GLL points rests on this structure (Sec. 2.2-2.3)."""
+    e = FDM1D(p)
+    x = np.random.default_rng(1).uniform(-1, 1, 23)
+    s, sm = e.s(x), e.s(-x)
+    assert np.allclose(sm[:, p], s[:, 0], atol=1e-12)
+    assert np.allclose(sm[:, 0], s[:, p], atol=1e-12)
+    for j in range(1, p):
+        sign = 1.0 if j % 2 == 1 else -1.0
+        assert np.allclose(sm[:, j], sign * s[:, j], atol=1e-11 * np.abs(s[:, j]).max())
+    r, rm = e.r(x), e.r(-x)
+    for i in range(p):
+        sign = 1.0 if i % 2 == 0 else -1.0
+        assert np.allclose(rm[:, i], sign * r[:, i], atol=1e-11 * np.abs(r[:, i]).max())
+
+
 @pytest.mark.parametrize("p", [1, 2, 4, 7, 11])
 def test_r_orthonormal(p):
     """r-hat is L2-orthonormal, (r_0, r_j) = 0 (Sec. 2.3)."""
