@@ -44,7 +44,7 @@ SPACES = [
 VARIANTS = {"fp64": dict(precision=0, flexible=0), "mixed_fp32": dict(precision=1, flexible=1)}
 HEADLINE = "mixed_fp32"
 APPLY_TRAFFIC_BYTES = 52_455_168  # ncu capture of the H(grad) general apply (profiles/)
-FP64_PEAK_TFLOPS = 1.20   # measured FP64 FMA throughput of this GB300 pool (FP64 DFMA probe)
+FP64_PEAK_TFLOPS = 1.20   # measured FP64 FMA throughput of a GB300 (DFMA throughput probe)
 # The general apply computes in double-float (pairs of FP32, ~48 bits) on the
 # FP32 pipe.  Its ceiling from unit counts and clocks: 152 SMs x 128 FP32
 # lanes x 2.07 GHz = 40.3 T FP32 instructions/s; a double-float FMA (2 FP64-
@@ -78,7 +78,7 @@ def job_value(world: int, steps: int, dofs: int, ms: float) -> float:
 
 # ---------------------------------------------------------------------------
 def apply_flops(k: int, p: int) -> float:
-    """Algorithmic FP64 flops of one sum-factorised apply on one cell:
+    """Algorithmic flops (FP64-equivalent) of one sum-factorised apply on one cell:
     interpolation to and from the q^3 GLL points for V^k and V^{k+1}
     (three 1D contractions each way), D-hat and D-hat^T, and the pointwise
     metric products.  The pullback metric itself is computed once at setup
@@ -248,7 +248,7 @@ def run_ours(args):
     head = summarise(HEADLINE)
     ms_h, stats_h = results[HEADLINE]
     launches = sum(i["kernel_launches"] for (_, i) in stats_h)
-    # dominant kernel: the operator apply (FP64, ALU-bound); its average
+    # dominant kernel: the operator apply (double-float, ALU-bound); its average
     # duration over the timed region, from the solver's own CUDA events
     app_ms = sum(i["apply_ms"] for (_, i) in stats_h)
     app_calls = sum(i["apply_calls"] for (_, i) in stats_h)
