@@ -342,6 +342,9 @@ Csr assemble_aux(const Layout &L, const Geometry &geo, const double *mcoef,
   nthreads = omp_get_max_threads();
 #endif
   std::vector<std::vector<Trip>> trips(nthreads);
+  // a cell whose Jacobian is not positive somewhere; reported after the
+  // parallel region (an exception must not leave it)
+  int bad_cell = -1;
 
 #pragma omp parallel
   {
@@ -377,6 +380,11 @@ Csr assemble_aux(const Layout &L, const Geometry &geo, const double *mcoef,
             double xi[3] = {C.xq[q1], C.xq[q2], C.xq[q3]};
             double J[9], W[9];
             jacobian(X8, xi, J);
+            if (!(det3(J) > 0)) {
+#pragma omp critical
+              bad_cell = c;
+              for (int a = 0; a < 9; ++a) J[a] = (a % 4 == 0) ? 1.0 : 0.0;  // placeholder, discarded
+            }
             double w = C.wq[q1] * C.wq[q2] * C.wq[q3];
             int qi = q1 + q * (q2 + q * q3);
             form_weight(k, J, W);
@@ -482,6 +490,7 @@ Csr assemble_aux(const Layout &L, const Geometry &geo, const double *mcoef,
       ent.clear();
     }
   }
+  if (bad_cell >= 0) throw std::runtime_error("inverted or degenerate cell " + std::to_string(bad_cell));
   std::vector<Trip> all;
   size_t tot = 0;
   for (auto &t : trips) tot += t.size();

@@ -197,3 +197,14 @@ def test_icc_breakdown_agrees(probe):
     P = assemble_aux(pr)[pr.free][:, pr.free]
     with pytest.raises(np.linalg.LinAlgError):
         SCPAFW(pr, P, factor="icc", coarse=False)
+
+
+def test_inverted_cell_is_an_error(probe):
+    """A cell whose trilinear map folds over (negative Jacobian) is reported
+    as an error by the multithreaded assembly, not a process abort."""
+    n = 2
+    X = inputs.vertices(n, seed=1).reshape(n + 1, n + 1, n + 1, 3).copy()
+    X[1, 1, 1] += 1.2 / n  # the interior vertex beyond its neighbours
+    al = inputs.constant_coefficient(n)
+    with pytest.raises(RuntimeError, match="inverted or degenerate cell"):
+        probe.build(0, n, 2, X.reshape(-1, 3), al, al, mode=0, factor=0, coarse=False)
