@@ -65,30 +65,67 @@ void Layout::coords(long long idx, int &m, long long g[3]) const {
   g[2] = r / N[m][1];
 }
 
-Csr csr_from_triplets(int nrows, int ncols, std::vector<Trip> &t) {
+// A key whose integer order is the numeric order of doubles (a total order,
+// NaNs included).
+static inline int64_t total_order_key(double v) {
+  int64_t k;
+  std::memcpy(&k, &v, sizeof k);
+  return k < 0 ? (int64_t)((uint64_t)k ^ 0x7fffffffffffffffULL) : k;
+}
+
+// CSR from lists of triplets (duplicates summed).  The triplets are counted
+// and scattered in parallel, in no particular order; each row is then sorted
+// by column and its duplicates are merged in value order, so the result does
+// not depend on the order of the triplets or on the thread count.  The lists
+// are freed.
+static Csr csr_from_parts(int nrows, int ncols, std::vector<std::vector<Trip>> &parts) {
   Csr A;
   A.nrows = nrows;
   A.ncols = ncols;
+  // chunks of at most 1 << 20 triplets, so that even one list keeps every
+  // thread busy
+  struct Span {
+    const Trip *p;
+    size_t n;
+  };
+  std::vector<Span> spans;
+  for (auto &t : parts)
+    for (size_t a = 0; a < t.size(); a += (size_t)1 << 20)
+      spans.push_back({t.data() + a, std::min(t.size() - a, (size_t)1 << 20)});
+  const int ns = (int)spans.size();
   std::vector<int64_t> cnt(nrows + 1, 0);
-  for (auto &x : t) cnt[x.r + 1]++;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int q = 0; q < ns; ++q)
+    for (size_t a = 0; a < spans[q].n; ++a) {
+      const int r = spans[q].p[a].r;
+#pragma omp atomic
+      cnt[r + 1]++;
+    }
   for (int i = 0; i < nrows; ++i) cnt[i + 1] += cnt[i];
-  std::vector<int> cc(t.size());
-  std::vector<double> vv(t.size());
+  std::vector<int> cc(cnt[nrows]);
+  std::vector<double> vv(cnt[nrows]);
   {
     std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
-    for (auto &x : t) {
-      int64_t p = pos[x.r]++;
-      cc[p] = x.c;
-      vv[p] = x.v;
-    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int q = 0; q < ns; ++q)
+      for (size_t a = 0; a < spans[q].n; ++a) {
+        const Trip &x = spans[q].p[a];
+        int64_t at;
+#pragma omp atomic capture
+        at = pos[x.r]++;
+        cc[at] = x.c;
+        vv[at] = x.v;
+      }
   }
-  std::vector<Trip>().swap(t);
+  for (auto &t : parts) std::vector<Trip>().swap(t);
   A.ptr.assign(nrows + 1, 0);
   std::vector<int64_t> rowlen(nrows, 0);
   // sort & merge per row
 #pragma omp parallel
   {
     std::vector<int> ord;
+    std::vector<int> c2;
+    std::vector<double> v2;
 #pragma omp for schedule(dynamic, 256)
     for (int i = 0; i < nrows; ++i) {
       int64_t b = cnt[i], e = cnt[i + 1];
@@ -96,11 +133,14 @@ Csr csr_from_triplets(int nrows, int ncols, std::vector<Trip> &t) {
       if (len == 0) continue;
       ord.resize(len);
       std::iota(ord.begin(), ord.end(), 0);
-      std::sort(ord.begin(), ord.end(), [&](int a, int c) { return cc[b + a] < cc[b + c]; });
-      std::vector<int> c2;
-      std::vector<double> v2;
-      c2.reserve(len);
-      v2.reserve(len);
+      // duplicates merge in value order, so the sums do not depend on the
+      // order the (multithreaded) producers emitted them in
+      std::sort(ord.begin(), ord.end(), [&](int a, int c) {
+        if (cc[b + a] != cc[b + c]) return cc[b + a] < cc[b + c];
+        return total_order_key(vv[b + a]) < total_order_key(vv[b + c]);
+      });
+      c2.clear();
+      v2.clear();
       for (int a : ord) {
         if (!c2.empty() && c2.back() == cc[b + a])
           v2.back() += vv[b + a];
@@ -119,12 +159,18 @@ Csr csr_from_triplets(int nrows, int ncols, std::vector<Trip> &t) {
   for (int i = 0; i < nrows; ++i) A.ptr[i + 1] = A.ptr[i] + rowlen[i];
   A.col.resize(A.ptr[nrows]);
   A.val.resize(A.ptr[nrows]);
-  for (int i = 0; i < nrows; ++i)
-    for (int64_t a = 0; a < rowlen[i]; ++a) {
-      A.col[A.ptr[i] + a] = cc[cnt[i] + a];
-      A.val[A.ptr[i] + a] = vv[cnt[i] + a];
-    }
+#pragma omp parallel for schedule(dynamic, 1024)
+  for (int i = 0; i < nrows; ++i) {
+    std::copy(cc.begin() + cnt[i], cc.begin() + cnt[i] + rowlen[i], A.col.begin() + A.ptr[i]);
+    std::copy(vv.begin() + cnt[i], vv.begin() + cnt[i] + rowlen[i], A.val.begin() + A.ptr[i]);
+  }
   return A;
+}
+
+Csr csr_from_triplets(int nrows, int ncols, std::vector<Trip> &t) {
+  std::vector<std::vector<Trip>> parts(1);
+  parts[0].swap(t);
+  return csr_from_parts(nrows, ncols, parts);
 }
 
 Csr transpose(const Csr &A) {
@@ -491,16 +537,8 @@ Csr assemble_aux(const Layout &L, const Geometry &geo, const double *mcoef,
     }
   }
   if (bad_cell >= 0) throw std::runtime_error("inverted or degenerate cell " + std::to_string(bad_cell));
-  std::vector<Trip> all;
-  size_t tot = 0;
-  for (auto &t : trips) tot += t.size();
-  all.reserve(tot);
-  for (auto &t : trips) {
-    all.insert(all.end(), t.begin(), t.end());
-    std::vector<Trip>().swap(t);
-  }
   (void)nloc1;
-  return csr_from_triplets(nfree, nfree, all);
+  return csr_from_parts(nfree, nfree, trips);
 }
 
 // ---------------------------------------------------------------------------
@@ -539,6 +577,59 @@ static void invert_small(std::vector<double> &A, int n) {
     }
   }
   A = I;
+}
+
+// CSR from rows computed independently: row_fn(i, cols, vals) fills row i
+// (columns in any order, no duplicates).  The listed rows (increasing) are
+// split into one contiguous range per chunk, computed and column-sorted in
+// parallel and copied into place; every other row is empty.
+template <class RowFn>
+static Csr csr_from_rows(int nrows, int ncols, const std::vector<int> &rows, RowFn row_fn) {
+  Csr A;
+  A.nrows = nrows;
+  A.ncols = ncols;
+  const int nr = (int)rows.size();
+  int nch = 1;
+#ifdef _OPENMP
+  nch = 4 * omp_get_max_threads();
+#endif
+  std::vector<std::vector<int>> tc(nch);
+  std::vector<std::vector<double>> tv(nch);
+  std::vector<int64_t> len(nr, 0);
+  auto lo = [&](int t) { return (int)((int64_t)nr * t / nch); };
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int t = 0; t < nch; ++t) {
+    std::vector<int> c, ord;
+    std::vector<double> v;
+    for (int r = lo(t); r < lo(t + 1); ++r) {
+      c.clear();
+      v.clear();
+      row_fn(rows[r], c, v);
+      ord.resize(c.size());
+      std::iota(ord.begin(), ord.end(), 0);
+      std::sort(ord.begin(), ord.end(), [&](int a, int b) { return c[a] < c[b]; });
+      for (int a : ord) {
+        tc[t].push_back(c[a]);
+        tv[t].push_back(v[a]);
+      }
+      len[r] = (int64_t)c.size();
+    }
+  }
+  A.ptr.assign(nrows + 1, 0);
+  for (int r = 0; r < nr; ++r) A.ptr[rows[r] + 1] = len[r];
+  for (int i = 0; i < nrows; ++i) A.ptr[i + 1] += A.ptr[i];
+  A.col.resize(A.ptr[nrows]);
+  A.val.resize(A.ptr[nrows]);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int t = 0; t < nch; ++t) {
+    if (lo(t) == lo(t + 1)) continue;
+    const int64_t at = A.ptr[rows[lo(t)]];
+    std::copy(tc[t].begin(), tc[t].end(), A.col.begin() + at);
+    std::copy(tv[t].begin(), tv[t].end(), A.val.begin() + at);
+    std::vector<int>().swap(tc[t]);
+    std::vector<double>().swap(tv[t]);
+  }
+  return A;
 }
 
 Condensed condense(const Layout &L, const FreeMap &fm, const Csr &P) {
@@ -597,46 +688,72 @@ Condensed condense(const Layout &L, const FreeMap &fm, const Csr &P) {
       for (int c = 0; c < n; ++c) tb.push_back({ix[a], ix[c], A[a * n + c]});
   }
   R.Binv = csr_from_triplets(nf, nf, tb);
-  // E = P_GI Binv
-  std::vector<Trip> te;
-  for (int g : R.G) {
-    std::unordered_map<int, double> acc;
-    for (int64_t e = P.ptr[g]; e < P.ptr[g + 1]; ++e) {
-      int i = P.col[e];
-      if (!inI[i] || P.val[e] == 0.0) continue;
-      int b = blk_of[i];
-      const auto &ix = blist[b];
-      int n = (int)ix.size();
-      int a = (int)(std::find(ix.begin(), ix.end(), i) - ix.begin());
-      for (int c = 0; c < n; ++c) acc[ix[c]] += P.val[e] * binv[b][a * n + c];
-    }
-    for (auto &kv : acc) te.push_back({g, kv.first, kv.second});
-  }
-  R.E = csr_from_triplets(nf, nf, te);
-  R.Et = transpose(R.E);
-  // S = P_GG - E P_IG
-  int nthreads = 1;
-#ifdef _OPENMP
-  nthreads = omp_get_max_threads();
-#endif
-  std::vector<std::vector<Trip>> ts(nthreads);
-#pragma omp parallel
+  // E = P_GI Binv, row by row (each entry summed in the order of P's row)
   {
-    int tid = 0;
+    int nth = 1;
 #ifdef _OPENMP
-    tid = omp_get_thread_num();
+    nth = omp_get_max_threads();
 #endif
-    std::vector<double> acc(nf, 0.0);
-    std::vector<char> m(nf, 0);
-    std::vector<int> touched;
-#pragma omp for schedule(dynamic, 512)
-    for (int gi = 0; gi < (int)R.G.size(); ++gi) {
-      int g = R.G[gi];
-      touched.clear();
+    std::vector<std::vector<double>> accs(nth);
+    std::vector<std::vector<char>> marks(nth);
+    R.E = csr_from_rows(nf, nf, R.G, [&](int g, std::vector<int> &cols, std::vector<double> &vals) {
+      int t = 0;
+#ifdef _OPENMP
+      t = omp_get_thread_num();
+#endif
+      std::vector<double> &acc = accs[t];
+      std::vector<char> &m = marks[t];
+      if (acc.empty()) {
+        acc.assign(nf, 0.0);
+        m.assign(nf, 0);
+      }
+      for (int64_t e = P.ptr[g]; e < P.ptr[g + 1]; ++e) {
+        int i = P.col[e];
+        if (!inI[i] || P.val[e] == 0.0) continue;
+        int b = blk_of[i];
+        const auto &ix = blist[b];
+        int n = (int)ix.size();
+        int a = (int)(std::find(ix.begin(), ix.end(), i) - ix.begin());
+        for (int c = 0; c < n; ++c) {
+          const int j = ix[c];
+          if (!m[j]) {
+            m[j] = 1;
+            acc[j] = 0.0;
+            cols.push_back(j);
+          }
+          acc[j] += P.val[e] * binv[b][a * n + c];
+        }
+      }
+      for (int j : cols) {
+        vals.push_back(acc[j]);
+        m[j] = 0;
+      }
+    });
+  }
+  R.Et = transpose(R.E);
+  // S = P_GG - E P_IG, row by row
+  {
+    int nth = 1;
+#ifdef _OPENMP
+    nth = omp_get_max_threads();
+#endif
+    std::vector<std::vector<double>> accs(nth);
+    std::vector<std::vector<char>> marks(nth);
+    R.S = csr_from_rows(nf, nf, R.G, [&](int g, std::vector<int> &cols, std::vector<double> &vals) {
+      int t = 0;
+#ifdef _OPENMP
+      t = omp_get_thread_num();
+#endif
+      std::vector<double> &acc = accs[t];
+      std::vector<char> &m = marks[t];
+      if (acc.empty()) {
+        acc.assign(nf, 0.0);
+        m.assign(nf, 0);
+      }
       for (int64_t e = P.ptr[g]; e < P.ptr[g + 1]; ++e) {
         int c = P.col[e];
         if (inI[c]) continue;
-        if (!m[c]) { m[c] = 1; touched.push_back(c); acc[c] = 0.0; }
+        if (!m[c]) { m[c] = 1; cols.push_back(c); acc[c] = 0.0; }
         acc[c] += P.val[e];
       }
       for (int64_t e = R.E.ptr[g]; e < R.E.ptr[g + 1]; ++e) {
@@ -645,19 +762,16 @@ Condensed condense(const Layout &L, const FreeMap &fm, const Csr &P) {
         for (int64_t f = P.ptr[j]; f < P.ptr[j + 1]; ++f) {
           int c = P.col[f];
           if (inI[c]) continue;
-          if (!m[c]) { m[c] = 1; touched.push_back(c); acc[c] = 0.0; }
+          if (!m[c]) { m[c] = 1; cols.push_back(c); acc[c] = 0.0; }
           acc[c] -= ev * P.val[f];
         }
       }
-      for (int c : touched) {
-        ts[tid].push_back({g, c, acc[c]});
+      for (int c : cols) {
+        vals.push_back(acc[c]);
         m[c] = 0;
       }
-    }
+    });
   }
-  std::vector<Trip> all;
-  for (auto &t : ts) all.insert(all.end(), t.begin(), t.end());
-  R.S = csr_from_triplets(nf, nf, all);
   return R;
 }
 

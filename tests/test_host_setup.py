@@ -208,3 +208,49 @@ def test_inverted_cell_is_an_error(probe):
     al = inputs.constant_coefficient(n)
     with pytest.raises(RuntimeError, match="inverted or degenerate cell"):
         probe.build(0, n, 2, X.reshape(-1, 3), al, al, mode=0, factor=0, coarse=False)
+
+
+_DIGEST = r"""
+import hashlib, sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from paper_2211_14284_gb300 import inputs
+from paper_2211_14284_gb300.rm import HostProbe
+n = 3
+X = inputs.vertices(n, perturb=0.12, seed=8)
+al = inputs.loguniform_coefficient(n, 0.1, 10, seed=9)
+be = inputs.loguniform_coefficient(n, 0.1, 10, seed=10)
+h = hashlib.sha256()
+for k, mode in ((0, 1), (1, 2)):
+    hp = HostProbe()
+    hp.build(k, n, 4, X, al, be, mode, 1)
+    for which in (0, 1, 2, 3, 4):
+        for a in hp.csr(which):
+            h.update(np.ascontiguousarray(a).tobytes())
+    for f in hp.families():
+        for key in sorted(f):
+            v = f[key]
+            if isinstance(v, dict):
+                for kk in sorted(v):
+                    h.update(np.ascontiguousarray(v[kk]).tobytes())
+            elif v is not None:
+                h.update(np.ascontiguousarray(v).tobytes())
+print(h.hexdigest())
+"""
+
+
+def test_setup_is_independent_of_the_thread_count():
+    """The multithreaded setup (assembly, condensation, patch factors, coarse
+    operator) gives bit-identical matrices for any number of threads: summed
+    duplicates are merged in a canonical order."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    digests = []
+    for threads in ("1", "3"):
+        env = dict(os.environ, OMP_NUM_THREADS=threads)
+        out = subprocess.run([sys.executable, "-c", _DIGEST, root], env=env, capture_output=True,
+                             text=True, timeout=300, check=True)
+        digests.append(out.stdout.strip())
+    assert digests[0] == digests[1] and len(digests[0]) == 64
