@@ -816,9 +816,11 @@ int rm_solve(rm_handle *h, const double *b, double *x, rm_info *info) {
       CK(cudaStreamEndCapture(h->cap, &g));
       h->pgraph_launches = launch_count() - l0;
       add_launches(-h->pgraph_launches);  // captured, not launched
-      const cudaError_t ei = cudaGraphInstantiate(&h->pgraph, g, 0);
+      cudaGraphExec_t ge = nullptr;
+      const cudaError_t ei = cudaGraphInstantiate(&ge, g, 0);
       cudaGraphDestroy(g);
       CK(ei);
+      h->pgraph = ge;
       h->pgraph_mode = h->corr_mode;
     }
     auto prec = [&] {
