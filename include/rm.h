@@ -8,7 +8,7 @@
  * of Brubeck & Farrell, "Multigrid solvers for the de Rham complex with
  * optimal complexity in polynomial degree" (arXiv 2211.14284), Sec. 1 Eqs.
  * hgrad/hcurl/hdiv, weak form Eq. common_weak_formulation with
- * Gamma_D = boundary of the unit cube.
+ * Gamma_D = boundary of the unit cube (or empty: rm_options.boundary).
  *
  * Discretisation: structured n1 x n2 x n3 hexahedral mesh with trilinear
  * cells, the FDM bases of Sec. 2 (interior functions orthonormal in L2 and
@@ -27,7 +27,8 @@
  * k=2: (s,r,r),(r,s,r),(r,r,s).  Entry (g1,g2,g3) of component m is at
  * offset_m + g1 + N1 (g2 + N2 g3); components are concatenated.  Local
  * index i_d of cell e_d sits at g_d = e_d p + i_d.  Entries with an s-type
- * index g_d in {0, n_d p} are Dirichlet: ignored on input, 0 on output.
+ * index g_d in {0, n_d p} are Dirichlet (RM_BC_DIRICHLET): ignored on input,
+ * 0 on output; with RM_BC_NONE every entry is a DOF.
  *
  * MESH LAYOUT: vertex (a1,a2,a3) at row a1 + (n1+1)(a2 + (n2+1) a3) of a
  * host array of 3 doubles per vertex; cell (e1,e2,e3) has corners
@@ -69,6 +70,26 @@ typedef enum { RM_CHOL = 0, RM_ICC = 1 } rm_factor;
  * geometric multigrid cycle (Galerkin levels, damped Jacobi), as the paper's
  * p-coarse GMG; for coarse spaces too large for the dense inverse. */
 typedef enum { RM_COARSE_NONE = 0, RM_COARSE_P1 = 1, RM_COARSE_GMG = 2 } rm_coarse;
+/* Stopping test of rm_solve (Sec. 5.1).  RM_NORM_L2: the recursive residual,
+ * ||r_k||_2 <= rtol ||b||_2.  RM_NORM_NATURAL: the paper's test, a reduction of
+ * the natural norm of the preconditioned residual by 1/rtol,
+ * sqrt(r_k^T B r_k) <= rtol sqrt(r_0^T B r_0), B the preconditioner.  Both
+ * histories are recorded in either mode (rm_history). */
+typedef enum { RM_NORM_L2 = 0, RM_NORM_NATURAL = 1 } rm_norm;
+/* Arithmetic of the operator apply y = A x (the CG operator; FP64 in and out
+ * in both).  RM_ARITH_FP64: IEEE double throughout.  RM_ARITH_DF64:
+ * double-float -- every value the unevaluated sum of two FP32 numbers (about
+ * 48 significant bits, FP32 exponent range), products and sums by error-free
+ * transformations on the FP32 pipe, which runs at 64x GB300's FP64 rate;
+ * results agree with FP64 to ~1e-14 relative while no input or
+ * intermediate leaves the FP32 exponent range (|v| in ~1e-30 .. 1e38). */
+typedef enum { RM_ARITH_FP64 = 0, RM_ARITH_DF64 = 1 } rm_arith;
+/* Gamma_D of the weak form (Eq. common_weak_formulation).  RM_BC_DIRICHLET:
+ * the whole boundary of the cube (entries with an s-type index on the
+ * boundary are Dirichlet).  RM_BC_NONE: Gamma_D empty, every lattice entry a
+ * DOF (natural boundary conditions; the operator is definite while beta > 0
+ * on a set of positive measure, as in the paper's Maxwell test, Sec. 5.2). */
+typedef enum { RM_BC_DIRICHLET = 0, RM_BC_NONE = 1 } rm_boundary;
 
 typedef struct {
   int nx, ny, nz;          /* cells per direction, each >= 2 */
@@ -86,17 +107,27 @@ typedef struct {
                               p >= 5): condense or take RM_ICC there */
   int coarse;              /* rm_coarse */
   int flexible;            /* 1: flexible CG (Polak-Ribiere beta) */
-  double rtol;             /* stop when ||b - A x||_2 <= rtol ||b||_2 (recursive residual) */
+  double rtol;             /* relative tolerance of the stopping test (norm) */
   int max_it;
   int check_every;         /* iterations between host reads of the residual */
   int profile;             /* 1: time every operator apply and preconditioner call
                               with CUDA events inside rm_solve (reported in rm_info) */
+  int norm;                /* rm_norm of the stopping test (default RM_NORM_L2) */
+  int arith;               /* rm_arith of the operator apply (default RM_ARITH_FP64) */
+  int boundary;            /* rm_boundary (default RM_BC_DIRICHLET) */
 } rm_options;
 
 typedef struct {
   int iterations;
   int status;              /* rm_status of the solve */
   double rel_res_l2;       /* final recursive ||r|| / ||b|| */
+  double rel_res_natural;  /* sqrt(r_k^T B r_k / r_0^T B r_0) at the last iterate whose
+                              preconditioned residual was formed (the final one under
+                              RM_NORM_NATURAL, the one before it under RM_NORM_L2) */
+  int iterations_natural;  /* first k with that ratio <= rtol: the paper's count
+                              (Sec. 5.1); -1 if not reached within the solve */
+  int history_len;         /* entries recorded per history (rm_history) */
+  double setup_s;          /* wall time of rm_setup for this handle */
   double solve_ms;         /* device time of the solve, CUDA events */
   double apply_ms;         /* profile = 1: total time of the operator applies */
   int apply_calls;
@@ -113,7 +144,8 @@ typedef struct {
 typedef struct rm_handle rm_handle;
 
 /* Defaults: FP64, PAFW, no static condensation, exact Cholesky, P1 coarse,
- * CG, rtol 1e-8, max_it 500, check_every 1. */
+ * CG, rtol 1e-8, max_it 500, check_every 1, RM_NORM_L2, RM_ARITH_FP64,
+ * RM_BC_DIRICHLET. */
 rm_options rm_default_options(void);
 
 /* Builds the discretisation and the preconditioner (host FP64 setup: 1D
@@ -131,23 +163,43 @@ int rm_setup(rm_handle **h, int space, const rm_mesh *mesh, int p,
 /* Lattice length (all entries) and number of free (non-Dirichlet) DOFs. */
 int rm_ndofs(const rm_handle *h, long long *lattice, long long *free_dofs);
 
+/* Shape of lattice component comp (VECTOR LAYOUT above; Sec. 2.4): dims[d] =
+ * N_d (n_d p + 1 for an s-type direction, n_d p for an r-type one) and
+ * *offset = the component's first entry in a vector (offset may be NULL).
+ * comp in 0 .. ncomp-1, ncomp = 1 for RM_HGRAD, 3 otherwise; other values
+ * return RM_ERR_ARG. */
+int rm_layout(const rm_handle *h, int comp, int dims[3], long long *offset);
+
 /* y = A x: the matrix-free sum-factorised operator of Eq. sum-factorization
  * on the true (trilinear) geometry, FP64.  x, y: device, lattice length;
  * y is overwritten. */
 int rm_apply(rm_handle *h, const double *x, double *y);
 
 /* z = B r, the additive two-level relaxation (FP64 in/out whatever the
- * precision option).  r, z: device, lattice length; z is overwritten. */
+ * precision option): the vertex-star PAFW sum of Eq. asm-afw, its
+ * statically-condensed form Eq. sc-asm-afw (interior solve, harmonic
+ * extension, Eq. schur), or the SC Pavarino-Hiptmair form Eq.
+ * sc-asm-hiptmair (edge stars plus the gradient of vertex-star potential
+ * solves), each plus the p = 1 coarse correction R_0^T A_0^-1 R_0 of Eq.
+ * asm-afw.  r, z: device, lattice length; z is overwritten. */
 int rm_precondition(rm_handle *h, const double *r, double *z);
 
-/* Preconditioned (flexible) CG for A x = b.  b: device (Dirichlet entries
- * ignored).  x: device, in = initial guess (zeros = the paper's setting),
- * out = solution.  info may be NULL.  The preconditioner of the iterations
- * is captured once per corrector mode as a CUDA graph (on a private stream
- * of the handle) and replayed on the handle's stream; with the learned
- * corrector or while recording training residuals it runs eagerly.  The
- * host reads the residual every check_every iterations. */
+/* Preconditioned (flexible) CG for A x = b (Sec. 5.1: zero initial guess,
+ * relative tolerance rtol; the stopping norm is options.norm).  b: device
+ * (Dirichlet entries ignored).  x: device, in = initial guess (zeros = the
+ * paper's setting), out = solution.  info may be NULL.  The preconditioner of
+ * the iterations is captured once per corrector mode as a CUDA graph (on a
+ * private stream of the handle) and replayed on the handle's stream; with the
+ * learned corrector or while recording training residuals it runs eagerly.
+ * The host reads the stopping quantity every check_every iterations. */
 int rm_solve(rm_handle *h, const double *b, double *x, rm_info *info);
+
+/* Residual history of the last rm_solve on this handle: which = RM_NORM_L2
+ * gives ||r_k|| / ||b|| for k = 0 .. iterations, RM_NORM_NATURAL gives
+ * sqrt(r_k^T B r_k / r_0^T B r_0) for the iterates whose preconditioned
+ * residual was formed.  out: host, cap doubles; *len = entries written
+ * (min(cap, recorded)).  The handle keeps max_it + 1 entries per history. */
+int rm_history(const rm_handle *h, int which, double *out, int cap, int *len);
 
 /* Number of patches, patch slots and factor nonzeros of the relaxation
  * (summed over patch families), for reporting. */
@@ -197,13 +249,18 @@ const char *rm_batch_last_error(const rm_batch *b);
  *
  * The call performs no cudaMalloc, cudaFree or other allocating call.  Its
  * scratch (2 x RM_NOALLOC_MAX_COARSE doubles) is a static device array of the
- * library, present on every GPU that loads it until the process exits.  The
- * first call on each device looks up that array's device address (a one-time
- * set-up); make that first call before any stream capture.  Every call shares
- * the array: calls that overlap on the GPU race on it.  Returns RM_ERR_ARG for
- * a statically condensed handle (whose relaxation needs lattice-sized scratch)
- * or a coarse space larger than RM_NOALLOC_MAX_COARSE.  r, z: device, lattice
- * length, not aliased; z is overwritten. */
+ * library, present on every GPU that loads it until the process exits.  Its
+ * device address is looked up by rm_setup on the handle's device (again by
+ * every rm_setup, so handles created after a cudaDeviceReset see the new
+ * context's address); the call itself only reads it.  Every call shares the
+ * array: calls that overlap on the GPU race on it.  Accepted: handles without
+ * static condensation whose coarse term is the plain p = 1 correction
+ * (RM_COARSE_P1, corrector mode RM_CORRECTOR_PLAIN) or none (RM_COARSE_NONE,
+ * or mode RM_CORRECTOR_OFF), in either precision.  Returns RM_ERR_ARG for a
+ * statically condensed handle (whose relaxation needs lattice-sized
+ * scratch), the coarse multigrid cycle or the learned coarse term (their own
+ * buffers), or a coarse space larger than RM_NOALLOC_MAX_COARSE.  r, z:
+ * device, lattice length, not aliased; z is overwritten. */
 #define RM_NOALLOC_MAX_COARSE 8192
 int rm_precondition_noalloc(rm_handle *h, const double *r, double *z);
 

@@ -456,6 +456,7 @@ class SCPH:
                      problem.alpha, problem.beta)
         B = assemble_aux(p0, mass_coef=np.zeros_like(problem.beta),
                          stiff_coef=problem.beta)
+        self.B = B
         free0 = p0.free
         self.sc0 = Condensed(B[free0][:, free0].tocsr(), p0.lat, free0)
         G0 = free0[self.sc0.G]

@@ -98,7 +98,8 @@ __global__ void metric_kernel(ApplyDev P, R *__restrict__ G) {
 
 cudaError_t launch_metric(const ApplyDev &A, void *G, cudaStream_t s) {
   const int ncell = A.n[0] * A.n[1] * A.n[2];
-  metric_kernel<DF><<<ncell, 256, 0, s>>>(A, static_cast<DF *>(G));
+  if (A.arith) metric_kernel<DF><<<ncell, 256, 0, s>>>(A, static_cast<DF *>(G));
+  else metric_kernel<double><<<ncell, 256, 0, s>>>(A, static_cast<double *>(G));
   add_launches(1);
   return cudaGetLastError();
 }

@@ -313,10 +313,9 @@ __device__ __forceinline__ void cell_io(const ApplyDev &P, const int e[3], const
   });
 }
 
-template <int K, int PP>
+template <int K, int PP, typename R>
 __global__ void __launch_bounds__(kApplyThreadsGeneral) apply_kernel(ApplyDev P, const double *__restrict__ x,
                                                               double *__restrict__ y) {
-  using R = DF;
   constexpr int p = PP, q = quad_q(PP), q3 = q * q * q;
   constexpr int NC0 = ncomp(K), NC1 = ncomp(K + 1), CS0 = csize(K, PP), CS1 = csize(K + 1, PP);
   constexpr int EOS = eo_size(true, PP), EOD = EOS + eo_size(false, PP);
@@ -394,13 +393,18 @@ __global__ void __launch_bounds__(kApplyThreadsGeneral) apply_kernel(ApplyDev P,
   cell_io<true, K, PP>(P, e, x, y, xl, yl);
 }
 
+template <int K, int PP, typename R>
+cudaError_t launch_kpr(const ApplyDev &A, const double *x, double *y, cudaStream_t s) {
+  const size_t smem = general_smem_doubles(K, PP) * sizeof(double);  // sizeof(R) == sizeof(double)
+  cudaError_t err =
+      cudaFuncSetAttribute(apply_kernel<K, PP, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  apply_kernel<K, PP, R><<<A.n[0] * A.n[1] * A.n[2], kApplyThreadsGeneral, smem, s>>>(A, x, y);
+  return cudaGetLastError();
+}
 template <int K, int PP>
 cudaError_t launch_kp(const ApplyDev &A, const double *x, double *y, cudaStream_t s) {
-  const size_t smem = general_smem_doubles(K, PP) * sizeof(double);
-  cudaError_t err = cudaFuncSetAttribute(apply_kernel<K, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (err != cudaSuccess) return err;
-  apply_kernel<K, PP><<<A.n[0] * A.n[1] * A.n[2], kApplyThreadsGeneral, smem, s>>>(A, x, y);
-  return cudaGetLastError();
+  return A.arith ? launch_kpr<K, PP, DF>(A, x, y, s) : launch_kpr<K, PP, double>(A, x, y, s);
 }
 template <int K, int PLO, int... PS>
 cudaError_t launch_range(int p, const ApplyDev &A, const double *x, double *y, cudaStream_t s,

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -204,6 +205,7 @@ struct rm_batch {
   int nprob = 0;
   int vt = 0;
   bool sc = false, ph = false;
+  double setup_s = 0.0;  // wall time of rm_batch_setup
   std::vector<long long> off, off0, coff, size;
   long long N = 0, N0 = 0, NC = 0;
   std::vector<void *> allocs;
@@ -388,10 +390,14 @@ int rm_batch_setup(rm_batch **out, int nprob, const int *space, const rm_mesh *m
   if (nprob > 4096) return bfail(nullptr, RM_ERR_ARG, "rm_batch_setup: at most 4096 problems");
   *out = nullptr;
   std::unique_ptr<rm_batch> B(new rm_batch());
+  const auto t_setup = std::chrono::steady_clock::now();
   try {
     B->opt = opt ? *opt : rm_default_options();
     const rm_options &o = B->opt;
     if (o.precision != RM_FP64 && o.precision != RM_FP32) throw std::invalid_argument("precision");
+    if (o.norm != RM_NORM_L2) throw std::invalid_argument("norm: the batched lock step stops on the l2 residual");
+    if (o.arith != RM_ARITH_FP64 && o.arith != RM_ARITH_DF64) throw std::invalid_argument("arith");
+    if (o.boundary != RM_BC_DIRICHLET) throw std::invalid_argument("boundary: only RM_BC_DIRICHLET");
     B->vt = o.precision == RM_FP32 ? 1 : 0;
     B->nprob = nprob;
     B->sc = o.static_condensation != 0;
@@ -452,6 +458,7 @@ int rm_batch_setup(rm_batch **out, int nprob, const int *space, const rm_mesh *m
           A.p = P.p;
           A.q = quad_points(P.p);
           A.prob = kv.second[gi];
+          A.arith = o.arith == RM_ARITH_DF64 ? 1 : 0;
           for (int d = 0; d < 3; ++d) A.n[d] = P.n[d];
           A.nc0 = P.L.ncomp;
           A.nc1 = L1.ncomp;
@@ -661,6 +668,7 @@ int rm_batch_setup(rm_batch **out, int nprob, const int *space, const rm_mesh *m
     return bfail(nullptr, w.find("breakdown") != std::string::npos ? RM_ERR_BREAKDOWN : RM_ERR_ARG,
                  std::string("rm_batch_setup: ") + w);
   }
+  B->setup_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_setup).count();
   *out = B.release();
   return RM_OK;
 }
@@ -705,8 +713,8 @@ int rm_batch_solve(rm_batch *B, const double *const *bvec, double *const *xvec, 
     int ndone = 0;
     for (int i = 0; i < B->nprob; ++i) {
       const double *sc = B->hscal + i * S_COUNT;
-      B->hdone[i] = (sc[S_RR] <= tol2 * sc[S_BB]) ? 1 : 0;
-      ndone += B->hdone[i];
+      B->hdone[i] = !std::isfinite(sc[S_RR]) ? 2 : (sc[S_RR] <= tol2 * sc[S_BB]) ? 1 : 0;
+      ndone += B->hdone[i] != 0;
     }
     BK(cudaMemcpyAsync(B->done, B->hdone, B->nprob * sizeof(int), cudaMemcpyHostToDevice, s));
     batch_precondition(B, B->r, B->z);
@@ -723,7 +731,7 @@ int rm_batch_solve(rm_batch *B, const double *const *bvec, double *const *xvec, 
       BK(cudaMemcpyAsync(B->hdone, B->done, B->nprob * sizeof(int), cudaMemcpyDeviceToHost, s));
       BK(cudaStreamSynchronize(s));
       ndone = 0;
-      for (int i = 0; i < B->nprob; ++i) ndone += B->hdone[i];
+      for (int i = 0; i < B->nprob; ++i) ndone += B->hdone[i] != 0;
     }
     for (int i = 0; i < B->nprob; ++i)
       BK(cudaMemcpyAsync(xvec[i], B->x + B->off[i], B->size[i] * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -739,12 +747,20 @@ int rm_batch_solve(rm_batch *B, const double *const *bvec, double *const *xvec, 
     for (int i = 0; i < B->nprob; ++i) {
       const double *sc = B->hscal + i * S_COUNT;
       const double rel = sc[S_BB] > 0 ? std::sqrt(sc[S_RR] / sc[S_BB]) : 0.0;
-      const int st = B->hdone[i] ? RM_OK : (std::isfinite(rel) ? RM_ERR_NOT_CONVERGED : RM_ERR_NAN);
+      // the problem's flag: 1 converged, 2 NaN/Inf residual, 3 CG breakdown
+      const int st = B->hdone[i] == 1   ? RM_OK
+                     : B->hdone[i] == 2 ? RM_ERR_NAN
+                     : B->hdone[i] == 3 ? RM_ERR_BREAKDOWN
+                                        : (std::isfinite(rel) ? RM_ERR_NOT_CONVERGED : RM_ERR_NAN);
       if (st != RM_OK) status = st;
       if (infos) {
         infos[i].iterations = hit[i];
         infos[i].status = st;
         infos[i].rel_res_l2 = rel;
+        infos[i].rel_res_natural = -1.0;  // the lock step stops on the l2 residual only
+        infos[i].iterations_natural = -1;
+        infos[i].history_len = 0;
+        infos[i].setup_s = B->setup_s;
         infos[i].solve_ms = ms;
         infos[i].apply_ms = 0.0;
         infos[i].apply_calls = 0;
@@ -760,7 +776,7 @@ int rm_batch_solve(rm_batch *B, const double *const *bvec, double *const *xvec, 
   } catch (const std::exception &e) {
     return bfail(B, RM_ERR_CUDA, e.what());
   }
-  if (status != RM_OK) bfail(B, status, "rm_batch_solve: not every problem converged");
+  if (status != RM_OK) bfail(B, status, "rm_batch_solve: not every problem converged (see infos[i].status)");
   return status;
 }
 

@@ -44,6 +44,36 @@ struct DevBuf {
 };
 }  // namespace
 
+namespace {
+// Scratch of rm_precondition_noalloc: the coarse right-hand side and
+// correction, 2 x RM_NOALLOC_MAX_COARSE doubles = 128 KiB, a file-scope
+// device array present on every GPU that loads the library until exit.
+static __device__ __align__(256) double g_noalloc_scratch[2 * RM_NOALLOC_MAX_COARSE];
+
+std::mutex g_noalloc_mutex;
+double *g_noalloc_ptr[64] = {};  // device address of the array, per device ordinal
+
+// In host code the array's name is only a host-side stand-in; its device
+// address is looked up with the device current.  rm_setup (which may
+// allocate, and runs before any handle exists) calls this every time, so a
+// handle created after a cudaDeviceReset re-reads the address of the new
+// context; rm_precondition_noalloc itself only reads the cached pointer.
+void refresh_noalloc_scratch(int dev) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (dev < 0 || dev >= 64) throw std::runtime_error("device ordinal out of range");
+  void *ptr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess) throw CudaError(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  g_noalloc_ptr[dev] = (double *)ptr;
+}
+double *noalloc_scratch(int dev) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (dev < 0 || dev >= 64 || !g_noalloc_ptr[dev])
+    throw std::runtime_error("no handle was set up on this device");
+  return g_noalloc_ptr[dev];
+}
+}  // namespace
+
 struct rm_handle {
   std::string err;
   cudaStream_t stream = nullptr;
@@ -74,6 +104,11 @@ struct rm_handle {
   double *w = nullptr, *rt = nullptr, *u0 = nullptr, *v0 = nullptr, *cc = nullptr, *ce = nullptr;
   double *r = nullptr, *z = nullptr, *pv = nullptr, *qv = nullptr, *scal = nullptr, *partial = nullptr;
   double *hscal = nullptr;  // pinned
+  // residual histories of the last solve: hrr[k] = (r_k, r_k), hrz[k] = (r_k, B r_k)
+  // (device, max_it + 1 each), and how many entries the solve wrote
+  double *hrr = nullptr, *hrz = nullptr;
+  int nhrr = 0, nhrz = 0;
+  double setup_s = 0.0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<cudaEvent_t> evpool;  // profile = 1: start/stop pairs
   // independent branches of the relaxation (patch families, the Hiptmair
@@ -529,6 +564,9 @@ rm_options rm_default_options(void) {
   o.max_it = 500;
   o.check_every = 1;
   o.profile = 0;
+  o.norm = RM_NORM_L2;
+  o.arith = RM_ARITH_FP64;
+  o.boundary = RM_BC_DIRICHLET;
   return o;
 }
 
@@ -542,6 +580,7 @@ int rm_setup(rm_handle **out, int space, const rm_mesh *mesh, int p, const doubl
   if (mesh->nx < 2 || mesh->ny < 2 || mesh->nz < 2)
     return fail(nullptr, RM_ERR_ARG, "rm_setup: at least 2 cells per direction");
   std::unique_ptr<rm_handle> h(new rm_handle());
+  const auto t_setup = std::chrono::steady_clock::now();
   try {
     h->opt = opt ? *opt : rm_default_options();
     h->stream = (cudaStream_t)stream;
@@ -555,6 +594,10 @@ int rm_setup(rm_handle **out, int space, const rm_mesh *mesh, int p, const doubl
     if (o.decomposition == RM_PH && (space != RM_HCURL || !o.static_condensation))
       throw std::invalid_argument("RM_PH needs RM_HCURL and static_condensation = 1");
     if (o.rtol <= 0 || o.max_it < 1 || o.check_every < 1) throw std::invalid_argument("rtol/max_it/check_every");
+    if (o.norm != RM_NORM_L2 && o.norm != RM_NORM_NATURAL) throw std::invalid_argument("norm");
+    if (o.arith != RM_ARITH_FP64 && o.arith != RM_ARITH_DF64) throw std::invalid_argument("arith");
+    if (o.boundary != RM_BC_DIRICHLET) throw std::invalid_argument("boundary: only RM_BC_DIRICHLET");
+    h->ad.arith = o.arith == RM_ARITH_DF64 ? 1 : 0;
     h->vt = o.precision == RM_FP32 ? 1 : 0;
     h->sc = o.static_condensation != 0;
     h->ph = o.decomposition == RM_PH;
@@ -693,6 +736,8 @@ int rm_setup(rm_handle **out, int space, const rm_mesh *mesh, int p, const doubl
     h->partial = h->dalloc<double>(kPartialDoubles);
     CK(cudaMemset(h->partial, 0, kPartialDoubles * sizeof(double)));
     CK(cudaMallocHost((void **)&h->hscal, S_COUNT * sizeof(double)));
+    h->hrr = h->dalloc<double>((size_t)o.max_it + 1);
+    h->hrz = h->dalloc<double>((size_t)o.max_it + 1);
     CK(cudaEventCreate(&h->ev0));
     CK(cudaEventCreate(&h->ev1));
     CK(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
@@ -702,6 +747,7 @@ int rm_setup(rm_handle **out, int space, const rm_mesh *mesh, int p, const doubl
     }
     CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
     CK(cudaDeviceSynchronize());
+    refresh_noalloc_scratch(dev);
   } catch (const CudaError &e) {
     return fail(nullptr, RM_ERR_CUDA, std::string("rm_setup: ") + e.what());
   } catch (const std::bad_alloc &) {
@@ -713,6 +759,7 @@ int rm_setup(rm_handle **out, int space, const rm_mesh *mesh, int p, const doubl
     int code = w.find("breakdown") != std::string::npos ? RM_ERR_BREAKDOWN : RM_ERR_ARG;
     return fail(nullptr, code, std::string("rm_setup: ") + w);
   }
+  h->setup_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_setup).count();
   *out = h.release();
   return RM_OK;
 }
@@ -729,6 +776,36 @@ int rm_stats(const rm_handle *h, long long *patches, long long *slots, long long
   if (patches) *patches = h->stat_patches;
   if (slots) *slots = h->stat_slots;
   if (factor_nnz) *factor_nnz = h->stat_nnz;
+  return RM_OK;
+}
+
+int rm_layout(const rm_handle *h, int comp, int dims[3], long long *offset) {
+  if (!h || !dims) return fail(nullptr, RM_ERR_ARG, "rm_layout: NULL argument");
+  if (comp < 0 || comp >= h->L.ncomp)
+    return fail(nullptr, RM_ERR_ARG, "rm_layout: component out of range");
+  for (int d = 0; d < 3; ++d) dims[d] = (int)h->L.N[comp][d];
+  if (offset) *offset = h->L.off[comp];
+  return RM_OK;
+}
+
+int rm_history(const rm_handle *h, int which, double *out, int cap, int *len) {
+  if (!h || (!out && cap > 0) || cap < 0) return fail(nullptr, RM_ERR_ARG, "rm_history: bad argument");
+  if (which != RM_NORM_L2 && which != RM_NORM_NATURAL) return fail(nullptr, RM_ERR_ARG, "rm_history: which");
+  const double *src = which == RM_NORM_L2 ? h->hrr : h->hrz;
+  const int nrec = which == RM_NORM_L2 ? h->nhrr : h->nhrz;
+  const int m = std::min(cap, nrec);
+  if (len) *len = m;
+  if (m == 0) return RM_OK;
+  std::vector<double> v(nrec);
+  // the first entry normalises: ||b|| for the l2 history (recorded as b's
+  // masked norm in the scalars), (r_0, B r_0) for the natural one
+  cudaError_t e = cudaMemcpy(v.data(), src, nrec * sizeof(double), cudaMemcpyDeviceToHost);
+  double bb = 0.0;
+  if (e == cudaSuccess && which == RM_NORM_L2)
+    e = cudaMemcpy(&bb, h->scal + S_BB, sizeof(double), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(nullptr, RM_ERR_CUDA, std::string("rm_history: ") + cudaGetErrorString(e));
+  const double d = which == RM_NORM_L2 ? bb : v[0];
+  for (int k = 0; k < m; ++k) out[k] = d > 0.0 ? std::sqrt(std::max(0.0, v[k]) / d) : 0.0;
   return RM_OK;
 }
 
@@ -792,7 +869,9 @@ int rm_solve(rm_handle *h, const double *b, double *x, rm_info *info) {
     CK(launch_sub(n, h->mask, b, h->qv, h->r, s));
     CK(launch_mask_copy(n, h->mask, b, h->z, s));
     CK(launch_dot(n, h->z, h->z, h->partial, h->scal, S_BB, s));
-    CK(launch_dot(n, h->r, h->r, h->partial, h->scal, S_RR, s));
+    CK(launch_dot(n, h->r, h->r, h->partial, h->scal, S_RR, s, h->hrr));
+    h->nhrr = 1;
+    h->nhrz = 0;
     timed(1, [&] { precondition(h, h->r, h->z); });
     // replay the preconditioner as a graph unless it talks to the host (the
     // learned corrector's judge) or records coarse residuals
@@ -831,25 +910,38 @@ int rm_solve(rm_handle *h, const double *b, double *x, rm_info *info) {
         precondition(h, h->r, h->z);
       }
     };
-    CK(launch_dot(n, h->r, h->z, h->partial, h->scal, S_RZ, s));
+    CK(launch_dot(n, h->r, h->z, h->partial, h->scal, S_RZ, s, h->hrz));
+    h->nhrz = 1;
     CK(cudaMemcpyAsync(h->pv, h->z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(h->hscal, h->scal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     const double bb = h->hscal[S_BB];
     const double tol2 = h->opt.rtol * h->opt.rtol * bb;
+    // natural norm (Sec. 5.1): (r_k, B r_k) <= rtol^2 (r_0, B r_0)
+    const bool natural = h->opt.norm == RM_NORM_NATURAL;
+    const double rz0 = h->hscal[S_RZ];
+    const double tol2n = h->opt.rtol * h->opt.rtol * rz0;
     double rr = h->hscal[S_RR];
     if (bb == 0.0) {
       rel = 0.0;
-    } else if (rr <= tol2) {
+    } else if (!std::isfinite(rr) || !std::isfinite(rz0)) {
+      status = RM_ERR_NAN;
+      rel = std::sqrt(rr / bb);
+    } else if (rr == 0.0 || (!natural && rr <= tol2)) {
+      rel = std::sqrt(rr / bb);
+    } else if (natural && !(rz0 > 0.0)) {
+      status = RM_ERR_BREAKDOWN;  // (r_0, B r_0) <= 0: B is not positive definite
       rel = std::sqrt(rr / bb);
     } else {
       status = RM_ERR_NOT_CONVERGED;
       while (it < h->opt.max_it) {
         timed(0, [&] { apply(h, h->pv, h->qv); });
         CK(launch_alpha(n, h->pv, h->qv, h->partial, h->scal, s));
-        CK(launch_update_xr(n, x, h->r, h->pv, h->qv, h->partial, h->scal, s));
+        CK(launch_update_xr(n, x, h->r, h->pv, h->qv, h->partial, h->scal, s, h->hrr + it + 1));
         ++it;
-        if (it % h->opt.check_every == 0 || it == h->opt.max_it) {
+        h->nhrr = it + 1;
+        const bool check = it % h->opt.check_every == 0 || it == h->opt.max_it;
+        if (!natural && check) {
           CK(cudaMemcpyAsync(h->hscal, h->scal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
           CK(cudaStreamSynchronize(s));
           rr = h->hscal[S_RR];
@@ -858,9 +950,20 @@ int rm_solve(rm_handle *h, const double *b, double *x, rm_info *info) {
           if (rr <= tol2) { status = RM_OK; break; }
         }
         timed(1, prec);
-        CK(launch_dot2(n, h->r, h->z, h->qv, h->partial, h->scal, flexible, s));
+        CK(launch_dot2(n, h->r, h->z, h->qv, h->partial, h->scal, flexible, s, h->hrz + it));
+        h->nhrz = it + 1;
+        if (natural && check) {
+          CK(cudaMemcpyAsync(h->hscal, h->scal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+          CK(cudaStreamSynchronize(s));
+          rr = h->hscal[S_RR];
+          const double rz = h->hscal[S_RZ];
+          if (!std::isfinite(rr) || !std::isfinite(rz)) { status = RM_ERR_NAN; break; }
+          if (!(h->hscal[S_PQ] > 0.0)) { status = RM_ERR_BREAKDOWN; break; }
+          if (rz <= tol2n) { status = RM_OK; break; }
+        }
         CK(launch_update_p(n, h->pv, h->z, h->scal, s));
       }
+      if (natural) rr = h->hscal[S_RR];
       rel = std::sqrt(rr / bb);
     }
     CK(cudaEventRecord(h->ev1, s));
@@ -876,10 +979,28 @@ int rm_solve(rm_handle *h, const double *b, double *x, rm_info *info) {
     if (info) info->status = RM_ERR_CUDA;
     return fail(h, RM_ERR_CUDA, e.what());
   }
+  // the natural-norm history: its final ratio and the paper's count
+  double rel_nat = -1.0;
+  int it_nat = -1;
+  if (h->nhrz > 0) {
+    std::vector<double> hz(h->nhrz);
+    if (cudaMemcpy(hz.data(), h->hrz, h->nhrz * sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess &&
+        hz[0] > 0.0) {
+      for (int k = 0; k < h->nhrz; ++k) {
+        const double ratio = std::sqrt(std::max(0.0, hz[k]) / hz[0]);
+        rel_nat = ratio;
+        if (it_nat < 0 && ratio <= h->opt.rtol) it_nat = k;
+      }
+    }
+  }
   if (info) {
     info->iterations = it;
     info->status = status;
     info->rel_res_l2 = rel;
+    info->rel_res_natural = rel_nat;
+    info->iterations_natural = it_nat;
+    info->history_len = h->nhrr;
+    info->setup_s = h->setup_s;
     info->solve_ms = ms;
     info->apply_ms = tk[0];
     info->apply_calls = nk[0];
@@ -896,7 +1017,7 @@ int rm_solve(rm_handle *h, const double *b, double *x, rm_info *info) {
   if (status != RM_OK) {
     const char *why = status == RM_ERR_NOT_CONVERGED ? "max_it reached"
                       : status == RM_ERR_NAN         ? "NaN/Inf residual"
-                                                     : "CG breakdown (p^T A p <= 0)";
+                                                     : "CG breakdown (p^T A p <= 0 or r^T B r <= 0)";
     fail(h, status, std::string("rm_solve: ") + why);
   }
   return status;
@@ -1222,34 +1343,15 @@ int rm_corrector_use(rm_handle *h, int mode, int judge_every, double judge_max) 
 // Allocation-free preconditioner entry point.
 //
 // Its scratch (the restricted residual and the coarse solution of the p = 1
-// correction) lives in this file-scope device array instead of in buffers
-// owned by the handle.  Every GPU that loads the library holds the array
-// (2 x RM_NOALLOC_MAX_COARSE doubles = 128 KiB) until the process exits.  All
-// calls share it and it keeps the last call's contents; both halves are fully
-// overwritten before they are read, so nothing needs clearing.  Calls whose
-// work overlaps on the GPU (on different streams) race on the array.
+// correction) lives in the file-scope device array g_noalloc_scratch instead
+// of in buffers owned by the handle.  Every GPU that loads the library holds
+// the array (2 x RM_NOALLOC_MAX_COARSE doubles = 128 KiB) until the process
+// exits.  Its device address was looked up by rm_setup, so a call only reads
+// the cached pointer.  All calls share the array and it keeps the last call's
+// contents; both halves are fully overwritten before they are read, so
+// nothing needs clearing.  Calls whose work overlaps on the GPU (on different
+// streams) race on the array.
 // ---------------------------------------------------------------------------
-namespace {
-static __device__ __align__(256) double g_noalloc_scratch[2 * RM_NOALLOC_MAX_COARSE];
-
-std::mutex g_noalloc_mutex;
-double *g_noalloc_ptr[64] = {};  // device address of the array, per device ordinal
-
-// In host code the array's name is only a host-side stand-in: the device
-// address is looked up once per device, with that device current.
-double *noalloc_scratch(int dev) {
-  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (dev < 0 || dev >= 64) throw std::runtime_error("device ordinal out of range");
-  if (!g_noalloc_ptr[dev]) {
-    void *ptr = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess)
-      throw CudaError(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_noalloc_ptr[dev] = (double *)ptr;
-  }
-  return g_noalloc_ptr[dev];
-}
-}  // namespace
 
 extern "C" int rm_precondition_noalloc(rm_handle *h, const double *r, double *z) {
   if (!h || !r || !z) return fail(h, RM_ERR_ARG, "rm_precondition_noalloc: NULL argument");
@@ -1262,9 +1364,10 @@ extern "C" int rm_precondition_noalloc(rm_handle *h, const double *r, double *z)
     return fail(h, RM_ERR_ARG,
                 "rm_precondition_noalloc: the coarse multigrid cycle needs per-level vectors; "
                 "use rm_precondition");
-  if (h->corr_mode != RM_CORRECTOR_PLAIN)
+  if (h->corr_mode == RM_CORRECTOR_LEARNED)
     return fail(h, RM_ERR_ARG,
-                "rm_precondition_noalloc: only the plain coarse correction; use rm_precondition");
+                "rm_precondition_noalloc: the learned coarse term needs the network's buffers; "
+                "use rm_precondition");
   if (h->nc > RM_NOALLOC_MAX_COARSE)
     return fail(h, RM_ERR_ARG,
                 "rm_precondition_noalloc: coarse space has " + std::to_string(h->nc) +
@@ -1278,7 +1381,7 @@ extern "C" int rm_precondition_noalloc(rm_handle *h, const double *r, double *z)
     cudaStream_t s = h->stream;
     CK(cudaMemsetAsync(z, 0, h->size * sizeof(double), s));
     for (auto &F : h->fam) CK(launch_patches(F, r, z, s));
-    if (h->nc > 0) {
+    if (h->nc > 0 && h->corr_mode != RM_CORRECTOR_OFF) {
       CK(launch_spmv(h->R0, r, cc, nullptr, 0, 1.0, s));
       CK(launch_gemv(h->nc, h->A0inv, 0, cc, ce, s));
       CK(launch_spmv(h->R0T, ce, z, nullptr, 1, 1.0, s));

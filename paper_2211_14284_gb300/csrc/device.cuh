@@ -36,6 +36,7 @@ struct ApplyDev {
   double bh_a, bh_b;
   const int *cidx;         // cart_index_table(k, p)
   int prob;                // batched solves: the problem's index
+  int arith;               // number type of the apply: 0 double, 1 double-float (DF)
 };
 
 // s-type test of component m of V^kk in direction d (Sec. 2.4): H(grad) all
@@ -286,14 +287,16 @@ constexpr int kDotBlocks = 592;  // 4 x 148 SMs-worth, fixed for deterministic s
 // partial buffer of the reductions below: 2 kDotBlocks partial sums and a
 // ticket counter (zero-initialised; the finishing CTA resets it)
 constexpr int kPartialDoubles = 2 * kDotBlocks + 1;
+// hist (may be null): the reduction's sum is also stored at *hist
 cudaError_t launch_dot(long long n, const double *a, const double *b, double *partial,
-                       double *scal, int slot, cudaStream_t s);
+                       double *scal, int slot, cudaStream_t s, double *hist = nullptr);
 cudaError_t launch_dot2(long long n, const double *r, const double *z, const double *q,
-                        double *partial, double *scal, int flexible, cudaStream_t s);
+                        double *partial, double *scal, int flexible, cudaStream_t s,
+                        double *hist = nullptr);
 cudaError_t launch_alpha(long long n, const double *p, const double *q, double *partial,
                          double *scal, cudaStream_t s);
 cudaError_t launch_update_xr(long long n, double *x, double *r, const double *p, const double *q,
-                             double *partial, double *scal, cudaStream_t s);
+                             double *partial, double *scal, cudaStream_t s, double *hist = nullptr);
 cudaError_t launch_update_p(long long n, double *p, const double *z, const double *scal,
                             cudaStream_t s);
 

@@ -238,10 +238,10 @@ __device__ void cart_cell_k(const ApplyDev &P, const int c, const double *__rest
   }
 }
 
-template <int K>
+template <int K, typename R>
 __global__ void __launch_bounds__(kApplyThreads) apply_cart_kernel(ApplyDev P, const double *__restrict__ x,
                                                                    double *__restrict__ y) {
-  cart_cell_k<K, DF>(P, blockIdx.x, x, y);
+  cart_cell_k<K, R>(P, blockIdx.x, x, y);
 }
 
 // Batched: work[b] = (problem, cell); descriptors in global memory.
@@ -255,9 +255,15 @@ __global__ void __launch_bounds__(kApplyThreads) apply_cart_batch_kernel(const A
   if (threadIdx.x == 0) Ps = descs[w.x];
   __syncthreads();
   if (done && done[Ps.prob]) return;  // converged problem: its y stays 0
-  if (Ps.k == 0) cart_cell_k<0, DF>(Ps, w.y, x, y);
-  else if (Ps.k == 1) cart_cell_k<1, DF>(Ps, w.y, x, y);
-  else cart_cell_k<2, DF>(Ps, w.y, x, y);
+  if (Ps.arith) {
+    if (Ps.k == 0) cart_cell_k<0, DF>(Ps, w.y, x, y);
+    else if (Ps.k == 1) cart_cell_k<1, DF>(Ps, w.y, x, y);
+    else cart_cell_k<2, DF>(Ps, w.y, x, y);
+  } else {
+    if (Ps.k == 0) cart_cell_k<0, double>(Ps, w.y, x, y);
+    else if (Ps.k == 1) cart_cell_k<1, double>(Ps, w.y, x, y);
+    else cart_cell_k<2, double>(Ps, w.y, x, y);
+  }
 }
 
 // One damped Jacobi sweep of the coarse multigrid: x_out = x_in + w (b - A x_in),
@@ -521,7 +527,9 @@ __device__ __forceinline__ double block_sum(double v) {
 // blockDim threads, so the result does not depend on which CTA finishes
 // last -- applies op and resets the counter.  No CTA waits for another.
 // op 0: scal[slot] = sum; op 1: pq -> alpha; op 2: (rz_new, zq) -> beta, rz.
-__device__ __forceinline__ void finish_reduction(double *partial, double *scal, int slot, int op, int flexible) {
+// hist (may be null): the sum is also stored there (residual histories).
+__device__ __forceinline__ void finish_reduction(double *partial, double *scal, int slot, int op, int flexible,
+                                                 double *hist = nullptr) {
   __shared__ bool last;
   unsigned int *count = reinterpret_cast<unsigned int *>(partial + 2 * kDotBlocks);
   __threadfence();  // this CTA's partials before its ticket
@@ -538,6 +546,7 @@ __device__ __forceinline__ void finish_reduction(double *partial, double *scal, 
   s = block_sum(s);
   if (op == 2) t = block_sum(t);
   if (threadIdx.x == 0) {
+    if (hist) *hist = s;
     if (op == 0) {
       scal[slot] = s;
     } else if (op == 1) {
@@ -555,18 +564,19 @@ __device__ __forceinline__ void finish_reduction(double *partial, double *scal, 
 }
 
 __global__ void dot_kernel(long long n, const double *__restrict__ a, const double *__restrict__ b,
-                           double *__restrict__ partial, double *__restrict__ scal, int slot, int op) {
+                           double *__restrict__ partial, double *__restrict__ scal, int slot, int op,
+                           double *hist) {
   double s = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     s = fma(a[i], b[i], s);
   s = block_sum(s);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
-  finish_reduction(partial, scal, slot, op, 0);
+  finish_reduction(partial, scal, slot, op, 0, hist);
 }
 
 __global__ void dot2_kernel(long long n, const double *__restrict__ r, const double *__restrict__ z,
                             const double *__restrict__ q, double *__restrict__ partial, double *__restrict__ scal,
-                            int flexible) {
+                            int flexible, double *hist) {
   double s = 0.0, t = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const double zi = z[i];
@@ -579,12 +589,12 @@ __global__ void dot2_kernel(long long n, const double *__restrict__ r, const dou
     partial[blockIdx.x] = s;
     partial[kDotBlocks + blockIdx.x] = t;
   }
-  finish_reduction(partial, scal, S_RZNEW, 2, flexible);
+  finish_reduction(partial, scal, S_RZNEW, 2, flexible, hist);
 }
 
 __global__ void update_xr_kernel(long long n, double *__restrict__ x, double *__restrict__ r,
                                  const double *__restrict__ p, const double *__restrict__ q,
-                                 double *__restrict__ partial, double *__restrict__ scal) {
+                                 double *__restrict__ partial, double *__restrict__ scal, double *hist) {
   const double a = scal[S_ALPHA];
   double s = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -595,7 +605,7 @@ __global__ void update_xr_kernel(long long n, double *__restrict__ x, double *__
   }
   s = block_sum(s);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
-  finish_reduction(partial, scal, S_RR, 0, 0);
+  finish_reduction(partial, scal, S_RR, 0, 0, hist);
 }
 
 __global__ void update_p_kernel(long long n, double *__restrict__ p, const double *__restrict__ z,
@@ -656,7 +666,9 @@ __global__ void seg_update_p_kernel(const int4 *__restrict__ chunk, double *__re
 }
 // One block per problem: fixed-order sum of its chunks' partials.
 // op 0: scal[slot] = s; op 1: pq -> alpha; op 2: rr -> convergence test;
-// op 3: (rz_new, zq) -> beta.
+// op 3: (rz_new, zq) -> beta.  done[prob]: 0 running, 1 converged, 2 NaN/Inf
+// residual, 3 breakdown (p^T A p <= 0); a nonzero flag freezes the problem
+// (alpha = beta = 0) and its cells, patches and rows are skipped.
 __global__ void seg_finalize_kernel(const int *__restrict__ cptr, int nchunk,
                                     const double *__restrict__ partial, double *__restrict__ scal,
                                     int *__restrict__ done, int *__restrict__ iters, int slot, int op,
@@ -676,12 +688,15 @@ __global__ void seg_finalize_kernel(const int *__restrict__ cptr, int nchunk,
     sc[slot] = s;
   } else if (op == 1) {
     sc[S_PQ] = s;
-    sc[S_ALPHA] = dn ? 0.0 : sc[S_RZ] / s;
+    const bool brk = !dn && !(s > 0.0);
+    if (brk) done[prob] = 3;
+    sc[S_ALPHA] = (dn || brk) ? 0.0 : sc[S_RZ] / s;
   } else if (op == 2) {
     if (!dn) {
       sc[S_RR] = s;
       iters[prob] += 1;
-      if (s <= tol2 * sc[S_BB]) done[prob] = 1;
+      if (!isfinite(s)) done[prob] = 2;
+      else if (s <= tol2 * sc[S_BB]) done[prob] = 1;
     }
   } else {
     sc[S_RZNEW] = s;
@@ -724,17 +739,14 @@ cudaError_t launch_apply(const ApplyDev &A, const double *x, double *y, cudaStre
   const int ncell = A.n[0] * A.n[1] * A.n[2];
   if (A.cartesian) {
     const size_t smem = cart_smem_doubles(A.k, A.p, A.nloc0, A.nloc1) * sizeof(double);
-    cudaError_t err = cudaSuccess;
-    if (A.k == 0) {
-      err = cudaFuncSetAttribute(apply_cart_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (err == cudaSuccess) apply_cart_kernel<0><<<ncell, kApplyThreads, smem, s>>>(A, x, y);
-    } else if (A.k == 1) {
-      err = cudaFuncSetAttribute(apply_cart_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (err == cudaSuccess) apply_cart_kernel<1><<<ncell, kApplyThreads, smem, s>>>(A, x, y);
-    } else {
-      err = cudaFuncSetAttribute(apply_cart_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (err == cudaSuccess) apply_cart_kernel<2><<<ncell, kApplyThreads, smem, s>>>(A, x, y);
-    }
+    auto go = [&](auto kern) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) kern<<<ncell, kApplyThreads, smem, s>>>(A, x, y);
+      return e;
+    };
+    cudaError_t err;
+    if (A.arith) err = A.k == 0 ? go(apply_cart_kernel<0, DF>) : A.k == 1 ? go(apply_cart_kernel<1, DF>) : go(apply_cart_kernel<2, DF>);
+    else err = A.k == 0 ? go(apply_cart_kernel<0, double>) : A.k == 1 ? go(apply_cart_kernel<1, double>) : go(apply_cart_kernel<2, double>);
     if (err != cudaSuccess) return err;
     g_launches += 1;
     return cudaGetLastError();
@@ -854,29 +866,29 @@ cudaError_t launch_sub(long long n, const uint8_t *mask, const double *b, const 
 }
 
 cudaError_t launch_dot(long long n, const double *a, const double *b, double *partial, double *scal,
-                       int slot, cudaStream_t s) {
-  dot_kernel<<<kDotBlocks, 256, 0, s>>>(n, a, b, partial, scal, slot, 0);
+                       int slot, cudaStream_t s, double *hist) {
+  dot_kernel<<<kDotBlocks, 256, 0, s>>>(n, a, b, partial, scal, slot, 0, hist);
   g_launches += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_alpha(long long n, const double *p, const double *q, double *partial, double *scal,
                          cudaStream_t s) {
-  dot_kernel<<<kDotBlocks, 256, 0, s>>>(n, p, q, partial, scal, S_PQ, 1);
+  dot_kernel<<<kDotBlocks, 256, 0, s>>>(n, p, q, partial, scal, S_PQ, 1, nullptr);
   g_launches += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_dot2(long long n, const double *r, const double *z, const double *q, double *partial,
-                        double *scal, int flexible, cudaStream_t s) {
-  dot2_kernel<<<kDotBlocks, 256, 0, s>>>(n, r, z, q, partial, scal, flexible);
+                        double *scal, int flexible, cudaStream_t s, double *hist) {
+  dot2_kernel<<<kDotBlocks, 256, 0, s>>>(n, r, z, q, partial, scal, flexible, hist);
   g_launches += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_update_xr(long long n, double *x, double *r, const double *p, const double *q,
-                             double *partial, double *scal, cudaStream_t s) {
-  update_xr_kernel<<<kDotBlocks, 256, 0, s>>>(n, x, r, p, q, partial, scal);
+                             double *partial, double *scal, cudaStream_t s, double *hist) {
+  update_xr_kernel<<<kDotBlocks, 256, 0, s>>>(n, x, r, p, q, partial, scal, hist);
   g_launches += 1;
   return cudaGetLastError();
 }

@@ -21,10 +21,13 @@ RM_FP64, RM_FP32 = 0, 1
 RM_PAFW, RM_PH = 0, 1
 RM_CHOL, RM_ICC = 0, 1
 RM_COARSE_NONE, RM_COARSE_P1, RM_COARSE_GMG = 0, 1, 2
+RM_NORM_L2, RM_NORM_NATURAL = 0, 1
+RM_ARITH_FP64, RM_ARITH_DF64 = 0, 1
+RM_BC_DIRICHLET, RM_BC_NONE = 0, 1
 STATUS = {0: "RM_OK", 1: "RM_ERR_ARG", 2: "RM_ERR_CUDA", 3: "RM_ERR_OOM",
           4: "RM_ERR_BREAKDOWN", 5: "RM_ERR_NOT_CONVERGED", 6: "RM_ERR_NAN"}
 
-EXPORTED = ["rm_default_options", "rm_setup", "rm_ndofs", "rm_apply",
+EXPORTED = ["rm_default_options", "rm_setup", "rm_ndofs", "rm_layout", "rm_history", "rm_apply",
             "rm_precondition", "rm_solve", "rm_stats", "rm_destroy", "rm_last_error",
             "rm_precondition_noalloc", "rm_batch_setup", "rm_batch_ndofs", "rm_batch_solve",
             "rm_batch_destroy", "rm_batch_last_error", "rm_default_train_options",
@@ -46,12 +49,15 @@ class RmOptions(ctypes.Structure):
                 ("static_condensation", ctypes.c_int), ("factor", ctypes.c_int),
                 ("coarse", ctypes.c_int), ("flexible", ctypes.c_int),
                 ("rtol", ctypes.c_double), ("max_it", ctypes.c_int),
-                ("check_every", ctypes.c_int), ("profile", ctypes.c_int)]
+                ("check_every", ctypes.c_int), ("profile", ctypes.c_int),
+                ("norm", ctypes.c_int), ("arith", ctypes.c_int), ("boundary", ctypes.c_int)]
 
 
 class RmInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("status", ctypes.c_int),
-                ("rel_res_l2", ctypes.c_double), ("solve_ms", ctypes.c_double),
+                ("rel_res_l2", ctypes.c_double), ("rel_res_natural", ctypes.c_double),
+                ("iterations_natural", ctypes.c_int), ("history_len", ctypes.c_int),
+                ("setup_s", ctypes.c_double), ("solve_ms", ctypes.c_double),
                 ("apply_ms", ctypes.c_double), ("apply_calls", ctypes.c_int),
                 ("precond_ms", ctypes.c_double), ("precond_calls", ctypes.c_int),
                 ("kernel_launches", ctypes.c_longlong),
@@ -100,6 +106,9 @@ def load():
     lib.rm_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong),
                              ctypes.POINTER(ctypes.c_longlong),
                              ctypes.POINTER(ctypes.c_longlong)]
+    lib.rm_layout.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                              ctypes.POINTER(ctypes.c_longlong)]
+    lib.rm_history.argtypes = [vp, ctypes.c_int, c_dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     lib.rm_apply.argtypes = [vp, vp, vp]
     lib.rm_precondition.argtypes = [vp, vp, vp]
     lib.rm_precondition_noalloc.argtypes = [vp, vp, vp]
@@ -222,12 +231,32 @@ class Solver:
         if check and rc not in (0,):
             self._check(rc)
         return {"iterations": info.iterations, "status": STATUS.get(info.status),
-                "rel_res_l2": info.rel_res_l2, "solve_ms": info.solve_ms,
+                "rel_res_l2": info.rel_res_l2, "rel_res_natural": info.rel_res_natural,
+                "iterations_natural": info.iterations_natural,
+                "history_len": info.history_len, "setup_s": info.setup_s,
+                "solve_ms": info.solve_ms,
                 "apply_ms": info.apply_ms, "apply_calls": info.apply_calls,
                 "precond_ms": info.precond_ms, "precond_calls": info.precond_calls,
                 "kernel_launches": info.kernel_launches, "learned_calls": info.learned_calls,
                 "judge_calls": info.judge_calls, "fallback_at": info.fallback_at,
                 "judge_eta": info.judge_eta}
+
+    def layout(self, comp):
+        """rm_layout: (dims, offset) of lattice component comp."""
+        d = (ctypes.c_int * 3)()
+        off = ctypes.c_longlong()
+        self._check(self.lib.rm_layout(self.h, comp, d, ctypes.byref(off)))
+        return tuple(d), off.value
+
+    def history(self, which=RM_NORM_L2, cap=None):
+        """rm_history of the last solve (l2 or natural), as a numpy array."""
+        import numpy as np
+        cap = 100000 if cap is None else cap
+        out = np.zeros(cap)
+        n = ctypes.c_int()
+        self._check(self.lib.rm_history(self.h, which, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        cap, ctypes.byref(n)))
+        return out[:n.value].copy()
 
     def corrector_train(self, rhs, **opts):
         """rm_corrector_train: rhs is a contiguous float64 CUDA tensor holding

@@ -75,3 +75,45 @@ def test_batch_rejects_distorted_meshes():
     X = inputs.vertices(2, perturb=0.1, seed=1)
     with pytest.raises(RmError, match="Cartesian"):
         BatchSolver([{"space": 1, "n": 2, "p": 2, "vertices": X}], **OPTS)
+
+
+def test_batch_nan_problem_stops_alone():
+    """A problem whose right-hand side holds a NaN is flagged RM_ERR_NAN on
+    the device and frozen at once; the other problems still converge and the
+    lock step does not run on to max_it."""
+    from paper_2211_14284_gb300.rm import BatchSolver
+    probs = _problems()[:3]
+    B = BatchSolver(probs, **dict(OPTS, rtol=1e-8, max_it=300))
+    bs = [torch.tensor(inputs.normal_rhs(sz, 60 + i), device="cuda") for i, sz in enumerate(B.sizes)]
+    N = 2 * 2 + 1
+    bs[1][N * N + N + 1 + B.sizes[1] // 3] = float("nan")   # a free entry of component 1
+    xs = [torch.zeros_like(b) for b in bs]
+    infos = B.solve(bs, xs, check=False)
+    assert infos[1]["status"] == "RM_ERR_NAN"
+    assert infos[0]["status"] == "RM_OK" and infos[2]["status"] == "RM_OK"
+    assert max(i["iterations"] for i in infos) < 100
+
+
+@pytest.mark.parametrize("arith", [0, 1], ids=["fp64", "df64"])
+def test_batch_high_degree_matches_single(arith):
+    """Degrees up to 12 (the top of the uneven batch's range) on small
+    meshes: every problem's batched solution equals the single solver's."""
+    from paper_2211_14284_gb300.rm import BatchSolver, Solver
+    spec = [(2, 12, 0.5), (2, 10, 3.0), (3, 9, 1.0)]
+    probs = []
+    for i, (n, p, beta) in enumerate(spec):
+        probs.append({"space": 1, "n": n, "p": p, "alpha": np.ones(n ** 3),
+                      "beta": np.full(n ** 3, beta), "rhs_seed": 70 + i})
+    opts = dict(OPTS, rtol=1e-10, arith=arith)
+    B = BatchSolver(probs, **opts)
+    bs = [torch.tensor(inputs.normal_rhs(sz, pr["rhs_seed"]), device="cuda")
+          for pr, sz in zip(probs, B.sizes)]
+    xs = [torch.zeros_like(b) for b in bs]
+    infos = B.solve(bs, xs)
+    for pr, b, x, info in zip(probs, bs, xs, infos):
+        assert info["status"] == "RM_OK"
+        s = Solver(1, pr["n"], pr["p"], alpha=pr["alpha"], beta=pr["beta"], **opts)
+        x1 = torch.zeros_like(x)
+        assert s.solve(b, x1)["status"] == "RM_OK"
+        xa = x1.cpu().numpy()
+        assert np.linalg.norm(x.cpu().numpy() - xa) <= 1e-8 * np.linalg.norm(xa)

@@ -1,0 +1,113 @@
+"""GPU checks of the C ABI's reporting: rm_layout, the l2 and natural-norm
+residual histories of rm_solve (Sec. 5.1: the paper stops on a 1e8
+reduction of the natural norm sqrt(r^T B r)), the natural-norm stopping
+test, setup_s, and the two number types of the operator apply."""
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle.auxiliary import assemble_aux
+from oracle.discretization import Lattice, Problem
+from oracle.krylov import pcg
+from oracle.relaxation import SCPAFW
+from paper_2211_14284_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    return torch.tensor(np.asarray(a, float), dtype=torch.float64, device="cuda")
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_layout_matches_lattice(k):
+    from paper_2211_14284_gb300.rm import RmError, Solver
+    n, p = (2, 3, 4), 2
+    s = Solver(k, n, p)
+    lat = Lattice(k, n, p)
+    for m in range(lat.ncomp):
+        dims, off = s.layout(m)
+        assert dims == lat.dims[m] and off == lat.offsets[m]
+    with pytest.raises(RmError):
+        s.layout(lat.ncomp)
+
+
+def _sc_problem(k=0):
+    n, p = 3, 3
+    X = inputs.vertices(n, perturb=0.1, seed=41)
+    al = inputs.loguniform_coefficient(n, 0.1, 10, seed=42)
+    be = inputs.constant_coefficient(n)
+    return n, p, X, al, be
+
+
+def test_histories_match_oracle_pcg():
+    """The GPU's l2 and natural-norm histories follow the oracle's PCG with
+    the same preconditioner, iteration by iteration, and the natural-norm
+    count equals the oracle's count for the same test."""
+    from paper_2211_14284_gb300.rm import RM_NORM_L2, RM_NORM_NATURAL, Solver
+    n, p, X, al, be = _sc_problem()
+    s = Solver(0, n, p, vertices=X, alpha=al, beta=be, static_condensation=1, factor=1, rtol=1e-10)
+    pr = Problem(0, n, p, X, al, be)
+    b = inputs.normal_rhs(pr.lat.size, 43)
+    x = torch.zeros(pr.lat.size, dtype=torch.float64, device="cuda")
+    info = s.solve(_dev(b), x)
+    assert info["status"] == "RM_OK" and info["setup_s"] > 0
+    hl2 = s.history(RM_NORM_L2)
+    hnat = s.history(RM_NORM_NATURAL)
+    assert len(hl2) == info["iterations"] + 1 == info["history_len"]
+    assert len(hnat) == info["iterations"]          # z of the last iterate is not formed
+    assert hl2[0] == pytest.approx(1.0) and hnat[0] == pytest.approx(1.0)
+    assert hl2[-1] == pytest.approx(info["rel_res_l2"], rel=1e-12)
+    assert hnat[-1] == pytest.approx(info["rel_res_natural"], rel=1e-12)
+    A = pr.A_free()
+    M = SCPAFW(pr, assemble_aux(pr)[pr.free][:, pr.free], factor="icc")
+    _, io = pcg(A, b[pr.free], M.apply, rtol=1e-10)
+    m = min(len(hl2), len(io["history_l2"]), 12)
+    # both run the same iteration; early entries agree to rounding growth
+    assert np.allclose(hl2[:m], io["history_l2"][:m], rtol=1e-6, atol=0)
+    m = min(len(hnat), len(io["history_natural"]), 12)
+    assert np.allclose(hnat[:m], io["history_natural"][:m], rtol=1e-6, atol=0)
+    want = next(i for i, v in enumerate(io["history_natural"]) if v <= 1e-8)
+    assert abs(info["iterations_natural"] - want) <= 1
+
+
+def test_natural_norm_stopping():
+    """RM_NORM_NATURAL stops at the first iterate whose natural norm fell by
+    1/rtol (the paper's test); the l2 history is still recorded."""
+    from paper_2211_14284_gb300.rm import RM_NORM_L2, RM_NORM_NATURAL, Solver
+    n, p, X, al, be = _sc_problem()
+    s = Solver(0, n, p, vertices=X, alpha=al, beta=be, static_condensation=1, factor=1,
+               rtol=1e-8, norm=RM_NORM_NATURAL)
+    b = _dev(inputs.normal_rhs(s.size, 44))
+    x = torch.zeros_like(b)
+    info = s.solve(b, x)
+    assert info["status"] == "RM_OK"
+    hnat = s.history(RM_NORM_NATURAL)
+    assert hnat[-1] <= 1e-8 and np.all(hnat[:-1] > 1e-8)
+    assert info["iterations"] == info["iterations_natural"] == len(hnat) - 1
+    assert len(s.history(RM_NORM_L2)) == info["iterations"] + 1
+
+
+@pytest.mark.parametrize("k", [0, 1])
+def test_fp64_and_df64_solves_agree(k):
+    """A solve to 1e-12 with the FP64 apply and with the double-float apply:
+    both within 1e-10 of the direct solve (distorted cells, the general
+    kernel)."""
+    from paper_2211_14284_gb300.rm import RM_ARITH_DF64, RM_ARITH_FP64, Solver
+    n, p, X, al, be = _sc_problem()
+    pr = Problem(k, n, p, X, al, be)
+    b = inputs.normal_rhs(pr.lat.size, 45)
+    xd = spla.spsolve(pr.A_free().tocsc(), b[pr.free])
+    opts = dict(static_condensation=1, factor=1, rtol=1e-12, max_it=800)
+    if k == 1:
+        opts["decomposition"] = 1
+    for arith in (RM_ARITH_FP64, RM_ARITH_DF64):
+        s = Solver(k, n, p, vertices=X, alpha=al, beta=be, arith=arith, **opts)
+        x = torch.zeros(pr.lat.size, dtype=torch.float64, device="cuda")
+        info = s.solve(_dev(b), x)
+        assert info["status"] == "RM_OK"
+        torch.cuda.synchronize()
+        got = x.cpu().numpy()[pr.free]
+        assert np.linalg.norm(got - xd) <= 1e-10 * np.linalg.norm(xd), arith

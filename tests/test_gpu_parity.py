@@ -50,9 +50,11 @@ APPLY_CASES = [(0, 2, 1, 0.0, False), (0, 3, 3, 0.15, True), (0, (2, 3, 4), 2, 0
                (2, (3, 2, 2), 2, 0.0, True), (0, 2, 7, 0.1, True), (1, 2, 5, 0.1, False)]
 
 
+@pytest.mark.parametrize("arith", [0, 1], ids=["fp64", "df64"])
 @pytest.mark.parametrize("k,n,p,perturb,coef", APPLY_CASES)
-def test_apply_parity(k, n, p, perturb, coef):
-    s, pr = _setup(k, n, p, perturb, coef)
+def test_apply_parity(k, n, p, perturb, coef, arith):
+    """Both number types of the apply (RM_ARITH_FP64, RM_ARITH_DF64)."""
+    s, pr = _setup(k, n, p, perturb, coef, arith=arith)
     x = inputs.normal_rhs(pr.lat.size, 21)
     y = torch.zeros(pr.lat.size, dtype=torch.float64, device="cuda")
     s.apply(_dev(x), y)
@@ -64,15 +66,16 @@ def test_apply_parity(k, n, p, perturb, coef):
     assert np.all(got[dmask] == 0.0)
 
 
+@pytest.mark.parametrize("arith", [0, 1], ids=["fp64", "df64"])
 @pytest.mark.parametrize("k,p", [(k, p) for k in (0, 1, 2) for p in range(1, 9)])
-def test_apply_parity_every_instantiation(k, p):
+def test_apply_parity_every_instantiation(k, p, arith):
     """The general-cell apply is one kernel per space k and degree p <= 8:
     each against the oracle on 2^3 cells around a moved interior vertex.
     From p = 5 the preconditioner is condensed with ICC factors: the default
     exact factors of uncondensed patches cost minutes of host setup there
     (and H(curl) refuses them from p = 7); the apply does not depend on it."""
     opts = {} if p <= 4 else dict(static_condensation=1, factor=1, decomposition=1 if k == 1 else 0)
-    s, pr = _setup(k, 2, p, 0.12, True, seed=5 + p, **opts)
+    s, pr = _setup(k, 2, p, 0.12, True, seed=5 + p, arith=arith, **opts)
     x = inputs.normal_rhs(pr.lat.size, 30 + p)
     y = torch.zeros(pr.lat.size, dtype=torch.float64, device="cuda")
     s.apply(_dev(x), y)
@@ -81,11 +84,12 @@ def test_apply_parity_every_instantiation(k, p):
     assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
 
 
+@pytest.mark.parametrize("arith", [0, 1], ids=["fp64", "df64"])
 @pytest.mark.parametrize("k,n,p", [(2, (2, 2, 3), 10), (1, 2, 10), (0, 2, 12)])
-def test_apply_parity_cartesian_high_p(k, n, p):
+def test_apply_parity_cartesian_high_p(k, n, p, arith):
     """High degrees on Cartesian meshes (the Kronecker kernel): sampled rows
     computed one by one by the oracle's quadrature."""
-    opts = dict(static_condensation=1, factor=1, decomposition=1 if k == 1 else 0)
+    opts = dict(static_condensation=1, factor=1, decomposition=1 if k == 1 else 0, arith=arith)
     s, pr = _setup(k, n, p, 0.0, True, **opts)
     x = inputs.normal_rhs(pr.lat.size, 24)
     y = torch.zeros(pr.lat.size, dtype=torch.float64, device="cuda")

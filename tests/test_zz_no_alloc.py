@@ -52,3 +52,52 @@ def test_noalloc_rejects_condensed_handles():
     z = torch.zeros_like(r)
     with pytest.raises(RmError, match="lattice-sized scratch"):
         s.precondition_noalloc(r, z)
+
+
+def _free_bytes():
+    free, _ = torch.cuda.mem_get_info()
+    return free
+
+
+def test_noalloc_allocates_nothing():
+    """The property the entry point exists for: after a warm-up call, many
+    calls leave the device's free memory unchanged (no cudaMalloc, no
+    caching-allocator growth)."""
+    s = _solver()
+    r = torch.tensor(inputs.normal_rhs(s.size, 50), dtype=torch.float64, device="cuda")
+    z = torch.empty_like(r)
+    s.precondition_noalloc(r, z)
+    torch.cuda.synchronize()
+    before = _free_bytes()
+    for _ in range(20):
+        s.precondition_noalloc(r, z)
+    torch.cuda.synchronize()
+    assert _free_bytes() == before
+
+
+def test_noalloc_fp32_and_off_modes():
+    """An FP32-preconditioner handle matches rm_precondition, and a handle
+    whose coarse term is switched off (RM_CORRECTOR_OFF) is served too."""
+    from paper_2211_14284_gb300.rm import RM_CORRECTOR_OFF
+    for opts, mode in ((dict(precision=1), None), ({}, RM_CORRECTOR_OFF)):
+        s = _solver(**opts)
+        if mode is not None:
+            s.corrector_use(mode)
+        r = torch.tensor(inputs.normal_rhs(s.size, 51), dtype=torch.float64, device="cuda")
+        z_ref = torch.empty_like(r)
+        z_new = torch.full_like(r, np.nan)
+        s.precondition(r, z_ref)
+        s.precondition_noalloc(r, z_new)
+        torch.cuda.synchronize()
+        a, b = z_ref.cpu().numpy(), z_new.cpu().numpy()
+        assert np.all(np.isfinite(b))
+        assert np.abs(a - b).max() <= 1e-6 * np.abs(a).max()
+
+
+def test_noalloc_rejects_multigrid_coarse():
+    from paper_2211_14284_gb300.rm import RmError
+    s = _solver(coarse=2)
+    r = torch.zeros(s.size, dtype=torch.float64, device="cuda")
+    z = torch.zeros_like(r)
+    with pytest.raises(RmError, match="multigrid"):
+        s.precondition_noalloc(r, z)
