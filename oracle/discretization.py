@@ -66,10 +66,17 @@ def kron3(T3, T2, T1):
 
 
 class Lattice:
-    """Global DOF lattice of V^k_{h,p} on an n1 x n2 x n3 mesh."""
+    """Global DOF lattice of V^k_{h,p} on an n1 x n2 x n3 mesh.
 
-    def __init__(self, k: int, n, p: int):
-        self.k, self.p = k, p
+    bc = "dirichlet": Gamma_D is the whole boundary of the cube (entries with
+    an s-type index on the boundary are not DOFs); bc = "none": Gamma_D is
+    empty and every lattice entry is a DOF (Eq. common_weak_formulation with
+    natural boundary conditions everywhere)."""
+
+    def __init__(self, k: int, n, p: int, bc: str = "dirichlet"):
+        if bc not in ("dirichlet", "none"):
+            raise ValueError(bc)
+        self.k, self.p, self.bc = k, p, bc
         self.n = (n, n, n) if np.isscalar(n) else tuple(int(v) for v in n)
         self.types = SPACE_TYPES[k]
         self.ncomp = len(self.types)
@@ -106,9 +113,11 @@ class Lattice:
                 np.concatenate(G[1]), np.concatenate(G[2]))
 
     def dirichlet_mask(self):
+        mask = np.zeros(self.size, bool)
+        if self.bc == "none":
+            return mask
         comp, g1, g2, g3 = self.coords()
         G = (g1, g2, g3)
-        mask = np.zeros(self.size, bool)
         for m in range(self.ncomp):
             sel = comp == m
             for d in range(3):
@@ -281,13 +290,14 @@ def element_matrix(ref: ReferenceElement, V8, alpha: float, beta: float):
 
 class Problem:
     """a^k on a structured mesh with per-cell alpha, beta (Eq.
-    common_weak_formulation), Gamma_D = boundary of the cube."""
+    common_weak_formulation), Gamma_D = boundary of the cube (bc =
+    "dirichlet") or empty (bc = "none")."""
 
-    def __init__(self, k, n, p, X, alpha, beta):
-        self.k, self.p = k, p
+    def __init__(self, k, n, p, X, alpha, beta, bc="dirichlet"):
+        self.k, self.p, self.bc = k, p, bc
         self.mesh = Mesh(n, X)
         self.n = self.mesh.n
-        self.lat = Lattice(k, self.n, p)
+        self.lat = Lattice(k, self.n, p, bc)
         ncell = self.n[0] * self.n[1] * self.n[2]
         self.alpha = np.broadcast_to(np.asarray(alpha, float), (ncell,)).copy()
         self.beta = np.broadcast_to(np.asarray(beta, float), (ncell,)).copy()

@@ -244,7 +244,7 @@ class Coarse:
     def __init__(self, problem: Problem, mode: str = "exact"):
         X = problem.mesh.X
         self.mode = mode
-        self.cp = Problem(problem.k, problem.n, 1, X, problem.alpha, problem.beta)
+        self.cp = Problem(problem.k, problem.n, 1, X, problem.alpha, problem.beta, problem.bc)
         P0 = prolongation(problem.lat, self.cp.lat)
         self.R0T = P0[problem.free][:, self.cp.free].tocsr()
         A0 = self.cp.A_free().tocsr()
@@ -256,7 +256,7 @@ class Coarse:
         A, lat, free, n = A0, self.cp.lat, self.cp.free, list(problem.n)
         while all(v % 2 == 0 and v >= 4 for v in n) and A.shape[0] > 512:
             nh = [v // 2 for v in n]
-            lat_h = Lattice(problem.k, tuple(nh), 1)
+            lat_h = Lattice(problem.k, tuple(nh), 1, problem.bc)
             free_h = lat_h.free()
             P = refinement(lat, lat_h)[free][:, free_h].tocsr()
             D = A.diagonal()
@@ -453,7 +453,7 @@ class SCPH:
                                          edge_factor))
         # potential space
         p0 = Problem(0, problem.n, problem.p, problem.mesh.X,
-                     problem.alpha, problem.beta)
+                     problem.alpha, problem.beta, problem.bc)
         B = assemble_aux(p0, mass_coef=np.zeros_like(problem.beta),
                          stiff_coef=problem.beta)
         self.B = B

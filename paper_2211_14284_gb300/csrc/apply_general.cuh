@@ -299,9 +299,9 @@ __device__ __forceinline__ void cell_io(const ApplyDev &P, const int e[3], const
     for (int l = threadIdx.x; l < CS; l += NT) {
       const int i1 = l % l0, i2 = (l / l0) % l1, i3 = l / (l0 * l1);
       const int g1 = e[0] * PP + i1, g2 = e[1] * PP + i2, g3 = e[2] * PP + i3;
-      const bool dir = (styp(KK, m, 0) && (g1 == 0 || g1 == P.n[0] * PP)) ||
+      const bool dir = !P.natural && ((styp(KK, m, 0) && (g1 == 0 || g1 == P.n[0] * PP)) ||
                        (styp(KK, m, 1) && (g2 == 0 || g2 == P.n[1] * PP)) ||
-                       (styp(KK, m, 2) && (g3 == 0 || g3 == P.n[2] * PP));
+                       (styp(KK, m, 2) && (g3 == 0 || g3 == P.n[2] * PP)));
       const long long gi = P.off[m] + g1 + (long long)P.N[m][0] * (g2 + (long long)P.N[m][1] * g3);
       if (SCATTER) {
         if (!dir) atomicAdd(&y[gi], rto(yl[m * CS + l]));

@@ -596,14 +596,15 @@ int rm_setup(rm_handle **out, int space, const rm_mesh *mesh, int p, const doubl
     if (o.rtol <= 0 || o.max_it < 1 || o.check_every < 1) throw std::invalid_argument("rtol/max_it/check_every");
     if (o.norm != RM_NORM_L2 && o.norm != RM_NORM_NATURAL) throw std::invalid_argument("norm");
     if (o.arith != RM_ARITH_FP64 && o.arith != RM_ARITH_DF64) throw std::invalid_argument("arith");
-    if (o.boundary != RM_BC_DIRICHLET) throw std::invalid_argument("boundary: only RM_BC_DIRICHLET");
+    if (o.boundary != RM_BC_DIRICHLET && o.boundary != RM_BC_NONE) throw std::invalid_argument("boundary");
     h->ad.arith = o.arith == RM_ARITH_DF64 ? 1 : 0;
+    h->ad.natural = o.boundary == RM_BC_NONE ? 1 : 0;
     h->vt = o.precision == RM_FP32 ? 1 : 0;
     h->sc = o.static_condensation != 0;
     h->ph = o.decomposition == RM_PH;
     int dev = 0;
     CK(cudaGetDevice(&dev));
-    h->L = Layout(space, h->n, p);
+    h->L = Layout(space, h->n, p, o.boundary == RM_BC_NONE);
     h->size = h->L.size;
     const int ncell = h->n[0] * h->n[1] * h->n[2];
     Geometry geo;
@@ -657,7 +658,7 @@ int rm_setup(rm_handle **out, int space, const rm_mesh *mesh, int p, const doubl
           h->fam.push_back(upload_family(h.get(), F));
         }
         // potential: H(grad) auxiliary operator with mass 0, stiffness beta
-        Layout L0(0, h->n, p);
+        Layout L0(0, h->n, p, h->L.natural);
         FreeMap fm0(L0);
         std::vector<double> zero(ncell, 0.0);
         Csr B = assemble_aux(L0, geo, zero.data(), be.data(), fm0);

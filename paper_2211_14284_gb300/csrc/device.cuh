@@ -37,6 +37,7 @@ struct ApplyDev {
   const int *cidx;         // cart_index_table(k, p)
   int prob;                // batched solves: the problem's index
   int arith;               // number type of the apply: 0 double, 1 double-float (DF)
+  int natural;             // 1: Gamma_D empty (no Dirichlet entries)
 };
 
 // s-type test of component m of V^kk in direction d (Sec. 2.4): H(grad) all

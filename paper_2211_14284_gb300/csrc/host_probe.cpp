@@ -66,12 +66,15 @@ int rmh_gll(int q, double *x, double *w) {
 }
 
 // Builds P, the Schur complement and the patch families as rm_setup would.
-// mode: 0 non-condensed PAFW, 1 SC-PAFW, 2 SC-PH (k = 1).
+// mode & 15: 0 non-condensed PAFW, 1 SC-PAFW, 2 SC-PH (k = 1); mode & 16:
+// Gamma_D empty (natural boundary conditions).
 int rmh_build(int k, const int n[3], int p, const double *X, const double *alpha,
               const double *beta, int mode, int factor, int coarse) {
   try {
     g.reset(new Probe());
-    g->L = Layout(k, n, p);
+    const bool natural = (mode & 16) != 0;
+    mode &= 15;
+    g->L = Layout(k, n, p, natural);
     g->fm = FreeMap(g->L);
     Geometry geo;
     for (int d = 0; d < 3; ++d) geo.n[d] = n[d];
@@ -90,7 +93,7 @@ int rmh_build(int k, const int n[3], int p, const double *X, const double *alpha
         g->fams.push_back(build_patches(g->L, g->fm, C.S, 0, true, factor));
       } else {
         for (int m = 0; m < 3; ++m) g->fams.push_back(build_patches(g->L, g->fm, C.S, 1 << m, true, 0));
-        g->L0 = Layout(0, n, p);
+        g->L0 = Layout(0, n, p, natural);
         g->fm0 = FreeMap(g->L0);
         std::vector<double> zero(ncell, 0.0);
         Csr B = assemble_aux(g->L0, geo, zero.data(), beta, g->fm0);

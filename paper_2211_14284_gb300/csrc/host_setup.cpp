@@ -32,7 +32,7 @@ static const DTerm kTerms[3][3][3] = {
     {{{2, 1, 1}, {1, 2, -1}}, {{0, 2, 1}, {2, 0, -1}}, {{1, 0, 1}, {0, 1, -1}}},
     {{{0, 0, 1}, {1, 1, 1}, {2, 2, 1}}, {}, {}}};
 
-Layout::Layout(int k_, const int n_[3], int p_) : k(k_), p(p_) {
+Layout::Layout(int k_, const int n_[3], int p_, bool natural_) : k(k_), p(p_), natural(natural_) {
   if (k < 0 || k > 3) throw std::runtime_error("Layout: k in 0..3");
   for (int d = 0; d < 3; ++d) n[d] = n_[d];
   ncomp = (k == 0 || k == 3) ? 1 : 3;
@@ -359,7 +359,7 @@ Csr assemble_aux(const Layout &L, const Geometry &geo, const double *mcoef,
   AuxCtx C;
   C.p = L.p;
   C.Lk = L;
-  C.Lk1 = Layout(L.k + 1, L.n, L.p);
+  C.Lk1 = Layout(L.k + 1, L.n, L.p, L.natural);
   const int p = L.p;
   Basis1D B(p);
   C.q = quad_points(p);
@@ -1293,7 +1293,7 @@ static std::vector<double> dense_spd_inverse(std::vector<double> Lm, int nc) {
 CoarseData build_coarse(const Layout &Lf, const Geometry &geo, const double *alpha,
                         const double *beta) {
   CoarseData C;
-  Layout Lc(Lf.k, Lf.n, 1);
+  Layout Lc(Lf.k, Lf.n, 1, Lf.natural);
   FreeMap fc(Lc);
   const int nc = (int)fc.free2lat.size();
   C.nc = nc;
@@ -1335,7 +1335,7 @@ CoarseData build_coarse_gmg(const Layout &Lf, const Geometry &geo, const double 
                             const double *beta, CoarseGMG &mg) {
   CoarseData C;
   const int k = Lf.k;
-  Layout Lc(k, Lf.n, 1);
+  Layout Lc(k, Lf.n, 1, Lf.natural);
   FreeMap fc(Lc);
   C.nc = (int)fc.free2lat.size();
   std::vector<Trip> t = coarse_triplets(Lf, Lc, fc, geo, alpha, beta);
@@ -1352,7 +1352,7 @@ CoarseData build_coarse_gmg(const Layout &Lf, const Geometry &geo, const double 
                      n[2] >= 4 && A.nrows > 512;
     if (!can) break;
     int nh[3] = {n[0] / 2, n[1] / 2, n[2] / 2};
-    Layout Lh(k, nh, 1);
+    Layout Lh(k, nh, 1, Lf.natural);
     FreeMap fh(Lh);
     // P: level l+1 (mesh nh) -> level l (mesh n), per direction
     // s-type: fine index g from coarse g/2 (even) or (g-1)/2, (g+1)/2 with 1/2

@@ -19,12 +19,16 @@ struct Layout {
   int loff[4] = {};
   long long size = 0;
   int nloc = 0;
+  // Gamma_D empty (natural boundary conditions everywhere): no entry is
+  // Dirichlet; otherwise Gamma_D is the whole boundary of the cube
+  bool natural = false;
   Layout() = default;
-  Layout(int k, const int n[3], int p);
+  Layout(int k, const int n[3], int p, bool natural = false);
   long long index(int m, long long g1, long long g2, long long g3) const {
     return off[m] + g1 + N[m][0] * (g2 + N[m][1] * g3);
   }
   bool dirichlet(int m, const long long g[3]) const {
+    if (natural) return false;
     for (int d = 0; d < 3; ++d)
       if (t[m][d] == 's' && (g[d] == 0 || g[d] == (long long)n[d] * p)) return true;
     return false;

@@ -123,8 +123,8 @@ __device__ void cart_cell_k(const ApplyDev &P, const int c, const double *__rest
     const bool s0 = styp(K, m, 0), s1 = styp(K, m, 1), s2 = styp(K, m, 2);
     const int l0 = s0 ? q1 : p, l1 = s1 ? q1 : p;
     const int g0 = e0 * p + i0, g1 = e1 * p + i1, g2 = e2 * p + i2;
-    const bool dir = (s0 && (g0 == 0 || g0 == n0 * p)) || (s1 && (g1 == 0 || g1 == n1 * p)) ||
-                     (s2 && (g2 == 0 || g2 == n2 * p));
+    const bool dir = !P.natural && ((s0 && (g0 == 0 || g0 == n0 * p)) || (s1 && (g1 == 0 || g1 == n1 * p)) ||
+                     (s2 && (g2 == 0 || g2 == n2 * p)));
     const long long N0 = (long long)n0 * p + s0, N1 = (long long)n1 * p + s1;
     const long long off = m == 0 ? off0 : (m == 1 ? off1 : off2);
     xl[m * sz0 + i0 + l0 * (i1 + l1 * i2)] = rfrom<R>(dir ? 0.0 : x[off + g0 + N0 * (g1 + N1 * g2)]);
@@ -228,8 +228,8 @@ __device__ void cart_cell_k(const ApplyDev &P, const int c, const double *__rest
       sacc = sg > 0 ? radd(sacc, v) : rsub(sacc, v);
     }
     const int g0 = e0 * p + i0, g1 = e1 * p + i1, g2 = e2 * p + i2;
-    const bool dir = (s0 && (g0 == 0 || g0 == n0 * p)) || (s1 && (g1 == 0 || g1 == n1 * p)) ||
-                     (s2 && (g2 == 0 || g2 == n2 * p));
+    const bool dir = !P.natural && ((s0 && (g0 == 0 || g0 == n0 * p)) || (s1 && (g1 == 0 || g1 == n1 * p)) ||
+                     (s2 && (g2 == 0 || g2 == n2 * p)));
     if (!dir) {
       const long long N0 = (long long)n0 * p + s0, N1 = (long long)n1 * p + s1;
       const long long off = m == 0 ? off0 : (m == 1 ? off1 : off2);

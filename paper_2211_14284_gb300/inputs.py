@@ -99,6 +99,19 @@ def lognormal_grf_coefficient(n, sigma: float = 1.0, ell: float = 0.1,
     return np.exp(sigma * f).ravel()
 
 
+def annulus_coefficient(n, inside: float, outside: float, r_in: float = 0.15,
+                        r_out: float = 0.3) -> np.ndarray:
+    """Two-material piecewise-constant coefficient: `inside` on the cells whose
+    centre lies in the annulus r_in <= r <= r_out around the vertical axis
+    x = y = 1/2 of the unit cube (a wire), `outside` elsewhere (the air)."""
+    n1, n2, n3 = _dims(n)
+    e3, e2, e1 = np.meshgrid(np.arange(n3), np.arange(n2), np.arange(n1), indexing="ij")
+    x = (e1.ravel() + 0.5) / n1 - 0.5
+    y = (e2.ravel() + 0.5) / n2 - 0.5
+    r = np.sqrt(x * x + y * y)
+    return np.where((r >= r_in) & (r <= r_out), float(inside), float(outside))
+
+
 def normal_rhs(length: int, seed: int) -> np.ndarray:
     """N(0, 1) entries, one per lattice DOF (Dirichlet entries are ignored)."""
     return rng(seed).standard_normal(int(length))

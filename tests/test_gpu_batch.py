@@ -85,8 +85,9 @@ def test_batch_nan_problem_stops_alone():
     probs = _problems()[:3]
     B = BatchSolver(probs, **dict(OPTS, rtol=1e-8, max_it=300))
     bs = [torch.tensor(inputs.normal_rhs(sz, 60 + i), device="cuda") for i, sz in enumerate(B.sizes)]
-    N = 2 * 2 + 1
-    bs[1][N * N + N + 1 + B.sizes[1] // 3] = float("nan")   # a free entry of component 1
+    from oracle.discretization import Lattice
+    free1 = Lattice(1, probs[1]["n"], probs[1]["p"]).free()
+    bs[1][int(free1[len(free1) // 2])] = float("nan")        # a free entry of problem 1
     xs = [torch.zeros_like(b) for b in bs]
     infos = B.solve(bs, xs, check=False)
     assert infos[1]["status"] == "RM_ERR_NAN"

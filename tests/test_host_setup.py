@@ -187,6 +187,38 @@ def test_coarse_matches_oracle(probe, k, perturb):
     assert abs(R0[:, pr.free] - c.R0T.T).max() < 1e-12
 
 
+@pytest.mark.parametrize("k,mode", [(0, 1), (1, 2), (2, 1)])
+def test_natural_boundary_setup_matches_oracle(probe, k, mode):
+    """Gamma_D empty: every lattice entry is a DOF; the auxiliary operator,
+    its Schur complement, the patch lists and factors (boundary-vertex stars
+    now hold the boundary entries) and the coarse space match the oracle's
+    natural-boundary problem."""
+    n, p = 2, 2
+    X = inputs.vertices(n, perturb=0.1, seed=13)
+    al = inputs.loguniform_coefficient(n, 0.1, 10, seed=14)
+    be = inputs.loguniform_coefficient(n, 0.1, 10, seed=15)
+    pr = Problem(k, n, p, X, al, be, bc="none")
+    assert len(pr.free) == pr.lat.size
+    probe.build(k, n, p, X, al, be, mode=mode | 16, factor=0, coarse=True)
+    nf = pr.lat.size
+    Po = assemble_aux(pr)
+    P = _csr_dense(*probe.csr(0), nf)
+    assert np.abs(P - Po.toarray()).max() < 1e-12 * abs(Po).max()
+    sc = Condensed(Po.tocsr(), pr.lat, pr.free)
+    S = sc.S.tocsr()
+    G = pr.free[sc.G]
+    pos = _free_pos(G, pr.lat.size)
+    fams = probe.families()
+    spans = [()] if mode == 1 else [(0,), (1,), (2,)]
+    for f, span in enumerate(spans):
+        _compare_family(fams[f], patch_lists(pr.lat, span, G),
+                        lambda idx: S[pos[idx]][:, pos[idx]].toarray(), "chol", pr.free)
+    c = Coarse(pr)
+    want = np.linalg.inv(c.A0)
+    assert c.A0.shape[0] == c.cp.lat.size
+    assert np.abs(probe.coarse_inverse() - want).max() < 1e-10 * np.abs(want).max()
+
+
 def test_icc_breakdown_agrees(probe):
     """ICC(0) of NCE_2 vertex-star Schur complements has a non-positive pivot
     (the paper notes that ICC(0) may fail); both sides report it."""

@@ -212,3 +212,61 @@ def test_l2_convergence_order(p, perturb):
     errs = [_solve_sin(n, p, perturb) for n in (2, 4, 8)]
     rate = np.log2(errs[-2] / errs[-1])
     assert rate > p + 1 - 0.35, (errs, rate)
+
+
+# -- natural boundary conditions (Gamma_D empty) ------------------------------
+@pytest.mark.parametrize("bc", ["none", "dirichlet"])
+def test_kernel_dimensions_follow_the_sequence(bc):
+    """With beta = 0 the kernel of a^k is d^{k-1} V^{k-1}, whose dimension the
+    exactness of the discrete de Rham sequence on the cube fixes (Sec. 2.4):
+    H(grad): the constants (Gamma_D empty) or nothing (Dirichlet); H(curl):
+    dim V^0 - dim ker grad; H(div): dim V^1 - dim ker curl.  Counting them
+    checks which boundary entries are DOFs under each condition."""
+    from oracle.discretization import Problem
+    n, p = 2, 2
+    X = inputs.vertices(n, perturb=0.1, seed=3)
+    dims = {}
+    for k in (0, 1, 2):
+        pr = Problem(k, n, p, X, 1.0, 0.0, bc=bc)
+        A = pr.A_free().toarray()
+        ev = np.linalg.eigvalsh(A)
+        dims[k] = (len(pr.free), int(np.sum(ev < 1e-10 * ev.max())))
+    ker0 = 1 if bc == "none" else 0
+    assert dims[0][1] == ker0
+    assert dims[1][1] == dims[0][0] - ker0
+    assert dims[2][1] == dims[1][0] - dims[1][1]
+    if bc == "none":
+        # every lattice entry is a DOF
+        assert dims[0][0] == (n * p + 1) ** 3
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_natural_bc_operator_is_definite(k):
+    """Gamma_D empty with beta > 0: A is symmetric positive definite."""
+    from oracle.discretization import Problem
+    n, p = 2, 2
+    X = inputs.vertices(n, perturb=0.1, seed=4)
+    be = inputs.loguniform_coefficient(n, 1e-3, 1.0, seed=5)
+    pr = Problem(k, n, p, X, 1.0, be, bc="none")
+    A = pr.A_free().toarray()
+    assert np.abs(A - A.T).max() <= 1e-13 * np.abs(A).max()
+    assert np.linalg.eigvalsh(A).min() > 0
+
+
+def test_neumann_manufactured_convergence():
+    """Gamma_D empty, H(grad): u = cos(pi x) cos(pi y) cos(pi z) has zero
+    normal derivative on the cube, so it solves u - div grad u = (1 + 3 pi^2) u
+    with natural boundary conditions; the L2 error falls at order p + 1
+    (boundary entries solved for, not fixed)."""
+    import scipy.sparse.linalg as spla
+    from oracle.discretization import Problem
+    u = lambda x: np.prod(np.cos(np.pi * x), axis=1)
+    for p in (1, 2):
+        errs = []
+        for n in (2, 4):
+            pr = Problem(0, n, p, inputs.vertices(n), 1.0, 1.0, bc="none")
+            b = pr.load_vector_hgrad(lambda x: (1 + 3 * np.pi ** 2) * u(x))
+            xh = spla.spsolve(pr.A_free().tocsc(), b)
+            errs.append(pr.l2_error_hgrad(xh, u))
+        order = np.log2(errs[0] / errs[1])
+        assert order > p + 1 - 0.35, (p, errs, order)
