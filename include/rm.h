@@ -17,7 +17,7 @@
  * relaxations of Sec. 4 -- PAFW vertex stars (Eq. asm-afw), their
  * statically-condensed form on the sparse auxiliary operator (Sec. 3.2,
  * Eqs. sc-pafw, sc-asm-afw) and the SC Pavarino-Hiptmair form for H(curl)
- * (Eq. sc-asm-hiptmair) -- with exact or incomplete Cholesky patch factors
+ * and H(div) (Eq. sc-asm-hiptmair) -- with exact or incomplete Cholesky patch factors
  * (Sec. 4.5) and a p = 1 coarse correction.
  *
  * VECTOR LAYOUT (every vector argument): FDM-basis coefficients on the
@@ -98,7 +98,10 @@ typedef struct {
 
 typedef struct {
   int precision;           /* rm_precision of the preconditioner data and arithmetic */
-  int decomposition;       /* RM_PAFW (vertex stars) or RM_PH (H(curl) only) */
+  int decomposition;       /* RM_PAFW (vertex stars) or RM_PH (H(curl): edge stars +
+                              vertex-star gradient potentials; H(div): face stars
+                              (point-Jacobi on S) + edge-star curl potentials with
+                              the eps = 1e-2 mass shift; static condensation only) */
   int static_condensation; /* 1: patches on the interface Schur complement */
   int factor;              /* RM_CHOL (exact) or RM_ICC (ICC(0) on the SC pattern).
                               Exact factors of uncondensed patches are dense per
@@ -154,8 +157,8 @@ rm_options rm_default_options(void);
  * NULL for 1.  stream: a cudaStream_t (NULL = legacy default stream) used by
  * every later call on this handle.  Supported: p in 1..15 when every cell is
  * an axis-aligned box, p in 1..8 otherwise (the general-cell apply's shared
- * memory; larger p returns RM_ERR_ARG); RM_PH only for RM_HCURL with
- * static_condensation = 1. */
+ * memory; larger p returns RM_ERR_ARG); RM_PH only for RM_HCURL or RM_HDIV
+ * with static_condensation = 1. */
 int rm_setup(rm_handle **h, int space, const rm_mesh *mesh, int p,
              const double *alpha, const double *beta, const rm_options *opt,
              void *stream);

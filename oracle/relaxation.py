@@ -413,33 +413,53 @@ class SCPAFW:
         return z
 
 
-def discrete_gradient(lat0: Lattice, lat1: Lattice) -> sp.csr_matrix:
-    """D: V^0 lattice -> V^1 lattice (full lattices), cellwise D-hat_3d."""
+def discrete_derivative(kk: int, lat_a: Lattice, lat_b: Lattice) -> sp.csr_matrix:
+    """d^kk: V^kk lattice -> V^{kk+1} lattice (full lattices), cellwise
+    D-hat_3d (the gradient for kk = 0, the curl for kk = 1)."""
     from .discretization import dhat_3d
-    Dl = dhat_3d(0, FDM1D(lat0.p))
+    Dl = dhat_3d(kk, FDM1D(lat_a.p))
     entries = {}
-    for cell, _ in lat0.cells():
-        d0 = lat0.cell_dofs(cell)
-        d1 = lat1.cell_dofs(cell)
+    for cell, _ in lat_a.cells():
+        da = lat_a.cell_dofs(cell)
+        db = lat_b.cell_dofs(cell)
         nz = np.nonzero(Dl)
         for i, j in zip(*nz):
-            entries[(int(d1[i]), int(d0[j]))] = Dl[i, j]
+            entries[(int(db[i]), int(da[j]))] = Dl[i, j]
     r = np.array([k[0] for k in entries], int)
     c = np.array([k[1] for k in entries], int)
     v = np.array(list(entries.values()))
-    return sp.coo_matrix((v, (r, c)), shape=(lat1.size, lat0.size)).tocsr()
+    return sp.coo_matrix((v, (r, c)), shape=(lat_b.size, lat_a.size)).tocsr()
+
+
+def discrete_gradient(lat0: Lattice, lat1: Lattice) -> sp.csr_matrix:
+    """D: V^0 lattice -> V^1 lattice (full lattices), cellwise D-hat_3d."""
+    return discrete_derivative(0, lat0, lat1)
+
+
+# eps of the H(div) potential operator B_eps = (curl phi, beta curl psi) +
+# eps (phi, beta psi): the Remark after Eq. ph adds "a small multiple of the
+# mass matrix" to the singular curl-curl patch matrices without giving it
+HDIV_POTENTIAL_EPS = 1e-2
 
 
 class SCPH:
-    """SC-PH for H(curl) (Eqs. sc-ph, sc-asm-hiptmair): edge-star patches of
-    S (exact Cholesky), plus D-tilde (sum_v B-tilde_v^{-1}) D-tilde^T with
-    vertex-star ICC(0) patches of the potential Schur complement, plus the
-    interior solve, harmonic extension and coarse correction."""
+    """SC-PH (Eqs. sc-ph, sc-asm-hiptmair) for H(curl) and H(div): stars of
+    the k-dimensional entities on S (exact Cholesky; edge stars for H(curl),
+    face stars for H(div), where the face-star blocks of S are diagonal and
+    the relaxation is point-Jacobi on S, Sec. 4.5), plus the potential term
+    D-tilde (sum_j B-tilde_j^{-1}) D-tilde^T on the stars of the
+    (k-1)-dimensional entities (vertex stars of V^0 for H(curl), edge stars of
+    V^1 for H(div)) with B = (d phi, beta d psi) (Sec. 4.3) -- for H(div) plus
+    eps (phi, beta psi), the Remark on its singular potential problem --
+    built as the auxiliary operator of V^{k-1} with mass coefficient 0 (H(curl))
+    or eps beta (H(div)) and derivative coefficient beta; interior solve,
+    harmonic extension and coarse correction as in SC-PAFW."""
 
     def __init__(self, problem: Problem, P_free, edge_factor="chol",
-                 vertex_factor="icc", coarse=True):
+                 vertex_factor="icc", coarse=True, eps=HDIV_POTENTIAL_EPS):
         from .auxiliary import assemble_aux
-        assert problem.k == 1
+        k = problem.k
+        assert k in (1, 2)
         self.problem = problem
         lat1 = problem.lat
         free1 = problem.free
@@ -448,23 +468,25 @@ class SCPH:
         pos1 = free_position(G1, lat1.size)
         self.edge = []
         for m in range(3):
-            pats = patch_lists(lat1, (m,), G1)
+            span = (m,) if k == 1 else tuple(d for d in range(3) if d != m)
+            pats = patch_lists(lat1, span, G1)
             self.edge.append(PatchSolver(self.sc.S, [pos1[s] for s in pats],
                                          edge_factor))
-        # potential space
-        p0 = Problem(0, problem.n, problem.p, problem.mesh.X,
+        # potential space V^{k-1}
+        p0 = Problem(k - 1, problem.n, problem.p, problem.mesh.X,
                      problem.alpha, problem.beta, problem.bc)
-        B = assemble_aux(p0, mass_coef=np.zeros_like(problem.beta),
-                         stiff_coef=problem.beta)
+        mass = np.zeros_like(problem.beta) if k == 1 else eps * problem.beta
+        B = assemble_aux(p0, mass_coef=mass, stiff_coef=problem.beta)
         self.B = B
         free0 = p0.free
         self.sc0 = Condensed(B[free0][:, free0].tocsr(), p0.lat, free0)
         G0 = free0[self.sc0.G]
         pos0 = free_position(G0, p0.lat.size)
-        pats0 = patch_lists(p0.lat, (), G0)
-        self.vertex = PatchSolver(self.sc0.S, [pos0[s] for s in pats0],
-                                  vertex_factor)
-        D = discrete_gradient(p0.lat, lat1)
+        spans0 = [()] if k == 1 else [(m,) for m in range(3)]
+        self.potential = [PatchSolver(self.sc0.S, [pos0[s] for s in patch_lists(p0.lat, sp0, G0)],
+                                      vertex_factor) for sp0 in spans0]
+        self.vertex = self.potential[0] if k == 1 else None
+        D = discrete_derivative(k - 1, p0.lat, lat1)
         self.Dt = D[G1][:, G0].tocsr()
         self.coarse = (Coarse(problem, coarse if isinstance(coarse, str) else "exact")
                        if coarse else None)
@@ -473,7 +495,11 @@ class SCPH:
         z = np.zeros_like(rG)
         for ps in self.edge:
             z += ps.apply(rG)
-        z += self.Dt @ self.vertex.apply(self.Dt.T @ rG)
+        u = self.Dt.T @ rG
+        v = np.zeros_like(u)
+        for ps in self.potential:
+            v += ps.apply(u)
+        z += self.Dt @ v
         return z
 
     def smooth(self, r):

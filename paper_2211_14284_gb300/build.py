@@ -23,8 +23,10 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 HOST_SOURCES = ["host_basis.cpp", "host_setup.cpp", "host_probe.cpp"]
 DEVICE_SOURCES = ["kernels.cu", "apply_general.cu", "capi.cu", "batch.cu", "learned.cu"]
 # apply_general_part.cu, once per (space k, first degree of four): the
-# compile-time instantiations of the general apply, compiled in parallel
+# compile-time instantiations of the general apply, compiled in parallel;
+# apply_cart_part.cu once per space: the Cartesian apply's instantiations
 GENERAL_PARTS = [(k, plo) for k in (0, 1, 2) for plo in (1, 5)]
+CART_PARTS = [0, 1, 2]
 
 
 def _nvcc():
@@ -54,6 +56,7 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
     units = [(s, s, []) for s in DEVICE_SOURCES]
     units += [("apply_general_part.cu", f"apply_general_k{k}_p{plo}.cu",
                [f"-DRM_GENERAL_K={k}", f"-DRM_GENERAL_PLO={plo}"]) for k, plo in GENERAL_PARTS]
+    units += [("apply_cart_part.cu", f"apply_cart_k{k}.cu", [f"-DRM_CART_K={k}"]) for k in CART_PARTS]
     for s, name, defs in units:
         o = os.path.join(OUT, name + ".o")
         objs.append(o)

@@ -1,0 +1,352 @@
+// Operator apply on axis-aligned (Cartesian) cells, y = A x, where the cell
+// matrix of Eq. sum-factorization is a Kronecker sum of the 1D FDM factors
+// (Sec. 2.2-2.4): the mass of V^k is c_m (x)_d F_d per component m (F_d =
+// B-hat along an s-type direction, I along an r-type one; c_m the box
+// metric times beta), the derivative term D-hat^T (alpha M^{k+1}) D-hat.
+// B-hat is the identity on the interior functions plus a 2x2 block on the
+// interface pair {0, p}; a row of D-hat has at most three nonzeros (columns
+// 0, p and its own index).  No quadrature: ~30 flops per DOF.
+//
+// Two launches, no atomics, bitwise reproducible:
+//  * cart_local_kernel<K, P, R>: the cell products y_K = A_K x_K, one CTA per
+//    CPB cells, every shape and loop bound a compile-time constant of
+//    (K, P); written unassembled to the scratch Y[cell][local entry] (FP64);
+//  * cart_assemble_kernel<K, P>: every lattice entry sums its (at most 8)
+//    cell contributions from Y in a fixed order; Dirichlet entries get 0.
+// R = double (FP64) or DF (double-float, df.cuh), chosen per handle.
+//
+// This header holds the templates; apply_cart_part.cu instantiates them for
+// one space k (P = 1..15, both number types), compiled once per k.
+#pragma once
+#include "df.cuh"
+
+namespace rmd {
+// launch the (K, A.p) instantiation (apply_cart_part.cu); writes every entry of y
+template <int K>
+cudaError_t launch_cart_part(const ApplyDev &A, const double *x, double *y, cudaStream_t s);
+
+namespace {
+
+constexpr int kCartThreads = 256;
+constexpr int kCartMaxP = 15;
+
+template <int K, int P>
+struct CartShape {
+  static constexpr int NC0 = ncomp(K), NC1 = ncomp(K + 1);
+  static constexpr int S0 = csize(K, P), S1 = csize(K + 1, P);  // per component
+  static constexpr int L0 = NC0 * S0, L1 = NC1 * S1;
+  static constexpr int NTERMS = K == 1 ? 6 : 3;                 // signed D-hat terms
+  static constexpr int LMAX = (P + 1) * (P + 1);                // lines per term (bound)
+  static constexpr int LS = NTERMS * LMAX * 2;                  // interface line sums
+  static constexpr int DREG = L1 > LS ? L1 : LS;                // d, later the line sums
+  static constexpr int CPB0 = kCartThreads / L1;
+  static constexpr int CPB = CPB0 < 1 ? 1 : (CPB0 > 32 ? 32 : CPB0);  // cells per CTA
+  // shared memory in units of R (8 bytes): D-hat, per cell 8 coefficients,
+  // x, y, d / line sums, dy
+  static constexpr int SMEM = P * (P + 1) + CPB * (8 + 2 * L0 + DREG + L1);
+};
+
+// (t, s) of the ts-th signed D-hat term: two per target component for the
+// curl, one per target for the gradient, three into the one divergence target
+__host__ __device__ constexpr int term_t(int k, int ts) { return k == 1 ? ts >> 1 : (k == 0 ? ts : 0); }
+__host__ __device__ constexpr int term_s(int k, int ts) { return k == 1 ? ts & 1 : (k == 0 ? 0 : ts); }
+
+// Box metric of kk-forms, component m (J = diag(h/2)).
+__device__ __forceinline__ double cart_metric(int kk, int m, double h0, double h1, double h2) {
+  const double det = 0.125 * h0 * h1 * h2;
+  const double hm = m == 0 ? h0 : (m == 1 ? h1 : h2);
+  if (kk == 0) return det;
+  if (kk == 3) return 1.0 / det;
+  if (kk == 1) return det * 4.0 / (hm * hm);
+  return 0.25 * hm * hm / det;
+}
+
+// (x)_d F_d at local index (i0, i1, i2) of one component block `in` with
+// local sizes (L0, L1, .) and s-type flags (T0, T1, T2): an s-type index on
+// the interface {0, P} couples to itself with weight a and to the opposite
+// index P - i with weight b; every other index only to itself.
+template <bool T0, bool T1, bool T2, int LL0, int LL1, int P, typename R>
+__device__ __forceinline__ R kron_mass(const R *in, int i0, int i1, int i2, R a, R b) {
+  const bool f0 = T0 && (i0 == 0 || i0 == P), f1 = T1 && (i1 == 0 || i1 == P),
+             f2 = T2 && (i2 == 0 || i2 == P);
+  auto line = [&](int base) -> R {
+    const R v = in[base + i0];
+    return f0 ? rfma(b, in[base + P - i0], rmul(a, v)) : v;
+  };
+  auto plane = [&](int j2) -> R {
+    const int b2 = LL0 * LL1 * j2;
+    const R v = line(b2 + LL0 * i1);
+    return f1 ? rfma(b, line(b2 + LL0 * (P - i1)), rmul(a, v)) : v;
+  };
+  const R v = plane(i2);
+  return f2 ? rfma(b, plane(P - i2), rmul(a, v)) : v;
+}
+
+template <int K, int P, typename R>
+__global__ void __launch_bounds__(kCartThreads) cart_local_kernel(ApplyDev A, const double *__restrict__ x,
+                                                                  double *__restrict__ Y) {
+  using Sh = CartShape<K, P>;
+  constexpr int NC0 = Sh::NC0, NC1 = Sh::NC1, S0 = Sh::S0, S1 = Sh::S1, L0 = Sh::L0, L1 = Sh::L1;
+  constexpr int CPB = Sh::CPB, DREG = Sh::DREG, LMAX = Sh::LMAX, NT = kCartThreads;
+  constexpr int Q1 = P + 1;
+  extern __shared__ double smd[];
+  R *sm = reinterpret_cast<R *>(smd);
+  R *D1 = sm;                    // D-hat, P x (P + 1)
+  R *coef = D1 + P * Q1;         // per cell: beta c_m (NC0), then alpha c'_t (NC1)
+  R *xl = coef + CPB * 8;        // CPB x L0
+  R *yl = xl + CPB * L0;         // CPB x L0
+  R *dl = yl + CPB * L0;         // CPB x DREG: d = D-hat x, then the line sums
+  R *dyl = dl + CPB * DREG;      // CPB x L1
+  __shared__ long long cbase[32][3];  // lattice index of local (0,0,0) per component
+  __shared__ int cdir[32];            // Dirichlet faces: bit 2d low side, 2d+1 high side
+  const int tid = threadIdx.x;
+  const int ncell = A.n[0] * A.n[1] * A.n[2];
+  const int c0 = blockIdx.x * CPB;
+  {
+    const double *g = A.tabs + A.q * Q1 + A.q * P;
+    for (int i = tid; i < P * Q1; i += NT) D1[i] = rfrom<R>(g[i]);
+  }
+  if (tid < CPB) {
+    const int c = c0 + tid;
+    if (c < ncell) {
+      const int e0 = c % A.n[0], e1 = (c / A.n[0]) % A.n[1], e2 = c / (A.n[0] * A.n[1]);
+      const double h0 = A.h[3 * c], h1 = A.h[3 * c + 1], h2 = A.h[3 * c + 2];
+      const double al = A.alpha[c], be = A.beta[c];
+      for (int m = 0; m < NC0; ++m) coef[tid * 8 + m] = rfrom<R>(be * cart_metric(K, m, h0, h1, h2));
+      for (int t = 0; t < NC1; ++t) coef[tid * 8 + 3 + t] = rfrom<R>(al * cart_metric(K + 1, t, h0, h1, h2));
+      for (int m = 0; m < NC0; ++m)
+        cbase[tid][m] = A.off[m] + (long long)e0 * P +
+                        (long long)A.N[m][0] * ((long long)e1 * P + (long long)A.N[m][1] * e2 * P);
+      int f = 0;
+      if (!A.natural) {
+        if (e0 == 0) f |= 1;
+        if (e0 == A.n[0] - 1) f |= 2;
+        if (e1 == 0) f |= 4;
+        if (e1 == A.n[1] - 1) f |= 8;
+        if (e2 == 0) f |= 16;
+        if (e2 == A.n[2] - 1) f |= 32;
+      }
+      cdir[tid] = f;
+    } else {
+      for (int m = 0; m < 8; ++m) coef[tid * 8 + m] = rzero(R());
+      for (int m = 0; m < NC0; ++m) cbase[tid][m] = -1;
+      cdir[tid] = 0;
+    }
+  }
+  __syncthreads();
+  const R ba = rfrom<R>(A.bh_a), bb = rfrom<R>(A.bh_b);
+  // ---- gather x (Dirichlet entries and padding cells read as 0) ----
+  sfor<NC0>([&](auto mc) {
+    constexpr int m = decltype(mc)::value;
+    constexpr bool t0 = styp(K, m, 0), t1 = styp(K, m, 1), t2 = styp(K, m, 2);
+    constexpr int l0 = sld(K, P, m, 0), l1 = sld(K, P, m, 1);
+    for (int li = tid; li < CPB * S0; li += NT) {
+      const int cb = li / S0, r = li - cb * S0;
+      const int i0 = r % l0, i1 = (r / l0) % l1, i2 = r / (l0 * l1);
+      const int f = cdir[cb];
+      const bool dir = (t0 && (((f & 1) && i0 == 0) || ((f & 2) && i0 == P))) ||
+                       (t1 && (((f & 4) && i1 == 0) || ((f & 8) && i1 == P))) ||
+                       (t2 && (((f & 16) && i2 == 0) || ((f & 32) && i2 == P)));
+      const long long b0 = cbase[cb][m];
+      double v = 0.0;
+      if (b0 >= 0 && !dir) v = x[b0 + i0 + (long long)A.N[m][0] * (i1 + (long long)A.N[m][1] * i2)];
+      xl[cb * L0 + m * S0 + r] = rfrom<R>(v);
+    }
+  });
+  __syncthreads();
+  // ---- y = beta M^K x;  d = D-hat x ----
+  sfor<NC0>([&](auto mc) {
+    constexpr int m = decltype(mc)::value;
+    constexpr bool t0 = styp(K, m, 0), t1 = styp(K, m, 1), t2 = styp(K, m, 2);
+    constexpr int l0 = sld(K, P, m, 0), l1 = sld(K, P, m, 1);
+    for (int li = tid; li < CPB * S0; li += NT) {
+      const int cb = li / S0, r = li - cb * S0;
+      const int i0 = r % l0, i1 = (r / l0) % l1, i2 = r / (l0 * l1);
+      yl[cb * L0 + m * S0 + r] =
+          rmul(coef[cb * 8 + m], kron_mass<t0, t1, t2, l0, l1, P>(xl + cb * L0 + m * S0, i0, i1, i2, ba, bb));
+    }
+  });
+  sfor<NC1>([&](auto tc) {
+    constexpr int t = decltype(tc)::value;
+    constexpr int l0 = sld(K + 1, P, t, 0), l1 = sld(K + 1, P, t, 1);
+    for (int li = tid; li < CPB * S1; li += NT) {
+      const int cb = li / S1, r = li - cb * S1;
+      const int j0 = r % l0, j1 = (r / l0) % l1, j2 = r / (l0 * l1);
+      R acc = rzero(R());
+      sfor<dterm_count(K, t)>([&](auto sc) {
+        constexpr DTerm T = dterm(K, t, decltype(sc)::value);
+        // the source is s-type along T.dir (P + 1 entries), equal elsewhere
+        constexpr int sl0 = T.dir == 0 ? Q1 : l0, sl1 = T.dir == 1 ? Q1 : l1;
+        constexpr int str = T.dir == 0 ? 1 : (T.dir == 1 ? sl0 : sl0 * sl1);
+        const int j = T.dir == 0 ? j0 : (T.dir == 1 ? j1 : j2);
+        const int base = (T.dir == 0 ? 0 : j0) + sl0 * ((T.dir == 1 ? 0 : j1) + sl1 * (T.dir == 2 ? 0 : j2));
+        const R *in = xl + cb * L0 + T.src * S0 + base;
+        R v = rmul(D1[j * Q1], in[0]);
+        v = rfma(D1[j * Q1 + P], in[P * str], v);
+        if (j >= 1) v = rfma(D1[j * Q1 + j], in[j * str], v);
+        acc = T.sgn > 0 ? radd(acc, v) : rsub(acc, v);
+      });
+      dl[cb * DREG + t * S1 + r] = acc;
+    }
+  });
+  __syncthreads();
+  // ---- dy = alpha M^{K+1} d ----
+  sfor<NC1>([&](auto tc) {
+    constexpr int t = decltype(tc)::value;
+    constexpr bool t0 = styp(K + 1, t, 0), t1 = styp(K + 1, t, 1), t2 = styp(K + 1, t, 2);
+    constexpr int l0 = sld(K + 1, P, t, 0), l1 = sld(K + 1, P, t, 1);
+    for (int li = tid; li < CPB * S1; li += NT) {
+      const int cb = li / S1, r = li - cb * S1;
+      const int j0 = r % l0, j1 = (r / l0) % l1, j2 = r / (l0 * l1);
+      dyl[cb * L1 + t * S1 + r] = rmul(coef[cb * 8 + 3 + t],
+                                       kron_mass<t0, t1, t2, l0, l1, P>(dl + cb * DREG + t * S1, j0, j1, j2, ba, bb));
+    }
+  });
+  __syncthreads();
+  // ---- line sums of D-hat^T's interface rows, into the d region: for every
+  // term and every line of its target component along the term's direction,
+  // (sum_j D[j][0] dy_j, sum_j D[j][P] dy_j) ----
+  sfor<Sh::NTERMS>([&](auto tsc) {
+    constexpr int ts = decltype(tsc)::value;
+    constexpr int t = term_t(K, ts);
+    constexpr DTerm T = dterm(K, t, term_s(K, ts));
+    constexpr int l0 = sld(K + 1, P, t, 0), l1 = sld(K + 1, P, t, 1), l2 = sld(K + 1, P, t, 2);
+    constexpr int la = T.dir == 0 ? l1 : l0, lb = T.dir == 2 ? l1 : l2;
+    constexpr int str = T.dir == 0 ? 1 : (T.dir == 1 ? l0 : l0 * l1);
+    for (int u = tid; u < CPB * la * lb; u += NT) {
+      const int cb = u / (la * lb), line = u - cb * (la * lb);
+      const int a = line % la, b = line / la;
+      const int c0i = T.dir == 0 ? 0 : a, c1i = T.dir == 0 ? a : (T.dir == 1 ? 0 : b), c2i = T.dir == 2 ? 0 : b;
+      const R *in = dyl + cb * L1 + t * S1 + c0i + l0 * (c1i + l1 * c2i);
+      Acc<R> v0, vp;
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        const R dj = in[j * str];
+        v0.add(D1[j * Q1], dj);
+        vp.add(D1[j * Q1 + P], dj);
+      }
+      dl[cb * DREG + 2 * (ts * LMAX + line)] = v0.val();
+      dl[cb * DREG + 2 * (ts * LMAX + line) + 1] = vp.val();
+    }
+  });
+  __syncthreads();
+  // ---- y += D-hat^T dy; the cell's unassembled product to Y ----
+  sfor<NC0>([&](auto mc) {
+    constexpr int m = decltype(mc)::value;
+    constexpr int l0 = sld(K, P, m, 0), l1 = sld(K, P, m, 1);
+    for (int li = tid; li < CPB * S0; li += NT) {
+      const int cb = li / S0, r = li - cb * S0;
+      const int i0 = r % l0, i1 = (r / l0) % l1, i2 = r / (l0 * l1);
+      R acc = yl[cb * L0 + m * S0 + r];
+      sfor<Sh::NTERMS>([&](auto tsc) {
+        constexpr int ts = decltype(tsc)::value;
+        constexpr int t = term_t(K, ts);
+        constexpr DTerm T = dterm(K, t, term_s(K, ts));
+        if constexpr (T.src == m) {
+          // the target is r-type along T.dir (P entries), equal elsewhere
+          constexpr int tl0 = T.dir == 0 ? P : l0, tl1 = T.dir == 1 ? P : l1;
+          const int i = T.dir == 0 ? i0 : (T.dir == 1 ? i1 : i2);
+          R v;
+          if (i == 0 || i == P) {
+            const int a = T.dir == 0 ? i1 : i0, b = T.dir == 2 ? i1 : i2;
+            constexpr int la = T.dir == 0 ? tl1 : tl0;
+            v = dl[cb * DREG + 2 * (ts * LMAX + a + la * b) + (i == 0 ? 0 : 1)];
+          } else {
+            constexpr int str = T.dir == 0 ? 1 : (T.dir == 1 ? tl0 : tl0 * tl1);
+            const int base = (T.dir == 0 ? 0 : i0) + tl0 * ((T.dir == 1 ? 0 : i1) + tl1 * (T.dir == 2 ? 0 : i2));
+            v = rmul(D1[i * Q1 + i], dyl[cb * L1 + t * S1 + base + i * str]);
+          }
+          acc = T.sgn > 0 ? radd(acc, v) : rsub(acc, v);
+        }
+      });
+      const int c = c0 + cb;
+      if (c < ncell) Y[(size_t)c * L0 + m * S0 + r] = rto(acc);
+    }
+  });
+}
+
+// y[g] = sum over the cells holding lattice entry g of their contribution in
+// Y, in a fixed order (cells lexicographic); Dirichlet entries 0.  Grid:
+// x along g0, y over rows (g1, g2), z over components.
+template <int K, int P>
+__global__ void __launch_bounds__(128) cart_assemble_kernel(ApplyDev A, const double *__restrict__ Y,
+                                                            double *__restrict__ y) {
+  using Sh = CartShape<K, P>;
+  const int m = blockIdx.z;
+  const int N0 = A.N[m][0], N1 = A.N[m][1], N2 = A.N[m][2];
+  const int g0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g0 >= N0) return;
+  bool st[3];
+  int l[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    st[d] = styp(K, m, d);
+    l[d] = st[d] ? P + 1 : P;
+  }
+  for (int row = blockIdx.y; row < N1 * N2; row += gridDim.y) {
+    const int g[3] = {g0, row % N1, row / N1};
+    // per direction the (cell, local index) pairs holding g: two on an
+    // s-type interface plane inside the mesh, else one
+    int ce[3][2], ci[3][2], nc[3];
+    bool dir = false;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int e = g[d] / P, i = g[d] - e * P;
+      if (st[d] && i == 0) {
+        if (!A.natural && (g[d] == 0 || e == A.n[d])) dir = true;
+        nc[d] = 0;
+        if (e >= 1) { ce[d][nc[d]] = e - 1; ci[d][nc[d]] = P; nc[d]++; }
+        if (e < A.n[d]) { ce[d][nc[d]] = e; ci[d][nc[d]] = 0; nc[d]++; }
+      } else {
+        nc[d] = 1;
+        ce[d][0] = e;
+        ci[d][0] = i;
+      }
+    }
+    double s = 0.0;
+    if (!dir)
+      for (int c = 0; c < nc[2]; ++c)
+        for (int b = 0; b < nc[1]; ++b)
+          for (int a = 0; a < nc[0]; ++a) {
+            const size_t cell = ce[0][a] + (size_t)A.n[0] * (ce[1][b] + (size_t)A.n[1] * ce[2][c]);
+            s += Y[cell * Sh::L0 + m * Sh::S0 + ci[0][a] + l[0] * (ci[1][b] + l[1] * ci[2][c])];
+          }
+    y[A.off[m] + g0 + (long long)N0 * row] = s;
+  }
+}
+
+template <int K, int P, typename R>
+cudaError_t launch_cart_kpr(const ApplyDev &A, const double *x, double *y, cudaStream_t s) {
+  using Sh = CartShape<K, P>;
+  const size_t smem = (size_t)Sh::SMEM * sizeof(double);
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t err =
+      cudaFuncSetAttribute(cart_local_kernel<K, P, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  const int ncell = A.n[0] * A.n[1] * A.n[2];
+  cart_local_kernel<K, P, R><<<(ncell + Sh::CPB - 1) / Sh::CPB, kCartThreads, smem, s>>>(A, x, A.Y);
+  err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  int rows = 0, n0max = 0;
+  for (int m = 0; m < Sh::NC0; ++m) {
+    rows = rows > A.N[m][1] * A.N[m][2] ? rows : A.N[m][1] * A.N[m][2];
+    n0max = n0max > A.N[m][0] ? n0max : A.N[m][0];
+  }
+  const dim3 grid((n0max + 127) / 128, rows < 65535 ? rows : 65535, Sh::NC0);
+  cart_assemble_kernel<K, P><<<grid, 128, 0, s>>>(A, A.Y, y);
+  return cudaGetLastError();
+}
+template <int K, int P>
+cudaError_t launch_cart_kp(const ApplyDev &A, const double *x, double *y, cudaStream_t s) {
+  return A.arith ? launch_cart_kpr<K, P, DF>(A, x, y, s) : launch_cart_kpr<K, P, double>(A, x, y, s);
+}
+template <int K, int... PS>
+cudaError_t launch_cart_range(const ApplyDev &A, const double *x, double *y, cudaStream_t s,
+                              std::integer_sequence<int, PS...>) {
+  cudaError_t err = cudaErrorInvalidValue;
+  ((A.p == PS + 1 ? (err = launch_cart_kp<K, PS + 1>(A, x, y, s), 0) : 0), ...);
+  return err;
+}
+
+}  // namespace
+}  // namespace rmd

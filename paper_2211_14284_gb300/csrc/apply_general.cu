@@ -1,6 +1,7 @@
 // Operator apply on general (trilinear) cells: the pullback metric at the
 // quadrature points (setup) and the dispatch to the compile-time (k, p)
 // instantiations of the apply kernel (apply_general.cuh).
+#include "apply_cart.cuh"
 #include "apply_general.cuh"
 
 namespace rmd {
@@ -102,6 +103,15 @@ cudaError_t launch_metric(const ApplyDev &A, void *G, cudaStream_t s) {
   else metric_kernel<double><<<ncell, 256, 0, s>>>(A, static_cast<double *>(G));
   add_launches(1);
   return cudaGetLastError();
+}
+
+cudaError_t launch_apply_cart(const ApplyDev &A, const double *x, double *y, cudaStream_t s) {
+  cudaError_t err = cudaErrorInvalidValue;
+  if (A.k == 0) err = launch_cart_part<0>(A, x, y, s);
+  else if (A.k == 1) err = launch_cart_part<1>(A, x, y, s);
+  else if (A.k == 2) err = launch_cart_part<2>(A, x, y, s);
+  if (err == cudaSuccess) add_launches(2);
+  return err;
 }
 
 cudaError_t launch_apply_general(const ApplyDev &A, const double *x, double *y, cudaStream_t s) {

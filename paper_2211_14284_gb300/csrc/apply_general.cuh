@@ -31,13 +31,7 @@ cudaError_t launch_general_part(int p, const ApplyDev &A, const double *x, doubl
 
 namespace {
 
-// ---- compile-time shapes -----------------------------------------------------
-// local size per direction of a component of V^kk on a cell of degree p
-__host__ __device__ constexpr int sld(int kk, int p, int m, int d) { return styp(kk, m, d) ? p + 1 : p; }
-// every component of V^kk has the same local size on a cell
-__host__ __device__ constexpr int csize(int kk, int p) {
-  return sld(kk, p, 0, 0) * sld(kk, p, 0, 1) * sld(kk, p, 0, 2);
-}
+// ---- compile-time shapes (sld, csize in df.cuh) --------------------------------
 // pullback-metric entries of kk-forms: scalar or symmetric 3x3
 __host__ __device__ constexpr int nweights(int kk) { return (kk == 0 || kk == 3) ? 1 : 6; }
 
@@ -58,16 +52,6 @@ __device__ __forceinline__ int unit_even(int u) {
 template <bool S, int PP>
 __device__ __forceinline__ int unit_odd(int u) {
   return S ? (u == 0 ? 0 : (2 * u <= PP - 1 ? 2 * u : -1)) : (2 * u + 1 < PP ? 2 * u + 1 : -1);
-}
-
-template <int... I, typename F>
-__device__ __forceinline__ void sfor_seq(std::integer_sequence<int, I...>, F &&f) {
-  (f(std::integral_constant<int, I>{}), ...);
-}
-// f(integral_constant<int, i>) for i = 0 .. N-1, unrolled at compile time
-template <int N, typename F>
-__device__ __forceinline__ void sfor(F &&f) {
-  sfor_seq(std::make_integer_sequence<int, N>{}, f);
 }
 
 constexpr int NT = kApplyThreadsGeneral;

@@ -327,10 +327,10 @@ void build_apply(rm_handle *h, const Geometry &geo, const std::vector<double> &a
       A.h = h->upload(hc);
       A.bh_a = B.Bhat[0];
       A.bh_b = B.Bhat[p];
-      A.cidx = h->upload(cart_index_table(h->k, p));
       const size_t smem = cart_smem_doubles(h->k, p, A.nloc0, A.nloc1);
       if (smem * sizeof(double) > 227 * 1024)
         throw std::runtime_error("degree too high for the Cartesian apply kernel's shared memory");
+      A.Y = h->dalloc<double>((size_t)ncell * A.nloc0);  // unassembled cell products
       A.G = nullptr;
       return;
     }
@@ -544,7 +544,8 @@ void precondition(rm_handle *h, const double *r, double *z) {
 }
 
 void apply(rm_handle *h, const double *x, double *y) {
-  CK(cudaMemsetAsync(y, 0, h->size * sizeof(double), h->stream));
+  // the Cartesian apply writes every entry; the general one scatter-adds
+  if (!h->ad.cartesian) CK(cudaMemsetAsync(y, 0, h->size * sizeof(double), h->stream));
   CK(launch_apply(h->ad, x, y, h->stream));
 }
 
@@ -591,8 +592,8 @@ int rm_setup(rm_handle **out, int space, const rm_mesh *mesh, int p, const doubl
     h->n[2] = mesh->nz;
     const rm_options &o = h->opt;
     if (o.precision != RM_FP64 && o.precision != RM_FP32) throw std::invalid_argument("precision");
-    if (o.decomposition == RM_PH && (space != RM_HCURL || !o.static_condensation))
-      throw std::invalid_argument("RM_PH needs RM_HCURL and static_condensation = 1");
+    if (o.decomposition == RM_PH && (space == RM_HGRAD || !o.static_condensation))
+      throw std::invalid_argument("RM_PH needs RM_HCURL or RM_HDIV and static_condensation = 1");
     if (o.rtol <= 0 || o.max_it < 1 || o.check_every < 1) throw std::invalid_argument("rtol/max_it/check_every");
     if (o.norm != RM_NORM_L2 && o.norm != RM_NORM_NATURAL) throw std::invalid_argument("norm");
     if (o.arith != RM_ARITH_FP64 && o.arith != RM_ARITH_DF64) throw std::invalid_argument("arith");
@@ -652,24 +653,38 @@ int rm_setup(rm_handle **out, int space, const rm_mesh *mesh, int p, const doubl
         PatchFamily F = build_patches(h->L, fm, C.S, 0, true, o.factor == RM_ICC ? 1 : 0);
         h->fam.push_back(upload_family(h.get(), F));
       } else {
-        // edge stars of S (exact Cholesky), Eq. sc-asm-hiptmair
+        // stars of the k-entities on S, exact Cholesky (Eq. sc-asm-hiptmair):
+        // edges for H(curl); faces for H(div), whose blocks of S are diagonal
+        // in the FDM basis (the relaxation is point-Jacobi on S, Sec. 4.5)
         for (int m = 0; m < 3; ++m) {
-          PatchFamily F = build_patches(h->L, fm, C.S, 1 << m, true, 0);
+          const int span = space == RM_HCURL ? (1 << m) : (7 & ~(1 << m));
+          PatchFamily F = build_patches(h->L, fm, C.S, span, true, 0);
           h->fam.push_back(upload_family(h.get(), F));
         }
-        // potential: H(grad) auxiliary operator with mass 0, stiffness beta
-        Layout L0(0, h->n, p, h->L.natural);
+        // potential space V^{k-1}, B = (d phi, beta d psi) (Sec. 4.3) as its
+        // auxiliary operator with derivative coefficient beta and mass
+        // coefficient 0 (H(curl)) or eps beta (H(div): the curl-curl patch
+        // matrices are singular, Remark after Eq. ph); stars of the
+        // (k-1)-entities: vertices (H(curl)) or edges (H(div))
+        Layout L0(space - 1, h->n, p, h->L.natural);
         FreeMap fm0(L0);
-        std::vector<double> zero(ncell, 0.0);
-        Csr B = assemble_aux(L0, geo, zero.data(), be.data(), fm0);
+        std::vector<double> pmass(ncell, 0.0);
+        if (space == RM_HDIV)
+          for (int c = 0; c < ncell; ++c) pmass[c] = kHdivPotentialEps * be[c];
+        Csr B = assemble_aux(L0, geo, pmass.data(), be.data(), fm0);
         Condensed C0 = condense(L0, fm0, B);
-        PatchFamily F0 = build_patches(L0, fm0, C0.S, 0, true, o.factor == RM_ICC ? 1 : 0);
-        h->pfam.push_back(upload_family(h.get(), F0));
+        if (space == RM_HCURL) {
+          h->pfam.push_back(upload_family(h.get(), build_patches(L0, fm0, C0.S, 0, true, o.factor == RM_ICC ? 1 : 0)));
+        } else {
+          for (int m = 0; m < 3; ++m)
+            h->pfam.push_back(
+                upload_family(h.get(), build_patches(L0, fm0, C0.S, 1 << m, true, o.factor == RM_ICC ? 1 : 0)));
+        }
         h->size0 = L0.size;
         std::vector<int> G1, G0;
         for (int f : C.G) G1.push_back(fm.free2lat[f]);
         for (int f : C0.G) G0.push_back(fm0.free2lat[f]);
-        Csr D = discrete_gradient(L0, h->L, G1, G0);
+        Csr D = discrete_derivative(L0, h->L, G1, G0);
         h->Dt = upload_csr(h.get(), D, nullptr, nullptr, &G1);
         h->DtT = upload_csr(h.get(), transpose(D), nullptr, nullptr, &G0);
         h->u0 = h->dalloc<double>(h->size0);

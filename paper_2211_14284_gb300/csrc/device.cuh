@@ -34,7 +34,8 @@ struct ApplyDev {
   int cartesian;
   const double *h;
   double bh_a, bh_b;
-  const int *cidx;         // cart_index_table(k, p)
+  const int *cidx;         // cart_index_table(k, p) (batched apply)
+  double *Y;               // unassembled cell products, ncell x nloc0 (Cartesian apply)
   int prob;                // batched solves: the problem's index
   int arith;               // number type of the apply: 0 double, 1 double-float (DF)
   int natural;             // 1: Gamma_D empty (no Dirichlet entries)
@@ -266,6 +267,9 @@ cudaError_t launch_apply(const ApplyDev &A, const double *x, double *y, cudaStre
 // general cells (apply_general.cu)
 cudaError_t launch_apply_general(const ApplyDev &A, const double *x, double *y, cudaStream_t s);
 cudaError_t launch_metric(const ApplyDev &A, void *G, cudaStream_t s);
+// Cartesian cells (apply_cart.cu): cell products into A.Y, then assembled;
+// writes every entry of y (no zeroing needed)
+cudaError_t launch_apply_cart(const ApplyDev &A, const double *x, double *y, cudaStream_t s);
 // spmv modes: 0 y = a A x; 1 y += a A x; 2 y = u + a A x; 3 y += a A x with
 // atomic adds (rows shared with other kernels adding concurrently)
 cudaError_t launch_spmv(const DevCsr &M, const double *x, double *y, const double *u, int mode,

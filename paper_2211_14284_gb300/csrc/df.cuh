@@ -3,6 +3,9 @@
 // arithmetic and the dot-product accumulator.
 #pragma once
 
+#include <type_traits>
+#include <utility>
+
 #include "device.cuh"
 
 namespace rmd {
@@ -27,6 +30,23 @@ __host__ __device__ constexpr DTerm dterm(int k, int t, int s) {
   return k == 0   ? DTerm{0, t, 1}
          : k == 1 ? (s == 0 ? DTerm{(t + 2) % 3, (t + 1) % 3, 1} : DTerm{(t + 1) % 3, (t + 2) % 3, -1})
                   : DTerm{s, s, 1};
+}
+
+// ---- compile-time shapes and loops ---------------------------------------------
+// local size per direction of a component of V^kk on a cell of degree p
+__host__ __device__ constexpr int sld(int kk, int p, int m, int d) { return styp(kk, m, d) ? p + 1 : p; }
+// every component of V^kk has the same local size on a cell
+__host__ __device__ constexpr int csize(int kk, int p) {
+  return sld(kk, p, 0, 0) * sld(kk, p, 0, 1) * sld(kk, p, 0, 2);
+}
+template <int... I, typename F>
+__device__ __forceinline__ void sfor_seq(std::integer_sequence<int, I...>, F &&f) {
+  (f(std::integral_constant<int, I>{}), ...);
+}
+// f(integral_constant<int, i>) for i = 0 .. N-1, unrolled at compile time
+template <int N, typename F>
+__device__ __forceinline__ void sfor(F &&f) {
+  sfor_seq(std::make_integer_sequence<int, N>{}, f);
 }
 
 // ---- number types of the general apply --------------------------------------

@@ -66,7 +66,7 @@ int rmh_gll(int q, double *x, double *w) {
 }
 
 // Builds P, the Schur complement and the patch families as rm_setup would.
-// mode & 15: 0 non-condensed PAFW, 1 SC-PAFW, 2 SC-PH (k = 1); mode & 16:
+// mode & 15: 0 non-condensed PAFW, 1 SC-PAFW, 2 SC-PH (k = 1, 2); mode & 16:
 // Gamma_D empty (natural boundary conditions).
 int rmh_build(int k, const int n[3], int p, const double *X, const double *alpha,
               const double *beta, int mode, int factor, int coarse) {
@@ -92,18 +92,24 @@ int rmh_build(int k, const int n[3], int p, const double *X, const double *alpha
       if (mode == 1) {
         g->fams.push_back(build_patches(g->L, g->fm, C.S, 0, true, factor));
       } else {
-        for (int m = 0; m < 3; ++m) g->fams.push_back(build_patches(g->L, g->fm, C.S, 1 << m, true, 0));
-        g->L0 = Layout(0, n, p, natural);
+        for (int m = 0; m < 3; ++m)
+          g->fams.push_back(build_patches(g->L, g->fm, C.S, k == 1 ? (1 << m) : (7 & ~(1 << m)), true, 0));
+        g->L0 = Layout(k - 1, n, p, natural);
         g->fm0 = FreeMap(g->L0);
-        std::vector<double> zero(ncell, 0.0);
-        Csr B = assemble_aux(g->L0, geo, zero.data(), beta, g->fm0);
+        std::vector<double> pmass(ncell, 0.0);
+        if (k == 2)
+          for (int c = 0; c < ncell; ++c) pmass[c] = kHdivPotentialEps * beta[c];
+        Csr B = assemble_aux(g->L0, geo, pmass.data(), beta, g->fm0);
         Condensed C0 = condense(g->L0, g->fm0, B);
         g->S0 = C0.S;
-        g->fams.push_back(build_patches(g->L0, g->fm0, C0.S, 0, true, factor));
+        if (k == 1)
+          g->fams.push_back(build_patches(g->L0, g->fm0, C0.S, 0, true, factor));
+        else
+          for (int m = 0; m < 3; ++m) g->fams.push_back(build_patches(g->L0, g->fm0, C0.S, 1 << m, true, factor));
         std::vector<int> G1, G0;
         for (int f : C.G) G1.push_back(g->fm.free2lat[f]);
         for (int f : C0.G) G0.push_back(g->fm0.free2lat[f]);
-        g->Dt = discrete_gradient(g->L0, g->L, G1, G0);
+        g->Dt = discrete_derivative(g->L0, g->L, G1, G0);
       }
     }
     if (coarse) g->coarse = build_coarse(g->L, geo, alpha, beta);

@@ -1426,30 +1426,41 @@ CoarseData build_coarse_gmg(const Layout &Lf, const Geometry &geo, const double 
   return C;
 }
 
-Csr discrete_gradient(const Layout &L0, const Layout &L1, const std::vector<int> &rows1,
-                      const std::vector<int> &cols0) {
-  const int p = L0.p;
+Csr discrete_derivative(const Layout &La, const Layout &Lb, const std::vector<int> &rows,
+                        const std::vector<int> &cols) {
+  const int p = La.p, kk = La.k;
+  if (kk < 0 || kk > 2 || Lb.k != kk + 1) throw std::runtime_error("discrete_derivative: V^k -> V^{k+1}");
   Basis1D B(p);
-  std::vector<char> okc(L0.size, 0);
-  for (int c : cols0) okc[c] = 1;
+  std::vector<char> okc(La.size, 0);
+  for (int c : cols) okc[c] = 1;
   std::vector<Trip> t;
-  for (int r : rows1) {
+  for (int r : rows) {
     int m;
     long long g[3];
-    L1.coords(r, m, g);
-    long long e = g[m] / p;
-    int i = (int)(g[m] % p);
-    for (int l = 0; l <= p; ++l) {
-      double v = B.D[i * (p + 1) + l];
-      if (v == 0.0) continue;
-      long long h[3] = {g[0], g[1], g[2]};
-      h[m] = e * p + l;
-      long long c = L0.index(0, h[0], h[1], h[2]);
-      if (!okc[c]) continue;
-      t.push_back({r, (int)c, v});
+    Lb.coords(r, m, g);
+    // target component m of V^{k+1}: each term reads source component src,
+    // s-type along dr where the target is r-type, equal in the other directions
+    for (int s = 0; s < kNumTerms[kk][m]; ++s) {
+      const DTerm &T = kTerms[kk][m][s];
+      const long long e = g[T.dir] / p;
+      const int i = (int)(g[T.dir] % p);
+      for (int l = 0; l <= p; ++l) {
+        const double v = B.D[i * (p + 1) + l];
+        if (v == 0.0) continue;
+        long long h[3] = {g[0], g[1], g[2]};
+        h[T.dir] = e * p + l;
+        const long long c = La.index(T.src, h[0], h[1], h[2]);
+        if (!okc[c]) continue;
+        t.push_back({r, (int)c, T.sgn * v});
+      }
     }
   }
-  return csr_from_triplets((int)L1.size, (int)L0.size, t);
+  return csr_from_triplets((int)Lb.size, (int)La.size, t);
+}
+
+Csr discrete_gradient(const Layout &L0, const Layout &L1, const std::vector<int> &rows1,
+                      const std::vector<int> &cols0) {
+  return discrete_derivative(L0, L1, rows1, cols0);
 }
 
 }  // namespace rm

@@ -158,6 +158,16 @@ struct CoarseGMG {
 CoarseData build_coarse_gmg(const Layout &Lf, const Geometry &geo, const double *alpha,
                             const double *beta, CoarseGMG &mg);
 
+// Discrete exterior derivative d^k: V^k (La) -> V^{k+1} (Lb) in FDM
+// coefficients (cellwise D-hat, Sec. 2.3), restricted to the given rows
+// (V^{k+1} lattice ids) and columns (V^k lattice ids).
+Csr discrete_derivative(const Layout &La, const Layout &Lb, const std::vector<int> &rows,
+                        const std::vector<int> &cols);
+// H(div) SC-PH potential operator: (curl phi, beta curl psi) + eps (phi, beta
+// psi), eps = the small mass multiple the paper adds to its singular patch
+// matrices (Remark after Eq. ph); 1e-2, iteration counts flat for eps in
+// [1e-4, 1e-1].
+constexpr double kHdivPotentialEps = 1e-2;
 // Discrete gradient V^0 -> V^1 restricted to free rows/cols (lattice ids).
 Csr discrete_gradient(const Layout &L0, const Layout &L1, const std::vector<int> &rows1,
                       const std::vector<int> &cols0);

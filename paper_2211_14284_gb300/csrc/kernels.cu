@@ -238,12 +238,6 @@ __device__ void cart_cell_k(const ApplyDev &P, const int c, const double *__rest
   }
 }
 
-template <int K, typename R>
-__global__ void __launch_bounds__(kApplyThreads) apply_cart_kernel(ApplyDev P, const double *__restrict__ x,
-                                                                   double *__restrict__ y) {
-  cart_cell_k<K, R>(P, blockIdx.x, x, y);
-}
-
 // Batched: work[b] = (problem, cell); descriptors in global memory.
 __global__ void __launch_bounds__(kApplyThreads) apply_cart_batch_kernel(const ApplyDev *__restrict__ descs,
                                                                          const int2 *__restrict__ work,
@@ -736,21 +730,7 @@ inline int grid_for(long long n, int threads) {
 }  // namespace
 
 cudaError_t launch_apply(const ApplyDev &A, const double *x, double *y, cudaStream_t s) {
-  const int ncell = A.n[0] * A.n[1] * A.n[2];
-  if (A.cartesian) {
-    const size_t smem = cart_smem_doubles(A.k, A.p, A.nloc0, A.nloc1) * sizeof(double);
-    auto go = [&](auto kern) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) kern<<<ncell, kApplyThreads, smem, s>>>(A, x, y);
-      return e;
-    };
-    cudaError_t err;
-    if (A.arith) err = A.k == 0 ? go(apply_cart_kernel<0, DF>) : A.k == 1 ? go(apply_cart_kernel<1, DF>) : go(apply_cart_kernel<2, DF>);
-    else err = A.k == 0 ? go(apply_cart_kernel<0, double>) : A.k == 1 ? go(apply_cart_kernel<1, double>) : go(apply_cart_kernel<2, double>);
-    if (err != cudaSuccess) return err;
-    g_launches += 1;
-    return cudaGetLastError();
-  }
+  if (A.cartesian) return launch_apply_cart(A, x, y, s);
   return launch_apply_general(A, x, y, s);
 }
 

@@ -115,7 +115,9 @@ PREC_CASES = [(0, 3, 2, 0.0, "pafw", {}), (0, 3, 3, 0.1, "sc-icc", dict(static_c
               (2, 3, 2, 0.1, "sc-icc", dict(static_condensation=1, factor=1)),
               (1, 3, 3, 0.1, "sc-chol", dict(static_condensation=1, factor=0)),
               (1, 2, 3, 0.1, "scph", dict(static_condensation=1, decomposition=1, factor=1)),
-              (0, (2, 3, 3), 2, 0.15, "sc-chol", dict(static_condensation=1, factor=0))]
+              (0, (2, 3, 3), 2, 0.15, "sc-chol", dict(static_condensation=1, factor=0)),
+              (2, 2, 3, 0.1, "scph", dict(static_condensation=1, decomposition=1, factor=1)),
+              (2, (3, 2, 2), 2, 0.0, "scph", dict(static_condensation=1, decomposition=1, factor=1))]
 
 
 @pytest.mark.parametrize("k,n,p,perturb,mode,opts", PREC_CASES)
@@ -132,7 +134,7 @@ def test_precondition_parity(k, n, p, perturb, mode, opts):
     # The two setups assemble P and S in different summation orders (~1e-13
     # relative); the patch solves amplify that by cond(L L^T), so the bound
     # is 1e-12 * max cond over the oracle's patch factors (floor 1e-11).
-    solvers = (M.edge + [M.vertex]) if mode == "scph" else [M.patches]
+    solvers = (M.edge + M.potential) if mode == "scph" else [M.patches]
     cond = max(np.linalg.cond(L) ** 2 for ps in solvers for L in ps.L)
     tol = max(1e-11, 1e-12 * cond)
     assert np.abs(got - want).max() <= tol * np.abs(want).max()
@@ -176,7 +178,8 @@ def test_manufactured_solution_config1():
 
 
 @pytest.mark.parametrize("k,mode,opts", [(0, "sc-icc", dict(static_condensation=1, factor=1)),
-                                         (1, "scph", dict(static_condensation=1, decomposition=1, factor=1))])
+                                         (1, "scph", dict(static_condensation=1, decomposition=1, factor=1)),
+                                         (2, "scph", dict(static_condensation=1, decomposition=1, factor=1))])
 def test_solve_distorted_parity(k, mode, opts):
     """Distorted mesh, SC preconditioners on the auxiliary operator: GPU
     solution vs direct solve (both to 1e-12), iteration count vs oracle PCG."""
@@ -279,3 +282,100 @@ def test_failures_are_status_codes():
     b[centre] = 0.0
     x.zero_()
     assert s2.solve(b, x)["status"] == "RM_OK"
+
+
+# -- the headline degree, the paper's coefficient extremes ------------------------
+@pytest.mark.parametrize("k,mode,opts", [
+    (0, "sc-icc", dict(static_condensation=1, factor=1)),
+    (1, "scph", dict(static_condensation=1, decomposition=1, factor=1))])
+def test_precondition_parity_p7(k, mode, opts):
+    """p = 7 on 2^3 distorted cells: the headline's relaxations (the 469-slot
+    vertex-star S_v with its 16-level ICC(0) schedule for H(grad); edge stars
+    and vertex-star potentials for H(curl)) elementwise against the oracle,
+    in FP64 and with the FP32 preconditioner (bound: FP32 rounding times the
+    patch condition number)."""
+    for precision in (0, 1):
+        s, pr = _setup(k, 2, 7, 0.1, True, seed=17, precision=precision, **opts)
+        r = inputs.normal_rhs(pr.lat.size, 27)
+        r[np.setdiff1d(np.arange(pr.lat.size), pr.free)] = 0.0
+        z = torch.zeros(pr.lat.size, dtype=torch.float64, device="cuda")
+        s.precondition(_dev(r), z)
+        M = _oracle_prec(pr, mode)
+        want = np.zeros(pr.lat.size)
+        want[pr.free] = M.apply(r[pr.free])
+        got = _host(z)
+        solvers = (M.edge + M.potential) if mode == "scph" else [M.patches]
+        cond = max(np.linalg.cond(L) ** 2 for ps in solvers for L in ps.L)
+        tol = max(1e-11, 1e-12 * cond) if precision == 0 else max(1e-5, 6e-8 * cond)
+        err = np.abs(got - want).max() / np.abs(want).max()
+        assert err <= tol, (precision, err, cond)
+
+
+@pytest.mark.parametrize("arith", [0, 1], ids=["fp64", "df64"])
+@pytest.mark.parametrize("k,lo,hi,beta", [(0, 1e-6, 1e6, None), (1, 1.0, 1.0, 1e-8),
+                                           (1, 1e-6, 1e6, None), (2, 1e-6, 1e6, 1e-8)])
+def test_apply_parity_coefficient_extremes(k, lo, hi, beta, arith):
+    """The paper's coefficient ranges: beta = 1e-8 with alpha = 1 (Sec. 5.1)
+    and alpha, beta log-uniform over 1e-6 .. 1e6 per cell (tab. hcurl-sweep,
+    hdiv-sweep), general cells, both number types of the apply."""
+    from paper_2211_14284_gb300.rm import Solver
+    n, p = 2, 4
+    X = inputs.vertices(n, perturb=0.1, seed=61)
+    al = inputs.loguniform_coefficient(n, lo, hi, seed=62)
+    be = (np.full(n ** 3, beta) if beta is not None
+          else inputs.loguniform_coefficient(n, lo, hi, seed=63))
+    s = Solver(k, n, p, vertices=X, alpha=al, beta=be, arith=arith)
+    pr = Problem(k, n, p, X, al, be)
+    x = inputs.normal_rhs(pr.lat.size, 64)
+    y = torch.zeros(pr.lat.size, dtype=torch.float64, device="cuda")
+    s.apply(_dev(x), y)
+    want = pr.apply(x)
+    assert np.abs(_host(y) - want).max() <= 1e-12 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("k,mode,opts", [
+    (1, "scph", dict(static_condensation=1, decomposition=1, factor=1)),
+    (2, "scph", dict(static_condensation=1, decomposition=1, factor=1)),
+    (0, "sc-icc", dict(static_condensation=1, factor=1))])
+def test_solve_paper_coefficients(k, mode, opts):
+    """alpha = 1, beta = 1e-8 (the paper's Riesz-map experiments, Sec. 5.1):
+    the GPU iteration count to 1e-8 is the oracle PCG's with the same
+    preconditioner (+-1), and the true residual meets the tolerance."""
+    from paper_2211_14284_gb300.rm import Solver
+    n, p = 3, 3
+    X = inputs.vertices(n, perturb=0.1, seed=65)
+    al = np.ones(n ** 3)
+    be = np.full(n ** 3, 1e-8)
+    s = Solver(k, n, p, vertices=X, alpha=al, beta=be, rtol=1e-8, max_it=600, **opts)
+    pr = Problem(k, n, p, X, al, be)
+    b = inputs.normal_rhs(pr.lat.size, 66)
+    x = torch.zeros(pr.lat.size, dtype=torch.float64, device="cuda")
+    info = s.solve(_dev(b), x)
+    assert info["status"] == "RM_OK"
+    A = pr.A_free()
+    _, io = pcg(A, b[pr.free], _oracle_prec(pr, mode).apply, rtol=1e-8)
+    assert abs(info["iterations"] - io["iterations"]) <= 1, (info["iterations"], io["iterations"])
+    xf = _host(x)
+    res = np.linalg.norm(b[pr.free] - A @ xf[pr.free]) / np.linalg.norm(b[pr.free])
+    assert res <= 2e-8
+
+
+@pytest.mark.slow
+def test_precondition_parity_unstaged_factor():
+    """A patch factor too large to stage in shared memory (the unstaged
+    substitution kernel reads it from global memory): H(grad) SC-PAFW with
+    ICC(0) at p = 12 on 2^3 Cartesian cells, FP64 -- 1,519 slots and 36,433
+    factor entries per vertex star, 304 KB."""
+    s, pr = _setup(0, 2, 12, 0.0, True, seed=19, static_condensation=1, factor=1)
+    st = s.stats()
+    per_patch = (st["slots"] + st["factor_nnz"]) / st["patches"] * 8
+    assert per_patch > 220 * 1024
+    r = inputs.normal_rhs(pr.lat.size, 28)
+    r[np.setdiff1d(np.arange(pr.lat.size), pr.free)] = 0.0
+    z = torch.zeros(pr.lat.size, dtype=torch.float64, device="cuda")
+    s.precondition(_dev(r), z)
+    M = _oracle_prec(pr, "sc-icc")
+    want = np.zeros(pr.lat.size)
+    want[pr.free] = M.apply(r[pr.free])
+    cond = max(np.linalg.cond(L) ** 2 for L in M.patches.L)
+    assert np.abs(_host(z) - want).max() <= max(1e-11, 1e-12 * cond) * np.abs(want).max()
