@@ -41,10 +41,35 @@ SPACES = [
     ("hgrad", 0, dict(static_condensation=1, factor=1)),
     ("hcurl", 1, dict(static_condensation=1, factor=1, decomposition=1)),
 ]
-VARIANTS = {"fp64": dict(precision=0, flexible=0), "mixed_fp32": dict(precision=1, flexible=1)}
+# fp64: the plain FP64 solver (FP64 preconditioner, FP64 operator apply, CG);
+# fp64_df: the same with the double-float apply; mixed_fp32 (headline): FP32
+# preconditioner inside FP64 flexible CG, double-float apply
+VARIANTS = {"fp64": dict(precision=0, flexible=0, arith=0),
+            "fp64_df": dict(precision=0, flexible=0, arith=1),
+            "mixed_fp32": dict(precision=1, flexible=1, arith=1)}
+DTYPES = {"fp64": "f64 (CG, apply, preconditioner)",
+          "fp64_df": "f64 CG and preconditioner, double-float (2 x f32) apply",
+          "mixed_fp32": "f64 CG, double-float (2 x f32) apply, f32 preconditioner"}
 HEADLINE = "mixed_fp32"
 APPLY_TRAFFIC_BYTES = 52_455_168  # ncu capture of the H(grad) general apply (profiles/)
 FP64_PEAK_TFLOPS = 1.20   # measured FP64 FMA throughput of a GB300 (DFMA throughput probe)
+# Algorithmic HBM bytes per lattice DOF per CG iteration of the whole solve:
+# CG vectors ~80 B (FP64, fused updates and dots), operator apply 16 B (x in,
+# y out), condensation ~4 vector passes, patch factors nnz(L)/DOF x value
+# bytes (~19 nnz per DOF for H(grad) SC vertex stars at p = 7) + 2 vector
+# passes, coarse ~0: ~260 B with an FP64 preconditioner, ~185 B with FP32.
+SOLVE_BYTES_PER_DOF_ITER = {"fp64": 260.0, "fp64_df": 260.0, "mixed_fp32": 185.0}
+
+
+def measured_peaks():
+    """HBM copy bandwidth and BF16 GEMM rate measured on the GB300s
+    (MEASURED_PEAKS.json beside this file), else the fallback figures."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
 # The general apply computes in double-float (pairs of FP32, ~48 bits) on the
 # FP32 pipe.  Its ceiling from unit counts and clocks: 152 SMs x 128 FP32
 # lanes x 2.07 GHz = 40.3 T FP32 instructions/s; a double-float FMA (2 FP64-
@@ -234,15 +259,28 @@ def run_ours(args):
     clocks = clk.summary()
     e2e_ms, _ = timed(HEADLINE, True, args.steps, max(1, args.warmup // 2))
 
+    peaks = measured_peaks()
+
     def summarise(vname):
         ms, stats = results[vname]
         it = {s: [i["iterations"] for (sn, i) in stats if sn == s] for s, _, _ in SPACES}
+        dof_its = sum(sizes[sn] * i["iterations"] for (sn, i) in stats)
+        byts = SOLVE_BYTES_PER_DOF_ITER[vname] * dof_its
         return {
             "value": job_value(world, args.steps, dofs, ms),
             "ms_per_step": ms / args.steps,
+            "dtype": DTYPES[vname],
             "iterations": {s: int(statistics.median(v)) for s, v in it.items()},
+            "iterations_natural": {s: int(statistics.median([i["iterations_natural"] for (sn, i) in stats
+                                                            if sn == s])) for s, _, _ in SPACES},
             "solve_ms": {s: statistics.median([i["solve_ms"] for (sn, i) in stats if sn == s])
                          for s, _, _ in SPACES},
+            "apply_ms_per_call": sum(i["apply_ms"] for (_, i) in stats) /
+                                 max(1, sum(i["apply_calls"] for (_, i) in stats)),
+            # whole-solve HBM roofline: algorithmic bytes (per DOF per iteration
+            # x DOF-iterations) over the measured time, against the measured copy rate
+            "hbm_frac_solve": byts / (ms / 1e3) / (peaks["hbm_gbs"] * 1e9),
+            "hbm_bytes_per_dof_iter": SOLVE_BYTES_PER_DOF_ITER[vname],
         }
 
     head = summarise(HEADLINE)
@@ -270,7 +308,9 @@ def run_ours(args):
             "fp64_pipe_peak": FP64_PEAK_TFLOPS,
             "avg_launch_ms": app_ms / max(app_calls, 1),
             "time_share_of_step": app_ms / ms_h,
-            "preconditioner_share_of_step": sum(i["precond_ms"] for (_, i) in stats_h) / ms_h}
+            "preconditioner_share_of_step": sum(i["precond_ms"] for (_, i) in stats_h) / ms_h,
+            "hbm_frac_solve": head["hbm_frac_solve"],
+            "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_source": peaks["source"]}
     line = {
         "metric": METRIC,
         "value": head["value"],
@@ -282,7 +322,7 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64 CG, double-float (2 x f32) operator apply, f32 preconditioner",
+        "dtype": DTYPES[HEADLINE],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "lattice_dofs": dofs,
                    "lattice_dofs_per_space": sizes, "rtol": 1e-8,
@@ -303,7 +343,7 @@ def run_ours(args):
         line["variants"]["learned"] = run_learned(args.steps, max(1, args.warmup // 2),
                                                   args.learned_epochs, args.learned_size, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args, budget_s=30.0)
+        line["cpu_baseline"] = cpu_baseline_full() if args.cpu_baseline_full else cpu_baseline(args, budget_s=30.0)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -349,8 +389,61 @@ def cpu_baseline(args, budget_s=30.0):
         if t_tot > budget_s / 3 or steps >= 3:
             break
     return {"value": steps * dofs / t_tot, "unit": "DOFs/s", "cores": cores, "kind": "oracle",
+            "same_config": False,
             "sample": f"oracle PCG solves (setup excluded) of the same H(grad)+H(curl) problems "
                       f"on a 3x3x3 mesh, p={DEGREE} ({dofs} lattice DOFs), {steps} step(s)"}
+
+
+def oracle_full_worker():
+    """The oracle's solves of the whole workload (8x8x8 mesh, p = 7, both
+    spaces): setup timed apart from the solve; one JSON line."""
+    from oracle.auxiliary import assemble_aux
+    from oracle.discretization import Problem
+    from oracle.krylov import pcg
+    from oracle.relaxation import SCPAFW, SCPH
+    from paper_2211_14284_gb300 import inputs
+    n = N_CELLS
+    X = inputs.vertices(n, perturb=PERTURB, seed=2)
+    al = inputs.constant_coefficient(n)
+    be = inputs.constant_coefficient(n)
+    out = {"dofs": 0, "setup_s": 0.0, "solve_s": 0.0, "iterations": {}}
+    for sname, k, _ in SPACES:
+        t0 = time.time()
+        pr = Problem(k, n, DEGREE, X, al, be)
+        A = pr.A_free()
+        P = assemble_aux(pr)[pr.free][:, pr.free]
+        M = SCPAFW(pr, P, factor="icc") if k == 0 else SCPH(pr, P)
+        b = inputs.normal_rhs(pr.lat.size, 100 + k)[pr.free]
+        t1 = time.time()
+        _, info = pcg(A, b, M.apply, rtol=1e-8, flexible=True)
+        t2 = time.time()
+        out["dofs"] += pr.lat.size
+        out["setup_s"] += t1 - t0
+        out["solve_s"] += t2 - t1
+        out["iterations"][sname] = info["iterations"]
+    print(json.dumps(out))
+
+
+def cpu_baseline_full():
+    """The oracle on the full workload, single-threaded and with BLAS/OpenMP
+    threads on every core of this host (each in its own process)."""
+    cores = len(os.sched_getaffinity(0))
+    res = {}
+    for label, th in (("1_thread", 1), ("all_cores", cores)):
+        env = dict(os.environ)
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[v] = str(th)
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-full-worker"],
+                           capture_output=True, text=True, env=env)
+        if r.returncode != 0:
+            raise RuntimeError(r.stderr[-2000:])
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        d["value"] = d["dofs"] / d["solve_s"]
+        d["threads"] = th
+        res[label] = d
+    return {"value": res["all_cores"]["value"], "unit": "DOFs/s", "cores": cores, "kind": "oracle",
+            "same_config": True, "runs": res,
+            "sample": f"the whole workload (8x8x8, p={DEGREE}, H(grad)+H(curl)), setup excluded"}
 
 
 def run_reference(args):
@@ -533,6 +626,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-baseline-full", action="store_true",
+                    help="time the oracle on the whole workload (minutes of host setup) instead of a sample")
+    ap.add_argument("--oracle-full-worker", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--batch-count", type=int, default=8,
                     help="problems of the uneven H(curl) batch to time (64 = all; 0 = skip)")
     ap.add_argument("--learned-size", type=int, default=32,
@@ -540,6 +636,9 @@ def main():
     ap.add_argument("--learned-epochs", type=int, default=10,
                     help="training epochs of the learned coarse corrector (0 = skip that variant)")
     args = ap.parse_args()
+    if args.oracle_full_worker:
+        oracle_full_worker()
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -70,6 +70,20 @@ typedef enum { RM_CHOL = 0, RM_ICC = 1 } rm_factor;
  * geometric multigrid cycle (Galerkin levels, damped Jacobi), as the paper's
  * p-coarse GMG; for coarse spaces too large for the dense inverse. */
 typedef enum { RM_COARSE_NONE = 0, RM_COARSE_P1 = 1, RM_COARSE_GMG = 2 } rm_coarse;
+/* Smoother of the RM_COARSE_GMG cycle for H(curl) and H(div) (H(grad) always
+ * uses damped point Jacobi).  RM_SMOOTH_STAR: additive vertex stars (exact
+ * star solves, weight 1/8).  RM_SMOOTH_HIPTMAIR: the paper's Hiptmair-Jacobi
+ * relaxation on the p-coarse space (Sec. 5.1, solver diagram): a damped
+ * Jacobi sweep on A, then one on the potential operator G^T A G through the
+ * lowest-order discrete gradient (H(curl)) or curl (H(div)) G, in reverse
+ * order after the coarse correction; weights 1 / ||D^-1 M||_inf. */
+typedef enum { RM_SMOOTH_STAR = 0, RM_SMOOTH_HIPTMAIR = 1 } rm_smoother;
+/* How the fine relaxation S and the coarse correction C combine.
+ * RM_ADDITIVE: B = S + C (Eqs. asm-afw, asm-hiptmair).  RM_HYBRID: the
+ * hybrid multigrid/Schwarz V(1,1) cycle of the paper's experiments (Sec. 5):
+ * z = w S r; z += C (r - A z); z += w S (r - A z), w = hybrid_omega; two
+ * operator applies per call. */
+typedef enum { RM_ADDITIVE = 0, RM_HYBRID = 1 } rm_composition;
 /* Stopping test of rm_solve (Sec. 5.1).  RM_NORM_L2: the recursive residual,
  * ||r_k||_2 <= rtol ||b||_2.  RM_NORM_NATURAL: the paper's test, a reduction of
  * the natural norm of the preconditioned residual by 1/rtol,
@@ -118,6 +132,10 @@ typedef struct {
   int norm;                /* rm_norm of the stopping test (default RM_NORM_L2) */
   int arith;               /* rm_arith of the operator apply (default RM_ARITH_FP64) */
   int boundary;            /* rm_boundary (default RM_BC_DIRICHLET) */
+  int coarse_smoother;     /* rm_smoother of RM_COARSE_GMG (default RM_SMOOTH_STAR) */
+  int composition;         /* rm_composition (default RM_ADDITIVE) */
+  double hybrid_omega;     /* RM_HYBRID relaxation weight, 0 < w <= 1 (default 1/8: at
+                              most eight vertex stars overlap a DOF) */
 } rm_options;
 
 typedef struct {
@@ -148,7 +166,7 @@ typedef struct rm_handle rm_handle;
 
 /* Defaults: FP64, PAFW, no static condensation, exact Cholesky, P1 coarse,
  * CG, rtol 1e-8, max_it 500, check_every 1, RM_NORM_L2, RM_ARITH_FP64,
- * RM_BC_DIRICHLET. */
+ * RM_BC_DIRICHLET, RM_SMOOTH_STAR, RM_ADDITIVE, hybrid_omega 1/8. */
 rm_options rm_default_options(void);
 
 /* Builds the discretisation and the preconditioner (host FP64 setup: 1D

@@ -237,13 +237,19 @@ class Coarse:
     replaced by one symmetric V(2,2) cycle of geometric multigrid (the
     paper's p-coarse multigrid, Sec. 5.1): Galerkin levels P^T A P with the
     lowest-order refinement while every n_d is even and >= 4 and the level
-    has more than 512 DOFs; damped point Jacobi with weight
-    1 / ||D^-1 A||_inf; a dense solve on the coarsest level.  Parity unpinned
-    against the paper (its smoother is Hiptmair-Jacobi; point Jacobi here)."""
+    has more than 512 DOFs; a dense solve on the coarsest level (the h-coarse
+    Cholesky of the solver diagram).  Smoother: damped point Jacobi with
+    weight 1 / ||D^-1 A||_inf for k = 0; for k = 1, 2 smoother = "default":
+    additive vertex stars (weight 1/8), "hiptmair": the paper's
+    Hiptmair-Jacobi relaxation (damped Jacobi on A, then damped Jacobi on
+    the potential operator G^T A G through the discrete gradient or curl G),
+    "jacobi": damped Jacobi on A alone (no potential correction; for
+    comparison)."""
 
-    def __init__(self, problem: Problem, mode: str = "exact"):
+    def __init__(self, problem: Problem, mode: str = "exact", smoother: str = "default"):
         X = problem.mesh.X
         self.mode = mode
+        self.smoother = smoother if problem.k >= 1 else "default"
         self.cp = Problem(problem.k, problem.n, 1, X, problem.alpha, problem.beta, problem.bc)
         P0 = prolongation(problem.lat, self.cp.lat)
         self.R0T = P0[problem.free][:, self.cp.free].tocsr()
@@ -262,7 +268,9 @@ class Coarse:
             D = A.diagonal()
             omega = 1.0 / np.max(np.asarray(abs(A).sum(1)).ravel() / D)
             star = None
-            if problem.k >= 1:
+            if problem.k >= 1 and self.smoother == "hiptmair":
+                star = self._hiptmair_level(problem.k, A, lat, free, tuple(n))
+            elif problem.k >= 1 and self.smoother != "jacobi":
                 pos = free_position(free, lat.size)
                 star = PatchSolver(A, [pos[s] for s in patch_lists(lat, (), free)], "chol")
             self.levels.append((A, P, omega / D, star))
@@ -270,10 +278,45 @@ class Coarse:
             lat, free, n = lat_h, free_h, nh
         self.A_last = A.toarray()
 
+    @staticmethod
+    def _hiptmair_level(k, A, lat, free, n):
+        """Hiptmair-Jacobi data of one level (the paper's p-coarse relaxation,
+        Sec. 5.1 and its solver diagram): the discrete gradient (k = 1) or curl
+        (k = 2) G from the level's V^{k-1}_{h,1} into its V^k_{h,1}, the
+        potential operator B = G^T A G and the damped Jacobi weights of A and
+        of B (omega = 1 / ||D^-1 M||_inf each)."""
+        lat0 = Lattice(k - 1, n, 1, lat.bc)
+        free0 = lat0.free()
+        G = discrete_derivative(k - 1, lat0, lat)[free][:, free0].tocsr()
+        B = (G.T @ A @ G).tocsr()
+        Db = B.diagonal()
+        wb = 1.0 / np.max(np.asarray(abs(B).sum(1)).ravel() / Db) / Db
+        return ("hiptmair", G, wb)
+
+    def _hiptmair_sweep(self, A, w, G, wb, b, x, space_first):
+        """One multiplicative Hiptmair-Jacobi sweep: damped Jacobi on A, then
+        damped Jacobi on the potential, x += G W_B G^T (b - A x) (reversed
+        for the post-smoother, so that the cycle stays symmetric)."""
+        def space(x):
+            return x + w * (b - A @ x)
+
+        def potential(x):
+            return x + G @ (wb * (G.T @ (b - A @ x)))
+        return potential(space(x)) if space_first else space(potential(x))
+
     def _vcycle(self, l, b):
         if l == len(self.levels):
             return np.linalg.solve(self.A_last, b)
         A, P, w, star = self.levels[l]
+        if isinstance(star, tuple):
+            _, G, wb = star
+            x = np.zeros_like(b)
+            for _ in range(2):
+                x = self._hiptmair_sweep(A, w, G, wb, b, x, True)
+            x = x + P @ self._vcycle(l + 1, P.T @ (b - A @ x))
+            for _ in range(2):
+                x = self._hiptmair_sweep(A, w, G, wb, b, x, False)
+            return x
         if star is not None:
             # H(curl)/H(div): additive vertex-star smoother (Arnold-Falk-Winther),
             # weight 1/8 (at most 8 stars overlap a DOF)

@@ -98,6 +98,14 @@ struct rm_handle {
   double *mgAinv = nullptr;
   std::vector<DevPatch> mgStar;  // k = 1, 2: vertex-star smoother per level
   double mgOmega = 0.125;
+  // k = 1, 2 Hiptmair-Jacobi smoother: per level G, G^T, the potential's
+  // Jacobi weights and a potential-space vector
+  bool mgHip = false;
+  std::vector<DevCsr> mgG, mgGT;
+  std::vector<double *> mgWB, mgU;
+  std::vector<int> mgNB;
+  // RM_HYBRID: residual and second relaxation vectors
+  double *hy_t = nullptr, *hy_w = nullptr;
   std::vector<DevPatch> fam;   // families acting on the main space
   std::vector<DevPatch> pfam;  // potential-space families (Hiptmair)
   long long size0 = 0;         // potential (H(grad)) lattice size
@@ -366,6 +374,34 @@ void vcycle(rm_handle *h, int l) {
   const DevCsr &A = h->mgA[l];
   const int nl = h->mgN[l];
   double *b = h->mgB[l], *x = h->mgX[l], *t = h->mgT[l], *w = h->mgW[l], *r = h->mgR[l];
+  if (h->mgHip) {
+    // Hiptmair-Jacobi (Sec. 5.1): damped Jacobi on A, then on the potential
+    // operator through G: x += G W_B G^T (b - A x); the post-smoother runs
+    // the two in reverse order, so the cycle stays symmetric
+    const DevCsr &G = h->mgG[l], &GT = h->mgGT[l];
+    double *u = h->mgU[l];
+    const double *wb = h->mgWB[l];
+    const int nb = h->mgNB[l];
+    auto pot = [&](double *xx) {
+      CK(launch_spmv(A, xx, r, b, 2, -1.0, s));       // r = b - A x
+      CK(launch_spmv(GT, r, u, nullptr, 0, 1.0, s));  // u = G^T r
+      CK(launch_diag_scale(nb, wb, u, u, s));         // u = W_B u
+      CK(launch_spmv(G, u, xx, nullptr, 1, 1.0, s));  // x += G u
+    };
+    CK(launch_diag_scale(nl, w, b, t, s));  // space sweep from 0
+    pot(t);
+    CK(launch_jacobi(A, b, t, w, x, s));    // x = t + W (b - A t)
+    pot(x);
+    CK(launch_spmv(A, x, r, b, 2, -1.0, s));
+    CK(launch_spmv(h->mgPT[l], r, h->mgB[l + 1], nullptr, 0, 1.0, s));
+    vcycle(h, l + 1);
+    CK(launch_spmv(h->mgP[l], h->mgX[l + 1], x, nullptr, 1, 1.0, s));
+    pot(x);
+    CK(launch_jacobi(A, b, x, w, t, s));
+    pot(t);
+    CK(launch_jacobi(A, b, t, w, x, s));
+    return;
+  }
   if (!h->mgStar.empty()) {
     // additive vertex-star smoother: x += omega sum_v R_v^T A_v^-1 R_v (b - A x)
     const DevPatch &F = h->mgStar[l];
@@ -483,7 +519,49 @@ void learned_coarse(rm_handle *h) {
 // after the condensation and a join before the interior expansion; the
 // coarse solve runs beside them and its prolongation is added last (it
 // enters the interior rows too, which the expansion overwrites).
+void apply(rm_handle *h, const double *x, double *y);
+
+// z += C r, the coarse correction R_0^T A_0^-1 R_0 r (or its cycle / learned
+// form), on the handle's stream (the hybrid composition)
+void coarse_add(rm_handle *h, const double *r, double *z) {
+  if (h->nc == 0 || h->corr_mode == RM_CORRECTOR_OFF) return;
+  cudaStream_t s = h->stream;
+  CK(launch_spmv(h->R0, r, h->cc, nullptr, 0, 1.0, s));
+  if (h->rec && h->rec_n < h->rec_cap) {
+    CK(cudaMemcpyAsync(h->rec + (size_t)h->rec_n * h->nc, h->cc, h->nc * sizeof(double),
+                       cudaMemcpyDeviceToDevice, s));
+    h->rec_n++;
+  }
+  if (h->corr_mode == RM_CORRECTOR_LEARNED && h->net && h->lc_fallback < 0) learned_coarse(h);
+  else plain_coarse(h);
+  CK(launch_spmv(h->R0T, h->ce, z, nullptr, 1, 1.0, s));
+}
+
+void relax(rm_handle *h, const double *r, double *z, bool with_coarse);
+
+// z = B r.  RM_ADDITIVE: B = S + C; RM_HYBRID: the V(1,1) cycle
+// z = w S r, z += C (r - A z), z += w S (r - A z) (Sec. 5).
 void precondition(rm_handle *h, const double *r, double *z) {
+  if (h->opt.composition != RM_HYBRID) {
+    relax(h, r, z, true);
+    return;
+  }
+  cudaStream_t s = h->stream;
+  const int n = (int)h->size;
+  const double om = h->opt.hybrid_omega;
+  relax(h, r, z, false);
+  CK(launch_axpy(n, om, z, z, 0, s));              // z = w S r
+  apply(h, z, h->hy_t);
+  CK(launch_sub(n, h->mask, r, h->hy_t, h->hy_t, s));  // t = r - A z
+  coarse_add(h, h->hy_t, z);
+  apply(h, z, h->hy_t);
+  CK(launch_sub(n, h->mask, r, h->hy_t, h->hy_t, s));
+  relax(h, h->hy_t, h->hy_w, false);
+  CK(launch_axpy(n, om, h->hy_w, z, 1, s));        // z += w S t
+}
+
+// z = S r (+ C r with with_coarse): the additive relaxation
+void relax(rm_handle *h, const double *r, double *z, bool with_coarse) {
   cudaStream_t s = h->stream;
   CK(cudaMemsetAsync(z, 0, h->size * sizeof(double), s));
   const double *rr = r;
@@ -511,8 +589,8 @@ void precondition(rm_handle *h, const double *r, double *z) {
     for (auto &F : h->pfam) CK(launch_patches(F, h->u0, h->v0, b));
     CK(launch_spmv(h->Dt, h->v0, z, nullptr, 3, 1.0, b));          // z_G += D~ v0
   }
-  const bool record = h->rec && h->rec_n < h->rec_cap;
-  if (h->nc > 0 && (h->corr_mode != RM_CORRECTOR_OFF || record)) {
+  const bool record = with_coarse && h->rec && h->rec_n < h->rec_cap;
+  if (with_coarse && h->nc > 0 && (h->corr_mode != RM_CORRECTOR_OFF || record)) {
     cudaStream_t b = branch();
     std::swap(h->stream, b);  // the coarse helpers launch on h->stream
     try {
@@ -539,7 +617,7 @@ void precondition(rm_handle *h, const double *r, double *z) {
     }
   if (h->sc) CK(launch_spmv(h->Et, z, z, h->w, 2, -1.0, s));       // z_I = w_I - E^T z_G
   // the coarse term enters every row, after the interior expansion
-  if (h->nc > 0 && h->corr_mode != RM_CORRECTOR_OFF)
+  if (with_coarse && h->nc > 0 && h->corr_mode != RM_CORRECTOR_OFF)
     CK(launch_spmv(h->R0T, h->ce, z, nullptr, 1, 1.0, s));       // z += R_0^T ce
 }
 
@@ -568,6 +646,9 @@ rm_options rm_default_options(void) {
   o.norm = RM_NORM_L2;
   o.arith = RM_ARITH_FP64;
   o.boundary = RM_BC_DIRICHLET;
+  o.coarse_smoother = RM_SMOOTH_STAR;
+  o.composition = RM_ADDITIVE;
+  o.hybrid_omega = 0.125;
   return o;
 }
 
@@ -596,6 +677,11 @@ int rm_setup(rm_handle **out, int space, const rm_mesh *mesh, int p, const doubl
       throw std::invalid_argument("RM_PH needs RM_HCURL or RM_HDIV and static_condensation = 1");
     if (o.rtol <= 0 || o.max_it < 1 || o.check_every < 1) throw std::invalid_argument("rtol/max_it/check_every");
     if (o.norm != RM_NORM_L2 && o.norm != RM_NORM_NATURAL) throw std::invalid_argument("norm");
+    if (o.coarse_smoother != RM_SMOOTH_STAR && o.coarse_smoother != RM_SMOOTH_HIPTMAIR)
+      throw std::invalid_argument("coarse_smoother");
+    if (o.composition != RM_ADDITIVE && o.composition != RM_HYBRID) throw std::invalid_argument("composition");
+    if (o.composition == RM_HYBRID && !(o.hybrid_omega > 0.0 && o.hybrid_omega <= 1.0))
+      throw std::invalid_argument("hybrid_omega must be in (0, 1]");
     if (o.arith != RM_ARITH_FP64 && o.arith != RM_ARITH_DF64) throw std::invalid_argument("arith");
     if (o.boundary != RM_BC_DIRICHLET && o.boundary != RM_BC_NONE) throw std::invalid_argument("boundary");
     h->ad.arith = o.arith == RM_ARITH_DF64 ? 1 : 0;
@@ -706,7 +792,9 @@ int rm_setup(rm_handle **out, int space, const rm_mesh *mesh, int p, const doubl
       if (space == RM_HGRAD) corrector_data(h.get(), cd, al);
     } else if (o.coarse == RM_COARSE_GMG) {
       CoarseGMG mg;
-      CoarseData cd = build_coarse_gmg(h->L, geo, al.data(), be.data(), mg);
+      CoarseData cd = build_coarse_gmg(h->L, geo, al.data(), be.data(), mg,
+                                       o.coarse_smoother == RM_SMOOTH_HIPTMAIR);
+      h->mgHip = mg.hiptmair;
       h->nc = cd.nc;
       std::vector<int> crow(cd.nc);
       for (int i = 0; i < cd.nc; ++i) crow[i] = i;
@@ -729,6 +817,17 @@ int rm_setup(rm_handle **out, int space, const rm_mesh *mesh, int p, const doubl
         h->mgP.push_back(upload_csr(h.get(), mg.P[l], nullptr, nullptr, &prow, true));
         h->mgPT.push_back(upload_csr(h.get(), mg.PT[l], nullptr, nullptr, &trow, true));
         h->mgW.push_back(h->upload(mg.dinv[l]));
+        if (mg.hiptmair) {
+          const int nb = mg.G[l].ncols;
+          std::vector<int> grow(nl), trow(nb);
+          for (int i = 0; i < nl; ++i) grow[i] = i;
+          for (int i = 0; i < nb; ++i) trow[i] = i;
+          h->mgG.push_back(upload_csr(h.get(), mg.G[l], nullptr, nullptr, &grow, true));
+          h->mgGT.push_back(upload_csr(h.get(), mg.GT[l], nullptr, nullptr, &trow, true));
+          h->mgWB.push_back(h->upload(mg.dinvB[l]));
+          h->mgU.push_back(h->dalloc<double>(nb));
+          h->mgNB.push_back(nb);
+        }
         if (!mg.star.empty()) {
           const int saved = h->vt;
           h->vt = 0;  // the coarse cycle stays in FP64
@@ -743,6 +842,10 @@ int rm_setup(rm_handle **out, int space, const rm_mesh *mesh, int p, const doubl
       h->cc = h->mgB[0];
       h->ce = h->mgX[0];
       if (space == RM_HGRAD) corrector_data(h.get(), cd, al);
+    }
+    if (o.composition == RM_HYBRID) {
+      h->hy_t = h->dalloc<double>(h->size);
+      h->hy_w = h->dalloc<double>(h->size);
     }
     h->r = h->dalloc<double>(h->size);
     h->z = h->dalloc<double>(h->size);

@@ -1331,8 +1331,39 @@ static Csr spgemm(const Csr &A, const Csr &B) {
   return csr_from_triplets(A.nrows, B.ncols, t);
 }
 
+// 1 / diag(M) / ||diag(M)^-1 M||_inf: damped Jacobi weights
+static std::vector<double> jacobi_weights(const Csr &M, const char *what) {
+  std::vector<double> dinv(M.nrows);
+  double norm = 0.0;
+  for (int i = 0; i < M.nrows; ++i) {
+    double diag = 0.0, rs = 0.0;
+    for (int64_t e = M.ptr[i]; e < M.ptr[i + 1]; ++e) {
+      rs += std::fabs(M.val[e]);
+      if (M.col[e] == i) diag = M.val[e];
+    }
+    if (!(diag > 0)) throw std::runtime_error(std::string(what) + ": non-positive diagonal");
+    dinv[i] = 1.0 / diag;
+    norm = std::max(norm, rs / diag);
+  }
+  for (double &v : dinv) v /= norm;
+  return dinv;
+}
+
+// M with rows and columns renumbered by rmap / cmap (lattice -> compact, -1
+// dropped), nrows x ncols
+static Csr compact_csr(const Csr &M, const std::vector<int> &rmap, const std::vector<int> &cmap, int nrows,
+                       int ncols) {
+  std::vector<Trip> t;
+  for (int i = 0; i < M.nrows; ++i) {
+    if (rmap[i] < 0) continue;
+    for (int64_t e = M.ptr[i]; e < M.ptr[i + 1]; ++e)
+      if (cmap[M.col[e]] >= 0) t.push_back({rmap[i], cmap[M.col[e]], M.val[e]});
+  }
+  return csr_from_triplets(nrows, ncols, t);
+}
+
 CoarseData build_coarse_gmg(const Layout &Lf, const Geometry &geo, const double *alpha,
-                            const double *beta, CoarseGMG &mg) {
+                            const double *beta, CoarseGMG &mg, bool hiptmair) {
   CoarseData C;
   const int k = Lf.k;
   Layout Lc(k, Lf.n, 1, Lf.natural);
@@ -1344,6 +1375,7 @@ CoarseData build_coarse_gmg(const Layout &Lf, const Geometry &geo, const double 
   C.A0 = A;
   C.free2lat = fc.free2lat;
   mg = CoarseGMG();
+  mg.hiptmair = hiptmair && k >= 1;
   int n[3] = {Lf.n[0], Lf.n[1], Lf.n[2]};
   Layout L = Lc;
   FreeMap fm = fc;
@@ -1385,24 +1417,23 @@ CoarseData build_coarse_gmg(const Layout &Lf, const Geometry &geo, const double 
     Csr PT = transpose(P);
     Csr Ah = spgemm(PT, spgemm(A, P));
     // smoother weights
-    std::vector<double> dinv(A.nrows);
-    double norm = 0.0;
-    for (int i = 0; i < A.nrows; ++i) {
-      double diag = 0.0, rs = 0.0;
-      for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
-        rs += std::fabs(A.val[e]);
-        if (A.col[e] == i) diag = A.val[e];
-      }
-      if (!(diag > 0)) throw std::runtime_error("coarse multigrid: non-positive diagonal");
-      dinv[i] = 1.0 / diag;
-      norm = std::max(norm, rs / diag);
-    }
-    for (double &v : dinv) v /= norm;
     mg.A.push_back(A);
     mg.P.push_back(P);
     mg.PT.push_back(PT);
-    mg.dinv.push_back(dinv);
-    if (k >= 1) {
+    mg.dinv.push_back(jacobi_weights(A, "coarse multigrid"));
+    if (mg.hiptmair) {
+      // Hiptmair-Jacobi: the level's lowest-order d^{k-1} from the potential
+      // space V^{k-1}_{h,1} and the Jacobi weights of B = G^T A G
+      Layout L0(k - 1, n, 1, Lf.natural);
+      FreeMap f0(L0);
+      Csr D = discrete_derivative(L0, L, fm.free2lat, f0.free2lat);
+      Csr G = compact_csr(D, fm.lat2free, f0.lat2free, (int)fm.free2lat.size(), (int)f0.free2lat.size());
+      Csr GT = transpose(G);
+      Csr B = spgemm(GT, spgemm(A, G));
+      mg.dinvB.push_back(jacobi_weights(B, "coarse multigrid potential"));
+      mg.G.push_back(std::move(G));
+      mg.GT.push_back(std::move(GT));
+    } else if (k >= 1) {
       // vertex stars of the level (exact, block inverses); slot maps renumbered
       // to the level's compact free numbering
       PatchFamily F = build_patches(L, fm, A, 0, false, 0);

@@ -151,12 +151,19 @@ struct CoarseGMG {
   // compact numbering
   std::vector<PatchFamily> star;
   double star_omega = 0.125;
+  // k = 1, 2 with the Hiptmair-Jacobi smoother: per level the lowest-order
+  // discrete gradient / curl G (level free x potential free), G^T, and the
+  // damped Jacobi weights of the potential operator B = G^T A G
+  bool hiptmair = false;
+  std::vector<Csr> G, GT;
+  std::vector<std::vector<double>> dinvB;
   std::vector<double> Ainv;     // coarsest dense inverse
   int ncoarsest = 0;
 };
-// R_0 and the multigrid hierarchy of the coarse problem.
+// R_0 and the multigrid hierarchy of the coarse problem.  hiptmair (k = 1,
+// 2): Hiptmair-Jacobi smoothing data instead of the vertex stars.
 CoarseData build_coarse_gmg(const Layout &Lf, const Geometry &geo, const double *alpha,
-                            const double *beta, CoarseGMG &mg);
+                            const double *beta, CoarseGMG &mg, bool hiptmair = false);
 
 // Discrete exterior derivative d^k: V^k (La) -> V^{k+1} (Lb) in FDM
 // coefficients (cellwise D-hat, Sec. 2.3), restricted to the given rows

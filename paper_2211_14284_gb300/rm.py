@@ -24,6 +24,8 @@ RM_COARSE_NONE, RM_COARSE_P1, RM_COARSE_GMG = 0, 1, 2
 RM_NORM_L2, RM_NORM_NATURAL = 0, 1
 RM_ARITH_FP64, RM_ARITH_DF64 = 0, 1
 RM_BC_DIRICHLET, RM_BC_NONE = 0, 1
+RM_SMOOTH_STAR, RM_SMOOTH_HIPTMAIR = 0, 1
+RM_ADDITIVE, RM_HYBRID = 0, 1
 STATUS = {0: "RM_OK", 1: "RM_ERR_ARG", 2: "RM_ERR_CUDA", 3: "RM_ERR_OOM",
           4: "RM_ERR_BREAKDOWN", 5: "RM_ERR_NOT_CONVERGED", 6: "RM_ERR_NAN"}
 
@@ -50,7 +52,9 @@ class RmOptions(ctypes.Structure):
                 ("coarse", ctypes.c_int), ("flexible", ctypes.c_int),
                 ("rtol", ctypes.c_double), ("max_it", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("profile", ctypes.c_int),
-                ("norm", ctypes.c_int), ("arith", ctypes.c_int), ("boundary", ctypes.c_int)]
+                ("norm", ctypes.c_int), ("arith", ctypes.c_int), ("boundary", ctypes.c_int),
+                ("coarse_smoother", ctypes.c_int), ("composition", ctypes.c_int),
+                ("hybrid_omega", ctypes.c_double)]
 
 
 class RmInfo(ctypes.Structure):

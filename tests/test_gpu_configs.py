@@ -153,3 +153,98 @@ def test_hgrad_32_p6_full_size():
     al = inputs.lognormal_grf_coefficient(32, 1.0, 0.1, seed=5)
     info = _full_size(0, 32, 6, al, dict(static_condensation=1, factor=1, coarse=2), 5)
     assert info["iterations"] < 200
+
+
+def test_coarse_multigrid_hiptmair_parity():
+    """RM_COARSE_GMG with RM_SMOOTH_HIPTMAIR: the paper's p-coarse multigrid
+    (Hiptmair-Jacobi relaxation, h-coarse direct solve) inside SC-PH for
+    H(curl) equals the oracle's same cycle."""
+    from oracle.relaxation import SCPH, Coarse
+    from paper_2211_14284_gb300.rm import RM_SMOOTH_HIPTMAIR, Solver
+    n, p = 8, 2
+    X = inputs.vertices(n)
+    al = inputs.loguniform_coefficient(n, 0.1, 10, seed=4)
+    be = inputs.constant_coefficient(n, 1e-2)
+    s = Solver(1, n, p, vertices=X, alpha=al, beta=be, static_condensation=1, decomposition=1,
+               factor=0, coarse=2, coarse_smoother=RM_SMOOTH_HIPTMAIR)
+    pr = Problem(1, n, p, X, al, be)
+    P = assemble_aux(pr)[pr.free][:, pr.free]
+    M = SCPH(pr, P, vertex_factor="chol", coarse=False)
+    M.coarse = Coarse(pr, "gmg", smoother="hiptmair")
+    assert len(M.coarse.levels) == 1 and isinstance(M.coarse.levels[0][3], tuple)
+    r = inputs.normal_rhs(pr.lat.size, 10)
+    r[np.setdiff1d(np.arange(pr.lat.size), pr.free)] = 0.0
+    z = torch.zeros(pr.lat.size, dtype=torch.float64, device="cuda")
+    s.precondition(_dev(r), z)
+    want = np.zeros(pr.lat.size)
+    want[pr.free] = M.apply(r[pr.free])
+    conds = [np.linalg.cond(L) ** 2 for ps in M.edge + M.potential for L in ps.L]
+    conds.append(np.linalg.cond(M.coarse.levels[0][0].toarray()))
+    conds.append(np.linalg.cond(M.coarse.A_last))
+    assert np.abs(_host(z) - want).max() <= max(1e-11, 1e-11 * max(conds)) * np.abs(want).max()
+
+
+@pytest.mark.parametrize("k,mode", [(0, "sc-icc"), (1, "scph"), (2, "scph")])
+def test_hybrid_composition_parity(k, mode):
+    """RM_HYBRID, the V(1,1) hybrid multigrid/Schwarz cycle of the paper's
+    experiments (Sec. 5): the GPU preconditioner equals the oracle's Hybrid
+    with the same relaxation and exact coarse solve, and the solve takes the
+    oracle PCG's iteration count (+-1)."""
+    from oracle.krylov import pcg
+    from oracle.relaxation import SCPH, Coarse, Hybrid
+    from paper_2211_14284_gb300.rm import RM_HYBRID, Solver
+    n, p = 3, 3
+    X = inputs.vertices(n, perturb=0.1, seed=71)
+    al = inputs.loguniform_coefficient(n, 0.1, 10, seed=72)
+    be = inputs.loguniform_coefficient(n, 0.1, 10, seed=73)
+    opts = dict(static_condensation=1, factor=1, decomposition=0 if k == 0 else 1,
+                composition=RM_HYBRID, hybrid_omega=0.125, rtol=1e-8, max_it=400)
+    s = Solver(k, n, p, vertices=X, alpha=al, beta=be, **opts)
+    pr = Problem(k, n, p, X, al, be)
+    A = pr.A_free()
+    P = assemble_aux(pr)[pr.free][:, pr.free]
+    relax = SCPAFW(pr, P, factor="icc", coarse=False) if k == 0 else SCPH(pr, P, coarse=False)
+    H = Hybrid(A, relax, Coarse(pr), omega=0.125)
+    r = inputs.normal_rhs(pr.lat.size, 74)
+    r[np.setdiff1d(np.arange(pr.lat.size), pr.free)] = 0.0
+    z = torch.zeros(pr.lat.size, dtype=torch.float64, device="cuda")
+    s.precondition(_dev(r), z)
+    want = np.zeros(pr.lat.size)
+    want[pr.free] = H.apply(r[pr.free])
+    solvers = [relax.patches] if k == 0 else relax.edge + relax.potential
+    cond = max(np.linalg.cond(L) ** 2 for ps in solvers for L in ps.L)
+    assert np.abs(_host(z) - want).max() <= max(1e-11, 1e-12 * cond) * np.abs(want).max()
+    b = inputs.normal_rhs(pr.lat.size, 75)
+    x = torch.zeros(pr.lat.size, dtype=torch.float64, device="cuda")
+    info = s.solve(_dev(b), x)
+    assert info["status"] == "RM_OK"
+    _, io = pcg(A, b[pr.free], H.apply, rtol=1e-8)
+    assert abs(info["iterations"] - io["iterations"]) <= 1, (info["iterations"], io["iterations"])
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_paper_iterations_p1_on_gpu(k):
+    """The paper's printed counts at p = 1, l = 0 (tests/golden, tab.
+    hgrad-iter, hcurl-iter, hdiv-iter) reproduced by the GPU solver in the
+    paper's setting: hybrid V(1,1), alpha = 1, beta = 1e-8, the Riesz
+    representative right-hand side b = A_{1,1} w (Eq. random_rhs, computed by
+    the oracle), natural-norm stopping at 1e-8, 3 x 3 x 6 cells."""
+    from pathlib import Path
+    from paper_2211_14284_gb300.rm import RM_HYBRID, RM_NORM_NATURAL, Solver
+    want = None
+    for line in open(Path(__file__).parent / "golden" / "riesz_iterations_p1_l0.txt"):
+        f = line.split()
+        if f and not line.startswith("#") and int(f[1]) == k:
+            want = int(f[2])
+    n = (3, 3, 6)
+    X = inputs.vertices(n, perturb=0.15, seed=3)
+    w = inputs.normal_rhs(Problem(k, n, 1, X, 1.0, 1.0).lat.size, 7)
+    pr1 = Problem(k, n, 1, X, 1.0, 1.0)
+    b = np.zeros(pr1.lat.size)
+    b[pr1.free] = pr1.A_free() @ w[pr1.free]
+    s = Solver(k, n, 1, vertices=X, alpha=np.ones(54), beta=np.full(54, 1e-8),
+               composition=RM_HYBRID, norm=RM_NORM_NATURAL, rtol=1e-8, max_it=20)
+    x = torch.zeros(pr1.lat.size, dtype=torch.float64, device="cuda")
+    info = s.solve(_dev(b), x)
+    assert info["status"] == "RM_OK"
+    assert info["iterations_natural"] == want, (info, want)
