@@ -363,8 +363,14 @@ class Condensed:
         self.PGI = P[self.G][:, self.I].tocsr()
         PGG = P[self.G][:, self.G].tocsr()
         # P_II is block diagonal (blocks of at most d x d, Remark after Eq.
-        # schur): invert it block by block on its connected components
-        # (couplings below 1e-13 sqrt(|P_ii P_jj|) are quadrature round-off).
+        # schur): factor it block by block on its connected components
+        # (couplings below 1e-13 sqrt(|P_ii P_jj|) are quadrature round-off),
+        # P_II = L L^T.  Then P_II^{-1} = L^{-T} L^{-1} and
+        # S = P_GG - W^T W with W = L^{-1} P_IG: the quantities of Eq. schur,
+        # formed so that they stay symmetric positive definite in floating
+        # point when P_II is ill conditioned (beta << alpha: its interior
+        # gradients or curls are nearly singular), where an explicit inverse
+        # in P_GI P_II^{-1} P_IG loses both properties.
         PIId = self.PII.tocsr()
         dg = np.sqrt(np.abs(PIId.diagonal()))
         C = PIId.tocoo()
@@ -372,17 +378,21 @@ class Condensed:
         graph = sp.csr_matrix((np.ones(keep.sum()), (C.row[keep], C.col[keep])),
                               shape=PIId.shape)
         ncomp, lab = sp.csgraph.connected_components(graph, directed=False)
-        rows, cols, vals = [], [], []
+        rows, cols, vals, lvals = [], [], [], []
         for c in range(ncomp):
             ix = np.flatnonzero(lab == c)
-            Binv = np.linalg.inv(PIId[ix][:, ix].toarray())
+            L = np.linalg.cholesky(PIId[ix][:, ix].toarray())
+            Li = scipy.linalg.solve_triangular(L, np.eye(len(ix)), lower=True)
             rows.append(np.repeat(ix, len(ix)))
             cols.append(np.tile(ix, len(ix)))
-            vals.append(Binv.ravel())
+            vals.append((Li.T @ Li).ravel())
+            lvals.append(Li.ravel())
         nI = len(self.I)
-        self.PII_inv = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows),
-                                      np.concatenate(cols))), shape=(nI, nI))
-        self.S = (PGG - self.PGI @ (self.PII_inv @ self.PIG)).tocsr()
+        r_, c_ = np.concatenate(rows), np.concatenate(cols)
+        self.PII_inv = sp.csr_matrix((np.concatenate(vals), (r_, c_)), shape=(nI, nI))
+        Linv = sp.csr_matrix((np.concatenate(lvals), (r_, c_)), shape=(nI, nI))
+        W = (Linv @ self.PIG).tocsr()
+        self.S = (PGG - (W.T @ W)).tocsr()
 
     def condense(self, r):
         """(y_I, R_G r) with y_I = P_II^{-1} r_I."""

@@ -553,30 +553,30 @@ static bool is_interior(const Layout &L, long long lat) {
   return true;
 }
 
-static void invert_small(std::vector<double> &A, int n) {
-  // Gauss-Jordan with partial pivoting
-  std::vector<double> I(n * n, 0.0);
-  for (int i = 0; i < n; ++i) I[i * n + i] = 1.0;
-  for (int c = 0; c < n; ++c) {
-    int piv = c;
-    for (int r = c + 1; r < n; ++r)
-      if (std::fabs(A[r * n + c]) > std::fabs(A[piv * n + c])) piv = r;
-    if (A[piv * n + c] == 0.0) throw std::runtime_error("singular interior block");
-    if (piv != c)
-      for (int j = 0; j < n; ++j) {
-        std::swap(A[c * n + j], A[piv * n + j]);
-        std::swap(I[c * n + j], I[piv * n + j]);
-      }
-    double d = A[c * n + c];
-    for (int j = 0; j < n; ++j) { A[c * n + j] /= d; I[c * n + j] /= d; }
-    for (int r = 0; r < n; ++r) {
-      if (r == c) continue;
-      double f = A[r * n + c];
-      if (f == 0.0) continue;
-      for (int j = 0; j < n; ++j) { A[r * n + j] -= f * A[c * n + j]; I[r * n + j] -= f * I[c * n + j]; }
+// The inverse Cholesky factor of a small SPD block (row-major, n x n):
+// A = L L^T, returns L^-1 (lower triangular).  A non-positive pivot is an
+// error (the interior block of the auxiliary operator is SPD).
+static std::vector<double> inverse_cholesky_small(const std::vector<double> &A, int n) {
+  std::vector<double> L(n * n, 0.0), Li(n * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    double d = A[j * n + j];
+    for (int k = 0; k < j; ++k) d -= L[j * n + k] * L[j * n + k];
+    if (!(d > 0.0)) throw std::runtime_error("interior block not positive definite");
+    L[j * n + j] = std::sqrt(d);
+    for (int i = j + 1; i < n; ++i) {
+      double v = A[i * n + j];
+      for (int k = 0; k < j; ++k) v -= L[i * n + k] * L[j * n + k];
+      L[i * n + j] = v / L[j * n + j];
     }
   }
-  A = I;
+  for (int c = 0; c < n; ++c) {  // columns of L^-1 by forward substitution
+    for (int i = c; i < n; ++i) {
+      double v = i == c ? 1.0 : 0.0;
+      for (int k = c; k < i; ++k) v -= L[i * n + k] * Li[k * n + c];
+      Li[i * n + c] = v / L[i * n + i];
+    }
+  }
+  return Li;
 }
 
 // CSR from rows computed independently: row_fn(i, cols, vals) fills row i
@@ -674,7 +674,9 @@ Condensed condense(const Layout &L, const FreeMap &fm, const Csr &P) {
     auto it = std::lower_bound(b, e, j);
     return (it != e && *it == j) ? P.val[it - P.col.begin()] : 0.0;
   };
-  std::vector<std::vector<double>> binv(blist.size());
+  // P_II = L L^T blockwise; P_II^-1 = L^-T L^-1 formed as that product, so it
+  // is symmetric to the last bit and positive definite
+  std::vector<std::vector<double>> binv(blist.size()), linv(blist.size());
   std::vector<Trip> tb;
   for (size_t b = 0; b < blist.size(); ++b) {
     const auto &ix = blist[b];
@@ -682,10 +684,18 @@ Condensed condense(const Layout &L, const FreeMap &fm, const Csr &P) {
     std::vector<double> A(n * n);
     for (int a = 0; a < n; ++a)
       for (int c = 0; c < n; ++c) A[a * n + c] = getP(ix[a], ix[c]);
-    invert_small(A, n);
-    binv[b] = A;
+    linv[b] = inverse_cholesky_small(A, n);
+    const std::vector<double> &Li = linv[b];
+    std::vector<double> Bi(n * n, 0.0);
     for (int a = 0; a < n; ++a)
-      for (int c = 0; c < n; ++c) tb.push_back({ix[a], ix[c], A[a * n + c]});
+      for (int c = 0; c < n; ++c) {
+        double v = 0.0;
+        for (int k = std::max(a, c); k < n; ++k) v += Li[k * n + a] * Li[k * n + c];
+        Bi[a * n + c] = v;
+      }
+    binv[b] = Bi;
+    for (int a = 0; a < n; ++a)
+      for (int c = 0; c < n; ++c) tb.push_back({ix[a], ix[c], Bi[a * n + c]});
   }
   R.Binv = csr_from_triplets(nf, nf, tb);
   // E = P_GI Binv, row by row (each entry summed in the order of P's row)
@@ -731,14 +741,49 @@ Condensed condense(const Layout &L, const FreeMap &fm, const Csr &P) {
     });
   }
   R.Et = transpose(R.E);
-  // S = P_GG - E P_IG, row by row
+  // S = P_GG - W^T W with W = L^-1 P_IG (blockwise): the Schur complement of
+  // Eq. schur in a form that stays symmetric positive definite in floating
+  // point when P_II is ill conditioned (beta << alpha makes the interior
+  // gradients (curls) nearly singular): the product E P_IG through an
+  // explicit inverse loses both properties there.  Per block: its interface
+  // columns (sorted) and W_b = L_b^-1 P_{b,cols}.
+  std::vector<std::vector<int>> wcols(blist.size());
+  std::vector<std::vector<double>> wval(blist.size());
+  {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 64)
+#endif
+    for (long long bb = 0; bb < (long long)blist.size(); ++bb) {
+      const auto &ix = blist[bb];
+      const int n = (int)ix.size();
+      std::vector<int> &cols = wcols[bb];
+      for (int i : ix)
+        for (int64_t e = P.ptr[i]; e < P.ptr[i + 1]; ++e)
+          if (!inI[P.col[e]] && P.val[e] != 0.0) cols.push_back(P.col[e]);
+      std::sort(cols.begin(), cols.end());
+      cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+      const int nc = (int)cols.size();
+      std::vector<double> PB(n * nc, 0.0);
+      for (int a = 0; a < n; ++a)
+        for (int c = 0; c < nc; ++c) PB[a * nc + c] = getP(ix[a], cols[c]);
+      const std::vector<double> &Li = linv[bb];
+      std::vector<double> &W = wval[bb];
+      W.assign(n * nc, 0.0);
+      for (int k = 0; k < n; ++k)
+        for (int c = 0; c < nc; ++c) {
+          double v = 0.0;
+          for (int a = 0; a <= k; ++a) v += Li[k * n + a] * PB[a * nc + c];
+          W[k * nc + c] = v;
+        }
+    }
+  }
   {
     int nth = 1;
 #ifdef _OPENMP
     nth = omp_get_max_threads();
 #endif
     std::vector<std::vector<double>> accs(nth);
-    std::vector<std::vector<char>> marks(nth);
+    std::vector<std::vector<char>> marks(nth), bmarks(nth);
     R.S = csr_from_rows(nf, nf, R.G, [&](int g, std::vector<int> &cols, std::vector<double> &vals) {
       int t = 0;
 #ifdef _OPENMP
@@ -746,9 +791,11 @@ Condensed condense(const Layout &L, const FreeMap &fm, const Csr &P) {
 #endif
       std::vector<double> &acc = accs[t];
       std::vector<char> &m = marks[t];
+      std::vector<char> &bm = bmarks[t];
       if (acc.empty()) {
         acc.assign(nf, 0.0);
         m.assign(nf, 0);
+        bm.assign(blist.size(), 0);
       }
       for (int64_t e = P.ptr[g]; e < P.ptr[g + 1]; ++e) {
         int c = P.col[e];
@@ -756,14 +803,27 @@ Condensed condense(const Layout &L, const FreeMap &fm, const Csr &P) {
         if (!m[c]) { m[c] = 1; cols.push_back(c); acc[c] = 0.0; }
         acc[c] += P.val[e];
       }
-      for (int64_t e = R.E.ptr[g]; e < R.E.ptr[g + 1]; ++e) {
-        int j = R.E.col[e];
-        double ev = R.E.val[e];
-        for (int64_t f = P.ptr[j]; f < P.ptr[j + 1]; ++f) {
-          int c = P.col[f];
-          if (inI[c]) continue;
-          if (!m[c]) { m[c] = 1; cols.push_back(c); acc[c] = 0.0; }
-          acc[c] -= ev * P.val[f];
+      // the blocks coupled to g, in the order of P's row g
+      std::vector<int> bl;
+      for (int64_t e = P.ptr[g]; e < P.ptr[g + 1]; ++e) {
+        int i = P.col[e];
+        if (!inI[i] || P.val[e] == 0.0) continue;
+        const int b = blk_of[i];
+        if (!bm[b]) { bm[b] = 1; bl.push_back(b); }
+      }
+      for (int b : bl) {
+        bm[b] = 0;
+        const std::vector<int> &wc = wcols[b];
+        const std::vector<double> &W = wval[b];
+        const int n = (int)blist[b].size(), nc = (int)wc.size();
+        const int gi = (int)(std::lower_bound(wc.begin(), wc.end(), g) - wc.begin());
+        if (gi == nc || wc[gi] != g) continue;  // P_{b,g} = 0: no contribution
+        for (int c = 0; c < nc; ++c) {
+          double v = 0.0;
+          for (int k = 0; k < n; ++k) v += W[k * nc + gi] * W[k * nc + c];
+          const int cc = wc[c];
+          if (!m[cc]) { m[cc] = 1; cols.push_back(cc); acc[cc] = 0.0; }
+          acc[cc] -= v;
         }
       }
       for (int c : cols) {

@@ -186,10 +186,8 @@ def test_maxwell_two_material_robust():
     its = {}
     for bair in (1e-6, 1e-3, 1.0, 1e3, 1e6):
         be = inputs.annulus_coefficient(n, 1.0, bair)
-        # exact potential factors: at beta_air = 1e-6 ICC(0) of the
-        # vertex-star potentials breaks down (a non-positive pivot)
         s = Solver(1, n, p, beta=be, boundary=RM_BC_NONE, static_condensation=1,
-                   decomposition=1, factor=0, rtol=1e-8, max_it=400)
+                   decomposition=1, factor=1, rtol=1e-8, max_it=400)
         b = _dev(inputs.normal_rhs(s.size, 59))
         x = torch.zeros_like(b)
         info = s.solve(b, x)

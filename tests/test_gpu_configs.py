@@ -126,7 +126,7 @@ def test_hdiv_16_p10_full_size():
                 "ph_fp64": dict(decomposition=1, precision=0),
                 "ph_fp32": dict(decomposition=1, precision=1, flexible=1, arith=1)}
     for name, v in variants.items():
-        s = Solver(2, n, p, vertices=X, alpha=al, beta=be, rtol=1e-8, max_it=400,
+        s = Solver(2, n, p, vertices=X, alpha=al, beta=be, rtol=1e-8, max_it=600,
                    static_condensation=1, factor=1, coarse=2, **v)
         if name == "pafw_fp64":
             x = inputs.normal_rhs(pr.lat.size, 25)
@@ -135,7 +135,8 @@ def test_hdiv_16_p10_full_size():
             yh = _host(y)
             assert np.abs(yh[rows] - pr.apply_rows(x, rows)).max() <= 1e-12 * np.abs(yh).max()
         xs = torch.zeros(pr.lat.size, dtype=torch.float64, device="cuda")
-        info = s.solve(_dev(b), xs)
+        info = s.solve(_dev(b), xs, check=False)
+        print(name, info["status"], info["iterations"], info["rel_res_l2"], flush=True)
         assert info["status"] == "RM_OK" and info["rel_res_l2"] <= 1e-8, (name, info)
         r_rows = b[rows] - pr.apply_rows(_host(xs), rows)
         assert np.abs(r_rows).max() <= 1.5e-8 * bn, name
