@@ -136,6 +136,10 @@ typedef struct {
   int composition;         /* rm_composition (default RM_ADDITIVE) */
   double hybrid_omega;     /* RM_HYBRID relaxation weight, 0 < w <= 1 (default 1/8: at
                               most eight vertex stars overlap a DOF) */
+  int relaxation;          /* 1 (default): build the preconditioner; 0: the operator
+                              alone (rm_apply only; alpha or beta may then be 0, e.g.
+                              a mass matrix alone; rm_precondition and rm_solve
+                              return RM_ERR_ARG) */
 } rm_options;
 
 typedef struct {
@@ -166,7 +170,7 @@ typedef struct rm_handle rm_handle;
 
 /* Defaults: FP64, PAFW, no static condensation, exact Cholesky, P1 coarse,
  * CG, rtol 1e-8, max_it 500, check_every 1, RM_NORM_L2, RM_ARITH_FP64,
- * RM_BC_DIRICHLET, RM_SMOOTH_STAR, RM_ADDITIVE, hybrid_omega 1/8. */
+ * RM_BC_DIRICHLET, RM_SMOOTH_STAR, RM_ADDITIVE, hybrid_omega 1/8, relaxation 1. */
 rm_options rm_default_options(void);
 
 /* Builds the discretisation and the preconditioner (host FP64 setup: 1D
@@ -284,6 +288,42 @@ const char *rm_batch_last_error(const rm_batch *b);
  * device, lattice length, not aliased; z is overwritten. */
 #define RM_NOALLOC_MAX_COARSE 8192
 int rm_precondition_noalloc(rm_handle *h, const double *r, double *z);
+
+/* ---- mixed Hodge Laplacians (Sec. 5.3) ------------------------------------------
+ * Find (sigma, u) in V^{k-1} x V^k (k = 1, 2, 3), Gamma_D empty, with
+ *     -(tau, sigma) + (d tau, u) = 0,   (v, d sigma) + (d v, d u) = F(v),
+ * i.e. K (sigma, u) = (0, F) with K = [[-M_{k-1}, D^T M_k], [M_k D, K_k]]: M the
+ * masses, D the discrete exterior derivative d^{k-1} in FDM coefficients, K_k
+ * the (d v, d u) term (0 for k = 3).  MINRES, preconditioned by
+ * blockdiag(R_{k-1}^-1, R_k^-1) with the Riesz maps (alpha = beta = 1) each
+ * inverted approximately by cheb_its Chebyshev iterations (the paper uses 4)
+ * preconditioned by its statically condensed relaxation and the p = 1 coarse
+ * correction (SC-PAFW on V^0, SC-PH on V^1 and V^2) or, for the L2 block of
+ * k = 3, point-Jacobi on the V^3 mass.  Chebyshev interval: [0.9 theta_min,
+ * 1.1 theta_max] from the Ritz values of 20 preconditioned CG steps on a
+ * seeded right-hand side at setup.  Stops when the natural norm
+ * sqrt(r^T P r) of the preconditioned residual has fallen by 1/rtol, from a
+ * zero initial guess.  Vectors are (sigma, u) concatenated, each in the
+ * VECTOR LAYOUT of its space (every entry a DOF). */
+typedef struct rm_hodge rm_hodge;
+/* opt: the Riesz blocks' options (precision, factor, arith, coarse) and the
+ * solve's rtol and max_it; boundary, static condensation and composition are
+ * fixed as above.  mesh and p as in rm_setup. */
+int rm_hodge_setup(rm_hodge **h, int k, const rm_mesh *mesh, int p, const rm_options *opt, int cheb_its,
+                   void *stream);
+int rm_hodge_ndofs(const rm_hodge *h, long long *n_sigma, long long *n_u);
+/* the Chebyshev intervals [a, b] of the two blocks (host, 2 doubles each or NULL) */
+int rm_hodge_intervals(const rm_hodge *h, double interval0[2], double interval1[2]);
+/* y = K x; x, y device, n_sigma + n_u, not aliased */
+int rm_hodge_apply(rm_hodge *h, const double *x, double *y);
+/* z = the block preconditioner applied to r (device, not aliased) */
+int rm_hodge_precondition(rm_hodge *h, const double *r, double *z);
+/* x = MINRES solution of K x = b (b device, x device out; zero initial
+ * guess); info: iterations, status, rel_res_natural (the final natural-norm
+ * ratio), solve_ms, setup_s; rel_res_l2 = -1. */
+int rm_hodge_solve(rm_hodge *h, const double *b, double *x, rm_info *info);
+void rm_hodge_destroy(rm_hodge *h);
+const char *rm_hodge_last_error(const rm_hodge *h);
 
 /* ---- learned coarse corrector (H(grad) only) ---------------------------------
  * Not in the paper.  A small convolutional network N (a 3D U-Net, BF16

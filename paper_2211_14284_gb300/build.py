@@ -21,7 +21,7 @@ LIB = os.path.join(HERE, "librm.so")
 HOSTLIB = os.path.join(HERE, "librm_host.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 HOST_SOURCES = ["host_basis.cpp", "host_setup.cpp", "host_probe.cpp"]
-DEVICE_SOURCES = ["kernels.cu", "apply_general.cu", "capi.cu", "batch.cu", "learned.cu"]
+DEVICE_SOURCES = ["kernels.cu", "apply_general.cu", "capi.cu", "batch.cu", "learned.cu", "hodge.cu"]
 # apply_general_part.cu, once per (space k, first degree of four): the
 # compile-time instantiations of the general apply, compiled in parallel;
 # apply_cart_part.cu once per space: the Cartesian apply's instantiations

@@ -106,6 +106,7 @@ struct rm_handle {
   std::vector<int> mgNB;
   // RM_HYBRID: residual and second relaxation vectors
   double *hy_t = nullptr, *hy_w = nullptr;
+  bool op_only = false;  // relaxation = 0: the operator alone
   std::vector<DevPatch> fam;   // families acting on the main space
   std::vector<DevPatch> pfam;  // potential-space families (Hiptmair)
   long long size0 = 0;         // potential (H(grad)) lattice size
@@ -649,6 +650,7 @@ rm_options rm_default_options(void) {
   o.coarse_smoother = RM_SMOOTH_STAR;
   o.composition = RM_ADDITIVE;
   o.hybrid_omega = 0.125;
+  o.relaxation = 1;
   return o;
 }
 
@@ -713,8 +715,10 @@ int rm_setup(rm_handle **out, int space, const rm_mesh *mesh, int p, const doubl
     std::vector<double> al(ncell, 1.0), be(ncell, 1.0);
     if (alpha) std::memcpy(al.data(), alpha, ncell * sizeof(double));
     if (beta) std::memcpy(be.data(), beta, ncell * sizeof(double));
+    const bool relax_on = o.relaxation != 0;
     for (int c = 0; c < ncell; ++c)
-      if (!(al[c] > 0) || !(be[c] >= 0)) throw std::invalid_argument("alpha must be > 0 and beta >= 0");
+      if (relax_on ? (!(al[c] > 0) || !(be[c] >= 0)) : (!(al[c] >= 0) || !(be[c] >= 0)))
+        throw std::invalid_argument(relax_on ? "alpha must be > 0 and beta >= 0" : "alpha and beta must be >= 0");
     build_apply(h.get(), geo, al, be);
     FreeMap fm(h->L);
     h->nfree = (long long)fm.free2lat.size();
@@ -722,6 +726,13 @@ int rm_setup(rm_handle **out, int space, const rm_mesh *mesh, int p, const doubl
       std::vector<uint8_t> mask(h->size, 1);
       for (int l : fm.free2lat) mask[l] = 0;
       h->mask = h->upload(mask);
+    }
+    h->op_only = !relax_on;
+    if (h->op_only) {
+      CK(cudaDeviceSynchronize());
+      h->setup_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_setup).count();
+      *out = h.release();
+      return RM_OK;
     }
     // relaxation
     Csr P = assemble_aux(h->L, geo, be.data(), al.data(), fm);
@@ -940,6 +951,7 @@ int rm_apply(rm_handle *h, const double *x, double *y) {
 
 int rm_precondition(rm_handle *h, const double *r, double *z) {
   if (!h || !r || !z) return fail(h, RM_ERR_ARG, "rm_precondition: NULL argument");
+  if (h->op_only) return fail(h, RM_ERR_ARG, "rm_precondition: handle built with relaxation = 0");
   if (r == z) return fail(h, RM_ERR_ARG, "rm_precondition: r and z must not alias");
   try {
     precondition(h, r, z);
@@ -951,6 +963,7 @@ int rm_precondition(rm_handle *h, const double *r, double *z) {
 
 int rm_solve(rm_handle *h, const double *b, double *x, rm_info *info) {
   if (!h || !b || !x) return fail(h, RM_ERR_ARG, "rm_solve: NULL argument");
+  if (h->op_only) return fail(h, RM_ERR_ARG, "rm_solve: handle built with relaxation = 0");
   const long long n = h->size;
   cudaStream_t s = h->stream;
   int status = RM_OK, it = 0;

@@ -1554,4 +1554,79 @@ Csr discrete_gradient(const Layout &L0, const Layout &L1, const std::vector<int>
   return discrete_derivative(L0, L1, rows1, cols0);
 }
 
+Csr mass_v3(const Layout &L3, const Geometry &geo, const double *coef) {
+  if (L3.k != 3) throw std::runtime_error("mass_v3: a V^3 layout");
+  const int p = L3.p, q = quad_points(p);
+  Basis1D B(p);
+  std::vector<double> xq, wq;
+  gll_rule(q, xq, wq);
+  std::vector<double> R(q * p);  // R[o * p + i] = r_i(x_o)
+  B.tab_r(xq.data(), q, R.data());
+  const int n0 = L3.n[0], n1 = L3.n[1], n2 = L3.n[2];
+  const int ncell = n0 * n1 * n2, nl = p * p * p;
+  std::vector<std::vector<Trip>> parts(ncell);
+  int inverted = -1;  // an inverted cell, reported after the parallel region
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 8)
+#endif
+  for (int c = 0; c < ncell; ++c) {
+    const int e0 = c % n0, e1 = (c / n0) % n1, e2 = c / (n0 * n1);
+    bool bad = false;
+    double X8[24];
+    geo.cell_vertices(e0, e1, e2, X8);
+    // weight per point: w / det J (the 3-form pullback) times the coefficient
+    std::vector<double> W(q * q * q);
+    for (int a3 = 0; a3 < q; ++a3)
+      for (int a2 = 0; a2 < q; ++a2)
+        for (int a1 = 0; a1 < q; ++a1) {
+          const double xi[3] = {xq[a1], xq[a2], xq[a3]};
+          double J[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+          for (int cn = 0; cn < 8; ++cn) {
+            const int c1 = cn & 1, c2 = (cn >> 1) & 1, c3 = cn >> 2;
+            const double N[3] = {c1 ? 0.5 * (1 + xi[0]) : 0.5 * (1 - xi[0]),
+                                 c2 ? 0.5 * (1 + xi[1]) : 0.5 * (1 - xi[1]),
+                                 c3 ? 0.5 * (1 + xi[2]) : 0.5 * (1 - xi[2])};
+            const double dN[3] = {c1 ? 0.5 : -0.5, c2 ? 0.5 : -0.5, c3 ? 0.5 : -0.5};
+            const double g[3] = {dN[0] * N[1] * N[2], N[0] * dN[1] * N[2], N[0] * N[1] * dN[2]};
+            for (int r = 0; r < 3; ++r)
+              for (int d = 0; d < 3; ++d) J[3 * r + d] += X8[3 * cn + r] * g[d];
+          }
+          const double det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
+                             J[2] * (J[3] * J[7] - J[4] * J[6]);
+          if (!(det > 0)) bad = true;
+          W[a1 + q * (a2 + q * a3)] = wq[a1] * wq[a2] * wq[a3] * coef[c] / det;
+        }
+    if (bad) {
+#ifdef _OPENMP
+#pragma omp critical(rm_mass_v3_inverted)
+#endif
+      inverted = c;
+      continue;
+    }
+    std::vector<Trip> &t = parts[c];
+    for (int i3 = 0; i3 < p; ++i3)
+      for (int i2 = 0; i2 < p; ++i2)
+        for (int i1 = 0; i1 < p; ++i1)
+          for (int j3 = 0; j3 < p; ++j3)
+            for (int j2 = 0; j2 < p; ++j2)
+              for (int j1 = 0; j1 < p; ++j1) {
+                double v = 0.0;
+                for (int a3 = 0; a3 < q; ++a3)
+                  for (int a2 = 0; a2 < q; ++a2) {
+                    const double f = R[a3 * p + i3] * R[a3 * p + j3] * R[a2 * p + i2] * R[a2 * p + j2];
+                    for (int a1 = 0; a1 < q; ++a1)
+                      v += f * R[a1 * p + i1] * R[a1 * p + j1] * W[a1 + q * (a2 + q * a3)];
+                  }
+                const long long gi = L3.index(0, (long long)e0 * p + i1, (long long)e1 * p + i2, (long long)e2 * p + i3);
+                const long long gj = L3.index(0, (long long)e0 * p + j1, (long long)e1 * p + j2, (long long)e2 * p + j3);
+                t.push_back({(int)gi, (int)gj, v});
+              }
+  }
+  (void)nl;
+  if (inverted >= 0) throw std::runtime_error("mass_v3: inverted cell " + std::to_string(inverted));
+  std::vector<Trip> all;
+  for (auto &pt : parts) all.insert(all.end(), pt.begin(), pt.end());
+  return csr_from_triplets((int)L3.size, (int)L3.size, all);
+}
+
 }  // namespace rm

@@ -179,6 +179,12 @@ constexpr double kHdivPotentialEps = 1e-2;
 Csr discrete_gradient(const Layout &L0, const Layout &L1, const std::vector<int> &rows1,
                       const std::vector<int> &cols0);
 
+// Mass matrix of V^3 (DQ_{p-1}, the FDM r-basis, Sec. 2.4) with the 3-form
+// pullback weight 1/det J and a per-cell coefficient, by the GLL rule of
+// quad_points(p): block diagonal (every entry lives in one cell), rows and
+// columns lattice indices of L3 (k = 3).
+Csr mass_v3(const Layout &L3, const Geometry &geo, const double *coef);
+
 // Quadrature points per direction: ceil(3(p+1)/2) (Sec. 5).
 inline int quad_points(int p) { return (3 * (p + 1) + 1) / 2; }
 

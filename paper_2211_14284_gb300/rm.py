@@ -36,7 +36,9 @@ EXPORTED = ["rm_default_options", "rm_setup", "rm_ndofs", "rm_layout", "rm_histo
             "rm_corrector_train", "rm_corrector_save", "rm_corrector_load", "rm_corrector_use",
             "rm_net_create", "rm_net_num_params", "rm_net_get_params", "rm_net_set_params",
             "rm_net_forward", "rm_net_backward", "rm_net_adam", "rm_net_destroy",
-            "rm_net_last_error"]
+            "rm_net_last_error", "rm_hodge_setup", "rm_hodge_ndofs", "rm_hodge_intervals",
+            "rm_hodge_apply", "rm_hodge_precondition", "rm_hodge_solve", "rm_hodge_destroy",
+            "rm_hodge_last_error"]
 RM_NOALLOC_MAX_COARSE = 8192
 RM_CORRECTOR_PLAIN, RM_CORRECTOR_LEARNED, RM_CORRECTOR_OFF = 0, 1, 2
 
@@ -54,7 +56,7 @@ class RmOptions(ctypes.Structure):
                 ("check_every", ctypes.c_int), ("profile", ctypes.c_int),
                 ("norm", ctypes.c_int), ("arith", ctypes.c_int), ("boundary", ctypes.c_int),
                 ("coarse_smoother", ctypes.c_int), ("composition", ctypes.c_int),
-                ("hybrid_omega", ctypes.c_double)]
+                ("hybrid_omega", ctypes.c_double), ("relaxation", ctypes.c_int)]
 
 
 class RmInfo(ctypes.Structure):
@@ -150,6 +152,17 @@ def load():
     lib.rm_net_destroy.argtypes = [vp]
     lib.rm_net_destroy.restype = None
     lib.rm_net_last_error.restype = ctypes.c_char_p
+    lib.rm_hodge_setup.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(RmMesh), ctypes.c_int,
+                                   ctypes.POINTER(RmOptions), ctypes.c_int, vp]
+    lib.rm_hodge_ndofs.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+    lib.rm_hodge_intervals.argtypes = [vp, c_dp, c_dp]
+    lib.rm_hodge_apply.argtypes = [vp, vp, vp]
+    lib.rm_hodge_precondition.argtypes = [vp, vp, vp]
+    lib.rm_hodge_solve.argtypes = [vp, vp, vp, ctypes.POINTER(RmInfo)]
+    lib.rm_hodge_destroy.argtypes = [vp]
+    lib.rm_hodge_destroy.restype = None
+    lib.rm_hodge_last_error.argtypes = [vp]
+    lib.rm_hodge_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
@@ -295,6 +308,67 @@ class Solver:
     def close(self):
         if getattr(self, "h", None):
             self.lib.rm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class HodgeSolver:
+    """rm_hodge_*: the mixed Hodge Laplacian of degree k (Gamma_D empty) with
+    MINRES and the Riesz-map block preconditioner."""
+
+    def __init__(self, k, n, p, vertices=None, cheb_its=4, stream=None, **opts):
+        lib = load()
+        n = (n, n, n) if isinstance(n, int) else tuple(n)
+        self._keep = []
+        mesh = RmMesh(n[0], n[1], n[2], None)
+        if vertices is not None:
+            arr, ptr = _dbl_array(vertices)
+            self._keep.append(arr)
+            mesh.vertices = ptr
+        o = options(**opts)
+        s = ctypes.c_void_p(0 if stream is None else stream.cuda_stream)
+        h = ctypes.c_void_p()
+        rc = lib.rm_hodge_setup(ctypes.byref(h), k, ctypes.byref(mesh), p, ctypes.byref(o), cheb_its, s)
+        if rc != 0:
+            raise RmError(rc, lib.rm_hodge_last_error(None).decode())
+        self.h, self.lib, self.k = h, lib, k
+        a, b = ctypes.c_longlong(), ctypes.c_longlong()
+        lib.rm_hodge_ndofs(h, ctypes.byref(a), ctypes.byref(b))
+        self.n_sigma, self.n_u = a.value, b.value
+        self.size = self.n_sigma + self.n_u
+
+    def _check(self, rc):
+        if rc != 0:
+            raise RmError(rc, self.lib.rm_hodge_last_error(self.h).decode())
+
+    def intervals(self):
+        a, b = (ctypes.c_double * 2)(), (ctypes.c_double * 2)()
+        self._check(self.lib.rm_hodge_intervals(self.h, a, b))
+        return tuple(a), tuple(b)
+
+    def apply(self, x, y):
+        self._check(self.lib.rm_hodge_apply(self.h, _ptr(x), _ptr(y)))
+
+    def precondition(self, r, z):
+        self._check(self.lib.rm_hodge_precondition(self.h, _ptr(r), _ptr(z)))
+
+    def solve(self, b, x, check=True):
+        info = RmInfo()
+        rc = self.lib.rm_hodge_solve(self.h, _ptr(b), _ptr(x), ctypes.byref(info))
+        if check and rc != 0:
+            self._check(rc)
+        return {"iterations": info.iterations, "status": STATUS.get(info.status),
+                "rel_res_natural": info.rel_res_natural, "solve_ms": info.solve_ms,
+                "setup_s": info.setup_s}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rm_hodge_destroy(self.h)
             self.h = None
 
     def __del__(self):
