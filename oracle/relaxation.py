@@ -383,9 +383,10 @@ class Condensed:
             ix = np.flatnonzero(lab == c)
             L = np.linalg.cholesky(PIId[ix][:, ix].toarray())
             Li = scipy.linalg.solve_triangular(L, np.eye(len(ix)), lower=True)
+            Bi = Li.T @ Li
             rows.append(np.repeat(ix, len(ix)))
             cols.append(np.tile(ix, len(ix)))
-            vals.append((Li.T @ Li).ravel())
+            vals.append((0.5 * (Bi + Bi.T)).ravel())   # symmetric to the last bit
             lvals.append(Li.ravel())
         nI = len(self.I)
         r_, c_ = np.concatenate(rows), np.concatenate(cols)
@@ -393,16 +394,24 @@ class Condensed:
         Linv = sp.csr_matrix((np.concatenate(lvals), (r_, c_)), shape=(nI, nI))
         W = (Linv @ self.PIG).tocsr()
         self.S = (PGG - (W.T @ W)).tocsr()
+        # the harmonic extension E = P_GI P_II^{-1} as one matrix, used with
+        # its exact transpose in condense and expand: the condensed
+        # preconditioner [[P_II^-1 + E^T M E, -E^T M], [-M E, M]] is then
+        # symmetric in floating point too (applying P_II^{-1} and P_IG in
+        # sequence leaves an asymmetry amplified by cond(P_II), 1e11 at
+        # beta / alpha = 1e-8, which CG does not survive)
+        self.E = (self.PGI @ self.PII_inv).tocsr()
+        self.Et = self.E.T.tocsr()
 
     def condense(self, r):
-        """(y_I, R_G r) with y_I = P_II^{-1} r_I."""
+        """(y_I, R_G r) with y_I = P_II^{-1} r_I and R_G r = r_G - E r_I."""
         yI = self.PII_inv @ r[self.I]
-        return yI, r[self.G] - self.PGI @ yI
+        return yI, r[self.G] - self.E @ r[self.I]
 
     def expand(self, yI, zG):
-        """z = R_I^T y_I + R_G^T z_G, written as [y_I - P_II^{-1} P_IG z_G; z_G]."""
+        """z = R_I^T y_I + R_G^T z_G, written as [y_I - E^T z_G; z_G]."""
         z = np.zeros(len(self.free))
-        z[self.I] = yI - self.PII_inv @ (self.PIG @ zG)
+        z[self.I] = yI - self.Et @ zG
         z[self.G] = zG
         return z
 

@@ -518,9 +518,11 @@ int rm_batch_setup(rm_batch **out, int nprob, const int *space, const rm_mesh *m
           cdt.append(transpose(P.D), &P.G0, nullptr, nullptr, B->off0[i], B->off[i]);
         }
       }
-      B->Binv = B->upload_cat(cb);
-      B->E = B->upload_cat(ce);
-      B->Et = B->upload_cat(cet);
+      // the interior solve and harmonic extension in FP64 whatever the
+      // precision (as in rm_setup)
+      B->Binv = B->upload_cat(cb, true);
+      B->E = B->upload_cat(ce, true);
+      B->Et = B->upload_cat(cet, true);
       if (B->ph) {
         B->Dt = B->upload_cat(cd);
         B->DtT = B->upload_cat(cdt);

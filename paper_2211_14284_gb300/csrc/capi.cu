@@ -743,9 +743,16 @@ int rm_setup(rm_handle **out, int space, const rm_mesh *mesh, int p, const doubl
     } else {
       Condensed C = condense(h->L, fm, P);
       P = Csr();
-      h->Binv = upload_csr(h.get(), C.Binv, &fm.free2lat, &fm.free2lat, &C.I);
-      h->E = upload_csr(h.get(), C.E, &fm.free2lat, &fm.free2lat, &C.G);
-      h->Et = upload_csr(h.get(), C.Et, &fm.free2lat, &fm.free2lat, &C.I);
+      // the interior solve and the harmonic extension stay FP64 in every
+      // precision: an FP32 interior expansion leaves rounding noise in the
+      // cell-interior DOFs, whose stiffness (up to alpha p^4 / h^2) makes A z
+      // dominated by that noise at high degree and coefficient contrast
+      // (H(div), 16^3, p = 10, alpha in [1e-2, 1e2]: FCG diverged); the
+      // extension of an FP32 interface correction is energy-minimising, so
+      // the FP32 patch solves do not have that problem
+      h->Binv = upload_csr(h.get(), C.Binv, &fm.free2lat, &fm.free2lat, &C.I, true);
+      h->E = upload_csr(h.get(), C.E, &fm.free2lat, &fm.free2lat, &C.G, true);
+      h->Et = upload_csr(h.get(), C.Et, &fm.free2lat, &fm.free2lat, &C.I, true);
       if (!h->ph) {
         PatchFamily F = build_patches(h->L, fm, C.S, 0, true, o.factor == RM_ICC ? 1 : 0);
         h->fam.push_back(upload_family(h.get(), F));

@@ -114,6 +114,39 @@ __device__ __forceinline__ DF rfrom<DF>(double x) {
 __device__ __forceinline__ double rto(double a) { return a; }
 __device__ __forceinline__ double rto(DF a) { return (double)a.hi + (double)a.lo; }
 
+// The conversions between FP64 and double-float without the FP64 pipe
+// (1/64 of the FP32 rate on GB300), by integer operations on the bit
+// patterns.  df_split: hi = the leading 24 significand bits of x (truncated),
+// lo = the next 24 (truncated), so hi + lo agrees with x to 2^-48 relative;
+// for |x| < 2^-70 (lo would leave the FP32 range), |x| >= 2^127 and zero the
+// FP64 path rfrom<DF> is taken.
+__device__ __forceinline__ DF df_split(double x) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((bits >> 52) & 0x7FF) - 1023;  // unbiased exponent
+  if (e < -70 || e > 126) return rfrom<DF>(x);       // zero, tiny, huge: rare
+  const unsigned sign = (unsigned)(bits >> 32) & 0x80000000u;
+  const unsigned long long frac = bits & 0xFFFFFFFFFFFFFULL;
+  const float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)(frac >> 29));
+  const unsigned r = (unsigned)(frac & 0x1FFFFFFFu);  // the 29 bits below hi, weight 2^(e - 52)
+  if (r == 0u) return {hi, 0.f};
+  const int lead = 31 - __clz(r);                     // 0 .. 28
+  const unsigned m = lead >= 23 ? (r >> (lead - 23)) : (r << (23 - lead));
+  const float lo = __uint_as_float(sign | ((unsigned)(e - 52 + lead + 127) << 23) | (m & 0x7FFFFFu));
+  return {hi, lo};
+}
+// a normal FP32 value as FP64, by its bits (exact)
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xFFu;
+  if (ex == 0u || ex == 0xFFu) return (double)f;  // zero, subnormal, inf, nan
+  const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(ex - 127 + 1023) << 52) |
+                               ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)b);
+}
+// hi + lo in FP64: the two exact conversions by bits and one FP64 add
+__device__ __forceinline__ double df_to_double(DF a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
+
 // Dot-product accumulator: for double-float, the compensated scheme of
 // Ogita, Rump and Oishi (Dot2): the running sum h and a compensation l take
 // every exact product a.hi b.hi = p + e (plus the cross terms) through one

