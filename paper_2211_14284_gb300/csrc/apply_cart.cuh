@@ -10,9 +10,14 @@
 // Two launches, no atomics, bitwise reproducible:
 //  * cart_local_kernel<K, P, R>: the cell products y_K = A_K x_K, one CTA per
 //    CPB cells, every shape and loop bound a compile-time constant of
-//    (K, P); written unassembled to the scratch Y[cell][local entry] (FP64);
-//  * cart_assemble_kernel<K, P>: every lattice entry sums its (at most 8)
-//    cell contributions from Y in a fixed order; Dirichlet entries get 0.
+//    (K, P); written unassembled to the scratch Y[cell][local entry] in the
+//    number type R;
+//  * cart_assemble_kernel<K, P, R>: every lattice entry sums its (at most 8)
+//    cell contributions from Y in a fixed order, in R, and converts once to
+//    FP64; Dirichlet entries get 0.
+// The double-float instances convert between FP64 and pairs of FP32 by
+// integer operations on the bit patterns (df_split, df_to_double), off the
+// FP64 pipe.
 // R = double (FP64) or DF (double-float, df.cuh), chosen per handle.
 //
 // This header holds the templates; apply_cart_part.cu instantiates them for
@@ -84,7 +89,7 @@ __device__ __forceinline__ R kron_mass(const R *in, int i0, int i1, int i2, R a,
 
 template <int K, int P, typename R>
 __global__ void __launch_bounds__(kCartThreads) cart_local_kernel(ApplyDev A, const double *__restrict__ x,
-                                                                  double *__restrict__ Y) {
+                                                                  R *__restrict__ Y) {
   using Sh = CartShape<K, P>;
   constexpr int NC0 = Sh::NC0, NC1 = Sh::NC1, S0 = Sh::S0, S1 = Sh::S1, L0 = Sh::L0, L1 = Sh::L1;
   constexpr int CPB = Sh::CPB, DREG = Sh::DREG, LMAX = Sh::LMAX, NT = kCartThreads;
@@ -150,7 +155,7 @@ __global__ void __launch_bounds__(kCartThreads) cart_local_kernel(ApplyDev A, co
       const long long b0 = cbase[cb][m];
       double v = 0.0;
       if (b0 >= 0 && !dir) v = x[b0 + i0 + (long long)A.N[m][0] * (i1 + (long long)A.N[m][1] * i2)];
-      xl[cb * L0 + m * S0 + r] = rfrom<R>(v);
+      xl[cb * L0 + m * S0 + r] = to_r<R>(v);
     }
   });
   __syncthreads();
@@ -172,7 +177,7 @@ __global__ void __launch_bounds__(kCartThreads) cart_local_kernel(ApplyDev A, co
     for (int li = tid; li < CPB * S1; li += NT) {
       const int cb = li / S1, r = li - cb * S1;
       const int j0 = r % l0, j1 = (r / l0) % l1, j2 = r / (l0 * l1);
-      R acc = rzero(R());
+      Acc<R> acc;
       sfor<dterm_count(K, t)>([&](auto sc) {
         constexpr DTerm T = dterm(K, t, decltype(sc)::value);
         // the source is s-type along T.dir (P + 1 entries), equal elsewhere
@@ -181,12 +186,13 @@ __global__ void __launch_bounds__(kCartThreads) cart_local_kernel(ApplyDev A, co
         const int j = T.dir == 0 ? j0 : (T.dir == 1 ? j1 : j2);
         const int base = (T.dir == 0 ? 0 : j0) + sl0 * ((T.dir == 1 ? 0 : j1) + sl1 * (T.dir == 2 ? 0 : j2));
         const R *in = xl + cb * L0 + T.src * S0 + base;
-        R v = rmul(D1[j * Q1], in[0]);
-        v = rfma(D1[j * Q1 + P], in[P * str], v);
-        if (j >= 1) v = rfma(D1[j * Q1 + j], in[j * str], v);
-        acc = T.sgn > 0 ? radd(acc, v) : rsub(acc, v);
+        // the term's sign on the input (a sign flip is exact)
+        auto sg = [&](R v) { return T.sgn > 0 ? v : rneg(v); };
+        acc.add(D1[j * Q1], sg(in[0]));
+        acc.add(D1[j * Q1 + P], sg(in[P * str]));
+        if (j >= 1) acc.add(D1[j * Q1 + j], sg(in[j * str]));
       });
-      dl[cb * DREG + t * S1 + r] = acc;
+      dl[cb * DREG + t * S1 + r] = acc.val();
     }
   });
   __syncthreads();
@@ -237,7 +243,7 @@ __global__ void __launch_bounds__(kCartThreads) cart_local_kernel(ApplyDev A, co
     for (int li = tid; li < CPB * S0; li += NT) {
       const int cb = li / S0, r = li - cb * S0;
       const int i0 = r % l0, i1 = (r / l0) % l1, i2 = r / (l0 * l1);
-      R acc = yl[cb * L0 + m * S0 + r];
+      Acc<R> acc(yl[cb * L0 + m * S0 + r]);
       sfor<Sh::NTERMS>([&](auto tsc) {
         constexpr int ts = decltype(tsc)::value;
         constexpr int t = term_t(K, ts);
@@ -246,21 +252,21 @@ __global__ void __launch_bounds__(kCartThreads) cart_local_kernel(ApplyDev A, co
           // the target is r-type along T.dir (P entries), equal elsewhere
           constexpr int tl0 = T.dir == 0 ? P : l0, tl1 = T.dir == 1 ? P : l1;
           const int i = T.dir == 0 ? i0 : (T.dir == 1 ? i1 : i2);
-          R v;
           if (i == 0 || i == P) {
             const int a = T.dir == 0 ? i1 : i0, b = T.dir == 2 ? i1 : i2;
             constexpr int la = T.dir == 0 ? tl1 : tl0;
-            v = dl[cb * DREG + 2 * (ts * LMAX + a + la * b) + (i == 0 ? 0 : 1)];
+            const R v = dl[cb * DREG + 2 * (ts * LMAX + a + la * b) + (i == 0 ? 0 : 1)];
+            acc.add_value(T.sgn > 0 ? v : rneg(v));
           } else {
             constexpr int str = T.dir == 0 ? 1 : (T.dir == 1 ? tl0 : tl0 * tl1);
             const int base = (T.dir == 0 ? 0 : i0) + tl0 * ((T.dir == 1 ? 0 : i1) + tl1 * (T.dir == 2 ? 0 : i2));
-            v = rmul(D1[i * Q1 + i], dyl[cb * L1 + t * S1 + base + i * str]);
+            const R v = dyl[cb * L1 + t * S1 + base + i * str];
+            acc.add(D1[i * Q1 + i], T.sgn > 0 ? v : rneg(v));
           }
-          acc = T.sgn > 0 ? radd(acc, v) : rsub(acc, v);
         }
       });
       const int c = c0 + cb;
-      if (c < ncell) Y[(size_t)c * L0 + m * S0 + r] = rto(acc);
+      if (c < ncell) Y[(size_t)c * L0 + m * S0 + r] = acc.val();
     }
   });
 }
@@ -268,8 +274,8 @@ __global__ void __launch_bounds__(kCartThreads) cart_local_kernel(ApplyDev A, co
 // y[g] = sum over the cells holding lattice entry g of their contribution in
 // Y, in a fixed order (cells lexicographic); Dirichlet entries 0.  Grid:
 // x along g0, y over rows (g1, g2), z over components.
-template <int K, int P>
-__global__ void __launch_bounds__(128) cart_assemble_kernel(ApplyDev A, const double *__restrict__ Y,
+template <int K, int P, typename R>
+__global__ void __launch_bounds__(128) cart_assemble_kernel(ApplyDev A, const R *__restrict__ Y,
                                                             double *__restrict__ y) {
   using Sh = CartShape<K, P>;
   const int m = blockIdx.z;
@@ -303,15 +309,15 @@ __global__ void __launch_bounds__(128) cart_assemble_kernel(ApplyDev A, const do
         ci[d][0] = i;
       }
     }
-    double s = 0.0;
+    R s = rzero(R());
     if (!dir)
       for (int c = 0; c < nc[2]; ++c)
         for (int b = 0; b < nc[1]; ++b)
           for (int a = 0; a < nc[0]; ++a) {
             const size_t cell = ce[0][a] + (size_t)A.n[0] * (ce[1][b] + (size_t)A.n[1] * ce[2][c]);
-            s += Y[cell * Sh::L0 + m * Sh::S0 + ci[0][a] + l[0] * (ci[1][b] + l[1] * ci[2][c])];
+            s = radd(s, Y[cell * Sh::L0 + m * Sh::S0 + ci[0][a] + l[0] * (ci[1][b] + l[1] * ci[2][c])]);
           }
-    y[A.off[m] + g0 + (long long)N0 * row] = s;
+    y[A.off[m] + g0 + (long long)N0 * row] = to_double(s);
   }
 }
 
@@ -324,7 +330,7 @@ cudaError_t launch_cart_kpr(const ApplyDev &A, const double *x, double *y, cudaS
       cudaFuncSetAttribute(cart_local_kernel<K, P, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   const int ncell = A.n[0] * A.n[1] * A.n[2];
-  cart_local_kernel<K, P, R><<<(ncell + Sh::CPB - 1) / Sh::CPB, kCartThreads, smem, s>>>(A, x, A.Y);
+  cart_local_kernel<K, P, R><<<(ncell + Sh::CPB - 1) / Sh::CPB, kCartThreads, smem, s>>>(A, x, reinterpret_cast<R *>(A.Y));
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   int rows = 0, n0max = 0;
@@ -333,7 +339,7 @@ cudaError_t launch_cart_kpr(const ApplyDev &A, const double *x, double *y, cudaS
     n0max = n0max > A.N[m][0] ? n0max : A.N[m][0];
   }
   const dim3 grid((n0max + 127) / 128, rows < 65535 ? rows : 65535, Sh::NC0);
-  cart_assemble_kernel<K, P><<<grid, 128, 0, s>>>(A, A.Y, y);
+  cart_assemble_kernel<K, P, R><<<grid, 128, 0, s>>>(A, reinterpret_cast<const R *>(A.Y), y);
   return cudaGetLastError();
 }
 template <int K, int P>

@@ -134,6 +134,13 @@ __device__ __forceinline__ DF df_split(double x) {
   const float lo = __uint_as_float(sign | ((unsigned)(e - 52 + lead + 127) << 23) | (m & 0x7FFFFFu));
   return {hi, lo};
 }
+// FP64 <-> the apply's number type: the integer split for double-float
+template <typename R>
+__device__ __forceinline__ R to_r(double x);
+template <>
+__device__ __forceinline__ double to_r<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ DF to_r<DF>(double x) { return df_split(x); }
 // a normal FP32 value as FP64, by its bits (exact)
 __device__ __forceinline__ double f2d_bits(float f) {
   const unsigned u = __float_as_uint(f);
@@ -146,6 +153,8 @@ __device__ __forceinline__ double f2d_bits(float f) {
 }
 // hi + lo in FP64: the two exact conversions by bits and one FP64 add
 __device__ __forceinline__ double df_to_double(DF a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
+__device__ __forceinline__ double to_double(double a) { return a; }
+__device__ __forceinline__ double to_double(DF a) { return df_to_double(a); }
 
 // Dot-product accumulator: for double-float, the compensated scheme of
 // Ogita, Rump and Oishi (Dot2): the running sum h and a compensation l take
@@ -157,12 +166,23 @@ struct Acc;
 template <>
 struct Acc<double> {
   double s = 0.0;
+  Acc() = default;
+  __device__ __forceinline__ explicit Acc(double v) : s(v) {}
   __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+  __device__ __forceinline__ void add_value(double v) { s += v; }
   __device__ __forceinline__ double val() const { return s; }
 };
 template <>
 struct Acc<DF> {
   float h = 0.f, l = 0.f;
+  Acc() = default;
+  __device__ __forceinline__ explicit Acc(DF v) : h(v.hi), l(v.lo) {}
+  // the pair v.hi + v.lo taken in like a product's p + e
+  __device__ __forceinline__ void add_value(DF v) {
+    const DF t = two_sum(h, v.hi);
+    h = t.hi;
+    l = __fadd_rn(l, __fadd_rn(t.lo, v.lo));
+  }
   __device__ __forceinline__ void add(DF a, DF b) {
     const float p = __fmul_rn(a.hi, b.hi);
     float e = fmaf(a.hi, b.hi, -p);
