@@ -22,6 +22,7 @@ sample of the same workload (3x3x3 mesh, same p, perturbation and solvers).
 from __future__ import annotations
 
 import argparse
+import concurrent.futures
 import json
 import os
 import statistics
@@ -198,12 +199,17 @@ def run_ours(args):
     al = inputs.constant_coefficient(n)
     be = inputs.constant_coefficient(n)
 
+    # the two problems of a step are independent: each solves on its own
+    # stream, driven by its own host thread, so their latency-bound kernels
+    # overlap on the GPU
+    space_streams = {sname: torch.cuda.Stream() for sname, _, _ in SPACES}
+    pool = concurrent.futures.ThreadPoolExecutor(max_workers=len(SPACES))
     solvers = {}
     t0 = time.time()
     for vname, vopt in VARIANTS.items():
         for sname, k, sopt in SPACES:
             solvers[(vname, sname)] = Solver(k, n, p, vertices=X, alpha=al, beta=be,
-                                             stream=stream, rtol=1e-8, max_it=1000,
+                                             stream=space_streams[sname], rtol=1e-8, max_it=1000,
                                              profile=1, **sopt, **vopt)
     setup_s = time.time() - t0
     sizes = {sname: solvers[(HEADLINE, sname)].size for sname, _, _ in SPACES}
@@ -221,8 +227,10 @@ def run_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
-    def one_step(vname, e2e, stats):
-        for sname, _, _ in SPACES:
+    def solve_space(vname, sname, e2e, start):
+        st = space_streams[sname]
+        st.wait_event(start)
+        with torch.cuda.stream(st):
             if e2e:
                 bd[sname].copy_(bh[sname], non_blocking=True)
             xd[sname].zero_()
@@ -231,6 +239,19 @@ def run_ours(args):
                 raise RuntimeError(f"{vname}/{sname} did not converge: {info}")
             if e2e:
                 xh[sname].copy_(xd[sname], non_blocking=True)
+            done = torch.cuda.Event()
+            done.record(st)
+        return sname, info, done
+
+    def one_step(vname, e2e, stats):
+        """Both problems from the main stream's current point; returns when
+        the main stream has been made to wait for both."""
+        start = torch.cuda.Event()
+        start.record(stream)
+        futs = [pool.submit(solve_space, vname, sname, e2e, start) for sname, _, _ in SPACES]
+        for f in futs:
+            sname, info, done = f.result()
+            stream.wait_event(done)
             stats.append((sname, info))
 
     def timed(vname, e2e, steps, warmup):
@@ -558,7 +579,7 @@ def run_batched(count, steps, warmup, stream):
                        f"first {len(probs)} problems with n, p <= 8")}
 
 
-def run_learned(steps, warmup, epochs, n, stream):
+def run_learned(steps, warmup, epochs, n, stream, on_policy_rounds=2):
     """H(grad) on n^3 (default 32^3) uniform cells, p = 6, lognormal Gaussian-random-field
     alpha: the learned coarse corrector (trained here on pairs the solver
     generates) against the plain coarse correction (the V(2,2) cycle) and
@@ -578,7 +599,6 @@ def run_learned(steps, warmup, epochs, n, stream):
     rhs = torch.randn(150, s.size, dtype=torch.float64, device="cuda", generator=gen)
     train = s.corrector_train(rhs, pairs=2000, epochs=epochs, levels=3, width=16, batch=16,
                               lr=2e-3)
-    del rhs
     b = torch.tensor(inputs.normal_rhs(s.size, 77), device="cuda")
     x = torch.zeros_like(b)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
@@ -614,6 +634,15 @@ def run_learned(steps, warmup, epochs, n, stream):
            "learned": time_mode(RM_CORRECTOR_LEARNED, 4, 0.9, steps, warmup),
            "learned_unjudged": time_mode(RM_CORRECTOR_LEARNED, 0, 1.0, 1, 0),
            "off": time_mode(RM_CORRECTOR_OFF, 0, 1.0, 1, 0)}
+    # on-policy: two more rounds of pairs from solves that use the network
+    if on_policy_rounds > 0:
+        s.corrector_use(RM_CORRECTOR_PLAIN, 0, 1.0)
+        out["train_on_policy"] = s.corrector_train(rhs, pairs=2000, epochs=epochs, levels=3, width=16,
+                                                   batch=16, lr=2e-3, rounds=on_policy_rounds,
+                                                   round_pairs=500, round_epochs=max(1, epochs // 2))
+        out["learned_on_policy"] = time_mode(RM_CORRECTOR_LEARNED, 4, 0.9, steps, warmup)
+        out["learned_on_policy_unjudged"] = time_mode(RM_CORRECTOR_LEARNED, 0, 1.0, 1, 0)
+    del rhs
     s.corrector_use(RM_CORRECTOR_PLAIN, 0, 1.0)
     out["value"] = out["learned"]["value"]
     return out

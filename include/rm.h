@@ -354,10 +354,17 @@ typedef struct {
   double off_fraction;     /* pairs recorded from one-level solves (no coarse term,
                               64 iterations each), the rest from plain two-level
                               solves (default 0) */
+  int rounds;              /* on-policy rounds after the first training (default 0):
+                              each records round_pairs more pairs from solves that
+                              use the current network (unjudged), computes their
+                              targets and trains round_epochs more epochs on all
+                              training pairs */
+  int round_pairs;         /* pairs per round (default 500) */
+  int round_epochs;        /* epochs per round (default 5) */
 } rm_train_options;
 
 typedef struct {
-  int pairs, solves;       /* pairs collected, plain solves run to collect them */
+  int pairs, solves;       /* pairs collected (all rounds), solves run to collect them */
   long long params;        /* network parameters */
   double gen_s, train_s;   /* wall time of data generation and of training */
   double train_loss;       /* mean squared error over the last epoch */

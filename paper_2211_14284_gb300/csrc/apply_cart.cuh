@@ -87,6 +87,57 @@ __device__ __forceinline__ R kron_mass(const R *in, int i0, int i1, int i2, R a,
   return f2 ? rfma(b, plane(P - i2), rmul(a, v)) : v;
 }
 
+
+// Lines along direction 0 of a component block with local sizes (., L1, L2),
+// in the CTA's CPB cells: f(cb, i1, i2) once per line, lines spread over
+// the threads.
+template <int CPB, int LL1, int LL2, typename F>
+__device__ __forceinline__ void for_lines(F &&f, int = 0) {
+  constexpr int NL = LL1 * LL2;
+  for (int u = threadIdx.x; u < CPB * NL; u += kCartThreads) {
+    const int cb = u / NL, r = u - cb * NL;
+    f(cb, r % LL1, r / LL1);
+  }
+}
+
+// (x)_d F_d on the whole line (i1, i2) of a component block `in` (local sizes
+// LL0, LL1, .): the lines at P - i1 and P - i2 enter where i1, i2 lie on the
+// s-type interface {0, P} (weights a on the own index, b on the opposite
+// one), then the same along direction 0 at the compile-time ends.
+template <bool T0, bool T1, bool T2, int LL0, int LL1, int P, typename R>
+__device__ __forceinline__ void line_mass(const R *in, int i1, int i2, R a, R b, R (&u)[LL0]) {
+  const bool f1 = T1 && (i1 == 0 || i1 == P), f2 = T2 && (i2 == 0 || i2 == P);
+  const R *l00 = in + LL0 * (i1 + LL1 * i2);
+  R w[LL0];
+#pragma unroll
+  for (int i0 = 0; i0 < LL0; ++i0) w[i0] = l00[i0];
+  if (f1) {
+    const R *l10 = in + LL0 * ((P - i1) + LL1 * i2);
+#pragma unroll
+    for (int i0 = 0; i0 < LL0; ++i0) w[i0] = rfma(b, l10[i0], rmul(a, w[i0]));
+  }
+  if (f2) {
+    const R *l01 = in + LL0 * (i1 + LL1 * (P - i2));
+    R v[LL0];
+#pragma unroll
+    for (int i0 = 0; i0 < LL0; ++i0) v[i0] = l01[i0];
+    if (f1) {
+      const R *l11 = in + LL0 * ((P - i1) + LL1 * (P - i2));
+#pragma unroll
+      for (int i0 = 0; i0 < LL0; ++i0) v[i0] = rfma(b, l11[i0], rmul(a, v[i0]));
+    }
+#pragma unroll
+    for (int i0 = 0; i0 < LL0; ++i0) w[i0] = rfma(b, v[i0], rmul(a, w[i0]));
+  }
+  if constexpr (T0) {
+#pragma unroll
+    for (int i0 = 0; i0 < LL0; ++i0) u[i0] = (i0 == 0 || i0 == P) ? rfma(b, w[P - i0], rmul(a, w[i0])) : w[i0];
+  } else {
+#pragma unroll
+    for (int i0 = 0; i0 < LL0; ++i0) u[i0] = w[i0];
+  }
+}
+
 template <int K, int P, typename R>
 __global__ void __launch_bounds__(kCartThreads) cart_local_kernel(ApplyDev A, const double *__restrict__ x,
                                                                   R *__restrict__ Y) {
@@ -140,73 +191,98 @@ __global__ void __launch_bounds__(kCartThreads) cart_local_kernel(ApplyDev A, co
   }
   __syncthreads();
   const R ba = rfrom<R>(A.bh_a), bb = rfrom<R>(A.bh_b);
+  // Every phase runs over lines along direction 0: a thread takes one line
+  // (cell cb, indices i1, i2) and walks its l0 entries with a compile-time
+  // unrolled loop, so index decoding happens once per line and the
+  // interface tests along direction 0 fold into constants.
   // ---- gather x (Dirichlet entries and padding cells read as 0) ----
   sfor<NC0>([&](auto mc) {
     constexpr int m = decltype(mc)::value;
     constexpr bool t0 = styp(K, m, 0), t1 = styp(K, m, 1), t2 = styp(K, m, 2);
-    constexpr int l0 = sld(K, P, m, 0), l1 = sld(K, P, m, 1);
-    for (int li = tid; li < CPB * S0; li += NT) {
-      const int cb = li / S0, r = li - cb * S0;
-      const int i0 = r % l0, i1 = (r / l0) % l1, i2 = r / (l0 * l1);
+    constexpr int l0 = sld(K, P, m, 0), l1 = sld(K, P, m, 1), l2 = sld(K, P, m, 2);
+    for_lines<CPB, l1, l2>([&](int cb, int i1, int i2) {
       const int f = cdir[cb];
-      const bool dir = (t0 && (((f & 1) && i0 == 0) || ((f & 2) && i0 == P))) ||
-                       (t1 && (((f & 4) && i1 == 0) || ((f & 8) && i1 == P))) ||
-                       (t2 && (((f & 16) && i2 == 0) || ((f & 32) && i2 == P)));
       const long long b0 = cbase[cb][m];
-      double v = 0.0;
-      if (b0 >= 0 && !dir) v = x[b0 + i0 + (long long)A.N[m][0] * (i1 + (long long)A.N[m][1] * i2)];
-      xl[cb * L0 + m * S0 + r] = to_r<R>(v);
-    }
+      const bool dl_ = (t1 && (((f & 4) && i1 == 0) || ((f & 8) && i1 == P))) ||
+                       (t2 && (((f & 16) && i2 == 0) || ((f & 32) && i2 == P)));
+      const double *src = x + (b0 >= 0 ? b0 + (long long)A.N[m][0] * (i1 + (long long)A.N[m][1] * i2) : 0);
+      R *dst = xl + cb * L0 + m * S0 + l0 * (i1 + l1 * i2);
+#pragma unroll
+      for (int i0 = 0; i0 < l0; ++i0) {
+        const bool d = dl_ || (t0 && (((f & 1) && i0 == 0) || ((f & 2) && i0 == P)));
+        dst[i0] = to_r<R>((b0 >= 0 && !d) ? src[i0] : 0.0);
+      }
+    });
   });
   __syncthreads();
   // ---- y = beta M^K x;  d = D-hat x ----
   sfor<NC0>([&](auto mc) {
     constexpr int m = decltype(mc)::value;
     constexpr bool t0 = styp(K, m, 0), t1 = styp(K, m, 1), t2 = styp(K, m, 2);
-    constexpr int l0 = sld(K, P, m, 0), l1 = sld(K, P, m, 1);
-    for (int li = tid; li < CPB * S0; li += NT) {
-      const int cb = li / S0, r = li - cb * S0;
-      const int i0 = r % l0, i1 = (r / l0) % l1, i2 = r / (l0 * l1);
-      yl[cb * L0 + m * S0 + r] =
-          rmul(coef[cb * 8 + m], kron_mass<t0, t1, t2, l0, l1, P>(xl + cb * L0 + m * S0, i0, i1, i2, ba, bb));
-    }
+    constexpr int l0 = sld(K, P, m, 0), l1 = sld(K, P, m, 1), l2 = sld(K, P, m, 2);
+    for_lines<CPB, l1, l2>([&](int cb, int i1, int i2) {
+      R u[l0];
+      line_mass<t0, t1, t2, l0, l1, P>(xl + cb * L0 + m * S0, i1, i2, ba, bb, u);
+      R *dst = yl + cb * L0 + m * S0 + l0 * (i1 + l1 * i2);
+      const R cm = coef[cb * 8 + m];
+#pragma unroll
+      for (int i0 = 0; i0 < l0; ++i0) dst[i0] = rmul(cm, u[i0]);
+    });
   });
   sfor<NC1>([&](auto tc) {
     constexpr int t = decltype(tc)::value;
-    constexpr int l0 = sld(K + 1, P, t, 0), l1 = sld(K + 1, P, t, 1);
-    for (int li = tid; li < CPB * S1; li += NT) {
-      const int cb = li / S1, r = li - cb * S1;
-      const int j0 = r % l0, j1 = (r / l0) % l1, j2 = r / (l0 * l1);
-      Acc<R> acc;
+    constexpr int l0 = sld(K + 1, P, t, 0), l1 = sld(K + 1, P, t, 1), l2 = sld(K + 1, P, t, 2);
+    for_lines<CPB, l1, l2>([&](int cb, int j1, int j2) {
+      Acc<R> acc[l0];
       sfor<dterm_count(K, t)>([&](auto sc) {
         constexpr DTerm T = dterm(K, t, decltype(sc)::value);
         // the source is s-type along T.dir (P + 1 entries), equal elsewhere
         constexpr int sl0 = T.dir == 0 ? Q1 : l0, sl1 = T.dir == 1 ? Q1 : l1;
-        constexpr int str = T.dir == 0 ? 1 : (T.dir == 1 ? sl0 : sl0 * sl1);
-        const int j = T.dir == 0 ? j0 : (T.dir == 1 ? j1 : j2);
-        const int base = (T.dir == 0 ? 0 : j0) + sl0 * ((T.dir == 1 ? 0 : j1) + sl1 * (T.dir == 2 ? 0 : j2));
-        const R *in = xl + cb * L0 + T.src * S0 + base;
-        // the term's sign on the input (a sign flip is exact)
+        const R *src = xl + cb * L0 + T.src * S0;
         auto sg = [&](R v) { return T.sgn > 0 ? v : rneg(v); };
-        acc.add(D1[j * Q1], sg(in[0]));
-        acc.add(D1[j * Q1 + P], sg(in[P * str]));
-        if (j >= 1) acc.add(D1[j * Q1 + j], sg(in[j * str]));
+        if constexpr (T.dir == 0) {
+          const R *in = src + sl0 * (j1 + sl1 * j2);
+#pragma unroll
+          for (int j = 0; j < l0; ++j) {
+            acc[j].add(D1[j * Q1], sg(in[0]));
+            acc[j].add(D1[j * Q1 + P], sg(in[P]));
+            if (j >= 1) acc[j].add(D1[j * Q1 + j], sg(in[j]));
+          }
+        } else {
+          const int j = T.dir == 1 ? j1 : j2;
+          // the three source lines at index 0, P and j along T.dir
+          auto line_at = [&](int i) {
+            return T.dir == 1 ? src + sl0 * (i + sl1 * j2) : src + sl0 * (j1 + sl1 * i);
+          };
+          const R *s0 = line_at(0), *sp = line_at(P), *sj = line_at(j);
+          const R d0 = D1[j * Q1], dp = D1[j * Q1 + P], dj = D1[j * Q1 + j];
+#pragma unroll
+          for (int i0 = 0; i0 < l0; ++i0) {
+            acc[i0].add(d0, sg(s0[i0]));
+            acc[i0].add(dp, sg(sp[i0]));
+            if (j >= 1) acc[i0].add(dj, sg(sj[i0]));
+          }
+        }
       });
-      dl[cb * DREG + t * S1 + r] = acc.val();
-    }
+      R *dst = dl + cb * DREG + t * S1 + l0 * (j1 + l1 * j2);
+#pragma unroll
+      for (int i0 = 0; i0 < l0; ++i0) dst[i0] = acc[i0].val();
+    });
   });
   __syncthreads();
   // ---- dy = alpha M^{K+1} d ----
   sfor<NC1>([&](auto tc) {
     constexpr int t = decltype(tc)::value;
     constexpr bool t0 = styp(K + 1, t, 0), t1 = styp(K + 1, t, 1), t2 = styp(K + 1, t, 2);
-    constexpr int l0 = sld(K + 1, P, t, 0), l1 = sld(K + 1, P, t, 1);
-    for (int li = tid; li < CPB * S1; li += NT) {
-      const int cb = li / S1, r = li - cb * S1;
-      const int j0 = r % l0, j1 = (r / l0) % l1, j2 = r / (l0 * l1);
-      dyl[cb * L1 + t * S1 + r] = rmul(coef[cb * 8 + 3 + t],
-                                       kron_mass<t0, t1, t2, l0, l1, P>(dl + cb * DREG + t * S1, j0, j1, j2, ba, bb));
-    }
+    constexpr int l0 = sld(K + 1, P, t, 0), l1 = sld(K + 1, P, t, 1), l2 = sld(K + 1, P, t, 2);
+    for_lines<CPB, l1, l2>([&](int cb, int j1, int j2) {
+      R u[l0];
+      line_mass<t0, t1, t2, l0, l1, P>(dl + cb * DREG + t * S1, j1, j2, ba, bb, u);
+      R *dst = dyl + cb * L1 + t * S1 + l0 * (j1 + l1 * j2);
+      const R cm = coef[cb * 8 + 3 + t];
+#pragma unroll
+      for (int i0 = 0; i0 < l0; ++i0) dst[i0] = rmul(cm, u[i0]);
+    });
   });
   __syncthreads();
   // ---- line sums of D-hat^T's interface rows, into the d region: for every
@@ -239,11 +315,12 @@ __global__ void __launch_bounds__(kCartThreads) cart_local_kernel(ApplyDev A, co
   // ---- y += D-hat^T dy; the cell's unassembled product to Y ----
   sfor<NC0>([&](auto mc) {
     constexpr int m = decltype(mc)::value;
-    constexpr int l0 = sld(K, P, m, 0), l1 = sld(K, P, m, 1);
-    for (int li = tid; li < CPB * S0; li += NT) {
-      const int cb = li / S0, r = li - cb * S0;
-      const int i0 = r % l0, i1 = (r / l0) % l1, i2 = r / (l0 * l1);
-      Acc<R> acc(yl[cb * L0 + m * S0 + r]);
+    constexpr int l0 = sld(K, P, m, 0), l1 = sld(K, P, m, 1), l2 = sld(K, P, m, 2);
+    for_lines<CPB, l1, l2>([&](int cb, int i1, int i2) {
+      const R *yline = yl + cb * L0 + m * S0 + l0 * (i1 + l1 * i2);
+      Acc<R> acc[l0];
+#pragma unroll
+      for (int i0 = 0; i0 < l0; ++i0) acc[i0] = Acc<R>(yline[i0]);
       sfor<Sh::NTERMS>([&](auto tsc) {
         constexpr int ts = decltype(tsc)::value;
         constexpr int t = term_t(K, ts);
@@ -251,23 +328,38 @@ __global__ void __launch_bounds__(kCartThreads) cart_local_kernel(ApplyDev A, co
         if constexpr (T.src == m) {
           // the target is r-type along T.dir (P entries), equal elsewhere
           constexpr int tl0 = T.dir == 0 ? P : l0, tl1 = T.dir == 1 ? P : l1;
-          const int i = T.dir == 0 ? i0 : (T.dir == 1 ? i1 : i2);
-          if (i == 0 || i == P) {
-            const int a = T.dir == 0 ? i1 : i0, b = T.dir == 2 ? i1 : i2;
-            constexpr int la = T.dir == 0 ? tl1 : tl0;
-            const R v = dl[cb * DREG + 2 * (ts * LMAX + a + la * b) + (i == 0 ? 0 : 1)];
-            acc.add_value(T.sgn > 0 ? v : rneg(v));
+          const R *lsum = dl + cb * DREG + 2 * ts * LMAX;
+          const R *dyt = dyl + cb * L1 + t * S1;
+          auto sg = [&](R v) { return T.sgn > 0 ? v : rneg(v); };
+          if constexpr (T.dir == 0) {
+            const R *dline = dyt + tl0 * (i1 + tl1 * i2);
+#pragma unroll
+            for (int i0 = 0; i0 < l0; ++i0) {
+              if (i0 == 0 || i0 == P) acc[i0].add_value(sg(lsum[2 * (i1 + tl1 * i2) + (i0 == 0 ? 0 : 1)]));
+              else acc[i0].add(D1[i0 * Q1 + i0], sg(dline[i0]));
+            }
           } else {
-            constexpr int str = T.dir == 0 ? 1 : (T.dir == 1 ? tl0 : tl0 * tl1);
-            const int base = (T.dir == 0 ? 0 : i0) + tl0 * ((T.dir == 1 ? 0 : i1) + tl1 * (T.dir == 2 ? 0 : i2));
-            const R v = dyl[cb * L1 + t * S1 + base + i * str];
-            acc.add(D1[i * Q1 + i], T.sgn > 0 ? v : rneg(v));
+            const int i = T.dir == 1 ? i1 : i2;
+            if (i == 0 || i == P) {
+              const int b = T.dir == 1 ? i2 : i1;
+#pragma unroll
+              for (int i0 = 0; i0 < l0; ++i0) acc[i0].add_value(sg(lsum[2 * (i0 + tl0 * b) + (i == 0 ? 0 : 1)]));
+            } else {
+              const R *dline = dyt + tl0 * (i1 + tl1 * i2);
+              const R di = D1[i * Q1 + i];
+#pragma unroll
+              for (int i0 = 0; i0 < l0; ++i0) acc[i0].add(di, sg(dline[i0]));
+            }
           }
         }
       });
       const int c = c0 + cb;
-      if (c < ncell) Y[(size_t)c * L0 + m * S0 + r] = acc.val();
-    }
+      if (c < ncell) {
+        R *dst = Y + (size_t)c * L0 + m * S0 + l0 * (i1 + l1 * i2);
+#pragma unroll
+        for (int i0 = 0; i0 < l0; ++i0) dst[i0] = acc[i0].val();
+      }
+    });
   });
 }
 

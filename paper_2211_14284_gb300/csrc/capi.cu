@@ -1187,6 +1187,9 @@ rm_train_options rm_default_train_options(void) {
   o.val_fraction = 0.1;
   o.target_cycles = 12;
   o.off_fraction = 0.0;
+  o.rounds = 0;
+  o.round_pairs = 500;
+  o.round_epochs = 5;
   return o;
 }
 
@@ -1200,7 +1203,7 @@ int rm_corrector_train(rm_handle *h, const rm_train_options *opt, int nrhs, cons
   if (o.pairs < 2 || o.epochs < 1 || o.batch < 1 || o.batch > 256 || !(o.lr > 0.f) ||
       o.levels < 0 || o.levels > 4 || o.width < 1 || o.width > 128 || !(o.val_fraction >= 0.0) ||
       o.val_fraction > 0.5 || o.target_cycles < 1 || !(o.off_fraction >= 0.0) ||
-      o.off_fraction > 1.0)
+      o.off_fraction > 1.0 || o.rounds < 0 || o.rounds > 16 || o.round_pairs < 1 || o.round_epochs < 1)
     return fail(h, RM_ERR_ARG, "rm_corrector_train: option out of range");
   for (int d = 0; d < 3; ++d)
     if (h->n[d] % (1 << o.levels) != 0)
@@ -1213,8 +1216,9 @@ int rm_corrector_train(rm_handle *h, const rm_train_options *opt, int nrhs, cons
   try {
     const auto t0 = clock::now();
     // 1. r_0 = R_0 r at every preconditioner call of plain solves
+    const int total_pairs = o.pairs + o.rounds * o.round_pairs;
     DevBuf recb, xb;
-    CK(cudaMalloc(&recb.p, (size_t)o.pairs * nc * sizeof(double)));
+    CK(cudaMalloc(&recb.p, (size_t)total_pairs * nc * sizeof(double)));
     CK(cudaMalloc(&xb.p, h->size * sizeof(double)));
     double *rec = (double *)recb.p, *x = (double *)xb.p;
     h->rec = rec;
@@ -1247,13 +1251,16 @@ int rm_corrector_train(rm_handle *h, const rm_train_options *opt, int nrhs, cons
                       std::to_string(np) + " pairs; pass more");
     // 2. targets c* = A_0^-1 r_0; inputs and targets scaled to sqrt(nc) / norm
     DevBuf Rb, Tb, cb, db;
-    CK(cudaMalloc(&Rb.p, (size_t)np * nc * sizeof(float)));
-    CK(cudaMalloc(&Tb.p, (size_t)np * nc * sizeof(float)));
+    CK(cudaMalloc(&Rb.p, (size_t)total_pairs * nc * sizeof(float)));
+    CK(cudaMalloc(&Tb.p, (size_t)total_pairs * nc * sizeof(float)));
     CK(cudaMalloc(&cb.p, (size_t)nc * sizeof(double)));
-    CK(cudaMalloc(&db.p, (size_t)3 * np * sizeof(double)));
+    CK(cudaMalloc(&db.p, (size_t)3 * total_pairs * sizeof(double)));
     float *R = (float *)Rb.p, *T = (float *)Tb.p;
     double *cs = (double *)cb.p, *dd = (double *)db.p;
-    for (int j = 0; j < np; ++j) {
+    // targets c* = A_0^-1 r_0 of the recorded pairs j0 .. j1-1, their norms,
+    // and the network's scaled inputs and targets
+    auto make_targets = [&](int j0, int j1) {
+    for (int j = j0; j < j1; ++j) {
       const double *r0 = rec + (size_t)j * nc;
       if (h->mgAinv) {
         CK(cudaMemsetAsync(cs, 0, nc * sizeof(double), s));
@@ -1271,8 +1278,10 @@ int rm_corrector_train(rm_handle *h, const rm_train_options *opt, int nrhs, cons
       rmn::corr_normalise(nc, r0, dd + 3 * j, R + (size_t)j * nc, s);
       rmn::corr_normalise(nc, cs, dd + 3 * j + 1, T + (size_t)j * nc, s);
     }
-    std::vector<double> hd(3 * (size_t)np);
-    CK(cudaMemcpyAsync(hd.data(), dd, hd.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    };
+    make_targets(0, np);
+    std::vector<double> hd(3 * (size_t)total_pairs);
+    CK(cudaMemcpyAsync(hd.data(), dd, 3 * (size_t)np * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     const double gen_s = std::chrono::duration<double>(clock::now() - t0).count();
     // 3. split (seeded permutation), network, training
@@ -1287,7 +1296,7 @@ int rm_corrector_train(rm_handle *h, const rm_train_options *opt, int nrhs, cons
     for (int j = 0; j < np; ++j) perm[j] = j;
     for (int j = np - 1; j > 0; --j) std::swap(perm[j], perm[next() % (uint64_t)(j + 1)]);
     const int nval = std::min(np - 1, (int)(o.val_fraction * np));
-    const int ntrain = np - nval;
+    int ntrain = np - nval;
     if (h->net) {
       rmn::destroy(h->net);
       h->net = nullptr;
@@ -1301,7 +1310,7 @@ int rm_corrector_train(rm_handle *h, const rm_train_options *opt, int nrhs, cons
     CK(cudaMalloc(&Yb.p, (size_t)B * nv * sizeof(float)));
     CK(cudaMalloc(&dYb.p, (size_t)B * nv * sizeof(float)));
     CK(cudaMalloc(&mb.p, (size_t)nv));
-    CK(cudaMalloc(&ib.p, (size_t)np * sizeof(int)));
+    CK(cudaMalloc(&ib.p, (size_t)total_pairs * sizeof(int)));
     CK(cudaMalloc(&lb.p, 2 * sizeof(double)));
     float *X = (float *)Xb.p, *Tt = (float *)Ttb.p, *Y = (float *)Yb.p, *dY = (float *)dYb.p;
     uint8_t *mask = (uint8_t *)mb.p;
@@ -1316,28 +1325,73 @@ int rm_corrector_train(rm_handle *h, const rm_train_options *opt, int nrhs, cons
     }
     const auto t1 = clock::now();
     double train_loss = 0.0;
-    for (int e = 0; e < o.epochs; ++e) {
-      for (int j = ntrain - 1; j > 0; --j) std::swap(perm[j], perm[next() % (uint64_t)(j + 1)]);
-      CK(cudaMemcpyAsync(idx, perm.data(), np * sizeof(int), cudaMemcpyHostToDevice, s));
-      float lr = o.lr;
-      if (2 * e >= o.epochs) lr *= 0.5f;
-      if (4 * e >= 3 * o.epochs) lr *= 0.5f;
-      CK(cudaMemsetAsync(loss, 0, sizeof(double), s));
-      int nb = 0;
-      for (int off = 0; off < ntrain; off += B) {
-        const int bs = std::min(B, ntrain - off);
-        rmn::corr_batch(bs, nc, nv, idx + off, R, T, h->c_lat2free, h->c_logal, X, Tt, s);
-        rmn::forward(h->net, bs, X, Y);
-        rmn::mse(bs, (int)nv, Y, Tt, mask, 1.f / ((float)bs * nc), dY, loss, s);
-        rmn::backward(h->net, dY, nullptr);
-        rmn::adam(h->net, lr, 0.9f, 0.999f, 1e-8f);
-        ++nb;
+    // epochs over the training pairs perm[0 .. ntrain); lr halved at 1/2
+    // and 3/4 of the epochs of this call
+    auto train = [&](int epochs, float lr0) {
+      for (int e = 0; e < epochs; ++e) {
+        for (int j = ntrain - 1; j > 0; --j) std::swap(perm[j], perm[next() % (uint64_t)(j + 1)]);
+        CK(cudaMemcpyAsync(idx, perm.data(), perm.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+        float lr = lr0;
+        if (2 * e >= epochs) lr *= 0.5f;
+        if (4 * e >= 3 * epochs) lr *= 0.5f;
+        CK(cudaMemsetAsync(loss, 0, sizeof(double), s));
+        int nb = 0;
+        for (int off = 0; off < ntrain; off += B) {
+          const int bs = std::min(B, ntrain - off);
+          rmn::corr_batch(bs, nc, nv, idx + off, R, T, h->c_lat2free, h->c_logal, X, Tt, s);
+          rmn::forward(h->net, bs, X, Y);
+          rmn::mse(bs, (int)nv, Y, Tt, mask, 1.f / ((float)bs * nc), dY, loss, s);
+          rmn::backward(h->net, dY, nullptr);
+          rmn::adam(h->net, lr, 0.9f, 0.999f, 1e-8f);
+          ++nb;
+        }
+        double hl = 0.0;
+        CK(cudaMemcpyAsync(&hl, loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        train_loss = hl / nb;
       }
-      double hl = 0.0;
-      CK(cudaMemcpyAsync(&hl, loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+    };
+    train(o.epochs, o.lr);
+    // on-policy rounds: residuals of solves that use the current network
+    // (they drift away from those of plain solves), appended to the
+    // training pairs; the held-out pairs stay the first recording's
+    for (int rd = 0; rd < o.rounds; ++rd) {
+      const int j0 = h->rec_n;
+      h->rec = rec;
+      h->rec_cap = j0 + o.round_pairs;
+      h->corr_mode = RM_CORRECTOR_LEARNED;
+      const int saved_je = h->judge_every;
+      h->judge_every = 0;
+      for (int i = 0; h->rec_n < h->rec_cap; ++i) {
+        CK(cudaMemsetAsync(x, 0, h->size * sizeof(double), s));
+        rm_info inf;
+        const int st = rm_solve(h, rhs + (size_t)(i % nrhs) * h->size, x, &inf);
+        ++solves;
+        if (st != RM_OK && st != RM_ERR_NOT_CONVERGED) {
+          h->judge_every = saved_je;
+          throw std::runtime_error(h->err);
+        }
+        if (i > 4 * nrhs) break;  // solves that record nothing (converged at once)
+      }
+      h->judge_every = saved_je;
+      h->rec = nullptr;
+      h->rec_cap = 0;
+      h->corr_mode = saved_mode;
+      const int j1 = h->rec_n;
+      if (j1 == j0) break;
+      make_targets(j0, j1);
+      CK(cudaMemcpyAsync(hd.data() + 3 * (size_t)j0, dd + 3 * (size_t)j0, 3 * (size_t)(j1 - j0) * sizeof(double),
+                         cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
-      train_loss = hl / nb;
+      // new pairs join the training part of perm, before the held-out ones
+      std::vector<int> np2(perm.begin(), perm.begin() + ntrain);
+      for (int j = j0; j < j1; ++j) np2.push_back(j);
+      np2.insert(np2.end(), perm.begin() + ntrain, perm.end());
+      perm.swap(np2);
+      ntrain += j1 - j0;
+      train(o.round_epochs, 0.5f * o.lr);
     }
+    const int np_all = (int)perm.size();
     const double train_s = std::chrono::duration<double>(clock::now() - t1).count();
     // 4. held-out pairs: loss and eta of the optimally scaled correction
     double val_loss = 0.0, val_eta = 0.0;
@@ -1347,8 +1401,8 @@ int rm_corrector_train(rm_handle *h, const rm_train_options *opt, int nrhs, cons
       double *vd = (double *)vb.p;
       CK(cudaMemsetAsync(loss, 0, sizeof(double), s));
       int nb = 0;
-      for (int off = ntrain; off < np; off += B) {
-        const int bs = std::min(B, np - off);
+      for (int off = ntrain; off < np_all; off += B) {
+        const int bs = std::min(B, np_all - off);
         rmn::corr_batch(bs, nc, nv, idx + off, R, T, h->c_lat2free, h->c_logal, X, Tt, s);
         rmn::forward(h->net, bs, X, Y);
         rmn::mse(bs, (int)nv, Y, Tt, mask, 1.f / ((float)bs * nc), dY, loss, s);
@@ -1375,7 +1429,7 @@ int rm_corrector_train(rm_handle *h, const rm_train_options *opt, int nrhs, cons
       }
     }
     if (info) {
-      info->pairs = np;
+      info->pairs = np_all;
       info->solves = solves;
       info->params = rmn::num_params(h->net);
       info->gen_s = gen_s;

@@ -75,7 +75,8 @@ class RmTrainOptions(ctypes.Structure):
     _fields_ = [("pairs", ctypes.c_int), ("epochs", ctypes.c_int), ("batch", ctypes.c_int),
                 ("lr", ctypes.c_float), ("levels", ctypes.c_int), ("width", ctypes.c_int),
                 ("seed", ctypes.c_ulonglong), ("val_fraction", ctypes.c_double),
-                ("target_cycles", ctypes.c_int), ("off_fraction", ctypes.c_double)]
+                ("target_cycles", ctypes.c_int), ("off_fraction", ctypes.c_double),
+                ("rounds", ctypes.c_int), ("round_pairs", ctypes.c_int), ("round_epochs", ctypes.c_int)]
 
 
 class RmTrainInfo(ctypes.Structure):
