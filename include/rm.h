@@ -57,7 +57,8 @@ typedef enum {
   RM_ERR_OOM = 3,           /* device or host allocation failed */
   RM_ERR_BREAKDOWN = 4,     /* ICC pivot <= 0, or CG p^T A p <= 0 */
   RM_ERR_NOT_CONVERGED = 5, /* max_it reached */
-  RM_ERR_NAN = 6            /* NaN/Inf in a residual */
+  RM_ERR_NAN = 6,           /* NaN/Inf in a residual */
+  RM_ERR_TIMEOUT = 7        /* a bounded device wait gave up (reported by the next rm_solve) */
 } rm_status;
 
 typedef enum { RM_HGRAD = 0, RM_HCURL = 1, RM_HDIV = 2 } rm_space;

@@ -255,8 +255,30 @@ DevPatch upload_family(rm_handle *h, const PatchFamily &F) {
     D.bptr = h->upload(F.bptr);
     D.boff = h->upload(F.boff);
     D.val = h->upload_vals(F.device_values());
+    D.vstride = D.nnz;
   } else {
-    D.val = h->upload_vals(F.device_values());
+    // factor values per patch padded to 16 bytes (the warp kernel's bulk
+    // copies); the template as 16-bit arrays when its sizes allow
+    const int per16 = h->vt == 0 ? 2 : 4;
+    D.vstride = (D.nnz + per16 - 1) / per16 * per16;
+    const std::vector<double> v = F.device_values();
+    std::vector<double> vp((size_t)F.npatch * D.vstride, 0.0);
+    for (int pi = 0; pi < F.npatch; ++pi)
+      std::copy(v.begin() + (size_t)pi * D.nnz, v.begin() + (size_t)(pi + 1) * D.nnz,
+                vp.begin() + (size_t)pi * D.vstride);
+    D.val = h->upload_vals(vp);
+    if (F.nslots + 1 < 65536 && D.nnz < 65536) {
+      const std::vector<int> *parts[9] = {&F.rowptr, &F.col, &F.flev, &F.frows, &F.blev,
+                                          &F.brows, &F.tptr, &F.trow, &F.tpos};
+      std::vector<unsigned short> blob;
+      for (int a = 0; a < 9; ++a) {
+        D.toff[a] = (int)blob.size();
+        for (int v16 : *parts[a]) blob.push_back((unsigned short)v16);
+      }
+      while ((blob.size() * sizeof(unsigned short)) % 16) blob.push_back(0);
+      D.tmpl = h->upload(blob);
+      D.tmpl_bytes = (int)(blob.size() * sizeof(unsigned short));
+    }
   }
   h->stat_patches += F.npatch;
   h->stat_slots += (long long)F.npatch * F.nslots;
@@ -1108,6 +1130,11 @@ int rm_solve(rm_handle *h, const double *b, double *x, rm_info *info) {
     CK(cudaEventRecord(h->ev1, s));
     CK(cudaEventSynchronize(h->ev1));
     CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    {
+      cudaError_t te = cudaSuccess;
+      if (patch_timeouts(&te)) status = RM_ERR_TIMEOUT;  // a patch kernel's bounded wait gave up
+      CK(te);
+    }
     for (size_t j = 0; j < kinds.size(); ++j) {
       float t = 0.f;
       CK(cudaEventElapsedTime(&t, h->evpool[2 * j], h->evpool[2 * j + 1]));
@@ -1156,6 +1183,7 @@ int rm_solve(rm_handle *h, const double *b, double *x, rm_info *info) {
   if (status != RM_OK) {
     const char *why = status == RM_ERR_NOT_CONVERGED ? "max_it reached"
                       : status == RM_ERR_NAN         ? "NaN/Inf residual"
+                      : status == RM_ERR_TIMEOUT     ? "a device wait timed out in the relaxation"
                                                      : "CG breakdown (p^T A p <= 0 or r^T B r <= 0)";
     fail(h, status, std::string("rm_solve: ") + why);
   }

@@ -258,6 +258,16 @@ struct DevPatch {
   const int *pos_slot = nullptr, *pos_blk = nullptr, *bptr = nullptr, *boff = nullptr;
   // batched solves: the problem of every patch and the convergence flags
   const int *pprob = nullptr, *done = nullptr;
+  // elements between consecutive patches' factor values (>= nnz; padded to
+  // 16 bytes when the warp kernel stages them with bulk copies)
+  int vstride = 0;
+  // warp-per-patch substitution (patch_warp_kernel): the template as one
+  // 16-byte aligned blob of 16-bit arrays -- rowptr[ns+1], col[nnz],
+  // flev[nflev+1], frows[ns], blev[nblev+1], brows[ns], tptr[ns+1],
+  // trow[nstrict], tpos[nstrict] at element offsets toff[0..8] -- or null
+  const unsigned short *tmpl = nullptr;
+  int tmpl_bytes = 0;
+  int toff[9] = {};
 };
 
 // launchers (kernels.cu); launch_count() = kernels launched so far in this process
@@ -275,6 +285,11 @@ cudaError_t launch_apply_cart(const ApplyDev &A, const double *x, double *y, cud
 cudaError_t launch_spmv(const DevCsr &M, const double *x, double *y, const double *u, int mode,
                         double a, cudaStream_t s);
 cudaError_t launch_patches(const DevPatch &F, const double *r, double *z, cudaStream_t s);
+// the warp-per-patch kernel's bounded waits: 1 if any gave up since the last
+// call (the flag is cleared), 0 otherwise; a CUDA error code on failure
+int patch_timeouts(cudaError_t *err);
+// patches per CTA of the warp kernel for a family (0: it does not fit)
+int patch_warps_per_block(const DevPatch &F);
 cudaError_t launch_gemv(int n, const void *A, int vt, const double *x, double *y, cudaStream_t s);
 // coarse multigrid: x_out = x_in + w (b - A x_in) (A FP64, rows compact); x = w b
 cudaError_t launch_jacobi(const DevCsr &A, const double *b, const double *xin, const double *w,

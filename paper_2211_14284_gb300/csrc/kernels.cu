@@ -387,7 +387,7 @@ __global__ void patch_kernel(DevPatch F, const double *__restrict__ r, double *_
   VT *xs = reinterpret_cast<VT *>(smem_raw);
   const int ns = F.nslots;
   const int *sm = F.slotmap + (size_t)blockIdx.x * ns;
-  const VT *Lg = reinterpret_cast<const VT *>(F.val) + (size_t)blockIdx.x * F.nnz;
+  const VT *Lg = reinterpret_cast<const VT *>(F.val) + (size_t)blockIdx.x * (F.vstride ? F.vstride : F.nnz);
   // the factor follows x (ns values of VT, padded to whole doubles)
   VT *Ls = reinterpret_cast<VT *>(smem_raw + (ns * sizeof(VT) + sizeof(double) - 1) / sizeof(double));
   gather_slots(sm, ns, r, xs);
@@ -429,6 +429,132 @@ __global__ void patch_kernel(DevPatch F, const double *__restrict__ r, double *_
     __syncthreads();
   }
   for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+    const int g = sm[s];
+    if (g >= 0) atomicAdd(&z[g], (double)xs[s]);
+  }
+}
+
+// ---- warp-per-patch substitution --------------------------------------------
+// WPB patches per CTA, one warp each.  The family's template (16-bit index
+// arrays, shared by every patch) and the CTA's factors are staged into
+// shared memory by bulk copies (cp.async.bulk, the TMA unit) completing on
+// one mbarrier, while the warps gather their patch residuals; each warp then
+// runs its patch's level-scheduled forward and backward substitutions with
+// __syncwarp between levels instead of CTA barriers.  Every wait on the
+// mbarrier is bounded: on timeout the CTA records it in g_patch_timeout,
+// waits once more (bounded) for its copies and returns without touching z.
+__device__ int g_patch_timeout = 0;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// true once phase `parity` of the mbarrier completed; false after ~1 s
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity) {
+  const long long t0 = clock64();
+  for (long long it = 0; it < (1LL << 26); ++it) {
+    unsigned ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > 2000000000LL) break;
+  }
+  return false;
+}
+
+constexpr int kPatchWarpMaxWPB = 8;
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+// shared memory of the warp kernel: mbarrier, template, then per warp the
+// factor and the slot values
+template <typename VT>
+__host__ __device__ inline size_t patch_warp_smem(const DevPatch &F, int wpb) {
+  return 16 + align16((size_t)F.tmpl_bytes) +
+         (size_t)wpb * (align16((size_t)F.vstride * sizeof(VT)) + align16((size_t)F.nslots * sizeof(VT)));
+}
+
+template <typename VT, int WPB>
+__global__ void __launch_bounds__(WPB * 32) patch_warp_kernel(DevPatch F, const double *__restrict__ r,
+                                                              double *__restrict__ z) {
+  extern __shared__ __align__(16) unsigned char psm[];
+  unsigned long long *bar = reinterpret_cast<unsigned long long *>(psm);
+  const unsigned short *T = reinterpret_cast<const unsigned short *>(psm + 16);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p0 = blockIdx.x * WPB;
+  const int nblk = min(WPB, F.npatch - p0);
+  const size_t fbytes = align16((size_t)F.vstride * sizeof(VT)), xbytes = align16((size_t)F.nslots * sizeof(VT));
+  unsigned char *wbase = psm + 16 + align16((size_t)F.tmpl_bytes) + (size_t)warp * (fbytes + xbytes);
+  const VT *L = reinterpret_cast<const VT *>(wbase);
+  VT *xs = reinterpret_cast<VT *>(wbase + fbytes);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(bar, (unsigned)(F.tmpl_bytes + (size_t)nblk * F.vstride * sizeof(VT)));
+    bulk_g2s(psm + 16, F.tmpl, (unsigned)F.tmpl_bytes, bar);
+    for (int w = 0; w < nblk; ++w)
+      bulk_g2s(psm + 16 + align16((size_t)F.tmpl_bytes) + (size_t)w * (fbytes + xbytes),
+               reinterpret_cast<const VT *>(F.val) + (size_t)(p0 + w) * F.vstride,
+               (unsigned)((size_t)F.vstride * sizeof(VT)), bar);
+  }
+  const int patch = p0 + warp;
+  const bool live = warp < nblk && !(F.pprob && F.done[F.pprob[patch]]);
+  const int ns = F.nslots;
+  const int *sm = F.slotmap + (size_t)(live ? patch : 0) * ns;
+  if (live)
+    for (int s = lane; s < ns; s += 32) {
+      const int g = sm[s];
+      xs[s] = g >= 0 ? (VT)r[g] : (VT)0;
+    }
+  if (!mbar_wait_bounded(bar, 0)) {
+    if (threadIdx.x == 0) atomicExch(&g_patch_timeout, 1);
+    mbar_wait_bounded(bar, 0);  // the copies in flight still target this CTA's memory
+    return;
+  }
+  __syncwarp();
+  if (!live) return;
+  const unsigned short *rowptr = T + F.toff[0], *col = T + F.toff[1], *flev = T + F.toff[2],
+                       *frows = T + F.toff[3], *blev = T + F.toff[4], *brows = T + F.toff[5],
+                       *tptr = T + F.toff[6], *trow = T + F.toff[7], *tpos = T + F.toff[8];
+  for (int lv = 0; lv < F.nflev; ++lv) {
+    for (int t = flev[lv] + lane; t < flev[lv + 1]; t += 32) {
+      const int i = frows[t];
+      const int b = rowptr[i], d = rowptr[i + 1] - 1;
+      VT v = xs[i];
+#pragma unroll 4
+      for (int e = b; e < d; ++e) v = fma(-L[e], xs[col[e]], v);
+      xs[i] = v * L[d];
+    }
+    __syncwarp();
+  }
+  for (int lv = 0; lv < F.nblev; ++lv) {
+    for (int t = blev[lv] + lane; t < blev[lv + 1]; t += 32) {
+      const int j = brows[t];
+      VT v = xs[j];
+      const int e1 = tptr[j + 1];
+#pragma unroll 4
+      for (int e = tptr[j]; e < e1; ++e) v = fma(-L[tpos[e]], xs[trow[e]], v);
+      xs[j] = v * L[rowptr[j + 1] - 1];
+    }
+    __syncwarp();
+  }
+  for (int s = lane; s < ns; s += 32) {
     const int g = sm[s];
     if (g >= 0) atomicAdd(&z[g], (double)xs[s]);
   }
@@ -765,7 +891,29 @@ cudaError_t launch_spmv(const DevCsr &M, const double *x, double *y, const doubl
 }
 
 template <typename VT>
+static int warps_per_block(const DevPatch &F) {
+  if (!F.tmpl || F.inverse) return 0;
+  for (int w = kPatchWarpMaxWPB; w >= 1; w /= 2)
+    if (patch_warp_smem<VT>(F, w) <= 200 * 1024) return w;
+  return 0;
+}
+
+template <typename VT>
 static void patch_dispatch(const DevPatch &F, const double *r, double *z, cudaStream_t s) {
+  const int wpb = warps_per_block<VT>(F);
+  if (wpb > 0) {
+    const size_t smem = patch_warp_smem<VT>(F, wpb);
+    const int grid = (F.npatch + wpb - 1) / wpb;
+    auto go = [&](auto kern) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      kern<<<grid, wpb * 32, smem, s>>>(F, r, z);
+    };
+    if (wpb == 8) go(patch_warp_kernel<VT, 8>);
+    else if (wpb == 4) go(patch_warp_kernel<VT, 4>);
+    else if (wpb == 2) go(patch_warp_kernel<VT, 2>);
+    else go(patch_warp_kernel<VT, 1>);
+    return;
+  }
   if (F.inverse) {
     const size_t smem = 2 * (size_t)F.nslots * sizeof(VT);
     cudaFuncSetAttribute(patch_inv_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -782,6 +930,19 @@ static void patch_dispatch(const DevPatch &F, const double *r, double *z, cudaSt
     cudaFuncSetAttribute(patch_kernel<VT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)base);
     patch_kernel<VT, false><<<F.npatch, 128, base, s>>>(F, r, z);
   }
+}
+
+int patch_warps_per_block(const DevPatch &F) {
+  return F.vt == 0 ? warps_per_block<double>(F) : warps_per_block<float>(F);
+}
+
+int patch_timeouts(cudaError_t *err) {
+  int v = 0;
+  const int zero = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, g_patch_timeout, sizeof(int));
+  if (e == cudaSuccess && v) e = cudaMemcpyToSymbol(g_patch_timeout, &zero, sizeof(int));
+  if (err) *err = e;
+  return v;
 }
 
 cudaError_t launch_patches(const DevPatch &F, const double *r, double *z, cudaStream_t s) {

@@ -27,7 +27,7 @@ RM_BC_DIRICHLET, RM_BC_NONE = 0, 1
 RM_SMOOTH_STAR, RM_SMOOTH_HIPTMAIR = 0, 1
 RM_ADDITIVE, RM_HYBRID = 0, 1
 STATUS = {0: "RM_OK", 1: "RM_ERR_ARG", 2: "RM_ERR_CUDA", 3: "RM_ERR_OOM",
-          4: "RM_ERR_BREAKDOWN", 5: "RM_ERR_NOT_CONVERGED", 6: "RM_ERR_NAN"}
+          4: "RM_ERR_BREAKDOWN", 5: "RM_ERR_NOT_CONVERGED", 6: "RM_ERR_NAN", 7: "RM_ERR_TIMEOUT"}
 
 EXPORTED = ["rm_default_options", "rm_setup", "rm_ndofs", "rm_layout", "rm_history", "rm_apply",
             "rm_precondition", "rm_solve", "rm_stats", "rm_destroy", "rm_last_error",
