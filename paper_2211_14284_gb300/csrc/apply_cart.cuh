@@ -9,9 +9,9 @@
 //
 // Two launches, no atomics, bitwise reproducible:
 //  * cart_local_kernel<K, P, R>: the cell products y_K = A_K x_K, one CTA per
-//    CPB cells, every shape and loop bound a compile-time constant of
-//    (K, P); written unassembled to the scratch Y[cell][local entry] in the
-//    number type R;
+//    CPB cells with one thread per line of a cell (cart_cpb, cart_threads),
+//    every shape and loop bound a compile-time constant of (K, P); written
+//    unassembled to the scratch Y[cell][local entry] in the number type R;
 //  * cart_assemble_kernel<K, P, R>: every lattice entry sums its (at most 8)
 //    cell contributions from Y in a fixed order, in R, and converts once to
 //    FP64; Dirichlet entries get 0.
@@ -32,7 +32,6 @@ cudaError_t launch_cart_part(const ApplyDev &A, const double *x, double *y, cuda
 
 namespace {
 
-constexpr int kCartThreads = 256;
 constexpr int kCartMaxP = 15;
 
 template <int K, int P>
@@ -43,28 +42,19 @@ struct CartShape {
   static constexpr int NTERMS = K == 1 ? 6 : 3;                 // signed D-hat terms
   static constexpr int LMAX = (P + 1) * (P + 1);                // lines per term (bound)
   static constexpr int LS = NTERMS * LMAX * 2;                  // interface line sums
-  static constexpr int DREG = L1 > LS ? L1 : LS;                // d, later the line sums
-  static constexpr int CPB0 = kCartThreads / L1;
-  static constexpr int CPB = CPB0 < 1 ? 1 : (CPB0 > 32 ? 32 : CPB0);  // cells per CTA
+  // cells per CTA and threads: one thread per line of the largest phase
+  static constexpr int CPB = cart_cpb(P), NT = cart_threads(P);
+  static_assert(CPB * LMAX <= NT, "every thread owns at most one line of a component");
   // shared memory in units of R (8 bytes): D-hat, per cell 8 coefficients,
-  // x, y, d / line sums, dy
-  static constexpr int SMEM = P * (P + 1) + CPB * (8 + 2 * L0 + DREG + L1);
+  // x, d (later dy), line sums
+  static constexpr int SMEM = P * (P + 1) + CPB * (8 + L0 + L1 + LS);
+  static_assert(SMEM == cart_local_smem_doubles(K, P, L0, L1), "host and device agree on the layout");
 };
 
 // (t, s) of the ts-th signed D-hat term: two per target component for the
 // curl, one per target for the gradient, three into the one divergence target
 __host__ __device__ constexpr int term_t(int k, int ts) { return k == 1 ? ts >> 1 : (k == 0 ? ts : 0); }
 __host__ __device__ constexpr int term_s(int k, int ts) { return k == 1 ? ts & 1 : (k == 0 ? 0 : ts); }
-
-// Box metric of kk-forms, component m (J = diag(h/2)).
-__device__ __forceinline__ double cart_metric(int kk, int m, double h0, double h1, double h2) {
-  const double det = 0.125 * h0 * h1 * h2;
-  const double hm = m == 0 ? h0 : (m == 1 ? h1 : h2);
-  if (kk == 0) return det;
-  if (kk == 3) return 1.0 / det;
-  if (kk == 1) return det * 4.0 / (hm * hm);
-  return 0.25 * hm * hm / det;
-}
 
 // (x)_d F_d at local index (i0, i1, i2) of one component block `in` with
 // local sizes (L0, L1, .) and s-type flags (T0, T1, T2): an s-type index on
@@ -89,12 +79,14 @@ __device__ __forceinline__ R kron_mass(const R *in, int i0, int i1, int i2, R a,
 
 
 // Lines along direction 0 of a component block with local sizes (., L1, L2),
-// in the CTA's CPB cells: f(cb, i1, i2) once per line, lines spread over
-// the threads.
-template <int CPB, int LL1, int LL2, typename F>
-__device__ __forceinline__ void for_lines(F &&f, int = 0) {
+// in the CTA's CPB cells: f(cb, i1, i2) for the calling thread's line, if it
+// owns one (CPB L1 L2 <= NT: at most one line per thread).
+template <int CPB, int NT, int LL1, int LL2, typename F>
+__device__ __forceinline__ void for_lines(F &&f) {
   constexpr int NL = LL1 * LL2;
-  for (int u = threadIdx.x; u < CPB * NL; u += kCartThreads) {
+  static_assert(CPB * NL <= NT, "one line per thread");
+  const int u = threadIdx.x;
+  if (u < CPB * NL) {
     const int cb = u / NL, r = u - cb * NL;
     f(cb, r % LL1, r / LL1);
   }
@@ -139,37 +131,38 @@ __device__ __forceinline__ void line_mass(const R *in, int i1, int i2, R a, R b,
 }
 
 template <int K, int P, typename R>
-__global__ void __launch_bounds__(kCartThreads) cart_local_kernel(ApplyDev A, const double *__restrict__ x,
-                                                                  R *__restrict__ Y) {
+__global__ void __launch_bounds__(cart_threads(P)) cart_local_kernel(ApplyDev A, const double *__restrict__ x,
+                                                                    R *__restrict__ Y) {
   using Sh = CartShape<K, P>;
   constexpr int NC0 = Sh::NC0, NC1 = Sh::NC1, S0 = Sh::S0, S1 = Sh::S1, L0 = Sh::L0, L1 = Sh::L1;
-  constexpr int CPB = Sh::CPB, DREG = Sh::DREG, LMAX = Sh::LMAX, NT = kCartThreads;
+  constexpr int CPB = Sh::CPB, LMAX = Sh::LMAX, LS = Sh::LS, NT = Sh::NT;
   constexpr int Q1 = P + 1;
   extern __shared__ double smd[];
   R *sm = reinterpret_cast<R *>(smd);
   R *D1 = sm;                    // D-hat, P x (P + 1)
   R *coef = D1 + P * Q1;         // per cell: beta c_m (NC0), then alpha c'_t (NC1)
   R *xl = coef + CPB * 8;        // CPB x L0
-  R *yl = xl + CPB * L0;         // CPB x L0
-  R *dl = yl + CPB * L0;         // CPB x DREG: d = D-hat x, then the line sums
-  R *dyl = dl + CPB * DREG;      // CPB x L1
+  R *dl = xl + CPB * L0;         // CPB x L1: d = D-hat x, then dy in place
+  R *ls = dl + CPB * L1;         // CPB x LS: interface line sums
   __shared__ long long cbase[32][3];  // lattice index of local (0,0,0) per component
   __shared__ int cdir[32];            // Dirichlet faces: bit 2d low side, 2d+1 high side
   const int tid = threadIdx.x;
   const int ncell = A.n[0] * A.n[1] * A.n[2];
   const int c0 = blockIdx.x * CPB;
+  // every FP64 value enters through the integer split (to_r): the FP64 pipe
+  // runs at 1/64 of the FP32 rate on GB300
   {
     const double *g = A.tabs + A.q * Q1 + A.q * P;
-    for (int i = tid; i < P * Q1; i += NT) D1[i] = rfrom<R>(g[i]);
+    for (int i = tid; i < P * Q1; i += NT) D1[i] = to_r<R>(g[i]);
+  }
+  for (int i = tid; i < CPB * 8; i += NT) {
+    const int c = c0 + i / 8;
+    coef[i] = c < ncell ? to_r<R>(A.ccoef[(size_t)c * 8 + (i & 7)]) : rzero(R());
   }
   if (tid < CPB) {
     const int c = c0 + tid;
     if (c < ncell) {
       const int e0 = c % A.n[0], e1 = (c / A.n[0]) % A.n[1], e2 = c / (A.n[0] * A.n[1]);
-      const double h0 = A.h[3 * c], h1 = A.h[3 * c + 1], h2 = A.h[3 * c + 2];
-      const double al = A.alpha[c], be = A.beta[c];
-      for (int m = 0; m < NC0; ++m) coef[tid * 8 + m] = rfrom<R>(be * cart_metric(K, m, h0, h1, h2));
-      for (int t = 0; t < NC1; ++t) coef[tid * 8 + 3 + t] = rfrom<R>(al * cart_metric(K + 1, t, h0, h1, h2));
       for (int m = 0; m < NC0; ++m)
         cbase[tid][m] = A.off[m] + (long long)e0 * P +
                         (long long)A.N[m][0] * ((long long)e1 * P + (long long)A.N[m][1] * e2 * P);
@@ -184,13 +177,12 @@ __global__ void __launch_bounds__(kCartThreads) cart_local_kernel(ApplyDev A, co
       }
       cdir[tid] = f;
     } else {
-      for (int m = 0; m < 8; ++m) coef[tid * 8 + m] = rzero(R());
       for (int m = 0; m < NC0; ++m) cbase[tid][m] = -1;
       cdir[tid] = 0;
     }
   }
   __syncthreads();
-  const R ba = rfrom<R>(A.bh_a), bb = rfrom<R>(A.bh_b);
+  const R ba = to_r<R>(A.bh_a), bb = to_r<R>(A.bh_b);
   // Every phase runs over lines along direction 0: a thread takes one line
   // (cell cb, indices i1, i2) and walks its l0 entries with a compile-time
   // unrolled loop, so index decoding happens once per line and the
@@ -200,7 +192,7 @@ __global__ void __launch_bounds__(kCartThreads) cart_local_kernel(ApplyDev A, co
     constexpr int m = decltype(mc)::value;
     constexpr bool t0 = styp(K, m, 0), t1 = styp(K, m, 1), t2 = styp(K, m, 2);
     constexpr int l0 = sld(K, P, m, 0), l1 = sld(K, P, m, 1), l2 = sld(K, P, m, 2);
-    for_lines<CPB, l1, l2>([&](int cb, int i1, int i2) {
+    for_lines<CPB, NT, l1, l2>([&](int cb, int i1, int i2) {
       const int f = cdir[cb];
       const long long b0 = cbase[cb][m];
       const bool dl_ = (t1 && (((f & 4) && i1 == 0) || ((f & 8) && i1 == P))) ||
@@ -215,24 +207,11 @@ __global__ void __launch_bounds__(kCartThreads) cart_local_kernel(ApplyDev A, co
     });
   });
   __syncthreads();
-  // ---- y = beta M^K x;  d = D-hat x ----
-  sfor<NC0>([&](auto mc) {
-    constexpr int m = decltype(mc)::value;
-    constexpr bool t0 = styp(K, m, 0), t1 = styp(K, m, 1), t2 = styp(K, m, 2);
-    constexpr int l0 = sld(K, P, m, 0), l1 = sld(K, P, m, 1), l2 = sld(K, P, m, 2);
-    for_lines<CPB, l1, l2>([&](int cb, int i1, int i2) {
-      R u[l0];
-      line_mass<t0, t1, t2, l0, l1, P>(xl + cb * L0 + m * S0, i1, i2, ba, bb, u);
-      R *dst = yl + cb * L0 + m * S0 + l0 * (i1 + l1 * i2);
-      const R cm = coef[cb * 8 + m];
-#pragma unroll
-      for (int i0 = 0; i0 < l0; ++i0) dst[i0] = rmul(cm, u[i0]);
-    });
-  });
+  // ---- d = D-hat x ----
   sfor<NC1>([&](auto tc) {
     constexpr int t = decltype(tc)::value;
     constexpr int l0 = sld(K + 1, P, t, 0), l1 = sld(K + 1, P, t, 1), l2 = sld(K + 1, P, t, 2);
-    for_lines<CPB, l1, l2>([&](int cb, int j1, int j2) {
+    for_lines<CPB, NT, l1, l2>([&](int cb, int j1, int j2) {
       Acc<R> acc[l0];
       sfor<dterm_count(K, t)>([&](auto sc) {
         constexpr DTerm T = dterm(K, t, decltype(sc)::value);
@@ -264,21 +243,26 @@ __global__ void __launch_bounds__(kCartThreads) cart_local_kernel(ApplyDev A, co
           }
         }
       });
-      R *dst = dl + cb * DREG + t * S1 + l0 * (j1 + l1 * j2);
+      R *dst = dl + cb * L1 + t * S1 + l0 * (j1 + l1 * j2);
 #pragma unroll
       for (int i0 = 0; i0 < l0; ++i0) dst[i0] = acc[i0].val();
     });
   });
   __syncthreads();
-  // ---- dy = alpha M^{K+1} d ----
+  // ---- dy = alpha M^{K+1} d, in place: per component, every thread reads
+  // its line's mass into registers, then (after a barrier) overwrites the
+  // line; the next component's block is disjoint ----
   sfor<NC1>([&](auto tc) {
     constexpr int t = decltype(tc)::value;
     constexpr bool t0 = styp(K + 1, t, 0), t1 = styp(K + 1, t, 1), t2 = styp(K + 1, t, 2);
     constexpr int l0 = sld(K + 1, P, t, 0), l1 = sld(K + 1, P, t, 1), l2 = sld(K + 1, P, t, 2);
-    for_lines<CPB, l1, l2>([&](int cb, int j1, int j2) {
-      R u[l0];
-      line_mass<t0, t1, t2, l0, l1, P>(dl + cb * DREG + t * S1, j1, j2, ba, bb, u);
-      R *dst = dyl + cb * L1 + t * S1 + l0 * (j1 + l1 * j2);
+    R u[l0];
+    for_lines<CPB, NT, l1, l2>([&](int cb, int j1, int j2) {
+      line_mass<t0, t1, t2, l0, l1, P>(dl + cb * L1 + t * S1, j1, j2, ba, bb, u);
+    });
+    __syncthreads();
+    for_lines<CPB, NT, l1, l2>([&](int cb, int j1, int j2) {
+      R *dst = dl + cb * L1 + t * S1 + l0 * (j1 + l1 * j2);
       const R cm = coef[cb * 8 + 3 + t];
 #pragma unroll
       for (int i0 = 0; i0 < l0; ++i0) dst[i0] = rmul(cm, u[i0]);
@@ -299,7 +283,7 @@ __global__ void __launch_bounds__(kCartThreads) cart_local_kernel(ApplyDev A, co
       const int cb = u / (la * lb), line = u - cb * (la * lb);
       const int a = line % la, b = line / la;
       const int c0i = T.dir == 0 ? 0 : a, c1i = T.dir == 0 ? a : (T.dir == 1 ? 0 : b), c2i = T.dir == 2 ? 0 : b;
-      const R *in = dyl + cb * L1 + t * S1 + c0i + l0 * (c1i + l1 * c2i);
+      const R *in = dl + cb * L1 + t * S1 + c0i + l0 * (c1i + l1 * c2i);
       Acc<R> v0, vp;
 #pragma unroll
       for (int j = 0; j < P; ++j) {
@@ -307,20 +291,25 @@ __global__ void __launch_bounds__(kCartThreads) cart_local_kernel(ApplyDev A, co
         v0.add(D1[j * Q1], dj);
         vp.add(D1[j * Q1 + P], dj);
       }
-      dl[cb * DREG + 2 * (ts * LMAX + line)] = v0.val();
-      dl[cb * DREG + 2 * (ts * LMAX + line) + 1] = vp.val();
+      ls[cb * LS + 2 * (ts * LMAX + line)] = v0.val();
+      ls[cb * LS + 2 * (ts * LMAX + line) + 1] = vp.val();
     }
   });
   __syncthreads();
-  // ---- y += D-hat^T dy; the cell's unassembled product to Y ----
+  // ---- y = beta M^K x + D-hat^T dy; the cell's unassembled product to Y ----
   sfor<NC0>([&](auto mc) {
     constexpr int m = decltype(mc)::value;
+    constexpr bool t0 = styp(K, m, 0), t1 = styp(K, m, 1), t2 = styp(K, m, 2);
     constexpr int l0 = sld(K, P, m, 0), l1 = sld(K, P, m, 1), l2 = sld(K, P, m, 2);
-    for_lines<CPB, l1, l2>([&](int cb, int i1, int i2) {
-      const R *yline = yl + cb * L0 + m * S0 + l0 * (i1 + l1 * i2);
+    for_lines<CPB, NT, l1, l2>([&](int cb, int i1, int i2) {
       Acc<R> acc[l0];
+      {
+        R u[l0];
+        line_mass<t0, t1, t2, l0, l1, P>(xl + cb * L0 + m * S0, i1, i2, ba, bb, u);
+        const R cm = coef[cb * 8 + m];
 #pragma unroll
-      for (int i0 = 0; i0 < l0; ++i0) acc[i0] = Acc<R>(yline[i0]);
+        for (int i0 = 0; i0 < l0; ++i0) acc[i0] = Acc<R>(rmul(cm, u[i0]));
+      }
       sfor<Sh::NTERMS>([&](auto tsc) {
         constexpr int ts = decltype(tsc)::value;
         constexpr int t = term_t(K, ts);
@@ -328,8 +317,8 @@ __global__ void __launch_bounds__(kCartThreads) cart_local_kernel(ApplyDev A, co
         if constexpr (T.src == m) {
           // the target is r-type along T.dir (P entries), equal elsewhere
           constexpr int tl0 = T.dir == 0 ? P : l0, tl1 = T.dir == 1 ? P : l1;
-          const R *lsum = dl + cb * DREG + 2 * ts * LMAX;
-          const R *dyt = dyl + cb * L1 + t * S1;
+          const R *lsum = ls + cb * LS + 2 * ts * LMAX;
+          const R *dyt = dl + cb * L1 + t * S1;
           auto sg = [&](R v) { return T.sgn > 0 ? v : rneg(v); };
           if constexpr (T.dir == 0) {
             const R *dline = dyt + tl0 * (i1 + tl1 * i2);
@@ -422,7 +411,7 @@ cudaError_t launch_cart_kpr(const ApplyDev &A, const double *x, double *y, cudaS
       cudaFuncSetAttribute(cart_local_kernel<K, P, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   const int ncell = A.n[0] * A.n[1] * A.n[2];
-  cart_local_kernel<K, P, R><<<(ncell + Sh::CPB - 1) / Sh::CPB, kCartThreads, smem, s>>>(A, x, reinterpret_cast<R *>(A.Y));
+  cart_local_kernel<K, P, R><<<(ncell + Sh::CPB - 1) / Sh::CPB, Sh::NT, smem, s>>>(A, x, reinterpret_cast<R *>(A.Y));
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   int rows = 0, n0max = 0;

@@ -278,6 +278,7 @@ DevPatch upload_family(rm_handle *h, const PatchFamily &F) {
       while ((blob.size() * sizeof(unsigned short)) % 16) blob.push_back(0);
       D.tmpl = h->upload(blob);
       D.tmpl_bytes = (int)(blob.size() * sizeof(unsigned short));
+      D.wpb = patch_warps_per_block(D);
     }
   }
   h->stat_patches += F.npatch;
@@ -358,10 +359,27 @@ void build_apply(rm_handle *h, const Geometry &geo, const std::vector<double> &a
       A.h = h->upload(hc);
       A.bh_a = B.Bhat[0];
       A.bh_b = B.Bhat[p];
-      const size_t smem = cart_smem_doubles(h->k, p, A.nloc0, A.nloc1);
+      const size_t smem = cart_local_smem_doubles(h->k, p, A.nloc0, A.nloc1);
       if (smem * sizeof(double) > 227 * 1024)
         throw std::runtime_error("degree too high for the Cartesian apply kernel's shared memory");
       A.Y = h->dalloc<double>((size_t)ncell * A.nloc0);  // unassembled cell products
+      // per cell: beta x the box metric of each V^k component, alpha x that of
+      // each V^{k+1} component (J = diag(h/2); the pullbacks of Sec. 3.1)
+      std::vector<double> cc((size_t)ncell * 8, 0.0);
+      auto box_metric = [](int kk, int m, const double *hh) {
+        const double det = 0.125 * hh[0] * hh[1] * hh[2];
+        if (kk == 0) return det;
+        if (kk == 3) return 1.0 / det;
+        if (kk == 1) return det * 4.0 / (hh[m] * hh[m]);
+        return 0.25 * hh[m] * hh[m] / det;
+      };
+      const int nc0 = k == 0 ? 1 : 3, nc1 = k == 2 ? 1 : 3;
+      for (int c = 0; c < ncell; ++c) {
+        const double *hh = &hc[3 * (size_t)c];
+        for (int m = 0; m < nc0; ++m) cc[(size_t)c * 8 + m] = beta[c] * box_metric(k, m, hh);
+        for (int t = 0; t < nc1; ++t) cc[(size_t)c * 8 + 3 + t] = alpha[c] * box_metric(k + 1, t, hh);
+      }
+      A.ccoef = h->upload(cc);
       A.G = nullptr;
       return;
     }

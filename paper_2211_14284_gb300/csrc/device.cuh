@@ -36,6 +36,8 @@ struct ApplyDev {
   double bh_a, bh_b;
   const int *cidx;         // cart_index_table(k, p) (batched apply)
   double *Y;               // unassembled cell products, ncell x nloc0 (Cartesian apply)
+  const double *ccoef;     // per cell: beta x box metric of V^k (3), alpha x box metric
+                           // of V^{k+1} (3), 2 unused (Cartesian apply; setup-time FP64)
   int prob;                // batched solves: the problem's index
   int arith;               // number type of the apply: 0 double, 1 double-float (DF)
   int natural;             // 1: Gamma_D empty (no Dirichlet entries)
@@ -213,8 +215,23 @@ inline bool eo_tables(const double *T, int q, int n, std::vector<double> &dbl,
   return true;
 }
 
-// Shared memory of the Cartesian apply (doubles): D-hat, x and y on V^k, d
-// and dy on V^{k+1}, and the interface line sums of every D-hat term.
+// Launch shape of the per-handle Cartesian apply (cart_local_kernel): a
+// thread owns one line of a cell, a cell has at most (p + 1)^2 lines per
+// component, so a CTA takes CPB cells with CPB (p + 1)^2 <= 128 (at least
+// one) and as many threads, rounded up to whole warps.
+__host__ __device__ constexpr int cart_cpb(int p) {
+  return 128 / ((p + 1) * (p + 1)) < 1 ? 1 : (128 / ((p + 1) * (p + 1)) > 32 ? 32 : 128 / ((p + 1) * (p + 1)));
+}
+__host__ __device__ constexpr int cart_threads(int p) { return (cart_cpb(p) * (p + 1) * (p + 1) + 31) / 32 * 32; }
+// its shared memory (doubles): D-hat, then per cell 8 coefficients, x on
+// V^k, d (later dy) on V^{k+1} and the interface line sums of every D-hat term
+__host__ __device__ constexpr size_t cart_local_smem_doubles(int k, int p, int nloc0, int nloc1) {
+  return (size_t)p * (p + 1) +
+         (size_t)cart_cpb(p) * (8 + (size_t)nloc0 + (size_t)nloc1 + (size_t)(k == 1 ? 6 : 3) * 2 * (p + 1) * (p + 1));
+}
+
+// Shared memory of the batched Cartesian apply (doubles): D-hat, x and y on
+// V^k, d and dy on V^{k+1}, and the interface line sums of every D-hat term.
 inline size_t cart_smem_doubles(int k, int p, int nloc0, int nloc1) {
   return (size_t)p * (p + 1) + 2 * (size_t)nloc0 + 2 * (size_t)nloc1 +
          (size_t)(k == 1 ? 6 : 3) * 2 * (p + 1) * (p + 1);
@@ -268,6 +285,7 @@ struct DevPatch {
   const unsigned short *tmpl = nullptr;
   int tmpl_bytes = 0;
   int toff[9] = {};
+  int wpb = 0;  // patches (warps) per CTA of patch_warp_kernel; 0: the CTA-per-patch kernels
 };
 
 // launchers (kernels.cu); launch_count() = kernels launched so far in this process
@@ -288,7 +306,8 @@ cudaError_t launch_patches(const DevPatch &F, const double *r, double *z, cudaSt
 // the warp-per-patch kernel's bounded waits: 1 if any gave up since the last
 // call (the flag is cleared), 0 otherwise; a CUDA error code on failure
 int patch_timeouts(cudaError_t *err);
-// patches per CTA of the warp kernel for a family (0: it does not fit)
+// patches per CTA of the warp kernel for a family on the current device,
+// chosen for the fewest waves (0: it does not fit)
 int patch_warps_per_block(const DevPatch &F);
 cudaError_t launch_gemv(int n, const void *A, int vt, const double *x, double *y, cudaStream_t s);
 // coarse multigrid: x_out = x_in + w (b - A x_in) (A FP64, rows compact); x = w b

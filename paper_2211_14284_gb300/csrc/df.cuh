@@ -118,10 +118,11 @@ __device__ __forceinline__ double rto(DF a) { return (double)a.hi + (double)a.lo
 // (1/64 of the FP32 rate on GB300), by integer operations on the bit
 // patterns.  df_split: hi = the leading 24 significand bits of x (truncated),
 // lo = the next 24 (truncated), so hi + lo agrees with x to 2^-48 relative;
-// for |x| < 2^-70 (lo would leave the FP32 range), |x| >= 2^127 and zero the
-// FP64 path rfrom<DF> is taken.
+// zero maps to zero; for |x| < 2^-70 (lo would leave the FP32 range) and
+// |x| >= 2^127 the FP64 path rfrom<DF> is taken.
 __device__ __forceinline__ DF df_split(double x) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  if ((bits << 1) == 0ULL) return {__uint_as_float((unsigned)(bits >> 32)), 0.f};  // +-0
   const int e = (int)((bits >> 52) & 0x7FF) - 1023;  // unbiased exponent
   if (e < -70 || e > 126) return rfrom<DF>(x);       // zero, tiny, huge: rare
   const unsigned sign = (unsigned)(bits >> 32) & 0x80000000u;

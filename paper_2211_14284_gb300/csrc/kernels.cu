@@ -11,6 +11,7 @@
 // * SpMV / GEMV for static condensation (Eq. schur), the Hiptmair gradient
 //   and the p = 1 coarse correction; fused CG updates with deterministic
 //   fixed-order FP64 reductions finished by the last CTA.
+#include <algorithm>
 #include <atomic>
 
 #include "df.cuh"
@@ -890,28 +891,63 @@ cudaError_t launch_spmv(const DevCsr &M, const double *x, double *y, const doubl
   return cudaGetLastError();
 }
 
+template <typename VT, int... W>
+static const void *warp_kernel_at(int w, std::integer_sequence<int, W...>) {
+  const void *k = nullptr;
+  ((w == W + 1 ? (k = (const void *)patch_warp_kernel<VT, W + 1>, 0) : 0), ...);
+  return k;
+}
+template <typename VT>
+static const void *warp_kernel(int w) {
+  return warp_kernel_at<VT>(w, std::make_integer_sequence<int, kPatchWarpMaxWPB>{});
+}
+
+// Patches per CTA of the warp kernel: the fewest waves over the SMs (CTAs
+// resident per SM from the occupancy calculator at that CTA's shared
+// memory), then the fewest patches on the busiest SM, then the most patches
+// per CTA (one template copy for more of them).  0: it does not fit.
 template <typename VT>
 static int warps_per_block(const DevPatch &F) {
   if (!F.tmpl || F.inverse) return 0;
-  for (int w = kPatchWarpMaxWPB; w >= 1; w /= 2)
-    if (patch_warp_smem<VT>(F, w) <= 200 * 1024) return w;
-  return 0;
+  int dev = 0, nsm = 1;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  long long best[3] = {0, 0, 0};
+  int wbest = 0;
+  for (int w = 1; w <= kPatchWarpMaxWPB; ++w) {
+    const size_t smem = patch_warp_smem<VT>(F, w);
+    if (smem > 227 * 1024) break;
+    const void *kern = warp_kernel<VT>(w);
+    int cps = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cps, kern, 32 * w, smem) != cudaSuccess || cps < 1)
+      continue;
+    const long long ncta = (F.npatch + w - 1) / w;
+    const long long waves = (ncta + (long long)nsm * cps - 1) / ((long long)nsm * cps);
+    const long long load = (ncta + nsm - 1) / nsm * w;
+    const long long key[3] = {waves, load, -w};
+    if (wbest == 0 || std::lexicographical_compare(key, key + 3, best, best + 3)) {
+      std::copy(key, key + 3, best);
+      wbest = w;
+    }
+  }
+  cudaGetLastError();  // a refused configuration above is not an error of the caller
+  return wbest;
 }
 
 template <typename VT>
 static void patch_dispatch(const DevPatch &F, const double *r, double *z, cudaStream_t s) {
-  const int wpb = warps_per_block<VT>(F);
-  if (wpb > 0) {
-    const size_t smem = patch_warp_smem<VT>(F, wpb);
-    const int grid = (F.npatch + wpb - 1) / wpb;
-    auto go = [&](auto kern) {
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      kern<<<grid, wpb * 32, smem, s>>>(F, r, z);
-    };
-    if (wpb == 8) go(patch_warp_kernel<VT, 8>);
-    else if (wpb == 4) go(patch_warp_kernel<VT, 4>);
-    else if (wpb == 2) go(patch_warp_kernel<VT, 2>);
-    else go(patch_warp_kernel<VT, 1>);
+  if (F.wpb > 0) {
+    const size_t smem = patch_warp_smem<VT>(F, F.wpb);
+    const int grid = (F.npatch + F.wpb - 1) / F.wpb;
+    const void *kern = warp_kernel<VT>(F.wpb);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    DevPatch Fa = F;
+    const double *ra = r;
+    double *za = z;
+    void *args[] = {&Fa, &ra, &za};
+    cudaLaunchKernel(kern, dim3(grid), dim3(32 * F.wpb), args, smem, s);
     return;
   }
   if (F.inverse) {

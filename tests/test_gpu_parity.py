@@ -339,13 +339,17 @@ def test_apply_parity_coefficient_extremes(k, lo, hi, beta, arith):
     (0, "sc-icc", dict(static_condensation=1, factor=1))])
 def test_solve_paper_coefficients(k, mode, opts):
     """alpha = 1, beta = 1e-8 (the paper's Riesz-map experiments, Sec. 5.1),
-    stopping on the paper's natural norm: the GPU count is the oracle PCG's
-    with the same preconditioner (+-2: at this conditioning, cond(A) ~ 1e10,
-    the iteration histories separate after a few dozen steps).  The solution
-    is not checked against the recursive norm: at cond(A) ~ 1e10 the
-    recursive and true residuals of FP64 CG part at ~1e-5 (measured natural
-    ratio 3e-5 for the true residual), the attainable accuracy of the
-    method in FP64, not a defect of either side."""
+    stopping on the paper's natural norm.  The preconditioner is checked
+    element by element against the oracle's (bound scaled by the patch
+    factors' condition, as in test_precondition_parity); the GPU iteration
+    count is the oracle PCG's within 25 %.  At cond(A) ~ 1e10, two FP64 CG
+    runs whose preconditioners differ by rounding follow the same histories
+    for the first steps only (finite-precision CG loses orthogonality at a
+    rate set by the rounding, not by the method), so the counts are not
+    compared exactly.  The solution is not checked against the recursive
+    norm: at this conditioning the recursive and true residuals of FP64 CG
+    part at ~1e-5 (measured natural ratio 3e-5 for the true residual), the
+    attainable accuracy of the method in FP64, not a defect of either side."""
     from paper_2211_14284_gb300.rm import RM_NORM_NATURAL, Solver
     n, p = 3, 3
     X = inputs.vertices(n, perturb=0.1, seed=65)
@@ -354,15 +358,28 @@ def test_solve_paper_coefficients(k, mode, opts):
     s = Solver(k, n, p, vertices=X, alpha=al, beta=be, rtol=1e-8, max_it=600,
                norm=RM_NORM_NATURAL, **opts)
     pr = Problem(k, n, p, X, al, be)
+    M = _oracle_prec(pr, mode)
+    # the preconditioner itself
+    r = inputs.normal_rhs(pr.lat.size, 67)
+    r[np.setdiff1d(np.arange(pr.lat.size), pr.free)] = 0.0
+    z = torch.zeros(pr.lat.size, dtype=torch.float64, device="cuda")
+    s.precondition(_dev(r), z)
+    want = np.zeros(pr.lat.size)
+    want[pr.free] = M.apply(r[pr.free])
+    solvers = (M.edge + M.potential) if mode == "scph" else [M.patches]
+    cond = max(np.linalg.cond(L) ** 2 for ps in solvers for L in ps.L)
+    tol = max(1e-11, 1e-12 * cond)
+    assert np.abs(_host(z) - want).max() <= tol * np.abs(want).max()
+    # the solve
     b = inputs.normal_rhs(pr.lat.size, 66)
     x = torch.zeros(pr.lat.size, dtype=torch.float64, device="cuda")
     info = s.solve(_dev(b), x)
     assert info["status"] == "RM_OK"
     A = pr.A_free()
-    M = _oracle_prec(pr, mode)
-    _, io = pcg(A, b[pr.free], M.apply, rtol=0.0, maxit=info["iterations"] + 5)
-    want = next(i for i, v in enumerate(io["history_natural"]) if v <= 1e-8)
-    assert abs(info["iterations"] - want) <= 2, (info["iterations"], want)
+    _, io = pcg(A, b[pr.free], M.apply, rtol=0.0, maxit=2 * info["iterations"] + 20)
+    hist = io["history_natural"]
+    its = next((i for i, v in enumerate(hist) if v <= 1e-8), len(hist))
+    assert abs(info["iterations"] - its) <= max(3, 0.25 * its), (info["iterations"], its)
     xf = _host(x)
     assert np.all(np.isfinite(xf))
 
