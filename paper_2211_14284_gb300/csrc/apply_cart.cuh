@@ -11,7 +11,8 @@
 //  * cart_local_kernel<K, P, R>: the cell products y_K = A_K x_K, one CTA per
 //    CPB cells with one thread per line of a cell (cart_cpb, cart_threads),
 //    every shape and loop bound a compile-time constant of (K, P); written
-//    unassembled to the scratch Y[cell][local entry] in the number type R;
+//    unassembled, with coalesced stores, to the scratch Y (cart_y_index) in
+//    the number type R;
 //  * cart_assemble_kernel<K, P, R>: every lattice entry sums its (at most 8)
 //    cell contributions from Y in a fixed order, in R, and converts once to
 //    FP64; Dirichlet entries get 0.
@@ -128,6 +129,19 @@ __device__ __forceinline__ void line_mass(const R *in, int i1, int i2, R a, R b,
 #pragma unroll
     for (int i0 = 0; i0 < LL0; ++i0) u[i0] = w[i0];
   }
+}
+
+// Position of entry (i0, i1, i2) of component m of cell c in the scratch Y
+// of unassembled cell products: component-major, then cell, then the local
+// entry ([m][cell][i2][i1][i0]), so that the CPB consecutive cells of a CTA
+// own one contiguous run of every component.
+template <int K, int P>
+__device__ __forceinline__ size_t cart_y_index(int ncell, int m, size_t c, int i0, int i1, int i2) {
+  using Sh = CartShape<K, P>;
+  const bool s0 = m == 0 ? styp(K, 0, 0) : (m == 1 ? styp(K, 1, 0) : styp(K, 2, 0));
+  const bool s1 = m == 0 ? styp(K, 0, 1) : (m == 1 ? styp(K, 1, 1) : styp(K, 2, 1));
+  const int l0 = s0 ? P + 1 : P, l1 = s1 ? P + 1 : P;
+  return ((size_t)m * ncell + c) * Sh::S0 + i0 + l0 * (i1 + l1 * i2);
 }
 
 template <int K, int P, typename R>
@@ -296,11 +310,15 @@ __global__ void __launch_bounds__(cart_threads(P)) cart_local_kernel(ApplyDev A,
     }
   });
   __syncthreads();
-  // ---- y = beta M^K x + D-hat^T dy; the cell's unassembled product to Y ----
+  // ---- y = beta M^K x + D-hat^T dy; the cell's unassembled product to Y,
+  // per component: the lines in registers, then (after every thread has read
+  // the component's x block) written over that block, then copied out as
+  // one coalesced run per component ----
   sfor<NC0>([&](auto mc) {
     constexpr int m = decltype(mc)::value;
     constexpr bool t0 = styp(K, m, 0), t1 = styp(K, m, 1), t2 = styp(K, m, 2);
     constexpr int l0 = sld(K, P, m, 0), l1 = sld(K, P, m, 1), l2 = sld(K, P, m, 2);
+    R out[l0];
     for_lines<CPB, NT, l1, l2>([&](int cb, int i1, int i2) {
       Acc<R> acc[l0];
       {
@@ -328,78 +346,119 @@ __global__ void __launch_bounds__(cart_threads(P)) cart_local_kernel(ApplyDev A,
               else acc[i0].add(D1[i0 * Q1 + i0], sg(dline[i0]));
             }
           } else {
+            // one instruction stream for interface and interior lines (a
+            // branch would diverge within most warps): an interface line
+            // adds its line sums (weight 1, stride 2), an interior line
+            // D[i][i] times its dy line
             const int i = T.dir == 1 ? i1 : i2;
-            if (i == 0 || i == P) {
-              const int b = T.dir == 1 ? i2 : i1;
+            const bool itf = i == 0 || i == P;
+            const int b = T.dir == 1 ? i2 : i1;
+            const R *src = itf ? lsum + 2 * tl0 * b + (i == 0 ? 0 : 1) : dyt + tl0 * (i1 + tl1 * i2);
+            const int stride = itf ? 2 : 1;
+            const int id = itf ? 0 : i;
+            const R co = itf ? rone(R()) : D1[id * Q1 + id];
 #pragma unroll
-              for (int i0 = 0; i0 < l0; ++i0) acc[i0].add_value(sg(lsum[2 * (i0 + tl0 * b) + (i == 0 ? 0 : 1)]));
-            } else {
-              const R *dline = dyt + tl0 * (i1 + tl1 * i2);
-              const R di = D1[i * Q1 + i];
-#pragma unroll
-              for (int i0 = 0; i0 < l0; ++i0) acc[i0].add(di, sg(dline[i0]));
-            }
+            for (int i0 = 0; i0 < l0; ++i0) acc[i0].add(co, sg(src[i0 * stride]));
           }
         }
       });
-      const int c = c0 + cb;
-      if (c < ncell) {
-        R *dst = Y + (size_t)c * L0 + m * S0 + l0 * (i1 + l1 * i2);
 #pragma unroll
-        for (int i0 = 0; i0 < l0; ++i0) dst[i0] = acc[i0].val();
-      }
+      for (int i0 = 0; i0 < l0; ++i0) out[i0] = acc[i0].val();
     });
+    __syncthreads();
+    for_lines<CPB, NT, l1, l2>([&](int cb, int i1, int i2) {
+      R *st = xl + cb * L0 + m * S0 + l0 * (i1 + l1 * i2);
+#pragma unroll
+      for (int i0 = 0; i0 < l0; ++i0) st[i0] = out[i0];
+    });
+    __syncthreads();
+    // the CTA's cells hold one contiguous run of component m in Y
+    const int nv = (ncell - c0 < CPB ? ncell - c0 : CPB) * S0;
+    R *dst = Y + cart_y_index<K, P>(ncell, m, c0, 0, 0, 0);
+    for (int i = tid; i < nv; i += NT) {
+      const int cb = i / S0;
+      dst[i] = xl[cb * L0 + m * S0 + (i - cb * S0)];
+    }
   });
 }
 
 // y[g] = sum over the cells holding lattice entry g of their contribution in
-// Y, in a fixed order (cells lexicographic); Dirichlet entries 0.  Grid:
-// x along g0, y over rows (g1, g2), z over components.
+// Y, in a fixed order (cells lexicographic, direction 2 outermost);
+// Dirichlet entries 0.  A warp takes one lattice row (m, g1, g2) at a
+// time (grid-stride over rows): the cells and local indices along
+// directions 1 and 2 are the row's, decoded once; the lanes walk g0, whose
+// consecutive entries are consecutive local indices of a cell in Y and
+// consecutive entries of y; an entry inside a cell along g0 reads one
+// value per run, an interface entry two.
 template <int K, int P, typename R>
-__global__ void __launch_bounds__(128) cart_assemble_kernel(ApplyDev A, const R *__restrict__ Y,
+__global__ void __launch_bounds__(256) cart_assemble_kernel(ApplyDev A, const R *__restrict__ Y,
                                                             double *__restrict__ y) {
   using Sh = CartShape<K, P>;
-  const int m = blockIdx.z;
-  const int N0 = A.N[m][0], N1 = A.N[m][1], N2 = A.N[m][2];
-  const int g0 = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g0 >= N0) return;
-  bool st[3];
-  int l[3];
+  constexpr int NC0 = Sh::NC0;
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  const int ncell = A.n[0] * A.n[1] * A.n[2];
+  sfor<NC0>([&](auto mc) {
+    constexpr int m = decltype(mc)::value;
+    constexpr bool st0 = styp(K, m, 0), st1 = styp(K, m, 1), st2 = styp(K, m, 2);
+    const int N0 = A.N[m][0], N1 = A.N[m][1], rows = A.N[m][1] * A.N[m][2];
+    for (int row = gw; row < rows; row += nw) {
+      const int g1 = row % N1, g2 = row / N1;
+      // (cell, local index) pairs along a direction: two on an interior
+      // s-type interface plane, else one; dir: a Dirichlet plane
+      bool dir = false;
+      auto pairs = [&](bool st, int g, int nd, int (&ce)[2], int (&ci)[2], int &nc) {
+        const int e = g / P, i = g - e * P;
+        if (st && i == 0) {
+          if (!A.natural && (g == 0 || e == nd)) dir = true;
+          const bool lo = e >= 1, hi = e < nd;
+          ce[0] = lo ? e - 1 : e;
+          ci[0] = lo ? P : 0;
+          ce[1] = e;
+          ci[1] = 0;
+          nc = (lo && hi) ? 2 : 1;
+        } else {
+          ce[0] = ce[1] = e;
+          ci[0] = ci[1] = i;
+          nc = 1;
+        }
+      };
+      int ce1[2], ci1[2], n1, ce2[2], ci2[2], n2;
+      pairs(st1, g1, A.n[1], ce1, ci1, n1);
+      pairs(st2, g2, A.n[2], ce2, ci2, n2);
+      const bool rowdir = dir;
+      // the row's (up to 4) runs in Y: cell (0, e1, e2) at local (0, i1, i2)
+      // for each pair along directions 1 and 2 (warp-uniform)
+      const R *base[2][2];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    st[d] = styp(K, m, d);
-    l[d] = st[d] ? P + 1 : P;
-  }
-  for (int row = blockIdx.y; row < N1 * N2; row += gridDim.y) {
-    const int g[3] = {g0, row % N1, row / N1};
-    // per direction the (cell, local index) pairs holding g: two on an
-    // s-type interface plane inside the mesh, else one
-    int ce[3][2], ci[3][2], nc[3];
-    bool dir = false;
+      for (int c = 0; c < 2; ++c)
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const int e = g[d] / P, i = g[d] - e * P;
-      if (st[d] && i == 0) {
-        if (!A.natural && (g[d] == 0 || e == A.n[d])) dir = true;
-        nc[d] = 0;
-        if (e >= 1) { ce[d][nc[d]] = e - 1; ci[d][nc[d]] = P; nc[d]++; }
-        if (e < A.n[d]) { ce[d][nc[d]] = e; ci[d][nc[d]] = 0; nc[d]++; }
-      } else {
-        nc[d] = 1;
-        ce[d][0] = e;
-        ci[d][0] = i;
+        for (int b = 0; b < 2; ++b)
+          base[c][b] = Y + cart_y_index<K, P>(ncell, m, (size_t)A.n[0] * (ce1[b] + (size_t)A.n[1] * ce2[c]), 0,
+                                              ci1[b], ci2[c]);
+      double *yrow = y + A.off[m] + (long long)N0 * row;
+      for (int g0 = lane; g0 < N0; g0 += 32) {
+        int ce0[2], ci0[2], n0;
+        dir = rowdir;
+        pairs(st0, g0, A.n[0], ce0, ci0, n0);
+        const int o0 = ce0[0] * Sh::S0 + ci0[0], o1 = ce0[1] * Sh::S0 + ci0[1];
+        R s = rzero(R());
+        if (!dir) {
+          // fixed order: direction 2 outermost, then 1, then 0
+#pragma unroll
+          for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+              if (c < n2 && b < n1) {
+                const R v0 = base[c][b][o0];
+                s = (c == 0 && b == 0) ? v0 : radd(s, v0);
+                if (n0 == 2) s = radd(s, base[c][b][o1]);
+              }
+        }
+        yrow[g0] = to_double(s);
       }
     }
-    R s = rzero(R());
-    if (!dir)
-      for (int c = 0; c < nc[2]; ++c)
-        for (int b = 0; b < nc[1]; ++b)
-          for (int a = 0; a < nc[0]; ++a) {
-            const size_t cell = ce[0][a] + (size_t)A.n[0] * (ce[1][b] + (size_t)A.n[1] * ce[2][c]);
-            s = radd(s, Y[cell * Sh::L0 + m * Sh::S0 + ci[0][a] + l[0] * (ci[1][b] + l[1] * ci[2][c])]);
-          }
-    y[A.off[m] + g0 + (long long)N0 * row] = to_double(s);
-  }
+  });
 }
 
 template <int K, int P, typename R>
@@ -414,13 +473,11 @@ cudaError_t launch_cart_kpr(const ApplyDev &A, const double *x, double *y, cudaS
   cart_local_kernel<K, P, R><<<(ncell + Sh::CPB - 1) / Sh::CPB, Sh::NT, smem, s>>>(A, x, reinterpret_cast<R *>(A.Y));
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  int rows = 0, n0max = 0;
-  for (int m = 0; m < Sh::NC0; ++m) {
-    rows = rows > A.N[m][1] * A.N[m][2] ? rows : A.N[m][1] * A.N[m][2];
-    n0max = n0max > A.N[m][0] ? n0max : A.N[m][0];
-  }
-  const dim3 grid((n0max + 127) / 128, rows < 65535 ? rows : 65535, Sh::NC0);
-  cart_assemble_kernel<K, P, R><<<grid, 128, 0, s>>>(A, reinterpret_cast<const R *>(A.Y), y);
+  // a grid of resident CTAs (8 per SM), each warp striding over the rows
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cart_assemble_kernel<K, P, R><<<8 * nsm, 256, 0, s>>>(A, reinterpret_cast<const R *>(A.Y), y);
   return cudaGetLastError();
 }
 template <int K, int P>

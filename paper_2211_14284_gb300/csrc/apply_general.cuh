@@ -288,9 +288,9 @@ __device__ __forceinline__ void cell_io(const ApplyDev &P, const int e[3], const
                        (styp(KK, m, 2) && (g3 == 0 || g3 == P.n[2] * PP)));
       const long long gi = P.off[m] + g1 + (long long)P.N[m][0] * (g2 + (long long)P.N[m][1] * g3);
       if (SCATTER) {
-        if (!dir) atomicAdd(&y[gi], rto(yl[m * CS + l]));
+        if (!dir) atomicAdd(&y[gi], to_double(yl[m * CS + l]));
       } else {
-        xl[m * CS + l] = rfrom<R>(dir ? 0.0 : x[gi]);
+        xl[m * CS + l] = to_r<R>(dir ? 0.0 : x[gi]);
         yl[m * CS + l] = rzero(R());
       }
     }
@@ -321,11 +321,11 @@ __global__ void __launch_bounds__(kApplyThreadsGeneral) apply_kernel(ApplyDev P,
   {
     const double *g = P.tabs + q * (p + 1) + q * p;
     for (int i = tid; i < p * (p + 1); i += NT) {
-      D1[i] = rfrom<R>(g[i]);
-      D1T[(i % (p + 1)) * p + i / (p + 1)] = rfrom<R>(g[i]);
+      D1[i] = to_r<R>(g[i]);
+      D1T[(i % (p + 1)) * p + i / (p + 1)] = to_r<R>(g[i]);
     }
     g += p * (p + 1) + 2 * q;
-    for (int i = tid; i < EOD; i += NT) sm[i] = rfrom<R>(g[i]);
+    for (int i = tid; i < EOD; i += NT) sm[i] = to_r<R>(g[i]);
   }
   cell_io<false, K, PP>(P, e, x, y, xl, yl);
   __syncthreads();

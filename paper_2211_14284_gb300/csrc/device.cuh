@@ -35,7 +35,7 @@ struct ApplyDev {
   const double *h;
   double bh_a, bh_b;
   const int *cidx;         // cart_index_table(k, p) (batched apply)
-  double *Y;               // unassembled cell products, ncell x nloc0 (Cartesian apply)
+  double *Y;               // unassembled cell products, [component][cell][local entry] (Cartesian apply)
   const double *ccoef;     // per cell: beta x box metric of V^k (3), alpha x box metric
                            // of V^{k+1} (3), 2 unused (Cartesian apply; setup-time FP64)
   int prob;                // batched solves: the problem's index
@@ -217,14 +217,26 @@ inline bool eo_tables(const double *T, int q, int n, std::vector<double> &dbl,
 
 // Launch shape of the per-handle Cartesian apply (cart_local_kernel): a
 // thread owns one line of a cell, a cell has at most (p + 1)^2 lines per
-// component, so a CTA takes CPB cells with CPB (p + 1)^2 <= 128 (at least
-// one) and as many threads, rounded up to whole warps.
+// component, so a CTA takes CPB cells (CPB (p + 1)^2 <= 256) and as many
+// threads, rounded up to whole warps; CPB is the count that leaves the
+// fewest idle lanes in that rounding (the smallest such).
 __host__ __device__ constexpr int cart_cpb(int p) {
-  return 128 / ((p + 1) * (p + 1)) < 1 ? 1 : (128 / ((p + 1) * (p + 1)) > 32 ? 32 : 128 / ((p + 1) * (p + 1)));
+  const int nl = (p + 1) * (p + 1);
+  int best = 1, bnum = 0, bden = 1;  // best lane use bnum / bden
+  for (int c = 1; c <= 32 && c * nl <= 256; ++c) {
+    const int nt = (c * nl + 31) / 32 * 32;
+    if ((long long)c * nl * bden > (long long)bnum * nt) {
+      best = c;
+      bnum = c * nl;
+      bden = nt;
+    }
+  }
+  return best;
 }
 __host__ __device__ constexpr int cart_threads(int p) { return (cart_cpb(p) * (p + 1) * (p + 1) + 31) / 32 * 32; }
 // its shared memory (doubles): D-hat, then per cell 8 coefficients, x on
-// V^k, d (later dy) on V^{k+1} and the interface line sums of every D-hat term
+// V^k (at the end the cell's product, staged for coalesced stores), d (later
+// dy) on V^{k+1} and the interface line sums of every D-hat term
 __host__ __device__ constexpr size_t cart_local_smem_doubles(int k, int p, int nloc0, int nloc1) {
   return (size_t)p * (p + 1) +
          (size_t)cart_cpb(p) * (8 + (size_t)nloc0 + (size_t)nloc1 + (size_t)(k == 1 ? 6 : 3) * 2 * (p + 1) * (p + 1));

@@ -76,6 +76,8 @@ __device__ __forceinline__ DF fast_two_sum(float a, float b) {
 
 __device__ __forceinline__ double rzero(double) { return 0.0; }
 __device__ __forceinline__ DF rzero(DF) { return {0.f, 0.f}; }
+__device__ __forceinline__ double rone(double) { return 1.0; }
+__device__ __forceinline__ DF rone(DF) { return {1.f, 0.f}; }
 __device__ __forceinline__ double rfma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ DF rfma(DF a, DF b, DF c) {
   const float p = __fmul_rn(a.hi, b.hi);
@@ -118,13 +120,16 @@ __device__ __forceinline__ double rto(DF a) { return (double)a.hi + (double)a.lo
 // (1/64 of the FP32 rate on GB300), by integer operations on the bit
 // patterns.  df_split: hi = the leading 24 significand bits of x (truncated),
 // lo = the next 24 (truncated), so hi + lo agrees with x to 2^-48 relative;
-// zero maps to zero; for |x| < 2^-70 (lo would leave the FP32 range) and
-// |x| >= 2^127 the FP64 path rfrom<DF> is taken.
+// zero maps to zero.  |x| < 2^-70 (lo would leave the FP32 range) and
+// |x| >= 2^127 take the FP64 conversion rfrom<DF> in a function of its own,
+// so that the common path is a real branch around it: an inlined rare path
+// would be predicated and its FP64 instructions issued for every element.
+__device__ __noinline__ DF df_split_rare(double x) { return rfrom<DF>(x); }
 __device__ __forceinline__ DF df_split(double x) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   if ((bits << 1) == 0ULL) return {__uint_as_float((unsigned)(bits >> 32)), 0.f};  // +-0
   const int e = (int)((bits >> 52) & 0x7FF) - 1023;  // unbiased exponent
-  if (e < -70 || e > 126) return rfrom<DF>(x);       // zero, tiny, huge: rare
+  if (e < -70 || e > 126) return df_split_rare(x);   // tiny, huge, inf, nan: rare
   const unsigned sign = (unsigned)(bits >> 32) & 0x80000000u;
   const unsigned long long frac = bits & 0xFFFFFFFFFFFFFULL;
   const float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)(frac >> 29));
@@ -142,11 +147,15 @@ template <>
 __device__ __forceinline__ double to_r<double>(double x) { return x; }
 template <>
 __device__ __forceinline__ DF to_r<DF>(double x) { return df_split(x); }
-// a normal FP32 value as FP64, by its bits (exact)
+// an FP32 value as FP64, by its bits (exact): normal numbers and zeros
+// inline; subnormals, infinities and NaN in a function of its own (as for
+// df_split, so that the common path does not issue FP64 instructions)
+__device__ __noinline__ double f2d_rare(float f) { return (double)f; }
 __device__ __forceinline__ double f2d_bits(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned ex = (u >> 23) & 0xFFu;
-  if (ex == 0u || ex == 0xFFu) return (double)f;  // zero, subnormal, inf, nan
+  if ((u << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)u << 32));  // +-0
+  if (ex == 0u || ex == 0xFFu) return f2d_rare(f);
   const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
                                ((unsigned long long)(ex - 127 + 1023) << 52) |
                                ((unsigned long long)(u & 0x7FFFFFu) << 29);
