@@ -24,6 +24,7 @@ from __future__ import annotations
 import argparse
 import concurrent.futures
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -52,7 +53,10 @@ DTYPES = {"fp64": "f64 (CG, apply, preconditioner)",
           "fp64_df": "f64 CG and preconditioner, double-float (2 x f32) apply",
           "mixed_fp32": "f64 CG, double-float (2 x f32) apply, f32 preconditioner"}
 HEADLINE = "mixed_fp32"
-APPLY_TRAFFIC_BYTES = 52_455_168  # ncu capture of the H(grad) general apply (profiles/)
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the H(grad)
+# general apply (apply_kernel<0,7>, double-float, 8^3 cells) in an ncu
+# capture of this workload (profiles/apply_kernel_hgrad_8cubed_p7.md)
+APPLY_TRAFFIC_BYTES = 52_453_632
 FP64_PEAK_TFLOPS = 1.20   # measured FP64 FMA throughput of a GB300 (DFMA throughput probe)
 # Algorithmic HBM bytes per lattice DOF per CG iteration of the whole solve:
 # CG vectors ~80 B (FP64, fused updates and dots), operator apply 16 B (x in,
@@ -122,6 +126,62 @@ def apply_flops(k: int, p: int) -> float:
     nterms = {0: 3, 1: 6, 2: 3}[k]
     fma += 2 * nterms * p * (p + 1) * (p + 1) * (p + 1)   # D-hat and its transpose
     return 2.0 * fma
+
+
+def cart_apply_flops(k: int, p: int) -> float:
+    """Algorithmic flops (FP64-equivalent) of the Cartesian apply on one cell:
+    per signed D-hat term the D-hat product (three nonzeros per row of D-hat
+    in the FDM basis, two in its first row) and the D-hat^T product (one
+    multiply-add per interior row, the 2P-entry line sums for the interface
+    rows), plus the beta and alpha coefficient scalings.  The 2x2 B-hat
+    interface blocks are not counted (a lower bound)."""
+    types = {0: ["sss"], 1: ["rss", "srs", "ssr"], 2: ["srr", "rsr", "rrs"], 3: ["rrr"]}
+
+    def size(kk):
+        t = types[kk][0]
+        return math.prod(p + 1 if c == "s" else p for c in t)
+    s0, s1 = size(k), size(k + 1)
+    nterms = {0: 3, 1: 6, 2: 3}[k]
+    per_term = (3 * p - 1) * (s1 // p) + (3 * p - 1) * (s0 // (p + 1))
+    macs = nterms * per_term + len(types[k]) * s0 + len(types[k + 1]) * s1
+    return 2.0 * macs
+
+
+def run_apply_kernels(steps, stream):
+    """The operator apply alone on the axis-aligned-cell workloads (the
+    Cartesian kernel pair): 32^3 H(grad) at p = 6 and 16^3 H(div) at p = 10,
+    double-float and FP64.  Inputs, output and the unassembled scratch
+    (> 200 MB) exceed L2, so no flush is needed between applies."""
+    import torch
+    from paper_2211_14284_gb300.rm import Solver
+    peaks = measured_peaks()
+    out = {}
+    for name, k, n, p in (("hgrad_32cubed_p6", 0, 32, 6), ("hdiv_16cubed_p10", 2, 16, 10)):
+        res = {}
+        for aname, arith in (("df64", 1), ("fp64", 0)):
+            s = Solver(k, n, p, relaxation=0, arith=arith, stream=stream)
+            x = torch.randn(s.size, dtype=torch.float64, device="cuda")
+            y = torch.zeros_like(x)
+            for _ in range(3):
+                s.apply(x, y)
+            reps = max(10, 4 * steps)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(reps):
+                s.apply(x, y)
+            ev1.record(stream)
+            ev1.synchronize()
+            ms = ev0.elapsed_time(ev1) / reps
+            tflops = cart_apply_flops(k, p) * n ** 3 / (ms / 1e3) / 1e12
+            res[aname] = {"ms_per_apply": ms, "dofs": s.size, "dofs_per_s": s.size / (ms / 1e3),
+                          "tflops_fp64_equiv": tflops,
+                          "alu_frac": tflops / (DF_PEAK_TFLOPS if arith else FP64_PEAK_TFLOPS),
+                          "hbm_frac": 16.0 * s.size / (ms / 1e3) / (peaks["hbm_gbs"] * 1e9)}
+            s.close()
+        out[name] = res
+    return out
 
 
 class ClockSampler:
@@ -248,9 +308,12 @@ def run_ours(args):
         the main stream has been made to wait for both."""
         start = torch.cuda.Event()
         start.record(stream)
-        futs = [pool.submit(solve_space, vname, sname, e2e, start) for sname, _, _ in SPACES]
-        for f in futs:
-            sname, info, done = f.result()
+        if args.sequential:
+            results = [solve_space(vname, sname, e2e, start) for sname, _, _ in SPACES]
+        else:
+            results = [f.result() for f in [pool.submit(solve_space, vname, sname, e2e, start)
+                                            for sname, _, _ in SPACES]]
+        for sname, info, done in results:
             stream.wait_event(done)
             stats.append((sname, info))
 
@@ -349,6 +412,7 @@ def run_ours(args):
                    "lattice_dofs_per_space": sizes, "rtol": 1e-8,
                    "variant": HEADLINE, "l2": "flushed between steps (256 MiB write)",
                    "parallelism": "independent replicas" if world > 1 else "1 GPU",
+                   "spaces": "one after another" if args.sequential else "concurrent (a stream and host thread each)",
                    "iterations": head["iterations"], "setup_s": setup_s},
         "e2e": {"value": job_value(world, args.steps, dofs, e2e_ms), "unit": "DOFs/s",
                 "h2d_bytes_per_step": 8 * dofs, "d2h_bytes_per_step": 8 * dofs},
@@ -357,6 +421,8 @@ def run_ours(args):
         "variants": {v: summarise(v) for v in VARIANTS},
         "clocks": clocks,
     }
+    if not args.no_apply_kernels:
+        line["apply_kernels"] = run_apply_kernels(args.steps, stream)
     if args.batch_count > 0:
         line["variants"]["batched"] = run_batched(args.batch_count, args.steps,
                                                   max(1, args.warmup // 2), stream)
@@ -396,8 +462,21 @@ def _oracle_sample():
 
 
 def cpu_baseline(args, budget_s=30.0):
-    from oracle.krylov import pcg
     cores = len(os.sched_getaffinity(0))
+    if args.cpu_baseline_full:
+        # the whole workload (one solve per space, set-up excluded), minutes
+        full = cpu_baseline_full()
+        v = full["value"]
+        dofs = full["runs"]["all_cores"]["dofs"]
+        print(json.dumps({
+            "metric": METRIC, "value": v, "unit": "DOFs/s", "n_gpus": world, "steps": 1, "warmup": 0,
+            "ms_per_step": 1e3 * dofs / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "lattice_dofs": dofs},
+            "cpu_baseline": full,
+            "e2e": {"value": v, "unit": "DOFs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return
+    from oracle.krylov import pcg
     sample = _oracle_sample()
     dofs = sum(s[1] for s in sample)
     t_tot, steps = 0.0, 0
@@ -415,30 +494,42 @@ def cpu_baseline(args, budget_s=30.0):
                       f"on a 3x3x3 mesh, p={DEGREE} ({dofs} lattice DOFs), {steps} step(s)"}
 
 
-def oracle_full_worker():
+def oracle_full_worker(cache):
     """The oracle's solves of the whole workload (8x8x8 mesh, p = 7, both
-    spaces): setup timed apart from the solve; one JSON line."""
+    spaces): setup timed apart from the solve; one JSON line.  The set-up
+    problems (operator, preconditioner, right-hand side) are pickled to
+    `cache` by the first run and loaded by later ones."""
+    import pickle
     from oracle.auxiliary import assemble_aux
     from oracle.discretization import Problem
     from oracle.krylov import pcg
     from oracle.relaxation import SCPAFW, SCPH
     from paper_2211_14284_gb300 import inputs
     n = N_CELLS
-    X = inputs.vertices(n, perturb=PERTURB, seed=2)
-    al = inputs.constant_coefficient(n)
-    be = inputs.constant_coefficient(n)
-    out = {"dofs": 0, "setup_s": 0.0, "solve_s": 0.0, "iterations": {}}
+    out = {"dofs": 0, "setup_s": 0.0, "solve_s": 0.0, "iterations": {}, "setup_cached": False}
     for sname, k, _ in SPACES:
+        path = os.path.join(cache, f"oracle_{sname}.pickle")
         t0 = time.time()
-        pr = Problem(k, n, DEGREE, X, al, be)
-        A = pr.A_free()
-        P = assemble_aux(pr)[pr.free][:, pr.free]
-        M = SCPAFW(pr, P, factor="icc") if k == 0 else SCPH(pr, P)
-        b = inputs.normal_rhs(pr.lat.size, 100 + k)[pr.free]
+        if os.path.exists(path):
+            with open(path, "rb") as f:
+                size, A, M, b = pickle.load(f)
+            out["setup_cached"] = True
+        else:
+            X = inputs.vertices(n, perturb=PERTURB, seed=2)
+            al = inputs.constant_coefficient(n)
+            be = inputs.constant_coefficient(n)
+            pr = Problem(k, n, DEGREE, X, al, be)
+            A = pr.A_free()
+            P = assemble_aux(pr)[pr.free][:, pr.free]
+            M = SCPAFW(pr, P, factor="icc") if k == 0 else SCPH(pr, P)
+            b = inputs.normal_rhs(pr.lat.size, 100 + k)[pr.free]
+            size = pr.lat.size
+            with open(path, "wb") as f:
+                pickle.dump((size, A, M, b), f, protocol=pickle.HIGHEST_PROTOCOL)
         t1 = time.time()
         _, info = pcg(A, b, M.apply, rtol=1e-8, flexible=True)
         t2 = time.time()
-        out["dofs"] += pr.lat.size
+        out["dofs"] += size
         out["setup_s"] += t1 - t0
         out["solve_s"] += t2 - t1
         out["iterations"][sname] = info["iterations"]
@@ -446,22 +537,24 @@ def oracle_full_worker():
 
 
 def cpu_baseline_full():
-    """The oracle on the full workload, single-threaded and with BLAS/OpenMP
-    threads on every core of this host (each in its own process)."""
+    """The oracle on the full workload, with BLAS/OpenMP threads on every
+    core of this host and single-threaded (each in its own process; the
+    second loads the first one's set-up from a scratch directory)."""
     cores = len(os.sched_getaffinity(0))
     res = {}
-    for label, th in (("1_thread", 1), ("all_cores", cores)):
-        env = dict(os.environ)
-        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-            env[v] = str(th)
-        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-full-worker"],
-                           capture_output=True, text=True, env=env)
-        if r.returncode != 0:
-            raise RuntimeError(r.stderr[-2000:])
-        d = json.loads(r.stdout.strip().splitlines()[-1])
-        d["value"] = d["dofs"] / d["solve_s"]
-        d["threads"] = th
-        res[label] = d
+    with tempfile.TemporaryDirectory() as cache:
+        for label, th in (("all_cores", cores), ("1_thread", 1)):
+            env = dict(os.environ)
+            for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+                env[v] = str(th)
+            r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-full-worker", cache],
+                               capture_output=True, text=True, env=env)
+            if r.returncode != 0:
+                raise RuntimeError(r.stderr[-2000:])
+            d = json.loads(r.stdout.strip().splitlines()[-1])
+            d["value"] = d["dofs"] / d["solve_s"]
+            d["threads"] = th
+            res[label] = d
     return {"value": res["all_cores"]["value"], "unit": "DOFs/s", "cores": cores, "kind": "oracle",
             "same_config": True, "runs": res,
             "sample": f"the whole workload (8x8x8, p={DEGREE}, H(grad)+H(curl)), setup excluded"}
@@ -471,8 +564,21 @@ def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
         return
-    from oracle.krylov import pcg
     cores = len(os.sched_getaffinity(0))
+    if args.cpu_baseline_full:
+        # the whole workload (one solve per space, set-up excluded), minutes
+        full = cpu_baseline_full()
+        v = full["value"]
+        dofs = full["runs"]["all_cores"]["dofs"]
+        print(json.dumps({
+            "metric": METRIC, "value": v, "unit": "DOFs/s", "n_gpus": world, "steps": 1, "warmup": 0,
+            "ms_per_step": 1e3 * dofs / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "lattice_dofs": dofs},
+            "cpu_baseline": full,
+            "e2e": {"value": v, "unit": "DOFs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return
+    from oracle.krylov import pcg
     sample = _oracle_sample()
     dofs = sum(s[1] for s in sample)
 
@@ -657,7 +763,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-baseline-full", action="store_true",
                     help="time the oracle on the whole workload (minutes of host setup) instead of a sample")
-    ap.add_argument("--oracle-full-worker", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-full-worker", metavar="CACHE_DIR", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--no-apply-kernels", action="store_true",
+                    help="skip timing the Cartesian operator apply on its own workloads")
+    ap.add_argument("--sequential", action="store_true",
+                    help="solve the two problems of a step one after another on one host thread "
+                         "(for profilers, which serialise kernels anyway)")
     ap.add_argument("--batch-count", type=int, default=8,
                     help="problems of the uneven H(curl) batch to time (64 = all; 0 = skip)")
     ap.add_argument("--learned-size", type=int, default=32,
@@ -666,7 +777,7 @@ def main():
                     help="training epochs of the learned coarse corrector (0 = skip that variant)")
     args = ap.parse_args()
     if args.oracle_full_worker:
-        oracle_full_worker()
+        oracle_full_worker(args.oracle_full_worker)
         return
     if args.impl == "reference":
         run_reference(args)
