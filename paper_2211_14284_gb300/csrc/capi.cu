@@ -1152,6 +1152,8 @@ int rm_solve(rm_handle *h, const double *b, double *x, rm_info *info) {
       cudaError_t te = cudaSuccess;
       if (patch_timeouts(&te)) status = RM_ERR_TIMEOUT;  // a patch kernel's bounded wait gave up
       CK(te);
+      if (h->net && rmn::conv_timeouts(&te)) status = RM_ERR_TIMEOUT;  // a tensor-core conv's wait
+      CK(te);
     }
     for (size_t j = 0; j < kinds.size(); ++j) {
       float t = 0.f;

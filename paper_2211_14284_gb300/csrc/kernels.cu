@@ -15,6 +15,7 @@
 #include <atomic>
 
 #include "df.cuh"
+#include "mbarrier.cuh"
 
 namespace rmd {
 
@@ -445,38 +446,6 @@ __global__ void patch_kernel(DevPatch F, const double *__restrict__ r, double *_
 // mbarrier is bounded: on timeout the CTA records it in g_patch_timeout,
 // waits once more (bounded) for its copies and returns without touching z.
 __device__ int g_patch_timeout = 0;
-
-__device__ __forceinline__ unsigned smem_u32(const void *p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-// true once phase `parity` of the mbarrier completed; false after ~1 s
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity) {
-  const long long t0 = clock64();
-  for (long long it = 0; it < (1LL << 26); ++it) {
-    unsigned ok;
-    asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    if (clock64() - t0 > 2000000000LL) break;
-  }
-  return false;
-}
 
 constexpr int kPatchWarpMaxWPB = 8;
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }

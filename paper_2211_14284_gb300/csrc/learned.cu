@@ -17,6 +17,7 @@
 #include "../../include/rm.h"
 #include "device.cuh"
 #include "learned.cuh"
+#include "mbarrier.cuh"
 
 namespace rmn {
 namespace {
@@ -167,15 +168,9 @@ __global__ void conv_finish_kernel(long long n, int cout, int splits, const floa
   put(out + i, v);
 }
 
-// Tensor-core form of the same convolution (output channels >= 16): an
-// implicit GEMM out[v][c_out] = sum_k A[v][k] W[c_out][k] with k = tap * c_in
-// + c_in index (K = 27 c_in), A the gathered input (im2col, built in shared
-// memory per chunk of 32 k, BF16) and mma.sync m16n8k16 BF16 -> FP32.  CTA
-// tile: 128 voxels (4 warps x 32) x BN output channels; blockIdx.z takes the
-// K chunks [z * per, (z + 1) * per) (split reduction for small grids, as in
-// conv_kernel).  Shared rows are padded to 40 BF16 (80 B) so the fragment
-// reads of the 8 row groups fall in distinct banks.
-constexpr int kMmaBM = 128, kMmaKC = 32, kMmaLd = 40;
+// mma.sync tile constants of the weight-gradient kernel (rows padded to 40
+// BF16 = 80 B so fragment reads of the 8 row groups fall in distinct banks)
+constexpr int kMmaLd = 40;
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   const uint32_t l = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
@@ -185,53 +180,141 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 __device__ __forceinline__ float tof_any(bf16 v) { return __bfloat162float(v); }
 __device__ __forceinline__ float tof_any(float v) { return v; }
 
+// ---- tcgen05 (5th-generation tensor core) helpers, inline PTX ----------------
+using rmd::mbar_init;
+using rmd::mbar_wait_bounded;
+using rmd::smem_u32;
+
+// Shared-memory matrix descriptor of a K-major BF16 operand tile without
+// swizzling: 8-row x 16-byte core matrices, LBO = byte distance between core
+// matrices adjacent along K, SBO = between 8-row groups; bits 46-48 hold the
+// descriptor version 1, swizzle mode 0.
+__device__ __forceinline__ unsigned long long tc_desc(unsigned saddr, unsigned lbo, unsigned sbo) {
+  return (unsigned long long)((saddr >> 4) & 0x3FFFu) | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ULL << 46);
+}
+// Instruction descriptor of kind::f16: FP32 accumulator (D format 1), BF16 A
+// and B (format 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr unsigned tc_idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(n >> 3) << 17) | ((unsigned)(m >> 4) << 24);
+}
+__device__ __forceinline__ void tc_mma(unsigned tmem_d, unsigned long long ad, unsigned long long bd, unsigned idesc,
+                                       unsigned accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// arrive on the mbarrier once every tcgen05.mma issued so far by this thread completed
+__device__ __forceinline__ void tc_commit(unsigned long long *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// generic-proxy shared-memory writes made visible to the tensor core's reads
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// 16 consecutive 32-bit TMEM columns of this warp's 32 lanes (row = lane)
+__device__ __forceinline__ void tc_ld16(unsigned taddr, float (&v)[16]) {
+  unsigned r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// a conv whose tensor-core waits gave up: set once, read and cleared by the host
+__device__ int g_conv_timeout = 0;
+
+// Tensor-core form of the same convolution (output channels >= 16): an
+// implicit GEMM out[v][c_out] = sum_k A[v][k] W[c_out][k] with k = tap * c_in
+// + c_in index (K = 27 c_in), A the gathered input (im2col).  Per CTA a tile
+// of 128 voxels x BN output channels accumulates in tensor memory (BN FP32
+// columns, TMEM rows = voxels) through tcgen05.mma (M = 128, N = BN, K = 16
+// per instruction, BF16 operands) issued by one thread; the threads stage
+// 64-wide K chunks of A (one voxel row each) and of W into shared memory in
+// the no-swizzle K-major core-matrix layout, double-buffered: chunk i + 1 is
+// gathered while the tensor core works on chunk i, and a buffer is rewritten
+// only after the mbarrier that tcgen05.commit arrives on says its MMAs are
+// done.  blockIdx.z takes the K chunks [z * per, (z + 1) * per) (split
+// reduction for small grids, as in conv_kernel).  Every mbarrier wait is
+// bounded; on timeout the CTA records it in g_conv_timeout, writes NaN for
+// its outputs, waits once more for its MMAs and frees its tensor memory.
+constexpr int kTcBM = 128, kTcKC = 64;
+// bytes of one buffer: A (128 rows) and B (64 rows max) chunks of 64 BF16
+constexpr int kTcABytes = kTcBM * kTcKC * 2, kTcBBytes = 64 * kTcKC * 2;
+constexpr int kTcSmem = 2 * (kTcABytes + kTcBBytes) + 128;
+
+// byte offset of element (r, k) of a rows x 64 BF16 tile: 8-row groups of
+// 1024 B, in each group 8 core matrices of 8 rows x 16 B along K
+__device__ __forceinline__ int tc_off(int r, int k) { return (r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2; }
+
 template <typename TI, typename TO, int BN>
-__global__ void __launch_bounds__(128) conv_mma_kernel(ConvArgs a, long long total, int per,
-                                                       const TI *__restrict__ in,
-                                                       const bf16 *__restrict__ W,
-                                                       const float *__restrict__ bias,
-                                                       TO *__restrict__ out, float *__restrict__ part) {
-  __shared__ __align__(16) bf16 As[kMmaBM * kMmaLd];
-  __shared__ __align__(16) bf16 Bs[BN * kMmaLd];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int g = lane >> 2, t4 = lane & 3;
-  const long long v0 = (long long)blockIdx.x * kMmaBM;
+__global__ void __launch_bounds__(128) conv_tc_kernel(ConvArgs a, long long total, int per,
+                                                      const TI *__restrict__ in, const bf16 *__restrict__ W,
+                                                      const float *__restrict__ bias, TO *__restrict__ out,
+                                                      float *__restrict__ part) {
+  static_assert(BN == 16 || BN == 32 || BN == 64, "N of the MMA tile");
+  constexpr int NCOLS = BN < 32 ? 32 : BN;  // TMEM allocation: a power of two >= 32
+  constexpr unsigned IDESC = tc_idesc_bf16(kTcBM, BN);
+  extern __shared__ __align__(128) unsigned char tsm[];
+  unsigned long long *bar = reinterpret_cast<unsigned long long *>(tsm + 2 * (kTcABytes + kTcBBytes));
+  unsigned *tmem_slot = reinterpret_cast<unsigned *>(bar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const long long v0 = (long long)blockIdx.x * kTcBM;
   const int n0 = blockIdx.y * BN;
   const int K = 27 * a.cin;
-  const int nkc = (K + kMmaKC - 1) / kMmaKC;
-  const int kc1 = min(nkc, (int)(blockIdx.z + 1) * per);
+  const int nkc = (K + kTcKC - 1) / kTcKC;
+  const int kc0 = blockIdx.z * per, kc1 = min(nkc, kc0 + per);
   const int nvo = a.dout[0] * a.dout[1] * a.dout[2];
   const long long nvi = (long long)a.din[0] * a.din[1] * a.din[2];
-  // the voxel this thread stages (one row of A per thread)
-  const long long gv = v0 + tid;
+  const long long gv = v0 + tid;  // the voxel (row of A) this thread stages
   const bool live = gv < total;
   const long long b = live ? gv / nvo : 0;
   const int vo = live ? (int)(gv - b * nvo) : 0;
   const int ox = vo % a.dout[0], oy = (vo / a.dout[0]) % a.dout[1], oz = vo / (a.dout[0] * a.dout[1]);
   const TI *base = in + b * nvi * a.cin;
-  // 16-byte staging only where every piece is aligned: c_in a multiple of 8
-  // (8 consecutive k in one tap) and 16-byte aligned tensors
   const bool avec = a.cin % 8 == 0 && (reinterpret_cast<uintptr_t>(in) & 15) == 0;
   const bool bvec = !a.transposed && a.w_si == 1 && a.cin % 8 == 0 && a.w_so % 8 == 0 &&
                     (reinterpret_cast<uintptr_t>(W) & 15) == 0;
-  float acc[2][BN / 8][4];
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(NCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    tc_fence_before();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tmem = *tmem_slot;
+  bool ok = true;
+  int issued = 0;  // chunks whose MMAs were issued and committed (the same in every thread)
+  for (int kc = kc0; kc < kc1 && ok; ++kc) {
+    const int i = kc - kc0, buf = i & 1;
+    if (i >= 2 && !mbar_wait_bounded(&bar[buf], ((i - 2) >> 1) & 1)) ok = false;  // MMAs of chunk i - 2 done
+    if (!__syncthreads_and(ok)) {
+      ok = false;
+      break;
+    }
+    const int k0 = kc * kTcKC;
+    // A: row tid, k0 .. k0 + 63 (zero outside the input, beyond K or the voxels)
+    unsigned char *As = tsm + buf * kTcABytes;
 #pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < BN / 8; ++nt)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) acc[mt][nt][r] = 0.f;
-  for (int kc = blockIdx.z * per; kc < kc1; ++kc) {
-    const int k0 = kc * kMmaKC;
-    __syncthreads();
-    // A: row tid, k0 .. k0 + 31 (zero outside the input, beyond K or the voxels)
-    if (avec) {
-      // 8 consecutive k share a tap: one source voxel, one 16-byte row piece
-      bf16 *row = As + tid * kMmaLd;
-#pragma unroll
-      for (int gq = 0; gq < kMmaKC / 8; ++gq) {
-        const int k = k0 + 8 * gq;
-        uint4 pk = make_uint4(0u, 0u, 0u, 0u);
+    for (int gq = 0; gq < kTcKC / 8; ++gq) {
+      const int k = k0 + 8 * gq;
+      uint4 pk = make_uint4(0u, 0u, 0u, 0u);
+      if (avec) {
         if (live && k < K) {
           const int tap = k / a.cin, ci = k - tap * a.cin;
           const int ix = tap_src(ox, tap % 3, a.stride, a.din[0], a.transposed);
@@ -249,104 +332,112 @@ __global__ void __launch_bounds__(128) conv_mma_kernel(ConvArgs a, long long tot
             }
           }
         }
-        *reinterpret_cast<uint4 *>(row + 8 * gq) = pk;
-      }
-    } else {
-      bf16 *row = As + tid * kMmaLd;
-#pragma unroll 4
-      for (int kk = 0; kk < kMmaKC; kk += 2) {
-        float x0 = 0.f, x1 = 0.f;
+      } else {
+        float xv[8];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int k = k0 + kk + h;
-          float xv = 0.f;
-          if (live && k < K) {
-            const int tap = k / a.cin, ci = k - tap * a.cin;
+        for (int h = 0; h < 8; ++h) {
+          const int kk = k + h;
+          xv[h] = 0.f;
+          if (live && kk < K) {
+            const int tap = kk / a.cin, ci = kk - tap * a.cin;
             const int ix = tap_src(ox, tap % 3, a.stride, a.din[0], a.transposed);
             const int iy = tap_src(oy, (tap / 3) % 3, a.stride, a.din[1], a.transposed);
             const int iz = tap_src(oz, tap / 9, a.stride, a.din[2], a.transposed);
             if (ix >= 0 && iy >= 0 && iz >= 0)
-              xv = tof_any(base[((long long)(iz * a.din[1] + iy) * a.din[0] + ix) * a.cin + ci]);
+              xv[h] = tof_any(base[((long long)(iz * a.din[1] + iy) * a.din[0] + ix) * a.cin + ci]);
           }
-          if (h == 0) x0 = xv; else x1 = xv;
         }
-        *reinterpret_cast<uint32_t *>(row + kk) = pack_bf16(x0, x1);
+        pk = make_uint4(pack_bf16(xv[0], xv[1]), pack_bf16(xv[2], xv[3]), pack_bf16(xv[4], xv[5]),
+                        pack_bf16(xv[6], xv[7]));
       }
+      *reinterpret_cast<uint4 *>(As + tc_off(tid, 8 * gq)) = pk;
     }
-    // B: BN rows (output channels) x 32 k; forward weights are contiguous in k
-    if (bvec) {
-      for (int e = tid; e < BN * (kMmaKC / 8); e += 128) {
-        const int n = e / (kMmaKC / 8), gq = e - n * (kMmaKC / 8), k = k0 + 8 * gq, co = n0 + n;
-        uint4 pk = make_uint4(0u, 0u, 0u, 0u);
-        if (co < a.cout && k < K)
-          pk = *reinterpret_cast<const uint4 *>(W + (long long)co * a.w_so + k);
-        *reinterpret_cast<uint4 *>(Bs + n * kMmaLd + 8 * gq) = pk;
+    // B: BN rows (output channels) x 64 k
+    unsigned char *Bs = tsm + 2 * kTcABytes + buf * kTcBBytes;
+    for (int e = tid; e < BN * (kTcKC / 8); e += 128) {
+      const int n = e / (kTcKC / 8), gq = e - n * (kTcKC / 8), co = n0 + n;
+      const int k = k0 + 8 * gq;
+      uint4 pk = make_uint4(0u, 0u, 0u, 0u);
+      if (bvec) {
+        if (co < a.cout && k < K) pk = *reinterpret_cast<const uint4 *>(W + (long long)co * a.w_so + k);
+      } else {
+        unsigned short w[8];
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+          const int kk = k + h;
+          bf16 wv = __float2bfloat16_rn(0.f);
+          if (co < a.cout && kk < K) {
+            const int tap = kk / a.cin, ci = kk - tap * a.cin;
+            wv = W[(long long)co * a.w_so + (long long)tap * a.w_sd + (long long)ci * a.w_si];
+          }
+          w[h] = __bfloat16_as_ushort(wv);
+        }
+        pk = make_uint4(w[0] | ((unsigned)w[1] << 16), w[2] | ((unsigned)w[3] << 16), w[4] | ((unsigned)w[5] << 16),
+                        w[6] | ((unsigned)w[7] << 16));
       }
-    } else
-    for (int e = tid; e < BN * kMmaKC; e += 128) {
-      const int n = e / kMmaKC, kk = e - n * kMmaKC, k = k0 + kk, co = n0 + n;
-      bf16 w = __float2bfloat16_rn(0.f);
-      if (co < a.cout && k < K) {
-        const int tap = k / a.cin, ci = k - tap * a.cin;
-        w = W[(long long)co * a.w_so + (long long)tap * a.w_sd + (long long)ci * a.w_si];
-      }
-      Bs[n * kMmaLd + kk] = w;
+      *reinterpret_cast<uint4 *>(Bs + tc_off(n, 8 * gq)) = pk;
     }
+    fence_async_smem();
     __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const unsigned sa = smem_u32(As), sb = smem_u32(Bs);
 #pragma unroll
-    for (int ks = 0; ks < kMmaKC; ks += 16) {
-      uint32_t af[2][4];
+      for (int ks = 0; ks < kTcKC / 16; ++ks)  // K = 16 per MMA: two core matrices along K
+        tc_mma(tmem, tc_desc(sa + 256 * ks, 128, 1024), tc_desc(sb + 256 * ks, 128, 1024), IDESC,
+               (i > 0 || ks > 0) ? 1u : 0u);
+      tc_commit(&bar[buf]);
+    }
+    issued = i + 1;
+  }
+  // the last commit covers every MMA before it
+  const int nch = kc1 - kc0;
+  if (ok && issued > 0) ok = mbar_wait_bounded(&bar[(issued - 1) & 1], ((issued - 1) >> 1) & 1);
+  ok = __syncthreads_and(ok);
+  if (!ok) {
+    if (tid == 0) atomicExch(&g_conv_timeout, 1);
+    // MMAs still in flight write this CTA's tensor memory: wait (bounded) for them
+    if (issued > 0) mbar_wait_bounded(&bar[(issued - 1) & 1], ((issued - 1) >> 1) & 1);
+  }
+  tc_fence_after();
+  // epilogue: thread tid holds row tid (TMEM lane), columns 0 .. BN - 1
+  const long long vr = v0 + tid;
+  const unsigned trow = tmem + ((unsigned)(warp * 32) << 16);
 #pragma unroll
-      for (int mt = 0; mt < 2; ++mt) {
-        const bf16 *r0 = As + (warp * 32 + mt * 16 + g) * kMmaLd + ks + 2 * t4;
-        const bf16 *r8 = r0 + 8 * kMmaLd;
-        af[mt][0] = *reinterpret_cast<const uint32_t *>(r0);
-        af[mt][1] = *reinterpret_cast<const uint32_t *>(r8);
-        af[mt][2] = *reinterpret_cast<const uint32_t *>(r0 + 8);
-        af[mt][3] = *reinterpret_cast<const uint32_t *>(r8 + 8);
-      }
+  for (int c0 = 0; c0 < BN; c0 += 16) {
+    float v[16];
+    tc_ld16(trow + c0, v);
+    tc_wait_ld();
+    if (vr < total && nch > 0) {
 #pragma unroll
-      for (int nt = 0; nt < BN / 8; ++nt) {
-        const bf16 *bp = Bs + (nt * 8 + g) * kMmaLd + ks + 2 * t4;
-        const uint32_t b0 = *reinterpret_cast<const uint32_t *>(bp);
-        const uint32_t b1 = *reinterpret_cast<const uint32_t *>(bp + 8);
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-          float *c = acc[mt][nt];
-          asm volatile(
-              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-              "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
-              : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-              : "r"(af[mt][0]), "r"(af[mt][1]), "r"(af[mt][2]), "r"(af[mt][3]), "r"(b0), "r"(b1));
+      for (int j = 0; j < 16; ++j) {
+        const int co = n0 + c0 + j;
+        if (co >= a.cout) continue;
+        const float val = ok ? v[j] : __int_as_float(0x7fc00000);
+        if (gridDim.z > 1) {
+          part[(long long)blockIdx.z * total * a.cout + vr * a.cout + co] = val;
+        } else {
+          float y = val + (bias ? bias[co] : 0.f);
+          if (a.relu) y = fmaxf(y, 0.f);
+          TO *dst = out + vr * a.cout + co;
+          if (a.accumulate) y += tof(*dst);
+          put(dst, y);
         }
+      }
+    } else if (vr < total && gridDim.z > 1) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int co = n0 + c0 + j;
+        if (co < a.cout) part[(long long)blockIdx.z * total * a.cout + vr * a.cout + co] = 0.f;
       }
     }
   }
-  // epilogue: rows warp * 32 + mt * 16 + g (+8), columns nt * 8 + 2 t4 (+1)
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int hr = 0; hr < 2; ++hr) {
-      const long long vr = v0 + warp * 32 + mt * 16 + g + 8 * hr;
-      if (vr >= total) continue;
-#pragma unroll
-      for (int nt = 0; nt < BN / 8; ++nt)
-#pragma unroll
-        for (int hc = 0; hc < 2; ++hc) {
-          const int co = n0 + nt * 8 + 2 * t4 + hc;
-          if (co >= a.cout) continue;
-          const float v = acc[mt][nt][2 * hr + hc];
-          if (gridDim.z > 1) {
-            part[(long long)blockIdx.z * total * a.cout + vr * a.cout + co] = v;
-          } else {
-            float y = v + (bias ? bias[co] : 0.f);
-            if (a.relu) y = fmaxf(y, 0.f);
-            TO *dst = out + vr * a.cout + co;
-            if (a.accumulate) y += tof(*dst);
-            put(dst, y);
-          }
-        }
-    }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS) : "memory");
+  }
 }
 
 // Arguments of the weight gradient of a forward conv (wgrad_mma_kernel).
@@ -678,23 +769,30 @@ constexpr int kSMs = 152;
 constexpr long long kSplitScratch = (4LL + 2LL) * kSMs * 128 * 64;
 
 // tensor-core path (output channels >= 16): BN = 16, 32 or 64 channels per CTA
+template <typename TI, typename TO, int BN>
+void launch_conv_tc(dim3 grid, const ConvArgs &a, long long total, int per, const TI *in, const bf16 *W,
+                    const float *bias, TO *out, float *part, cudaStream_t s) {
+  CKN(cudaFuncSetAttribute(conv_tc_kernel<TI, TO, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+  conv_tc_kernel<TI, TO, BN><<<grid, 128, kTcSmem, s>>>(a, total, per, in, W, bias, out, part);
+}
+
 template <typename TI, typename TO>
 void run_conv_mma(const ConvArgs &a, int batch, const TI *in, const bf16 *W, const float *bias,
                   TO *out, float *part, cudaStream_t s) {
   const long long total = (long long)batch * a.dout[0] * a.dout[1] * a.dout[2];
   const int bn = a.cout <= 16 ? 16 : (a.cout <= 32 ? 32 : 64);
-  const long long bxy = (long long)grid1(total, kMmaBM) * ((a.cout + bn - 1) / bn);
-  const int nkc = (27 * a.cin + kMmaKC - 1) / kMmaKC;
+  const long long bxy = (long long)grid1(total, kTcBM) * ((a.cout + bn - 1) / bn);
+  const int nkc = (27 * a.cin + kTcKC - 1) / kTcKC;
   int splits = 1;
   if (bxy < 2 * kSMs) splits = (int)std::min<long long>(nkc, (4 * kSMs + bxy - 1) / bxy);
   const int per = (nkc + splits - 1) / splits;
   splits = (nkc + per - 1) / per;
   if (splits > 1 && (long long)splits * total * a.cout > kSplitScratch)
     throw std::runtime_error("conv split scratch too small");
-  dim3 grid(grid1(total, kMmaBM), (a.cout + bn - 1) / bn, splits);
-  if (bn == 16) conv_mma_kernel<TI, TO, 16><<<grid, 128, 0, s>>>(a, total, per, in, W, bias, out, part);
-  else if (bn == 32) conv_mma_kernel<TI, TO, 32><<<grid, 128, 0, s>>>(a, total, per, in, W, bias, out, part);
-  else conv_mma_kernel<TI, TO, 64><<<grid, 128, 0, s>>>(a, total, per, in, W, bias, out, part);
+  dim3 grid(grid1(total, kTcBM), (a.cout + bn - 1) / bn, splits);
+  if (bn == 16) launch_conv_tc<TI, TO, 16>(grid, a, total, per, in, W, bias, out, part, s);
+  else if (bn == 32) launch_conv_tc<TI, TO, 32>(grid, a, total, per, in, W, bias, out, part, s);
+  else launch_conv_tc<TI, TO, 64>(grid, a, total, per, in, W, bias, out, part, s);
   CKN(cudaGetLastError());
   rmd::add_launches(1);
   if (splits > 1) {
@@ -897,6 +995,14 @@ Net *create(const NetSpec &s, uint64_t seed, cudaStream_t stream) {
 }
 
 void destroy(Net *net) { delete net; }
+
+int conv_timeouts(cudaError_t *err) {
+  int v = 0, zero = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, g_conv_timeout, sizeof(int));
+  if (e == cudaSuccess && v) e = cudaMemcpyToSymbol(g_conv_timeout, &zero, sizeof(int));
+  if (err) *err = e;
+  return e == cudaSuccess ? v : 0;
+}
 const NetSpec &spec(const Net *net) { return net->s; }
 long long num_params(const Net *net) { return net->nparams; }
 float *grads(Net *net) { return net->grad; }

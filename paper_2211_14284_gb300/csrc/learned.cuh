@@ -46,6 +46,10 @@ void forward(Net *net, int batch, const float *x, float *y);
 // After forward(): parameter gradients of sum(dy * y) (FP32, device, in
 // the parameter order) and, if dx != NULL, the input gradient.
 void backward(Net *net, const float *dy, float *dx);
+// 1 if a tensor-core convolution gave up a bounded wait since the last call
+// (its outputs are NaN; the flag is cleared), 0 otherwise; a CUDA error code
+// in *err when reading the flag fails
+int conv_timeouts(cudaError_t *err);
 float *grads(Net *net);
 // Adam (Kingma & Ba) on the FP32 master weights; refreshes the BF16 copy.
 void adam(Net *net, float lr, float beta1, float beta2, float eps);
