@@ -240,11 +240,13 @@ const char *rm_last_error(const rm_handle *h);
  * every cell an axis-aligned box) solved together with the same options.
  * The problems are set up one by one on the host (as rm_setup would) and
  * concatenated on the device into one block-diagonal system: one launch per
- * patch template (problems of equal space and p share templates), one apply
- * launch per (space, p) over a (problem, cell) work list whose CTA size is
- * picked by timing at setup, lock-step CG with per-problem scalars and
- * convergence masks, one iteration captured in a CUDA graph and replayed
- * check_every times between host reads of the convergence flags.
+ * patch template (problems of equal space and p share templates), each
+ * problem's operator apply by the Cartesian kernel pair of rm_apply (cell
+ * products, then the fixed-order assembly, whose grid per (space, p) is
+ * picked by timing at setup), lock-step CG with per-problem scalars and
+ * convergence masks (converged problems skip their cells, patches and rows),
+ * one iteration captured in a CUDA graph and replayed check_every times
+ * between host reads of the convergence flags.
  * Coarse correction: RM_COARSE_P1 (exact) or RM_COARSE_NONE. */
 typedef struct rm_batch rm_batch;
 

@@ -160,6 +160,7 @@ __global__ void __launch_bounds__(cart_threads(P)) cart_local_kernel(ApplyDev A,
   R *ls = dl + CPB * L1;         // CPB x LS: interface line sums
   __shared__ long long cbase[32][3];  // lattice index of local (0,0,0) per component
   __shared__ int cdir[32];            // Dirichlet faces: bit 2d low side, 2d+1 high side
+  if (A.done && A.done[A.prob]) return;  // a converged problem of a batch (uniform per CTA)
   const int tid = threadIdx.x;
   const int ncell = A.n[0] * A.n[1] * A.n[2];
   const int c0 = blockIdx.x * CPB;
@@ -398,6 +399,7 @@ __global__ void __launch_bounds__(256) cart_assemble_kernel(ApplyDev A, const R 
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   const int ncell = A.n[0] * A.n[1] * A.n[2];
+  const bool frozen = A.done && A.done[A.prob];  // a converged problem of a batch: y = 0
   sfor<NC0>([&](auto mc) {
     constexpr int m = decltype(mc)::value;
     constexpr bool st0 = styp(K, m, 0), st1 = styp(K, m, 1), st2 = styp(K, m, 2);
@@ -426,7 +428,7 @@ __global__ void __launch_bounds__(256) cart_assemble_kernel(ApplyDev A, const R 
       int ce1[2], ci1[2], n1, ce2[2], ci2[2], n2;
       pairs(st1, g1, A.n[1], ce1, ci1, n1);
       pairs(st2, g2, A.n[2], ce2, ci2, n2);
-      const bool rowdir = dir;
+      const bool rowdir = dir || frozen;
       // the row's (up to 4) runs in Y: cell (0, e1, e2) at local (0, i1, i2)
       // for each pair along directions 1 and 2 (warp-uniform)
       const R *base[2][2];
@@ -473,11 +475,15 @@ cudaError_t launch_cart_kpr(const ApplyDev &A, const double *x, double *y, cudaS
   cart_local_kernel<K, P, R><<<(ncell + Sh::CPB - 1) / Sh::CPB, Sh::NT, smem, s>>>(A, x, reinterpret_cast<R *>(A.Y));
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  // a grid of resident CTAs (8 per SM), each warp striding over the rows
-  int dev = 0, nsm = 152;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cart_assemble_kernel<K, P, R><<<8 * nsm, 256, 0, s>>>(A, reinterpret_cast<const R *>(A.Y), y);
+  // a grid of resident CTAs (by default 8 per SM), each warp striding over the rows
+  int grid = A.asm_grid;
+  if (grid <= 0) {
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    grid = 8 * nsm;
+  }
+  cart_assemble_kernel<K, P, R><<<grid, 256, 0, s>>>(A, reinterpret_cast<const R *>(A.Y), y);
   return cudaGetLastError();
 }
 template <int K, int P>

@@ -3,12 +3,12 @@
 // host as rm_setup would; the device objects are then concatenated into one
 // block-diagonal system: vectors back to back, SpMV matrices with offset
 // rows/columns, patch families of identical templates (same space, p and
-// family) merged into one launch, the Cartesian apply grouped by (space, p)
-// over a (problem, cell) work list.  CG runs in lock step with per-problem
-// scalars and convergence masks entirely on the device; one iteration is
-// captured in a CUDA graph and replayed `check_every` times between host
-// reads of the convergence flags.  The apply's CTA size per degree is picked
-// at setup by timing the candidates (autotuner).
+// family) merged into one launch, every problem's apply by the per-handle
+// Cartesian kernel pair on its slice of the vectors.  CG runs in lock step
+// with per-problem scalars and convergence masks entirely on the device; one
+// iteration is captured in a CUDA graph and replayed `check_every` times
+// between host reads of the convergence flags.  The assembly grid per
+// (space, degree) is picked at setup by timing the candidates (autotuner).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -183,13 +183,10 @@ bool same_template(const PatchFamily &a, const PatchFamily &b) {
 
 }  // namespace
 
+// problems of one (space, degree): the autotuner picks their assembly grid
 struct ApplyGroup {
   int k = 0, p = 0;
-  ApplyDev *descs = nullptr;  // device array
-  int2 *work = nullptr;       // device (problem-in-group, cell)
-  int nwork = 0;
-  int threads = kApplyThreads;
-  size_t smem = 0;
+  std::vector<int> probs;
 };
 
 struct rm_batch {
@@ -210,6 +207,7 @@ struct rm_batch {
   long long N = 0, N0 = 0, NC = 0;
   std::vector<void *> allocs;
   std::vector<ApplyGroup> groups;
+  std::vector<ApplyDev> capply;  // per problem: the Cartesian apply (cell products + assembly)
   uint8_t *mask = nullptr;
   DevCsr Binv, E, Et, Dt, DtT, R0, R0T;
   std::vector<DevPatch> fam, pfam;
@@ -314,10 +312,11 @@ int bfail(rm_batch *b, int code, const std::string &msg) {
   return code;
 }
 
+// y = A x for every problem: the per-handle Cartesian kernel pair on each
+// problem's slice of the concatenated vectors (every entry written; a
+// converged problem's cells are skipped and its entries set to 0)
 void batch_apply(rm_batch *B, const double *x, double *y) {
-  BK(cudaMemsetAsync(y, 0, B->N * sizeof(double), B->stream));
-  for (auto &g : B->groups)
-    BK(launch_apply_batch(g.descs, g.work, g.nwork, g.threads, g.smem, x, y, B->done, B->stream));
+  for (const ApplyDev &A : B->capply) BK(launch_apply_cart(A, x, y, B->stream));
 }
 
 // z = B r for every problem: the condensation on the batch stream, then the
@@ -439,7 +438,7 @@ int rm_batch_setup(rm_batch **out, int nprob, const int *space, const rm_mesh *m
         for (int l : H[i].fm.free2lat) mask[B->off[i] + l] = 0;
       B->mask = B->upload(mask);
     }
-    // ---- apply groups by (space, p) ----
+    // ---- the Cartesian apply of every problem, grouped by (space, p) ----
     {
       std::map<std::pair<int, int>, std::vector<int>> byp;
       for (int i = 0; i < nprob; ++i) byp[{H[i].k, H[i].p}].push_back(i);
@@ -447,57 +446,56 @@ int rm_batch_setup(rm_batch **out, int nprob, const int *space, const rm_mesh *m
         ApplyGroup g;
         g.k = kv.first.first;
         g.p = kv.first.second;
-        std::vector<ApplyDev> descs;
-        std::vector<int2> work;
-        for (int gi = 0; gi < (int)kv.second.size(); ++gi) {
-          const HostProb &P = H[kv.second[gi]];
-          const long long voff = B->off[kv.second[gi]];
-          ApplyDev A{};
-          Layout L1(P.k + 1, P.n, P.p);
-          A.k = P.k;
-          A.p = P.p;
-          A.q = quad_points(P.p);
-          A.prob = kv.second[gi];
-          A.arith = o.arith == RM_ARITH_DF64 ? 1 : 0;
-          for (int d = 0; d < 3; ++d) A.n[d] = P.n[d];
-          A.nc0 = P.L.ncomp;
-          A.nc1 = L1.ncomp;
-          for (int m = 0; m < 3; ++m)
-            for (int d = 0; d < 3; ++d) {
-              A.N[m][d] = (int)P.L.N[m][d];
-              A.ld0[m][d] = P.L.ld[m][d];
-              A.ld1[m][d] = L1.ld[m][d];
-              A.t0[m][d] = P.L.t[m][d];
-              A.t1[m][d] = L1.t[m][d];
-            }
-          for (int m = 0; m < 3; ++m) A.off[m] = P.L.off[m] + voff;
-          for (int m = 0; m < 4; ++m) {
-            A.loff0[m] = P.L.loff[m];
-            A.loff1[m] = L1.loff[m];
-          }
-          A.nloc0 = P.L.nloc;
-          A.nloc1 = L1.nloc;
-          A.alpha = B->upload(P.al);
-          A.beta = B->upload(P.be);
-          // the Cartesian kernel reads D-hat at offset q(p+1) + qp of tabs
-          std::vector<double> tabs((size_t)A.q * (P.p + 1) + (size_t)A.q * P.p, 0.0);
-          tabs.insert(tabs.end(), P.D1.begin(), P.D1.end());
-          A.tabs = B->upload(tabs);
-          A.cartesian = 1;
-          A.h = B->upload(P.hcell);
-          A.bh_a = P.bh_a;
-          A.bh_b = P.bh_b;
-          A.cidx = B->upload(cart_index_table(A.k, P.p));
-          descs.push_back(A);
-          const int ncell = P.n[0] * P.n[1] * P.n[2];
-          for (int c = 0; c < ncell; ++c) work.push_back(make_int2(gi, c));
-          g.smem = std::max(g.smem, cart_smem_doubles(A.k, P.p, A.nloc0, A.nloc1) * sizeof(double));
-        }
-        if (g.smem > 227 * 1024) throw std::invalid_argument("degree too high for the Cartesian apply kernel");
-        g.descs = B->upload(descs);
-        g.work = B->upload(work);
-        g.nwork = (int)work.size();
+        g.probs = kv.second;
         B->groups.push_back(g);
+      }
+      B->capply.resize(nprob);
+      for (int i = 0; i < nprob; ++i) {
+        const HostProb &P = H[i];
+        ApplyDev A{};
+        Layout L1(P.k + 1, P.n, P.p);
+        A.k = P.k;
+        A.p = P.p;
+        A.q = quad_points(P.p);
+        A.prob = i;
+        A.arith = o.arith == RM_ARITH_DF64 ? 1 : 0;
+        for (int d = 0; d < 3; ++d) A.n[d] = P.n[d];
+        A.nc0 = P.L.ncomp;
+        A.nc1 = L1.ncomp;
+        for (int m = 0; m < 3; ++m)
+          for (int d = 0; d < 3; ++d) A.N[m][d] = (int)P.L.N[m][d];
+        for (int m = 0; m < 3; ++m) A.off[m] = P.L.off[m] + B->off[i];
+        A.nloc0 = P.L.nloc;
+        A.nloc1 = L1.nloc;
+        // the Cartesian kernel reads D-hat at offset q(p+1) + qp of tabs
+        std::vector<double> tabs((size_t)A.q * (P.p + 1) + (size_t)A.q * P.p, 0.0);
+        tabs.insert(tabs.end(), P.D1.begin(), P.D1.end());
+        A.tabs = B->upload(tabs);
+        A.cartesian = 1;
+        A.bh_a = P.bh_a;
+        A.bh_b = P.bh_b;
+        const int ncell = P.n[0] * P.n[1] * P.n[2];
+        // per cell: beta x the box metric of each V^k component, alpha x that
+        // of each V^{k+1} component (J = diag(h/2); the pullbacks of Sec. 3.1)
+        std::vector<double> cc((size_t)ncell * 8, 0.0);
+        auto box_metric = [](int kk, int m, const double *hh) {
+          const double det = 0.125 * hh[0] * hh[1] * hh[2];
+          if (kk == 0) return det;
+          if (kk == 3) return 1.0 / det;
+          if (kk == 1) return det * 4.0 / (hh[m] * hh[m]);
+          return 0.25 * hh[m] * hh[m] / det;
+        };
+        const int nc0 = P.k == 0 ? 1 : 3, nc1 = P.k == 2 ? 1 : 3;
+        for (int c = 0; c < ncell; ++c) {
+          const double *hh = &P.hcell[3 * (size_t)c];
+          for (int m = 0; m < nc0; ++m) cc[(size_t)c * 8 + m] = P.be[c] * box_metric(P.k, m, hh);
+          for (int t = 0; t < nc1; ++t) cc[(size_t)c * 8 + 3 + t] = P.al[c] * box_metric(P.k + 1, t, hh);
+        }
+        A.ccoef = B->upload(cc);
+        if (cart_local_smem_doubles(A.k, A.p, A.nloc0, A.nloc1) * sizeof(double) > 227 * 1024)
+          throw std::invalid_argument("degree too high for the Cartesian apply kernel");
+        A.Y = B->dalloc<double>((size_t)ncell * A.nloc0);  // unassembled cell products
+        B->capply[i] = A;
       }
     }
     // ---- static condensation, Hiptmair gradient, coarse (concatenated) ----
@@ -621,32 +619,46 @@ int rm_batch_setup(rm_batch **out, int nprob, const int *space, const rm_mesh *m
     for (DevCsr *M : {&B->Binv, &B->E, &B->Et, &B->Dt, &B->DtT, &B->R0, &B->R0T}) M->done = B->done;
     for (auto &F : B->fam) F.done = B->done;
     for (auto &F : B->pfam) F.done = B->done;
+    for (auto &A : B->capply) A.done = B->done;
     B->iters = B->dalloc<int>(nprob);
     BK(cudaMallocHost((void **)&B->hdone, nprob * sizeof(int)));
     BK(cudaMallocHost((void **)&B->hscal, (size_t)nprob * S_COUNT * sizeof(double)));
-    // ---- autotuner: CTA size of the apply per (space, p) group ----
+    // ---- autotuner: grid of the Cartesian assembly per (space, p) group ----
+    // (the cell-product kernel's shape per degree is fixed at compile time
+    // by its lane-use rule; the assembly grid is timed here: 2 to 16 CTAs
+    // per SM, the fastest kept for every problem of the group)
     BK(cudaMemsetAsync(B->pv, 0, B->N * sizeof(double), B->stream));
-    cudaEvent_t e0, e1;
-    BK(cudaEventCreate(&e0));
-    BK(cudaEventCreate(&e1));
-    for (auto &g : B->groups) {
-      float best = 1e30f;
-      int bestt = kApplyThreads;
-      for (int t : {64, 128, 256}) {
-        BK(launch_apply_batch(g.descs, g.work, g.nwork, t, g.smem, B->pv, B->qv, B->done, B->stream));
-        BK(cudaEventRecord(e0, B->stream));
-        for (int rep = 0; rep < 3; ++rep)
-          BK(launch_apply_batch(g.descs, g.work, g.nwork, t, g.smem, B->pv, B->qv, B->done, B->stream));
-        BK(cudaEventRecord(e1, B->stream));
-        BK(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        BK(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) { best = ms; bestt = t; }
+    BK(cudaMemsetAsync(B->done, 0, nprob * sizeof(int), B->stream));
+    {
+      cudaEvent_t e0, e1;
+      BK(cudaEventCreate(&e0));
+      BK(cudaEventCreate(&e1));
+      int dev = 0, nsm = 152;
+      BK(cudaGetDevice(&dev));
+      BK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+      for (auto &g : B->groups) {
+        float best = 1e30f;
+        int bestg = 8 * nsm;
+        for (int per : {2, 4, 8, 16}) {
+          for (int i : g.probs) B->capply[i].asm_grid = per * nsm;
+          for (int i : g.probs) BK(launch_apply_cart(B->capply[i], B->pv, B->qv, B->stream));
+          BK(cudaEventRecord(e0, B->stream));
+          for (int rep = 0; rep < 3; ++rep)
+            for (int i : g.probs) BK(launch_apply_cart(B->capply[i], B->pv, B->qv, B->stream));
+          BK(cudaEventRecord(e1, B->stream));
+          BK(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          BK(cudaEventElapsedTime(&ms, e0, e1));
+          if (ms < best) {
+            best = ms;
+            bestg = per * nsm;
+          }
+        }
+        for (int i : g.probs) B->capply[i].asm_grid = bestg;
       }
-      g.threads = bestt;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     // ---- capture one lock-step iteration in a CUDA graph ----
     batch_iteration(B.get(), 0.0);  // warm-up: sets kernel attributes before capture
     BK(cudaStreamSynchronize(B->stream));

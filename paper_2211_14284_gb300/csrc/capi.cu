@@ -356,7 +356,6 @@ void build_apply(rm_handle *h, const Geometry &geo, const std::vector<double> &a
     }
     A.cartesian = cart ? 1 : 0;
     if (cart) {
-      A.h = h->upload(hc);
       A.bh_a = B.Bhat[0];
       A.bh_b = B.Bhat[p];
       const size_t smem = cart_local_smem_doubles(h->k, p, A.nloc0, A.nloc1);

@@ -6,7 +6,6 @@
 
 namespace rmd {
 
-constexpr int kApplyThreads = 256;
 // general-cell apply: 512 threads, two CTAs (32 warps) per SM to hide the
 // shared-memory latency of the contraction chains
 constexpr int kApplyThreadsGeneral = 512;
@@ -29,18 +28,19 @@ struct ApplyDev {
   const void *G;           // pullback weights per cell and point (metric_kernel),
                            // in the general apply's number type (double-float)
   int nA, nAB;             // entries of stage A, of both stages (1 or 6 each)
-  // Cartesian fast path (every cell an axis-aligned box): cell sizes
-  // h[3 * cell + d] and the 1D factors of B-hat (a = B_00 = B_pp, b = B_0p)
+  // Cartesian fast path (every cell an axis-aligned box): the 1D factors
+  // of B-hat (a = B_00 = B_pp, b = B_0p)
   int cartesian;
-  const double *h;
   double bh_a, bh_b;
-  const int *cidx;         // cart_index_table(k, p) (batched apply)
   double *Y;               // unassembled cell products, [component][cell][local entry] (Cartesian apply)
   const double *ccoef;     // per cell: beta x box metric of V^k (3), alpha x box metric
                            // of V^{k+1} (3), 2 unused (Cartesian apply; setup-time FP64)
   int prob;                // batched solves: the problem's index
   int arith;               // number type of the apply: 0 double, 1 double-float (DF)
   int natural;             // 1: Gamma_D empty (no Dirichlet entries)
+  const int *done = nullptr;  // batched solves: convergence flags (problem prob skipped
+                              // by the Cartesian apply once set; its y entries are 0)
+  int asm_grid = 0;        // CTAs of the Cartesian assembly (0: 8 per SM)
 };
 
 // s-type test of component m of V^kk in direction d (Sec. 2.4): H(grad) all
@@ -49,31 +49,6 @@ __host__ __device__ constexpr bool styp(int kk, int m, int d) {
   return kk == 0 ? true : (kk == 3 ? false : (kk == 1 ? d != m : d == m));
 }
 __host__ __device__ constexpr int ncomp(int kk) { return (kk == 0 || kk == 3) ? 1 : 3; }
-
-// Local indices of a Cartesian cell block, packed i0 | i1 << 8 | i2 << 16 |
-// m << 24: the elements of V^k, then those of V^{k+1}, components one
-// after another (each of the same size).  Within a component the elements
-// are grouped by which directions put them on the interface {0, p} of an
-// s-type direction, so the threads of a warp take the same branches.
-inline std::vector<int> cart_index_table(int k, int p) {
-  std::vector<int> t;
-  for (int kk = k; kk <= k + 1; ++kk)
-    for (int m = 0; m < ncomp(kk); ++m) {
-      const int l0 = styp(kk, m, 0) ? p + 1 : p, l1 = styp(kk, m, 1) ? p + 1 : p,
-                l2 = styp(kk, m, 2) ? p + 1 : p;
-      for (int sig = 0; sig < 8; ++sig)
-        for (int i2 = 0; i2 < l2; ++i2)
-          for (int i1 = 0; i1 < l1; ++i1)
-            for (int i0 = 0; i0 < l0; ++i0) {
-              const int ii[3] = {i0, i1, i2};
-              int s = 0;
-              for (int d = 0; d < 3; ++d)
-                if (styp(kk, m, d) && (ii[d] == 0 || ii[d] == p)) s |= 1 << d;
-              if (s == sig) t.push_back(i0 | i1 << 8 | i2 << 16 | m << 24);
-            }
-    }
-  return t;
-}
 
 // Reflection split of a 1D tabulation T (q points x n functions, row-major)
 // at the symmetric GLL points x_{q-1-o} = -x_o.  Each function reflects
@@ -242,13 +217,6 @@ __host__ __device__ constexpr size_t cart_local_smem_doubles(int k, int p, int n
          (size_t)cart_cpb(p) * (8 + (size_t)nloc0 + (size_t)nloc1 + (size_t)(k == 1 ? 6 : 3) * 2 * (p + 1) * (p + 1));
 }
 
-// Shared memory of the batched Cartesian apply (doubles): D-hat, x and y on
-// V^k, d and dy on V^{k+1}, and the interface line sums of every D-hat term.
-inline size_t cart_smem_doubles(int k, int p, int nloc0, int nloc1) {
-  return (size_t)p * (p + 1) + 2 * (size_t)nloc0 + 2 * (size_t)nloc1 +
-         (size_t)(k == 1 ? 6 : 3) * 2 * (p + 1) * (p + 1);
-}
-
 // Compressed sparse rows with explicit row ids (lattice or compact).
 // Threads per row of the CSR SpMV for an average row length avg: each
 // lane takes about four entries (their loads in flight together), few warps
@@ -352,9 +320,6 @@ cudaError_t launch_update_p(long long n, double *p, const double *z, const doubl
                             cudaStream_t s);
 
 // batched solver (batch.cu)
-cudaError_t launch_apply_batch(const ApplyDev *descs, const int2 *work, int nwork, int threads,
-                               size_t smem, const double *x, double *y, const int *done,
-                               cudaStream_t s);
 cudaError_t launch_seg_dot(const int4 *chunk, int nchunk, const int *cptr, int nprob, const double *a,
                            const double *b, double *partial, double *scal, int *done, int *iters,
                            int slot, int op, double tol2, cudaStream_t s);

@@ -25,243 +25,6 @@ void add_launches(long long k) { g_launches += k; }
 
 namespace {
 
-// ---------------------------------------------------------------------------
-// Cartesian cells (axis-aligned boxes with constant alpha, beta): the cell
-// matrix is a Kronecker sum of the 1D FDM factors (Sec. 2.2-2.4).  The mass
-// of V^kk is c_m (x)_d F_d per component m, F_d = B-hat (s-type) or I
-// (r-type), with the box metric c_m; the derivative term is
-// D-hat^T (alpha M^{k+1}) D-hat.  B-hat is the identity on the interior plus
-// a 2x2 block on {0, p}; a row of D-hat has at most three nonzeros.  No
-// quadrature is needed (~30 flops per DOF).
-
-// Box metric of kk-forms, component m (J = diag(h/2)).
-__device__ __forceinline__ double box_metric(int kk, int m, double h0, double h1, double h2) {
-  const double det = 0.125 * h0 * h1 * h2;
-  const double hm = m == 0 ? h0 : (m == 1 ? h1 : h2);
-  if (kk == 0) return det;
-  if (kk == 3) return 1.0 / det;
-  if (kk == 1) return det * 4.0 / (hm * hm);
-  return 0.25 * hm * hm / det;
-}
-
-// (x)_d F_d applied to one component at local index (i0, i1, i2), F_d =
-// B-hat (s-type) or I (r-type): an s-type index on the interface {0, p}
-// couples to itself with weight a and to the opposite interface index p - i
-// with weight b; any other index only to itself.  Evaluated direction by
-// direction, so an interior element costs no arithmetic and each interface
-// direction one multiply-add pair.
-template <typename R>
-__device__ __forceinline__ R mass_at(const R *__restrict__ in, bool s0, bool s1, bool s2, int i0,
-                                     int i1, int i2, int l0, int l1, int p, R a, R b) {
-  const bool t0 = s0 && (i0 == 0 || i0 == p), t1 = s1 && (i1 == 0 || i1 == p),
-             t2 = s2 && (i2 == 0 || i2 == p);
-  const int o0 = p - i0, o1 = p - i1, o2 = p - i2;
-  auto line = [&](const R *row) { return t0 ? rfma(b, row[o0], rmul(a, row[i0])) : row[i0]; };
-  auto plane = [&](int j2) {
-    const R *base = in + l0 * l1 * j2;
-    const R v = line(base + l0 * i1);
-    return t1 ? rfma(b, line(base + l0 * o1), rmul(a, v)) : v;
-  };
-  const R v = plane(i2);
-  return t2 ? rfma(b, plane(o2), rmul(a, v)) : v;
-}
-
-// One Cartesian cell c of the problem described by P, form degree K (shared
-// by the single and the batched kernels; the batched one bakes each
-// problem's offset in the concatenated vectors into P.off).  Every
-// component of V^kk has the same local size on a cell, so component m of a
-// cell block starts at m * size.  The cell matrix is a Kronecker sum of the
-// 1D FDM factors (Sec. 2.2-2.4): the mass of V^kk is c_m (x)_d F_d per
-// component with the box metric c_m, the derivative term D-hat^T
-// (alpha M^{k+1}) D-hat; a row of D-hat has at most three nonzeros (columns
-// 0, p and its own index).  No quadrature (~30 flops per DOF).
-template <int K, typename R>
-__device__ void cart_cell_k(const ApplyDev &P, const int c, const double *__restrict__ x,
-                            double *__restrict__ y) {
-  constexpr int NC0 = ncomp(K), NC1 = ncomp(K + 1);
-  extern __shared__ double smd[];
-  R *sm = reinterpret_cast<R *>(smd);
-  const int p = P.p, q1 = p + 1;
-  const int tid = threadIdx.x, NT = blockDim.x;
-  const int n0 = P.n[0], n1 = P.n[1], n2 = P.n[2];
-  const int e0 = c % n0, e1 = (c / n0) % n1, e2 = c / (n0 * n1);
-  const double h0 = P.h[3 * c], h1 = P.h[3 * c + 1], h2 = P.h[3 * c + 2];
-  const double al = P.alpha[c], be = P.beta[c];
-  const R ba = rfrom<R>(P.bh_a), bb = rfrom<R>(P.bh_b);
-  // coefficient x box metric per component, once per thread (not per element)
-  const R cm00 = rfrom<R>(be * box_metric(K, 0, h0, h1, h2));
-  const R cm01 = rfrom<R>(NC0 > 1 ? be * box_metric(K, 1, h0, h1, h2) : 0.0);
-  const R cm02 = rfrom<R>(NC0 > 1 ? be * box_metric(K, 2, h0, h1, h2) : 0.0);
-  const R cm10 = rfrom<R>(al * box_metric(K + 1, 0, h0, h1, h2));
-  const R cm11 = rfrom<R>(NC1 > 1 ? al * box_metric(K + 1, 1, h0, h1, h2) : 0.0);
-  const R cm12 = rfrom<R>(NC1 > 1 ? al * box_metric(K + 1, 2, h0, h1, h2) : 0.0);
-  // local size of every component of V^K and V^{K+1}
-  constexpr int NS0 = K == 0 ? 3 : (K == 1 ? 2 : 1), NS1 = NS0 - 1;
-  int sz0 = 1, sz1 = 1;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    sz0 *= d < NS0 ? q1 : p;
-    sz1 *= d < NS1 ? q1 : p;
-  }
-  // D-hat terms: (target t, term s) -> line sums of the interface columns
-  constexpr int NTERMS = K == 1 ? 6 : 3;
-  const int lmax = q1 * q1;
-  R *D1 = sm;
-  R *xl = D1 + p * q1;
-  R *yl = xl + NC0 * sz0;
-  R *dl = yl + NC0 * sz0;
-  R *dyl = dl + NC1 * sz1;
-  R *ls = dyl + NC1 * sz1;  // NTERMS x lmax x 2
-  {
-    const double *g = P.tabs + P.q * q1 + P.q * p;
-    for (int i = tid; i < p * q1; i += NT) D1[i] = rfrom<R>(g[i]);
-  }
-  const long long off0 = P.off[0], off1 = NC0 > 1 ? P.off[1] : 0, off2 = NC0 > 1 ? P.off[2] : 0;
-  const int *tab0 = P.cidx, *tab1 = P.cidx + NC0 * sz0;
-  // gather (Dirichlet entries read as 0)
-  for (int l = tid; l < NC0 * sz0; l += NT) {
-    const int pk = __ldg(tab0 + l);
-    const int m = pk >> 24, i0 = pk & 255, i1 = (pk >> 8) & 255, i2 = (pk >> 16) & 255;
-    const bool s0 = styp(K, m, 0), s1 = styp(K, m, 1), s2 = styp(K, m, 2);
-    const int l0 = s0 ? q1 : p, l1 = s1 ? q1 : p;
-    const int g0 = e0 * p + i0, g1 = e1 * p + i1, g2 = e2 * p + i2;
-    const bool dir = !P.natural && ((s0 && (g0 == 0 || g0 == n0 * p)) || (s1 && (g1 == 0 || g1 == n1 * p)) ||
-                     (s2 && (g2 == 0 || g2 == n2 * p)));
-    const long long N0 = (long long)n0 * p + s0, N1 = (long long)n1 * p + s1;
-    const long long off = m == 0 ? off0 : (m == 1 ? off1 : off2);
-    xl[m * sz0 + i0 + l0 * (i1 + l1 * i2)] = rfrom<R>(dir ? 0.0 : x[off + g0 + N0 * (g1 + N1 * g2)]);
-  }
-  __syncthreads();
-  // y = beta M^K x;  d = D-hat x (component t of V^{K+1})
-  for (int l = tid; l < NC0 * sz0; l += NT) {
-    const int pk = __ldg(tab0 + l);
-    const int m = pk >> 24, i0 = pk & 255, i1 = (pk >> 8) & 255, i2 = (pk >> 16) & 255;
-    const bool s0 = styp(K, m, 0), s1 = styp(K, m, 1), s2 = styp(K, m, 2);
-    const int l0 = s0 ? q1 : p, l1 = s1 ? q1 : p;
-    yl[m * sz0 + i0 + l0 * (i1 + l1 * i2)] =
-        rmul(m == 0 ? cm00 : (m == 1 ? cm01 : cm02),
-             mass_at(xl + m * sz0, s0, s1, s2, i0, i1, i2, l0, l1, p, ba, bb));
-  }
-  for (int l = tid; l < NC1 * sz1; l += NT) {
-    const int pk = __ldg(tab1 + l);
-    const int t = pk >> 24, j0 = pk & 255, j1 = (pk >> 8) & 255, j2 = (pk >> 16) & 255;
-    const bool s0 = styp(K + 1, t, 0), s1 = styp(K + 1, t, 1);
-    const int l0 = s0 ? q1 : p, l1 = s1 ? q1 : p;
-    R sacc = rzero(R());
-    for (int s = 0; s < c_nterms[K][t]; ++s) {
-      const int src = c_terms[K][t][s].src, dr = c_terms[K][t][s].dir, sg = c_terms[K][t][s].sgn;
-      // the source component is s-type along dr (p+1 entries) and equal to
-      // the target elsewhere
-      const int sl0 = dr == 0 ? q1 : l0, sl1 = dr == 1 ? q1 : l1;
-      const R *in = xl + src * sz0;
-      const int j = dr == 0 ? j0 : (dr == 1 ? j1 : j2);
-      const int str = dr == 0 ? 1 : (dr == 1 ? sl0 : sl0 * sl1);
-      const int base = (dr == 0 ? 0 : j0) + sl0 * ((dr == 1 ? 0 : j1) + sl1 * (dr == 2 ? 0 : j2));
-      R v = rmul(D1[j * q1], in[base]);
-      v = rfma(D1[j * q1 + p], in[base + p * str], v);
-      if (j >= 1) v = rfma(D1[j * q1 + j], in[base + j * str], v);
-      sacc = sg > 0 ? radd(sacc, v) : rsub(sacc, v);
-    }
-    dl[t * sz1 + j0 + l0 * (j1 + l1 * j2)] = sacc;
-  }
-  __syncthreads();
-  // dy = alpha M^{K+1} d
-  for (int l = tid; l < NC1 * sz1; l += NT) {
-    const int pk = __ldg(tab1 + l);
-    const int t = pk >> 24, j0 = pk & 255, j1 = (pk >> 8) & 255, j2 = (pk >> 16) & 255;
-    const bool s0 = styp(K + 1, t, 0), s1 = styp(K + 1, t, 1), s2 = styp(K + 1, t, 2);
-    const int l0 = s0 ? q1 : p, l1 = s1 ? q1 : p;
-    dyl[t * sz1 + j0 + l0 * (j1 + l1 * j2)] =
-        rmul(t == 0 ? cm10 : (t == 1 ? cm11 : cm12),
-             mass_at(dl + t * sz1, s0, s1, s2, j0, j1, j2, l0, l1, p, ba, bb));
-  }
-  __syncthreads();
-  // line sums of D-hat^T's interface rows: for every term (t, s) and every
-  // line of component t along the term's direction dr,
-  //   ls[0] = sum_j D-hat[j][0] dy[j],  ls[1] = sum_j D-hat[j][p] dy[j]
-  // (one thread per line: the same 2p FMAs in every lane)
-  for (int u = tid; u < NTERMS * lmax; u += NT) {
-    const int ts = u / lmax, line = u - ts * lmax;
-    const int t = K == 1 ? ts >> 1 : (K == 0 ? ts : 0), s = K == 1 ? ts & 1 : (K == 0 ? 0 : ts);
-    const int dr = c_terms[K][t][s].dir;
-    const bool s0 = styp(K + 1, t, 0), s1 = styp(K + 1, t, 1), s2 = styp(K + 1, t, 2);
-    const int l0 = s0 ? q1 : p, l1 = s1 ? q1 : p, l2 = s2 ? q1 : p;
-    const int la = dr == 0 ? l1 : l0, lb = dr == 2 ? l1 : l2;  // the two other dims
-    if (line >= la * lb) continue;
-    const int a = line % la, b = line / la;
-    const int c0 = dr == 0 ? 0 : a, c1 = dr == 0 ? a : (dr == 1 ? 0 : b), c2 = dr == 2 ? 0 : b;
-    const int str = dr == 0 ? 1 : (dr == 1 ? l0 : l0 * l1);
-    const R *in = dyl + t * sz1 + c0 + l0 * (c1 + l1 * c2);
-    R v0 = rzero(R()), vp = rzero(R());
-    for (int j = 0; j < p; ++j) {
-      const R dj = in[j * str];
-      v0 = rfma(D1[j * q1], dj, v0);
-      vp = rfma(D1[j * q1 + p], dj, vp);
-    }
-    ls[2 * u] = v0;
-    ls[2 * u + 1] = vp;
-  }
-  __syncthreads();
-  // y += D-hat^T dy; scatter-add (Dirichlet rows skipped)
-  for (int l = tid; l < NC0 * sz0; l += NT) {
-    const int pk = __ldg(tab0 + l);
-    const int m = pk >> 24, i0 = pk & 255, i1 = (pk >> 8) & 255, i2 = (pk >> 16) & 255;
-    const bool s0 = styp(K, m, 0), s1 = styp(K, m, 1), s2 = styp(K, m, 2);
-    const int l0 = s0 ? q1 : p, l1 = s1 ? q1 : p;
-    R sacc = yl[m * sz0 + i0 + l0 * (i1 + l1 * i2)];
-#pragma unroll
-    for (int ts = 0; ts < NTERMS; ++ts) {
-      const int t = K == 1 ? ts >> 1 : (K == 0 ? ts : 0), s = K == 1 ? ts & 1 : (K == 0 ? 0 : ts);
-      if (c_terms[K][t][s].src != m) continue;
-      const int dr = c_terms[K][t][s].dir, sg = c_terms[K][t][s].sgn;
-      // the target component is r-type along dr (p entries), equal elsewhere
-      const int tl0 = dr == 0 ? p : l0, tl1 = dr == 1 ? p : l1;
-      const int i = dr == 0 ? i0 : (dr == 1 ? i1 : i2);
-      R v;
-      if (i == 0 || i == p) {
-        const int a = dr == 0 ? i1 : i0, b = dr == 2 ? i1 : i2;
-        const int la = dr == 0 ? tl1 : tl0;
-        v = ls[2 * (ts * lmax + a + la * b) + (i == 0 ? 0 : 1)];
-      } else {
-        const int str = dr == 0 ? 1 : (dr == 1 ? tl0 : tl0 * tl1);
-        const int base = (dr == 0 ? 0 : i0) + tl0 * ((dr == 1 ? 0 : i1) + tl1 * (dr == 2 ? 0 : i2));
-        v = rmul(D1[i * q1 + i], dyl[t * sz1 + base + i * str]);
-      }
-      sacc = sg > 0 ? radd(sacc, v) : rsub(sacc, v);
-    }
-    const int g0 = e0 * p + i0, g1 = e1 * p + i1, g2 = e2 * p + i2;
-    const bool dir = !P.natural && ((s0 && (g0 == 0 || g0 == n0 * p)) || (s1 && (g1 == 0 || g1 == n1 * p)) ||
-                     (s2 && (g2 == 0 || g2 == n2 * p)));
-    if (!dir) {
-      const long long N0 = (long long)n0 * p + s0, N1 = (long long)n1 * p + s1;
-      const long long off = m == 0 ? off0 : (m == 1 ? off1 : off2);
-      atomicAdd(&y[off + g0 + N0 * (g1 + N1 * g2)], rto(sacc));
-    }
-  }
-}
-
-// Batched: work[b] = (problem, cell); descriptors in global memory.
-__global__ void __launch_bounds__(kApplyThreads) apply_cart_batch_kernel(const ApplyDev *__restrict__ descs,
-                                                                         const int2 *__restrict__ work,
-                                                                         const double *__restrict__ x,
-                                                                         double *__restrict__ y,
-                                                                         const int *__restrict__ done) {
-  __shared__ ApplyDev Ps;
-  const int2 w = work[blockIdx.x];
-  if (threadIdx.x == 0) Ps = descs[w.x];
-  __syncthreads();
-  if (done && done[Ps.prob]) return;  // converged problem: its y stays 0
-  if (Ps.arith) {
-    if (Ps.k == 0) cart_cell_k<0, DF>(Ps, w.y, x, y);
-    else if (Ps.k == 1) cart_cell_k<1, DF>(Ps, w.y, x, y);
-    else cart_cell_k<2, DF>(Ps, w.y, x, y);
-  } else {
-    if (Ps.k == 0) cart_cell_k<0, double>(Ps, w.y, x, y);
-    else if (Ps.k == 1) cart_cell_k<1, double>(Ps, w.y, x, y);
-    else cart_cell_k<2, double>(Ps, w.y, x, y);
-  }
-}
-
 // One damped Jacobi sweep of the coarse multigrid: x_out = x_in + w (b - A x_in),
 // w = omega / diag(A) (FP64 CSR, TPR threads per row).
 template <int TPR>
@@ -1041,17 +804,6 @@ cudaError_t launch_update_xr(long long n, double *x, double *r, const double *p,
 
 cudaError_t launch_update_p(long long n, double *p, const double *z, const double *scal, cudaStream_t s) {
   update_p_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, p, z, scal);
-  g_launches += 1;
-  return cudaGetLastError();
-}
-
-cudaError_t launch_apply_batch(const ApplyDev *descs, const int2 *work, int nwork, int threads,
-                               size_t smem, const double *x, double *y, const int *done,
-                               cudaStream_t s) {
-  cudaError_t err = cudaFuncSetAttribute(apply_cart_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-  if (err != cudaSuccess) return err;
-  apply_cart_batch_kernel<<<nwork, threads, smem, s>>>(descs, work, x, y, done);
   g_launches += 1;
   return cudaGetLastError();
 }
