@@ -53,10 +53,11 @@ DTYPES = {"fp64": "f64 (CG, apply, preconditioner)",
           "fp64_df": "f64 CG and preconditioner, double-float (2 x f32) apply",
           "mixed_fp32": "f64 CG, double-float (2 x f32) apply, f32 preconditioner"}
 HEADLINE = "mixed_fp32"
-# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the H(grad)
-# general apply (apply_kernel<0,7>, double-float, 8^3 cells) in an ncu
-# capture of this workload (profiles/apply_kernel_hgrad_8cubed_p7.md)
-APPLY_TRAFFIC_BYTES = 52_453_632
+# dram__bytes_read.sum + dram__bytes_write.sum of one H(grad) general apply
+# (apply_kernel<0,7> and its assembly, double-float, 8^3 cells) in an ncu
+# capture of this workload (profiles/apply_kernel_hgrad_8cubed_p7.md); None
+# until the current kernels have been captured
+APPLY_TRAFFIC_BYTES = None
 FP64_PEAK_TFLOPS = 1.20   # measured FP64 FMA throughput of a GB300 (DFMA throughput probe)
 # Algorithmic HBM bytes per lattice DOF per CG iteration of the whole solve:
 # CG vectors ~80 B (FP64, fused updates and dots), operator apply 16 B (x in,
@@ -380,15 +381,16 @@ def run_ours(args):
         flops += calls * apply_flops(k, DEGREE) * N_CELLS ** 3
     achieved = flops / (app_ms / 1e3) / 1e12
     roof = {"bound": "alu",
-            "kernel": "apply_kernel (sum-factorised operator, double-float on the FP32 pipe)",
+            "kernel": "apply_kernel + cart_assemble_kernel (sum-factorised operator, double-float on "
+                      "the FP32 pipe, then the fixed-order assembly of the cell products)",
             "achieved": achieved, "peak": DF_PEAK_TFLOPS,
             "unit": "TFLOP/s (FP64-equivalent; peak = double-float FMA rate from unit counts)",
             "frac": achieved / DF_PEAK_TFLOPS,
-            # DRAM bytes of one launch (ncu dram__bytes_read.sum + write.sum,
-            # H(grad) instance, 512 cells): the pullback metric (49.5 MB) plus
-            # the cell gathers and scatters, no re-reads
+            # DRAM bytes of one apply (ncu dram__bytes_read.sum + write.sum of
+            # the two kernels, H(grad) instance, 512 cells): the pullback
+            # metric (49.5 MB) plus the cell gathers and the products, no re-reads
             "traffic": APPLY_TRAFFIC_BYTES,
-            "traffic_launch": "apply_kernel<0,7>, 8^3 cells, one launch (ncu)",
+            "traffic_launch": "apply_kernel<0,7> + cart_assemble_kernel<0,7>, 8^3 cells, one apply (ncu)",
             "fp64_pipe_peak": FP64_PEAK_TFLOPS,
             "avg_launch_ms": app_ms / max(app_calls, 1),
             "time_share_of_step": app_ms / ms_h,

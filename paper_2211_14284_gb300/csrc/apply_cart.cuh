@@ -30,6 +30,10 @@ namespace rmd {
 // launch the (K, A.p) instantiation (apply_cart_part.cu); writes every entry of y
 template <int K>
 cudaError_t launch_cart_part(const ApplyDev &A, const double *x, double *y, cudaStream_t s);
+// the assembly alone (the general apply's second kernel): y from the cell
+// products in A.Y; writes every entry of y
+template <int K>
+cudaError_t launch_cart_assemble_part(const ApplyDev &A, double *y, cudaStream_t s);
 
 namespace {
 
@@ -464,17 +468,7 @@ __global__ void __launch_bounds__(256) cart_assemble_kernel(ApplyDev A, const R 
 }
 
 template <int K, int P, typename R>
-cudaError_t launch_cart_kpr(const ApplyDev &A, const double *x, double *y, cudaStream_t s) {
-  using Sh = CartShape<K, P>;
-  const size_t smem = (size_t)Sh::SMEM * sizeof(double);
-  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  cudaError_t err =
-      cudaFuncSetAttribute(cart_local_kernel<K, P, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (err != cudaSuccess) return err;
-  const int ncell = A.n[0] * A.n[1] * A.n[2];
-  cart_local_kernel<K, P, R><<<(ncell + Sh::CPB - 1) / Sh::CPB, Sh::NT, smem, s>>>(A, x, reinterpret_cast<R *>(A.Y));
-  err = cudaGetLastError();
-  if (err != cudaSuccess) return err;
+cudaError_t launch_assemble_kpr(const ApplyDev &A, double *y, cudaStream_t s) {
   // a grid of resident CTAs (by default 8 per SM), each warp striding over the rows
   int grid = A.asm_grid;
   if (grid <= 0) {
@@ -486,6 +480,20 @@ cudaError_t launch_cart_kpr(const ApplyDev &A, const double *x, double *y, cudaS
   cart_assemble_kernel<K, P, R><<<grid, 256, 0, s>>>(A, reinterpret_cast<const R *>(A.Y), y);
   return cudaGetLastError();
 }
+template <int K, int P, typename R>
+cudaError_t launch_cart_kpr(const ApplyDev &A, const double *x, double *y, cudaStream_t s) {
+  using Sh = CartShape<K, P>;
+  const size_t smem = (size_t)Sh::SMEM * sizeof(double);
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t err =
+      cudaFuncSetAttribute(cart_local_kernel<K, P, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  const int ncell = A.n[0] * A.n[1] * A.n[2];
+  cart_local_kernel<K, P, R><<<(ncell + Sh::CPB - 1) / Sh::CPB, Sh::NT, smem, s>>>(A, x, reinterpret_cast<R *>(A.Y));
+  err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  return launch_assemble_kpr<K, P, R>(A, y, s);
+}
 template <int K, int P>
 cudaError_t launch_cart_kp(const ApplyDev &A, const double *x, double *y, cudaStream_t s) {
   return A.arith ? launch_cart_kpr<K, P, DF>(A, x, y, s) : launch_cart_kpr<K, P, double>(A, x, y, s);
@@ -495,6 +503,16 @@ cudaError_t launch_cart_range(const ApplyDev &A, const double *x, double *y, cud
                               std::integer_sequence<int, PS...>) {
   cudaError_t err = cudaErrorInvalidValue;
   ((A.p == PS + 1 ? (err = launch_cart_kp<K, PS + 1>(A, x, y, s), 0) : 0), ...);
+  return err;
+}
+template <int K, int... PS>
+cudaError_t launch_assemble_range(const ApplyDev &A, double *y, cudaStream_t s, std::integer_sequence<int, PS...>) {
+  cudaError_t err = cudaErrorInvalidValue;
+  ((A.p == PS + 1 ? (err = A.arith ? launch_assemble_kpr<K, PS + 1, DF>(A, y, s)
+                                   : launch_assemble_kpr<K, PS + 1, double>(A, y, s),
+    0)
+                  : 0),
+   ...);
   return err;
 }
 

@@ -14,5 +14,10 @@ cudaError_t launch_cart_part(const ApplyDev &A, const double *x, double *y, cuda
   return launch_cart_range<K>(A, x, y, s, std::make_integer_sequence<int, kCartMaxP>{});
 }
 template cudaError_t launch_cart_part<RM_CART_K>(const ApplyDev &, const double *, double *, cudaStream_t);
+template <int K>
+cudaError_t launch_cart_assemble_part(const ApplyDev &A, double *y, cudaStream_t s) {
+  return launch_assemble_range<K>(A, y, s, std::make_integer_sequence<int, kCartMaxP>{});
+}
+template cudaError_t launch_cart_assemble_part<RM_CART_K>(const ApplyDev &, double *, cudaStream_t);
 
 }  // namespace rmd

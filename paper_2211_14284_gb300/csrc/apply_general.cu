@@ -121,7 +121,12 @@ cudaError_t launch_apply_general(const ApplyDev &A, const double *x, double *y, 
   if (A.k == 0) err = lo ? launch_general_part<0, 1>(A.p, A, x, y, s) : launch_general_part<0, 5>(A.p, A, x, y, s);
   else if (A.k == 1) err = lo ? launch_general_part<1, 1>(A.p, A, x, y, s) : launch_general_part<1, 5>(A.p, A, x, y, s);
   else if (A.k == 2) err = lo ? launch_general_part<2, 1>(A.p, A, x, y, s) : launch_general_part<2, 5>(A.p, A, x, y, s);
-  if (err == cudaSuccess) add_launches(1);
+  if (err != cudaSuccess) return err;
+  // the cells' products to y: fixed-order sums, Dirichlet entries 0
+  if (A.k == 0) err = launch_cart_assemble_part<0>(A, y, s);
+  else if (A.k == 1) err = launch_cart_assemble_part<1>(A, y, s);
+  else err = launch_cart_assemble_part<2>(A, y, s);
+  if (err == cudaSuccess) add_launches(2);
   return err;
 }
 

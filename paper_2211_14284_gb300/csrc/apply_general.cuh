@@ -272,11 +272,24 @@ __device__ __forceinline__ void from_points(const R *Um, R *SA, R *SB, R *out, c
 }
 
 // Gather (SCATTER = false: xl = x on the cell, Dirichlet entries 0, yl = 0)
-// or scatter-add (SCATTER = true: y += yl, Dirichlet rows skipped).
+// or store (SCATTER = true: the cell's product yl to its run of the scratch
+// P.Y, [component][cell][local entry], coalesced; the assembly kernel sums
+// the contributions of every lattice entry in a fixed order, no atomics).
 template <bool SCATTER, int KK, int PP, typename R>
 __device__ __forceinline__ void cell_io(const ApplyDev &P, const int e[3], const double *__restrict__ x,
                                         double *__restrict__ y, R *xl, R *yl) {
   constexpr int CS = csize(KK, PP);
+  if constexpr (SCATTER) {
+    const size_t ncell = (size_t)P.n[0] * P.n[1] * P.n[2];
+    const size_t c = e[0] + (size_t)P.n[0] * (e[1] + (size_t)P.n[1] * e[2]);
+    R *Yr = reinterpret_cast<R *>(P.Y);
+    sfor<ncomp(KK)>([&](auto mc) {
+      constexpr int m = decltype(mc)::value;
+      R *dst = Yr + ((size_t)m * ncell + c) * CS;
+      for (int l = threadIdx.x; l < CS; l += NT) dst[l] = yl[m * CS + l];
+    });
+    return;
+  }
   sfor<ncomp(KK)>([&](auto mc) {
     constexpr int m = decltype(mc)::value;
     constexpr int l0 = sld(KK, PP, m, 0), l1 = sld(KK, PP, m, 1);
@@ -287,12 +300,8 @@ __device__ __forceinline__ void cell_io(const ApplyDev &P, const int e[3], const
                        (styp(KK, m, 1) && (g2 == 0 || g2 == P.n[1] * PP)) ||
                        (styp(KK, m, 2) && (g3 == 0 || g3 == P.n[2] * PP)));
       const long long gi = P.off[m] + g1 + (long long)P.N[m][0] * (g2 + (long long)P.N[m][1] * g3);
-      if (SCATTER) {
-        if (!dir) atomicAdd(&y[gi], to_double(yl[m * CS + l]));
-      } else {
-        xl[m * CS + l] = to_r<R>(dir ? 0.0 : x[gi]);
-        yl[m * CS + l] = rzero(R());
-      }
+      xl[m * CS + l] = to_r<R>(dir ? 0.0 : x[gi]);
+      yl[m * CS + l] = rzero(R());
     }
   });
 }

@@ -393,6 +393,7 @@ void build_apply(rm_handle *h, const Geometry &geo, const std::vector<double> &a
   A.nAB = A.nA + (k == 2 ? 1 : 6);
   double *G = h->dalloc<double>((size_t)ncell * A.nAB * q3);
   A.G = G;
+  A.Y = h->dalloc<double>((size_t)ncell * A.nloc0);  // unassembled cell products
   CK(launch_metric(A, G, h->stream));
   CK(cudaStreamSynchronize(h->stream));
 }
@@ -662,8 +663,7 @@ void relax(rm_handle *h, const double *r, double *z, bool with_coarse) {
 }
 
 void apply(rm_handle *h, const double *x, double *y) {
-  // the Cartesian apply writes every entry; the general one scatter-adds
-  if (!h->ad.cartesian) CK(cudaMemsetAsync(y, 0, h->size * sizeof(double), h->stream));
+  // both applies write every entry of y (cell products, then a fixed-order assembly)
   CK(launch_apply(h->ad, x, y, h->stream));
 }
 

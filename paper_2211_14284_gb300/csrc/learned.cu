@@ -238,7 +238,7 @@ __device__ int g_conv_timeout = 0;
 // of 128 voxels x BN output channels accumulates in tensor memory (BN FP32
 // columns, TMEM rows = voxels) through tcgen05.mma (M = 128, N = BN, K = 16
 // per instruction, BF16 operands) issued by one thread; the threads stage
-// 64-wide K chunks of A (one voxel row each) and of W into shared memory in
+// 32-wide K chunks of A (one voxel row each) and of W into shared memory in
 // the no-swizzle K-major core-matrix layout, double-buffered: chunk i + 1 is
 // gathered while the tensor core works on chunk i, and a buffer is rewritten
 // only after the mbarrier that tcgen05.commit arrives on says its MMAs are
@@ -246,14 +246,21 @@ __device__ int g_conv_timeout = 0;
 // reduction for small grids, as in conv_kernel).  Every mbarrier wait is
 // bounded; on timeout the CTA records it in g_conv_timeout, writes NaN for
 // its outputs, waits once more for its MMAs and frees its tensor memory.
-constexpr int kTcBM = 128, kTcKC = 64;
-// bytes of one buffer: A (128 rows) and B (64 rows max) chunks of 64 BF16
+constexpr int kTcBM = 128, kTcKC = 32;
+// bytes of one buffer: A (128 rows) and B (64 rows max) chunks of 32 BF16
 constexpr int kTcABytes = kTcBM * kTcKC * 2, kTcBBytes = 64 * kTcKC * 2;
-constexpr int kTcSmem = 2 * (kTcABytes + kTcBBytes) + 128;
+// 8-row group stride: kTcKC / 8 core matrices of 8 rows x 16 B along K
+constexpr int kTcSBO = kTcKC / 8 * 128;
+// two stages of A and B plus the barriers, padded to 28 KB: 8 CTAs per SM,
+// whose 8 x 64 tensor-memory columns fill the SM's 512 exactly
+constexpr int kTcSmem = 28 * 1024;
+static_assert(2 * (kTcABytes + kTcBBytes) + 128 <= kTcSmem, "shared memory of the conv stages");
 
-// byte offset of element (r, k) of a rows x 64 BF16 tile: 8-row groups of
-// 1024 B, in each group 8 core matrices of 8 rows x 16 B along K
-__device__ __forceinline__ int tc_off(int r, int k) { return (r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2; }
+// byte offset of element (r, k) of a rows x kTcKC BF16 tile: 8-row groups of
+// kTcSBO bytes, in each group the core matrices of 8 rows x 16 B along K
+__device__ __forceinline__ int tc_off(int r, int k) {
+  return (r >> 3) * kTcSBO + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
 
 template <typename TI, typename TO, int BN>
 __global__ void __launch_bounds__(128) conv_tc_kernel(ConvArgs a, long long total, int per,
@@ -384,7 +391,7 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(ConvArgs a, long long tota
       const unsigned sa = smem_u32(As), sb = smem_u32(Bs);
 #pragma unroll
       for (int ks = 0; ks < kTcKC / 16; ++ks)  // K = 16 per MMA: two core matrices along K
-        tc_mma(tmem, tc_desc(sa + 256 * ks, 128, 1024), tc_desc(sb + 256 * ks, 128, 1024), IDESC,
+        tc_mma(tmem, tc_desc(sa + 256 * ks, 128, kTcSBO), tc_desc(sb + 256 * ks, 128, kTcSBO), IDESC,
                (i > 0 || ks > 0) ? 1u : 0u);
       tc_commit(&bar[buf]);
     }

@@ -67,6 +67,23 @@ def test_apply_parity(k, n, p, perturb, coef, arith):
 
 
 @pytest.mark.parametrize("arith", [0, 1], ids=["fp64", "df64"])
+@pytest.mark.parametrize("k,perturb", [(0, 0.1), (1, 0.1), (2, 0.0), (1, 0.0)])
+def test_apply_bitwise_repeatable(k, perturb, arith):
+    """Both applies (general and Cartesian cells) store each cell's product
+    and sum the contributions of every lattice entry in a fixed order: two
+    applies of the same vector agree bit for bit."""
+    s, pr = _setup(k, 4, 4, perturb, True, arith=arith, static_condensation=1, factor=1,
+                   decomposition=1 if k == 1 else 0)
+    x = _dev(inputs.normal_rhs(pr.lat.size, 40 + k))
+    y1 = torch.zeros_like(x)
+    y2 = torch.full_like(x, 7.0)
+    s.apply(x, y1)
+    s.apply(x, y2)
+    torch.cuda.synchronize()
+    assert torch.equal(y1, y2)
+
+
+@pytest.mark.parametrize("arith", [0, 1], ids=["fp64", "df64"])
 @pytest.mark.parametrize("k,p", [(k, p) for k in (0, 1, 2) for p in range(1, 9)])
 def test_apply_parity_every_instantiation(k, p, arith):
     """The general-cell apply is one kernel per space k and degree p <= 8:
