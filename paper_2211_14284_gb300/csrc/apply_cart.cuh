@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(cart_threads(P)) cart_local_kernel(ApplyDev A,
 // y[g] = sum over the cells holding lattice entry g of their contribution in
 // Y, in a fixed order (cells lexicographic, direction 2 outermost);
 // Dirichlet entries 0.  A warp takes one lattice row (m, g1, g2) at a
-// time (grid-stride over rows): the cells and local indices along
+// time (grid-stride over the rows of all components): the cells and local indices along
 // directions 1 and 2 are the row's, decoded once; the lanes walk g0, whose
 // consecutive entries are consecutive local indices of a cell in Y and
 // consecutive entries of y; an entry inside a cell along g0 reads one
@@ -404,67 +404,76 @@ __global__ void __launch_bounds__(256) cart_assemble_kernel(ApplyDev A, const R 
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   const int ncell = A.n[0] * A.n[1] * A.n[2];
   const bool frozen = A.done && A.done[A.prob];  // a converged problem of a batch: y = 0
-  sfor<NC0>([&](auto mc) {
-    constexpr int m = decltype(mc)::value;
-    constexpr bool st0 = styp(K, m, 0), st1 = styp(K, m, 1), st2 = styp(K, m, 2);
-    const int N0 = A.N[m][0], N1 = A.N[m][1], rows = A.N[m][1] * A.N[m][2];
-    for (int row = gw; row < rows; row += nw) {
-      const int g1 = row % N1, g2 = row / N1;
-      // (cell, local index) pairs along a direction: two on an interior
-      // s-type interface plane, else one; dir: a Dirichlet plane
-      bool dir = false;
-      auto pairs = [&](bool st, int g, int nd, int (&ce)[2], int (&ci)[2], int &nc) {
-        const int e = g / P, i = g - e * P;
-        if (st && i == 0) {
-          if (!A.natural && (g == 0 || e == nd)) dir = true;
-          const bool lo = e >= 1, hi = e < nd;
-          ce[0] = lo ? e - 1 : e;
-          ci[0] = lo ? P : 0;
-          ce[1] = e;
-          ci[1] = 0;
-          nc = (lo && hi) ? 2 : 1;
-        } else {
-          ce[0] = ce[1] = e;
-          ci[0] = ci[1] = i;
-          nc = 1;
+  // the rows of every component form one range of work items, so a small
+  // lattice's components are assembled in one pass of the warps
+  int total = 0;
+  for (int m = 0; m < NC0; ++m) total += A.N[m][1] * A.N[m][2];
+  for (int w = gw; w < total; w += nw) {
+    int start = 0;
+    sfor<NC0>([&](auto mc) {
+      constexpr int m = decltype(mc)::value;
+      constexpr bool st0 = styp(K, m, 0), st1 = styp(K, m, 1), st2 = styp(K, m, 2);
+      const int N0 = A.N[m][0], N1 = A.N[m][1], rows = A.N[m][1] * A.N[m][2];
+      const int row = w - start;
+      start += rows;
+      if (row >= 0 && row < rows) {
+        const int g1 = row % N1, g2 = row / N1;
+        // (cell, local index) pairs along a direction: two on an interior
+        // s-type interface plane, else one; dir: a Dirichlet plane
+        bool dir = false;
+        auto pairs = [&](bool st, int g, int nd, int (&ce)[2], int (&ci)[2], int &nc) {
+          const int e = g / P, i = g - e * P;
+          if (st && i == 0) {
+            if (!A.natural && (g == 0 || e == nd)) dir = true;
+            const bool lo = e >= 1, hi = e < nd;
+            ce[0] = lo ? e - 1 : e;
+            ci[0] = lo ? P : 0;
+            ce[1] = e;
+            ci[1] = 0;
+            nc = (lo && hi) ? 2 : 1;
+          } else {
+            ce[0] = ce[1] = e;
+            ci[0] = ci[1] = i;
+            nc = 1;
+          }
+        };
+        int ce1[2], ci1[2], n1, ce2[2], ci2[2], n2;
+        pairs(st1, g1, A.n[1], ce1, ci1, n1);
+        pairs(st2, g2, A.n[2], ce2, ci2, n2);
+        const bool rowdir = dir || frozen;
+        // the row's (up to 4) runs in Y: cell (0, e1, e2) at local (0, i1, i2)
+        // for each pair along directions 1 and 2 (warp-uniform)
+        const R *base[2][2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+          for (int b = 0; b < 2; ++b)
+            base[c][b] = Y + cart_y_index<K, P>(ncell, m, (size_t)A.n[0] * (ce1[b] + (size_t)A.n[1] * ce2[c]), 0,
+                                                ci1[b], ci2[c]);
+        double *yrow = y + A.off[m] + (long long)N0 * row;
+        for (int g0 = lane; g0 < N0; g0 += 32) {
+          int ce0[2], ci0[2], n0;
+          dir = rowdir;
+          pairs(st0, g0, A.n[0], ce0, ci0, n0);
+          const int o0 = ce0[0] * Sh::S0 + ci0[0], o1 = ce0[1] * Sh::S0 + ci0[1];
+          R s = rzero(R());
+          if (!dir) {
+            // fixed order: direction 2 outermost, then 1, then 0
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+              for (int b = 0; b < 2; ++b)
+                if (c < n2 && b < n1) {
+                  const R v0 = base[c][b][o0];
+                  s = (c == 0 && b == 0) ? v0 : radd(s, v0);
+                  if (n0 == 2) s = radd(s, base[c][b][o1]);
+                }
+          }
+          yrow[g0] = to_double(s);
         }
-      };
-      int ce1[2], ci1[2], n1, ce2[2], ci2[2], n2;
-      pairs(st1, g1, A.n[1], ce1, ci1, n1);
-      pairs(st2, g2, A.n[2], ce2, ci2, n2);
-      const bool rowdir = dir || frozen;
-      // the row's (up to 4) runs in Y: cell (0, e1, e2) at local (0, i1, i2)
-      // for each pair along directions 1 and 2 (warp-uniform)
-      const R *base[2][2];
-#pragma unroll
-      for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int b = 0; b < 2; ++b)
-          base[c][b] = Y + cart_y_index<K, P>(ncell, m, (size_t)A.n[0] * (ce1[b] + (size_t)A.n[1] * ce2[c]), 0,
-                                              ci1[b], ci2[c]);
-      double *yrow = y + A.off[m] + (long long)N0 * row;
-      for (int g0 = lane; g0 < N0; g0 += 32) {
-        int ce0[2], ci0[2], n0;
-        dir = rowdir;
-        pairs(st0, g0, A.n[0], ce0, ci0, n0);
-        const int o0 = ce0[0] * Sh::S0 + ci0[0], o1 = ce0[1] * Sh::S0 + ci0[1];
-        R s = rzero(R());
-        if (!dir) {
-          // fixed order: direction 2 outermost, then 1, then 0
-#pragma unroll
-          for (int c = 0; c < 2; ++c)
-#pragma unroll
-            for (int b = 0; b < 2; ++b)
-              if (c < n2 && b < n1) {
-                const R v0 = base[c][b][o0];
-                s = (c == 0 && b == 0) ? v0 : radd(s, v0);
-                if (n0 == 2) s = radd(s, base[c][b][o1]);
-              }
-        }
-        yrow[g0] = to_double(s);
       }
-    }
-  });
+    });
+  }
 }
 
 template <int K, int P, typename R>
