@@ -55,9 +55,8 @@ DTYPES = {"fp64": "f64 (CG, apply, preconditioner)",
 HEADLINE = "mixed_fp32"
 # dram__bytes_read.sum + dram__bytes_write.sum of one H(grad) general apply
 # (apply_kernel<0,7> and its assembly, double-float, 8^3 cells) in an ncu
-# capture of this workload (profiles/apply_kernel_hgrad_8cubed_p7.md); None
-# until the current kernels have been captured
-APPLY_TRAFFIC_BYTES = None
+# capture of this workload (profiles/apply_kernel_hgrad_8cubed_p7.md)
+APPLY_TRAFFIC_BYTES = 53_107_712
 FP64_PEAK_TFLOPS = 1.20   # measured FP64 FMA throughput of a GB300 (DFMA throughput probe)
 # Algorithmic HBM bytes per lattice DOF per CG iteration of the whole solve:
 # CG vectors ~80 B (FP64, fused updates and dots), operator apply 16 B (x in,
