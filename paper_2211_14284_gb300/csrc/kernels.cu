@@ -1,13 +1,13 @@
 // Device kernels of the Riesz-map solvers (sm_103a).
 //
-// * apply_cart_kernel<k>: y = A x on axis-aligned cells, where the cell
-//   matrix of Eq. sum-factorization is a Kronecker sum of the 1D FDM factors
-//   (the general-cell apply is in apply_general.cuh).
-// * patch_kernel: z += sum_j R_j^T L_j^-T L_j^-1 R_j r over a patch family
-//   (Eqs. asm-afw, sc-asm-afw, sc-asm-hiptmair): one CTA per patch, level-
-//   scheduled sparse forward/backward substitution in shared memory on the
-//   template pattern shared by all patches of the family; patch_inv_kernel
-//   for exact factors stored as block inverses.
+// (The operator applies are in apply_general.cuh, general cells, and
+// apply_cart.cuh, axis-aligned cells and the shared assembly.)
+// * patch_warp_kernel / patch_kernel: z += sum_j R_j^T L_j^-T L_j^-1 R_j r
+//   over a patch family (Eqs. asm-afw, sc-asm-afw, sc-asm-hiptmair):
+//   level-scheduled sparse forward/backward substitutions on the template
+//   pattern shared by all patches of the family, a warp per patch with the
+//   factors staged by bulk copies, or a CTA per patch for factors too large
+//   to stage; patch_inv_kernel for exact factors stored as block inverses.
 // * SpMV / GEMV for static condensation (Eq. schur), the Hiptmair gradient
 //   and the p = 1 coarse correction; fused CG updates with deterministic
 //   fixed-order FP64 reductions finished by the last CTA.
