@@ -141,6 +141,15 @@ typedef struct {
                               alone (rm_apply only; alpha or beta may then be 0, e.g.
                               a mass matrix alone; rm_precondition and rm_solve
                               return RM_ERR_ARG) */
+  int deterministic;       /* 0 (default): the patch solves add into z with atomics and
+                              the relaxation's branches run concurrently on their own
+                              streams (fastest; z may differ in the last bits from run
+                              to run); 1: every patch writes its solution to a scratch
+                              array, each lattice entry sums its patches' values in a
+                              fixed order, the branches run one after another: z = B r
+                              and whole solves are bitwise reproducible.  Single-problem
+                              handles only (rm_batch_setup and rm_precondition_noalloc
+                              refuse it) */
 } rm_options;
 
 typedef struct {

@@ -397,6 +397,8 @@ int rm_batch_setup(rm_batch **out, int nprob, const int *space, const rm_mesh *m
     if (o.norm != RM_NORM_L2) throw std::invalid_argument("norm: the batched lock step stops on the l2 residual");
     if (o.arith != RM_ARITH_FP64 && o.arith != RM_ARITH_DF64) throw std::invalid_argument("arith");
     if (o.boundary != RM_BC_DIRICHLET) throw std::invalid_argument("boundary: only RM_BC_DIRICHLET");
+    if (o.deterministic != 0)
+      throw std::invalid_argument("deterministic: single-problem handles only (the batch scatters patches with atomics)");
     B->vt = o.precision == RM_FP32 ? 1 : 0;
     B->nprob = nprob;
     B->sc = o.static_condensation != 0;

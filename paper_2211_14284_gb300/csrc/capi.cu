@@ -281,6 +281,33 @@ DevPatch upload_family(rm_handle *h, const PatchFamily &F) {
       D.wpb = patch_warps_per_block(D);
     }
   }
+  if (h->opt.deterministic) {
+    // the family's scatter as a gather: per lattice entry, its (patch, slot)
+    // values in increasing patch-major order
+    std::vector<std::pair<int, long long>> ent;
+    for (int pi = 0; pi < F.npatch; ++pi)
+      for (int sl = 0; sl < F.nslots; ++sl) {
+        const int g = F.slotmap[(size_t)pi * F.nslots + sl];
+        if (g >= 0) ent.emplace_back(g, (long long)pi * F.nslots + sl);
+      }
+    std::sort(ent.begin(), ent.end());
+    if ((size_t)F.npatch * F.nslots > (size_t)INT32_MAX)
+      throw std::runtime_error("deterministic relaxation: patch family too large");
+    std::vector<int> grow, gptr{0}, gidx;
+    for (size_t e = 0; e < ent.size(); ++e) {
+      if (e == 0 || ent[e].first != ent[e - 1].first) {
+        if (e > 0) gptr.push_back((int)gidx.size());
+        grow.push_back(ent[e].first);
+      }
+      gidx.push_back((int)ent[e].second);
+    }
+    if (!ent.empty()) gptr.push_back((int)gidx.size());
+    D.ng = (int)grow.size();
+    D.grow = h->upload(grow);
+    D.gptr = h->upload(gptr);
+    D.gidx = h->upload(gidx);
+    D.zp = h->dalloc<double>((size_t)F.npatch * F.nslots);
+  }
   h->stat_patches += F.npatch;
   h->stat_slots += (long long)F.npatch * F.nslots;
   h->stat_nnz += (long long)F.npatch * (F.inverse ? F.ivals() : F.nnz());
@@ -611,8 +638,10 @@ void relax(rm_handle *h, const double *r, double *z, bool with_coarse) {
     CK(launch_spmv(h->E, r, h->rt, r, 2, -1.0, s));              // rt_G = r_G - P_GI P_II^-1 r_I
     rr = h->rt;
   }
-  // the learned coarse term talks to the host (judge): keep everything on s
-  const bool fork = h->corr_mode != RM_CORRECTOR_LEARNED;
+  // the learned coarse term talks to the host (judge), and the deterministic
+  // relaxation orders every addition into z: keep everything on s
+  const bool det = h->opt.deterministic != 0;
+  const bool fork = h->corr_mode != RM_CORRECTOR_LEARNED && !det;
   int nb = 0;
   auto branch = [&]() -> cudaStream_t {
     if (!fork) return s;
@@ -622,13 +651,20 @@ void relax(rm_handle *h, const double *r, double *z, bool with_coarse) {
     return b;
   };
   if (fork) CK(cudaEventRecord(h->fork, s));
-  for (auto &F : h->fam) CK(launch_patches(F, rr, z, branch()));  // z_G += sum_v S_v^-1 rt
+  for (auto &F : h->fam) {
+    cudaStream_t b = branch();
+    CK(launch_patches(F, rr, z, b));                               // z_G += sum_v S_v^-1 rt
+    CK(launch_patch_gather(F, z, b));                              // (deterministic form)
+  }
   if (h->ph) {
     cudaStream_t b = branch();
     CK(launch_spmv(h->DtT, rr, h->u0, nullptr, 0, 1.0, b));        // u0 = D~^T rt
     CK(cudaMemsetAsync(h->v0, 0, h->size0 * sizeof(double), b));
-    for (auto &F : h->pfam) CK(launch_patches(F, h->u0, h->v0, b));
-    CK(launch_spmv(h->Dt, h->v0, z, nullptr, 3, 1.0, b));          // z_G += D~ v0
+    for (auto &F : h->pfam) {
+      CK(launch_patches(F, h->u0, h->v0, b));
+      CK(launch_patch_gather(F, h->v0, b));
+    }
+    CK(launch_spmv(h->Dt, h->v0, z, nullptr, det ? 1 : 3, 1.0, b)); // z_G += D~ v0
   }
   const bool record = with_coarse && h->rec && h->rec_n < h->rec_cap;
   if (with_coarse && h->nc > 0 && (h->corr_mode != RM_CORRECTOR_OFF || record)) {
@@ -690,6 +726,7 @@ rm_options rm_default_options(void) {
   o.composition = RM_ADDITIVE;
   o.hybrid_omega = 0.125;
   o.relaxation = 1;
+  o.deterministic = 0;
   return o;
 }
 
@@ -721,6 +758,7 @@ int rm_setup(rm_handle **out, int space, const rm_mesh *mesh, int p, const doubl
     if (o.coarse_smoother != RM_SMOOTH_STAR && o.coarse_smoother != RM_SMOOTH_HIPTMAIR)
       throw std::invalid_argument("coarse_smoother");
     if (o.composition != RM_ADDITIVE && o.composition != RM_HYBRID) throw std::invalid_argument("composition");
+    if (o.deterministic != 0 && o.deterministic != 1) throw std::invalid_argument("deterministic");
     if (o.composition == RM_HYBRID && !(o.hybrid_omega > 0.0 && o.hybrid_omega <= 1.0))
       throw std::invalid_argument("hybrid_omega must be in (0, 1]");
     if (o.arith != RM_ARITH_FP64 && o.arith != RM_ARITH_DF64) throw std::invalid_argument("arith");
@@ -1600,6 +1638,10 @@ extern "C" int rm_precondition_noalloc(rm_handle *h, const double *r, double *z)
     return fail(h, RM_ERR_ARG,
                 "rm_precondition_noalloc: statically condensed relaxations need "
                 "lattice-sized scratch; use rm_precondition");
+  if (h->opt.deterministic)
+    return fail(h, RM_ERR_ARG,
+                "rm_precondition_noalloc: the deterministic relaxation gathers from per-patch "
+                "scratch; use rm_precondition");
   if (h->mgAinv)
     return fail(h, RM_ERR_ARG,
                 "rm_precondition_noalloc: the coarse multigrid cycle needs per-level vectors; "

@@ -266,6 +266,13 @@ struct DevPatch {
   int tmpl_bytes = 0;
   int toff[9] = {};
   int wpb = 0;  // patches (warps) per CTA of patch_warp_kernel; 0: the CTA-per-patch kernels
+  // deterministic relaxation: the kernels store patch p's slot s value at
+  // zp[p * nslots + s] instead of adding it into z; launch_patch_gather then
+  // adds, for each of the family's ng lattice entries grow[i], the values
+  // zp[gidx[gptr[i] .. gptr[i + 1])] in that (fixed) order
+  double *zp = nullptr;
+  int ng = 0;
+  const int *grow = nullptr, *gptr = nullptr, *gidx = nullptr;
 };
 
 // launchers (kernels.cu); launch_count() = kernels launched so far in this process
@@ -283,6 +290,8 @@ cudaError_t launch_apply_cart(const ApplyDev &A, const double *x, double *y, cud
 cudaError_t launch_spmv(const DevCsr &M, const double *x, double *y, const double *u, int mode,
                         double a, cudaStream_t s);
 cudaError_t launch_patches(const DevPatch &F, const double *r, double *z, cudaStream_t s);
+// z[grow[i]] += the family's stored patch values of that entry, in a fixed order
+cudaError_t launch_patch_gather(const DevPatch &F, double *z, cudaStream_t s);
 // the warp-per-patch kernel's bounded waits: 1 if any gave up since the last
 // call (the flag is cleared), 0 otherwise; a CUDA error code on failure
 int patch_timeouts(cudaError_t *err);

@@ -193,6 +193,10 @@ __global__ void patch_kernel(DevPatch F, const double *__restrict__ r, double *_
     }
     __syncthreads();
   }
+  if (F.zp) {  // deterministic relaxation: the values, summed later in a fixed order
+    for (int s = threadIdx.x; s < ns; s += blockDim.x) F.zp[(size_t)blockIdx.x * ns + s] = (double)xs[s];
+    return;
+  }
   for (int s = threadIdx.x; s < ns; s += blockDim.x) {
     const int g = sm[s];
     if (g >= 0) atomicAdd(&z[g], (double)xs[s]);
@@ -287,6 +291,10 @@ __global__ void __launch_bounds__(WPB * 32) patch_warp_kernel(DevPatch F, const 
     }
     __syncwarp();
   }
+  if (F.zp) {  // deterministic relaxation: the values, summed later in a fixed order
+    for (int s = lane; s < ns; s += 32) F.zp[(size_t)patch * ns + s] = (double)xs[s];
+    return;
+  }
   for (int s = lane; s < ns; s += 32) {
     const int g = sm[s];
     if (g >= 0) atomicAdd(&z[g], (double)xs[s]);
@@ -330,10 +338,28 @@ __global__ void patch_inv_kernel(DevPatch F, const double *__restrict__ r, doubl
     ys[t] = acc;
   }
   __syncthreads();
+  if (F.zp) {  // deterministic relaxation: the values, summed later in a fixed order
+    for (int t = threadIdx.x; t < ns; t += blockDim.x)
+      F.zp[(size_t)blockIdx.x * ns + F.pos_slot[t]] = (double)ys[t];
+    return;
+  }
   for (int t = threadIdx.x; t < ns; t += blockDim.x) {
     const int g = sm[F.pos_slot[t]];
     if (g >= 0) atomicAdd(&z[g], (double)ys[t]);
   }
+}
+
+// z[grow[i]] += sum of zp[gidx[k]], k = gptr[i] .. gptr[i + 1] - 1, in that
+// order: the deterministic form of a patch family's scatter (one thread per
+// lattice entry the family touches; the entries are distinct)
+__global__ void patch_gather_kernel(int ng, const int *__restrict__ grow, const int *__restrict__ gptr,
+                                    const int *__restrict__ gidx, const double *__restrict__ zp,
+                                    double *__restrict__ z) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ng) return;
+  double acc = 0.0;
+  for (int k = gptr[i]; k < gptr[i + 1]; ++k) acc += zp[gidx[k]];
+  z[grow[i]] += acc;
 }
 
 template <typename VT>
@@ -698,6 +724,13 @@ static void patch_dispatch(const DevPatch &F, const double *r, double *z, cudaSt
     cudaFuncSetAttribute(patch_kernel<VT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)base);
     patch_kernel<VT, false><<<F.npatch, 128, base, s>>>(F, r, z);
   }
+}
+
+cudaError_t launch_patch_gather(const DevPatch &F, double *z, cudaStream_t s) {
+  if (!F.zp || F.ng == 0) return cudaSuccess;
+  patch_gather_kernel<<<(F.ng + 255) / 256, 256, 0, s>>>(F.ng, F.grow, F.gptr, F.gidx, F.zp, z);
+  g_launches += 1;
+  return cudaGetLastError();
 }
 
 int patch_warps_per_block(const DevPatch &F) {

@@ -56,7 +56,8 @@ class RmOptions(ctypes.Structure):
                 ("check_every", ctypes.c_int), ("profile", ctypes.c_int),
                 ("norm", ctypes.c_int), ("arith", ctypes.c_int), ("boundary", ctypes.c_int),
                 ("coarse_smoother", ctypes.c_int), ("composition", ctypes.c_int),
-                ("hybrid_omega", ctypes.c_double), ("relaxation", ctypes.c_int)]
+                ("hybrid_omega", ctypes.c_double), ("relaxation", ctypes.c_int),
+                ("deterministic", ctypes.c_int)]
 
 
 class RmInfo(ctypes.Structure):

@@ -77,6 +77,13 @@ def test_batch_rejects_distorted_meshes():
         BatchSolver([{"space": 1, "n": 2, "p": 2, "vertices": X}], **OPTS)
 
 
+def test_batch_rejects_deterministic():
+    """The deterministic relaxation is for single-problem handles."""
+    from paper_2211_14284_gb300.rm import BatchSolver, RmError
+    with pytest.raises(RmError, match="deterministic"):
+        BatchSolver([{"space": 1, "n": 2, "p": 2}], **dict(OPTS, deterministic=1))
+
+
 def test_batch_nan_problem_stops_alone():
     """A problem whose right-hand side holds a NaN is flagged RM_ERR_NAN on
     the device and frozen at once; the other problems still converge and the

@@ -157,6 +157,58 @@ def test_precondition_parity(k, n, p, perturb, mode, opts):
     assert np.abs(got - want).max() <= tol * np.abs(want).max()
 
 
+@pytest.mark.parametrize("k,n,p,perturb,mode,opts", [PREC_CASES[0], PREC_CASES[1], PREC_CASES[4],
+                                                     PREC_CASES[6]])
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32"])
+def test_deterministic_precondition(k, n, p, perturb, mode, opts, precision):
+    """rm_options.deterministic = 1: every patch stores its solution and each
+    lattice entry sums its patches' values in a fixed order, the branches
+    run one after another.  z = B r is bit for bit the same on two calls,
+    equals the default (atomic, concurrent) relaxation up to the order of
+    the FP64 additions (1e-12 of max |z|, both precisions), and in FP64
+    matches the oracle with test_precondition_parity's bound."""
+    s, pr = _setup(k, n, p, perturb, True, deterministic=1, precision=precision, **opts)
+    s0, _ = _setup(k, n, p, perturb, True, precision=precision, **opts)
+    r = inputs.normal_rhs(pr.lat.size, 22)
+    r[np.setdiff1d(np.arange(pr.lat.size), pr.free)] = 0.0
+    z1 = torch.zeros(pr.lat.size, dtype=torch.float64, device="cuda")
+    z2 = torch.full_like(z1, 3.0)
+    z0 = torch.zeros_like(z1)
+    s.precondition(_dev(r), z1)
+    s.precondition(_dev(r), z2)
+    s0.precondition(_dev(r), z0)
+    torch.cuda.synchronize()
+    assert torch.equal(z1, z2)
+    got, ref = _host(z1), _host(z0)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+    if precision == 0:
+        M = _oracle_prec(pr, mode)
+        want = np.zeros(pr.lat.size)
+        want[pr.free] = M.apply(r[pr.free])
+        solvers = (M.edge + M.potential) if mode == "scph" else [M.patches]
+        cond = max(np.linalg.cond(L) ** 2 for ps in solvers for L in ps.L)
+        tol = max(1e-11, 1e-12 * cond)
+        assert np.abs(got - want).max() <= tol * np.abs(want).max()
+
+
+@pytest.mark.parametrize("k", [0, 1])
+def test_deterministic_solve_repeatable(k):
+    """With the deterministic relaxation (and the atomic-free applies) two
+    solves of the same system agree bit for bit, iteration count included."""
+    opts = dict(static_condensation=1, factor=1, decomposition=1 if k == 1 else 0,
+                precision=1, flexible=1, arith=1, rtol=1e-8, deterministic=1)
+    s, pr = _setup(k, 3, 4, 0.1, True, **opts)
+    b = _dev(inputs.normal_rhs(pr.lat.size, 70 + k))
+    x1 = torch.zeros_like(b)
+    x2 = torch.zeros_like(b)
+    i1 = s.solve(b, x1)
+    i2 = s.solve(b, x2)
+    torch.cuda.synchronize()
+    assert i1["status"] == "RM_OK" and i1["rel_res_l2"] <= 1e-8
+    assert i1["iterations"] == i2["iterations"]
+    assert torch.equal(x1, x2)
+
+
 def test_solve_config1_parity():
     """4x4x4 uniform mesh, Q_4 (4913 lattice DOFs), PAFW additive with exact
     Cholesky and P1 coarse: GPU solution vs the direct solve, both to 1e-12."""

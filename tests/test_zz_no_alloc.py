@@ -101,3 +101,14 @@ def test_noalloc_rejects_multigrid_coarse():
     z = torch.zeros_like(r)
     with pytest.raises(RmError, match="multigrid"):
         s.precondition_noalloc(r, z)
+
+
+def test_noalloc_rejects_deterministic_relaxation():
+    """A deterministic handle gathers its patch values from per-patch scratch,
+    which this entry point does not use."""
+    from paper_2211_14284_gb300.rm import RmError
+    s = _solver(deterministic=1)
+    r = torch.zeros(s.size, dtype=torch.float64, device="cuda")
+    z = torch.zeros_like(r)
+    with pytest.raises(RmError, match="deterministic"):
+        s.precondition_noalloc(r, z)
