@@ -301,6 +301,16 @@ const char *rm_batch_last_error(const rm_batch *b);
 #define RM_NOALLOC_MAX_COARSE 8192
 int rm_precondition_noalloc(rm_handle *h, const double *r, double *z);
 
+/* Testing aid for the failure path of the bounded device waits (no
+ * counterpart in the paper).  on = 1: every warp-per-patch substitution
+ * kernel launched afterwards on the current device waits for 16 bytes that
+ * its copies never deliver, so each of its CTAs gives up after ~1 s (twice:
+ * its wait, then a last wait for its copies), leaves z untouched and records
+ * the timeout; rm_solve then returns RM_ERR_TIMEOUT.  on = 0 restores normal
+ * operation.  Affects every handle on the device; not for production use.
+ * Returns RM_ERR_CUDA if the flag cannot be written. */
+int rm_debug_patch_timeout(int on);
+
 /* ---- mixed Hodge Laplacians (Sec. 5.3) ------------------------------------------
  * Find (sigma, u) in V^{k-1} x V^k (k = 1, 2, 3), Gamma_D empty, with
  *     -(tau, sigma) + (d tau, u) = 0,   (v, d sigma) + (d v, d u) = F(v),

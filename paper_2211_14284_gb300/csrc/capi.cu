@@ -1631,6 +1631,12 @@ int rm_corrector_use(rm_handle *h, int mode, int judge_every, double judge_max) 
 // streams) race on the array.
 // ---------------------------------------------------------------------------
 
+extern "C" int rm_debug_patch_timeout(int on) {
+  const cudaError_t e = patch_inject_timeout(on);
+  if (e != cudaSuccess) return fail(nullptr, RM_ERR_CUDA, std::string("rm_debug_patch_timeout: ") + cudaGetErrorString(e));
+  return RM_OK;
+}
+
 extern "C" int rm_precondition_noalloc(rm_handle *h, const double *r, double *z) {
   if (!h || !r || !z) return fail(h, RM_ERR_ARG, "rm_precondition_noalloc: NULL argument");
   if (r == z) return fail(h, RM_ERR_ARG, "rm_precondition_noalloc: r and z must not alias");

@@ -295,6 +295,9 @@ cudaError_t launch_patch_gather(const DevPatch &F, double *z, cudaStream_t s);
 // the warp-per-patch kernel's bounded waits: 1 if any gave up since the last
 // call (the flag is cleared), 0 otherwise; a CUDA error code on failure
 int patch_timeouts(cudaError_t *err);
+// testing aid: 1 makes the warp kernel's bounded waits give up (see
+// rm_debug_patch_timeout), 0 restores normal operation
+cudaError_t patch_inject_timeout(int on);
 // patches per CTA of the warp kernel for a family on the current device,
 // chosen for the fewest waves (0: it does not fit)
 int patch_warps_per_block(const DevPatch &F);

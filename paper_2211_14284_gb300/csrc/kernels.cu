@@ -213,6 +213,10 @@ __global__ void patch_kernel(DevPatch F, const double *__restrict__ r, double *_
 // mbarrier is bounded: on timeout the CTA records it in g_patch_timeout,
 // waits once more (bounded) for its copies and returns without touching z.
 __device__ int g_patch_timeout = 0;
+// testing aid (rm_debug_patch_timeout): when set, every CTA of the warp
+// kernel expects 16 bytes more than its copies deliver, so its bounded wait
+// gives up as a wait on a lost copy would
+__device__ int g_patch_inject = 0;
 
 constexpr int kPatchWarpMaxWPB = 8;
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
@@ -243,7 +247,8 @@ __global__ void __launch_bounds__(WPB * 32) patch_warp_kernel(DevPatch F, const 
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    mbar_expect_tx(bar, (unsigned)(F.tmpl_bytes + (size_t)nblk * F.vstride * sizeof(VT)));
+    const unsigned extra = g_patch_inject ? 16u : 0u;
+    mbar_expect_tx(bar, (unsigned)(F.tmpl_bytes + (size_t)nblk * F.vstride * sizeof(VT)) + extra);
     bulk_g2s(psm + 16, F.tmpl, (unsigned)F.tmpl_bytes, bar);
     for (int w = 0; w < nblk; ++w)
       bulk_g2s(psm + 16 + align16((size_t)F.tmpl_bytes) + (size_t)w * (fbytes + xbytes),
@@ -735,6 +740,11 @@ cudaError_t launch_patch_gather(const DevPatch &F, double *z, cudaStream_t s) {
 
 int patch_warps_per_block(const DevPatch &F) {
   return F.vt == 0 ? warps_per_block<double>(F) : warps_per_block<float>(F);
+}
+
+cudaError_t patch_inject_timeout(int on) {
+  const int v = on ? 1 : 0;
+  return cudaMemcpyToSymbol(g_patch_inject, &v, sizeof(int));
 }
 
 int patch_timeouts(cudaError_t *err) {

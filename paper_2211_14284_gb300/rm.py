@@ -31,7 +31,7 @@ STATUS = {0: "RM_OK", 1: "RM_ERR_ARG", 2: "RM_ERR_CUDA", 3: "RM_ERR_OOM",
 
 EXPORTED = ["rm_default_options", "rm_setup", "rm_ndofs", "rm_layout", "rm_history", "rm_apply",
             "rm_precondition", "rm_solve", "rm_stats", "rm_destroy", "rm_last_error",
-            "rm_precondition_noalloc", "rm_batch_setup", "rm_batch_ndofs", "rm_batch_solve",
+            "rm_precondition_noalloc", "rm_debug_patch_timeout", "rm_batch_setup", "rm_batch_ndofs", "rm_batch_solve",
             "rm_batch_destroy", "rm_batch_last_error", "rm_default_train_options",
             "rm_corrector_train", "rm_corrector_save", "rm_corrector_load", "rm_corrector_use",
             "rm_net_create", "rm_net_num_params", "rm_net_get_params", "rm_net_set_params",
@@ -120,6 +120,7 @@ def load():
     lib.rm_apply.argtypes = [vp, vp, vp]
     lib.rm_precondition.argtypes = [vp, vp, vp]
     lib.rm_precondition_noalloc.argtypes = [vp, vp, vp]
+    lib.rm_debug_patch_timeout.argtypes = [ctypes.c_int]
     lib.rm_solve.argtypes = [vp, vp, vp, ctypes.POINTER(RmInfo)]
     lib.rm_destroy.argtypes = [vp]
     lib.rm_destroy.restype = None
@@ -167,6 +168,15 @@ def load():
     lib.rm_hodge_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
+
+
+def debug_patch_timeout(on):
+    """rm_debug_patch_timeout: a testing aid that makes the warp-per-patch
+    kernels' bounded waits give up (on=True) or restores them (on=False)."""
+    lib = load()
+    rc = lib.rm_debug_patch_timeout(1 if on else 0)
+    if rc != 0:
+        raise RmError(rc, lib.rm_last_error(None).decode())
 
 
 def _ptr(t):

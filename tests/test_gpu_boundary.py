@@ -194,3 +194,26 @@ def test_maxwell_two_material_robust():
         assert info["status"] == "RM_OK", (bair, info)
         its[bair] = info["iterations"]
     assert max(its.values()) <= 2.5 * min(its.values()), its
+
+
+def test_patch_wait_timeout_is_reported():
+    """A bounded device wait that runs out (made to, on the host's request:
+    the warp patch kernel expects 16 bytes that never arrive) ends the
+    kernel after ~1 s per CTA, rm_solve reports RM_ERR_TIMEOUT, and the
+    context stays usable: with the aid switched off the same handle solves
+    normally."""
+    from paper_2211_14284_gb300.rm import Solver, debug_patch_timeout
+    n, p = 2, 3
+    s = Solver(0, n, p, static_condensation=1, factor=1, rtol=1e-8, max_it=2)
+    b = torch.tensor(inputs.normal_rhs(s.size, 90), dtype=torch.float64, device="cuda")
+    x = torch.zeros_like(b)
+    debug_patch_timeout(True)
+    try:
+        info = s.solve(b, x, check=False)
+    finally:
+        debug_patch_timeout(False)
+    assert info["status"] == "RM_ERR_TIMEOUT"
+    s2 = Solver(0, n, p, static_condensation=1, factor=1, rtol=1e-8, max_it=200)
+    x.zero_()
+    info = s2.solve(b, x)
+    assert info["status"] == "RM_OK" and info["rel_res_l2"] <= 1e-8
