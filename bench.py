@@ -270,7 +270,8 @@ def run_ours(args):
         for sname, k, sopt in SPACES:
             solvers[(vname, sname)] = Solver(k, n, p, vertices=X, alpha=al, beta=be,
                                              stream=space_streams[sname], rtol=1e-8, max_it=1000,
-                                             profile=1, **sopt, **vopt)
+                                             profile=1, deterministic=1 if args.deterministic else 0,
+                                             **sopt, **vopt)
     setup_s = time.time() - t0
     sizes = {sname: solvers[(HEADLINE, sname)].size for sname, _, _ in SPACES}
     dofs = sum(sizes.values())
@@ -412,6 +413,8 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "lattice_dofs": dofs,
                    "lattice_dofs_per_space": sizes, "rtol": 1e-8,
                    "variant": HEADLINE, "l2": "flushed between steps (256 MiB write)",
+                   "relaxation": "deterministic (fixed-order patch sums, branches in sequence)"
+                                 if args.deterministic else "default (atomic patch scatters, concurrent branches)",
                    "parallelism": "independent replicas" if world > 1 else "1 GPU",
                    "spaces": "one after another" if args.sequential else "concurrent (a stream and host thread each)",
                    "iterations": head["iterations"], "setup_s": setup_s},
@@ -767,6 +770,8 @@ def main():
     ap.add_argument("--oracle-full-worker", metavar="CACHE_DIR", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--no-apply-kernels", action="store_true",
                     help="skip timing the Cartesian operator apply on its own workloads")
+    ap.add_argument("--deterministic", action="store_true",
+                    help="bitwise-reproducible relaxation (rm_options.deterministic = 1) in every variant")
     ap.add_argument("--sequential", action="store_true",
                     help="solve the two problems of a step one after another on one host thread "
                          "(for profilers, which serialise kernels anyway)")
